@@ -1,0 +1,1627 @@
+/*
+ * adgi_oracle.c -- plain, slow CPU oracle of the ADGI per-frame probe update.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and the
+ * cpu_baseline / reference legs of bench.py may load this library.  It shares
+ * no source, header, table or constant generator with the CUDA library; the
+ * two are written independently from the paper (Datta, Goli, Zhang,
+ * "Adaptive Dynamic Global Illumination", arXiv 2301.05125) and from the
+ * published methods cited below.
+ *
+ * Two numeric paths:
+ *   - an FP32 path for every floating-point computation whose result is turned
+ *     into an integer or a discrete decision (pilot and main ray directions,
+ *     ray/triangle hits and the hit index, shadow-ray visibility, the
+ *     quantised heuristics q_v / q_r / q_c, texel binning).  It uses only
+ *     IEEE +, -, *, / and sqrt, in the stated order, compiled with
+ *     -ffp-contract=off, so any correct IEEE implementation gets the same bits;
+ *   - an FP64 path for everything that is compared with a tolerance
+ *     (shading, multi-bounce query, blending, the irradiance query).
+ *
+ * Section map (paper):
+ *   Sec. 4.1 Eq. cameraD        -> q_c (camera distance heuristic f_c)
+ *   Sec. 4.1 Eq. ProbeVis       -> q_v (f_v = exp(-2t/s), t = trace(p,-w))
+ *   Sec. 4.1 "Incoming radiance"-> q_r (f_r = min(r,beta)/beta, beta = 5)
+ *   Sec. 4.1 Eq. tempGradVis, tempGradIrr, Tr, spatial convolution
+ *                               -> temporal trigger + 5x5x5 x octant sum
+ *   Sec. 4.2 Eq. priorDynamic   -> f_d = f_c f_v (f_dv + mu f_dr), mu = 2
+ *   Sec. 4.4 "Improving construction efficiency" -> pilot rays, AABB pattern
+ *   Sec. 3.5 Alg. ApproxAlgo + Sec. 4.7 Alg. MovingAvgUpdate -> nearest-texel
+ *                                 moving average with hysteresis
+ *   Sec. 3.6 (MCMC analysis)    -> texel stores the texel-average of g
+ *   Sec. 3.1 (DDGI background)  -> octahedral tiles with borders, 8-probe
+ *                                 trilinear x Chebyshev query
+ *   Sec. 3.4 (fixed sample budget) -> integer allocation under a fixed total
+ * Published methods restated here: SplitMix64 (Steele, Lea, Flood, OOPSLA
+ * 2014); watertight ray/triangle intersection (Woop, Benthin, Wald, JCGT
+ * 2(1), 2013); spherical Fibonacci point sets (Keinert et al., 2015);
+ * binned-SAH BVH construction (Wald, 2007).
+ *
+ * Parity pins: every exported function is pinned by a -m "not gpu" test in
+ * tests/test_oracle_*.py against closed forms, invariants or brute force.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <pthread.h>
+
+#define EXPORT __attribute__((visibility("default")))
+
+/* ------------------------------------------------------------------------ */
+/* SplitMix64 output function (Steele et al. 2014): one generator step from  */
+/* state x.  Counter-based use: every random number the method draws is      */
+/* sm(sm(sm(seed) ^ a) ^ b) for its own counters a, b.                        */
+/* ------------------------------------------------------------------------ */
+EXPORT uint64_t orc_splitmix64(uint64_t x)
+{
+    uint64_t z = x + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+static uint64_t hash3(uint64_t a, uint64_t b, uint64_t c)
+{
+    return orc_splitmix64(orc_splitmix64(orc_splitmix64(a) ^ b) ^ c);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Pilot ray directions (Sec. 4.4): one stratified random direction per      */
+/* octant; the directions depend on the frame pair floor(t/2) only, so the   */
+/* two frames of a pair (A A B B C C ...) trace identical rays.              */
+/* Octant index o = [x<0] | [y<0]<<1 | [z<0]<<2.                              */
+/* ------------------------------------------------------------------------ */
+EXPORT void orc_pilot_dir(uint64_t seed, uint64_t frame, uint32_t probe, int octant, float out[3])
+{
+    uint64_t pair = frame >> 1;
+    uint64_t h = hash3(seed, pair, (uint64_t)probe * 8u + (uint64_t)octant);
+    const float two_m24 = 5.9604644775390625e-08f; /* 2^-24 */
+    float u1 = (float)(uint32_t)(h >> 40) * two_m24;
+    float u2 = (float)(uint32_t)((h >> 16) & 0xFFFFFFu) * two_m24;
+    if (u1 + u2 > 1.0f) {
+        float a = 1.0f - u2;
+        float b = 1.0f - u1;
+        u1 = a;
+        u2 = b;
+    }
+    float v[3];
+    v[0] = u1;
+    v[1] = u2;
+    v[2] = (1.0f - u1) - u2;
+    if (octant & 1) v[0] = -v[0];
+    if (octant & 2) v[1] = -v[1];
+    if (octant & 4) v[2] = -v[2];
+    float len2 = (v[0] * v[0] + v[1] * v[1]) + v[2] * v[2];
+    float len = sqrtf(len2);
+    out[0] = v[0] / len;
+    out[1] = v[1] / len;
+    out[2] = v[2] / len;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Per-frame random rotation of the main-ray pattern (DDGI's rotated         */
+/* spiral, Sec. 3.1).  A uniform unit quaternion by rejection from the 4-ball */
+/* in FP64, converted to a matrix in FP64 and rounded to FP32.               */
+/* ------------------------------------------------------------------------ */
+EXPORT void orc_frame_rotation(uint64_t seed, uint64_t frame, float R[9])
+{
+    const double two_m53 = 1.1102230246251565e-16; /* 2^-53 */
+    double q[4] = {1.0, 0.0, 0.0, 0.0};
+    for (uint64_t attempt = 0; attempt < 1000; ++attempt) {
+        double c[4];
+        for (int k = 0; k < 4; ++k) {
+            uint64_t h = hash3(seed ^ 0x524F54ull, frame, attempt * 4u + (uint64_t)k);
+            c[k] = ((double)(h >> 11) * two_m53) * 2.0 - 1.0;
+        }
+        double n2 = ((c[0] * c[0] + c[1] * c[1]) + c[2] * c[2]) + c[3] * c[3];
+        if (n2 > 1e-6 && n2 <= 1.0) {
+            double n = sqrt(n2);
+            for (int k = 0; k < 4; ++k) q[k] = c[k] / n;
+            break;
+        }
+    }
+    double w = q[0], x = q[1], y = q[2], z = q[3];
+    double m[9];
+    m[0] = 1.0 - 2.0 * (y * y + z * z);
+    m[1] = 2.0 * (x * y - w * z);
+    m[2] = 2.0 * (x * z + w * y);
+    m[3] = 2.0 * (x * y + w * z);
+    m[4] = 1.0 - 2.0 * (x * x + z * z);
+    m[5] = 2.0 * (y * z - w * x);
+    m[6] = 2.0 * (x * z - w * y);
+    m[7] = 2.0 * (y * z + w * x);
+    m[8] = 1.0 - 2.0 * (x * x + y * y);
+    for (int k = 0; k < 9; ++k) R[k] = (float)m[k];
+}
+
+/* ------------------------------------------------------------------------ */
+/* Spherical Fibonacci point set with m points (Keinert et al. 2015):        */
+/* z_i = 1 - (2i+1)/m, phi_i = i * golden angle, golden angle = pi(3-sqrt5). */
+/* cos/sin(phi_i) by the exact complex recurrence from cos/sin(golden angle) */
+/* so only IEEE basic operations are used.  FP64, rounded to FP32.          */
+/* ------------------------------------------------------------------------ */
+static const double GA_COS = -0.7373688780783197;
+static const double GA_SIN = 0.6754902942615238;
+
+EXPORT void orc_sf_points(int m, float* out /* m*3 */)
+{
+    double c = 1.0, s = 0.0;
+    for (int i = 0; i < m; ++i) {
+        double z = 1.0 - (2.0 * (double)i + 1.0) / (double)m;
+        double r2 = 1.0 - z * z;
+        double r = r2 > 0.0 ? sqrt(r2) : 0.0;
+        out[3 * i + 0] = (float)(r * c);
+        out[3 * i + 1] = (float)(r * s);
+        out[3 * i + 2] = (float)z;
+        double cn = c * GA_COS - s * GA_SIN;
+        double sn = s * GA_COS + c * GA_SIN;
+        c = cn;
+        s = sn;
+    }
+}
+
+/* FP32 rotation d = R * v in a fixed order (row-major R). */
+static void rotate_f32(const float R[9], const float v[3], float d[3])
+{
+    d[0] = (R[0] * v[0] + R[1] * v[1]) + R[2] * v[2];
+    d[1] = (R[3] * v[0] + R[4] * v[1]) + R[5] * v[2];
+    d[2] = (R[6] * v[0] + R[7] * v[1]) + R[8] * v[2];
+}
+
+/* ------------------------------------------------------------------------ */
+/* Octahedral map (Sec. 3.1; DDGI's spherical mapping of probe texels).      */
+/* encode: p = w.xy / (|x|+|y|+|z|); lower hemisphere folded outward with    */
+/* sign(0) = +1.  decode is its inverse.  FP64 versions for the reference     */
+/* path, an FP32 version for texel binning (a discrete decision).            */
+/* ------------------------------------------------------------------------ */
+static double sgn_d(double v) { return v >= 0.0 ? 1.0 : -1.0; }
+static float sgn_f(float v) { return v >= 0.0f ? 1.0f : -1.0f; }
+
+EXPORT void orc_oct_encode(const double w[3], double p[2])
+{
+    double l1 = (fabs(w[0]) + fabs(w[1])) + fabs(w[2]);
+    double px = w[0] / l1, py = w[1] / l1;
+    if (w[2] < 0.0) {
+        double qx = (1.0 - fabs(py)) * sgn_d(px);
+        double qy = (1.0 - fabs(px)) * sgn_d(py);
+        px = qx;
+        py = qy;
+    }
+    p[0] = px;
+    p[1] = py;
+}
+
+EXPORT void orc_oct_decode(const double p[2], double w[3])
+{
+    double x = p[0], y = p[1];
+    double z = (1.0 - fabs(x)) - fabs(y);
+    if (z < 0.0) {
+        double nx = (1.0 - fabs(y)) * sgn_d(x);
+        double ny = (1.0 - fabs(x)) * sgn_d(y);
+        x = nx;
+        y = ny;
+    }
+    double n = sqrt((x * x + y * y) + z * z);
+    w[0] = x / n;
+    w[1] = y / n;
+    w[2] = z / n;
+}
+
+static void oct_encode_f32(const float w[3], float p[2])
+{
+    float l1 = (fabsf(w[0]) + fabsf(w[1])) + fabsf(w[2]);
+    float px = w[0] / l1, py = w[1] / l1;
+    if (w[2] < 0.0f) {
+        float qx = (1.0f - fabsf(py)) * sgn_f(px);
+        float qy = (1.0f - fabsf(px)) * sgn_f(py);
+        px = qx;
+        py = qy;
+    }
+    p[0] = px;
+    p[1] = py;
+}
+
+/* Nearest interior texel of direction w in a tile with interior n x n and a */
+/* one-texel border (Alg. ApproxAlgo: a sample updates the closest entry).   */
+/* Returns row*(n+2)+col with row from p.y and col from p.x, both in 1..n.   */
+EXPORT int orc_texel_of_dir(const float w[3], int n)
+{
+    float p[2];
+    oct_encode_f32(w, p);
+    float fn = (float)n;
+    int cx = (int)floorf(((p[0] + 1.0f) * 0.5f) * fn);
+    int cy = (int)floorf(((p[1] + 1.0f) * 0.5f) * fn);
+    if (cx < 0) cx = 0;
+    if (cx > n - 1) cx = n - 1;
+    if (cy < 0) cy = 0;
+    if (cy > n - 1) cy = n - 1;
+    return (cy + 1) * (n + 2) + (cx + 1);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Watertight ray/triangle intersection (Woop, Benthin, Wald 2013), FP32.    */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    float o[3], d[3];
+    int kx, ky, kz;
+    float Sx, Sy, Sz;
+} wray;
+
+static void wray_setup(wray* r, const float o[3], const float d[3])
+{
+    for (int k = 0; k < 3; ++k) {
+        r->o[k] = o[k];
+        r->d[k] = d[k];
+    }
+    int kz = 0;
+    if (fabsf(d[1]) > fabsf(d[kz])) kz = 1;
+    if (fabsf(d[2]) > fabsf(d[kz])) kz = 2;
+    int kx = kz + 1;
+    if (kx == 3) kx = 0;
+    int ky = kx + 1;
+    if (ky == 3) ky = 0;
+    if (d[kz] < 0.0f) {
+        int t = kx;
+        kx = ky;
+        ky = t;
+    }
+    r->kx = kx;
+    r->ky = ky;
+    r->kz = kz;
+    r->Sx = d[kx] / d[kz];
+    r->Sy = d[ky] / d[kz];
+    r->Sz = 1.0f / d[kz];
+}
+
+/* Returns 1 and (t, det) when the ray's line crosses the triangle; the caller */
+/* applies its own t interval.  det < 0 <=> the ray meets the back face      */
+/* (geometric normal (B-A)x(C-A) points along the ray); pinned by a test.    */
+static int wtri(const wray* r, const float* A, const float* B, const float* C, float* t_out, float* det_out)
+{
+    float a[3], b[3], c[3];
+    for (int k = 0; k < 3; ++k) {
+        a[k] = A[k] - r->o[k];
+        b[k] = B[k] - r->o[k];
+        c[k] = C[k] - r->o[k];
+    }
+    const int kx = r->kx, ky = r->ky, kz = r->kz;
+    float Ax = a[kx] - r->Sx * a[kz];
+    float Ay = a[ky] - r->Sy * a[kz];
+    float Bx = b[kx] - r->Sx * b[kz];
+    float By = b[ky] - r->Sy * b[kz];
+    float Cx = c[kx] - r->Sx * c[kz];
+    float Cy = c[ky] - r->Sy * c[kz];
+    float U = Cx * By - Cy * Bx;
+    float V = Ax * Cy - Ay * Cx;
+    float W = Bx * Ay - By * Ax;
+    if (U == 0.0f || V == 0.0f || W == 0.0f) {
+        double CxBy = (double)Cx * (double)By, CyBx = (double)Cy * (double)Bx;
+        double AxCy = (double)Ax * (double)Cy, AyCx = (double)Ay * (double)Cx;
+        double BxAy = (double)Bx * (double)Ay, ByAx = (double)By * (double)Ax;
+        U = (float)(CxBy - CyBx);
+        V = (float)(AxCy - AyCx);
+        W = (float)(BxAy - ByAx);
+    }
+    if ((U < 0.0f || V < 0.0f || W < 0.0f) && (U > 0.0f || V > 0.0f || W > 0.0f)) return 0;
+    float det = (U + V) + W;
+    if (det == 0.0f) return 0;
+    float Az = r->Sz * a[kz];
+    float Bz = r->Sz * b[kz];
+    float Cz = r->Sz * c[kz];
+    float T = (U * Az + V * Bz) + W * Cz;
+    *t_out = T / det;
+    *det_out = det;
+    return 1;
+}
+
+EXPORT int orc_intersect_tri(const float o[3], const float d[3], const float A[3], const float B[3],
+                             const float C[3], float* t_out, float* det_out)
+{
+    wray r;
+    wray_setup(&r, o, d);
+    return wtri(&r, A, B, C, t_out, det_out);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Scene + CPU BVH.  The BVH only accelerates: its answer must equal brute   */
+/* force exactly (pinned), so its boxes are enlarged and its pruning slack.  */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    double lo[3], hi[3];
+    int left, right; /* children; leaf when count > 0 */
+    int first, count;
+} bnode;
+
+typedef struct {
+    int nt;
+    const float* V;   /* vertices xyz */
+    const int* I;     /* triangle indices */
+    bnode* nodes;
+    int n_nodes;
+    int* order;       /* triangle ids in leaf order */
+    double eps;       /* absolute box enlargement */
+} cbvh;
+
+static void tri_bounds(const float* V, const int* I, int t, double lo[3], double hi[3])
+{
+    for (int k = 0; k < 3; ++k) {
+        lo[k] = 1e300;
+        hi[k] = -1e300;
+    }
+    for (int v = 0; v < 3; ++v) {
+        const float* p = V + 3 * (size_t)I[3 * (size_t)t + v];
+        for (int k = 0; k < 3; ++k) {
+            if (p[k] < lo[k]) lo[k] = p[k];
+            if (p[k] > hi[k]) hi[k] = p[k];
+        }
+    }
+}
+
+typedef struct {
+    double lo[3], hi[3], c[3];
+} tbox;
+
+static double area_of(const double lo[3], const double hi[3])
+{
+    double dx = hi[0] - lo[0], dy = hi[1] - lo[1], dz = hi[2] - lo[2];
+    if (dx < 0 || dy < 0 || dz < 0) return 0.0;
+    return 2.0 * (dx * dy + dy * dz + dz * dx);
+}
+
+static int bvh_build_rec(cbvh* b, tbox* tb, int* ids, int first, int count, int* next)
+{
+    int me = (*next)++;
+    bnode* n = &b->nodes[me];
+    for (int k = 0; k < 3; ++k) {
+        n->lo[k] = 1e300;
+        n->hi[k] = -1e300;
+    }
+    double clo[3] = {1e300, 1e300, 1e300}, chi[3] = {-1e300, -1e300, -1e300};
+    for (int i = first; i < first + count; ++i) {
+        tbox* t = &tb[ids[i]];
+        for (int k = 0; k < 3; ++k) {
+            if (t->lo[k] < n->lo[k]) n->lo[k] = t->lo[k];
+            if (t->hi[k] > n->hi[k]) n->hi[k] = t->hi[k];
+            if (t->c[k] < clo[k]) clo[k] = t->c[k];
+            if (t->c[k] > chi[k]) chi[k] = t->c[k];
+        }
+    }
+    for (int k = 0; k < 3; ++k) {
+        n->lo[k] -= b->eps;
+        n->hi[k] += b->eps;
+    }
+    if (count <= 4) {
+        n->left = n->right = -1;
+        n->first = first;
+        n->count = count;
+        return me;
+    }
+    /* binned SAH over centroids, 16 bins per axis */
+    enum { NB = 16 };
+    int best_axis = -1, best_split = -1;
+    double best_cost = 1e300;
+    for (int ax = 0; ax < 3; ++ax) {
+        double ext = chi[ax] - clo[ax];
+        if (!(ext > 0.0)) continue;
+        int cnt[NB] = {0};
+        double blo[NB][3], bhi[NB][3];
+        for (int i = 0; i < NB; ++i)
+            for (int k = 0; k < 3; ++k) {
+                blo[i][k] = 1e300;
+                bhi[i][k] = -1e300;
+            }
+        for (int i = first; i < first + count; ++i) {
+            tbox* t = &tb[ids[i]];
+            int bi = (int)((t->c[ax] - clo[ax]) / ext * NB);
+            if (bi >= NB) bi = NB - 1;
+            if (bi < 0) bi = 0;
+            cnt[bi]++;
+            for (int k = 0; k < 3; ++k) {
+                if (t->lo[k] < blo[bi][k]) blo[bi][k] = t->lo[k];
+                if (t->hi[k] > bhi[bi][k]) bhi[bi][k] = t->hi[k];
+            }
+        }
+        for (int s = 1; s < NB; ++s) {
+            double llo[3] = {1e300, 1e300, 1e300}, lhi[3] = {-1e300, -1e300, -1e300};
+            double rlo[3] = {1e300, 1e300, 1e300}, rhi[3] = {-1e300, -1e300, -1e300};
+            int lc = 0, rc = 0;
+            for (int i = 0; i < NB; ++i) {
+                double* lo = i < s ? llo : rlo;
+                double* hi = i < s ? lhi : rhi;
+                if (i < s)
+                    lc += cnt[i];
+                else
+                    rc += cnt[i];
+                for (int k = 0; k < 3; ++k) {
+                    if (blo[i][k] < lo[k]) lo[k] = blo[i][k];
+                    if (bhi[i][k] > hi[k]) hi[k] = bhi[i][k];
+                }
+            }
+            if (lc == 0 || rc == 0) continue;
+            double cost = area_of(llo, lhi) * lc + area_of(rlo, rhi) * rc;
+            if (cost < best_cost) {
+                best_cost = cost;
+                best_axis = ax;
+                best_split = s;
+            }
+        }
+    }
+    int mid;
+    if (best_axis < 0) {
+        mid = first + count / 2; /* all centroids equal: split by position */
+    } else {
+        double ext = chi[best_axis] - clo[best_axis];
+        int i = first, j = first + count - 1;
+        while (i <= j) {
+            tbox* t = &tb[ids[i]];
+            int bi = (int)((t->c[best_axis] - clo[best_axis]) / ext * NB);
+            if (bi >= NB) bi = NB - 1;
+            if (bi < 0) bi = 0;
+            if (bi < best_split) {
+                ++i;
+            } else {
+                int tmp = ids[i];
+                ids[i] = ids[j];
+                ids[j] = tmp;
+                --j;
+            }
+        }
+        mid = i;
+        if (mid == first || mid == first + count) mid = first + count / 2;
+    }
+    n->count = 0;
+    n->first = -1;
+    int l = bvh_build_rec(b, tb, ids, first, mid - first, next);
+    int r = bvh_build_rec(b, tb, ids, mid, first + count - mid, next);
+    b->nodes[me].left = l;
+    b->nodes[me].right = r;
+    return me;
+}
+
+static void cbvh_free(cbvh* b)
+{
+    free(b->nodes);
+    free(b->order);
+    b->nodes = NULL;
+    b->order = NULL;
+    b->n_nodes = 0;
+}
+
+static int cbvh_build(cbvh* b, const float* V, int nv, const int* I, int nt)
+{
+    cbvh_free(b);
+    b->nt = nt;
+    b->V = V;
+    b->I = I;
+    if (nt == 0) return 0;
+    tbox* tb = (tbox*)malloc(sizeof(tbox) * (size_t)nt);
+    int* ids = (int*)malloc(sizeof(int) * (size_t)nt);
+    if (!tb || !ids) {
+        free(tb);
+        free(ids);
+        return -1;
+    }
+    double slo[3] = {1e300, 1e300, 1e300}, shi[3] = {-1e300, -1e300, -1e300};
+    for (int v = 0; v < nv; ++v)
+        for (int k = 0; k < 3; ++k) {
+            double x = V[3 * (size_t)v + k];
+            if (x < slo[k]) slo[k] = x;
+            if (x > shi[k]) shi[k] = x;
+        }
+    double ext = 0.0, mag = 0.0;
+    for (int k = 0; k < 3; ++k) {
+        if (shi[k] - slo[k] > ext) ext = shi[k] - slo[k];
+        if (fabs(slo[k]) > mag) mag = fabs(slo[k]);
+        if (fabs(shi[k]) > mag) mag = fabs(shi[k]);
+    }
+    b->eps = 1e-5 * (ext > mag ? ext : mag) + 1e-30;
+    for (int t = 0; t < nt; ++t) {
+        tri_bounds(V, I, t, tb[t].lo, tb[t].hi);
+        for (int k = 0; k < 3; ++k) tb[t].c[k] = 0.5 * (tb[t].lo[k] + tb[t].hi[k]);
+        ids[t] = t;
+    }
+    b->nodes = (bnode*)malloc(sizeof(bnode) * (size_t)(2 * nt));
+    if (!b->nodes) {
+        free(tb);
+        free(ids);
+        return -1;
+    }
+    int next = 0;
+    bvh_build_rec(b, tb, ids, 0, nt, &next);
+    b->n_nodes = next;
+    b->order = ids;
+    free(tb);
+    return 0;
+}
+
+/* slab test in FP64 against [0, tlim]; conservative by the box enlargement */
+static int box_hit(const bnode* n, const float o[3], const float d[3], double tlim)
+{
+    double tn = 0.0, tf = tlim;
+    for (int k = 0; k < 3; ++k) {
+        double ok = o[k], dk = d[k];
+        if (dk == 0.0) {
+            if (ok < n->lo[k] || ok > n->hi[k]) return 0;
+            continue;
+        }
+        double inv = 1.0 / dk;
+        double t0 = (n->lo[k] - ok) * inv, t1 = (n->hi[k] - ok) * inv;
+        if (t0 > t1) {
+            double t = t0;
+            t0 = t1;
+            t1 = t;
+        }
+        if (t0 > tn) tn = t0;
+        if (t1 < tf) tf = t1;
+        if (tn > tf) return 0;
+    }
+    return 1;
+}
+
+typedef struct {
+    float t;
+    int tri;
+    float det;
+} hitrec;
+
+/* nearest hit with t in (tmin, tmax]; ties on t broken by the smaller index */
+static hitrec closest_brute(const float* V, const int* I, int nt, const float o[3], const float d[3], float tmin,
+                            float tmax)
+{
+    wray r;
+    wray_setup(&r, o, d);
+    hitrec h = {tmax, -1, 0.0f};
+    for (int t = 0; t < nt; ++t) {
+        float tt, det;
+        const int* ix = I + 3 * (size_t)t;
+        if (!wtri(&r, V + 3 * (size_t)ix[0], V + 3 * (size_t)ix[1], V + 3 * (size_t)ix[2], &tt, &det)) continue;
+        if (!(tt > tmin)) continue;
+        if (h.tri < 0 ? !(tt <= tmax) : !(tt < h.t)) continue;
+        h.t = tt;
+        h.tri = t;
+        h.det = det;
+    }
+    return h;
+}
+
+static hitrec closest_bvh(const cbvh* b, const float o[3], const float d[3], float tmin, float tmax)
+{
+    hitrec h = {tmax, -1, 0.0f};
+    if (b->nt == 0) return h;
+    wray r;
+    wray_setup(&r, o, d);
+    int stack[256];
+    int sp = 0;
+    stack[sp++] = 0;
+    while (sp) {
+        const bnode* n = &b->nodes[stack[--sp]];
+        double lim = (double)h.t * (1.0 + 1e-4) + 1e-30;
+        if (!box_hit(n, o, d, lim)) continue;
+        if (n->count > 0) {
+            for (int i = n->first; i < n->first + n->count; ++i) {
+                int t = b->order[i];
+                const int* ix = b->I + 3 * (size_t)t;
+                float tt, det;
+                if (!wtri(&r, b->V + 3 * (size_t)ix[0], b->V + 3 * (size_t)ix[1], b->V + 3 * (size_t)ix[2], &tt, &det))
+                    continue;
+                if (!(tt > tmin)) continue;
+                int better;
+                if (h.tri < 0)
+                    better = tt <= tmax;
+                else
+                    better = tt < h.t || (tt == h.t && t < h.tri);
+                if (!better) continue;
+                h.t = tt;
+                h.tri = t;
+                h.det = det;
+            }
+        } else {
+            stack[sp++] = n->left;
+            stack[sp++] = n->right;
+        }
+    }
+    return h;
+}
+
+/* any hit with t strictly inside (tlo, thi) */
+static int anyhit_brute(const float* V, const int* I, int nt, const float o[3], const float d[3], float tlo, float thi)
+{
+    wray r;
+    wray_setup(&r, o, d);
+    for (int t = 0; t < nt; ++t) {
+        float tt, det;
+        const int* ix = I + 3 * (size_t)t;
+        if (!wtri(&r, V + 3 * (size_t)ix[0], V + 3 * (size_t)ix[1], V + 3 * (size_t)ix[2], &tt, &det)) continue;
+        if (tt > tlo && tt < thi) return 1;
+    }
+    return 0;
+}
+
+static int anyhit_bvh(const cbvh* b, const float o[3], const float d[3], float tlo, float thi)
+{
+    if (b->nt == 0) return 0;
+    wray r;
+    wray_setup(&r, o, d);
+    int stack[256];
+    int sp = 0;
+    stack[sp++] = 0;
+    double lim = (double)thi * (1.0 + 1e-4) + 1e-30;
+    if (isinf(thi)) lim = 1e300;
+    while (sp) {
+        const bnode* n = &b->nodes[stack[--sp]];
+        if (!box_hit(n, o, d, lim)) continue;
+        if (n->count > 0) {
+            for (int i = n->first; i < n->first + n->count; ++i) {
+                int t = b->order[i];
+                const int* ix = b->I + 3 * (size_t)t;
+                float tt, det;
+                if (!wtri(&r, b->V + 3 * (size_t)ix[0], b->V + 3 * (size_t)ix[1], b->V + 3 * (size_t)ix[2], &tt, &det))
+                    continue;
+                if (tt > tlo && tt < thi) return 1;
+            }
+        } else {
+            stack[sp++] = n->left;
+            stack[sp++] = n->right;
+        }
+    }
+    return 0;
+}
+
+/* Stand-alone tracing entry points (used by the intersection pins). */
+EXPORT void orc_trace_closest(const float* V, int nv, const int* I, int nt, int n_rays, const float* O, const float* D,
+                              float tmin, float tmax, int use_bvh, float* t_out, int* tri_out, float* det_out)
+{
+    cbvh b;
+    memset(&b, 0, sizeof(b));
+    if (use_bvh) cbvh_build(&b, V, nv, I, nt);
+    for (int i = 0; i < n_rays; ++i) {
+        hitrec h = use_bvh ? closest_bvh(&b, O + 3 * (size_t)i, D + 3 * (size_t)i, tmin, tmax)
+                           : closest_brute(V, I, nt, O + 3 * (size_t)i, D + 3 * (size_t)i, tmin, tmax);
+        t_out[i] = h.t;
+        tri_out[i] = h.tri;
+        if (det_out) det_out[i] = h.det;
+    }
+    cbvh_free(&b);
+}
+
+EXPORT void orc_trace_any(const float* V, int nv, const int* I, int nt, int n_rays, const float* O, const float* D,
+                          float tlo, float thi, int use_bvh, uint8_t* out)
+{
+    cbvh b;
+    memset(&b, 0, sizeof(b));
+    if (use_bvh) cbvh_build(&b, V, nv, I, nt);
+    for (int i = 0; i < n_rays; ++i)
+        out[i] = (uint8_t)(use_bvh ? anyhit_bvh(&b, O + 3 * (size_t)i, D + 3 * (size_t)i, tlo, thi)
+                                   : anyhit_brute(V, I, nt, O + 3 * (size_t)i, D + 3 * (size_t)i, tlo, thi));
+    cbvh_free(&b);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Ray allocation under a fixed total budget (Sec. 3.4: the number of        */
+/* samples per frame is an input, independent of the probe count).  The     */
+/* paper draws the samples with Metropolis chains; this oracle follows the  */
+/* deterministic reading: integer proportional shares of the extra budget   */
+/* by the change weight W_p, with per-probe caps, then the remainder one by */
+/* one in probe-index order.                                                */
+/*   n_p = m0 + extra_p, m0 = max(rays_min, 8), sum n_p = rays_avg * P.      */
+/*   off[p] = exclusive prefix of the main-ray counts n_p - 8.               */
+/* Returns 0, or -1 when the budget cannot be met.                           */
+/* ------------------------------------------------------------------------ */
+#define ORC_ALLOC_MAX_ITERS 64
+
+EXPORT int orc_allocate(const uint32_t* W, int P, int avg, int rmin, int rmax, uint32_t* n_out, uint32_t* off_out)
+{
+    if (P <= 0) return -1;
+    int m0 = rmin > 8 ? rmin : 8;
+    if (avg < m0 || avg > rmax || m0 > rmax) return -1;
+    uint64_t B = (uint64_t)avg * (uint64_t)P;
+    uint64_t E = B - (uint64_t)m0 * (uint64_t)P;
+    uint64_t cap = (uint64_t)(rmax - m0);
+    uint64_t* extra = (uint64_t*)calloc((size_t)P, sizeof(uint64_t));
+    uint8_t* inU = (uint8_t*)calloc((size_t)P, 1);
+    if (!extra || !inU) {
+        free(extra);
+        free(inU);
+        return -1;
+    }
+    uint64_t S = 0;
+    for (int p = 0; p < P; ++p) S += W[p];
+    if (S == 0) {
+        uint64_t q = E / (uint64_t)P, r = E % (uint64_t)P;
+        for (int p = 0; p < P; ++p) extra[p] = q + ((uint64_t)p < r ? 1u : 0u);
+    } else {
+        uint64_t Erem = E;
+        for (int p = 0; p < P; ++p) inU[p] = W[p] > 0 && cap > 0;
+        for (int it = 0; it < ORC_ALLOC_MAX_ITERS; ++it) {
+            uint64_t SU = 0;
+            for (int p = 0; p < P; ++p)
+                if (inU[p]) SU += W[p];
+            if (SU == 0 || Erem == 0) break;
+            uint64_t given = 0;
+            for (int p = 0; p < P; ++p) {
+                if (!inU[p]) continue;
+                uint64_t share = Erem * (uint64_t)W[p] / SU;
+                uint64_t room = cap - extra[p];
+                uint64_t a = share < room ? share : room;
+                extra[p] += a;
+                given += a;
+            }
+            if (given == 0) break;
+            Erem -= given;
+            for (int p = 0; p < P; ++p)
+                if (inU[p] && extra[p] == cap) inU[p] = 0;
+        }
+        /* remainder: one ray each, probe-index order, probes with W > 0 first */
+        while (Erem > 0) {
+            int anyA = 0;
+            for (int p = 0; p < P; ++p)
+                if (W[p] > 0 && extra[p] < cap) {
+                    anyA = 1;
+                    break;
+                }
+            for (int p = 0; p < P && Erem > 0; ++p) {
+                int elig = extra[p] < cap && (anyA ? W[p] > 0 : 1);
+                if (elig) {
+                    extra[p] += 1;
+                    Erem -= 1;
+                }
+            }
+        }
+    }
+    uint32_t acc = 0;
+    for (int p = 0; p < P; ++p) {
+        n_out[p] = (uint32_t)((uint64_t)m0 + extra[p]);
+        if (off_out) off_out[p] = acc;
+        acc += n_out[p] - 8u;
+    }
+    if (off_out) off_out[P] = acc;
+    free(extra);
+    free(inU);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Volume state                                                              */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    float origin[3], spacing[3];
+    int dims[3];
+    int n_irr, n_dep;     /* interior texel counts per side */
+    int avg, rmin, rmax;  /* ray budget */
+    float hyst;           /* hysteresis h */
+    float depth_max;      /* depth clamp; <= 0 selects 1.5 * voxel diagonal */
+    int theta;            /* temporal trigger decay length (frames) */
+} orc_desc;
+
+typedef struct {
+    int kind; /* 0 point, 1 directional (v = direction light travels) */
+    float v[3];
+    float rgb[3];
+} orc_light;
+
+typedef struct {
+    uint64_t frame, seed;
+    const orc_light* lights;
+    int n_lights;
+    float sky[3];
+    int has_camera;
+    float cam[3];
+    float cam_k;
+} orc_frame;
+
+typedef struct orc_vol {
+    orc_desc d;
+    int P, m0, Ti, Td; /* probes, min rays, tile sides */
+    double s;          /* voxel diagonal (Eq. ProbeVis) */
+    float tmin, depth_max, qv_scale, qc_scale;
+    uint16_t lut_v[4096], lut_c[4096];
+    int sf_M;
+    float* sf; /* concatenated SF sets for m = 1..sf_M, set m at m(m-1)/2 */
+    /* scene */
+    int nv, nt;
+    float* V;
+    int* I;
+    float* alb;
+    cbvh bvh;
+    int bvh_dirty;
+    /* atlases, FP64 */
+    double* irr;    /* P * Ti*Ti * 3 */
+    uint8_t* irr_n; /* P * Ti*Ti */
+    double* dep;    /* P * Td*Td * 2 */
+    uint8_t* dep_n; /* P * Td*Td */
+    /* change state, per probe and octant */
+    uint16_t *qv_even, *qr_even, *qv, *qr;
+    uint16_t *amp_v, *amp_r; /* trigger pulse heights */
+    uint8_t *age_v, *age_r;  /* frames since the pulse */
+    uint16_t *trv, *trr;     /* trigger outputs f_1, f_3 */
+    int64_t last_even;
+    /* last update's intermediates */
+    uint32_t *W, *n, *off;
+    float* pil_t;
+    int* pil_tri;
+    float* pil_lum;
+    float* pil_dir;  /* P*8*3 */
+    double* pil_rad; /* P*8*3 */
+    double* pil_dep; /* P*8 */
+    size_t R_main;
+    float* m_t;
+    int* m_tri;
+    double* m_rad;
+    double* m_dep;
+    float R[9];
+    int nthreads;
+} orc_vol;
+
+static void build_luts(orc_vol* v)
+{
+    /* q_v LUT: f_v = exp(-2 t / s) at the centre of distance bin i of width s/256 */
+    for (int i = 0; i < 4096; ++i) {
+        double f = exp(-2.0 * ((double)i + 0.5) / 256.0);
+        v->lut_v[i] = (uint16_t)floor(1023.0 * f);
+    }
+    /* q_c LUT: f_c = exp(-(|p-c| - k)) at the centre of bin i of width s/64 */
+    for (int i = 0; i < 4096; ++i) {
+        double f = exp(-((double)i + 0.5) * v->s / 64.0);
+        v->lut_c[i] = (uint16_t)floor(1023.0 * f);
+    }
+}
+
+EXPORT void orc_luts(double s, uint16_t* lut_v, uint16_t* lut_c)
+{
+    orc_vol tmp;
+    memset(&tmp, 0, sizeof(tmp));
+    tmp.s = s;
+    build_luts(&tmp);
+    memcpy(lut_v, tmp.lut_v, sizeof(tmp.lut_v));
+    memcpy(lut_c, tmp.lut_c, sizeof(tmp.lut_c));
+}
+
+EXPORT orc_vol* orc_create(const orc_desc* d, int nthreads)
+{
+    if (d->dims[0] < 2 || d->dims[1] < 2 || d->dims[2] < 2) return NULL;
+    if (d->n_irr < 1 || d->n_dep < 1 || d->theta < 1) return NULL;
+    int m0 = d->rmin > 8 ? d->rmin : 8;
+    if (d->avg < m0 || d->avg > d->rmax) return NULL;
+    orc_vol* v = (orc_vol*)calloc(1, sizeof(orc_vol));
+    v->d = *d;
+    v->P = d->dims[0] * d->dims[1] * d->dims[2];
+    v->m0 = m0;
+    v->Ti = d->n_irr + 2;
+    v->Td = d->n_dep + 2;
+    double sx = d->spacing[0], sy = d->spacing[1], sz = d->spacing[2];
+    v->s = sqrt((sx * sx + sy * sy) + sz * sz);
+    v->tmin = (float)(1e-4 * v->s);
+    v->depth_max = d->depth_max > 0.0f ? d->depth_max : (float)(1.5 * v->s);
+    v->qv_scale = (float)(256.0 / v->s);
+    v->qc_scale = (float)(64.0 / v->s);
+    build_luts(v);
+    v->sf_M = d->rmax - 8;
+    if (v->sf_M > 0) {
+        size_t tot = (size_t)v->sf_M * (size_t)(v->sf_M + 1) / 2;
+        v->sf = (float*)malloc(sizeof(float) * 3 * tot);
+        for (int m = 1; m <= v->sf_M; ++m) orc_sf_points(m, v->sf + 3 * ((size_t)m * (size_t)(m - 1) / 2));
+    }
+    size_t P = (size_t)v->P;
+    v->irr = (double*)calloc(P * v->Ti * v->Ti * 3, sizeof(double));
+    v->irr_n = (uint8_t*)calloc(P * v->Ti * v->Ti, 1);
+    v->dep = (double*)calloc(P * v->Td * v->Td * 2, sizeof(double));
+    v->dep_n = (uint8_t*)calloc(P * v->Td * v->Td, 1);
+    v->qv_even = (uint16_t*)calloc(P * 8, 2);
+    v->qr_even = (uint16_t*)calloc(P * 8, 2);
+    v->trv = (uint16_t*)calloc(P * 8, 2);
+    v->trr = (uint16_t*)calloc(P * 8, 2);
+    v->amp_v = (uint16_t*)calloc(P * 8, 2);
+    v->amp_r = (uint16_t*)calloc(P * 8, 2);
+    v->age_v = (uint8_t*)malloc(P * 8);
+    v->age_r = (uint8_t*)malloc(P * 8);
+    memset(v->age_v, 255, P * 8);
+    memset(v->age_r, 255, P * 8);
+    v->qv = (uint16_t*)calloc(P * 8, 2);
+    v->qr = (uint16_t*)calloc(P * 8, 2);
+    v->last_even = -2;
+    v->W = (uint32_t*)calloc(P, 4);
+    v->n = (uint32_t*)calloc(P, 4);
+    v->off = (uint32_t*)calloc(P + 1, 4);
+    v->pil_t = (float*)calloc(P * 8, 4);
+    v->pil_tri = (int*)calloc(P * 8, 4);
+    v->pil_lum = (float*)calloc(P * 8, 4);
+    v->pil_dir = (float*)calloc(P * 8 * 3, 4);
+    v->pil_rad = (double*)calloc(P * 8 * 3, 8);
+    v->pil_dep = (double*)calloc(P * 8, 8);
+    v->R_main = (size_t)(d->avg - 8) * P;
+    v->m_t = (float*)calloc(v->R_main + 1, 4);
+    v->m_tri = (int*)calloc(v->R_main + 1, 4);
+    v->m_rad = (double*)calloc((v->R_main + 1) * 3, 8);
+    v->m_dep = (double*)calloc(v->R_main + 1, 8);
+    v->nthreads = nthreads > 0 ? nthreads : 1;
+    return v;
+}
+
+EXPORT void orc_destroy(orc_vol* v)
+{
+    if (!v) return;
+    cbvh_free(&v->bvh);
+    free(v->sf);
+    free(v->V);
+    free(v->I);
+    free(v->alb);
+    free(v->irr);
+    free(v->irr_n);
+    free(v->dep);
+    free(v->dep_n);
+    free(v->qv_even);
+    free(v->qr_even);
+    free(v->trv);
+    free(v->trr);
+    free(v->amp_v);
+    free(v->amp_r);
+    free(v->age_v);
+    free(v->age_r);
+    free(v->qv);
+    free(v->qr);
+    free(v->W);
+    free(v->n);
+    free(v->off);
+    free(v->pil_t);
+    free(v->pil_tri);
+    free(v->pil_lum);
+    free(v->pil_dir);
+    free(v->pil_rad);
+    free(v->pil_dep);
+    free(v->m_t);
+    free(v->m_tri);
+    free(v->m_rad);
+    free(v->m_dep);
+    free(v);
+}
+
+EXPORT int orc_set_scene(orc_vol* v, const float* verts, int nv, const int* idx, int nt, const float* albedo)
+{
+    for (int t = 0; t < 3 * nt; ++t)
+        if (idx[t] < 0 || idx[t] >= nv) return -1;
+    free(v->V);
+    free(v->I);
+    free(v->alb);
+    v->V = (float*)malloc(sizeof(float) * 3 * (size_t)(nv > 0 ? nv : 1));
+    v->I = (int*)malloc(sizeof(int) * 3 * (size_t)(nt > 0 ? nt : 1));
+    v->alb = (float*)malloc(sizeof(float) * 3 * (size_t)(nt > 0 ? nt : 1));
+    memcpy(v->V, verts, sizeof(float) * 3 * (size_t)nv);
+    memcpy(v->I, idx, sizeof(int) * 3 * (size_t)nt);
+    memcpy(v->alb, albedo, sizeof(float) * 3 * (size_t)nt);
+    v->nv = nv;
+    v->nt = nt;
+    v->bvh_dirty = 1;
+    return 0;
+}
+
+EXPORT int orc_move_vertices(orc_vol* v, int first, int count, const float* verts)
+{
+    if (first < 0 || count < 0 || first + count > v->nv) return -1;
+    memcpy(v->V + 3 * (size_t)first, verts, sizeof(float) * 3 * (size_t)count);
+    v->bvh_dirty = 1;
+    return 0;
+}
+
+/* probe position, FP32: origin + spacing * index */
+static void probe_pos(const orc_vol* v, int p, float out[3])
+{
+    int ix = p % v->d.dims[0];
+    int iy = (p / v->d.dims[0]) % v->d.dims[1];
+    int iz = p / (v->d.dims[0] * v->d.dims[1]);
+    out[0] = v->d.origin[0] + v->d.spacing[0] * (float)ix;
+    out[1] = v->d.origin[1] + v->d.spacing[1] * (float)iy;
+    out[2] = v->d.origin[2] + v->d.spacing[2] * (float)iz;
+}
+
+static void main_dir(const orc_vol* v, int m, int i, float d[3])
+{
+    const float* s = v->sf + 3 * ((size_t)m * (size_t)(m - 1) / 2 + (size_t)i);
+    rotate_f32(v->R, s, d);
+}
+
+/* geometric normal, FP32, normalised: (B-A) x (C-A) / |.| */
+static void tri_normal_f32(const orc_vol* v, int t, float n[3])
+{
+    const int* ix = v->I + 3 * (size_t)t;
+    const float *A = v->V + 3 * (size_t)ix[0], *B = v->V + 3 * (size_t)ix[1], *C = v->V + 3 * (size_t)ix[2];
+    float e1[3] = {B[0] - A[0], B[1] - A[1], B[2] - A[2]};
+    float e2[3] = {C[0] - A[0], C[1] - A[1], C[2] - A[2]};
+    float c[3];
+    c[0] = e1[1] * e2[2] - e1[2] * e2[1];
+    c[1] = e1[2] * e2[0] - e1[0] * e2[2];
+    c[2] = e1[0] * e2[1] - e1[1] * e2[0];
+    float l = sqrtf((c[0] * c[0] + c[1] * c[1]) + c[2] * c[2]);
+    if (l > 0.0f) {
+        n[0] = c[0] / l;
+        n[1] = c[1] / l;
+        n[2] = c[2] / l;
+    } else {
+        n[0] = 0.0f;
+        n[1] = 0.0f;
+        n[2] = 1.0f;
+    }
+}
+
+static void tri_normal_f64(const orc_vol* v, int t, double n[3])
+{
+    const int* ix = v->I + 3 * (size_t)t;
+    const float *A = v->V + 3 * (size_t)ix[0], *B = v->V + 3 * (size_t)ix[1], *C = v->V + 3 * (size_t)ix[2];
+    double e1[3] = {(double)B[0] - A[0], (double)B[1] - A[1], (double)B[2] - A[2]};
+    double e2[3] = {(double)C[0] - A[0], (double)C[1] - A[1], (double)C[2] - A[2]};
+    double c[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
+    double l = sqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
+    if (l > 0.0) {
+        n[0] = c[0] / l;
+        n[1] = c[1] / l;
+        n[2] = c[2] / l;
+    } else {
+        n[0] = 0.0;
+        n[1] = 0.0;
+        n[2] = 1.0;
+    }
+}
+
+static hitrec vol_closest(const orc_vol* v, const float o[3], const float d[3], float tmin, float tmax)
+{
+    return closest_bvh(&v->bvh, o, d, tmin, tmax);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Irradiance query (Sec. 3.1, DDGI lookup; Chebyshev visibility g_c of     */
+/* Table "List of symbols"), FP64.                                          */
+/* ------------------------------------------------------------------------ */
+static void bilinear(const double* tile, int T, int n, int ch, const double dir[3], double* out)
+{
+    double p[2];
+    orc_oct_encode(dir, p);
+    double fx = (1.0 + (p[0] + 1.0) * 0.5 * n) - 0.5;
+    double fy = (1.0 + (p[1] + 1.0) * 0.5 * n) - 0.5;
+    int x0 = (int)floor(fx), y0 = (int)floor(fy);
+    if (x0 < 0) x0 = 0;
+    if (x0 > n) x0 = n;
+    if (y0 < 0) y0 = 0;
+    if (y0 > n) y0 = n;
+    double ax = fx - x0, ay = fy - y0;
+    if (ax < 0.0) ax = 0.0;
+    if (ax > 1.0) ax = 1.0;
+    if (ay < 0.0) ay = 0.0;
+    if (ay > 1.0) ay = 1.0;
+    for (int c = 0; c < ch; ++c) {
+        double v00 = tile[(y0 * T + x0) * ch + c], v01 = tile[(y0 * T + x0 + 1) * ch + c];
+        double v10 = tile[((y0 + 1) * T + x0) * ch + c], v11 = tile[((y0 + 1) * T + x0 + 1) * ch + c];
+        out[c] = (1.0 - ay) * ((1.0 - ax) * v00 + ax * v01) + ay * ((1.0 - ax) * v10 + ax * v11);
+    }
+}
+
+static void query_point(const orc_vol* v, const double x[3], const double nrm[3], double out[3])
+{
+    double g[3], a[3];
+    int b[3];
+    for (int k = 0; k < 3; ++k) {
+        g[k] = (x[k] - (double)v->d.origin[k]) / (double)v->d.spacing[k];
+        double f = floor(g[k]);
+        int bi = (int)(f < -1e9 ? -1e9 : (f > 1e9 ? 1e9 : f));
+        if (bi < 0) bi = 0;
+        if (bi > v->d.dims[k] - 2) bi = v->d.dims[k] - 2;
+        b[k] = bi;
+        double al = g[k] - bi;
+        if (al < 0.0) al = 0.0;
+        if (al > 1.0) al = 1.0;
+        a[k] = al;
+    }
+    double nl = sqrt(nrm[0] * nrm[0] + nrm[1] * nrm[1] + nrm[2] * nrm[2]);
+    double nd[3] = {0.0, 0.0, 1.0};
+    if (nl > 0.0) {
+        nd[0] = nrm[0] / nl;
+        nd[1] = nrm[1] / nl;
+        nd[2] = nrm[2] / nl;
+    }
+    double sum[3] = {0, 0, 0}, sumt[3] = {0, 0, 0}, sw = 0.0;
+    double varmin = 1e-6 * v->s * v->s;
+    for (int c = 0; c < 8; ++c) {
+        int o[3] = {c & 1, (c >> 1) & 1, (c >> 2) & 1};
+        double wt = 1.0;
+        int ii[3];
+        for (int k = 0; k < 3; ++k) {
+            wt *= o[k] ? a[k] : 1.0 - a[k];
+            ii[k] = b[k] + o[k];
+        }
+        int p = ii[0] + v->d.dims[0] * (ii[1] + v->d.dims[1] * ii[2]);
+        float pp[3];
+        probe_pos(v, p, pp);
+        double dv[3] = {x[0] - pp[0], x[1] - pp[1], x[2] - pp[2]};
+        double dist = sqrt(dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2]);
+        double dir[3] = {0.0, 0.0, 1.0};
+        if (dist > 0.0) {
+            dir[0] = dv[0] / dist;
+            dir[1] = dv[1] / dist;
+            dir[2] = dv[2] / dist;
+        }
+        double mom[2];
+        bilinear(v->dep + (size_t)p * v->Td * v->Td * 2, v->Td, v->d.n_dep, 2, dir, mom);
+        double wc = 1.0;
+        if (dist > mom[0]) {
+            double var = mom[1] - mom[0] * mom[0];
+            if (var < varmin) var = varmin;
+            double dd = dist - mom[0];
+            wc = var / (var + dd * dd);
+        }
+        double E[3];
+        bilinear(v->irr + (size_t)p * v->Ti * v->Ti * 3, v->Ti, v->d.n_irr, 3, nd, E);
+        double w = wt * wc;
+        for (int k = 0; k < 3; ++k) {
+            sum[k] += w * E[k];
+            sumt[k] += wt * E[k];
+        }
+        sw += w;
+    }
+    for (int k = 0; k < 3; ++k) out[k] = sw >= 1e-12 ? sum[k] / sw : sumt[k];
+}
+
+EXPORT void orc_query(const orc_vol* v, int n, const float* pos, const float* nrm, double* out)
+{
+    for (int i = 0; i < n; ++i) {
+        double x[3] = {pos[3 * i], pos[3 * i + 1], pos[3 * i + 2]};
+        double nn[3] = {nrm[3 * i], nrm[3 * i + 1], nrm[3 * i + 2]};
+        query_point(v, x, nn, out + 3 * (size_t)i);
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Shading of one ray.                                                       */
+/* Direct light with shadow rays + multi-bounce albedo * Q_{t-1}(x, n)       */
+/* (Sec. 4.1 "Incoming radiance"; Sec. 4.5 static sampling traces the       */
+/* scene; DDGI multi-bounce, Sec. 3.1).  Visibility and the lit test are     */
+/* FP32 decisions; magnitudes are FP64.  lum32 receives the FP32 luminance   */
+/* of the direct-only radiance (the r of f_r).                              */
+/* ------------------------------------------------------------------------ */
+static const float LUM_R = 0.2126f, LUM_G = 0.7152f, LUM_B = 0.0722f;
+static const float INV_PI_F = 0.31830987f;
+
+static void shade_ray(const orc_vol* v, const orc_frame* fr, const float o[3], const float d[3], hitrec h,
+                      double rad[3], double* depth, float* lum32)
+{
+    if (h.tri < 0) {
+        for (int k = 0; k < 3; ++k) rad[k] = fr->sky[k];
+        *depth = v->depth_max;
+        if (lum32) *lum32 = (LUM_R * fr->sky[0] + LUM_G * fr->sky[1]) + LUM_B * fr->sky[2];
+        return;
+    }
+    *depth = h.t < v->depth_max ? h.t : v->depth_max;
+    if (h.det < 0.0f) { /* back face */
+        rad[0] = rad[1] = rad[2] = 0.0;
+        if (lum32) *lum32 = 0.0f;
+        return;
+    }
+    float x[3], n[3], xs[3];
+    for (int k = 0; k < 3; ++k) x[k] = o[k] + h.t * d[k];
+    tri_normal_f32(v, h.tri, n);
+    for (int k = 0; k < 3; ++k) xs[k] = x[k] + v->tmin * n[k];
+    double n64[3];
+    tri_normal_f64(v, h.tri, n64);
+    double x64[3];
+    for (int k = 0; k < 3; ++k) x64[k] = (double)o[k] + (double)h.t * (double)d[k];
+    const float* alb = v->alb + 3 * (size_t)h.tri;
+    double E[3] = {0, 0, 0};
+    float E32[3] = {0.0f, 0.0f, 0.0f};
+    for (int l = 0; l < fr->n_lights; ++l) {
+        const orc_light* L = &fr->lights[l];
+        float D[3];
+        float thi;
+        if (L->kind == 0) {
+            for (int k = 0; k < 3; ++k) D[k] = L->v[k] - xs[k];
+            thi = 1.0f;
+        } else {
+            for (int k = 0; k < 3; ++k) D[k] = -L->v[k];
+            thi = INFINITY;
+        }
+        float ndD = (n[0] * D[0] + n[1] * D[1]) + n[2] * D[2];
+        if (!(ndD > 0.0f)) continue;
+        if (anyhit_bvh(&v->bvh, xs, D, 0.0f, thi)) continue;
+        /* FP32 irradiance for the pilot luminance */
+        float g32;
+        if (L->kind == 0) {
+            float Dx[3] = {L->v[0] - x[0], L->v[1] - x[1], L->v[2] - x[2]};
+            float d2 = (Dx[0] * Dx[0] + Dx[1] * Dx[1]) + Dx[2] * Dx[2];
+            float nd = (n[0] * Dx[0] + n[1] * Dx[1]) + n[2] * Dx[2];
+            g32 = nd > 0.0f ? nd / (d2 * sqrtf(d2)) : 0.0f;
+        } else {
+            float l2 = (L->v[0] * L->v[0] + L->v[1] * L->v[1]) + L->v[2] * L->v[2];
+            g32 = ndD / sqrtf(l2);
+        }
+        for (int k = 0; k < 3; ++k) E32[k] = E32[k] + L->rgb[k] * g32;
+        /* FP64 irradiance */
+        double g;
+        if (L->kind == 0) {
+            double Dx[3] = {(double)L->v[0] - x64[0], (double)L->v[1] - x64[1], (double)L->v[2] - x64[2]};
+            double d2 = Dx[0] * Dx[0] + Dx[1] * Dx[1] + Dx[2] * Dx[2];
+            double nd = n64[0] * Dx[0] + n64[1] * Dx[1] + n64[2] * Dx[2];
+            g = nd > 0.0 ? nd / (d2 * sqrt(d2)) : 0.0;
+        } else {
+            double l2 = (double)L->v[0] * L->v[0] + (double)L->v[1] * L->v[1] + (double)L->v[2] * L->v[2];
+            double nd = -(n64[0] * L->v[0] + n64[1] * L->v[1] + n64[2] * L->v[2]);
+            g = nd > 0.0 ? nd / sqrt(l2) : 0.0;
+        }
+        for (int k = 0; k < 3; ++k) E[k] += (double)L->rgb[k] * g;
+    }
+    double Q[3];
+    query_point(v, x64, n64, Q);
+    for (int k = 0; k < 3; ++k) rad[k] = (double)alb[k] / M_PI * E[k] + (double)alb[k] * Q[k];
+    if (lum32) {
+        float r0 = (alb[0] * INV_PI_F) * E32[0];
+        float r1 = (alb[1] * INV_PI_F) * E32[1];
+        float r2 = (alb[2] * INV_PI_F) * E32[2];
+        *lum32 = (LUM_R * r0 + LUM_G * r1) + LUM_B * r2;
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Blend (Alg. ApproxAlgo + Alg. MovingAvgUpdate, batch form): every sample */
+/* of this frame updates its nearest texel; for a texel with k samples of   */
+/* mean m and stored (V, n):  V' = V + w (m - V),  w = max(1 - h, k/(n+k)),  */
+/* n' = min(n + k, 255).  Untouched texels keep their value.  Then the      */
+/* one-texel octahedral border is refreshed from the interior.             */
+/* ------------------------------------------------------------------------ */
+static void border_copy(double* tile, uint8_t* cnt, int n, int ch)
+{
+    int T = n + 2;
+#define CP(di, dj, si, sj)                                                    \
+    do {                                                                      \
+        for (int c = 0; c < ch; ++c) tile[((di)*T + (dj)) * ch + c] = tile[((si)*T + (sj)) * ch + c]; \
+        cnt[(di)*T + (dj)] = cnt[(si)*T + (sj)];                              \
+    } while (0)
+    for (int j = 1; j <= n; ++j) {
+        CP(0, j, 1, n + 1 - j);
+        CP(n + 1, j, n, n + 1 - j);
+    }
+    for (int i = 1; i <= n; ++i) {
+        CP(i, 0, n + 1 - i, 1);
+        CP(i, n + 1, n + 1 - i, n);
+    }
+    CP(0, 0, n, n);
+    CP(0, n + 1, n, 1);
+    CP(n + 1, 0, 1, n);
+    CP(n + 1, n + 1, 1, 1);
+#undef CP
+}
+
+static void blend_probe(orc_vol* v, int p, int use_pilots, double h)
+{
+    const int Ti = v->Ti, Td = v->Td, ni = v->d.n_irr, nd = v->d.n_dep;
+    double* irr = v->irr + (size_t)p * Ti * Ti * 3;
+    uint8_t* irn = v->irr_n + (size_t)p * Ti * Ti;
+    double* dep = v->dep + (size_t)p * Td * Td * 2;
+    uint8_t* den = v->dep_n + (size_t)p * Td * Td;
+    double* si = (double*)calloc((size_t)Ti * Ti * 3, sizeof(double));
+    int* ki = (int*)calloc((size_t)Ti * Ti, sizeof(int));
+    double* sd = (double*)calloc((size_t)Td * Td * 2, sizeof(double));
+    int* kd = (int*)calloc((size_t)Td * Td, sizeof(int));
+    const uint32_t mp = v->n[p] - 8u;
+    const int total = (int)mp + (use_pilots ? 8 : 0);
+    for (int j = 0; j < total; ++j) {
+        float d[3];
+        const double* rad;
+        double ds;
+        if (use_pilots && j < 8) {
+            const float* pd = v->pil_dir + ((size_t)p * 8 + (size_t)j) * 3;
+            d[0] = pd[0];
+            d[1] = pd[1];
+            d[2] = pd[2];
+            rad = v->pil_rad + ((size_t)p * 8 + (size_t)j) * 3;
+            ds = v->pil_dep[(size_t)p * 8 + (size_t)j];
+        } else {
+            int i = use_pilots ? j - 8 : j;
+            main_dir(v, (int)mp, i, d);
+            size_t r = (size_t)v->off[p] + (size_t)i;
+            rad = v->m_rad + r * 3;
+            ds = v->m_dep[r];
+        }
+        int ti = orc_texel_of_dir(d, ni);
+        int td = orc_texel_of_dir(d, nd);
+        for (int c = 0; c < 3; ++c) si[ti * 3 + c] += rad[c];
+        ki[ti] += 1;
+        sd[td * 2 + 0] += ds;
+        sd[td * 2 + 1] += ds * ds;
+        kd[td] += 1;
+    }
+    for (int t = 0; t < Ti * Ti; ++t) {
+        if (!ki[t]) continue;
+        double k = ki[t], n = irn[t];
+        double w = k / (n + k);
+        if (w < 1.0 - h) w = 1.0 - h;
+        for (int c = 0; c < 3; ++c) irr[t * 3 + c] += w * (si[t * 3 + c] / k - irr[t * 3 + c]);
+        int nn = irn[t] + ki[t];
+        irn[t] = (uint8_t)(nn > 255 ? 255 : nn);
+    }
+    for (int t = 0; t < Td * Td; ++t) {
+        if (!kd[t]) continue;
+        double k = kd[t], n = den[t];
+        double w = k / (n + k);
+        if (w < 1.0 - h) w = 1.0 - h;
+        for (int c = 0; c < 2; ++c) dep[t * 2 + c] += w * (sd[t * 2 + c] / k - dep[t * 2 + c]);
+        int nn = den[t] + kd[t];
+        den[t] = (uint8_t)(nn > 255 ? 255 : nn);
+    }
+    border_copy(irr, irn, ni, 3);
+    border_copy(dep, den, nd, 2);
+    free(si);
+    free(ki);
+    free(sd);
+    free(kd);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Heuristics (Sec. 4.1-4.2), integer form.                                 */
+/*   q_v(p,o) = LUT_v[min(floor(t * 256/s), 4095)], t from the pilot ray of */
+/*              the opposite octant 7-o (f_v uses trace(p, -w))              */
+/*   q_r(p,o) = floor(1023 * min(lum, 5) / 5)                                */
+/*   trigger Tr(., theta) (Fig. TrCam(a)): a pulse of height v starts a     */
+/*            signal that decays linearly to 0 over theta frames,           */
+/*            y = floor(v (theta - age) / theta); a new pulse replaces the  */
+/*            running one when it is at least the current value.  Pulses    */
+/*            are the deltas |q_t - q_{t-1}| taken on the second frame of   */
+/*            each pair (identical rays, Sec. 4.4); ages advance every frame */
+/*   f_D(p,o) = sum over the 5x5x5 probe box clipped to the grid and over    */
+/*              o' in {o, o^1, o^2, o^4} of Tr(p', o')                       */
+/*   q_d(p,o) = (q_c q_v (f_Dv + 2 f_Dr)) >> 20          (mu = 2)           */
+/*   W_p      = min(sum_o q_d(p,o), 2^24 - 1)                                */
+/* ------------------------------------------------------------------------ */
+static uint32_t qt_of(const orc_vol* v, float t, int hit)
+{
+    if (!hit) return 4095u;
+    float q = t * v->qv_scale;
+    if (!(q < 4095.0f)) return 4095u;
+    return (uint32_t)floorf(q);
+}
+
+static uint32_t qr_of(float lum)
+{
+    float c = lum < 5.0f ? lum : 5.0f;
+    if (!(c > 0.0f)) return 0u;
+    float q = floorf((c * 1023.0f) / 5.0f);
+    if (q > 1023.0f) q = 1023.0f;
+    return (uint32_t)q;
+}
+
+static uint32_t qc_of(const orc_vol* v, const orc_frame* fr, int p)
+{
+    if (!fr->has_camera) return 1023u;
+    float pp[3];
+    probe_pos(v, p, pp);
+    float dx = pp[0] - fr->cam[0], dy = pp[1] - fr->cam[1], dz = pp[2] - fr->cam[2];
+    float dist = sqrtf((dx * dx + dy * dy) + dz * dz);
+    if (dist < fr->cam_k) return 1023u;
+    float q = (dist - fr->cam_k) * v->qc_scale;
+    uint32_t i = (q < 4095.0f) ? (uint32_t)floorf(q) : 4095u;
+    return v->lut_c[i];
+}
+
+static void change_detect(orc_vol* v, const orc_frame* fr)
+{
+    const int P = v->P;
+    for (int p = 0; p < P; ++p)
+        for (int o = 0; o < 8; ++o) {
+            size_t opp = (size_t)p * 8 + (size_t)(7 - o);
+            v->qv[(size_t)p * 8 + o] = v->lut_v[qt_of(v, v->pil_t[opp], v->pil_tri[opp] >= 0)];
+            v->qr[(size_t)p * 8 + o] = (uint16_t)qr_of(v->pil_lum[(size_t)p * 8 + o]);
+        }
+    const int theta = v->d.theta;
+    const int even = (fr->frame & 1u) == 0;
+    const int valid = !even && v->last_even == (int64_t)fr->frame - 1;
+    for (size_t i = 0; i < (size_t)P * 8; ++i) {
+        uint16_t* amp[2] = {&v->amp_v[i], &v->amp_r[i]};
+        uint8_t* age[2] = {&v->age_v[i], &v->age_r[i]};
+        uint16_t* out[2] = {&v->trv[i], &v->trr[i]};
+        int delta[2] = {0, 0};
+        if (!even && valid) {
+            delta[0] = abs((int)v->qv[i] - (int)v->qv_even[i]);
+            delta[1] = abs((int)v->qr[i] - (int)v->qr_even[i]);
+        }
+        for (int c = 0; c < 2; ++c) {
+            int a = *age[c];
+            if (a < theta) a += 1; /* the running pulse ages by one frame */
+            int cur = a < theta ? (int)(((uint32_t)*amp[c] * (uint32_t)(theta - a)) / (uint32_t)theta) : 0;
+            if (delta[c] > 0 && delta[c] >= cur) {
+                *amp[c] = (uint16_t)delta[c];
+                a = 0;
+                cur = delta[c];
+            }
+            *age[c] = (uint8_t)(a < theta ? a : theta);
+            *out[c] = (uint16_t)cur;
+        }
+        if (even) {
+            v->qv_even[i] = v->qv[i];
+            v->qr_even[i] = v->qr[i];
+        }
+    }
+    if (even) v->last_even = (int64_t)fr->frame;
+    const int X = v->d.dims[0], Y = v->d.dims[1], Z = v->d.dims[2];
+    for (int p = 0; p < P; ++p) {
+        int ix = p % X, iy = (p / X) % Y, iz = p / (X * Y);
+        uint32_t qc = qc_of(v, fr, p);
+        uint64_t Wp = 0;
+        for (int o = 0; o < 8; ++o) {
+            uint64_t fdv = 0, fdr = 0;
+            for (int dz = -2; dz <= 2; ++dz)
+                for (int dy = -2; dy <= 2; ++dy)
+                    for (int dx = -2; dx <= 2; ++dx) {
+                        int jx = ix + dx, jy = iy + dy, jz = iz + dz;
+                        if (jx < 0 || jy < 0 || jz < 0 || jx >= X || jy >= Y || jz >= Z) continue;
+                        size_t q = ((size_t)jx + (size_t)X * ((size_t)jy + (size_t)Y * (size_t)jz)) * 8;
+                        const int nb[4] = {o, o ^ 1, o ^ 2, o ^ 4};
+                        for (int k = 0; k < 4; ++k) {
+                            fdv += v->trv[q + nb[k]];
+                            fdr += v->trr[q + nb[k]];
+                        }
+                    }
+            uint64_t qd = ((uint64_t)qc * (uint64_t)v->qv[(size_t)p * 8 + o] * (fdv + 2u * fdr)) >> 20;
+            Wp += qd;
+        }
+        v->W[p] = (uint32_t)(Wp < 0xFFFFFFu ? Wp : 0xFFFFFFu);
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* The per-frame update, in the paper's order (Fig. Method): pilot rays ->  */
+/* heuristics -> allocation -> adaptive rays -> cache update.  All shading  */
+/* reads the atlases as they were before this frame's blend.                */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    orc_vol* v;
+    const orc_frame* fr;
+    int phase;
+    int t0, t1;
+} job;
+
+static void pilot_probe(orc_vol* v, const orc_frame* fr, int p)
+{
+    float o[3];
+    probe_pos(v, p, o);
+    for (int k = 0; k < 8; ++k) {
+        size_t i = (size_t)p * 8 + (size_t)k;
+        float* d = v->pil_dir + i * 3;
+        orc_pilot_dir(fr->seed, fr->frame, (uint32_t)p, k, d);
+        hitrec h = vol_closest(v, o, d, v->tmin, INFINITY);
+        v->pil_t[i] = h.tri >= 0 ? h.t : INFINITY;
+        v->pil_tri[i] = h.tri;
+        shade_ray(v, fr, o, d, h, v->pil_rad + i * 3, v->pil_dep + i, v->pil_lum + i);
+    }
+}
+
+static void main_probe(orc_vol* v, const orc_frame* fr, int p)
+{
+    float o[3];
+    probe_pos(v, p, o);
+    int mp = (int)v->n[p] - 8;
+    for (int i = 0; i < mp; ++i) {
+        float d[3];
+        main_dir(v, mp, i, d);
+        size_t r = (size_t)v->off[p] + (size_t)i;
+        hitrec h = vol_closest(v, o, d, v->tmin, INFINITY);
+        v->m_t[r] = h.tri >= 0 ? h.t : INFINITY;
+        v->m_tri[r] = h.tri;
+        shade_ray(v, fr, o, d, h, v->m_rad + r * 3, v->m_dep + r, NULL);
+    }
+}
+
+static void* worker(void* arg)
+{
+    job* j = (job*)arg;
+    for (int p = j->t0; p < j->t1; ++p) {
+        if (j->phase == 0)
+            pilot_probe(j->v, j->fr, p);
+        else if (j->phase == 1)
+            main_probe(j->v, j->fr, p);
+        else
+            blend_probe(j->v, p, (j->fr->frame & 1u) == 0, (double)j->v->d.hyst);
+    }
+    return NULL;
+}
+
+static void run_phase(orc_vol* v, const orc_frame* fr, int phase)
+{
+    int nt = v->nthreads;
+    if (nt > v->P) nt = v->P;
+    pthread_t th[256];
+    job jobs[256];
+    if (nt > 256) nt = 256;
+    for (int t = 0; t < nt; ++t) {
+        jobs[t].v = v;
+        jobs[t].fr = fr;
+        jobs[t].phase = phase;
+        jobs[t].t0 = (int)((long long)v->P * t / nt);
+        jobs[t].t1 = (int)((long long)v->P * (t + 1) / nt);
+    }
+    if (nt == 1) {
+        worker(&jobs[0]);
+        return;
+    }
+    for (int t = 0; t < nt; ++t) pthread_create(&th[t], NULL, worker, &jobs[t]);
+    for (int t = 0; t < nt; ++t) pthread_join(th[t], NULL);
+}
+
+EXPORT int orc_update(orc_vol* v, const orc_frame* fr)
+{
+    if (v->bvh_dirty) {
+        if (cbvh_build(&v->bvh, v->V, v->nv, v->I, v->nt)) return -1;
+        v->bvh_dirty = 0;
+    }
+    orc_frame_rotation(fr->seed, fr->frame, v->R);
+    run_phase(v, fr, 0);
+    change_detect(v, fr);
+    if (orc_allocate(v->W, v->P, v->d.avg, v->d.rmin, v->d.rmax, v->n, v->off)) return -1;
+    run_phase(v, fr, 1);
+    run_phase(v, fr, 2);
+    return 0;
+}
+
+/* Trace + shade the pilot and main rays of a probe subset without blending */
+/* (timing sample for the CPU baseline).  Requires a previous orc_update.    */
+EXPORT long long orc_trace_shade_probes(orc_vol* v, const orc_frame* fr, const int* probes, int count)
+{
+    long long rays = 0;
+    for (int k = 0; k < count; ++k) {
+        int p = probes[k];
+        pilot_probe(v, fr, p);
+        main_probe(v, fr, p);
+        rays += v->n[p];
+    }
+    return rays;
+}
+
+/* ------------------------------------------------------------------------ */
+/* State readers for the tests.                                              */
+/* ------------------------------------------------------------------------ */
+EXPORT int orc_num_probes(const orc_vol* v) { return v->P; }
+EXPORT long long orc_num_main_rays(const orc_vol* v) { return (long long)v->R_main; }
+EXPORT const double* orc_irr(const orc_vol* v) { return v->irr; }
+EXPORT const uint8_t* orc_irr_n(const orc_vol* v) { return v->irr_n; }
+EXPORT const double* orc_dep(const orc_vol* v) { return v->dep; }
+EXPORT const uint8_t* orc_dep_n(const orc_vol* v) { return v->dep_n; }
+EXPORT const uint32_t* orc_W(const orc_vol* v) { return v->W; }
+EXPORT const uint32_t* orc_n(const orc_vol* v) { return v->n; }
+EXPORT const uint32_t* orc_off(const orc_vol* v) { return v->off; }
+EXPORT const uint16_t* orc_qv(const orc_vol* v) { return v->qv; }
+EXPORT const uint16_t* orc_qr(const orc_vol* v) { return v->qr; }
+EXPORT const uint16_t* orc_trv(const orc_vol* v) { return v->trv; }
+EXPORT const uint16_t* orc_trr(const orc_vol* v) { return v->trr; }
+EXPORT const float* orc_pil_t(const orc_vol* v) { return v->pil_t; }
+EXPORT const int* orc_pil_tri(const orc_vol* v) { return v->pil_tri; }
+EXPORT const float* orc_pil_lum(const orc_vol* v) { return v->pil_lum; }
+EXPORT const float* orc_pil_dir(const orc_vol* v) { return v->pil_dir; }
+EXPORT const double* orc_pil_rad(const orc_vol* v) { return v->pil_rad; }
+EXPORT const double* orc_pil_dep(const orc_vol* v) { return v->pil_dep; }
+EXPORT const float* orc_m_t(const orc_vol* v) { return v->m_t; }
+EXPORT const int* orc_m_tri(const orc_vol* v) { return v->m_tri; }
+EXPORT const double* orc_m_rad(const orc_vol* v) { return v->m_rad; }
+EXPORT const double* orc_m_dep(const orc_vol* v) { return v->m_dep; }
+EXPORT const float* orc_rot(const orc_vol* v) { return v->R; }
+EXPORT void orc_probe_pos(const orc_vol* v, int p, float out[3]) { probe_pos(v, p, out); }
+EXPORT void orc_main_dir(const orc_vol* v, int m, int i, float out[3]) { main_dir(v, m, i, out); }
+EXPORT double orc_voxel_diag(const orc_vol* v) { return v->s; }
+EXPORT float orc_depth_max(const orc_vol* v) { return v->depth_max; }
+EXPORT float orc_tmin(const orc_vol* v) { return v->tmin; }
+
+/* Test hooks: overwrite state to set up closed-form cases. */
+EXPORT void orc_set_atlas(orc_vol* v, const double* irr, const uint8_t* irr_n, const double* dep, const uint8_t* dep_n)
+{
+    size_t P = (size_t)v->P;
+    if (irr) memcpy(v->irr, irr, P * v->Ti * v->Ti * 3 * sizeof(double));
+    if (irr_n) memcpy(v->irr_n, irr_n, P * v->Ti * v->Ti);
+    if (dep) memcpy(v->dep, dep, P * v->Td * v->Td * 2 * sizeof(double));
+    if (dep_n) memcpy(v->dep_n, dep_n, P * v->Td * v->Td);
+}
+
+EXPORT void orc_border_copy(double* tile, uint8_t* cnt, int n, int ch) { border_copy(tile, cnt, n, ch); }
+
+/* Test hook: run the heuristics step (Sec. 4.1-4.2) on given pilot results. */
+EXPORT void orc_change_from_pilots(orc_vol* v, const orc_frame* fr, const float* pil_t, const int* pil_tri,
+                                   const float* pil_lum)
+{
+    size_t n = (size_t)v->P * 8;
+    memcpy(v->pil_t, pil_t, n * sizeof(float));
+    memcpy(v->pil_tri, pil_tri, n * sizeof(int));
+    memcpy(v->pil_lum, pil_lum, n * sizeof(float));
+    change_detect(v, fr);
+}

@@ -1,0 +1,631 @@
+"""Pins of the CPU oracle against what the paper and mathematics fix.
+
+Each test checks the oracle against something other than itself: published
+test vectors, closed forms, invariants, special cases that reduce to a
+textbook result, or brute force on tiny inputs.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2301_05125_gb300 import scenegen as S
+
+
+# --------------------------------------------------------------- generators
+def test_splitmix64_published_vectors():
+    # SplitMix64 seeded with 0: first two outputs (Steele, Lea, Flood 2014;
+    # reference outputs of Vigna's splitmix64.c).
+    assert O.splitmix64(0) == 0xE220A8397B1DCDAF
+    assert O.splitmix64(0x9E3779B97F4A7C15) == 0x6E789E6AA1B965F4
+
+
+def test_pilot_dirs_one_per_octant_and_pairs_repeat():
+    # Sec. 4.4: stratified random, one ray per octant; AABBCC pattern.
+    for probe in range(50):
+        for f in (0, 2, 7):
+            for o in range(8):
+                d = O.pilot_dir(3, f, probe, o)
+                assert abs(float(np.linalg.norm(d.astype(np.float64))) - 1.0) < 3e-7
+                sx = np.signbit(d[0]) if d[0] == 0 else d[0] < 0
+                sy = np.signbit(d[1]) if d[1] == 0 else d[1] < 0
+                sz = np.signbit(d[2]) if d[2] == 0 else d[2] < 0
+                assert int(sx) | (int(sy) << 1) | (int(sz) << 2) == o
+                np.testing.assert_array_equal(d, O.pilot_dir(3, f ^ 1, probe, o))
+    assert not np.array_equal(O.pilot_dir(3, 0, 5, 1), O.pilot_dir(3, 2, 5, 1))
+
+
+def test_pilot_dirs_uniform_within_octant():
+    # Uniform on the octant's spherical triangle in barycentric (u1,u2,u3)
+    # parametrisation before normalisation: the simplex mean is (1/3,1/3,1/3).
+    vs = np.array([O.pilot_dir(11, 0, p, 0) for p in range(4000)], np.float64)
+    l1 = vs / vs.sum(axis=1, keepdims=True)
+    np.testing.assert_allclose(l1.mean(axis=0), [1 / 3] * 3, atol=0.015)
+
+
+def test_frame_rotation_is_a_rotation():
+    zs = []
+    for f in range(200):
+        R = O.frame_rotation(7, f).astype(np.float64)
+        np.testing.assert_allclose(R @ R.T, np.eye(3), atol=2e-7)
+        assert abs(np.linalg.det(R) - 1.0) < 5e-7
+        zs.append(R[:, 2])
+    # a uniform random rotation maps e_z to a uniform direction: mean ~ 0
+    assert np.linalg.norm(np.mean(zs, axis=0)) < 0.15
+    assert not np.array_equal(O.frame_rotation(7, 0), O.frame_rotation(7, 1))
+
+
+def test_sf_points_closed_form():
+    # Spherical Fibonacci (Keinert et al. 2015): z_i = 1-(2i+1)/m,
+    # phi_i = i * pi * (3 - sqrt 5), compared with libm cos/sin.
+    for m in (1, 2, 7, 64, 1016):
+        pts = O.sf_points(m).astype(np.float64)
+        i = np.arange(m)
+        z = 1.0 - (2 * i + 1) / m
+        phi = i * math.pi * (3.0 - math.sqrt(5.0))
+        r = np.sqrt(np.maximum(0.0, 1.0 - z * z))
+        ref = np.stack([r * np.cos(phi), r * np.sin(phi), z], 1)
+        np.testing.assert_allclose(pts, ref, atol=2e-7)
+        np.testing.assert_allclose(np.linalg.norm(pts, axis=1), 1.0, atol=3e-7)
+
+
+# --------------------------------------------------------------- octahedral
+def test_oct_round_trip_and_special_directions():
+    rng = np.random.default_rng(0)
+    w = rng.normal(size=(2000, 3))
+    w /= np.linalg.norm(w, axis=1, keepdims=True)
+    for x in w:
+        np.testing.assert_allclose(O.oct_decode(O.oct_encode(x)), x, atol=1e-14)
+    np.testing.assert_allclose(O.oct_encode([0, 0, 1]), [0, 0], atol=0)
+    np.testing.assert_allclose(O.oct_encode([1, 0, 0]), [1, 0], atol=0)
+    np.testing.assert_allclose(O.oct_encode([0, -1, 0]), [0, -1], atol=0)
+    p = O.oct_encode([0, 0, -1])
+    assert abs(p[0]) == 1 and abs(p[1]) == 1
+    # the upper hemisphere maps inside the diamond |x|+|y| <= 1
+    for x in w[:200]:
+        p = O.oct_encode(x)
+        assert (abs(p[0]) + abs(p[1]) <= 1 + 1e-12) == (x[2] >= 0) or abs(x[2]) < 1e-12
+
+
+def test_texel_centres_bin_to_themselves():
+    for n in (6, 14):
+        T = n + 2
+        for i in range(1, n + 1):
+            for j in range(1, n + 1):
+                p = [((j - 1) + 0.5) / n * 2 - 1, ((i - 1) + 0.5) / n * 2 - 1]
+                w = O.oct_decode(p)
+                assert O.texel_of_dir(w.astype(np.float32), n) == i * T + j
+
+
+def _fold_partner(i, j, n):
+    """Interior texel whose centre is the mirror image of border texel (i,j)
+    across the nearest square edge, using the octahedral map's edge identity
+    (x, +-1 +- e) ~ (-x, +-1 -+ e) and (+-1 +- e, y) ~ (+-1 -+ e, -y)."""
+    # padded coordinates of the centre in units of one texel, edges at 1, n+1
+    cy, cx = i + 0.5, j + 0.5
+    if cy < 1:
+        cy, cx = 2 - cy, (n + 2) - cx
+    elif cy > n + 1:
+        cy, cx = 2 * (n + 1) - cy, (n + 2) - cx
+    if cx < 1:
+        cx, cy = 2 - cx, (n + 2) - cy
+    elif cx > n + 1:
+        cx, cy = 2 * (n + 1) - cx, (n + 2) - cy
+    return int(math.floor(cy)), int(math.floor(cx))
+
+
+def test_octahedral_edge_identity_and_border_copy():
+    # the identity used by _fold_partner: the square's edges fold onto
+    # themselves mirrored, and all four corners are the direction -z
+    rng = np.random.default_rng(1)
+    for a in rng.uniform(-1, 1, 200):
+        for e in (1.0, -1.0):
+            np.testing.assert_allclose(O.oct_decode([a, e]), O.oct_decode([-a, e]), atol=1e-15)
+            np.testing.assert_allclose(O.oct_decode([e, a]), O.oct_decode([e, -a]), atol=1e-15)
+    for cx in (-1, 1):
+        for cy in (-1, 1):
+            np.testing.assert_allclose(O.oct_decode([cx, cy]), [0, 0, -1], atol=1e-15)
+    for n in (6, 14):
+        T = n + 2
+        tile = rng.normal(size=(T, T, 2))
+        cnt = rng.integers(0, 255, (T, T)).astype(np.uint8)
+        t2, c2 = O.border_copy(tile, cnt, n)
+        np.testing.assert_array_equal(t2[1:-1, 1:-1], tile[1:-1, 1:-1])
+        for i in range(T):
+            for j in range(T):
+                if 1 <= i <= n and 1 <= j <= n:
+                    continue
+                si, sj = _fold_partner(i, j, n)
+                assert 1 <= si <= n and 1 <= sj <= n
+                np.testing.assert_array_equal(t2[i, j], tile[si, sj])
+                assert c2[i, j] == cnt[si, sj]
+
+
+# --------------------------------------------------------------- intersection
+def test_intersection_closed_form_and_facing():
+    # triangle in z = 0 with normal +z; a ray straight down hits at t = 1
+    hit, t, det = O.intersect_tri([0.25, 0.25, 1.0], [0, 0, -1], [0, 0, 0], [1, 0, 0], [0, 1, 0])
+    assert hit and t == 1.0 and det > 0  # front face: det > 0
+    hit, t, det = O.intersect_tri([0.25, 0.25, -2.0], [0, 0, 1], [0, 0, 0], [1, 0, 0], [0, 1, 0])
+    assert hit and t == 2.0 and det < 0  # back face: det < 0
+    hit, _, _ = O.intersect_tri([2.0, 2.0, 1.0], [0, 0, -1], [0, 0, 0], [1, 0, 0], [0, 1, 0])
+    assert not hit
+
+
+def test_intersection_against_fp64_barycentrics():
+    rng = np.random.default_rng(2)
+    n_mis = 0
+    for _ in range(20000):
+        A, B, Cv = rng.uniform(-1, 1, (3, 3)).astype(np.float32)
+        o = rng.uniform(-3, 3, 3).astype(np.float32)
+        target = (rng.dirichlet([1, 1, 1]) * 1.4 - 0.2) @ np.stack([A, B, Cv]).astype(np.float64)
+        d = (target - o).astype(np.float32)
+        hit, t, det = O.intersect_tri(o, d, A, B, Cv)
+        # FP64 reference: Moller-Trumbore style barycentrics in double
+        A64, B64, C64, o64, d64 = (x.astype(np.float64) for x in (A, B, Cv, o, d))
+        e1, e2 = B64 - A64, C64 - A64
+        n = np.cross(e1, e2)
+        denom = -np.dot(d64, n)
+        if abs(denom) < 1e-12:
+            continue
+        s = o64 - A64
+        t64 = np.dot(s, n) / denom
+        u = np.dot(d64, np.cross(s, e2)) / np.dot(d64, np.cross(e2, e1)) if False else None
+        # barycentrics of the line/plane point
+        x = o64 + t64 * d64
+        M = np.stack([e1, e2], 1)
+        uv, *_ = np.linalg.lstsq(M, x - A64, rcond=None)
+        b = np.array([1 - uv.sum(), uv[0], uv[1]])
+        inside = b.min() >= 0
+        if abs(b.min()) < 1e-5:
+            continue  # on an edge: either answer is correct
+        if hit != inside:
+            n_mis += 1
+            continue
+        if hit:
+            assert abs(t - t64) <= 1e-4 * max(1.0, abs(t64))
+            # det sign: front face <=> geometric normal faces the ray origin
+            assert (det > 0) == (np.dot(n, d64) < 0)
+    assert n_mis == 0
+
+
+def test_watertight_closed_mesh_never_misses():
+    # rays from inside a closed box shell must hit it (no leaks on edges)
+    v, t = S.boxes_mesh([[0, 0, 0]], [[8, 8, 8]], inward=True)
+    rng = np.random.default_rng(3)
+    O_ = np.repeat(np.array([[4.0, 4.0, 4.0]], np.float32), 20000, 0)
+    # aim exactly at edges and corners of the shell
+    tgt = rng.integers(0, 2, (20000, 3)).astype(np.float32) * 8.0
+    k = rng.integers(0, 3, 20000)
+    tgt[np.arange(20000), k] = rng.uniform(0, 8, 20000)
+    D = (tgt - O_).astype(np.float32)
+    tt, tri, det = O.trace_closest(v, t, O_, D, 1e-4, np.inf, use_bvh=False)
+    assert (tri >= 0).all()
+    assert (det > 0).all()  # the shell faces inward: all front-face hits
+
+
+def _random_rays(n, lo, hi, rng):
+    O_ = rng.uniform(lo, hi, (n, 3)).astype(np.float32)
+    D = rng.normal(size=(n, 3)).astype(np.float32)
+    return O_, D
+
+
+@pytest.mark.parametrize("scene", ["room", "city"])
+def test_bvh_equals_brute_force(scene):
+    rng = np.random.default_rng(4)
+    if scene == "room":
+        w = S.box_room(1)
+        O_, D = _random_rays(20000, 0.2, 7.8, rng)
+    else:
+        w = S.small_city(2, n_boxes=200)
+        O_, D = _random_rays(3000, -30, 30, rng)
+        O_[:, 1] = np.abs(O_[:, 1])
+    t1, i1, d1 = O.trace_closest(w.verts, w.idx, O_, D, 1e-4, np.inf, use_bvh=False)
+    t2, i2, d2 = O.trace_closest(w.verts, w.idx, O_, D, 1e-4, np.inf, use_bvh=True)
+    np.testing.assert_array_equal(i1, i2)
+    np.testing.assert_array_equal(t1, t2)
+    a1 = O.trace_any(w.verts, w.idx, O_, D, 0.0, 0.7, use_bvh=False)
+    a2 = O.trace_any(w.verts, w.idx, O_, D, 0.0, 0.7, use_bvh=True)
+    np.testing.assert_array_equal(a1, a2)
+
+
+def test_nearest_hit_ties_take_smaller_index():
+    # two identical triangles: the hit must report the smaller index
+    v = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0]], np.float32)
+    idx = np.array([[0, 1, 2], [0, 1, 2], [0, 1, 2]], np.int32)
+    O_ = np.array([[0.2, 0.2, 1.0]] * 3, np.float32)
+    D = np.array([[0, 0, -1]] * 3, np.float32)
+    for bvh in (False, True):
+        t, tri, _ = O.trace_closest(v, idx, O_, D, 1e-4, np.inf, use_bvh=bvh)
+        assert (tri == 0).all() and (t == 1.0).all()
+
+
+# --------------------------------------------------------------- allocation
+def _alloc_checks(W, avg, rmin, rmax):
+    n, off = O.allocate(W, avg, rmin, rmax)
+    P = len(W)
+    m0 = max(rmin, 8)
+    assert int(n.astype(np.int64).sum()) == avg * P
+    assert (n >= m0).all() and (n <= rmax).all()
+    np.testing.assert_array_equal(off[1:] - off[:-1], n - 8)
+    assert off[0] == 0
+    return n
+
+
+def test_allocation_closed_forms():
+    # uniform when nothing changes: E = P*(avg-m0) spread evenly, remainder to
+    # the lowest indices
+    n = _alloc_checks(np.zeros(5, np.uint32), 11, 8, 40)
+    np.testing.assert_array_equal(n, [11, 11, 11, 11, 11])
+    n = _alloc_checks(np.zeros(4, np.uint32), 9, 6, 40)  # m0 = 8, E = 4
+    np.testing.assert_array_equal(n, [9, 9, 9, 9])
+    n = _alloc_checks(np.zeros(3, np.uint32), 10, 8, 40)
+    np.testing.assert_array_equal(n, [10, 10, 10])
+    # proportional: W = (1, 3), E = 8 -> extras (2, 6)
+    n = _alloc_checks(np.array([1, 3], np.uint32), 12, 8, 100)
+    np.testing.assert_array_equal(n, [10, 14])
+    # cap: probe 1 capped at max, the rest of the extra goes to probe 0
+    n = _alloc_checks(np.array([1, 1000], np.uint32), 16, 8, 18)  # E = 16, cap 10
+    np.testing.assert_array_equal(n, [14, 18])
+    # only one probe changes: it takes min(cap, E), the remainder is spread
+    # one by one over the others in index order
+    n = _alloc_checks(np.array([0, 5, 0, 0], np.uint32), 14, 8, 20)  # E = 24, cap 12
+    np.testing.assert_array_equal(n, [12, 20, 12, 12])
+    # equal weights behave like the uniform case
+    n = _alloc_checks(np.full(3, 7, np.uint32), 10, 8, 40)
+    np.testing.assert_array_equal(n, [10, 10, 10])
+    n = _alloc_checks(np.full(3, 7, np.uint32), 9, 8, 40)  # E = 3 -> one each
+    np.testing.assert_array_equal(n, [9, 9, 9])
+    with pytest.raises(ValueError):
+        O.allocate(np.zeros(3, np.uint32), 7, 8, 40)  # avg below the pilot floor
+
+
+def test_allocation_invariants_random():
+    rng = np.random.default_rng(5)
+    for trial in range(300):
+        P = int(rng.integers(1, 300))
+        rmin = int(rng.integers(4, 20))
+        rmax = int(rng.integers(max(rmin, 8), 300))
+        avg = int(rng.integers(max(rmin, 8), rmax + 1))
+        kind = trial % 4
+        if kind == 0:
+            W = rng.integers(0, 1 << 24, P)
+        elif kind == 1:
+            W = rng.integers(0, 4, P)  # heavy ties and zeros
+        elif kind == 2:
+            W = np.where(rng.random(P) < 0.05, rng.integers(1, 1 << 24, P), 0)  # sparse, caps bite
+        else:
+            W = rng.integers(0, 2, P) * 1000
+        W = W.astype(np.uint32)
+        n = _alloc_checks(W, avg, rmin, rmax)
+        m0 = max(rmin, 8)
+        # scaling all weights by a constant does not change the allocation
+        if W.max() < (1 << 20):
+            n2, _ = O.allocate(W * 7, avg, rmin, rmax)
+            np.testing.assert_array_equal(n, n2)
+        # monotone up to the one-ray remainder
+        order = np.argsort(W, kind="stable")
+        Ws, ns = W[order], n[order].astype(np.int64)
+        for a in range(len(Ws) - 1):
+            if Ws[a + 1] > Ws[a]:
+                assert ns[a + 1] >= ns[a] - 1
+        # proportionality when nothing is capped
+        if W.sum() > 0 and n.max() < rmax:
+            E = (avg - m0) * P
+            share = E * W.astype(np.float64) / W.sum()
+            assert np.all(np.abs((n - m0) - share) < 2.0 + 1e-9)
+
+
+# --------------------------------------------------------------- heuristics
+def test_luts_closed_forms_and_no_boundary_ambiguity():
+    s = math.sqrt(12.0)
+    lv, lc = O.luts(s)
+    assert lv[0] == 1019  # floor(1023 e^{-1/256})
+    assert lv[256] == 137  # f_v at t = s: floor(1023 e^{-2 * 256.5/256}) = floor(137.9)
+    assert (np.diff(lv.astype(int)) <= 0).all() and (np.diff(lc.astype(int)) <= 0).all()
+    # every LUT value is far from an integer boundary, so any faithful exp()
+    # gives the same table
+    i = np.arange(4096)
+    xv = 1023.0 * np.exp(-2.0 * (i + 0.5) / 256.0)
+    xc = 1023.0 * np.exp(-(i + 0.5) * s / 64.0)
+    for x, lut in ((xv, lv), (xc, lc)):
+        frac = x - np.floor(x)
+        big = x >= 1.0
+        assert np.min(np.minimum(frac, 1 - frac)[big]) > 1e-9
+        np.testing.assert_array_equal(np.floor(x).astype(int), lut.astype(int))
+
+
+def _tiny_vol(**kw):
+    args = dict(origin=(0, 0, 0), spacing=(1, 1, 1), dims=(6, 5, 7), rays_avg=16, rays_min=8, rays_max=64,
+                theta=16)
+    args.update(kw)
+    return O.OracleVolume(**args)
+
+
+def test_trigger_impulse_closed_form():
+    # One probe/octant changes between the two frames of a pair: the trigger
+    # jumps to the delta (Fig. TrCam(a)) and then decays linearly over theta
+    # frames; the 5x5x5 x octant convolution spreads it to exactly the
+    # clipped box and the octant's three edge neighbours (Sec. 4.1).
+    v = _tiny_vol()
+    P = v.P
+    X, Y, Z = 6, 5, 7
+    t = np.full((P, 8), 0.5, np.float32)  # all pilot rays hit at t = 0.5
+    tri = np.zeros((P, 8), np.int32)
+    lum0 = np.full((P, 8), 1.0, np.float32)
+    p0 = 2 + X * (1 + Y * 3)  # (2,1,3)
+    o0 = 5
+    lum1 = lum0.copy()
+    lum1[p0, o0] = 3.0  # q_r: 204 -> 613, delta 409
+    v.change_from_pilots(0, t, tri, lum0)
+    assert (v.W() == 0).all()
+    v.change_from_pilots(1, t, tri, lum1)
+    delta = int(np.floor(3.0 * 1023 / 5)) - int(np.floor(1.0 * 1023 / 5))
+    trr = v.trr()
+    assert trr[p0, o0] == delta and trr.sum() == delta and v.trv().sum() == 0
+    qv = v.qv()
+    W = v.W()
+    theta = 16
+    for p in range(P):
+        ix, iy, iz = p % X, (p // X) % Y, p // (X * Y)
+        inbox = abs(ix - 2) <= 2 and abs(iy - 1) <= 2 and abs(iz - 3) <= 2
+        exp = 0
+        for o in range(8):
+            f = delta if inbox and o in (o0, o0 ^ 1, o0 ^ 2, o0 ^ 4) else 0
+            exp += (1023 * int(qv[p, o]) * 2 * f) >> 20
+        assert W[p] == min(exp, (1 << 24) - 1)
+    # linear decay: the pair after is unchanged (lum1 on both frames)
+    for k in range(1, 20):
+        v.change_from_pilots(1 + k, t, tri, lum1)
+        assert v.trr()[p0, o0] == (delta * (theta - k)) // theta if k < theta else v.trr()[p0, o0] == 0
+
+
+def test_static_scene_allocates_uniformly():
+    w = S.box_room(1)
+    vd = w.volume
+    v = O.OracleVolume(vd["origin"], vd["spacing"], vd["dims"], rays_avg=vd["rays_avg"], rays_min=8, rays_max=256)
+    v.set_scene(w.verts, w.idx, w.albedo)
+    light = w.lights_at(0)
+    for f in range(6):
+        v.update(f, 9, light)
+        assert (v.W() == 0).all() and (v.trv() == 0).all() and (v.trr() == 0).all()
+        assert (v.n() == 64).all()
+
+
+def test_light_toggle_pulse_then_linear_decay():
+    w = S.box_room(1)
+    vd = w.volume
+    v = O.OracleVolume(vd["origin"], vd["spacing"], vd["dims"], rays_avg=64, rays_min=8, rays_max=256, theta=8)
+    v.set_scene(w.verts, w.idx, w.albedo)
+    on = w.lights_at(0)
+    v.update(0, 9, [])  # light off on the first frame of the pair
+    v.update(1, 9, on)  # switched on: pulse of |q_r(on) - q_r(off)| = q_r(on)
+    qr_on = v.qr().astype(int)
+    tr1 = v.trr().astype(int)
+    np.testing.assert_array_equal(tr1, qr_on)
+    assert v.W().sum() > 0
+    for k in range(1, 10):
+        v.update(1 + k, 9, on)
+        np.testing.assert_array_equal(v.trr().astype(int), (qr_on * max(0, 8 - k)) // 8)
+
+
+# --------------------------------------------------------------- shading / blend
+def _sky_volume(avg=16, rmin=8, rmax=64, h=0.97, dims=(3, 3, 3)):
+    v = O.OracleVolume((0, 0, 0), (1, 1, 1), dims, rays_avg=avg, rays_min=rmin, rays_max=rmax, hysteresis=h)
+    v.set_scene(np.zeros((3, 3), np.float32), np.zeros((0, 3), np.int32), np.zeros((0, 3), np.float32))
+    return v
+
+
+def test_constant_environment_blends_to_itself():
+    # Texel estimate = texel-average of g (Sec. 3.6): a constant-radiance
+    # environment gives exactly that radiance in every touched texel.
+    v = _sky_volume()
+    c = (0.7, 1.3, 2.9)
+    for f in range(5):
+        v.update(f, 1, [], sky=c)
+        irr, n = v.irr(), v.irr_n()
+        touched = n > 0
+        assert touched.any()
+        c32 = np.array(c, np.float32).astype(np.float64)  # the sky radiance is an FP32 input
+        np.testing.assert_allclose(irr[touched], np.broadcast_to(c32, irr[touched].shape), rtol=1e-15)
+        assert (irr[~touched] == 0).all()
+        dep, dn = v.dep(), v.dep_n()
+        dm = v.depth_max
+        np.testing.assert_allclose(dep[dn > 0][:, 0], dm, rtol=1e-15)
+        np.testing.assert_allclose(dep[dn > 0][:, 1], dm * dm, rtol=1e-14)
+
+
+def _touches(v, frame, seed):
+    """texel sample counts per probe for this frame, recomputed from the ray
+    directions the oracle reports (pilot directions and rotated SF sets)."""
+    P, Ti = v.P, v.Ti
+    k = np.zeros((P, Ti * Ti), np.int64)
+    n = v.n()
+    pd = v.pilot_dir()
+    for p in range(P):
+        dirs = []
+        if frame % 2 == 0:
+            dirs += list(pd[p])
+        m = int(n[p]) - 8
+        dirs += [v.main_dir(m, i) for i in range(m)]
+        for d in dirs:
+            k[p, O.texel_of_dir(d, v.n_irr)] += 1
+    return k.reshape(P, Ti, Ti)
+
+
+def test_true_moving_average_then_hysteresis():
+    # Alg. MovingAvgUpdate: a true running mean while n is small, then an EMA
+    # with weight 1-h.  Closed forms: mean of all samples; step response
+    # c1 + (c0 - c1) * prod(1 - w_f).
+    h = 0.97
+    v = _sky_volume(avg=24, rmax=64, h=h)
+    skies = [0.5, 2.0, 1.0, 4.0]
+    S_ = np.zeros((v.P, v.Ti, v.Ti))
+    K = np.zeros((v.P, v.Ti, v.Ti))
+    for f, c in enumerate(skies):
+        v.update(f, 5, [], sky=(c, c, c))
+        k = _touches(v, f, 5)
+        S_ += k * c
+        K += k
+    irr = v.irr()[..., 0]
+    inner = (slice(None), slice(1, -1), slice(1, -1))
+    sel = K[inner] > 0
+    # every texel here has n small enough for the true-mean regime (n/k < 32)
+    np.testing.assert_allclose(irr[inner][sel], (S_[inner] / np.maximum(K[inner], 1))[sel], rtol=1e-13)
+    # saturated regime: counts at 255, sky steps from 1.0 to 3.0
+    v2 = _sky_volume(avg=8, rmin=8, rmax=8, h=h)
+    Pn = v2.P
+    v2.set_atlas(irr=np.ones((Pn, v2.Ti, v2.Ti, 3)), irr_n=np.full((Pn, v2.Ti, v2.Ti), 255, np.uint8))
+    pred = np.ones((Pn, v2.Ti, v2.Ti))
+    for f in range(8):
+        v2.update(f, 3, [], sky=(3.0, 3.0, 3.0))
+        k = _touches(v2, f, 3)
+        h32 = float(np.float32(h))  # the hysteresis is an FP32 parameter
+        w = np.where(k > 0, np.maximum(1 - h32, k / (255.0 + k)), 0.0)
+        pred = 3.0 + (pred - 3.0) * (1.0 - w)
+    got = v2.irr()[..., 0]
+    np.testing.assert_allclose(got[inner], pred[inner], rtol=1e-12)
+
+
+def test_sphere_depth_moments():
+    # a probe at the centre of a triangulated sphere of radius r: every depth
+    # sample is the distance to a facet, between the inscribed distance and r;
+    # so the mean is r to ~1e-3 and the variance ~ 0.
+    r = 3.0
+    sv, st = S.uv_sphere((0, 0, 0), r, 64, 32, inward=True)
+    # probe 0 sits exactly at the centre; the other probes of the 2x2x2 grid
+    # are off-centre and not checked
+    v = O.OracleVolume((0, 0, 0), (0.25, 0.25, 0.25), (2, 2, 2), rays_avg=200, rays_min=8, rays_max=400,
+                       depth_max=10.0)
+    v.set_scene(sv, st, np.full((len(st), 3), 0.5, np.float32))
+    for f in range(3):
+        v.update(f, 2, [])
+    dep, dn = v.dep()[0], v.dep_n()[0]
+    m = dn > 0
+    assert m.sum() > 150
+    mu, mu2 = dep[m][:, 0], dep[m][:, 1]
+    lo = r * math.cos(math.pi / 64) * math.cos(math.pi / 32)
+    assert (mu <= r * (1 + 1e-6)).all() and (mu >= lo * (1 - 1e-6)).all()
+    assert abs(mu.mean() - r) < 2e-3 * r
+    assert np.max(np.abs(mu2 - mu * mu)) < 1e-3 * r * r
+
+
+def test_direct_light_closed_form_and_shadow():
+    # a large floor (albedo a) under a point light of intensity I: a probe
+    # ray hitting x has radiance a/pi * I * cos / d^2 (Sec. 4.1 f_r uses the
+    # direct light at the hit); an occluder between removes it.
+    fv, ft = S.grid_plane(-50, 50, -50, 50, 0.0, 1, 1)
+    a = np.array([0.5, 0.25, 0.75], np.float32)
+    v = O.OracleVolume((-1, 1, -1), (2, 2, 2), (2, 2, 2), rays_avg=8, rays_min=8, rays_max=8, depth_max=1000.0)
+    v.set_scene(fv, ft, np.tile(a, (len(ft), 1)))
+    L = np.array([0.3, 10.0, -0.2])
+    I = 100.0
+    v.update(0, 4, [(0, L, (I, I, I))], sky=(0.2, 0.2, 0.2))
+    tri = v.pilot_tri()
+    t = v.pilot_t()
+    dirs = v.pilot_dir()
+    rad = v.pilot_rad()
+    lum = v.pilot_lum()
+    for p in range(v.P):
+        o = v.probe_pos(p).astype(np.float64)
+        for k in range(8):
+            d = dirs[p, k].astype(np.float64)
+            tp = -o[1] / d[1] if d[1] < 0 else np.inf
+            xp = o + tp * d if np.isfinite(tp) else None
+            if xp is None or max(abs(xp[0]), abs(xp[2])) > 49.9:
+                assert tri[p, k] < 0  # leaves above the floor or beyond its edge
+                np.testing.assert_allclose(rad[p, k], np.float32(0.2))
+                continue
+            assert tri[p, k] >= 0
+            x = o + float(t[p, k]) * d
+            assert abs(x[1]) < 1e-5
+            Dl = L - x
+            g = Dl[1] / np.linalg.norm(Dl) ** 3
+            ref = a.astype(np.float64) / math.pi * I * g
+            np.testing.assert_allclose(rad[p, k], ref, rtol=2e-6)
+            lref = 0.2126 * ref[0] + 0.7152 * ref[1] + 0.0722 * ref[2]
+            assert abs(lum[p, k] - lref) < 1e-5 * max(1.0, lref)
+    # occluder: a big horizontal quad at y = 5 facing down blocks the light
+    ov, ot = S.grid_plane(-50, 50, -50, 50, 5.0, 1, 1)
+    allv = np.concatenate([fv, ov])
+    allt = np.concatenate([ft, ot + len(fv)])
+    # fresh volume: the atlas is empty, so the multi-bounce term is 0 too
+    v = O.OracleVolume((-1, 1, -1), (2, 2, 2), (2, 2, 2), rays_avg=8, rays_min=8, rays_max=8, depth_max=1000.0)
+    v.set_scene(allv, allt, np.tile(a, (len(allt), 1)))
+    v.update(2, 4, [(0, L, (I, I, I))], sky=(0.2, 0.2, 0.2))
+    rad, tri = v.pilot_rad(), v.pilot_tri()
+    floor_hits = (tri >= 0) & (tri < len(ft))
+    assert floor_hits.any()
+    assert (rad[floor_hits] == 0).all()
+
+
+def test_backface_hits_are_black():
+    v, t = S.boxes_mesh([[-5, -5, -5]], [[5, 5, 5]], inward=False)  # outward: probes see back faces
+    vol = O.OracleVolume((-1, -1, -1), (2, 2, 2), (2, 2, 2), rays_avg=8, rays_min=8, rays_max=8)
+    vol.set_scene(v, t, np.full((len(t), 3), 0.8, np.float32))
+    vol.update(0, 1, [(0, (0, 4, 0), (50, 50, 50))], sky=(1, 1, 1))
+    assert (vol.pilot_tri() >= 0).all()
+    assert (vol.pilot_rad() == 0).all()
+
+
+# --------------------------------------------------------------- query
+def _query_volume(values, depth_mu, depth_mu2=None):
+    v = O.OracleVolume((0, 0, 0), (1, 1, 1), (2, 2, 2), rays_avg=8, rays_min=8, rays_max=8)
+    P = 8
+    irr = np.zeros((P, v.Ti, v.Ti, 3))
+    dep = np.zeros((P, v.Td, v.Td, 2))
+    for p in range(P):
+        irr[p] = values[p]
+        dep[p, ..., 0] = depth_mu[p]
+        dep[p, ..., 1] = depth_mu[p] ** 2 if depth_mu2 is None else depth_mu2[p]
+    v.set_atlas(irr=irr, dep=dep)
+    return v
+
+
+def test_query_equal_probes_and_trilinear():
+    rng = np.random.default_rng(6)
+    v = _query_volume([np.array([0.3, 0.6, 0.9])] * 8, [10.0] * 8)
+    pts = rng.uniform(0, 1, (100, 3)).astype(np.float32)
+    nrm = rng.normal(size=(100, 3)).astype(np.float32)
+    np.testing.assert_allclose(v.query(pts, nrm), np.tile([0.3, 0.6, 0.9], (100, 1)), rtol=1e-14)
+    # distinct constant probes, depth far away: Chebyshev weight 1 -> plain
+    # trilinear interpolation (weights sum to 1)
+    vals = rng.uniform(0, 5, (8, 3))
+    v = _query_volume(list(vals), [10.0] * 8)
+    q = v.query(pts, nrm)
+    for i, x in enumerate(pts.astype(np.float64)):
+        ref = np.zeros(3)
+        for c in range(8):
+            o = [(c >> k) & 1 for k in range(3)]
+            w = np.prod([x[k] if o[k] else 1 - x[k] for k in range(3)])
+            ref += w * vals[c]
+        np.testing.assert_allclose(q[i], ref, rtol=1e-12)
+    # a point exactly on probe 5 returns probe 5's value
+    q = v.query(np.array([[1, 0, 1]], np.float32), np.array([[0, 1, 0]], np.float32))
+    np.testing.assert_allclose(q[0], vals[5], rtol=1e-14)
+
+
+def test_query_chebyshev_weight():
+    # probe 0 sees a wall at mean depth 0.1 with zero variance: for a point at
+    # distance d > mu its weight is scaled by var/(var + (d-mu)^2), var floored
+    # at 1e-6 s^2 (one-sided Chebyshev bound, VSM).
+    rng = np.random.default_rng(7)
+    vals = rng.uniform(0, 5, (8, 3))
+    mu = [0.1] + [10.0] * 7
+    v = _query_volume(list(vals), mu)
+    s2 = 3.0
+    x = np.array([0.5, 0.25, 0.4])
+    q = v.query(x[None].astype(np.float32), np.array([[0, 0, 1]], np.float32))[0]
+    xf = x.astype(np.float32).astype(np.float64)
+    ref_w = []
+    for c in range(8):
+        o = [(c >> k) & 1 for k in range(3)]
+        w = np.prod([xf[k] if o[k] else 1 - xf[k] for k in range(3)])
+        if c == 0:
+            d = np.linalg.norm(xf)
+            var = 1e-6 * s2
+            w *= var / (var + (d - 0.1) ** 2)
+        ref_w.append(w)
+    ref_w = np.array(ref_w)
+    np.testing.assert_allclose(q, (ref_w[:, None] * vals).sum(0) / ref_w.sum(), rtol=1e-12)
