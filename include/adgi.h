@@ -1,0 +1,233 @@
+/*
+ * adgi.h -- C ABI of the GB300 (sm_103a) per-frame probe update of
+ * "Adaptive Dynamic Global Illumination" (Datta, Goli, Zhang, arXiv 2301.05125).
+ *
+ * One volume = a uniform probe grid with an octahedral irradiance atlas and an
+ * octahedral depth-moment atlas (Sec. 3.1, Fig. probeStructure), a triangle
+ * scene, and the per-probe heuristic state of Sec. 4.1.  Each adgi_update()
+ * runs the whole frame on the device, in this order:
+ *   1. pilot rays: 8 per probe, one per octant, directions fixed for a pair of
+ *      frames (Sec. 4.4 "Improving construction efficiency");
+ *   2. heuristics: f_v (Eq. ProbeVis), f_r (Sec. 4.1 "Incoming radiance"),
+ *      temporal gradients (Eq. tempGradVis, tempGradIrr), trigger Tr
+ *      (Fig. TrCam(a)), 5x5x5 x octant convolution, composition
+ *      f_d = f_c f_v (f_dv + mu f_dr) (Eq. priorDynamic, mu = 2), quantised
+ *      to integers;
+ *   3. allocation of a fixed total ray budget over the probes by f_d
+ *      (Sec. 3.4: the sample count is an input, decoupled from the probe count);
+ *   4. tracing of every probe's rays against the scene (Alg. ApproxAlgo
+ *      "evaluate sample, ray-trace") through a software BVH;
+ *   5. shading: direct light with shadow rays plus a multi-bounce term
+ *      albedo * Q_{t-1}(x, n) read from the atlases of the previous frame;
+ *   6. blending: every sample updates its nearest texel with the moving
+ *      average of Alg. MovingAvgUpdate (batched per texel, hysteresis h),
+ *      followed by the octahedral border copy.
+ * adgi_query_irradiance() is the 8-probe trilinear lookup with Chebyshev
+ * visibility weights (Sec. 3.1; g_c of Table "List of symbols").
+ *
+ * Conventions for every call:
+ *   - return ADGI_OK (0) or a negative ADGI_ERR_* code; adgi_last_error()
+ *     returns a message for the calling thread's last failure;
+ *   - every array argument is row-major, tightly packed; "host" pointers are
+ *     plain host memory (pageable or pinned), "device" pointers are CUDA
+ *     device memory of the volume's device;
+ *   - the caller owns every array it passes; the library copies what it keeps
+ *     and never frees caller memory;
+ *   - all device work of a volume is ordered on the stream given at creation
+ *     (adgi_set_stream() changes it); calls return once the work is enqueued
+ *     unless they read results back into host memory;
+ *   - a handle must not be used from two threads at once; different handles
+ *     are independent.
+ * Device memory is owned by the library and released by adgi_destroy().
+ */
+#ifndef ADGI_H
+#define ADGI_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ADGI_OK 0
+#define ADGI_ERR_INVALID_ARG (-1) /* an argument is out of range or NULL */
+#define ADGI_ERR_OOM (-2)         /* a device or host allocation failed */
+#define ADGI_ERR_OVER_BUDGET (-3) /* the volume does not fit the memory budget */
+#define ADGI_ERR_NO_SCENE (-4)    /* adgi_update() before adgi_set_scene() */
+#define ADGI_ERR_CUDA (-5)        /* a CUDA call failed (message in adgi_last_error) */
+#define ADGI_ERR_TIMEOUT (-6)     /* a bounded device-side wait gave up */
+
+typedef struct adgi_volume_s* adgi_volume;
+
+/* Probe grid and update parameters.  Probe (i,j,k) sits at
+ * origin + spacing * (i,j,k) (FP32), with probe index i + dims[0]*(j + dims[1]*k). */
+typedef struct {
+    float origin[3];
+    float spacing[3];
+    int32_t dims[3];        /* >= 2 each */
+    int32_t irr_interior;   /* irradiance tile interior n (tile n+2 with border); 8x8 tiles: 6 (Sec. 3.1) */
+    int32_t depth_interior; /* depth tile interior n; 16x16 tiles: 14 */
+    int32_t rays_avg;       /* fixed budget: rays_avg * probes rays per update, pilots included */
+    int32_t rays_min;       /* per-probe floor; the effective floor is max(rays_min, 8) (the pilots) */
+    int32_t rays_max;       /* per-probe cap, <= 4096 */
+    float hysteresis;       /* h of the moving average, in [0, 1) (Table cacheDetails: 0.98 / 0.91) */
+    float depth_max;        /* depth clamp and miss depth; <= 0 selects 1.5 * voxel diagonal */
+    int32_t atlas_fp16;     /* 1: atlases stored as half, blended in FP32 */
+    int32_t tr_theta;       /* trigger decay length theta in frames (Fig. TrCam(a)), >= 1, <= 255 */
+} adgi_volume_desc;
+
+/* kind 0: point light at pos_or_dir with intensity rgb (irradiance rgb/d^2);
+ * kind 1: directional light travelling along pos_or_dir with irradiance rgb. */
+typedef struct {
+    int32_t kind;
+    float pos_or_dir[3];
+    float rgb[3];
+} adgi_light;
+
+/* Per-frame input.  frame numbers pair up as (2k, 2k+1): both frames of a pair
+ * trace the same pilot rays; the change is measured on the second (Sec. 4.4). */
+typedef struct {
+    uint64_t frame;
+    uint64_t seed;
+    const adgi_light* lights; /* host array of n_lights, copied at the call */
+    int32_t n_lights;         /* 0..64 */
+    float sky_rgb[3];         /* radiance of rays that escape the scene */
+    int32_t has_camera;       /* 1: apply the camera-distance heuristic f_c (Eq. cameraD) */
+    float cam_pos[3];
+    float cam_k;              /* f_c = 1 within cam_k of the camera */
+} adgi_frame;
+
+typedef struct {
+    uint64_t frames;          /* updates run so far */
+    uint64_t rays_per_update; /* rays_avg * probes: pilot + adaptive rays */
+    uint64_t pilot_rays;      /* 8 * probes */
+    uint64_t shadow_rays;     /* shadow rays of the last update (counted on the device) */
+    uint32_t bvh_nodes;       /* internal nodes of the current BVH */
+    uint32_t n_tris;
+    uint64_t device_bytes;    /* device memory held by the volume */
+    float ms_last_update;     /* device time of the last update (0 unless timing was enabled) */
+} adgi_stats;
+
+/* Create a volume on the current CUDA device.  desc: host pointer, copied.
+ * cuda_stream: a cudaStream_t (NULL = legacy default stream).  *out receives
+ * the handle.  Allocates the atlases (zeroed), the heuristic state and the
+ * ray buffers for rays_avg * probes rays.  Errors: INVALID_ARG (NULL
+ * pointers, dims < 2, tile sizes < 1, rays_avg outside
+ * [max(rays_min, 8), rays_max], hysteresis outside [0,1), theta outside
+ * [1,255]), OOM, CUDA. */
+int adgi_create_volume(const adgi_volume_desc* desc, void* cuda_stream, adgi_volume* out);
+
+/* Replace the scene: n_verts xyz vertices (float[3*n_verts]), n_tris
+ * triangles of vertex indices (int32[3*n_tris], counter-clockwise = front,
+ * normal (B-A)x(C-A)), per-triangle albedo (float[3*n_tris]).  Pointers are
+ * host memory, or device memory when ptrs_on_device = 1; they are copied.
+ * The BVH is rebuilt on the volume's stream.  Errors: INVALID_ARG (an index
+ * outside [0, n_verts), negative counts), OOM, CUDA. */
+int adgi_set_scene(adgi_volume vol, const float* verts_xyz, int32_t n_verts, const int32_t* tri_idx,
+                   int32_t n_tris, const float* tri_albedo_rgb, int32_t ptrs_on_device);
+
+/* Overwrite vertices [first, first+count) with verts_xyz (host, or device
+ * when ptrs_on_device = 1) -- moving geometry (the paper's dynamic gate,
+ * Sec. 5).  The BVH is rebuilt at the next adgi_update().  Errors:
+ * INVALID_ARG (range outside the scene), NO_SCENE, CUDA. */
+int adgi_move_vertices(adgi_volume vol, int32_t first, int32_t count, const float* verts_xyz,
+                       int32_t ptrs_on_device);
+
+/* Run one per-frame update (steps 1-6 above) on the volume's stream.  Host
+ * data of *frame is copied before return; the call does not wait for the
+ * device.  Errors: INVALID_ARG, NO_SCENE, CUDA, TIMEOUT. */
+int adgi_update(adgi_volume vol, const adgi_frame* frame);
+
+/* Irradiance query at n points with normals (float[3*n] each): 8-probe
+ * trilinear interpolation weighted by the one-sided Chebyshev bound of the
+ * depth moments; out_rgb (float[3*n]).  Pointers are host memory (the call
+ * copies in, runs, copies out and synchronises the stream) or device memory
+ * when ptrs_on_device = 1 (enqueued only).  Errors: INVALID_ARG, OOM, CUDA. */
+int adgi_query_irradiance(adgi_volume vol, const float* pos, const float* nrm, int32_t n, float* out_rgb,
+                          int32_t ptrs_on_device);
+
+/* Counters of the volume; synchronises the stream.  Errors: INVALID_ARG, CUDA. */
+int adgi_get_stats(adgi_volume vol, adgi_stats* out);
+
+/* Destroy the volume: waits for its stream, frees its device memory.
+ * NULL is accepted. */
+int adgi_destroy(adgi_volume vol);
+
+/* ---------------------------------------------------------------------------
+ * Additional entry points.
+ * ------------------------------------------------------------------------- */
+
+/* Use another stream for all later work of the volume (cudaStream_t). */
+int adgi_set_stream(adgi_volume vol, void* cuda_stream);
+
+/* 1: time each adgi_update() with CUDA events (adgi_stats.ms_last_update). */
+int adgi_enable_timing(adgi_volume vol, int32_t enable);
+
+/* Debug readers: copy a piece of the volume's device state into host memory
+ * dst (bytes must equal adgi_state_bytes()); synchronises the stream.
+ * Layouts (P probes, Ti = irr_interior+2, Td = depth_interior+2, R = main rays
+ * = (rays_avg - 8) * P):
+ *   ADGI_STATE_W        uint32[P]        change weight W_p of the last update
+ *   ADGI_STATE_N        uint32[P]        rays of probe p (pilots included)
+ *   ADGI_STATE_OFF      uint32[P+1]      exclusive prefix of n_p - 8 (main rays)
+ *   ADGI_STATE_QV/QR    uint16[P][8]     quantised f_v / f_r of the last update
+ *   ADGI_STATE_TRV/TRR  uint16[P][8]     trigger outputs
+ *   ADGI_STATE_PILOT_HIT int32[P][8][2]  {tri (-1 miss; bit 31 = back face), t bits}
+ *   ADGI_STATE_PILOT_REC float[P][8][4]  {r, g, b, depth sample}
+ *   ADGI_STATE_PILOT_LUM float[P][8]     FP32 luminance of the direct light (f_r input)
+ *   ADGI_STATE_MAIN_HIT int32[R][2]      as PILOT_HIT, rays in probe order
+ *   ADGI_STATE_MAIN_REC float[R][4]
+ *   ADGI_STATE_IRR      float[P][Ti][Ti][4] {r,g,b,count} (half[...][4] when atlas_fp16)
+ *   ADGI_STATE_DEP      float[P][Td][Td][2] {mean, mean^2} (half[...][2] when atlas_fp16)
+ *   ADGI_STATE_DEP_N    uint8[P][Td][Td]  depth sample counts
+ *   ADGI_STATE_ROT      float[9]          main-ray rotation of the last update
+ */
+enum {
+    ADGI_STATE_W = 0,
+    ADGI_STATE_N = 1,
+    ADGI_STATE_OFF = 2,
+    ADGI_STATE_QV = 3,
+    ADGI_STATE_QR = 4,
+    ADGI_STATE_TRV = 5,
+    ADGI_STATE_TRR = 6,
+    ADGI_STATE_PILOT_HIT = 7,
+    ADGI_STATE_PILOT_REC = 8,
+    ADGI_STATE_PILOT_LUM = 9,
+    ADGI_STATE_MAIN_HIT = 10,
+    ADGI_STATE_MAIN_REC = 11,
+    ADGI_STATE_IRR = 12,
+    ADGI_STATE_DEP = 13,
+    ADGI_STATE_DEP_N = 14,
+    ADGI_STATE_ROT = 15
+};
+int adgi_state_bytes(adgi_volume vol, int32_t which, uint64_t* bytes);
+int adgi_read_state(adgi_volume vol, int32_t which, void* dst_host, uint64_t bytes);
+
+/* Overwrite the atlases from host memory (same layouts as ADGI_STATE_IRR /
+ * _DEP / _DEP_N; any pointer may be NULL to keep that part).  For tests and
+ * for restoring a saved state. */
+int adgi_write_atlas(adgi_volume vol, const void* irr, const void* dep, const uint8_t* dep_n);
+
+/* Trace n rays (origins o, directions d: float[3*n], device memory) against
+ * the volume's current scene: nearest hit with t in (tmin, tmax], ties broken
+ * by the smaller triangle index; writes t_out (float[n], tmax on a miss) and
+ * tri_out (int32[n], -1 on a miss, bit 31 set for a back-face hit).  The same
+ * watertight test and BVH as the update.  Enqueued on the volume's stream. */
+int adgi_trace_closest(adgi_volume vol, const float* o, const float* d, int32_t n, float tmin, float tmax,
+                       float* t_out, int32_t* tri_out);
+
+/* Ray allocation of step 3 as a stand-alone call on device arrays:
+ * W (uint32[P]) -> n_out (uint32[P], pilots included, sum = rays_avg * P),
+ * off_out (uint32[P+1], exclusive prefix of n_p - 8).  Enqueued on
+ * cuda_stream.  Errors: INVALID_ARG when the budget cannot be met. */
+int adgi_allocate_rays(const uint32_t* W, int32_t P, int32_t rays_avg, int32_t rays_min, int32_t rays_max,
+                       uint32_t* n_out, uint32_t* off_out, void* cuda_stream);
+
+/* Message of the calling thread's last error ("" if none). */
+const char* adgi_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ADGI_H */

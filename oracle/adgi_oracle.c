@@ -1142,8 +1142,11 @@ static void query_point(const orc_vol* v, const double x[3], const double nrm[3]
         bilinear(v->dep + (size_t)p * v->Td * v->Td * 2, v->Td, v->d.n_dep, 2, dir, mom);
         double wc = 1.0;
         if (dist > mom[0]) {
+            /* one-sided Chebyshev bound with a minimum variance (as in variance
+               shadow maps): max(mu2 - mu^2, 1e-3 mu2, 1e-6 s^2) */
             double var = mom[1] - mom[0] * mom[0];
-            if (var < varmin) var = varmin;
+            double vfloor = 1e-3 * mom[1] > varmin ? 1e-3 * mom[1] : varmin;
+            if (var < vfloor) var = vfloor;
             double dd = dist - mom[0];
             wc = var / (var + dd * dd);
         }

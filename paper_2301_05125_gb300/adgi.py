@@ -1,0 +1,368 @@
+"""Thin ctypes binding of the C ABI in include/adgi.h.
+
+Argument marshalling only: every step of the update runs in the CUDA kernels
+of libadgi.so.  There is no fallback: if the library is missing or fails to
+load, every call raises.  PyTorch is used only to hand over device memory
+(tensor data pointers) and streams.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libadgi.so")
+
+ADGI_OK = 0
+ERRORS = {-1: "INVALID_ARG", -2: "OOM", -3: "OVER_BUDGET", -4: "NO_SCENE", -5: "CUDA", -6: "TIMEOUT"}
+
+STATE = dict(W=0, N=1, OFF=2, QV=3, QR=4, TRV=5, TRR=6, PILOT_HIT=7, PILOT_REC=8, PILOT_LUM=9, MAIN_HIT=10,
+             MAIN_REC=11, IRR=12, DEP=13, DEP_N=14, ROT=15)
+
+
+class AdgiError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("adgi error %d (%s): %s" % (code, ERRORS.get(code, "?"), msg))
+        self.code = code
+
+
+class adgi_volume_desc(C.Structure):
+    _fields_ = [
+        ("origin", C.c_float * 3),
+        ("spacing", C.c_float * 3),
+        ("dims", C.c_int32 * 3),
+        ("irr_interior", C.c_int32),
+        ("depth_interior", C.c_int32),
+        ("rays_avg", C.c_int32),
+        ("rays_min", C.c_int32),
+        ("rays_max", C.c_int32),
+        ("hysteresis", C.c_float),
+        ("depth_max", C.c_float),
+        ("atlas_fp16", C.c_int32),
+        ("tr_theta", C.c_int32),
+    ]
+
+
+class adgi_light(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("pos_or_dir", C.c_float * 3), ("rgb", C.c_float * 3)]
+
+
+class adgi_frame(C.Structure):
+    _fields_ = [
+        ("frame", C.c_uint64),
+        ("seed", C.c_uint64),
+        ("lights", C.POINTER(adgi_light)),
+        ("n_lights", C.c_int32),
+        ("sky_rgb", C.c_float * 3),
+        ("has_camera", C.c_int32),
+        ("cam_pos", C.c_float * 3),
+        ("cam_k", C.c_float),
+    ]
+
+
+class adgi_stats(C.Structure):
+    _fields_ = [
+        ("frames", C.c_uint64),
+        ("rays_per_update", C.c_uint64),
+        ("pilot_rays", C.c_uint64),
+        ("shadow_rays", C.c_uint64),
+        ("bvh_nodes", C.c_uint32),
+        ("n_tris", C.c_uint32),
+        ("device_bytes", C.c_uint64),
+        ("ms_last_update", C.c_float),
+    ]
+
+
+EXPORTED = ["adgi_create_volume", "adgi_set_scene", "adgi_move_vertices", "adgi_update", "adgi_query_irradiance",
+            "adgi_get_stats", "adgi_destroy", "adgi_set_stream", "adgi_enable_timing", "adgi_state_bytes",
+            "adgi_read_state", "adgi_write_atlas", "adgi_trace_closest", "adgi_allocate_rays", "adgi_last_error"]
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libadgi.so (raises if it is missing: there is no fallback path)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("libadgi.so not built (%s); run __graft_entry__.build()" % path)
+    L = C.CDLL(path)
+    vp, i32, u64 = C.c_void_p, C.c_int32, C.c_uint64
+    L.adgi_create_volume.argtypes = [C.POINTER(adgi_volume_desc), vp, C.POINTER(vp)]
+    L.adgi_set_scene.argtypes = [vp, vp, i32, vp, i32, vp, i32]
+    L.adgi_move_vertices.argtypes = [vp, i32, i32, vp, i32]
+    L.adgi_update.argtypes = [vp, C.POINTER(adgi_frame)]
+    L.adgi_query_irradiance.argtypes = [vp, vp, vp, i32, vp, i32]
+    L.adgi_get_stats.argtypes = [vp, C.POINTER(adgi_stats)]
+    L.adgi_destroy.argtypes = [vp]
+    L.adgi_set_stream.argtypes = [vp, vp]
+    L.adgi_enable_timing.argtypes = [vp, i32]
+    L.adgi_state_bytes.argtypes = [vp, i32, C.POINTER(u64)]
+    L.adgi_read_state.argtypes = [vp, i32, vp, u64]
+    L.adgi_write_atlas.argtypes = [vp, vp, vp, vp]
+    L.adgi_trace_closest.argtypes = [vp, vp, vp, i32, C.c_float, C.c_float, vp, vp]
+    L.adgi_allocate_rays.argtypes = [vp, i32, i32, i32, i32, vp, vp, vp]
+    L.adgi_last_error.restype = C.c_char_p
+    for name in EXPORTED[:-1]:
+        getattr(L, name).restype = C.c_int
+    _lib = L
+    return L
+
+
+def _check(rc):
+    if rc != ADGI_OK:
+        raise AdgiError(rc, load().adgi_last_error().decode(errors="replace"))
+
+
+def _ptr(x):
+    """data pointer of a numpy array or a torch tensor (device or host)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    return x.data_ptr()
+
+
+def _is_dev(x):
+    return not isinstance(x, np.ndarray) and getattr(x, "is_cuda", False)
+
+
+# ------------------------------------------------------------ C-ABI, same names
+def adgi_create_volume(desc: adgi_volume_desc, stream=None):
+    h = C.c_void_p()
+    _check(load().adgi_create_volume(C.byref(desc), stream, C.byref(h)))
+    return h
+
+
+def adgi_set_scene(vol, verts, idx, albedo):
+    on_dev = _is_dev(verts)
+    nv = int(verts.shape[0]) if verts.ndim == 2 else int(verts.shape[0] // 3)
+    nt = int(idx.shape[0]) if idx.ndim == 2 else int(idx.shape[0] // 3)
+    _check(load().adgi_set_scene(vol, _ptr(verts), nv, _ptr(idx), nt, _ptr(albedo), int(on_dev)))
+
+
+def adgi_move_vertices(vol, first, verts):
+    on_dev = _is_dev(verts)
+    n = int(verts.shape[0]) if verts.ndim == 2 else int(verts.shape[0] // 3)
+    _check(load().adgi_move_vertices(vol, int(first), n, _ptr(verts), int(on_dev)))
+
+
+def adgi_update(vol, frame: adgi_frame):
+    _check(load().adgi_update(vol, C.byref(frame)))
+
+
+def adgi_query_irradiance(vol, pos, nrm, out):
+    on_dev = _is_dev(pos)
+    n = int(pos.shape[0]) if pos.ndim == 2 else int(pos.shape[0] // 3)
+    _check(load().adgi_query_irradiance(vol, _ptr(pos), _ptr(nrm), n, _ptr(out), int(on_dev)))
+
+
+def adgi_get_stats(vol) -> adgi_stats:
+    st = adgi_stats()
+    _check(load().adgi_get_stats(vol, C.byref(st)))
+    return st
+
+
+def adgi_destroy(vol):
+    _check(load().adgi_destroy(vol))
+
+
+def adgi_set_stream(vol, stream):
+    _check(load().adgi_set_stream(vol, stream))
+
+
+def adgi_enable_timing(vol, enable=True):
+    _check(load().adgi_enable_timing(vol, int(bool(enable))))
+
+
+def adgi_state_bytes(vol, which) -> int:
+    b = C.c_uint64()
+    _check(load().adgi_state_bytes(vol, STATE[which] if isinstance(which, str) else int(which), C.byref(b)))
+    return int(b.value)
+
+
+def adgi_read_state(vol, which, dtype) -> np.ndarray:
+    nb = adgi_state_bytes(vol, which)
+    out = np.empty(nb // np.dtype(dtype).itemsize, dtype)
+    _check(load().adgi_read_state(vol, STATE[which] if isinstance(which, str) else int(which), out.ctypes.data, nb))
+    return out
+
+
+def adgi_write_atlas(vol, irr=None, dep=None, dep_n=None):
+    keep = [np.ascontiguousarray(a) if a is not None else None for a in (irr, dep, dep_n)]
+    _check(load().adgi_write_atlas(vol, *[_ptr(a) for a in keep]))
+
+
+def adgi_trace_closest(vol, o, d, tmin, tmax, t_out, tri_out):
+    n = int(o.shape[0]) if o.ndim == 2 else int(o.shape[0] // 3)
+    _check(load().adgi_trace_closest(vol, _ptr(o), _ptr(d), n, float(tmin), float(tmax), _ptr(t_out), _ptr(tri_out)))
+
+
+def adgi_allocate_rays(W, rays_avg, rays_min, rays_max, n_out, off_out, stream=None):
+    _check(load().adgi_allocate_rays(_ptr(W), int(W.shape[0]), int(rays_avg), int(rays_min), int(rays_max),
+                                     _ptr(n_out), _ptr(off_out), stream))
+
+
+def adgi_last_error() -> str:
+    return load().adgi_last_error().decode(errors="replace")
+
+
+# ------------------------------------------------------------ convenience
+def make_desc(origin, spacing, dims, irr_interior=6, depth_interior=14, rays_avg=64, rays_min=8, rays_max=256,
+              hysteresis=0.97, depth_max=0.0, atlas_fp16=0, tr_theta=16) -> adgi_volume_desc:
+    d = adgi_volume_desc()
+    d.origin[:] = [float(x) for x in origin]
+    d.spacing[:] = [float(x) for x in spacing]
+    d.dims[:] = [int(x) for x in dims]
+    d.irr_interior, d.depth_interior = int(irr_interior), int(depth_interior)
+    d.rays_avg, d.rays_min, d.rays_max = int(rays_avg), int(rays_min), int(rays_max)
+    d.hysteresis = float(hysteresis)
+    d.depth_max = float(depth_max)
+    d.atlas_fp16 = int(atlas_fp16)
+    d.tr_theta = int(tr_theta)
+    return d
+
+
+def make_frame(frame, seed, lights, sky=(0.0, 0.0, 0.0), camera=None) -> adgi_frame:
+    arr = (adgi_light * max(1, len(lights)))()
+    for i, (kind, v, rgb) in enumerate(lights):
+        arr[i].kind = int(kind)
+        arr[i].pos_or_dir[:] = [float(x) for x in v]
+        arr[i].rgb[:] = [float(x) for x in rgb]
+    f = adgi_frame()
+    f.frame = int(frame)
+    f.seed = int(seed)
+    f.lights = C.cast(arr, C.POINTER(adgi_light))
+    f.n_lights = len(lights)
+    f.sky_rgb[:] = [float(x) for x in sky]
+    if camera is not None:
+        f.has_camera = 1
+        f.cam_pos[:] = [float(x) for x in camera[0]]
+        f.cam_k = float(camera[1])
+    f._keep = arr
+    return f
+
+
+class Volume:
+    """Owning wrapper of an adgi_volume handle."""
+
+    def __init__(self, stream=None, **desc):
+        self.desc = make_desc(**desc)
+        self.h = adgi_create_volume(self.desc, stream)
+        d = self.desc
+        self.P = d.dims[0] * d.dims[1] * d.dims[2]
+        self.Ti, self.Td = d.irr_interior + 2, d.depth_interior + 2
+        self.fp16 = bool(d.atlas_fp16)
+
+    def close(self):
+        if self.h:
+            adgi_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_scene(self, verts, idx, albedo):
+        if isinstance(verts, np.ndarray):
+            verts = np.ascontiguousarray(verts, np.float32)
+            idx = np.ascontiguousarray(idx, np.int32)
+            albedo = np.ascontiguousarray(albedo, np.float32)
+        adgi_set_scene(self.h, verts, idx, albedo)
+
+    def move_vertices(self, first, verts):
+        if isinstance(verts, np.ndarray):
+            verts = np.ascontiguousarray(verts, np.float32)
+        adgi_move_vertices(self.h, first, verts)
+
+    def update(self, frame, seed, lights, sky=(0, 0, 0), camera=None):
+        adgi_update(self.h, make_frame(frame, seed, lights, sky, camera))
+
+    def query(self, pos, nrm, out=None):
+        if isinstance(pos, np.ndarray):
+            pos = np.ascontiguousarray(pos, np.float32)
+            nrm = np.ascontiguousarray(nrm, np.float32)
+            out = np.empty_like(pos) if out is None else out
+        adgi_query_irradiance(self.h, pos, nrm, out)
+        return out
+
+    def stats(self):
+        return adgi_get_stats(self.h)
+
+    def state(self, which, dtype):
+        return adgi_read_state(self.h, which, dtype)
+
+    # typed readers
+    def W(self):
+        return self.state("W", np.uint32)
+
+    def n(self):
+        return self.state("N", np.uint32)
+
+    def off(self):
+        return self.state("OFF", np.uint32)
+
+    def qv(self):
+        return self.state("QV", np.uint16).reshape(self.P, 8)
+
+    def qr(self):
+        return self.state("QR", np.uint16).reshape(self.P, 8)
+
+    def trv(self):
+        return self.state("TRV", np.uint16).reshape(self.P, 8)
+
+    def trr(self):
+        return self.state("TRR", np.uint16).reshape(self.P, 8)
+
+    def pilot_hit(self):
+        return self.state("PILOT_HIT", np.int32).reshape(self.P, 8, 2)
+
+    def pilot_rec(self):
+        return self.state("PILOT_REC", np.float32).reshape(self.P, 8, 4)
+
+    def pilot_lum(self):
+        return self.state("PILOT_LUM", np.float32).reshape(self.P, 8)
+
+    def main_hit(self):
+        return self.state("MAIN_HIT", np.int32).reshape(-1, 2)
+
+    def main_rec(self):
+        return self.state("MAIN_REC", np.float32).reshape(-1, 4)
+
+    def irr(self):
+        dt = np.float16 if self.fp16 else np.float32
+        return self.state("IRR", dt).reshape(self.P, self.Ti, self.Ti, 4).astype(np.float32)
+
+    def dep(self):
+        dt = np.float16 if self.fp16 else np.float32
+        return self.state("DEP", dt).reshape(self.P, self.Td, self.Td, 2).astype(np.float32)
+
+    def dep_n(self):
+        return self.state("DEP_N", np.uint8).reshape(self.P, self.Td, self.Td)
+
+    def rotation(self):
+        return self.state("ROT", np.float32).reshape(3, 3)
+
+    def write_atlas(self, irr=None, dep=None, dep_n=None):
+        dt = np.float16 if self.fp16 else np.float32
+        adgi_write_atlas(self.h, None if irr is None else np.ascontiguousarray(irr, dt),
+                         None if dep is None else np.ascontiguousarray(dep, dt),
+                         None if dep_n is None else np.ascontiguousarray(dep_n, np.uint8))
+
+
+def hit_tri(hit):
+    """triangle index of packed hits (-1 on a miss), back-face bit removed."""
+    x = hit[..., 0].astype(np.int64) & 0xFFFFFFFF
+    return np.where(x == 0xFFFFFFFF, -1, x & 0x7FFFFFFF).astype(np.int64)
+
+
+def hit_back(hit):
+    x = hit[..., 0].astype(np.int64) & 0xFFFFFFFF
+    return (x != 0xFFFFFFFF) & ((x & 0x80000000) != 0)
+
+
+def hit_t(hit):
+    return hit[..., 1].astype(np.int32).view(np.float32)

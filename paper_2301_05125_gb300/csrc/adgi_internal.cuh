@@ -1,0 +1,482 @@
+// adgi_internal.cuh -- device data layout and inline device code shared by the
+// library's kernels (sm_103a).  Nothing here is shared with the CPU oracle.
+//
+// Exactness: every floating-point step whose result becomes an integer or a
+// discrete decision (ray directions, the watertight hit test, shadow
+// visibility, the lit test, the quantised heuristics, texel binning) is
+// written with the *_rn intrinsics, which are never fused or reordered, so it
+// reproduces IEEE single precision bit for bit.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+
+#include "../../include/adgi.h"
+
+namespace adgi {
+
+constexpr int kPilots = 8;
+constexpr int kMaxLights = 64;
+constexpr uint32_t kMiss = 0xFFFFFFFFu;
+constexpr uint32_t kBackBit = 0x80000000u;
+
+// ----------------------------------------------------------------- device data
+struct Light {
+    int kind;
+    float v[3];
+    float rgb[3];
+};
+
+// BVH node: the boxes of both children (so one fetch decides both) and the
+// child references; a child >= 0 is an internal node, < 0 is ~(triangle slot).
+struct __align__(16) BNode {
+    float4 a;  // c0.lo.xyz, c0.hi.x
+    float4 b;  // c0.hi.yz, c1.lo.xy
+    float4 c;  // c1.lo.z, c1.hi.xyz
+    int4 d;    // left, right, -, -
+};
+
+struct SceneDev {
+    int n_tris;
+    int n_verts;
+    const float4* tri_v;    // [n_tris*3] vertices in BVH order, .w of v0 = original index
+    const float4* tri_orig; // [n_tris*3] vertices in original order (shading normal)
+    const float* albedo;    // [n_tris*3]
+    const BNode* nodes;     // [n_tris-1] (>= 1 node)
+    int root_leaf;          // n_tris == 1: the single triangle slot
+    int max_iter;           // traversal step limit (a correct tree needs < n_tris steps)
+    int* err;               // anomaly flags (kErr*), 0 when all is well
+};
+
+constexpr int kErrTraversal = 1;  // a traversal exceeded max_iter
+constexpr int kErrRayRange = 2;   // a probe's ray range exceeded the buffers
+constexpr int kErrBvh = 4;        // the bottom-up box pass exceeded its depth bound
+
+struct FrameConst {
+    uint64_t pilot_key;     // sm(sm(seed) ^ pair)
+    float R[9];             // main-ray rotation
+    float sky[3];
+    int n_lights;
+    int even;               // first frame of a pair: pilots are blended
+    int pair_valid;         // the previous frame was the first of this pair
+    int has_camera;
+    float cam[3];
+    float cam_k;
+};
+
+struct VolConst {
+    float origin[3], spacing[3];
+    int dims[3];
+    int P;
+    int n_irr, n_dep, Ti, Td;
+    float tmin;             // (float)(1e-4 * s)
+    float depth_max;
+    float qv_scale;         // (float)(256 / s)
+    float qc_scale;         // (float)(64 / s)
+    float var_min;          // (float)(1e-6 * s^2)
+    float hyst;
+    int theta;
+    int m0, rays_max, rays_avg;
+    int fp16;
+    uint32_t R_main;        // main-ray buffer length
+    int* err;               // anomaly flags (kErr*)
+};
+
+// ----------------------------------------------------------------- exact FP32
+__device__ __forceinline__ float fa(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float fs(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float fm(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float fd(float a, float b) { return __fdiv_rn(a, b); }
+__device__ __forceinline__ float fsq(float a) { return __fsqrt_rn(a); }
+__device__ __forceinline__ float dot3x(float ax, float ay, float az, float bx, float by, float bz)
+{
+    return fa(fa(fm(ax, bx), fm(ay, by)), fm(az, bz));
+}
+
+__host__ __device__ __forceinline__ uint64_t splitmix(uint64_t x)
+{
+    uint64_t z = x + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// probe position (FP32): origin + spacing * index
+__device__ __forceinline__ float3 probe_pos(const VolConst& V, int p)
+{
+    int ix = p % V.dims[0];
+    int iy = (p / V.dims[0]) % V.dims[1];
+    int iz = p / (V.dims[0] * V.dims[1]);
+    return make_float3(fa(V.origin[0], fm(V.spacing[0], (float)ix)), fa(V.origin[1], fm(V.spacing[1], (float)iy)),
+                       fa(V.origin[2], fm(V.spacing[2], (float)iz)));
+}
+
+// Pilot direction of (probe, octant) for the frame pair encoded in key:
+// a uniform point of the octant's simplex from a 64-bit hash, normalised.
+__device__ __forceinline__ float3 pilot_dir(uint64_t key, uint32_t probe, int o)
+{
+    uint64_t h = splitmix(key ^ ((uint64_t)probe * 8u + (uint64_t)o));
+    const float k24 = 5.9604644775390625e-08f;
+    float u1 = fm(__uint2float_rn((uint32_t)(h >> 40)), k24);
+    float u2 = fm(__uint2float_rn((uint32_t)((h >> 16) & 0xFFFFFFu)), k24);
+    if (fa(u1, u2) > 1.0f) {
+        float a = fs(1.0f, u2), b = fs(1.0f, u1);
+        u1 = a;
+        u2 = b;
+    }
+    float x = u1, y = u2, z = fs(fs(1.0f, u1), u2);
+    if (o & 1) x = -x;
+    if (o & 2) y = -y;
+    if (o & 4) z = -z;
+    float l = fsq(dot3x(x, y, z, x, y, z));
+    return make_float3(fd(x, l), fd(y, l), fd(z, l));
+}
+
+__device__ __forceinline__ float3 rotate(const float* R, float4 s)
+{
+    return make_float3(fa(fa(fm(R[0], s.x), fm(R[1], s.y)), fm(R[2], s.z)),
+                       fa(fa(fm(R[3], s.x), fm(R[4], s.y)), fm(R[5], s.z)),
+                       fa(fa(fm(R[6], s.x), fm(R[7], s.y)), fm(R[8], s.z)));
+}
+
+// ----------------------------------------------------------------- octahedral
+__device__ __forceinline__ float sgnf(float v) { return v >= 0.0f ? 1.0f : -1.0f; }
+
+__device__ __forceinline__ float2 oct_encode_x(float3 w)
+{
+    float l1 = fa(fa(fabsf(w.x), fabsf(w.y)), fabsf(w.z));
+    float px = fd(w.x, l1), py = fd(w.y, l1);
+    if (w.z < 0.0f) {
+        float qx = fm(fs(1.0f, fabsf(py)), sgnf(px));
+        float qy = fm(fs(1.0f, fabsf(px)), sgnf(py));
+        px = qx;
+        py = qy;
+    }
+    return make_float2(px, py);
+}
+
+// nearest interior texel, as row*(n+2)+col with both in 1..n
+__device__ __forceinline__ int texel_of(float2 p, int n)
+{
+    float fn = (float)n;
+    int cx = (int)floorf(fm(fm(fa(p.x, 1.0f), 0.5f), fn));
+    int cy = (int)floorf(fm(fm(fa(p.y, 1.0f), 0.5f), fn));
+    cx = min(max(cx, 0), n - 1);
+    cy = min(max(cy, 0), n - 1);
+    return (cy + 1) * (n + 2) + (cx + 1);
+}
+
+// ----------------------------------------------------------------- watertight
+struct WRay {
+    float ox, oy, oz;
+    int kx, ky, kz;
+    float Sx, Sy, Sz;
+};
+
+__device__ __forceinline__ float comp(float x, float y, float z, int k) { return k == 0 ? x : (k == 1 ? y : z); }
+
+__device__ __forceinline__ WRay wray(float3 o, float3 d)
+{
+    WRay r;
+    r.ox = o.x;
+    r.oy = o.y;
+    r.oz = o.z;
+    int kz = 0;
+    float m = fabsf(d.x);
+    if (fabsf(d.y) > m) {
+        kz = 1;
+        m = fabsf(d.y);
+    }
+    if (fabsf(d.z) > m) kz = 2;
+    int kx = kz + 1 == 3 ? 0 : kz + 1;
+    int ky = kx + 1 == 3 ? 0 : kx + 1;
+    float dz = comp(d.x, d.y, d.z, kz);
+    if (dz < 0.0f) {
+        int t = kx;
+        kx = ky;
+        ky = t;
+    }
+    r.kx = kx;
+    r.ky = ky;
+    r.kz = kz;
+    r.Sx = fd(comp(d.x, d.y, d.z, kx), dz);
+    r.Sy = fd(comp(d.x, d.y, d.z, ky), dz);
+    r.Sz = fd(1.0f, dz);
+    return r;
+}
+
+// Woop-Benthin-Wald watertight test.  Returns true when the ray's line crosses
+// the triangle, with t and det; det > 0 is a front-face hit.
+__device__ __forceinline__ bool wtri(const WRay& r, float4 A4, float4 B4, float4 C4, float& t, float& det)
+{
+    float ax = fs(A4.x, r.ox), ay = fs(A4.y, r.oy), az = fs(A4.z, r.oz);
+    float bx = fs(B4.x, r.ox), by = fs(B4.y, r.oy), bz = fs(B4.z, r.oz);
+    float cx = fs(C4.x, r.ox), cy = fs(C4.y, r.oy), cz = fs(C4.z, r.oz);
+    float akz = comp(ax, ay, az, r.kz), bkz = comp(bx, by, bz, r.kz), ckz = comp(cx, cy, cz, r.kz);
+    float Ax = fs(comp(ax, ay, az, r.kx), fm(r.Sx, akz));
+    float Ay = fs(comp(ax, ay, az, r.ky), fm(r.Sy, akz));
+    float Bx = fs(comp(bx, by, bz, r.kx), fm(r.Sx, bkz));
+    float By = fs(comp(bx, by, bz, r.ky), fm(r.Sy, bkz));
+    float Cx = fs(comp(cx, cy, cz, r.kx), fm(r.Sx, ckz));
+    float Cy = fs(comp(cx, cy, cz, r.ky), fm(r.Sy, ckz));
+    float U = fs(fm(Cx, By), fm(Cy, Bx));
+    float V = fs(fm(Ax, Cy), fm(Ay, Cx));
+    float W = fs(fm(Bx, Ay), fm(By, Ax));
+    if (U == 0.0f || V == 0.0f || W == 0.0f) {
+        U = __double2float_rn(__dsub_rn(__dmul_rn((double)Cx, (double)By), __dmul_rn((double)Cy, (double)Bx)));
+        V = __double2float_rn(__dsub_rn(__dmul_rn((double)Ax, (double)Cy), __dmul_rn((double)Ay, (double)Cx)));
+        W = __double2float_rn(__dsub_rn(__dmul_rn((double)Bx, (double)Ay), __dmul_rn((double)By, (double)Ax)));
+    }
+    if ((U < 0.0f || V < 0.0f || W < 0.0f) && (U > 0.0f || V > 0.0f || W > 0.0f)) return false;
+    det = fa(fa(U, V), W);
+    if (det == 0.0f) return false;
+    float Az = fm(r.Sz, akz), Bz = fm(r.Sz, bkz), Cz = fm(r.Sz, ckz);
+    float T = fa(fa(fm(U, Az), fm(V, Bz)), fm(W, Cz));
+    t = fd(T, det);
+    return true;
+}
+
+// Conservative slab test of one box against [0, lim]; NaNs (0 * inf) drop out
+// of fminf/fmaxf, which keeps the test conservative.
+__device__ __forceinline__ bool slab(float lox, float loy, float loz, float hix, float hiy, float hiz, float3 o,
+                                     float3 inv, float lim, float& tnear)
+{
+    float tx0 = (lox - o.x) * inv.x, tx1 = (hix - o.x) * inv.x;
+    float ty0 = (loy - o.y) * inv.y, ty1 = (hiy - o.y) * inv.y;
+    float tz0 = (loz - o.z) * inv.z, tz1 = (hiz - o.z) * inv.z;
+    float tn = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fmaxf(fminf(tz0, tz1), 0.0f));
+    float tf = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fminf(fmaxf(tz0, tz1), lim));
+    tnear = tn;
+    return tn <= tf;
+}
+
+constexpr float kBoxSlack = 1.0001f;  // pruning slack on the best t (conservative)
+// LBVH depth is at most 95 (63 key bits + 32 index bits), so 96 entries never overflow.
+constexpr int kStack = 96;
+
+// nearest hit with t in (tmin, tmax]; (t, original index) lexicographic
+__device__ __forceinline__ void trace_closest(const SceneDev& S, float3 o, float3 d, float tmin, float tmax,
+                                              float& t_best, uint32_t& hit_best)
+{
+    t_best = tmax;
+    hit_best = kMiss;
+    if (S.n_tris == 0) return;
+    WRay wr = wray(o, d);
+    float3 inv = make_float3(1.0f / d.x, 1.0f / d.y, 1.0f / d.z);
+    int best_orig = 0x7FFFFFFF;
+    float best_det = 0.0f;
+    bool found = false;
+    auto test_tri = [&](int slot) {
+        const float4* tv = S.tri_v + 3 * (size_t)slot;
+        float4 A = __ldg(tv), B = __ldg(tv + 1), C = __ldg(tv + 2);
+        float tt, det;
+        if (!wtri(wr, A, B, C, tt, det)) return;
+        if (!(tt > tmin)) return;
+        int orig = __float_as_int(A.w);
+        bool better = found ? (tt < t_best || (tt == t_best && orig < best_orig)) : (tt <= tmax);
+        if (!better) return;
+        found = true;
+        t_best = tt;
+        best_orig = orig;
+        best_det = det;
+    };
+    if (S.root_leaf >= 0) {
+        test_tri(S.root_leaf);
+    } else {
+        int stack[kStack];
+        int sp = 0;
+        int node = 0;
+        for (int iter = 0;; ++iter) {
+            if (iter > S.max_iter) {
+                atomicOr(S.err, kErrTraversal);
+                break;
+            }
+            const BNode* nd = S.nodes + node;
+            float4 a = __ldg(&nd->a), b = __ldg(&nd->b), c = __ldg(&nd->c);
+            int4 ch = __ldg(&nd->d);
+            float lim = t_best * kBoxSlack;
+            float t0, t1;
+            bool h0 = slab(a.x, a.y, a.z, a.w, b.x, b.y, o, inv, lim, t0);
+            bool h1 = slab(b.z, b.w, c.x, c.y, c.z, c.w, o, inv, lim, t1);
+            int next = -1;
+            if (h0 && ch.x < 0) {
+                test_tri(~ch.x);
+                h0 = false;
+            }
+            if (h1 && ch.y < 0) {
+                test_tri(~ch.y);
+                h1 = false;
+            }
+            if (h0 && h1) {
+                int nearc = t0 <= t1 ? ch.x : ch.y;
+                int farc = t0 <= t1 ? ch.y : ch.x;
+                if (sp < kStack) stack[sp++] = farc;
+                next = nearc;
+            } else if (h0) {
+                next = ch.x;
+            } else if (h1) {
+                next = ch.y;
+            }
+            if (next < 0) {
+                if (sp == 0) break;
+                next = stack[--sp];
+            }
+            node = next;
+        }
+    }
+    if (found) hit_best = (uint32_t)best_orig | (best_det < 0.0f ? kBackBit : 0u);
+}
+
+// any hit with t strictly inside (tlo, thi)
+__device__ __forceinline__ bool trace_any(const SceneDev& S, float3 o, float3 d, float tlo, float thi)
+{
+    if (S.n_tris == 0) return false;
+    WRay wr = wray(o, d);
+    float3 inv = make_float3(1.0f / d.x, 1.0f / d.y, 1.0f / d.z);
+    float lim = isinf(thi) ? thi : thi * kBoxSlack;
+    auto test_tri = [&](int slot) -> bool {
+        const float4* tv = S.tri_v + 3 * (size_t)slot;
+        float4 A = __ldg(tv), B = __ldg(tv + 1), C = __ldg(tv + 2);
+        float tt, det;
+        if (!wtri(wr, A, B, C, tt, det)) return false;
+        return tt > tlo && tt < thi;
+    };
+    if (S.root_leaf >= 0) return test_tri(S.root_leaf);
+    int stack[kStack];
+    int sp = 0;
+    int node = 0;
+    for (int iter = 0;; ++iter) {
+        if (iter > S.max_iter) {
+            atomicOr(S.err, kErrTraversal);
+            break;
+        }
+        const BNode* nd = S.nodes + node;
+        float4 a = __ldg(&nd->a), b = __ldg(&nd->b), c = __ldg(&nd->c);
+        int4 ch = __ldg(&nd->d);
+        float t0, t1;
+        bool h0 = slab(a.x, a.y, a.z, a.w, b.x, b.y, o, inv, lim, t0);
+        bool h1 = slab(b.z, b.w, c.x, c.y, c.z, c.w, o, inv, lim, t1);
+        if (h0 && ch.x < 0) {
+            if (test_tri(~ch.x)) return true;
+            h0 = false;
+        }
+        if (h1 && ch.y < 0) {
+            if (test_tri(~ch.y)) return true;
+            h1 = false;
+        }
+        int next = -1;
+        if (h0 && h1) {
+            if (sp < kStack) stack[sp++] = ch.y;
+            next = ch.x;
+        } else if (h0) {
+            next = ch.x;
+        } else if (h1) {
+            next = ch.y;
+        }
+        if (next < 0) {
+            if (sp == 0) break;
+            next = stack[--sp];
+        }
+        node = next;
+    }
+    return false;
+}
+
+// ----------------------------------------------------------------- atlas access
+__device__ __forceinline__ float4 irr_load(const void* irr, size_t idx, int fp16)
+{
+    if (fp16) {
+        const __half2* h = reinterpret_cast<const __half2*>(irr) + 2 * idx;
+        float2 a = __half22float2(h[0]), b = __half22float2(h[1]);
+        return make_float4(a.x, a.y, b.x, b.y);
+    }
+    return reinterpret_cast<const float4*>(irr)[idx];
+}
+
+__device__ __forceinline__ float2 dep_load(const void* dep, size_t idx, int fp16)
+{
+    if (fp16) return __half22float2(reinterpret_cast<const __half2*>(dep)[idx]);
+    return reinterpret_cast<const float2*>(dep)[idx];
+}
+
+// bilinear sample of a padded tile at direction w (octahedral coordinates)
+template <int CH>
+__device__ __forceinline__ void tile_bilinear(const void* base, size_t tile_off, int T, int n, float2 p, int fp16,
+                                              float* out)
+{
+    float fx = (1.0f + (p.x + 1.0f) * 0.5f * (float)n) - 0.5f;
+    float fy = (1.0f + (p.y + 1.0f) * 0.5f * (float)n) - 0.5f;
+    int x0 = min(max((int)floorf(fx), 0), n);
+    int y0 = min(max((int)floorf(fy), 0), n);
+    float ax = fminf(fmaxf(fx - (float)x0, 0.0f), 1.0f);
+    float ay = fminf(fmaxf(fy - (float)y0, 0.0f), 1.0f);
+    size_t i00 = tile_off + (size_t)(y0 * T + x0);
+    if (CH == 3) {
+        float4 v00 = irr_load(base, i00, fp16), v01 = irr_load(base, i00 + 1, fp16);
+        float4 v10 = irr_load(base, i00 + T, fp16), v11 = irr_load(base, i00 + T + 1, fp16);
+        out[0] = (1.0f - ay) * ((1.0f - ax) * v00.x + ax * v01.x) + ay * ((1.0f - ax) * v10.x + ax * v11.x);
+        out[1] = (1.0f - ay) * ((1.0f - ax) * v00.y + ax * v01.y) + ay * ((1.0f - ax) * v10.y + ax * v11.y);
+        out[2] = (1.0f - ay) * ((1.0f - ax) * v00.z + ax * v01.z) + ay * ((1.0f - ax) * v10.z + ax * v11.z);
+    } else {
+        float2 v00 = dep_load(base, i00, fp16), v01 = dep_load(base, i00 + 1, fp16);
+        float2 v10 = dep_load(base, i00 + T, fp16), v11 = dep_load(base, i00 + T + 1, fp16);
+        out[0] = (1.0f - ay) * ((1.0f - ax) * v00.x + ax * v01.x) + ay * ((1.0f - ax) * v10.x + ax * v11.x);
+        out[1] = (1.0f - ay) * ((1.0f - ax) * v00.y + ax * v01.y) + ay * ((1.0f - ax) * v10.y + ax * v11.y);
+    }
+}
+
+// 8-probe trilinear x Chebyshev irradiance query (FP32)
+__device__ __forceinline__ float3 query_irr(const VolConst& V, const void* irr, const void* dep, float3 x, float3 nrm)
+{
+    float g[3] = {(x.x - V.origin[0]) / V.spacing[0], (x.y - V.origin[1]) / V.spacing[1],
+                  (x.z - V.origin[2]) / V.spacing[2]};
+    int b[3];
+    float al[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        float f = floorf(g[k]);
+        f = fminf(fmaxf(f, -1e9f), 1e9f);
+        int bi = (int)f;
+        bi = min(max(bi, 0), V.dims[k] - 2);
+        b[k] = bi;
+        al[k] = fminf(fmaxf(g[k] - (float)bi, 0.0f), 1.0f);
+    }
+    float nl = sqrtf(nrm.x * nrm.x + nrm.y * nrm.y + nrm.z * nrm.z);
+    float3 nd = nl > 0.0f ? make_float3(nrm.x / nl, nrm.y / nl, nrm.z / nl) : make_float3(0.f, 0.f, 1.f);
+    float2 pn = oct_encode_x(nd);
+    float sum[3] = {0.f, 0.f, 0.f}, sumt[3] = {0.f, 0.f, 0.f}, sw = 0.f;
+    const size_t ti2 = (size_t)V.Ti * V.Ti, td2 = (size_t)V.Td * V.Td;
+#pragma unroll 1
+    for (int c = 0; c < 8; ++c) {
+        int o0 = c & 1, o1 = (c >> 1) & 1, o2 = (c >> 2) & 1;
+        float wt = (o0 ? al[0] : 1.f - al[0]) * (o1 ? al[1] : 1.f - al[1]) * (o2 ? al[2] : 1.f - al[2]);
+        int p = (b[0] + o0) + V.dims[0] * ((b[1] + o1) + V.dims[1] * (b[2] + o2));
+        float3 pp = probe_pos(V, p);
+        float dx = x.x - pp.x, dy = x.y - pp.y, dz = x.z - pp.z;
+        float dist = sqrtf(dx * dx + dy * dy + dz * dz);
+        float3 dir = dist > 0.f ? make_float3(dx / dist, dy / dist, dz / dist) : make_float3(0.f, 0.f, 1.f);
+        float mom[2];
+        tile_bilinear<2>(dep, (size_t)p * td2, V.Td, V.n_dep, oct_encode_x(dir), V.fp16, mom);
+        float wc = 1.f;
+        if (dist > mom[0]) {
+            // minimum variance: max(1e-3 mu2, 1e-6 s^2) keeps the weight well
+            // conditioned at the precision of the stored moments
+            float var = fmaxf(mom[1] - mom[0] * mom[0], fmaxf(1e-3f * mom[1], V.var_min));
+            float dd = dist - mom[0];
+            wc = var / (var + dd * dd);
+        }
+        float E[3];
+        tile_bilinear<3>(irr, (size_t)p * ti2, V.Ti, V.n_irr, pn, V.fp16, E);
+        float w = wt * wc;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            sum[k] += w * E[k];
+            sumt[k] += wt * E[k];
+        }
+        sw += w;
+    }
+    if (sw >= 1e-12f) return make_float3(sum[0] / sw, sum[1] / sw, sum[2] / sw);
+    return make_float3(sumt[0], sumt[1], sumt[2]);
+}
+
+}  // namespace adgi

@@ -1,0 +1,648 @@
+// capi.cu -- host runtime behind include/adgi.h: volume objects, device memory,
+// per-frame constants, and the ordered launch sequence of one update.
+//
+// Host-side tables (built once per volume, in FP64 with only IEEE basic
+// operations plus exp for the two heuristic LUTs; compiled with
+// -ffp-contract=off so the rounding is that of the written order):
+//   * spherical Fibonacci sets SF_m, m = 1..rays_max-8 (Keinert et al. 2015),
+//     cos/sin of i * golden angle by the exact complex recurrence;
+//   * LUT_v[i] = floor(1023 exp(-2 (i+0.5)/256))   (Eq. ProbeVis, bin s/256)
+//   * LUT_c[i] = floor(1023 exp(-(i+0.5) s/64))    (Eq. cameraD, bin s/64)
+// Per frame: the pilot hash key of the frame pair and the main-ray rotation (a
+// uniform unit quaternion by rejection from the 4-ball, FP64 -> FP32).
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "adgi_internal.cuh"
+#include "bvh.cuh"
+#include "kernels.cuh"
+
+namespace adgi {
+size_t blend_smem_bytes(const VolConst& V);
+}
+
+using namespace adgi;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg)
+{
+    g_err = msg;
+    return code;
+}
+
+#define CK(call)                                                                                   \
+    do {                                                                                           \
+        cudaError_t e__ = (call);                                                                  \
+        if (e__ != cudaSuccess) return fail(ADGI_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e__)); \
+    } while (0)
+
+const double kGaCos = -0.7373688780783197;  // cos(pi (3 - sqrt 5))
+const double kGaSin = 0.6754902942615238;   // sin(pi (3 - sqrt 5))
+
+void build_sf(int M, std::vector<float4>& out)
+{
+    out.resize((size_t)M * (M + 1) / 2 + 1);
+    for (int m = 1; m <= M; ++m) {
+        float4* dst = out.data() + (size_t)m * (m - 1) / 2;
+        double c = 1.0, s = 0.0;
+        for (int i = 0; i < m; ++i) {
+            double z = 1.0 - (2.0 * (double)i + 1.0) / (double)m;
+            double r2 = 1.0 - z * z;
+            double r = r2 > 0.0 ? std::sqrt(r2) : 0.0;
+            dst[i] = make_float4((float)(r * c), (float)(r * s), (float)z, 0.0f);
+            double cn = c * kGaCos - s * kGaSin;
+            double sn = s * kGaCos + c * kGaSin;
+            c = cn;
+            s = sn;
+        }
+    }
+}
+
+uint64_t h3(uint64_t a, uint64_t b, uint64_t c) { return splitmix(splitmix(splitmix(a) ^ b) ^ c); }
+
+void frame_rotation(uint64_t seed, uint64_t frame, float R[9])
+{
+    const double k53 = 1.1102230246251565e-16;
+    double q[4] = {1.0, 0.0, 0.0, 0.0};
+    for (uint64_t att = 0; att < 1000; ++att) {
+        double c[4];
+        for (int k = 0; k < 4; ++k) c[k] = ((double)(h3(seed ^ 0x524F54ull, frame, att * 4u + k) >> 11) * k53) * 2.0 - 1.0;
+        double n2 = ((c[0] * c[0] + c[1] * c[1]) + c[2] * c[2]) + c[3] * c[3];
+        if (n2 > 1e-6 && n2 <= 1.0) {
+            double nn = std::sqrt(n2);
+            for (int k = 0; k < 4; ++k) q[k] = c[k] / nn;
+            break;
+        }
+    }
+    double w = q[0], x = q[1], y = q[2], z = q[3];
+    double m[9] = {1.0 - 2.0 * (y * y + z * z), 2.0 * (x * y - w * z),       2.0 * (x * z + w * y),
+                   2.0 * (x * y + w * z),       1.0 - 2.0 * (x * x + z * z), 2.0 * (y * z - w * x),
+                   2.0 * (x * z - w * y),       2.0 * (y * z + w * x),       1.0 - 2.0 * (x * x + y * y)};
+    for (int k = 0; k < 9; ++k) R[k] = (float)m[k];
+}
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t count, size_t* total)
+{
+    size_t sz = sizeof(T) * (count > 0 ? count : 1);
+    cudaError_t e = cudaMalloc((void**)p, sz);
+    if (e == cudaSuccess) *total += sz;
+    return e;
+}
+
+}  // namespace
+
+struct adgi_volume_s {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    adgi_volume_desc desc{};
+    VolConst V{};
+    double s = 0.0;
+    size_t bytes = 0;
+    // tables
+    float4* sf = nullptr;
+    uint16_t* lut_v = nullptr;
+    uint16_t* lut_c = nullptr;
+    // atlases
+    void* irr = nullptr;
+    void* dep = nullptr;
+    uint8_t* dep_n = nullptr;
+    // heuristic state
+    uint16_t *qv = nullptr, *qr = nullptr, *qv_even = nullptr, *qr_even = nullptr;
+    uint16_t *amp_v = nullptr, *amp_r = nullptr, *trv = nullptr, *trr = nullptr;
+    uint8_t *age_v = nullptr, *age_r = nullptr;
+    uint32_t* G = nullptr;
+    uint32_t *W = nullptr, *n = nullptr, *off = nullptr;
+    // rays
+    int2* pil_hit = nullptr;
+    float4* pil_rec = nullptr;
+    float* pil_lum = nullptr;
+    uint32_t R_main = 0;
+    int2* m_hit = nullptr;
+    float4* m_rec = nullptr;
+    unsigned long long* shadow_ctr = nullptr;
+    int* err = nullptr;  // device anomaly flags
+    // scene
+    float* verts = nullptr;
+    int* idx = nullptr;
+    float* albedo = nullptr;
+    int nv = 0, nt = 0;
+    bool has_scene = false, bvh_dirty = false;
+    float eps = 0.f;
+    Bvh bvh;
+    // frame bookkeeping
+    int64_t last_even = -2;
+    uint64_t frames = 0;
+    float R[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+    bool timing = false;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    bool timed_pending = false;
+    // query scratch for host pointers
+    float* q_buf = nullptr;
+    int q_cap = 0;
+};
+
+namespace {
+
+void free_volume(adgi_volume v)
+{
+    if (!v) return;
+    void* ptrs[] = {v->sf,      v->lut_v,   v->lut_c,  v->irr,   v->dep,     v->dep_n,   v->qv,     v->qr,
+                    v->qv_even, v->qr_even, v->amp_v,  v->amp_r, v->trv,     v->trr,     v->age_v,  v->age_r,
+                    v->G,       v->W,       v->n,      v->off,   v->pil_hit, v->pil_rec, v->pil_lum, v->m_hit,
+                    v->m_rec,   v->shadow_ctr, v->verts, v->idx, v->albedo,  v->q_buf, v->err};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    v->bvh.release();
+    if (v->ev0) cudaEventDestroy(v->ev0);
+    if (v->ev1) cudaEventDestroy(v->ev1);
+    delete v;
+}
+
+int validate_desc(const adgi_volume_desc* d)
+{
+    if (!d) return fail(ADGI_ERR_INVALID_ARG, "desc is NULL");
+    for (int k = 0; k < 3; ++k) {
+        if (d->dims[k] < 2) return fail(ADGI_ERR_INVALID_ARG, "dims must be >= 2");
+        if (!(d->spacing[k] > 0.0f) || !std::isfinite(d->spacing[k]))
+            return fail(ADGI_ERR_INVALID_ARG, "spacing must be positive");
+        if (!std::isfinite(d->origin[k])) return fail(ADGI_ERR_INVALID_ARG, "origin must be finite");
+    }
+    if ((int64_t)d->dims[0] * d->dims[1] * d->dims[2] > (1 << 26))
+        return fail(ADGI_ERR_INVALID_ARG, "too many probes");
+    if (d->irr_interior < 1 || d->irr_interior > 30 || d->depth_interior < 1 || d->depth_interior > 30)
+        return fail(ADGI_ERR_INVALID_ARG, "tile interior must be in [1, 30]");
+    int m0 = d->rays_min > 8 ? d->rays_min : 8;
+    if (d->rays_max > 4096 || d->rays_avg < m0 || d->rays_avg > d->rays_max)
+        return fail(ADGI_ERR_INVALID_ARG, "need max(rays_min, 8) <= rays_avg <= rays_max <= 4096");
+    if (!(d->hysteresis >= 0.0f && d->hysteresis < 1.0f)) return fail(ADGI_ERR_INVALID_ARG, "hysteresis in [0,1)");
+    if (d->tr_theta < 1 || d->tr_theta > 255) return fail(ADGI_ERR_INVALID_ARG, "tr_theta in [1,255]");
+    int64_t P = (int64_t)d->dims[0] * d->dims[1] * d->dims[2];
+    if (P * (int64_t)d->rays_avg >= (int64_t)1 << 31) return fail(ADGI_ERR_INVALID_ARG, "ray budget too large");
+    return ADGI_OK;
+}
+
+FrameConst frame_const(adgi_volume v, const adgi_frame* f)
+{
+    FrameConst F{};
+    F.pilot_key = splitmix(splitmix(f->seed) ^ (f->frame >> 1));
+    frame_rotation(f->seed, f->frame, v->R);
+    for (int k = 0; k < 9; ++k) F.R[k] = v->R[k];
+    for (int k = 0; k < 3; ++k) F.sky[k] = f->sky_rgb[k];
+    F.n_lights = f->n_lights;
+    F.even = (f->frame & 1u) == 0;
+    F.pair_valid = !F.even && v->last_even == (int64_t)f->frame - 1;
+    F.has_camera = f->has_camera ? 1 : 0;
+    for (int k = 0; k < 3; ++k) F.cam[k] = f->cam_pos[k];
+    F.cam_k = f->cam_k;
+    return F;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* adgi_last_error(void) { return g_err.c_str(); }
+
+int adgi_create_volume(const adgi_volume_desc* desc, void* cuda_stream, adgi_volume* out)
+{
+    if (!out) return fail(ADGI_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    int rc = validate_desc(desc);
+    if (rc) return rc;
+    adgi_volume v = new adgi_volume_s();
+    v->desc = *desc;
+    v->stream = (cudaStream_t)cuda_stream;
+    cudaGetDevice(&v->device);
+    const adgi_volume_desc& d = *desc;
+    VolConst& V = v->V;
+    for (int k = 0; k < 3; ++k) {
+        V.origin[k] = d.origin[k];
+        V.spacing[k] = d.spacing[k];
+        V.dims[k] = d.dims[k];
+    }
+    V.P = d.dims[0] * d.dims[1] * d.dims[2];
+    V.n_irr = d.irr_interior;
+    V.n_dep = d.depth_interior;
+    V.Ti = d.irr_interior + 2;
+    V.Td = d.depth_interior + 2;
+    double sx = d.spacing[0], sy = d.spacing[1], sz = d.spacing[2];
+    v->s = std::sqrt((sx * sx + sy * sy) + sz * sz);
+    V.tmin = (float)(1e-4 * v->s);
+    V.depth_max = d.depth_max > 0.0f ? d.depth_max : (float)(1.5 * v->s);
+    V.qv_scale = (float)(256.0 / v->s);
+    V.qc_scale = (float)(64.0 / v->s);
+    V.var_min = (float)(1e-6 * v->s * v->s);
+    V.hyst = d.hysteresis;
+    V.theta = d.tr_theta;
+    V.m0 = d.rays_min > 8 ? d.rays_min : 8;
+    V.rays_max = d.rays_max;
+    V.rays_avg = d.rays_avg;
+    V.fp16 = d.atlas_fp16 ? 1 : 0;
+    const size_t P = (size_t)V.P;
+    v->R_main = (uint32_t)((size_t)(d.rays_avg - 8) * P);
+    size_t& B = v->bytes;
+    cudaError_t e = cudaSuccess;
+#define DA(ptr, count)                                      \
+    do {                                                    \
+        e = dalloc(&(ptr), (count), &B);                    \
+        if (e != cudaSuccess) {                             \
+            free_volume(v);                                 \
+            return fail(ADGI_ERR_OOM, "device allocation"); \
+        }                                                   \
+    } while (0)
+    // tables
+    int M = d.rays_max - 8;
+    std::vector<float4> sf;
+    build_sf(M > 0 ? M : 0, sf);
+    DA(v->sf, sf.size());
+    DA(v->lut_v, 4096);
+    DA(v->lut_c, 4096);
+    std::vector<uint16_t> lv(4096), lc(4096);
+    for (int i = 0; i < 4096; ++i) {
+        lv[i] = (uint16_t)std::floor(1023.0 * std::exp(-2.0 * ((double)i + 0.5) / 256.0));
+        lc[i] = (uint16_t)std::floor(1023.0 * std::exp(-((double)i + 0.5) * v->s / 64.0));
+    }
+    // atlases
+    size_t ti2 = (size_t)V.Ti * V.Ti, td2 = (size_t)V.Td * V.Td;
+    size_t irr_bytes = P * ti2 * (V.fp16 ? 8 : 16), dep_bytes = P * td2 * (V.fp16 ? 4 : 8);
+    {
+        uint8_t* a;
+        DA(a, irr_bytes);
+        v->irr = a;
+        DA(a, dep_bytes);
+        v->dep = a;
+    }
+    DA(v->dep_n, P * td2);
+    DA(v->qv, P * 8);
+    DA(v->qr, P * 8);
+    DA(v->qv_even, P * 8);
+    DA(v->qr_even, P * 8);
+    DA(v->amp_v, P * 8);
+    DA(v->amp_r, P * 8);
+    DA(v->trv, P * 8);
+    DA(v->trr, P * 8);
+    DA(v->age_v, P * 8);
+    DA(v->age_r, P * 8);
+    DA(v->G, P * 8);
+    DA(v->W, P);
+    DA(v->n, P);
+    DA(v->off, P + 1);
+    DA(v->pil_hit, P * 8);
+    DA(v->pil_rec, P * 8);
+    DA(v->pil_lum, P * 8);
+    DA(v->m_hit, (size_t)v->R_main);
+    DA(v->m_rec, (size_t)v->R_main);
+    DA(v->shadow_ctr, 1);
+    DA(v->err, 1);
+#undef DA
+    V.R_main = v->R_main;
+    V.err = v->err;
+    cudaStream_t s = v->stream;
+#define CKV(call)                                                                                        \
+    do {                                                                                                 \
+        cudaError_t e__ = (call);                                                                        \
+        if (e__ != cudaSuccess) {                                                                        \
+            free_volume(v);                                                                              \
+            return fail(ADGI_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e__));             \
+        }                                                                                                \
+    } while (0)
+    CKV(cudaMemcpyAsync(v->sf, sf.data(), sizeof(float4) * sf.size(), cudaMemcpyHostToDevice, s));
+    CKV(cudaMemcpyAsync(v->lut_v, lv.data(), 2 * 4096, cudaMemcpyHostToDevice, s));
+    CKV(cudaMemcpyAsync(v->lut_c, lc.data(), 2 * 4096, cudaMemcpyHostToDevice, s));
+    CKV(cudaMemsetAsync(v->irr, 0, irr_bytes, s));
+    CKV(cudaMemsetAsync(v->dep, 0, dep_bytes, s));
+    CKV(cudaMemsetAsync(v->dep_n, 0, P * td2, s));
+    for (uint16_t* p : {v->qv, v->qr, v->qv_even, v->qr_even, v->amp_v, v->amp_r, v->trv, v->trr})
+        CKV(cudaMemsetAsync(p, 0, P * 8 * 2, s));
+    CKV(cudaMemsetAsync(v->age_v, 0xFF, P * 8, s));
+    CKV(cudaMemsetAsync(v->age_r, 0xFF, P * 8, s));
+    CKV(cudaMemsetAsync(v->W, 0, P * 4, s));
+    CKV(cudaMemsetAsync(v->shadow_ctr, 0, 8, s));
+    CKV(cudaMemsetAsync(v->err, 0, 4, s));
+    CKV(cudaEventCreate(&v->ev0));
+    CKV(cudaEventCreate(&v->ev1));
+    // the host vectors die at return: wait for the copies
+    CKV(cudaStreamSynchronize(s));
+#undef CKV
+    *out = v;
+    return ADGI_OK;
+}
+
+int adgi_destroy(adgi_volume v)
+{
+    if (!v) return ADGI_OK;
+    cudaStreamSynchronize(v->stream);
+    free_volume(v);
+    return ADGI_OK;
+}
+
+int adgi_set_stream(adgi_volume v, void* cuda_stream)
+{
+    if (!v) return fail(ADGI_ERR_INVALID_ARG, "volume is NULL");
+    v->stream = (cudaStream_t)cuda_stream;
+    return ADGI_OK;
+}
+
+int adgi_enable_timing(adgi_volume v, int32_t enable)
+{
+    if (!v) return fail(ADGI_ERR_INVALID_ARG, "volume is NULL");
+    v->timing = enable != 0;
+    return ADGI_OK;
+}
+
+int adgi_set_scene(adgi_volume v, const float* verts, int32_t nv, const int32_t* idx, int32_t nt, const float* albedo,
+                   int32_t on_device)
+{
+    if (!v) return fail(ADGI_ERR_INVALID_ARG, "volume is NULL");
+    if (nv < 0 || nt < 0 || (nv > 0 && !verts) || (nt > 0 && (!idx || !albedo)))
+        return fail(ADGI_ERR_INVALID_ARG, "bad scene arrays");
+    cudaStream_t s = v->stream;
+    std::vector<float> hv;
+    std::vector<int> hi;
+    std::vector<float> ha;
+    const int* idx_host = nullptr;
+    if (on_device) {
+        hi.resize(3 * (size_t)nt);
+        CK(cudaMemcpyAsync(hi.data(), idx, sizeof(int) * 3 * (size_t)nt, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        idx_host = hi.data();
+    } else {
+        idx_host = idx;
+    }
+    for (size_t k = 0; k < 3 * (size_t)nt; ++k)
+        if (idx_host[k] < 0 || idx_host[k] >= nv) return fail(ADGI_ERR_INVALID_ARG, "triangle index out of range");
+    // scene extent -> box enlargement
+    if (on_device) {
+        hv.resize(3 * (size_t)nv);
+        CK(cudaMemcpyAsync(hv.data(), verts, sizeof(float) * 3 * (size_t)nv, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+    }
+    const float* vh = on_device ? hv.data() : verts;
+    double lo[3] = {1e300, 1e300, 1e300}, hi3[3] = {-1e300, -1e300, -1e300};
+    for (size_t k = 0; k < (size_t)nv; ++k)
+        for (int c = 0; c < 3; ++c) {
+            double x = vh[3 * k + c];
+            if (!std::isfinite(x)) return fail(ADGI_ERR_INVALID_ARG, "non-finite vertex");
+            lo[c] = x < lo[c] ? x : lo[c];
+            hi3[c] = x > hi3[c] ? x : hi3[c];
+        }
+    double ext = 0.0, mag = 0.0;
+    for (int c = 0; c < 3 && nv > 0; ++c) {
+        ext = std::fmax(ext, hi3[c] - lo[c]);
+        mag = std::fmax(mag, std::fmax(std::fabs(lo[c]), std::fabs(hi3[c])));
+    }
+    v->eps = (float)(1e-5 * std::fmax(ext, mag) + 1e-30);
+    if (nv > v->nv || nt > v->nt || !v->verts) {
+        cudaFree(v->verts);
+        cudaFree(v->idx);
+        cudaFree(v->albedo);
+        v->verts = nullptr;
+        v->idx = nullptr;
+        v->albedo = nullptr;
+        size_t dummy = 0;
+        if (dalloc(&v->verts, 3 * (size_t)nv, &dummy) != cudaSuccess || dalloc(&v->idx, 3 * (size_t)nt, &dummy) != cudaSuccess ||
+            dalloc(&v->albedo, 3 * (size_t)nt, &dummy) != cudaSuccess)
+            return fail(ADGI_ERR_OOM, "scene allocation");
+    }
+    cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    if (nv) CK(cudaMemcpyAsync(v->verts, verts, sizeof(float) * 3 * (size_t)nv, k, s));
+    if (nt) {
+        CK(cudaMemcpyAsync(v->idx, idx, sizeof(int) * 3 * (size_t)nt, k, s));
+        CK(cudaMemcpyAsync(v->albedo, albedo, sizeof(float) * 3 * (size_t)nt, k, s));
+    }
+    v->nv = nv;
+    v->nt = nt;
+    if (!on_device) CK(cudaStreamSynchronize(s));  // pageable sources are read before return anyway
+    CK(v->bvh.build(v->verts, v->idx, nv, nt, v->eps, v->err, s));
+    v->has_scene = true;
+    v->bvh_dirty = false;
+    return ADGI_OK;
+}
+
+int adgi_move_vertices(adgi_volume v, int32_t first, int32_t count, const float* verts, int32_t on_device)
+{
+    if (!v) return fail(ADGI_ERR_INVALID_ARG, "volume is NULL");
+    if (!v->has_scene) return fail(ADGI_ERR_NO_SCENE, "no scene");
+    if (first < 0 || count < 0 || first + count > v->nv || (count > 0 && !verts))
+        return fail(ADGI_ERR_INVALID_ARG, "vertex range outside the scene");
+    if (count == 0) return ADGI_OK;
+    CK(cudaMemcpyAsync(v->verts + 3 * (size_t)first, verts, sizeof(float) * 3 * (size_t)count,
+                       on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, v->stream));
+    v->bvh_dirty = true;
+    return ADGI_OK;
+}
+
+int adgi_update(adgi_volume v, const adgi_frame* f)
+{
+    if (!v || !f) return fail(ADGI_ERR_INVALID_ARG, "NULL argument");
+    if (!v->has_scene) return fail(ADGI_ERR_NO_SCENE, "no scene");
+    if (f->n_lights < 0 || f->n_lights > kMaxLights || (f->n_lights > 0 && !f->lights))
+        return fail(ADGI_ERR_INVALID_ARG, "bad light list");
+    cudaStream_t s = v->stream;
+    const VolConst& V = v->V;
+    if (v->timing) CK(cudaEventRecord(v->ev0, s));
+    if (v->bvh_dirty) {
+        CK(v->bvh.build(v->verts, v->idx, v->nv, v->nt, v->eps, v->err, s));
+        v->bvh_dirty = false;
+    }
+    FrameConst F = frame_const(v, f);
+    LightSet L;
+    L.n = f->n_lights;
+    for (int i = 0; i < f->n_lights; ++i) {
+        L.l[i].kind = f->lights[i].kind;
+        for (int k = 0; k < 3; ++k) {
+            L.l[i].v[k] = f->lights[i].pos_or_dir[k];
+            L.l[i].rgb[k] = f->lights[i].rgb[k];
+        }
+    }
+    SceneDev S = v->bvh.view(v->albedo, v->nv, v->err);
+    CK(cudaMemsetAsync(v->shadow_ctr, 0, 8, s));
+    // 1. pilot rays (trace + shade; the shading reads the previous atlases)
+    CK(launch_pilot_trace(V, F, S, v->pil_hit, s));
+    CK(launch_pilot_shade(V, F, L, S, v->irr, v->dep, v->pil_hit, v->pil_rec, v->pil_lum, v->shadow_ctr, s));
+    // 2. heuristics -> W_p
+    ChangeBufs C{v->pil_hit, v->pil_lum, v->lut_v, v->lut_c, v->qv,  v->qr,  v->qv_even, v->qr_even,
+                 v->amp_v,   v->amp_r,   v->age_v, v->age_r, v->trv, v->trr, v->G,       v->W};
+    CK(launch_change(V, F, C, s));
+    // 3. allocation
+    CK(launch_allocate(v->W, V.P, V.rays_avg, V.m0, V.rays_max, v->n, v->off, s));
+    // 4-5. adaptive rays: trace, shade
+    CK(launch_main_trace(V, F, S, v->off, v->sf, v->R_main, v->m_hit, s));
+    CK(launch_main_shade(V, F, L, S, v->irr, v->dep, v->off, v->sf, v->R_main, v->m_hit, v->m_rec, v->shadow_ctr, s));
+    // 6. blend (after every read of the previous atlases)
+    BlendBufs Bb{v->off, v->sf, v->pil_rec, v->m_rec, v->irr, v->dep, v->dep_n};
+    CK(launch_blend(V, F, Bb, s));
+    if (v->timing) {
+        CK(cudaEventRecord(v->ev1, s));
+        v->timed_pending = true;
+    }
+    if (F.even) v->last_even = (int64_t)f->frame;
+    v->frames += 1;
+    return ADGI_OK;
+}
+
+int adgi_query_irradiance(adgi_volume v, const float* pos, const float* nrm, int32_t n, float* out, int32_t on_device)
+{
+    if (!v || n < 0 || (n > 0 && (!pos || !nrm || !out))) return fail(ADGI_ERR_INVALID_ARG, "bad query arguments");
+    if (n == 0) return ADGI_OK;
+    cudaStream_t s = v->stream;
+    if (on_device) {
+        CK(launch_query(v->V, v->irr, v->dep, pos, nrm, n, out, s));
+        return ADGI_OK;
+    }
+    if (n > v->q_cap) {
+        cudaFree(v->q_buf);
+        v->q_buf = nullptr;
+        size_t dummy = 0;
+        if (dalloc(&v->q_buf, 9 * (size_t)n, &dummy) != cudaSuccess) return fail(ADGI_ERR_OOM, "query buffer");
+        v->q_cap = n;
+    }
+    float* dp = v->q_buf;
+    float* dn = dp + 3 * (size_t)n;
+    float* dout = dn + 3 * (size_t)n;
+    CK(cudaMemcpyAsync(dp, pos, sizeof(float) * 3 * (size_t)n, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(dn, nrm, sizeof(float) * 3 * (size_t)n, cudaMemcpyHostToDevice, s));
+    CK(launch_query(v->V, v->irr, v->dep, dp, dn, n, dout, s));
+    CK(cudaMemcpyAsync(out, dout, sizeof(float) * 3 * (size_t)n, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return ADGI_OK;
+}
+
+int adgi_get_stats(adgi_volume v, adgi_stats* out)
+{
+    if (!v || !out) return fail(ADGI_ERR_INVALID_ARG, "NULL argument");
+    CK(cudaStreamSynchronize(v->stream));
+    std::memset(out, 0, sizeof(*out));
+    out->frames = v->frames;
+    out->rays_per_update = (uint64_t)v->V.P * (uint64_t)v->V.rays_avg;
+    out->pilot_rays = (uint64_t)v->V.P * 8u;
+    unsigned long long sc = 0;
+    CK(cudaMemcpy(&sc, v->shadow_ctr, 8, cudaMemcpyDeviceToHost));
+    out->shadow_rays = sc;
+    int ef = 0;
+    CK(cudaMemcpy(&ef, v->err, 4, cudaMemcpyDeviceToHost));
+    if (ef) return fail(ADGI_ERR_CUDA, "device anomaly flags set: " + std::to_string(ef));
+    out->bvh_nodes = v->nt > 1 ? (uint32_t)(v->nt - 1) : 0u;
+    out->n_tris = (uint32_t)v->nt;
+    out->device_bytes = v->bytes + v->bvh.bytes();
+    if (v->timed_pending) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, v->ev0, v->ev1));
+        out->ms_last_update = ms;
+    }
+    return ADGI_OK;
+}
+
+int adgi_state_bytes(adgi_volume v, int32_t which, uint64_t* bytes)
+{
+    if (!v || !bytes) return fail(ADGI_ERR_INVALID_ARG, "NULL argument");
+    const uint64_t P = (uint64_t)v->V.P, R = v->R_main;
+    const uint64_t ti2 = (uint64_t)v->V.Ti * v->V.Ti, td2 = (uint64_t)v->V.Td * v->V.Td;
+    switch (which) {
+    case ADGI_STATE_W:
+    case ADGI_STATE_N: *bytes = 4 * P; break;
+    case ADGI_STATE_OFF: *bytes = 4 * (P + 1); break;
+    case ADGI_STATE_QV:
+    case ADGI_STATE_QR:
+    case ADGI_STATE_TRV:
+    case ADGI_STATE_TRR: *bytes = 2 * 8 * P; break;
+    case ADGI_STATE_PILOT_HIT: *bytes = 8 * 8 * P; break;
+    case ADGI_STATE_PILOT_REC: *bytes = 16 * 8 * P; break;
+    case ADGI_STATE_PILOT_LUM: *bytes = 4 * 8 * P; break;
+    case ADGI_STATE_MAIN_HIT: *bytes = 8 * R; break;
+    case ADGI_STATE_MAIN_REC: *bytes = 16 * R; break;
+    case ADGI_STATE_IRR: *bytes = P * ti2 * (v->V.fp16 ? 8 : 16); break;
+    case ADGI_STATE_DEP: *bytes = P * td2 * (v->V.fp16 ? 4 : 8); break;
+    case ADGI_STATE_DEP_N: *bytes = P * td2; break;
+    case ADGI_STATE_ROT: *bytes = 36; break;
+    default: return fail(ADGI_ERR_INVALID_ARG, "unknown state");
+    }
+    return ADGI_OK;
+}
+
+int adgi_read_state(adgi_volume v, int32_t which, void* dst, uint64_t bytes)
+{
+    uint64_t need = 0;
+    int rc = adgi_state_bytes(v, which, &need);
+    if (rc) return rc;
+    if (!dst || bytes != need) return fail(ADGI_ERR_INVALID_ARG, "destination size mismatch");
+    CK(cudaStreamSynchronize(v->stream));
+    if (which == ADGI_STATE_ROT) {
+        std::memcpy(dst, v->R, 36);
+        return ADGI_OK;
+    }
+    const void* src = nullptr;
+    switch (which) {
+    case ADGI_STATE_W: src = v->W; break;
+    case ADGI_STATE_N: src = v->n; break;
+    case ADGI_STATE_OFF: src = v->off; break;
+    case ADGI_STATE_QV: src = v->qv; break;
+    case ADGI_STATE_QR: src = v->qr; break;
+    case ADGI_STATE_TRV: src = v->trv; break;
+    case ADGI_STATE_TRR: src = v->trr; break;
+    case ADGI_STATE_PILOT_HIT: src = v->pil_hit; break;
+    case ADGI_STATE_PILOT_REC: src = v->pil_rec; break;
+    case ADGI_STATE_PILOT_LUM: src = v->pil_lum; break;
+    case ADGI_STATE_MAIN_HIT: src = v->m_hit; break;
+    case ADGI_STATE_MAIN_REC: src = v->m_rec; break;
+    case ADGI_STATE_IRR: src = v->irr; break;
+    case ADGI_STATE_DEP: src = v->dep; break;
+    case ADGI_STATE_DEP_N: src = v->dep_n; break;
+    }
+    if (bytes) CK(cudaMemcpy(dst, src, bytes, cudaMemcpyDeviceToHost));
+    return ADGI_OK;
+}
+
+int adgi_write_atlas(adgi_volume v, const void* irr, const void* dep, const uint8_t* dep_n)
+{
+    if (!v) return fail(ADGI_ERR_INVALID_ARG, "volume is NULL");
+    uint64_t b;
+    CK(cudaStreamSynchronize(v->stream));
+    if (irr) {
+        adgi_state_bytes(v, ADGI_STATE_IRR, &b);
+        CK(cudaMemcpy(v->irr, irr, b, cudaMemcpyHostToDevice));
+    }
+    if (dep) {
+        adgi_state_bytes(v, ADGI_STATE_DEP, &b);
+        CK(cudaMemcpy(v->dep, dep, b, cudaMemcpyHostToDevice));
+    }
+    if (dep_n) {
+        adgi_state_bytes(v, ADGI_STATE_DEP_N, &b);
+        CK(cudaMemcpy(v->dep_n, dep_n, b, cudaMemcpyHostToDevice));
+    }
+    return ADGI_OK;
+}
+
+int adgi_trace_closest(adgi_volume v, const float* o, const float* d, int32_t n, float tmin, float tmax, float* t_out,
+                       int32_t* tri_out)
+{
+    if (!v || n < 0 || (n > 0 && (!o || !d || !t_out || !tri_out))) return fail(ADGI_ERR_INVALID_ARG, "bad arguments");
+    if (!v->has_scene) return fail(ADGI_ERR_NO_SCENE, "no scene");
+    if (v->bvh_dirty) {
+        CK(v->bvh.build(v->verts, v->idx, v->nv, v->nt, v->eps, v->err, v->stream));
+        v->bvh_dirty = false;
+    }
+    SceneDev S = v->bvh.view(v->albedo, v->nv, v->err);
+    CK(launch_trace_list(S, o, d, n, tmin, tmax, t_out, tri_out, v->stream));
+    return ADGI_OK;
+}
+
+int adgi_allocate_rays(const uint32_t* W, int32_t P, int32_t avg, int32_t rmin, int32_t rmax, uint32_t* n_out,
+                       uint32_t* off_out, void* cuda_stream)
+{
+    if (!W || !n_out || !off_out || P <= 0) return fail(ADGI_ERR_INVALID_ARG, "bad arguments");
+    int m0 = rmin > 8 ? rmin : 8;
+    if (avg < m0 || avg > rmax || rmax > 4096 || (int64_t)P * avg >= ((int64_t)1 << 31))
+        return fail(ADGI_ERR_INVALID_ARG, "budget cannot be met");
+    CK(launch_allocate(W, P, avg, m0, rmax, n_out, off_out, (cudaStream_t)cuda_stream));
+    return ADGI_OK;
+}
+
+}  // extern "C"

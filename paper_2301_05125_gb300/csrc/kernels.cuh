@@ -1,0 +1,62 @@
+// kernels.cuh -- launch wrappers of the update's kernels (host side).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "adgi_internal.cuh"
+
+namespace adgi {
+
+struct LightSet {
+    int n;
+    Light l[kMaxLights];
+};
+
+struct ChangeBufs {
+    const int2* pil_hit;
+    const float* pil_lum;
+    const uint16_t* lut_v;
+    const uint16_t* lut_c;
+    uint16_t* qv;
+    uint16_t* qr;
+    uint16_t* qv_even;
+    uint16_t* qr_even;
+    uint16_t* amp_v;
+    uint16_t* amp_r;
+    uint8_t* age_v;
+    uint8_t* age_r;
+    uint16_t* trv;
+    uint16_t* trr;
+    uint32_t* G;  // per (probe, octant): octant-neighbourhood sum of trv + 2 trr
+    uint32_t* W;
+};
+
+struct BlendBufs {
+    const uint32_t* off;
+    const float4* sf;
+    const float4* pil_rec;
+    const float4* main_rec;
+    void* irr;
+    void* dep;
+    uint8_t* dep_n;
+};
+
+cudaError_t launch_pilot_trace(const VolConst& V, const FrameConst& F, const SceneDev& S, int2* hit, cudaStream_t s);
+cudaError_t launch_main_trace(const VolConst& V, const FrameConst& F, const SceneDev& S, const uint32_t* off,
+                              const float4* sf, uint32_t R, int2* hit, cudaStream_t s);
+cudaError_t launch_pilot_shade(const VolConst& V, const FrameConst& F, const LightSet& L, const SceneDev& S,
+                               const void* irr, const void* dep, const int2* hit, float4* rec, float* lum,
+                               unsigned long long* counter, cudaStream_t s);
+cudaError_t launch_main_shade(const VolConst& V, const FrameConst& F, const LightSet& L, const SceneDev& S,
+                              const void* irr, const void* dep, const uint32_t* off, const float4* sf, uint32_t R,
+                              const int2* hit, float4* rec, unsigned long long* counter, cudaStream_t s);
+cudaError_t launch_trace_list(const SceneDev& S, const float* o, const float* d, int n, float tmin, float tmax,
+                              float* t_out, int* tri_out, cudaStream_t s);
+
+cudaError_t launch_change(const VolConst& V, const FrameConst& F, const ChangeBufs& B, cudaStream_t s);
+cudaError_t launch_allocate(const uint32_t* W, int P, int avg, int m0, int rmax, uint32_t* n_out, uint32_t* off_out,
+                            cudaStream_t s);
+cudaError_t launch_blend(const VolConst& V, const FrameConst& F, const BlendBufs& B, cudaStream_t s);
+cudaError_t launch_query(const VolConst& V, const void* irr, const void* dep, const float* pos, const float* nrm, int n,
+                         float* out, cudaStream_t s);
+
+}  // namespace adgi

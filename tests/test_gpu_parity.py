@@ -1,0 +1,249 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Bit-exact: ray allocation, heuristics, pilot luminance, hit indices and t,
+texel counts.  Tolerances (tests/_helpers.py): irradiance 1e-3 relative,
+depth moments 1e-4 relative.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2301_05125_gb300 import scenegen as S
+
+from _helpers import DEP_RTOL, IRR_RTOL, gpu_volume, oracle_volume, rel_check
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def adgi():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2301_05125_gb300 import adgi as A
+    from paper_2301_05125_gb300 import build
+
+    build.build()
+    A.load()
+    return A
+
+
+def _compare_update(gv, ov, frame, check_atlas=True, what=""):
+    tag = "%s frame %d" % (what, frame)
+    gv.stats()  # raises if a device-side anomaly flag was set
+    np.testing.assert_array_equal(gv.W(), ov.W(), err_msg=tag + " W")
+    np.testing.assert_array_equal(gv.n(), ov.n(), err_msg=tag + " n")
+    np.testing.assert_array_equal(gv.off(), ov.off(), err_msg=tag + " off")
+    np.testing.assert_array_equal(gv.qv(), ov.qv(), err_msg=tag + " qv")
+    np.testing.assert_array_equal(gv.qr(), ov.qr(), err_msg=tag + " qr")
+    np.testing.assert_array_equal(gv.trv(), ov.trv(), err_msg=tag + " trv")
+    np.testing.assert_array_equal(gv.trr(), ov.trr(), err_msg=tag + " trr")
+    ph = gv.pilot_hit()
+    from paper_2301_05125_gb300 import adgi as A
+
+    np.testing.assert_array_equal(A.hit_tri(ph), ov.pilot_tri(), err_msg=tag + " pilot tri")
+    hitm = ov.pilot_tri() >= 0
+    np.testing.assert_array_equal(A.hit_t(ph)[hitm], ov.pilot_t()[hitm], err_msg=tag + " pilot t")
+    np.testing.assert_array_equal(gv.pilot_lum(), ov.pilot_lum().astype(np.float32), err_msg=tag + " pilot lum")
+    R = int(ov.off()[-1])
+    mh = gv.main_hit()[:R]
+    np.testing.assert_array_equal(A.hit_tri(mh), ov.main_tri(), err_msg=tag + " main tri")
+    hm = ov.main_tri() >= 0
+    np.testing.assert_array_equal(A.hit_t(mh)[hm], ov.main_t()[hm], err_msg=tag + " main t")
+    rel_check(gv.main_rec()[:R, :3], ov.main_rad(), IRR_RTOL, tag + " main radiance")
+    rel_check(gv.main_rec()[:R, 3], ov.main_dep(), DEP_RTOL, tag + " main depth")
+    if check_atlas:
+        gi, oi = gv.irr(), ov.irr()
+        np.testing.assert_array_equal(gi[..., 3].astype(np.int64), ov.irr_n().astype(np.int64),
+                                      err_msg=tag + " irr counts")
+        np.testing.assert_array_equal(gv.dep_n(), ov.dep_n(), err_msg=tag + " depth counts")
+        e_i = rel_check(gi[..., :3], oi, IRR_RTOL, tag + " irradiance atlas")
+        e_d = rel_check(gv.dep(), ov.dep(), DEP_RTOL, tag + " depth atlas")
+        return e_i, e_d
+    return None
+
+
+# ------------------------------------------------------------------ allocation
+@pytest.mark.parametrize("P", [1, 7, 64, 1000, 1025, 16384, 131072])
+def test_allocation_bit_exact(adgi, P):
+    rng = np.random.default_rng(P)
+    cases = [
+        (rng.integers(0, 1 << 24, P), 64, 8, 256),
+        (rng.integers(0, 3, P), 64, 4, 512),
+        (np.where(rng.random(P) < 0.01, rng.integers(1, 1 << 24, P), 0), 256, 8, 1024),
+        (np.zeros(P, np.int64), 33, 8, 40),
+        (np.full(P, 5), 9, 8, 9),
+        (rng.integers(0, 2, P) * ((1 << 24) - 1), 100, 16, 101),
+    ]
+    dev = torch.device("cuda")
+    for W, avg, rmin, rmax in cases:
+        W = W.astype(np.uint32)
+        n_ref, off_ref = O.allocate(W, avg, rmin, rmax)
+        Wd = torch.from_numpy(W.view(np.int32)).to(dev)
+        nd = torch.empty(P, dtype=torch.int32, device=dev)
+        od = torch.empty(P + 1, dtype=torch.int32, device=dev)
+        adgi.adgi_allocate_rays(Wd, avg, rmin, rmax, nd, od, torch.cuda.current_stream().cuda_stream)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(nd.cpu().numpy().view(np.uint32), n_ref)
+        np.testing.assert_array_equal(od.cpu().numpy().view(np.uint32), off_ref)
+
+
+def test_allocation_rejects_impossible_budget(adgi):
+    dev = torch.device("cuda")
+    W = torch.zeros(10, dtype=torch.int32, device=dev)
+    n = torch.empty(10, dtype=torch.int32, device=dev)
+    off = torch.empty(11, dtype=torch.int32, device=dev)
+    with pytest.raises(adgi.AdgiError):
+        adgi.adgi_allocate_rays(W, 300, 8, 256, n, off)
+
+
+# ------------------------------------------------------------------ tracing
+def _trace_case(adgi, w, O_, D, use_bvh):
+    gv = gpu_volume(adgi, w)
+    dev = torch.device("cuda")
+    o = torch.from_numpy(O_).to(dev)
+    d = torch.from_numpy(D).to(dev)
+    n = O_.shape[0]
+    t = torch.empty(n, dtype=torch.float32, device=dev)
+    tri = torch.empty(n, dtype=torch.int32, device=dev)
+    adgi.adgi_trace_closest(gv.h, o, d, 1e-4, float("inf"), t, tri)
+    torch.cuda.synchronize()
+    t_ref, tri_ref, det_ref = O.trace_closest(w.verts, w.idx, O_, D, 1e-4, np.inf, use_bvh=use_bvh)
+    h = np.stack([tri.cpu().numpy(), t.cpu().numpy().view(np.int32)], 1)
+    np.testing.assert_array_equal(adgi.hit_tri(h), tri_ref)
+    np.testing.assert_array_equal(t.cpu().numpy(), t_ref)
+    hit = tri_ref >= 0
+    np.testing.assert_array_equal(adgi.hit_back(h)[hit], (det_ref < 0)[hit])
+    gv.close()
+
+
+def test_trace_room_bit_exact_vs_brute_force(adgi):
+    rng = np.random.default_rng(11)
+    w = S.box_room(1)
+    n = 200000
+    O_ = rng.uniform(0.1, 7.9, (n, 3)).astype(np.float32)
+    D = rng.normal(size=(n, 3)).astype(np.float32)
+    # rays aimed exactly at box edges and corners stress watertightness
+    tgt = w.verts[rng.integers(0, len(w.verts), n // 4)]
+    D[: n // 4] = (tgt - O_[: n // 4]).astype(np.float32)
+    _trace_case(adgi, w, O_, D, use_bvh=False)
+
+
+def test_trace_city_bit_exact_vs_oracle(adgi):
+    rng = np.random.default_rng(12)
+    w = S.small_city(3, n_boxes=2000)
+    n = 100000
+    O_ = rng.uniform(-40, 40, (n, 3)).astype(np.float32)
+    O_[:, 1] = rng.uniform(0.5, 30, n)
+    D = rng.normal(size=(n, 3)).astype(np.float32)
+    _trace_case(adgi, w, O_, D, use_bvh=True)
+
+
+def test_trace_degenerate_scenes(adgi):
+    rng = np.random.default_rng(13)
+    O_ = rng.uniform(-1, 1, (5000, 3)).astype(np.float32)
+    D = rng.normal(size=(5000, 3)).astype(np.float32)
+    one = S.Workload("one", 0, np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0]], np.float32),
+                     np.array([[0, 1, 2]], np.int32), np.ones((1, 3), np.float32), S.box_room(1).volume, 1,
+                     (0, 0, 0), lambda f: [])
+    _trace_case(adgi, one, O_, D, use_bvh=False)
+    # duplicated triangles: ties must resolve to the smaller index
+    dup = S.Workload("dup", 0, one.verts, np.repeat(one.idx, 5, 0), np.ones((5, 3), np.float32),
+                     S.box_room(1).volume, 1, (0, 0, 0), lambda f: [])
+    _trace_case(adgi, dup, O_, D, use_bvh=False)
+
+
+# ------------------------------------------------------------------ full update
+def test_update_room_bit_exact_and_within_tolerance(adgi):
+    w = S.box_room(1)
+    gv = gpu_volume(adgi, w)
+    ov = oracle_volume(O, w)
+    for f in range(w.frames):
+        gv.update(f, w.seed, w.lights_at(f), w.sky)
+        ov.update(f, w.seed, w.lights_at(f), w.sky)
+        _compare_update(gv, ov, f, what="room")
+    rng = np.random.default_rng(3)
+    pos = rng.uniform(0.5, 7.5, (4000, 3)).astype(np.float32)
+    nrm = rng.normal(size=(4000, 3)).astype(np.float32)
+    rel_check(gv.query(pos, nrm), ov.query(pos, nrm), IRR_RTOL, "room query")
+    gv.close()
+
+
+def test_update_small_city_ragged(adgi):
+    # 9 x 5 x 7 probes (ragged against every block size), moving occluders
+    w = S.small_city(4, n_boxes=800, dims=(9, 5, 7), rays_avg=40)
+    gv = gpu_volume(adgi, w)
+    ov = oracle_volume(O, w)
+    for f in range(4):
+        dv = w.dyn_at(f)
+        gv.move_vertices(w.dyn_first, dv)
+        ov.move_vertices(w.dyn_first, dv)
+        gv.update(f, w.seed, w.lights_at(f), w.sky)
+        ov.update(f, w.seed, w.lights_at(f), w.sky)
+        _compare_update(gv, ov, f, what="small city")
+    rng = np.random.default_rng(5)
+    pos = rng.uniform(-40, 40, (4000, 3)).astype(np.float32)
+    pos[:, 1] = rng.uniform(0, 40, 4000)
+    nrm = rng.normal(size=(4000, 3)).astype(np.float32)
+    rel_check(gv.query(pos, nrm), ov.query(pos, nrm), IRR_RTOL, "city query")
+    gv.close()
+
+
+@pytest.mark.parametrize("case", ["pilots_only", "uniform_forced", "empty_scene", "theta1_camera", "minimal_grid"])
+def test_update_edge_cases(adgi, case):
+    w = S.box_room(2)
+    over = {}
+    cam = None
+    if case == "pilots_only":
+        over = dict(rays_avg=8, rays_min=8, rays_max=8)
+    elif case == "uniform_forced":
+        over = dict(rays_avg=32, rays_min=32, rays_max=32)
+    elif case == "empty_scene":
+        w = S.Workload("empty", 1, np.zeros((3, 3), np.float32), np.zeros((0, 3), np.int32),
+                       np.zeros((0, 3), np.float32), w.volume, 3, (0.3, 0.5, 0.9), lambda f: [])
+    elif case == "theta1_camera":
+        over = dict(tr_theta=1)
+        cam = ((2.0, 3.0, 2.5), 1.5)
+    elif case == "minimal_grid":
+        over = dict(dims=(2, 2, 2), spacing=(4.0, 4.0, 4.0), rays_avg=100, rays_max=300)
+    gv = gpu_volume(adgi, w, **over)
+    ov = oracle_volume(O, w, **over)
+    for f in range(4):
+        gv.update(f, w.seed, w.lights_at(f), w.sky, camera=cam)
+        ov.update(f, w.seed, w.lights_at(f), w.sky, camera=cam)
+        _compare_update(gv, ov, f, what=case)
+    gv.close()
+
+
+def test_update_rejects_bad_calls(adgi):
+    w = S.box_room(1)
+    v = adgi.Volume(**w.volume)
+    with pytest.raises(adgi.AdgiError) as e:
+        v.update(0, 1, [])
+    assert e.value.code == -4  # no scene
+    v.set_scene(w.verts, w.idx, w.albedo)
+    with pytest.raises(adgi.AdgiError):
+        v.move_vertices(len(w.verts) - 1, np.zeros((2, 3), np.float32))
+    bad = w.idx.copy()
+    bad[0, 0] = len(w.verts)
+    with pytest.raises(adgi.AdgiError):
+        v.set_scene(w.verts, bad, w.albedo)
+    v.close()
+
+
+# ------------------------------------------------------------------ full size
+def test_tunnel_city_full_size_two_frames(adgi):
+    """The bench workload (16384 probes, 4.19M rays/update, ~200k triangles,
+    moving occluders) on both sides for two frames: allocation, heuristics and
+    every hit bit-exact; atlases within tolerance."""
+    w = S.tunnel_city(1)
+    gv = gpu_volume(adgi, w)
+    ov = oracle_volume(O, w)
+    for f in range(2):
+        dv = w.dyn_at(f)
+        gv.move_vertices(w.dyn_first, dv)
+        ov.move_vertices(w.dyn_first, dv)
+        gv.update(f, w.seed, w.lights_at(f), w.sky)
+        ov.update(f, w.seed, w.lights_at(f), w.sky)
+        _compare_update(gv, ov, f, what="tunnel")
+    gv.close()

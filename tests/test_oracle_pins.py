@@ -609,7 +609,8 @@ def test_query_equal_probes_and_trilinear():
 def test_query_chebyshev_weight():
     # probe 0 sees a wall at mean depth 0.1 with zero variance: for a point at
     # distance d > mu its weight is scaled by var/(var + (d-mu)^2), var floored
-    # at 1e-6 s^2 (one-sided Chebyshev bound, VSM).
+    # at max(1e-3 mu2, 1e-6 s^2) (one-sided Chebyshev bound with the minimum
+    # variance of variance shadow maps).
     rng = np.random.default_rng(7)
     vals = rng.uniform(0, 5, (8, 3))
     mu = [0.1] + [10.0] * 7
@@ -624,7 +625,7 @@ def test_query_chebyshev_weight():
         w = np.prod([xf[k] if o[k] else 1 - xf[k] for k in range(3)])
         if c == 0:
             d = np.linalg.norm(xf)
-            var = 1e-6 * s2
+            var = max(1e-3 * 0.1 ** 2, 1e-6 * s2)
             w *= var / (var + (d - 0.1) ** 2)
         ref_w.append(w)
     ref_w = np.array(ref_w)
