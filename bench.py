@@ -1,0 +1,436 @@
+#!/usr/bin/env python
+"""Throughput of the ADGI per-frame probe update on GB300.
+
+A step is one whole update (moving-occluder vertex update and BVH rebuild,
+pilot rays, heuristics, allocation, adaptive rays with shadow rays and the
+multi-bounce query, blend) of the tunnel + city workload: 32x16x32 probes,
+256 rays/probe (4,194,304 rays per update), ~200k triangles, 3 moving point
+lights + sun, 20 moving occluders; FP32 atlases.
+
+Prints one JSON line (rank 0).  `value` is probe rays per second per update
+with inputs resident in HBM (L2 flushed between timed steps); `e2e` is the
+same metric through the C ABI with host buffers (occluder vertices and a
+shading query in, query results out, copies inside the timed region).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+# FP32 lane operations per unit of traversal work (counted from the kernels'
+# arithmetic): one BVH node visit tests two child boxes (6 sub, 6 mul,
+# 8 min/max, 2 compare each = 22, so 44); one watertight triangle test is
+# 9 sub + 6 mul/sub pairs + 6 mul + 3 sub + 2 add (det) + 3 mul + 4 (T) +
+# 1 div (counted 8) + 6 compares = 55.
+OPS_NODE = 44
+OPS_TRI = 55
+# algorithmic blend bytes per touched probe tile: read + write of the
+# irradiance tile (8x8 float4 = 1024 B), depth tile (16x16 float2 = 2048 B)
+# and depth counts (256 B); plus 16 B per blended ray record read.
+TILE_BYTES_FP32 = 2 * (8 * 8 * 16 + 16 * 16 * 8 + 16 * 16)
+REC_BYTES = 16
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), d.get("sm_max_mhz", 2070.0), "measured"
+    return 6800.0, 2070.0, "fallback"
+
+
+def _source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2301_05125_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def _ncu_traffic(kernel):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on
+    the current kernel sources (else None)."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    e = d.get(kernel)
+    if not e or e.get("source_hash") != _source_hash():
+        return None
+    return e.get("dram_bytes_per_launch_scaled", e.get("dram_bytes_per_launch"))
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self):
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        idx = os.environ.get("LOCAL_RANK", "0")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(idx), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                smax.append(float(f[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    return ws, rank
+
+
+def _workload(name, seed):
+    from paper_2301_05125_gb300 import scenegen as S
+
+    return {"tunnel_city": S.tunnel_city, "box_room": S.box_room, "scaled": S.scaled}[name](seed)
+
+
+def _cpu_baseline(w, budget_s=20.0, threads=None, steps=None):
+    """The oracle as it stands on the host cores: full updates of the same
+    workload until the time budget is spent (at least one)."""
+    from oracle import oracle as O
+
+    threads = threads or os.cpu_count() or 1
+    vd = w.volume
+    ov = O.OracleVolume(vd["origin"], vd["spacing"], vd["dims"], vd["irr_interior"], vd["depth_interior"],
+                        vd["rays_avg"], vd["rays_min"], vd["rays_max"], vd["hysteresis"], vd["depth_max"],
+                        vd["tr_theta"], threads=threads)
+    ov.set_scene(w.verts, w.idx, w.albedo)
+    times = []
+    f = 0
+    t_start = time.perf_counter()
+    while True:
+        if w.dyn_at is not None:
+            ov.move_vertices(w.dyn_first, w.dyn_at(f))
+        t0 = time.perf_counter()
+        ov.update(f, w.seed, w.lights_at(f), w.sky)
+        times.append(time.perf_counter() - t0)
+        f += 1
+        if steps is not None:
+            if f >= steps:
+                break
+        elif time.perf_counter() - t_start > budget_s or f >= 8:
+            break
+    ov.close()
+    return times, threads
+
+
+def run_reference(args):
+    ws, rank = _dist()
+    if rank != 0:
+        return 0
+    w = _workload(args.workload, args.seed)
+    # warm-up updates are untimed; each timed step is one full oracle update
+    # unless that would not fit a few minutes, then a probe sample
+    from oracle import oracle as O
+
+    threads = os.cpu_count() or 1
+    vd = w.volume
+    ov = O.OracleVolume(vd["origin"], vd["spacing"], vd["dims"], vd["irr_interior"], vd["depth_interior"],
+                        vd["rays_avg"], vd["rays_min"], vd["rays_max"], vd["hysteresis"], vd["depth_max"],
+                        vd["tr_theta"], threads=threads)
+    ov.set_scene(w.verts, w.idx, w.albedo)
+    t0 = time.perf_counter()
+    ov.move_vertices(w.dyn_first, w.dyn_at(0))
+    ov.update(0, w.seed, w.lights_at(0), w.sky)
+    t_one = time.perf_counter() - t0
+    budget = 150.0
+    full = (args.steps + args.warmup) * t_one <= budget
+    frame = 1
+    for _ in range(max(0, args.warmup - 1)):
+        if full:
+            ov.move_vertices(w.dyn_first, w.dyn_at(frame))
+            ov.update(frame, w.seed, w.lights_at(frame), w.sky)
+            frame += 1
+    times, rays = [], []
+    if full:
+        sample = "full updates of the workload (every probe and phase, BVH rebuild included)"
+        for _ in range(args.steps):
+            ov.move_vertices(w.dyn_first, w.dyn_at(frame))
+            t0 = time.perf_counter()
+            ov.update(frame, w.seed, w.lights_at(frame), w.sky)
+            times.append(time.perf_counter() - t0)
+            rays.append(w.rays_per_update)
+            frame += 1
+    else:
+        frac = max(1e-3, budget / ((args.steps + args.warmup) * t_one))
+        stride = max(1, int(round(1.0 / frac)))
+        probes = np.arange(0, w.n_probes, stride, dtype=np.int32)
+        sample = "trace+shade of every %d-th probe (%d probes) per step, frame %d" % (stride, len(probes), frame)
+        for _ in range(args.steps):
+            t0 = time.perf_counter()
+            r = ov.trace_shade_probes(frame, w.seed, w.lights_at(frame), probes, w.sky)
+            times.append(time.perf_counter() - t0)
+            rays.append(r)
+    ov.close()
+    tot_t = sum(times)
+    value = sum(rays) / tot_t
+    line = {
+        "impl": "reference", "metric": "probe rays/s per update", "value": value, "unit": "rays/s",
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded generator standing in for the paper's scenes)",
+        "config": {"workload": w.name, "probes": w.n_probes, "rays_per_update": w.rays_per_update,
+                   "triangles": w.n_tris},
+        "cpu_baseline": {"value": value, "unit": "rays/s", "cores": threads, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "rays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+
+    from paper_2301_05125_gb300 import adgi
+    from paper_2301_05125_gb300 import build as pkg_build
+
+    ws, rank = _dist()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    if rank == 0:
+        pkg_build.build()
+    if ws > 1:
+        dist.barrier()
+    adgi.load()
+    dev = torch.device("cuda", local)
+    # replicas: every rank updates its own volume (independent seeds); no data-path collective
+    w = _workload(args.workload, args.seed + rank)
+    vd = dict(w.volume)
+    if args.fp16:
+        vd["atlas_fp16"] = 1
+    stream = torch.cuda.Stream(device=dev)
+    vol = adgi.Volume(stream=stream.cuda_stream, **vd)
+    vol.set_scene(w.verts, w.idx, w.albedo)
+    adgi.adgi_enable_timing(vol.h, True)
+    n_frames = args.warmup + args.steps
+    have_dyn = w.dyn_at is not None and w.dyn_count > 0
+    if have_dyn:
+        dyn_host = np.stack([w.dyn_at(f) for f in range(n_frames + args.steps + 2)]).astype(np.float32)
+        dyn_dev = torch.from_numpy(dyn_host).to(dev)
+    frames = [adgi.make_frame(f, w.seed, w.lights_at(f), w.sky) for f in range(n_frames + args.steps + 2)]
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > 129 MB L2
+
+    def step(f):
+        if have_dyn:
+            vol.move_vertices(w.dyn_first, dyn_dev[f])
+        adgi.adgi_update(vol.h, frames[f])
+
+    with torch.cuda.stream(stream):
+        for f in range(args.warmup):
+            step(f)
+    torch.cuda.synchronize()
+    phases = {k: [] for k in adgi.PHASES}
+    dev_ms, host_ms = [], []
+    tiles_touched, rays_blended = [], []
+    clocks = Clocks()
+    launches0 = vol.stats().kernels_launched
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t_wall0 = time.perf_counter()
+    for k in range(args.steps):
+        f = args.warmup + k
+        with torch.cuda.stream(stream):
+            flush.fill_(float(k))
+        stream.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        th0 = time.perf_counter()
+        e0.record(stream)
+        step(f)
+        e1.record(stream)
+        e1.synchronize()
+        host_ms.append(1e3 * (time.perf_counter() - th0))
+        dev_ms.append(e0.elapsed_time(e1))
+        st = vol.stats()
+        for i, name in enumerate(adgi.PHASES):
+            phases[name].append(st.ms_phase[i])
+        n = vol.n()
+        m = n.astype(np.int64) - 8
+        even = f % 2 == 0
+        tiles_touched.append(vol.P if even else int((m > 0).sum()))
+        rays_blended.append(int(m.sum()) + (8 * vol.P if even else 0))
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t_wall0
+    clk = clocks.stop()
+    launches = vol.stats().kernels_launched - launches0
+    last_frame = frames[args.warmup + args.steps - 1]
+    counts = adgi.adgi_count_traversal(vol.h, last_frame)
+    ms_step = float(np.mean(dev_ms))
+    if ws > 1:
+        t = torch.tensor([ms_step], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    rays = w.rays_per_update
+    value = ws * rays / (ms_step / 1e3)
+    hbm, smax_nominal, peak_src = _peaks()
+    mean_ph = {k: float(np.mean(v)) for k, v in phases.items()}
+    dominant = max(mean_ph, key=mean_ph.get)
+    # ALU roofline of a traversal kernel: counted FP32 lane ops / time vs
+    # 152 SMs x 128 FP32 lanes x max SM clock
+    alu_peak = 152 * 128 * smax_nominal * 1e6 / 1e12  # T lane-ops/s
+    work = {
+        "pilot_trace": OPS_NODE * counts[0] + OPS_TRI * counts[1],
+        "pilot_shade": OPS_NODE * counts[2] + OPS_TRI * counts[3],
+        "trace": OPS_NODE * counts[4] + OPS_TRI * counts[5],
+        "shade": OPS_NODE * counts[6] + OPS_TRI * counts[7],
+    }
+    tile_bytes = TILE_BYTES_FP32 if not args.fp16 else 2 * (8 * 8 * 8 + 16 * 16 * 4 + 16 * 16)
+    blend_bytes = float(np.mean(tiles_touched)) * tile_bytes + float(np.mean(rays_blended)) * REC_BYTES
+    blend_ach = blend_bytes / (mean_ph["blend"] / 1e3) / 1e9
+    kname = {"trace": "k_main_trace", "shade": "k_main_shade", "pilot_trace": "k_pilot_trace",
+             "pilot_shade": "k_pilot_shade", "blend": "k_blend", "bvh": "k_scatter"}
+    if dominant in work:
+        ach = work[dominant] / (mean_ph[dominant] / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": alu_peak, "unit": "Tops/s (FP32 lane ops)",
+                "frac": ach / alu_peak, "traffic": _ncu_traffic(kname.get(dominant, dominant)),
+                "kernel": kname.get(dominant, dominant), "ms": mean_ph[dominant],
+                "peak_source": "152 SMs x 128 FP32 lanes x %.0f MHz" % smax_nominal}
+    else:
+        roof = {"bound": "hbm", "achieved": blend_ach, "peak": hbm, "unit": "GB/s", "frac": blend_ach / hbm,
+                "traffic": _ncu_traffic("k_blend"), "kernel": "k_blend", "ms": mean_ph["blend"]}
+    roof_blend = {"bound": "hbm", "achieved": blend_ach, "peak": hbm, "unit": "GB/s", "frac": blend_ach / hbm,
+                  "traffic": _ncu_traffic("k_blend"), "algorithmic_bytes": blend_bytes, "ms": mean_ph["blend"],
+                  "peak_source": "%s hbm_gbs" % peak_src}
+    # end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        nq = 65536
+        rng = np.random.default_rng(7)
+        o = np.array(vd["origin"], np.float32)
+        ext = np.array(vd["spacing"], np.float32) * (np.array(vd["dims"]) - 1)
+        qpos = torch.from_numpy((o + rng.random((nq, 3)) * ext).astype(np.float32)).pin_memory()
+        qnrm = torch.from_numpy(rng.normal(size=(nq, 3)).astype(np.float32)).pin_memory()
+        qout = torch.empty((nq, 3), dtype=torch.float32).pin_memory()
+        dyn_pin = torch.from_numpy(dyn_host).pin_memory() if have_dyn else None
+        f0 = args.warmup + args.steps
+        e2e_ms = []
+        torch.cuda.synchronize()
+        for k in range(min(args.steps, 10)):
+            f = f0 + (k % 2)
+            t0 = time.perf_counter()
+            if have_dyn:
+                adgi.adgi_move_vertices(vol.h, w.dyn_first, dyn_pin[f].numpy())
+            adgi.adgi_update(vol.h, frames[f])
+            adgi.adgi_query_irradiance(vol.h, qpos.numpy(), qnrm.numpy(), qout.numpy())
+            e2e_ms.append(1e3 * (time.perf_counter() - t0))
+        h2d = (w.dyn_count * 12 if have_dyn else 0) + 2 * nq * 12 + len(w.lights_at(0)) * 28
+        e2e = {"value": ws * rays / (float(np.mean(e2e_ms)) / 1e3), "unit": "rays/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": nq * 12, "ms_per_step": float(np.mean(e2e_ms)),
+               "includes": "host->device occluder vertices + 65536-point shading query (positions, normals) "
+                           "from pinned memory, update, query results back to the host"}
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        times, cores = _cpu_baseline(w, budget_s=args.cpu_budget)
+        cpu = {"value": rays / float(np.mean(times)), "unit": "rays/s", "cores": cores, "kind": "oracle",
+               "sample": "%d full oracle update(s) of the same workload (frames 0-%d, every probe and phase, "
+                         "BVH rebuild included), host threads = cores" % (len(times), len(times) - 1)}
+    if rank == 0:
+        line = {
+            "metric": "probe rays/s per update", "value": value, "unit": "rays/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if not args.fp16 else "f32 (f16 atlases)",
+            "data": "synthetic (seeded tunnel+city generator standing in for the paper's scenes)",
+            "config": {"workload": w.name, "probes": w.n_probes, "rays_per_update": rays,
+                       "triangles": w.n_tris, "lights": len(w.lights_at(0)), "atlas": "fp16" if args.fp16 else "fp32",
+                       "l2": "flushed (256 MB write) between timed steps", "parallelism": "replicas" if ws > 1 else "1 GPU"},
+            "latency_ms": {"device_p50": float(np.percentile(dev_ms, 50)), "device_p99": float(np.percentile(dev_ms, 99)),
+                           "host_p50": float(np.percentile(host_ms, 50)), "host_p99": float(np.percentile(host_ms, 99))},
+            "phases_ms": mean_ph,
+            "traversal_counts": {"pilot_nodes": counts[0], "pilot_tris": counts[1], "pilot_shadow_nodes": counts[2],
+                                 "pilot_shadow_tris": counts[3], "nodes": counts[4], "tris": counts[5],
+                                 "shadow_nodes": counts[6], "shadow_tris": counts[7]},
+            "rays_incl_shadow_per_s": ws * (rays + vol.stats().shadow_rays) / (ms_step / 1e3),
+            "roofline": roof,
+            "roofline_blend": roof_blend,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": int(launches),
+            "clocks": clk,
+            "wall_s": wall,
+        }
+        print(json.dumps(line), flush=True)
+    vol.close()
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="tunnel_city", choices=["tunnel_city", "box_room", "scaled"])
+    ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--fp16", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -106,6 +106,10 @@ typedef struct {
     uint32_t n_tris;
     uint64_t device_bytes;    /* device memory held by the volume */
     float ms_last_update;     /* device time of the last update (0 unless timing was enabled) */
+    float ms_phase[8];        /* device time per phase of the last update (timing enabled):
+                                 0 BVH rebuild, 1 pilot trace, 2 pilot shade, 3 heuristics,
+                                 4 allocation, 5 adaptive trace, 6 adaptive shade, 7 blend */
+    uint64_t kernels_launched; /* kernels this library has launched in the process so far */
 } adgi_stats;
 
 /* Create a volume on the current CUDA device.  desc: host pointer, copied.
@@ -215,6 +219,15 @@ int adgi_write_atlas(adgi_volume vol, const void* irr, const void* dep, const ui
  * watertight test and BVH as the update.  Enqueued on the volume's stream. */
 int adgi_trace_closest(adgi_volume vol, const float* o, const float* d, int32_t n, float tmin, float tmax,
                        float* t_out, int32_t* tri_out);
+
+/* Traversal work of the last update, for roofline accounting: re-traces the
+ * last update's pilot and adaptive rays (and their shadow rays for the lights
+ * of *frame, which must be the last update's frame) with counters, without
+ * changing any state.  counts (host uint64[8]) receives, for the pilot rays
+ * then for the adaptive rays: nearest-hit node visits, nearest-hit triangle
+ * tests, shadow-ray node visits, shadow-ray triangle tests.  Synchronises the
+ * stream.  Errors: INVALID_ARG, NO_SCENE, CUDA. */
+int adgi_count_traversal(adgi_volume vol, const adgi_frame* frame, uint64_t* counts);
 
 /* Ray allocation of step 3 as a stand-alone call on device arrays:
  * W (uint32[P]) -> n_out (uint32[P], pilots included, sum = rays_avg * P),

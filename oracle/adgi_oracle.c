@@ -1094,18 +1094,25 @@ static void bilinear(const double* tile, int T, int n, int ch, const double dir[
     }
 }
 
+/* FP32 coordinate of probe plane j along axis k (where the probes sit) */
+static double pcoord(const orc_vol* v, int k, int j)
+{
+    float c = v->d.origin[k] + v->d.spacing[k] * (float)j;
+    return (double)c;
+}
+
+/* The probe cage holding x: along each axis the last probe plane at or below x
+   (clamped to the grid), and the trilinear fraction from that plane. */
 static void query_point(const orc_vol* v, const double x[3], const double nrm[3], double out[3])
 {
-    double g[3], a[3];
+    double a[3];
     int b[3];
     for (int k = 0; k < 3; ++k) {
-        g[k] = (x[k] - (double)v->d.origin[k]) / (double)v->d.spacing[k];
-        double f = floor(g[k]);
-        int bi = (int)(f < -1e9 ? -1e9 : (f > 1e9 ? 1e9 : f));
-        if (bi < 0) bi = 0;
-        if (bi > v->d.dims[k] - 2) bi = v->d.dims[k] - 2;
+        int n = v->d.dims[k];
+        int bi = 0;
+        while (bi < n - 2 && x[k] >= pcoord(v, k, bi + 1)) ++bi;
         b[k] = bi;
-        double al = g[k] - bi;
+        double al = (x[k] - pcoord(v, k, bi)) / (double)v->d.spacing[k];
         if (al < 0.0) al = 0.0;
         if (al > 1.0) al = 1.0;
         a[k] = al;

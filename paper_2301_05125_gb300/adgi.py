@@ -70,12 +70,18 @@ class adgi_stats(C.Structure):
         ("n_tris", C.c_uint32),
         ("device_bytes", C.c_uint64),
         ("ms_last_update", C.c_float),
+        ("ms_phase", C.c_float * 8),
+        ("kernels_launched", C.c_uint64),
     ]
+
+
+PHASES = ["bvh", "pilot_trace", "pilot_shade", "heuristics", "allocation", "trace", "shade", "blend"]
 
 
 EXPORTED = ["adgi_create_volume", "adgi_set_scene", "adgi_move_vertices", "adgi_update", "adgi_query_irradiance",
             "adgi_get_stats", "adgi_destroy", "adgi_set_stream", "adgi_enable_timing", "adgi_state_bytes",
-            "adgi_read_state", "adgi_write_atlas", "adgi_trace_closest", "adgi_allocate_rays", "adgi_last_error"]
+            "adgi_read_state", "adgi_write_atlas", "adgi_trace_closest", "adgi_count_traversal", "adgi_allocate_rays",
+            "adgi_last_error"]
 
 _lib = None
 
@@ -103,6 +109,7 @@ def load(path: str = LIB_PATH):
     L.adgi_write_atlas.argtypes = [vp, vp, vp, vp]
     L.adgi_trace_closest.argtypes = [vp, vp, vp, i32, C.c_float, C.c_float, vp, vp]
     L.adgi_allocate_rays.argtypes = [vp, i32, i32, i32, i32, vp, vp, vp]
+    L.adgi_count_traversal.argtypes = [vp, C.POINTER(adgi_frame), C.POINTER(C.c_uint64)]
     L.adgi_last_error.restype = C.c_char_p
     for name in EXPORTED[:-1]:
         getattr(L, name).restype = C.c_int
@@ -197,6 +204,12 @@ def adgi_write_atlas(vol, irr=None, dep=None, dep_n=None):
 def adgi_trace_closest(vol, o, d, tmin, tmax, t_out, tri_out):
     n = int(o.shape[0]) if o.ndim == 2 else int(o.shape[0] // 3)
     _check(load().adgi_trace_closest(vol, _ptr(o), _ptr(d), n, float(tmin), float(tmax), _ptr(t_out), _ptr(tri_out)))
+
+
+def adgi_count_traversal(vol, frame: adgi_frame):
+    out = (C.c_uint64 * 8)()
+    _check(load().adgi_count_traversal(vol, C.byref(frame), out))
+    return [int(x) for x in out]
 
 
 def adgi_allocate_rays(W, rays_avg, rays_min, rays_max, n_out, off_out, stream=None):

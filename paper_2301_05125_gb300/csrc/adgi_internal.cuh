@@ -256,7 +256,8 @@ constexpr int kStack = 96;
 
 // nearest hit with t in (tmin, tmax]; (t, original index) lexicographic
 __device__ __forceinline__ void trace_closest(const SceneDev& S, float3 o, float3 d, float tmin, float tmax,
-                                              float& t_best, uint32_t& hit_best)
+                                              float& t_best, uint32_t& hit_best, uint32_t* nvis = nullptr,
+                                              uint32_t* ntri = nullptr)
 {
     t_best = tmax;
     hit_best = kMiss;
@@ -267,6 +268,7 @@ __device__ __forceinline__ void trace_closest(const SceneDev& S, float3 o, float
     float best_det = 0.0f;
     bool found = false;
     auto test_tri = [&](int slot) {
+        if (ntri) ++*ntri;
         const float4* tv = S.tri_v + 3 * (size_t)slot;
         float4 A = __ldg(tv), B = __ldg(tv + 1), C = __ldg(tv + 2);
         float tt, det;
@@ -291,6 +293,7 @@ __device__ __forceinline__ void trace_closest(const SceneDev& S, float3 o, float
                 atomicOr(S.err, kErrTraversal);
                 break;
             }
+            if (nvis) ++*nvis;
             const BNode* nd = S.nodes + node;
             float4 a = __ldg(&nd->a), b = __ldg(&nd->b), c = __ldg(&nd->c);
             int4 ch = __ldg(&nd->d);
@@ -328,13 +331,15 @@ __device__ __forceinline__ void trace_closest(const SceneDev& S, float3 o, float
 }
 
 // any hit with t strictly inside (tlo, thi)
-__device__ __forceinline__ bool trace_any(const SceneDev& S, float3 o, float3 d, float tlo, float thi)
+__device__ __forceinline__ bool trace_any(const SceneDev& S, float3 o, float3 d, float tlo, float thi,
+                                          uint32_t* nvis = nullptr, uint32_t* ntri = nullptr)
 {
     if (S.n_tris == 0) return false;
     WRay wr = wray(o, d);
     float3 inv = make_float3(1.0f / d.x, 1.0f / d.y, 1.0f / d.z);
     float lim = isinf(thi) ? thi : thi * kBoxSlack;
     auto test_tri = [&](int slot) -> bool {
+        if (ntri) ++*ntri;
         const float4* tv = S.tri_v + 3 * (size_t)slot;
         float4 A = __ldg(tv), B = __ldg(tv + 1), C = __ldg(tv + 2);
         float tt, det;
@@ -350,6 +355,7 @@ __device__ __forceinline__ bool trace_any(const SceneDev& S, float3 o, float3 d,
             atomicOr(S.err, kErrTraversal);
             break;
         }
+        if (nvis) ++*nvis;
         const BNode* nd = S.nodes + node;
         float4 a = __ldg(&nd->a), b = __ldg(&nd->b), c = __ldg(&nd->c);
         int4 ch = __ldg(&nd->d);
@@ -425,21 +431,113 @@ __device__ __forceinline__ void tile_bilinear(const void* base, size_t tile_off,
     }
 }
 
-// 8-probe trilinear x Chebyshev irradiance query (FP32)
-__device__ __forceinline__ float3 query_irr(const VolConst& V, const void* irr, const void* dep, float3 x, float3 nrm)
+// FP32 coordinate of probe plane j along axis k (where the probes sit)
+__device__ __forceinline__ float pcoord(const VolConst& V, int k, int j)
 {
-    float g[3] = {(x.x - V.origin[0]) / V.spacing[0], (x.y - V.origin[1]) / V.spacing[1],
-                  (x.z - V.origin[2]) / V.spacing[2]};
+    return fa(V.origin[k], fm(V.spacing[k], (float)j));
+}
+
+// (o - pb) + t*d with the rounding errors of the product and the sum carried
+// (FMA residual + two-sum), so the result has a small *relative* error even
+// when the hit point sits next to a probe plane far from the world origin.
+__device__ __forceinline__ float local_offset(float o, float pb, float t, float d)
+{
+    float a = fs(o, pb);  // probe planes: exact difference
+    float p = fm(t, d);
+    float e = __fmaf_rn(t, d, -p);
+    float s = fa(a, p);
+    float bb = fs(s, a);
+    float err = fa(fs(a, fs(s, bb)), fs(p, bb));
+    return fa(s, fa(e, err));
+}
+
+// Depth moments of probe tile p at the direction of dv (not normalised:
+// the octahedral map is scale invariant), FP32 bilinear fractions.
+__device__ __forceinline__ void depth_moments(const VolConst& V, const void* dep, size_t tile, float dx, float dy,
+                                              float dz, float* mom, float* cond)
+{
+    float l1 = fabsf(dx) + fabsf(dy) + fabsf(dz);
+    float px = dx / l1, py = dy / l1;
+    if (dz < 0.0f) {
+        float qx = (1.0f - fabsf(py)) * sgnf(px);
+        float qy = (1.0f - fabsf(px)) * sgnf(py);
+        px = qx;
+        py = qy;
+    }
+    const int n = V.n_dep, T = V.Td;
+    float fx = (1.0f + (px + 1.0f) * 0.5f * (float)n) - 0.5f;
+    float fy = (1.0f + (py + 1.0f) * 0.5f * (float)n) - 0.5f;
+    int x0 = min(max((int)floorf(fx), 0), n);
+    int y0 = min(max((int)floorf(fy), 0), n);
+    float ax = fminf(fmaxf(fx - (float)x0, 0.0f), 1.0f);
+    float ay = fminf(fmaxf(fy - (float)y0, 0.0f), 1.0f);
+    size_t i00 = tile + (size_t)(y0 * T + x0);
+    float2 v00 = dep_load(dep, i00, V.fp16), v01 = dep_load(dep, i00 + 1, V.fp16);
+    float2 v10 = dep_load(dep, i00 + T, V.fp16), v11 = dep_load(dep, i00 + T + 1, V.fp16);
+    float w00 = (1.f - ax) * (1.f - ay), w01 = ax * (1.f - ay), w10 = (1.f - ax) * ay, w11 = ax * ay;
+    mom[0] = w00 * v00.x + w01 * v01.x + w10 * v10.x + w11 * v11.x;
+    mom[1] = w00 * v00.y + w01 * v01.y + w10 * v10.y + w11 * v11.y;
+    // conditioning of the filtered variance against the fractions: the spread
+    // of the footprint's means (squared) over the floored variance
+    float var = fmaxf(mom[1] - mom[0] * mom[0], fmaxf(1e-3f * mom[1], V.var_min));
+    float s2 = fmaxf(fmaxf(fabsf(v00.y - mom[1]), fabsf(v01.y - mom[1])), fmaxf(fabsf(v10.y - mom[1]), fabsf(v11.y - mom[1])));
+    *cond = s2 / var;
+}
+
+// The same lookup with the direction and the four bilinear weights in FP64
+// (for footprints where FP32 fractions would perturb the variance).
+static __device__ __noinline__ void depth_moments_fp64(const VolConst& V, const void* dep, size_t tile, double dx, double dy,
+                                                double dz, float* mom)
+{
+    double l1 = fabs(dx) + fabs(dy) + fabs(dz);
+    double px = dx / l1, py = dy / l1;
+    if (dz < 0.0) {
+        double qx = (1.0 - fabs(py)) * (px >= 0.0 ? 1.0 : -1.0);
+        double qy = (1.0 - fabs(px)) * (py >= 0.0 ? 1.0 : -1.0);
+        px = qx;
+        py = qy;
+    }
+    const int n = V.n_dep, T = V.Td;
+    double fx = (1.0 + (px + 1.0) * 0.5 * (double)n) - 0.5;
+    double fy = (1.0 + (py + 1.0) * 0.5 * (double)n) - 0.5;
+    int x0 = min(max((int)floor(fx), 0), n);
+    int y0 = min(max((int)floor(fy), 0), n);
+    double ax = fmin(fmax(fx - (double)x0, 0.0), 1.0);
+    double ay = fmin(fmax(fy - (double)y0, 0.0), 1.0);
+    size_t i00 = tile + (size_t)(y0 * T + x0);
+    float2 v00 = dep_load(dep, i00, V.fp16), v01 = dep_load(dep, i00 + 1, V.fp16);
+    float2 v10 = dep_load(dep, i00 + T, V.fp16), v11 = dep_load(dep, i00 + T + 1, V.fp16);
+    double w00 = (1.0 - ax) * (1.0 - ay), w01 = ax * (1.0 - ay), w10 = (1.0 - ax) * ay, w11 = ax * ay;
+    mom[0] = (float)(w00 * v00.x + w01 * v01.x + w10 * v10.x + w11 * v11.x);
+    mom[1] = (float)(w00 * v00.y + w01 * v01.y + w10 * v10.y + w11 * v11.y);
+}
+
+// 8-probe trilinear x Chebyshev irradiance query at x = o + t*d (the public
+// query passes t = 0).  The cage is the one whose FP32 probe planes bracket x;
+// offsets from each probe are formed without rounding x to world coordinates.
+__device__ __forceinline__ float3 query_irr_at(const VolConst& V, const void* irr, const void* dep, float3 o, float t,
+                                               float3 d, float3 nrm)
+{
+    float os[3] = {o.x, o.y, o.z}, ds[3] = {d.x, d.y, d.z};
     int b[3];
     float al[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        float f = floorf(g[k]);
-        f = fminf(fmaxf(f, -1e9f), 1e9f);
-        int bi = (int)f;
-        bi = min(max(bi, 0), V.dims[k] - 2);
+        float g = floorf((fa(os[k], fm(t, ds[k])) - V.origin[k]) / V.spacing[k]);
+        int bi = (int)fminf(fmaxf(g, 0.0f), (float)(V.dims[k] - 2));
+        float l = local_offset(os[k], pcoord(V, k, bi), t, ds[k]);
+        if (bi > 0 && l < 0.0f) {
+            --bi;
+            l = local_offset(os[k], pcoord(V, k, bi), t, ds[k]);
+        } else if (bi < V.dims[k] - 2) {
+            float l2 = local_offset(os[k], pcoord(V, k, bi + 1), t, ds[k]);
+            if (l2 >= 0.0f) {
+                ++bi;
+                l = l2;
+            }
+        }
         b[k] = bi;
-        al[k] = fminf(fmaxf(g[k] - (float)bi, 0.0f), 1.0f);
+        al[k] = fminf(fmaxf(l / V.spacing[k], 0.0f), 1.0f);
     }
     float nl = sqrtf(nrm.x * nrm.x + nrm.y * nrm.y + nrm.z * nrm.z);
     float3 nd = nl > 0.0f ? make_float3(nrm.x / nl, nrm.y / nl, nrm.z / nl) : make_float3(0.f, 0.f, 1.f);
@@ -450,13 +548,24 @@ __device__ __forceinline__ float3 query_irr(const VolConst& V, const void* irr, 
     for (int c = 0; c < 8; ++c) {
         int o0 = c & 1, o1 = (c >> 1) & 1, o2 = (c >> 2) & 1;
         float wt = (o0 ? al[0] : 1.f - al[0]) * (o1 ? al[1] : 1.f - al[1]) * (o2 ? al[2] : 1.f - al[2]);
-        int p = (b[0] + o0) + V.dims[0] * ((b[1] + o1) + V.dims[1] * (b[2] + o2));
-        float3 pp = probe_pos(V, p);
-        float dx = x.x - pp.x, dy = x.y - pp.y, dz = x.z - pp.z;
+        int ix = b[0] + o0, iy = b[1] + o1, iz = b[2] + o2;
+        int p = ix + V.dims[0] * (iy + V.dims[1] * iz);
+        float px = pcoord(V, 0, ix), py = pcoord(V, 1, iy), pz = pcoord(V, 2, iz);
+        float dx = local_offset(os[0], px, t, ds[0]);
+        float dy = local_offset(os[1], py, t, ds[1]);
+        float dz = local_offset(os[2], pz, t, ds[2]);
         float dist = sqrtf(dx * dx + dy * dy + dz * dz);
-        float3 dir = dist > 0.f ? make_float3(dx / dist, dy / dist, dz / dist) : make_float3(0.f, 0.f, 1.f);
-        float mom[2];
-        tile_bilinear<2>(dep, (size_t)p * td2, V.Td, V.n_dep, oct_encode_x(dir), V.fp16, mom);
+        float mom[2] = {0.f, 0.f};
+        if (dist > 0.f) {
+            float cond;
+            depth_moments(V, dep, (size_t)p * td2, dx, dy, dz, mom, &cond);
+            if (cond > 128.0f) {  // FP32 fractions would move the variance by > ~6e-5
+                double ddx = ((double)os[0] - (double)px) + (double)t * (double)ds[0];
+                double ddy = ((double)os[1] - (double)py) + (double)t * (double)ds[1];
+                double ddz = ((double)os[2] - (double)pz) + (double)t * (double)ds[2];
+                depth_moments_fp64(V, dep, (size_t)p * td2, ddx, ddy, ddz, mom);
+            }
+        }
         float wc = 1.f;
         if (dist > mom[0]) {
             // minimum variance: max(1e-3 mu2, 1e-6 s^2) keeps the weight well
@@ -477,6 +586,17 @@ __device__ __forceinline__ float3 query_irr(const VolConst& V, const void* irr, 
     }
     if (sw >= 1e-12f) return make_float3(sum[0] / sw, sum[1] / sw, sum[2] / sw);
     return make_float3(sumt[0], sumt[1], sumt[2]);
+}
+
+__device__ __forceinline__ float3 query_irr(const VolConst& V, const void* irr, const void* dep, float3 x, float3 nrm)
+{
+    return query_irr_at(V, irr, dep, x, 0.0f, make_float3(0.f, 0.f, 0.f), nrm);
+}
+
+__device__ __forceinline__ float3 query_irr_hit(const VolConst& V, const void* irr, const void* dep, float3 o, float t,
+                                                float3 d, float3 nrm)
+{
+    return query_irr_at(V, irr, dep, o, t, d, nrm);
 }
 
 }  // namespace adgi

@@ -10,6 +10,7 @@
 
 #include "adgi_internal.cuh"
 #include "bvh.cuh"
+#include "kernels.cuh"
 
 namespace adgi {
 
@@ -338,16 +339,22 @@ cudaError_t Bvh::build(const float* d_verts, const int* d_idx, int nv, int nt, f
     e = cudaMemcpyAsync(bounds, init, sizeof(init), cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return e;
     k_tri_prep<<<(nt + T - 1) / T, T, 0, s>>>(d_verts, d_idx, nt, tri_orig, bounds);
+    count_launches(1);
     k_morton<<<(nt + T - 1) / T, T, 0, s>>>(tri_orig, nt, bounds, keys[0], vals[0]);
+    count_launches(1);
     int nb = (nt + kSortTile - 1) / kSortTile;
     int cur = 0;
     for (int shift = 0; shift < 64; shift += 8) {
         k_hist<<<nb, kSortThreads, 0, s>>>(keys[cur], nt, shift, hist, nb);
+        count_launches(1);
         k_scan_small<<<1, 1024, 0, s>>>(hist, 256 * nb);
+        count_launches(1);
         k_scatter<<<nb, kSortThreads, 0, s>>>(keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], nt, shift, hist, nb);
+        count_launches(1);
         cur ^= 1;
     }
     k_tri_order<<<(nt + T - 1) / T, T, 0, s>>>(tri_orig, vals[cur], nt, tri_v);
+    count_launches(1);
     if (nt == 1) {
         root_leaf = 0;
         return cudaGetLastError();
@@ -356,7 +363,9 @@ cudaError_t Bvh::build(const float* d_verts, const int* d_idx, int nv, int nt, f
     e = cudaMemsetAsync(flags, 0, sizeof(int) * (size_t)nt, s);
     if (e != cudaSuccess) return e;
     k_hierarchy<<<(nt - 1 + T - 1) / T, T, 0, s>>>(keys[cur], nt, nodes, par_int, par_leaf);
+    count_launches(1);
     k_bounds<<<(nt + T - 1) / T, T, 0, s>>>(tri_v, nt, nodes, par_int, par_leaf, flags, eps, err);
+    count_launches(1);
     return cudaGetLastError();
 }
 

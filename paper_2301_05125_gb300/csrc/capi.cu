@@ -20,8 +20,14 @@
 #include "bvh.cuh"
 #include "kernels.cuh"
 
+#include <atomic>
+
 namespace adgi {
 size_t blend_smem_bytes(const VolConst& V);
+
+static std::atomic<unsigned long long> g_launches{0};
+void count_launches(unsigned n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+unsigned long long kernels_launched() { return g_launches.load(std::memory_order_relaxed); }
 }
 
 using namespace adgi;
@@ -142,6 +148,7 @@ struct adgi_volume_s {
     float R[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
     bool timing = false;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    cudaEvent_t ph[9] = {};  // phase boundaries of the last timed update
     bool timed_pending = false;
     // query scratch for host pointers
     float* q_buf = nullptr;
@@ -162,6 +169,8 @@ void free_volume(adgi_volume v)
     v->bvh.release();
     if (v->ev0) cudaEventDestroy(v->ev0);
     if (v->ev1) cudaEventDestroy(v->ev1);
+    for (cudaEvent_t e : v->ph)
+        if (e) cudaEventDestroy(e);
     delete v;
 }
 
@@ -328,6 +337,7 @@ int adgi_create_volume(const adgi_volume_desc* desc, void* cuda_stream, adgi_vol
     CKV(cudaMemsetAsync(v->err, 0, 4, s));
     CKV(cudaEventCreate(&v->ev0));
     CKV(cudaEventCreate(&v->ev1));
+    for (cudaEvent_t& e : v->ph) CKV(cudaEventCreate(&e));
     // the host vectors die at return: wait for the copies
     CKV(cudaStreamSynchronize(s));
 #undef CKV
@@ -447,7 +457,10 @@ int adgi_update(adgi_volume v, const adgi_frame* f)
         return fail(ADGI_ERR_INVALID_ARG, "bad light list");
     cudaStream_t s = v->stream;
     const VolConst& V = v->V;
+#define PHASE(i) \
+    if (v->timing) CK(cudaEventRecord(v->ph[i], s))
     if (v->timing) CK(cudaEventRecord(v->ev0, s));
+    PHASE(0);
     if (v->bvh_dirty) {
         CK(v->bvh.build(v->verts, v->idx, v->nv, v->nt, v->eps, v->err, s));
         v->bvh_dirty = false;
@@ -465,20 +478,29 @@ int adgi_update(adgi_volume v, const adgi_frame* f)
     SceneDev S = v->bvh.view(v->albedo, v->nv, v->err);
     CK(cudaMemsetAsync(v->shadow_ctr, 0, 8, s));
     // 1. pilot rays (trace + shade; the shading reads the previous atlases)
+    PHASE(1);
     CK(launch_pilot_trace(V, F, S, v->pil_hit, s));
+    PHASE(2);
     CK(launch_pilot_shade(V, F, L, S, v->irr, v->dep, v->pil_hit, v->pil_rec, v->pil_lum, v->shadow_ctr, s));
     // 2. heuristics -> W_p
+    PHASE(3);
     ChangeBufs C{v->pil_hit, v->pil_lum, v->lut_v, v->lut_c, v->qv,  v->qr,  v->qv_even, v->qr_even,
                  v->amp_v,   v->amp_r,   v->age_v, v->age_r, v->trv, v->trr, v->G,       v->W};
     CK(launch_change(V, F, C, s));
     // 3. allocation
+    PHASE(4);
     CK(launch_allocate(v->W, V.P, V.rays_avg, V.m0, V.rays_max, v->n, v->off, s));
     // 4-5. adaptive rays: trace, shade
+    PHASE(5);
     CK(launch_main_trace(V, F, S, v->off, v->sf, v->R_main, v->m_hit, s));
+    PHASE(6);
     CK(launch_main_shade(V, F, L, S, v->irr, v->dep, v->off, v->sf, v->R_main, v->m_hit, v->m_rec, v->shadow_ctr, s));
     // 6. blend (after every read of the previous atlases)
+    PHASE(7);
     BlendBufs Bb{v->off, v->sf, v->pil_rec, v->m_rec, v->irr, v->dep, v->dep_n};
     CK(launch_blend(V, F, Bb, s));
+    PHASE(8);
+#undef PHASE
     if (v->timing) {
         CK(cudaEventRecord(v->ev1, s));
         v->timed_pending = true;
@@ -532,10 +554,12 @@ int adgi_get_stats(adgi_volume v, adgi_stats* out)
     out->bvh_nodes = v->nt > 1 ? (uint32_t)(v->nt - 1) : 0u;
     out->n_tris = (uint32_t)v->nt;
     out->device_bytes = v->bytes + v->bvh.bytes();
+    out->kernels_launched = adgi::kernels_launched();
     if (v->timed_pending) {
         float ms = 0.f;
         CK(cudaEventElapsedTime(&ms, v->ev0, v->ev1));
         out->ms_last_update = ms;
+        for (int i = 0; i < 8; ++i) CK(cudaEventElapsedTime(&out->ms_phase[i], v->ph[i], v->ph[i + 1]));
     }
     return ADGI_OK;
 }
@@ -631,6 +655,42 @@ int adgi_trace_closest(adgi_volume v, const float* o, const float* d, int32_t n,
     }
     SceneDev S = v->bvh.view(v->albedo, v->nv, v->err);
     CK(launch_trace_list(S, o, d, n, tmin, tmax, t_out, tri_out, v->stream));
+    return ADGI_OK;
+}
+
+int adgi_count_traversal(adgi_volume v, const adgi_frame* f, uint64_t* counts)
+{
+    if (!v || !f || !counts) return fail(ADGI_ERR_INVALID_ARG, "NULL argument");
+    if (!v->has_scene) return fail(ADGI_ERR_NO_SCENE, "no scene");
+    if (f->n_lights < 0 || f->n_lights > kMaxLights || (f->n_lights > 0 && !f->lights))
+        return fail(ADGI_ERR_INVALID_ARG, "bad light list");
+    cudaStream_t s = v->stream;
+    float Rsave[9];
+    std::memcpy(Rsave, v->R, sizeof(Rsave));
+    int64_t le = v->last_even;
+    FrameConst F = frame_const(v, f);
+    v->last_even = le;
+    std::memcpy(v->R, Rsave, sizeof(Rsave));
+    LightSet L;
+    L.n = f->n_lights;
+    for (int i = 0; i < f->n_lights; ++i) {
+        L.l[i].kind = f->lights[i].kind;
+        for (int k = 0; k < 3; ++k) {
+            L.l[i].v[k] = f->lights[i].pos_or_dir[k];
+            L.l[i].rgb[k] = f->lights[i].rgb[k];
+        }
+    }
+    unsigned long long* d = nullptr;
+    size_t dummy = 0;
+    if (dalloc(&d, 8, &dummy) != cudaSuccess) return fail(ADGI_ERR_OOM, "counter buffer");
+    cudaError_t e = cudaMemsetAsync(d, 0, 64, s);
+    if (e == cudaSuccess) e = launch_count(v->V, F, L, v->bvh.view(v->albedo, v->nv, v->err), v->off, v->sf, v->R_main, d, s);
+    unsigned long long h[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, d, 64, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(d);
+    if (e != cudaSuccess) return fail(ADGI_ERR_CUDA, std::string("count: ") + cudaGetErrorString(e));
+    for (int i = 0; i < 8; ++i) counts[i] = h[i];
     return ADGI_OK;
 }
 

@@ -6,6 +6,10 @@
 
 namespace adgi {
 
+// process-wide count of kernels launched by this library (launch wrappers add to it)
+void count_launches(unsigned n);
+unsigned long long kernels_launched();
+
 struct LightSet {
     int n;
     Light l[kMaxLights];
@@ -49,6 +53,8 @@ cudaError_t launch_pilot_shade(const VolConst& V, const FrameConst& F, const Lig
 cudaError_t launch_main_shade(const VolConst& V, const FrameConst& F, const LightSet& L, const SceneDev& S,
                               const void* irr, const void* dep, const uint32_t* off, const float4* sf, uint32_t R,
                               const int2* hit, float4* rec, unsigned long long* counter, cudaStream_t s);
+cudaError_t launch_count(const VolConst& V, const FrameConst& F, const LightSet& L, const SceneDev& S,
+                         const uint32_t* off, const float4* sf, uint32_t R, unsigned long long* out, cudaStream_t s);
 cudaError_t launch_trace_list(const SceneDev& S, const float* o, const float* d, int n, float tmin, float tmax,
                               float* t_out, int* tri_out, cudaStream_t s);
 

@@ -146,7 +146,7 @@ __device__ __forceinline__ float4 shade(const VolConst& V, const FrameConst& F, 
     float r0 = fm(fm(a0, kInvPi), E0), r1 = fm(fm(a1, kInvPi), E1), r2 = fm(fm(a2, kInvPi), E2);
     *lum_out = fa(fa(fm(kLumR, r0), fm(kLumG, r1)), fm(kLumB, r2));
     if (bounce) {
-        float3 Q = query_irr(V, irr, dep, x, n);
+        float3 Q = query_irr_hit(V, irr, dep, o, t, d, n);
         r0 += a0 * Q.x;
         r1 += a1 * Q.y;
         r2 += a2 * Q.z;
@@ -208,6 +208,81 @@ __global__ void __launch_bounds__(128) k_main_shade(VolConst V, FrameConst F, co
     count_shadow(ns, counter);
 }
 
+// Re-trace the last update's rays with work counters (roofline accounting).
+__global__ void __launch_bounds__(128) k_count(VolConst V, FrameConst F, const __grid_constant__ LightSet L, SceneDev S,
+                                               const uint32_t* __restrict__ off, const float4* __restrict__ sf,
+                                               uint32_t R, unsigned long long* __restrict__ out)
+{
+    __shared__ int s_lo, s_hi;
+    const uint32_t NP = (uint32_t)V.P * kPilots;
+    uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+    // the main-ray part of this block, for the probe search
+    uint32_t b0 = blockIdx.x * blockDim.x;
+    uint32_t m0r = b0 > NP ? b0 - NP : 0u;
+    uint32_t m1r = min(R ? R - 1 : 0u, (b0 + blockDim.x - 1 > NP ? b0 + blockDim.x - 1 - NP : 0u));
+    if (R) block_probe_range(off, V.P, m0r, m1r, &s_lo, &s_hi);
+    uint32_t cv = 0, ct = 0, sv = 0, st = 0;
+    if (r < NP + R) {
+        float3 org, d;
+        bool ok = true;
+        if (r < NP) {
+            int p = r >> 3;
+            org = probe_pos(V, p);
+            d = pilot_dir(F.pilot_key, (uint32_t)p, r & 7);
+        } else {
+            uint32_t q = r - NP;
+            int p = probe_of_ray(off, q, s_lo, s_hi);
+            uint32_t base = __ldg(off + p), m = __ldg(off + p + 1) - base;
+            ok = m <= (uint32_t)(V.rays_max - kPilots) && q - base < m;
+            org = probe_pos(V, p);
+            if (ok) d = main_dir(F, sf, m, q - base);
+        }
+        if (ok) {
+            float t;
+            uint32_t h;
+            trace_closest(S, org, d, V.tmin, __int_as_float(0x7F800000), t, h, &cv, &ct);
+            if (h != kMiss && !(h & kBackBit)) {
+                int tri = (int)h;
+                float4 A = __ldg(S.tri_orig + 3 * (size_t)tri), B = __ldg(S.tri_orig + 3 * (size_t)tri + 1),
+                       C = __ldg(S.tri_orig + 3 * (size_t)tri + 2);
+                float e1x = fs(B.x, A.x), e1y = fs(B.y, A.y), e1z = fs(B.z, A.z);
+                float e2x = fs(C.x, A.x), e2y = fs(C.y, A.y), e2z = fs(C.z, A.z);
+                float cx = fs(fm(e1y, e2z), fm(e1z, e2y));
+                float cy = fs(fm(e1z, e2x), fm(e1x, e2z));
+                float cz = fs(fm(e1x, e2y), fm(e1y, e2x));
+                float cl = fsq(dot3x(cx, cy, cz, cx, cy, cz));
+                float3 n = cl > 0.0f ? make_float3(fd(cx, cl), fd(cy, cl), fd(cz, cl)) : make_float3(0.f, 0.f, 1.f);
+                float3 x = make_float3(fa(org.x, fm(t, d.x)), fa(org.y, fm(t, d.y)), fa(org.z, fm(t, d.z)));
+                float3 xs = make_float3(fa(x.x, fm(V.tmin, n.x)), fa(x.y, fm(V.tmin, n.y)), fa(x.z, fm(V.tmin, n.z)));
+                for (int l = 0; l < L.n; ++l) {
+                    const Light& Li = L.l[l];
+                    float3 D = Li.kind == 0 ? make_float3(fs(Li.v[0], xs.x), fs(Li.v[1], xs.y), fs(Li.v[2], xs.z))
+                                            : make_float3(-Li.v[0], -Li.v[1], -Li.v[2]);
+                    float thi = Li.kind == 0 ? 1.0f : __int_as_float(0x7F800000);
+                    if (!(dot3x(n.x, n.y, n.z, D.x, D.y, D.z) > 0.0f)) continue;
+                    trace_any(S, xs, D, 0.0f, thi, &sv, &st);
+                }
+            }
+        }
+    }
+    const bool main_ray = r >= NP && r < NP + R;
+    unsigned long long* o4 = out;
+#pragma unroll
+    for (int part = 0; part < 2; ++part) {
+        bool mine = (part == 1) == main_ray;
+        unsigned long long a = __reduce_add_sync(0xFFFFFFFFu, mine ? cv : 0u);
+        unsigned long long b = __reduce_add_sync(0xFFFFFFFFu, mine ? ct : 0u);
+        unsigned long long c = __reduce_add_sync(0xFFFFFFFFu, mine ? sv : 0u);
+        unsigned long long e = __reduce_add_sync(0xFFFFFFFFu, mine ? st : 0u);
+        if ((threadIdx.x & 31) == 0) {
+            atomicAdd(o4 + 4 * part + 0, a);
+            atomicAdd(o4 + 4 * part + 1, b);
+            atomicAdd(o4 + 4 * part + 2, c);
+            atomicAdd(o4 + 4 * part + 3, e);
+        }
+    }
+}
+
 __global__ void k_trace_list(SceneDev S, const float* __restrict__ o, const float* __restrict__ d, int n, float tmin,
                              float tmax, float* __restrict__ t_out, int* __restrict__ tri_out)
 {
@@ -228,6 +303,7 @@ cudaError_t launch_pilot_trace(const VolConst& V, const FrameConst& F, const Sce
 {
     int n = V.P * kPilots;
     k_pilot_trace<<<(n + 127) / 128, 128, 0, s>>>(V, F, S, hit);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -236,6 +312,7 @@ cudaError_t launch_main_trace(const VolConst& V, const FrameConst& F, const Scen
 {
     if (R == 0) return cudaSuccess;
     k_main_trace<<<(R + 127) / 128, 128, 0, s>>>(V, F, S, off, sf, R, hit);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -245,6 +322,7 @@ cudaError_t launch_pilot_shade(const VolConst& V, const FrameConst& F, const Lig
 {
     int n = V.P * kPilots;
     k_pilot_shade<<<(n + 127) / 128, 128, 0, s>>>(V, F, L, S, irr, dep, hit, rec, lum, counter);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -254,6 +332,16 @@ cudaError_t launch_main_shade(const VolConst& V, const FrameConst& F, const Ligh
 {
     if (R == 0) return cudaSuccess;
     k_main_shade<<<(R + 127) / 128, 128, 0, s>>>(V, F, L, S, irr, dep, off, sf, R, hit, rec, counter);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_count(const VolConst& V, const FrameConst& F, const LightSet& L, const SceneDev& S,
+                         const uint32_t* off, const float4* sf, uint32_t R, unsigned long long* out, cudaStream_t s)
+{
+    uint32_t n = (uint32_t)V.P * kPilots + R;
+    k_count<<<(n + 127) / 128, 128, 0, s>>>(V, F, L, S, off, sf, R, out);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -262,6 +350,7 @@ cudaError_t launch_trace_list(const SceneDev& S, const float* o, const float* d,
 {
     if (n == 0) return cudaSuccess;
     k_trace_list<<<(n + 127) / 128, 128, 0, s>>>(S, o, d, n, tmin, tmax, t_out, tri_out);
+    count_launches(1);
     return cudaGetLastError();
 }
 

@@ -434,7 +434,9 @@ size_t blend_smem_bytes(const VolConst& V)
 cudaError_t launch_change(const VolConst& V, const FrameConst& F, const ChangeBufs& B, cudaStream_t s)
 {
     k_change_state<<<(V.P + 127) / 128, 128, 0, s>>>(V, F, B);
+    count_launches(1);
     k_change_weight<<<(V.P + 127) / 128, 128, 0, s>>>(V, F, B);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -442,6 +444,7 @@ cudaError_t launch_allocate(const uint32_t* W, int P, int avg, int m0, int rmax,
                             cudaStream_t s)
 {
     k_allocate<<<1, kAllocThreads, 0, s>>>(W, P, avg, m0, rmax, n_out, off_out);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -453,6 +456,7 @@ cudaError_t launch_blend(const VolConst& V, const FrameConst& F, const BlendBufs
         if (e != cudaSuccess) return e;
     }
     k_blend<<<V.P, kBlendThreads, sm, s>>>(V, F, B);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -461,6 +465,7 @@ cudaError_t launch_query(const VolConst& V, const void* irr, const void* dep, co
 {
     if (n == 0) return cudaSuccess;
     k_query<<<(n + 127) / 128, 128, 0, s>>>(V, irr, dep, pos, nrm, n, out);
+    count_launches(1);
     return cudaGetLastError();
 }
 

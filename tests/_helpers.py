@@ -31,13 +31,15 @@ def gpu_volume(adgi, w, stream=None, **over):
     return v
 
 
-def rel_check(a, b, rtol, what=""):
+def rel_check(a, b, rtol, what="", dump=None):
     a = np.asarray(a, np.float64)
     b = np.asarray(b, np.float64)
-    scale = max(float(np.abs(b).mean()), 1e-30)
+    scale = max(float(np.abs(b).mean()), 1e-30) if b.size else 1e-30
     bound = rtol * np.maximum(np.abs(b), 1e-3 * scale)
     bad = np.abs(a - b) > bound
     if bad.any():
+        if dump is not None:
+            dump(np.flatnonzero(bad.reshape(bad.shape[0], -1).any(axis=1)))
         i = np.flatnonzero(bad.ravel())[:5]
         raise AssertionError("%s: %d of %d outside tolerance %g; first: gpu %s oracle %s" %
                              (what, int(bad.sum()), bad.size, rtol, a.ravel()[i], b.ravel()[i]))

@@ -28,6 +28,19 @@ def adgi():
     return A
 
 
+def _dump_rays(gv, ov, frame, what):
+    import os
+
+    def dump(rows):
+        os.makedirs("gpurun_out", exist_ok=True)
+        R = int(ov.off()[-1])
+        np.savez("gpurun_out/fail_%s_f%d.npz" % (what.replace(" ", "_"), frame), rows=rows[:64],
+                 gpu_rec=gv.main_rec()[:R][rows[:64]], ora_rad=ov.main_rad()[rows[:64]],
+                 ora_dep=ov.main_dep()[rows[:64]], tri=ov.main_tri()[rows[:64]], t=ov.main_t()[rows[:64]],
+                 off=ov.off(), n=ov.n())
+    return dump
+
+
 def _compare_update(gv, ov, frame, check_atlas=True, what=""):
     tag = "%s frame %d" % (what, frame)
     gv.stats()  # raises if a device-side anomaly flag was set
@@ -50,7 +63,8 @@ def _compare_update(gv, ov, frame, check_atlas=True, what=""):
     np.testing.assert_array_equal(A.hit_tri(mh), ov.main_tri(), err_msg=tag + " main tri")
     hm = ov.main_tri() >= 0
     np.testing.assert_array_equal(A.hit_t(mh)[hm], ov.main_t()[hm], err_msg=tag + " main t")
-    rel_check(gv.main_rec()[:R, :3], ov.main_rad(), IRR_RTOL, tag + " main radiance")
+    rel_check(gv.main_rec()[:R, :3], ov.main_rad(), IRR_RTOL, tag + " main radiance",
+              dump=_dump_rays(gv, ov, frame, what))
     rel_check(gv.main_rec()[:R, 3], ov.main_dep(), DEP_RTOL, tag + " main depth")
     if check_atlas:
         gi, oi = gv.irr(), ov.irr()
