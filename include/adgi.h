@@ -185,6 +185,9 @@ int adgi_enable_timing(adgi_volume vol, int32_t enable);
  *   ADGI_STATE_DEP      float[P][Td][Td][2] {mean, mean^2} (half[...][2] when atlas_fp16)
  *   ADGI_STATE_DEP_N    uint8[P][Td][Td]  depth sample counts
  *   ADGI_STATE_ROT      float[9]          main-ray rotation of the last update
+ *   ADGI_STATE_BVH_NODES bytes[max(T-1,1)][64]  BVH nodes of the current scene (T triangles;
+ *                       layout of adgi_build_bvh)
+ *   ADGI_STATE_BVH_TRIS  float[T][3][4]    triangles in BVH order (layout of adgi_build_bvh)
  */
 enum {
     ADGI_STATE_W = 0,
@@ -202,7 +205,9 @@ enum {
     ADGI_STATE_IRR = 12,
     ADGI_STATE_DEP = 13,
     ADGI_STATE_DEP_N = 14,
-    ADGI_STATE_ROT = 15
+    ADGI_STATE_ROT = 15,
+    ADGI_STATE_BVH_NODES = 16,
+    ADGI_STATE_BVH_TRIS = 17
 };
 int adgi_state_bytes(adgi_volume vol, int32_t which, uint64_t* bytes);
 int adgi_read_state(adgi_volume vol, int32_t which, void* dst_host, uint64_t bytes);
@@ -228,6 +233,28 @@ int adgi_trace_closest(adgi_volume vol, const float* o, const float* d, int32_t 
  * tests, shadow-ray node visits, shadow-ray triangle tests.  Synchronises the
  * stream.  Errors: INVALID_ARG, NO_SCENE, CUDA. */
 int adgi_count_traversal(adgi_volume vol, const adgi_frame* frame, uint64_t* counts);
+
+/* Build the update's software BVH (Morton codes, stable radix sort, radix
+ * tree, bottom-up child boxes enlarged by eps) for caller triangles into
+ * caller buffers -- the structure adgi_update() traces against.
+ *   verts:     device float[3*n_verts];  tri_idx: device int32[3*n_tris]
+ *   eps:       absolute box enlargement (adgi_set_scene uses 1e-5 x the
+ *              larger of the scene extent and the largest |coordinate|)
+ *   nodes_out: device buffer of max(n_tris-1, 1) * 64 bytes; node i holds
+ *              float[12] child boxes {lo0.xyz, hi0.xyz, lo1.xyz, hi1.xyz} then
+ *              int32[4] {left, right, 0, 0}: a child c >= 0 is node c, c < 0 is
+ *              triangle slot ~c; node 0 is the root (n_tris >= 2)
+ *   tris_out:  device float[n_tris][3][4]: the triangles in BVH order, vertex
+ *              xyz + w, where w of vertex 0 holds the original triangle index
+ *              as int32 bits
+ * Scratch (sort keys and values, parents, flags: about 84 bytes a triangle)
+ * is allocated on the stream with cudaMallocAsync and released with
+ * cudaFreeAsync.  Synchronises the stream before return.  Errors:
+ * INVALID_ARG (NULL pointers, negative counts, n_tris > 0 with n_verts <= 0,
+ * a vertex index outside [0, n_verts): detected on the device, the build
+ * then used vertex 0 for it), OOM, CUDA. */
+int adgi_build_bvh(const float* verts, int32_t n_verts, const int32_t* tri_idx, int32_t n_tris, float eps,
+                   void* nodes_out, void* tris_out, void* cuda_stream);
 
 /* Ray allocation of step 3 as a stand-alone call on device arrays:
  * W (uint32[P]) -> n_out (uint32[P], pilots included, sum = rays_avg * P),

@@ -17,7 +17,7 @@ ADGI_OK = 0
 ERRORS = {-1: "INVALID_ARG", -2: "OOM", -3: "OVER_BUDGET", -4: "NO_SCENE", -5: "CUDA", -6: "TIMEOUT"}
 
 STATE = dict(W=0, N=1, OFF=2, QV=3, QR=4, TRV=5, TRR=6, PILOT_HIT=7, PILOT_REC=8, PILOT_LUM=9, MAIN_HIT=10,
-             MAIN_REC=11, IRR=12, DEP=13, DEP_N=14, ROT=15)
+             MAIN_REC=11, IRR=12, DEP=13, DEP_N=14, ROT=15, BVH_NODES=16, BVH_TRIS=17)
 
 
 class AdgiError(RuntimeError):
@@ -80,8 +80,8 @@ PHASES = ["bvh", "pilot_trace", "pilot_shade", "heuristics", "allocation", "trac
 
 EXPORTED = ["adgi_create_volume", "adgi_set_scene", "adgi_move_vertices", "adgi_update", "adgi_query_irradiance",
             "adgi_get_stats", "adgi_destroy", "adgi_set_stream", "adgi_enable_timing", "adgi_state_bytes",
-            "adgi_read_state", "adgi_write_atlas", "adgi_trace_closest", "adgi_count_traversal", "adgi_allocate_rays",
-            "adgi_last_error"]
+            "adgi_read_state", "adgi_write_atlas", "adgi_trace_closest", "adgi_count_traversal", "adgi_build_bvh",
+            "adgi_allocate_rays", "adgi_last_error"]
 
 _lib = None
 
@@ -110,6 +110,7 @@ def load(path: str = LIB_PATH):
     L.adgi_trace_closest.argtypes = [vp, vp, vp, i32, C.c_float, C.c_float, vp, vp]
     L.adgi_allocate_rays.argtypes = [vp, i32, i32, i32, i32, vp, vp, vp]
     L.adgi_count_traversal.argtypes = [vp, C.POINTER(adgi_frame), C.POINTER(C.c_uint64)]
+    L.adgi_build_bvh.argtypes = [vp, i32, vp, i32, C.c_float, vp, vp, vp]
     L.adgi_last_error.restype = C.c_char_p
     for name in EXPORTED[:-1]:
         getattr(L, name).restype = C.c_int
@@ -210,6 +211,22 @@ def adgi_count_traversal(vol, frame: adgi_frame):
     out = (C.c_uint64 * 8)()
     _check(load().adgi_count_traversal(vol, C.byref(frame), out))
     return [int(x) for x in out]
+
+
+def adgi_build_bvh(verts, idx, eps, nodes_out, tris_out, stream=None):
+    nv = int(verts.shape[0]) if verts.ndim == 2 else int(verts.shape[0] // 3)
+    nt = int(idx.shape[0]) if idx.ndim == 2 else int(idx.shape[0] // 3)
+    _check(load().adgi_build_bvh(_ptr(verts), nv, _ptr(idx), nt, float(eps), _ptr(nodes_out), _ptr(tris_out), stream))
+
+
+def scene_eps(verts):
+    """The box enlargement adgi_set_scene uses for these vertices."""
+    v = np.asarray(verts, np.float64).reshape(-1, 3)
+    if v.size == 0:
+        return float(np.float32(1e-30))
+    ext = float((v.max(0) - v.min(0)).max())
+    mag = float(np.abs(v).max())
+    return float(np.float32(1e-5 * max(ext, mag) + 1e-30))
 
 
 def adgi_allocate_rays(W, rays_avg, rays_min, rays_max, n_out, off_out, stream=None):

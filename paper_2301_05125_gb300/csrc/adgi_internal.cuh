@@ -51,6 +51,7 @@ struct SceneDev {
 constexpr int kErrTraversal = 1;  // a traversal exceeded max_iter
 constexpr int kErrRayRange = 2;   // a probe's ray range exceeded the buffers
 constexpr int kErrBvh = 4;        // the bottom-up box pass exceeded its depth bound
+constexpr int kErrIndex = 8;      // a triangle referenced a vertex outside the array
 
 struct FrameConst {
     uint64_t pilot_key;     // sm(sm(seed) ^ pair)

@@ -27,8 +27,14 @@ __device__ __forceinline__ uint32_t f2ord(float f)
 }
 __device__ __forceinline__ float ord2f(uint32_t u) { return __uint_as_float((u & 0x80000000u) ? (u & 0x7FFFFFFFu) : ~u); }
 
-__global__ void k_tri_prep(const float* __restrict__ verts, const int* __restrict__ idx, int nt,
-                           float4* __restrict__ tri_orig, uint32_t* __restrict__ bounds)
+__global__ void k_init_bounds(uint32_t* __restrict__ bounds)
+{
+    if (threadIdx.x < 3) bounds[threadIdx.x] = 0xFFFFFFFFu;
+    else if (threadIdx.x < 6) bounds[threadIdx.x] = 0u;
+}
+
+__global__ void k_tri_prep(const float* __restrict__ verts, const int* __restrict__ idx, int nt, int nv,
+                           float4* __restrict__ tri_orig, uint32_t* __restrict__ bounds, int* __restrict__ err)
 {
     __shared__ uint32_t s_lo[3], s_hi[3];
     if (threadIdx.x < 3) {
@@ -41,6 +47,10 @@ __global__ void k_tri_prep(const float* __restrict__ verts, const int* __restric
         float c[3] = {0.f, 0.f, 0.f};
         for (int v = 0; v < 3; ++v) {
             int vi = idx[3 * (size_t)t + v];
+            if (vi < 0 || vi >= nv) {  // guarded: an out-of-range index reads vertex 0
+                atomicOr(err, kErrIndex);
+                vi = 0;
+            }
             float x = verts[3 * (size_t)vi], y = verts[3 * (size_t)vi + 1], z = verts[3 * (size_t)vi + 2];
             tri_orig[3 * (size_t)t + v] = make_float4(x, y, z, 0.f);
             c[0] += x;
@@ -274,20 +284,87 @@ __global__ void k_bounds(const float4* __restrict__ tri_v, int n, BNode* nodes, 
 
 size_t Bvh::bytes() const { return bytes_; }
 
+size_t bvh_scratch_bytes(int nt)
+{
+    BvhBufs B;
+    return carve_bvh_scratch(nullptr, nt, B);
+}
+
+// Carve the scratch buffers of a build for nt triangles out of one block
+// (base may be null to only compute the size); every piece 256-byte aligned.
+size_t carve_bvh_scratch(void* base, int nt, BvhBufs& B)
+{
+    const size_t n = (size_t)(nt > 0 ? nt : 1);
+    const size_t nb = (n + kSortTile - 1) / kSortTile;
+    size_t off = 0;
+    auto take = [&](size_t bytes) -> void* {
+        void* p = base ? (void*)((char*)base + off) : nullptr;
+        off += (bytes + 255) & ~(size_t)255;
+        return p;
+    };
+    B.tri_orig = (float4*)take(sizeof(float4) * 3 * n);
+    B.par_int = (int*)take(sizeof(int) * n);
+    B.par_leaf = (int*)take(sizeof(int) * n);
+    B.flags = (int*)take(sizeof(int) * n);
+    B.keys[0] = (uint64_t*)take(sizeof(uint64_t) * n);
+    B.keys[1] = (uint64_t*)take(sizeof(uint64_t) * n);
+    B.vals[0] = (uint32_t*)take(sizeof(uint32_t) * n);
+    B.vals[1] = (uint32_t*)take(sizeof(uint32_t) * n);
+    B.hist = (uint32_t*)take(sizeof(uint32_t) * 256 * nb);
+    B.bounds = (uint32_t*)take(sizeof(uint32_t) * 8);
+    B.err = (int*)take(sizeof(int) * 2);
+    return off;
+}
+
+// The build itself: every buffer comes from B (scratch) or the outputs
+// B.tri_v / B.nodes.  All work is ordered on stream s; nothing is allocated.
+cudaError_t build_lbvh(const BvhBufs& B, const float* d_verts, const int* d_idx, int nv, int nt, float eps, int* err,
+                       cudaStream_t s, int* root_leaf)
+{
+    if (nt <= 0) {
+        *root_leaf = -1;
+        return cudaSuccess;
+    }
+    const int T = 256;
+    k_init_bounds<<<1, 32, 0, s>>>(B.bounds);
+    count_launches(1);
+    k_tri_prep<<<(nt + T - 1) / T, T, 0, s>>>(d_verts, d_idx, nt, nv, B.tri_orig, B.bounds, err);
+    count_launches(1);
+    k_morton<<<(nt + T - 1) / T, T, 0, s>>>(B.tri_orig, nt, B.bounds, B.keys[0], B.vals[0]);
+    count_launches(1);
+    int nb = (nt + kSortTile - 1) / kSortTile;
+    int cur = 0;
+    for (int shift = 0; shift < 64; shift += 8) {
+        k_hist<<<nb, kSortThreads, 0, s>>>(B.keys[cur], nt, shift, B.hist, nb);
+        count_launches(1);
+        k_scan_small<<<1, 1024, 0, s>>>(B.hist, 256 * nb);
+        count_launches(1);
+        k_scatter<<<nb, kSortThreads, 0, s>>>(B.keys[cur], B.vals[cur], B.keys[cur ^ 1], B.vals[cur ^ 1], nt, shift,
+                                               B.hist, nb);
+        count_launches(1);
+        cur ^= 1;
+    }
+    k_tri_order<<<(nt + T - 1) / T, T, 0, s>>>(B.tri_orig, B.vals[cur], nt, B.tri_v);
+    count_launches(1);
+    if (nt == 1) {
+        *root_leaf = 0;
+        return cudaGetLastError();
+    }
+    *root_leaf = -1;
+    cudaError_t e = cudaMemsetAsync(B.flags, 0, sizeof(int) * (size_t)nt, s);
+    if (e != cudaSuccess) return e;
+    k_hierarchy<<<(nt - 1 + T - 1) / T, T, 0, s>>>(B.keys[cur], nt, B.nodes, B.par_int, B.par_leaf);
+    count_launches(1);
+    k_bounds<<<(nt + T - 1) / T, T, 0, s>>>(B.tri_v, nt, B.nodes, B.par_int, B.par_leaf, B.flags, eps, err);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
 void Bvh::release()
 {
-    cudaFree(tri_orig);
+    cudaFree(scratch);
     cudaFree(tri_v);
     cudaFree(nodes);
-    cudaFree(par_int);
-    cudaFree(par_leaf);
-    cudaFree(flags);
-    cudaFree(keys[0]);
-    cudaFree(keys[1]);
-    cudaFree(vals[0]);
-    cudaFree(vals[1]);
-    cudaFree(hist);
-    cudaFree(bounds);
     *this = Bvh();
 }
 
@@ -296,31 +373,19 @@ cudaError_t Bvh::reserve(int nt)
     if (nt <= cap_) return cudaSuccess;
     release();
     int n = nt > 0 ? nt : 1;
-    int nb = (n + kSortTile - 1) / kSortTile;
-    size_t b = 0;
-    cudaError_t e;
-#define ALLOC(ptr, count)                                                              \
-    do {                                                                               \
-        size_t sz = sizeof(*(ptr)) * (size_t)(count);                                  \
-        e = cudaMalloc((void**)&(ptr), sz);                                            \
-        if (e != cudaSuccess) return e;                                                \
-        b += sz;                                                                       \
-    } while (0)
-    ALLOC(tri_orig, 3 * (size_t)n);
-    ALLOC(tri_v, 3 * (size_t)n);
-    ALLOC(nodes, n);
-    ALLOC(par_int, n);
-    ALLOC(par_leaf, n);
-    ALLOC(flags, n);
-    ALLOC(keys[0], n);
-    ALLOC(keys[1], n);
-    ALLOC(vals[0], n);
-    ALLOC(vals[1], n);
-    ALLOC(hist, 256 * (size_t)nb);
-    ALLOC(bounds, 6);
-#undef ALLOC
+    size_t sb = bvh_scratch_bytes(n);
+    cudaError_t e = cudaMalloc(&scratch, sb);
+    if (e != cudaSuccess) return e;
+    e = cudaMalloc((void**)&tri_v, sizeof(float4) * 3 * (size_t)n);
+    if (e != cudaSuccess) return e;
+    e = cudaMalloc((void**)&nodes, sizeof(BNode) * (size_t)n);
+    if (e != cudaSuccess) return e;
+    carve_bvh_scratch(scratch, n, bufs);
+    bufs.tri_v = tri_v;
+    bufs.nodes = nodes;
+    tri_orig = bufs.tri_orig;
     cap_ = n;
-    bytes_ = b;
+    bytes_ = sb + sizeof(float4) * 3 * (size_t)n + sizeof(BNode) * (size_t)n;
     return cudaSuccess;
 }
 
@@ -328,45 +393,12 @@ cudaError_t Bvh::reserve(int nt)
 // and the largest coordinate magnitude).
 cudaError_t Bvh::build(const float* d_verts, const int* d_idx, int nv, int nt, float eps, int* err, cudaStream_t s)
 {
-    (void)nv;
     n_tris = 0;
     if (nt == 0) return cudaSuccess;
     cudaError_t e = reserve(nt);  // may reset every member
     if (e != cudaSuccess) return e;
     n_tris = nt;
-    const int T = 256;
-    uint32_t init[6] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0u, 0u, 0u};
-    e = cudaMemcpyAsync(bounds, init, sizeof(init), cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) return e;
-    k_tri_prep<<<(nt + T - 1) / T, T, 0, s>>>(d_verts, d_idx, nt, tri_orig, bounds);
-    count_launches(1);
-    k_morton<<<(nt + T - 1) / T, T, 0, s>>>(tri_orig, nt, bounds, keys[0], vals[0]);
-    count_launches(1);
-    int nb = (nt + kSortTile - 1) / kSortTile;
-    int cur = 0;
-    for (int shift = 0; shift < 64; shift += 8) {
-        k_hist<<<nb, kSortThreads, 0, s>>>(keys[cur], nt, shift, hist, nb);
-        count_launches(1);
-        k_scan_small<<<1, 1024, 0, s>>>(hist, 256 * nb);
-        count_launches(1);
-        k_scatter<<<nb, kSortThreads, 0, s>>>(keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], nt, shift, hist, nb);
-        count_launches(1);
-        cur ^= 1;
-    }
-    k_tri_order<<<(nt + T - 1) / T, T, 0, s>>>(tri_orig, vals[cur], nt, tri_v);
-    count_launches(1);
-    if (nt == 1) {
-        root_leaf = 0;
-        return cudaGetLastError();
-    }
-    root_leaf = -1;
-    e = cudaMemsetAsync(flags, 0, sizeof(int) * (size_t)nt, s);
-    if (e != cudaSuccess) return e;
-    k_hierarchy<<<(nt - 1 + T - 1) / T, T, 0, s>>>(keys[cur], nt, nodes, par_int, par_leaf);
-    count_launches(1);
-    k_bounds<<<(nt + T - 1) / T, T, 0, s>>>(tri_v, nt, nodes, par_int, par_leaf, flags, eps, err);
-    count_launches(1);
-    return cudaGetLastError();
+    return build_lbvh(bufs, d_verts, d_idx, nv, nt, eps, err, s, &root_leaf);
 }
 
 SceneDev Bvh::view(const float* albedo, int nv, int* err) const

@@ -586,6 +586,8 @@ int adgi_state_bytes(adgi_volume v, int32_t which, uint64_t* bytes)
     case ADGI_STATE_DEP: *bytes = P * td2 * (v->V.fp16 ? 4 : 8); break;
     case ADGI_STATE_DEP_N: *bytes = P * td2; break;
     case ADGI_STATE_ROT: *bytes = 36; break;
+    case ADGI_STATE_BVH_NODES: *bytes = 64 * (uint64_t)(v->nt > 1 ? v->nt - 1 : 1); break;
+    case ADGI_STATE_BVH_TRIS: *bytes = 48 * (uint64_t)v->nt; break;
     default: return fail(ADGI_ERR_INVALID_ARG, "unknown state");
     }
     return ADGI_OK;
@@ -619,6 +621,14 @@ int adgi_read_state(adgi_volume v, int32_t which, void* dst, uint64_t bytes)
     case ADGI_STATE_IRR: src = v->irr; break;
     case ADGI_STATE_DEP: src = v->dep; break;
     case ADGI_STATE_DEP_N: src = v->dep_n; break;
+    case ADGI_STATE_BVH_NODES: src = v->bvh.nodes; break;
+    case ADGI_STATE_BVH_TRIS: src = v->bvh.tri_v; break;
+    }
+    if ((which == ADGI_STATE_BVH_NODES && v->nt < 2) || (which == ADGI_STATE_BVH_TRIS && v->nt == 0) ||
+        (which == ADGI_STATE_BVH_NODES && v->bvh_dirty)) {
+        std::memset(dst, 0, bytes);
+        if (!(which == ADGI_STATE_BVH_NODES && v->bvh_dirty)) return ADGI_OK;
+        return fail(ADGI_ERR_INVALID_ARG, "BVH is rebuilt at the next update");
     }
     if (bytes) CK(cudaMemcpy(dst, src, bytes, cudaMemcpyDeviceToHost));
     return ADGI_OK;
@@ -691,6 +701,35 @@ int adgi_count_traversal(adgi_volume v, const adgi_frame* f, uint64_t* counts)
     cudaFree(d);
     if (e != cudaSuccess) return fail(ADGI_ERR_CUDA, std::string("count: ") + cudaGetErrorString(e));
     for (int i = 0; i < 8; ++i) counts[i] = h[i];
+    return ADGI_OK;
+}
+
+int adgi_build_bvh(const float* verts, int32_t nv, const int32_t* idx, int32_t nt, float eps, void* nodes_out,
+                   void* tris_out, void* cuda_stream)
+{
+    if (nv < 0 || nt < 0 || (nt > 0 && (nv <= 0 || !verts || !idx || !nodes_out || !tris_out)) || !(eps >= 0.0f))
+        return fail(ADGI_ERR_INVALID_ARG, "bad arguments");
+    if (nt == 0) return ADGI_OK;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    BvhBufs B;
+    size_t sb = carve_bvh_scratch(nullptr, nt, B);
+    void* scratch = nullptr;
+    cudaError_t e = cudaMallocAsync(&scratch, sb, s);
+    if (e != cudaSuccess) return fail(ADGI_ERR_OOM, std::string("scratch: ") + cudaGetErrorString(e));
+    carve_bvh_scratch(scratch, nt, B);
+    B.tri_v = (float4*)tris_out;
+    B.nodes = (BNode*)nodes_out;
+    int root = -1;
+    e = cudaMemsetAsync(B.err, 0, sizeof(int), s);
+    if (e == cudaSuccess) e = build_lbvh(B, verts, idx, nv, nt, eps, B.err, s, &root);
+    int herr = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, B.err, sizeof(int), cudaMemcpyDeviceToHost, s);
+    cudaError_t e2 = cudaFreeAsync(scratch, s);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail(ADGI_ERR_CUDA, std::string("build: ") + cudaGetErrorString(e));
+    if (herr & kErrIndex) return fail(ADGI_ERR_INVALID_ARG, "triangle index outside [0, n_verts)");
+    if (herr) return fail(ADGI_ERR_CUDA, "device anomaly flags set: " + std::to_string(herr));
     return ADGI_OK;
 }
 

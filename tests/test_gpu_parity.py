@@ -261,3 +261,48 @@ def test_tunnel_city_full_size_two_frames(adgi):
         ov.update(f, w.seed, w.lights_at(f), w.sky)
         _compare_update(gv, ov, f, what="tunnel")
     gv.close()
+
+
+# ------------------------------------------------------------------ stand-alone BVH build
+@pytest.mark.parametrize("scene", ["room", "city", "one", "two"])
+def test_build_bvh_matches_volume_bvh(adgi, scene):
+    if scene == "room":
+        w = S.box_room(1)
+    elif scene == "city":
+        w = S.small_city(6, n_boxes=1500)
+    else:
+        nt = 1 if scene == "one" else 2
+        v = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1]], np.float32)
+        w = S.Workload(scene, 0, v, np.array([[0, 1, 2], [1, 2, 3]], np.int32)[:nt], np.ones((nt, 3), np.float32),
+                       S.box_room(1).volume, 1, (0, 0, 0), lambda f: [])
+    gv = gpu_volume(adgi, w)
+    dev = torch.device("cuda")
+    nt = w.n_tris
+    V = torch.from_numpy(w.verts).to(dev)
+    I = torch.from_numpy(w.idx).to(dev)
+    nodes = torch.zeros(max(nt - 1, 1) * 16, dtype=torch.int32, device=dev)
+    tris = torch.zeros(nt * 12, dtype=torch.float32, device=dev)
+    adgi.adgi_build_bvh(V, I, adgi.scene_eps(w.verts), nodes, tris, torch.cuda.current_stream().cuda_stream)
+    ref_nodes = gv.state("BVH_NODES", np.int32)
+    ref_tris = gv.state("BVH_TRIS", np.int32)
+    if nt > 1:
+        np.testing.assert_array_equal(nodes.cpu().numpy(), ref_nodes)
+    np.testing.assert_array_equal(tris.cpu().numpy().view(np.int32), ref_tris)
+    # triangles in BVH order are a permutation of the input, tagged with their index
+    t = tris.cpu().numpy().reshape(nt, 3, 4)
+    orig = t[:, 0, 3].view(np.int32)
+    assert sorted(orig.tolist()) == list(range(nt))
+    np.testing.assert_array_equal(t[:, :, :3], w.verts[w.idx[orig]])
+    gv.close()
+
+
+def test_build_bvh_rejects_bad_index(adgi):
+    dev = torch.device("cuda")
+    w = S.box_room(1)
+    idx = w.idx.copy()
+    idx[5, 1] = len(w.verts) + 3
+    nodes = torch.zeros((w.n_tris - 1) * 16, dtype=torch.int32, device=dev)
+    tris = torch.zeros(w.n_tris * 12, dtype=torch.float32, device=dev)
+    with pytest.raises(adgi.AdgiError) as e:
+        adgi.adgi_build_bvh(torch.from_numpy(w.verts).to(dev), torch.from_numpy(idx).to(dev), 1e-4, nodes, tris)
+    assert e.value.code == -1 and "index" in str(e.value)
