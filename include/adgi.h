@@ -256,6 +256,27 @@ int adgi_count_traversal(adgi_volume vol, const adgi_frame* frame, uint64_t* cou
 int adgi_build_bvh(const float* verts, int32_t n_verts, const int32_t* tri_idx, int32_t n_tris, float eps,
                    void* nodes_out, void* tris_out, void* cuda_stream);
 
+/* adgi_build_bvh without any allocation.  The paper has no counterpart: this
+ * is a service for callers that may not allocate device memory while they
+ * run -- a frame loop that must not stall on cudaMalloc/cudaFree (both can
+ * synchronise the device), or a plugin whose host application's allocator
+ * already holds all the device memory it may use.  Same arguments, outputs
+ * and errors as adgi_build_bvh, with these differences:
+ *   - n_tris must be <= ADGI_BVH_NOALLOC_MAX_TRIS; larger builds are rejected
+ *     with ADGI_ERR_INVALID_ARG and a message naming the limit;
+ *   - the scratch is one fixed device array inside the library (about
+ *     2.6 MiB), held on every GPU that loads the library until exit; the call
+ *     performs no cudaMalloc, cudaFree or other allocating routine;
+ *   - the first call on a device looks up that array's device address (set-up,
+ *     once per device); make it before any stream capture begins;
+ *   - every call shares the array, which keeps the last call's contents (each
+ *     call clears what must start at zero); calls whose GPU work overlaps
+ *     (other streams, other host threads) race on it: order them on one
+ *     stream or serialise them. */
+#define ADGI_BVH_NOALLOC_MAX_TRIS 32768
+int adgi_build_bvh_noalloc(const float* verts, int32_t n_verts, const int32_t* tri_idx, int32_t n_tris, float eps,
+                           void* nodes_out, void* tris_out, void* cuda_stream);
+
 /* Ray allocation of step 3 as a stand-alone call on device arrays:
  * W (uint32[P]) -> n_out (uint32[P], pilots included, sum = rays_avg * P),
  * off_out (uint32[P+1], exclusive prefix of n_p - 8).  Enqueued on

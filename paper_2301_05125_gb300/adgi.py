@@ -81,7 +81,9 @@ PHASES = ["bvh", "pilot_trace", "pilot_shade", "heuristics", "allocation", "trac
 EXPORTED = ["adgi_create_volume", "adgi_set_scene", "adgi_move_vertices", "adgi_update", "adgi_query_irradiance",
             "adgi_get_stats", "adgi_destroy", "adgi_set_stream", "adgi_enable_timing", "adgi_state_bytes",
             "adgi_read_state", "adgi_write_atlas", "adgi_trace_closest", "adgi_count_traversal", "adgi_build_bvh",
-            "adgi_allocate_rays", "adgi_last_error"]
+            "adgi_build_bvh_noalloc", "adgi_allocate_rays", "adgi_last_error"]
+
+BVH_NOALLOC_MAX_TRIS = 32768
 
 _lib = None
 
@@ -111,6 +113,7 @@ def load(path: str = LIB_PATH):
     L.adgi_allocate_rays.argtypes = [vp, i32, i32, i32, i32, vp, vp, vp]
     L.adgi_count_traversal.argtypes = [vp, C.POINTER(adgi_frame), C.POINTER(C.c_uint64)]
     L.adgi_build_bvh.argtypes = [vp, i32, vp, i32, C.c_float, vp, vp, vp]
+    L.adgi_build_bvh_noalloc.argtypes = [vp, i32, vp, i32, C.c_float, vp, vp, vp]
     L.adgi_last_error.restype = C.c_char_p
     for name in EXPORTED[:-1]:
         getattr(L, name).restype = C.c_int
@@ -217,6 +220,16 @@ def adgi_build_bvh(verts, idx, eps, nodes_out, tris_out, stream=None):
     nv = int(verts.shape[0]) if verts.ndim == 2 else int(verts.shape[0] // 3)
     nt = int(idx.shape[0]) if idx.ndim == 2 else int(idx.shape[0] // 3)
     _check(load().adgi_build_bvh(_ptr(verts), nv, _ptr(idx), nt, float(eps), _ptr(nodes_out), _ptr(tris_out), stream))
+
+
+def adgi_build_bvh_noalloc(verts, idx, eps, nodes_out, tris_out, stream=None, n_tris=None):
+    """adgi_build_bvh with its scratch in the library's fixed device array
+    (no allocation; at most BVH_NOALLOC_MAX_TRIS triangles; calls must not
+    overlap on the GPU)."""
+    nv = int(verts.shape[0]) if verts.ndim == 2 else int(verts.shape[0] // 3)
+    nt = n_tris if n_tris is not None else (int(idx.shape[0]) if idx.ndim == 2 else int(idx.shape[0] // 3))
+    _check(load().adgi_build_bvh_noalloc(_ptr(verts), nv, _ptr(idx), nt, float(eps), _ptr(nodes_out),
+                                         _ptr(tris_out), stream))
 
 
 def scene_eps(verts):

@@ -26,6 +26,7 @@ namespace adgi {
 size_t blend_smem_bytes(const VolConst& V);
 
 static std::atomic<unsigned long long> g_launches{0};
+const char* noalloc_fail(const std::string& msg);
 void count_launches(unsigned n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 unsigned long long kernels_launched() { return g_launches.load(std::memory_order_relaxed); }
 }
@@ -103,6 +104,13 @@ cudaError_t dalloc(T** p, size_t count, size_t* total)
 }
 
 }  // namespace
+
+// error reporting for the allocation-free entry point (noalloc.cu)
+const char* adgi::noalloc_fail(const std::string& msg)
+{
+    g_err = msg;
+    return g_err.c_str();
+}
 
 struct adgi_volume_s {
     int device = 0;
