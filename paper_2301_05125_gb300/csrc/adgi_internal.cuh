@@ -485,32 +485,91 @@ __device__ __forceinline__ void depth_moments(const VolConst& V, const void* dep
     *cond = s2 / var;
 }
 
-// The same lookup with the direction and the four bilinear weights in FP64
-// (for footprints where FP32 fractions would perturb the variance).
-static __device__ __noinline__ void depth_moments_fp64(const VolConst& V, const void* dep, size_t tile, double dx, double dy,
-                                                double dz, float* mom)
+// ---------------------------------------------------------------- double-float
+// Unevaluated sums hi + lo of two floats (Dekker / Knuth error-free
+// transformations), for the few quantities that need ~2^-44 relative precision.
+struct df {
+    float h, l;
+};
+__device__ __forceinline__ df two_sum(float a, float b)
 {
-    double l1 = fabs(dx) + fabs(dy) + fabs(dz);
-    double px = dx / l1, py = dy / l1;
-    if (dz < 0.0) {
-        double qx = (1.0 - fabs(py)) * (px >= 0.0 ? 1.0 : -1.0);
-        double qy = (1.0 - fabs(px)) * (py >= 0.0 ? 1.0 : -1.0);
-        px = qx;
-        py = qy;
+    float s = fa(a, b);
+    float bb = fs(s, a);
+    return {s, fa(fs(a, fs(s, bb)), fs(b, bb))};
+}
+__device__ __forceinline__ df fast_two_sum(float a, float b)
+{
+    float s = fa(a, b);
+    return {s, fs(b, fs(s, a))};
+}
+__device__ __forceinline__ df two_prod(float a, float b)
+{
+    float p = fm(a, b);
+    return {p, __fmaf_rn(a, b, -p)};
+}
+__device__ __forceinline__ df df_add(df a, df b)
+{
+    df s = two_sum(a.h, b.h);
+    return fast_two_sum(s.h, fa(s.l, fa(a.l, b.l)));
+}
+__device__ __forceinline__ df df_neg(df a) { return {-a.h, -a.l}; }
+__device__ __forceinline__ df df_abs(df a) { return a.h < 0.0f ? df_neg(a) : a; }
+__device__ __forceinline__ df df_mul_f(df a, float b)
+{
+    df p = two_prod(a.h, b);
+    return fast_two_sum(p.h, __fmaf_rn(a.l, b, p.l));
+}
+__device__ __forceinline__ df df_div(df a, df b)
+{
+    float q1 = fd(a.h, b.h);
+    df r = df_add(a, df_neg(df_mul_f(b, q1)));
+    float q2 = fd(r.h, b.h);
+    return fast_two_sum(q1, q2);
+}
+// (o - p) + t*d as a double-float: exact inputs, error ~2^-44 relative
+__device__ __forceinline__ df df_offset(float o, float p, float t, float d)
+{
+    return df_add(two_sum(o, -p), two_prod(t, d));
+}
+
+// The depth lookup with the direction and the bilinear fractions in
+// double-float (for footprints where FP32 fractions would perturb the filtered
+// variance): the offset is rebuilt exactly from (o, p, t, d).
+static __device__ __noinline__ void depth_moments_precise(const VolConst& V, const void* dep, size_t tile,
+                                                          const float* o, const float* p, float t, const float* d,
+                                                          float* mom)
+{
+    df dx = df_offset(o[0], p[0], t, d[0]);
+    df dy = df_offset(o[1], p[1], t, d[1]);
+    df dz = df_offset(o[2], p[2], t, d[2]);
+    df l1 = df_add(df_add(df_abs(dx), df_abs(dy)), df_abs(dz));
+    df px = df_div(dx, l1), py = df_div(dy, l1);
+    if (dz.h < 0.0f) {
+        const df one = {1.0f, 0.0f};
+        df qx = df_add(one, df_neg(df_abs(py)));
+        df qy = df_add(one, df_neg(df_abs(px)));
+        px = px.h >= 0.0f ? qx : df_neg(qx);
+        py = py.h >= 0.0f ? qy : df_neg(qy);
     }
     const int n = V.n_dep, T = V.Td;
-    double fx = (1.0 + (px + 1.0) * 0.5 * (double)n) - 0.5;
-    double fy = (1.0 + (py + 1.0) * 0.5 * (double)n) - 0.5;
-    int x0 = min(max((int)floor(fx), 0), n);
-    int y0 = min(max((int)floor(fy), 0), n);
-    double ax = fmin(fmax(fx - (double)x0, 0.0), 1.0);
-    double ay = fmin(fmax(fy - (double)y0, 0.0), 1.0);
+    const float hn = 0.5f * (float)n;
+    df fx = df_add(df_mul_f(px, hn), {hn + 0.5f, 0.0f});
+    df fy = df_add(df_mul_f(py, hn), {hn + 0.5f, 0.0f});
+    float x0f = floorf(fx.h), y0f = floorf(fy.h);
+    if (fx.h == x0f && fx.l < 0.0f) x0f -= 1.0f;
+    if (fy.h == y0f && fy.l < 0.0f) y0f -= 1.0f;
+    int x0 = min(max((int)x0f, 0), n);
+    int y0 = min(max((int)y0f, 0), n);
+    float ax = fminf(fmaxf(fa(fs(fx.h, (float)x0), fx.l), 0.0f), 1.0f);
+    float ay = fminf(fmaxf(fa(fs(fy.h, (float)y0), fy.l), 0.0f), 1.0f);
+    float bx = fminf(fmaxf(fs(fs((float)(x0 + 1), fx.h), fx.l), 0.0f), 1.0f);
+    float by = fminf(fmaxf(fs(fs((float)(y0 + 1), fy.h), fy.l), 0.0f), 1.0f);
     size_t i00 = tile + (size_t)(y0 * T + x0);
     float2 v00 = dep_load(dep, i00, V.fp16), v01 = dep_load(dep, i00 + 1, V.fp16);
     float2 v10 = dep_load(dep, i00 + T, V.fp16), v11 = dep_load(dep, i00 + T + 1, V.fp16);
-    double w00 = (1.0 - ax) * (1.0 - ay), w01 = ax * (1.0 - ay), w10 = (1.0 - ax) * ay, w11 = ax * ay;
-    mom[0] = (float)(w00 * v00.x + w01 * v01.x + w10 * v10.x + w11 * v11.x);
-    mom[1] = (float)(w00 * v00.y + w01 * v01.y + w10 * v10.y + w11 * v11.y);
+    float w00 = bx * by, w01 = ax * by, w10 = bx * ay, w11 = ax * ay;
+    mom[0] = w00 * v00.x + w01 * v01.x + w10 * v10.x + w11 * v11.x;
+    mom[1] = w00 * v00.y + w01 * v01.y + w10 * v10.y + w11 * v11.y;
 }
 
 // 8-probe trilinear x Chebyshev irradiance query at x = o + t*d (the public
@@ -561,10 +620,8 @@ __device__ __forceinline__ float3 query_irr_at(const VolConst& V, const void* ir
             float cond;
             depth_moments(V, dep, (size_t)p * td2, dx, dy, dz, mom, &cond);
             if (cond > 128.0f) {  // FP32 fractions would move the variance by > ~6e-5
-                double ddx = ((double)os[0] - (double)px) + (double)t * (double)ds[0];
-                double ddy = ((double)os[1] - (double)py) + (double)t * (double)ds[1];
-                double ddz = ((double)os[2] - (double)pz) + (double)t * (double)ds[2];
-                depth_moments_fp64(V, dep, (size_t)p * td2, ddx, ddy, ddz, mom);
+                const float pc[3] = {px, py, pz};
+                depth_moments_precise(V, dep, (size_t)p * td2, os, pc, t, ds, mom);
             }
         }
         float wc = 1.f;

@@ -20,6 +20,7 @@
 #include "bvh.cuh"
 #include "kernels.cuh"
 
+#include <algorithm>
 #include <atomic>
 
 namespace adgi {
@@ -142,6 +143,13 @@ struct adgi_volume_s {
     float4* m_rec = nullptr;
     unsigned long long* shadow_ctr = nullptr;
     int* err = nullptr;  // device anomaly flags
+    // shading wavefront
+    unsigned long long* vis = nullptr;
+    uint4* jobs = nullptr;
+    uint8_t* job_light = nullptr;
+    unsigned* job_count = nullptr;
+    size_t job_cap = 0;
+    unsigned shadow_blocks = 0;
     // scene
     float* verts = nullptr;
     int* idx = nullptr;
@@ -171,7 +179,8 @@ void free_volume(adgi_volume v)
     void* ptrs[] = {v->sf,      v->lut_v,   v->lut_c,  v->irr,   v->dep,     v->dep_n,   v->qv,     v->qr,
                     v->qv_even, v->qr_even, v->amp_v,  v->amp_r, v->trv,     v->trr,     v->age_v,  v->age_r,
                     v->G,       v->W,       v->n,      v->off,   v->pil_hit, v->pil_rec, v->pil_lum, v->m_hit,
-                    v->m_rec,   v->shadow_ctr, v->verts, v->idx, v->albedo,  v->q_buf, v->err};
+                    v->m_rec,   v->shadow_ctr, v->verts, v->idx, v->albedo,  v->q_buf, v->err,
+                    v->vis,     v->jobs,    v->job_light, v->job_count};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     v->bvh.release();
@@ -318,6 +327,8 @@ int adgi_create_volume(const adgi_volume_desc* desc, void* cuda_stream, adgi_vol
     DA(v->m_rec, (size_t)v->R_main);
     DA(v->shadow_ctr, 1);
     DA(v->err, 1);
+    DA(v->vis, std::max<size_t>(P * 8, (size_t)v->R_main));
+    DA(v->job_count, 1);
 #undef DA
     V.R_main = v->R_main;
     V.err = v->err;
@@ -343,6 +354,7 @@ int adgi_create_volume(const adgi_volume_desc* desc, void* cuda_stream, adgi_vol
     CKV(cudaMemsetAsync(v->W, 0, P * 4, s));
     CKV(cudaMemsetAsync(v->shadow_ctr, 0, 8, s));
     CKV(cudaMemsetAsync(v->err, 0, 4, s));
+    v->shadow_blocks = shadow_grid_blocks();
     CKV(cudaEventCreate(&v->ev0));
     CKV(cudaEventCreate(&v->ev1));
     for (cudaEvent_t& e : v->ph) CKV(cudaEventCreate(&e));
@@ -485,11 +497,29 @@ int adgi_update(adgi_volume v, const adgi_frame* f)
     }
     SceneDev S = v->bvh.view(v->albedo, v->nv, v->err);
     CK(cudaMemsetAsync(v->shadow_ctr, 0, 8, s));
+    // shadow-job capacity: one job per lit light of every ray of the larger set
+    {
+        size_t need = (size_t)f->n_lights * std::max<size_t>((size_t)V.P * kPilots, (size_t)v->R_main);
+        if (need > v->job_cap) {
+            cudaFree(v->jobs);
+            cudaFree(v->job_light);
+            v->jobs = nullptr;
+            v->job_light = nullptr;
+            v->job_cap = 0;
+            size_t dummy = 0;
+            if (dalloc(&v->jobs, need, &dummy) != cudaSuccess || dalloc(&v->job_light, need, &dummy) != cudaSuccess)
+                return fail(ADGI_ERR_OOM, "shadow job buffer");
+            v->job_cap = need;
+        }
+    }
+    ShadeWork W{v->vis, v->jobs, v->job_light, v->job_count, (unsigned)std::min<size_t>(v->job_cap, 0xFFFFFFFFu),
+                v->shadow_blocks, v->shadow_ctr};
     // 1. pilot rays (trace + shade; the shading reads the previous atlases)
     PHASE(1);
     CK(launch_pilot_trace(V, F, S, v->pil_hit, s));
     PHASE(2);
-    CK(launch_pilot_shade(V, F, L, S, v->irr, v->dep, v->pil_hit, v->pil_rec, v->pil_lum, v->shadow_ctr, s));
+    CK(launch_shade(V, F, L, S, 0, (uint32_t)V.P * kPilots, nullptr, nullptr, v->irr, v->dep, v->pil_hit, v->pil_rec,
+                    v->pil_lum, F.even, W, s));
     // 2. heuristics -> W_p
     PHASE(3);
     ChangeBufs C{v->pil_hit, v->pil_lum, v->lut_v, v->lut_c, v->qv,  v->qr,  v->qv_even, v->qr_even,
@@ -502,7 +532,7 @@ int adgi_update(adgi_volume v, const adgi_frame* f)
     PHASE(5);
     CK(launch_main_trace(V, F, S, v->off, v->sf, v->R_main, v->m_hit, s));
     PHASE(6);
-    CK(launch_main_shade(V, F, L, S, v->irr, v->dep, v->off, v->sf, v->R_main, v->m_hit, v->m_rec, v->shadow_ctr, s));
+    CK(launch_shade(V, F, L, S, 1, v->R_main, v->off, v->sf, v->irr, v->dep, v->m_hit, v->m_rec, nullptr, 1, W, s));
     // 6. blend (after every read of the previous atlases)
     PHASE(7);
     BlendBufs Bb{v->off, v->sf, v->pil_rec, v->m_rec, v->irr, v->dep, v->dep_n};

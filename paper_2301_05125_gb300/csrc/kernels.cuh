@@ -34,6 +34,17 @@ struct ChangeBufs {
     uint32_t* W;
 };
 
+// work buffers of the shading wavefront (shade.cu)
+struct ShadeWork {
+    unsigned long long* vis;  // per ray: bit l = light l visible
+    uint4* jobs;              // shadow jobs {origin xyz, ray}
+    uint8_t* job_light;       // light of each job
+    unsigned* job_count;
+    unsigned job_cap;
+    unsigned shadow_blocks;   // persistent grid of the shadow kernel
+    unsigned long long* shadow_ctr;
+};
+
 struct BlendBufs {
     const uint32_t* off;
     const float4* sf;
@@ -47,12 +58,10 @@ struct BlendBufs {
 cudaError_t launch_pilot_trace(const VolConst& V, const FrameConst& F, const SceneDev& S, int2* hit, cudaStream_t s);
 cudaError_t launch_main_trace(const VolConst& V, const FrameConst& F, const SceneDev& S, const uint32_t* off,
                               const float4* sf, uint32_t R, int2* hit, cudaStream_t s);
-cudaError_t launch_pilot_shade(const VolConst& V, const FrameConst& F, const LightSet& L, const SceneDev& S,
-                               const void* irr, const void* dep, const int2* hit, float4* rec, float* lum,
-                               unsigned long long* counter, cudaStream_t s);
-cudaError_t launch_main_shade(const VolConst& V, const FrameConst& F, const LightSet& L, const SceneDev& S,
-                              const void* irr, const void* dep, const uint32_t* off, const float4* sf, uint32_t R,
-                              const int2* hit, float4* rec, unsigned long long* counter, cudaStream_t s);
+cudaError_t launch_shade(const VolConst& V, const FrameConst& F, const LightSet& L, const SceneDev& S, int mode,
+                         uint32_t n_rays, const uint32_t* off, const float4* sf, const void* irr, const void* dep,
+                         const int2* hit, float4* rec, float* lum, int bounce, const ShadeWork& W, cudaStream_t s);
+unsigned shadow_grid_blocks();
 cudaError_t launch_count(const VolConst& V, const FrameConst& F, const LightSet& L, const SceneDev& S,
                          const uint32_t* off, const float4* sf, uint32_t R, unsigned long long* out, cudaStream_t s);
 cudaError_t launch_trace_list(const SceneDev& S, const float* o, const float* d, int n, float tmin, float tmax,

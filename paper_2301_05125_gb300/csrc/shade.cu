@@ -1,0 +1,260 @@
+// shade.cu -- shading of probe rays as a three-kernel wavefront (sm_103a).
+//
+//   prep:    per ray, for a front-face hit: exact FP32 normal, hit point and
+//            biased shadow origin; every light passing the exact lit test
+//            appends one shadow job {origin, ray, light} (warp-aggregated);
+//   shadow:  a persistent grid walks the compacted jobs, one any-hit
+//            traversal per job, and sets the light's bit in the ray's
+//            visibility mask when nothing blocks it;
+//   finish:  per ray, direct light of the visible lights (exact FP32, light
+//            order fixed), the multi-bounce term albedo * Q_{t-1}(x, n) and the
+//            ray record {rgb, depth}.
+// Splitting the shadow rays out keeps SIMT lanes busy: a thread no longer
+// loops over lights while its neighbours missed the scene or faced away.
+#include "adgi_internal.cuh"
+#include "kernels.cuh"
+
+namespace adgi {
+
+namespace {
+
+constexpr float kInvPi = 0.31830987f;
+constexpr float kLumR = 0.2126f, kLumG = 0.7152f, kLumB = 0.0722f;
+
+__device__ __forceinline__ int probe_of_ray(const uint32_t* __restrict__ off, uint32_t r, int lo, int hi)
+{
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (__ldg(off + mid) <= r)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+// The rays of a block: pilot rays (ray r = probe r/8, octant r%8) or adaptive
+// rays (ray r of the prefix offsets off[]).  The block's probe range is found
+// once by two threads.
+struct RaySet {
+    int mode;                 // 0 pilot, 1 adaptive
+    uint32_t n;               // rays in the set
+    const uint32_t* off;      // adaptive: prefix offsets
+    const float4* sf;         // adaptive: spherical Fibonacci sets
+};
+
+__device__ __forceinline__ void block_range(const VolConst& V, const RaySet& Rs, int* s_lo, int* s_hi)
+{
+    if (Rs.mode == 1) {
+        uint32_t r0 = blockIdx.x * blockDim.x;
+        uint32_t r1 = min(Rs.n - 1, r0 + blockDim.x - 1);
+        if (threadIdx.x == 0) *s_lo = probe_of_ray(Rs.off, r0, 0, V.P - 1);
+        if (threadIdx.x == 32 % blockDim.x) *s_hi = probe_of_ray(Rs.off, r1, 0, V.P - 1);
+    }
+    __syncthreads();
+}
+
+// origin and direction of ray r; false if the ray range is inconsistent
+__device__ __forceinline__ bool ray_of(const VolConst& V, const FrameConst& F, const RaySet& Rs, uint32_t r, int lo,
+                                       int hi, float3& o, float3& d)
+{
+    if (Rs.mode == 0) {
+        int p = (int)(r >> 3);
+        o = probe_pos(V, p);
+        d = pilot_dir(F.pilot_key, (uint32_t)p, (int)(r & 7));
+        return true;
+    }
+    int p = probe_of_ray(Rs.off, r, lo, hi);
+    uint32_t base = __ldg(Rs.off + p), m = __ldg(Rs.off + p + 1) - base;
+    if (m > (uint32_t)(V.rays_max - kPilots) || r - base >= m) return false;
+    o = probe_pos(V, p);
+    float4 s = __ldg(Rs.sf + (size_t)m * (m - 1) / 2 + (r - base));
+    d = rotate(F.R, s);
+    return true;
+}
+
+// exact FP32 geometric normal of triangle tri (original order)
+__device__ __forceinline__ float3 tri_normal(const SceneDev& S, int tri)
+{
+    float4 A = __ldg(S.tri_orig + 3 * (size_t)tri), B = __ldg(S.tri_orig + 3 * (size_t)tri + 1),
+           C = __ldg(S.tri_orig + 3 * (size_t)tri + 2);
+    float e1x = fs(B.x, A.x), e1y = fs(B.y, A.y), e1z = fs(B.z, A.z);
+    float e2x = fs(C.x, A.x), e2y = fs(C.y, A.y), e2z = fs(C.z, A.z);
+    float cx = fs(fm(e1y, e2z), fm(e1z, e2y));
+    float cy = fs(fm(e1z, e2x), fm(e1x, e2z));
+    float cz = fs(fm(e1x, e2y), fm(e1y, e2x));
+    float cl = fsq(dot3x(cx, cy, cz, cx, cy, cz));
+    return cl > 0.0f ? make_float3(fd(cx, cl), fd(cy, cl), fd(cz, cl)) : make_float3(0.f, 0.f, 1.f);
+}
+
+__device__ __forceinline__ float3 shadow_dir(const Light& Li, float3 xs)
+{
+    return Li.kind == 0 ? make_float3(fs(Li.v[0], xs.x), fs(Li.v[1], xs.y), fs(Li.v[2], xs.z))
+                        : make_float3(-Li.v[0], -Li.v[1], -Li.v[2]);
+}
+
+__global__ void __launch_bounds__(128) k_shade_prep(VolConst V, FrameConst F, const __grid_constant__ LightSet L,
+                                                    SceneDev S, RaySet Rs, const int2* __restrict__ hit,
+                                                    unsigned long long* __restrict__ vis, uint4* __restrict__ jobs,
+                                                    uint8_t* __restrict__ job_light, unsigned* __restrict__ job_count,
+                                                    unsigned job_cap)
+{
+    __shared__ int s_lo, s_hi;
+    block_range(V, Rs, &s_lo, &s_hi);
+    const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+    bool front = false;
+    float3 xs = make_float3(0.f, 0.f, 0.f), n = make_float3(0.f, 0.f, 1.f);
+    if (r < Rs.n) {
+        vis[r] = 0ull;
+        int2 hv = hit[r];
+        uint32_t h = (uint32_t)hv.x;
+        float3 o, d;
+        if (h != kMiss && !(h & kBackBit) && ray_of(V, F, Rs, r, s_lo, s_hi, o, d)) {
+            float t = __int_as_float(hv.y);
+            n = tri_normal(S, (int)h);
+            float3 x = make_float3(fa(o.x, fm(t, d.x)), fa(o.y, fm(t, d.y)), fa(o.z, fm(t, d.z)));
+            xs = make_float3(fa(x.x, fm(V.tmin, n.x)), fa(x.y, fm(V.tmin, n.y)), fa(x.z, fm(V.tmin, n.z)));
+            front = true;
+        }
+    }
+    const unsigned lane = threadIdx.x & 31;
+    for (int l = 0; l < L.n; ++l) {
+        bool want = false;
+        if (front) {
+            float3 D = shadow_dir(L.l[l], xs);
+            want = dot3x(n.x, n.y, n.z, D.x, D.y, D.z) > 0.0f;
+        }
+        unsigned mask = __ballot_sync(0xFFFFFFFFu, want);
+        if (!mask) continue;
+        unsigned base = 0;
+        if (lane == 0) base = atomicAdd(job_count, (unsigned)__popc(mask));
+        base = __shfl_sync(0xFFFFFFFFu, base, 0);
+        if (want) {
+            unsigned slot = base + __popc(mask & ((1u << lane) - 1u));
+            if (slot < job_cap) {
+                jobs[slot] = make_uint4(__float_as_uint(xs.x), __float_as_uint(xs.y), __float_as_uint(xs.z), r);
+                job_light[slot] = (uint8_t)l;
+            } else {
+                atomicOr(V.err, kErrRayRange);
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(128) k_shadow(const __grid_constant__ LightSet L, SceneDev S,
+                                                const uint4* __restrict__ jobs, const uint8_t* __restrict__ job_light,
+                                                const unsigned* __restrict__ job_count, unsigned job_cap,
+                                                unsigned long long* __restrict__ vis, unsigned long long* shadow_ctr)
+{
+    const unsigned total = min(*job_count, job_cap);
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(shadow_ctr, (unsigned long long)total);
+    for (unsigned j = blockIdx.x * blockDim.x + threadIdx.x; j < total; j += gridDim.x * blockDim.x) {
+        uint4 jb = jobs[j];
+        int l = job_light[j];
+        const Light& Li = L.l[l];
+        float3 xs = make_float3(__uint_as_float(jb.x), __uint_as_float(jb.y), __uint_as_float(jb.z));
+        float3 D = shadow_dir(Li, xs);
+        float thi = Li.kind == 0 ? 1.0f : __int_as_float(0x7F800000);
+        if (!trace_any(S, xs, D, 0.0f, thi)) atomicOr(vis + jb.w, 1ull << l);
+    }
+}
+
+__global__ void __launch_bounds__(128) k_shade_finish(VolConst V, FrameConst F, const __grid_constant__ LightSet L,
+                                                      SceneDev S, RaySet Rs, const int2* __restrict__ hit,
+                                                      const unsigned long long* __restrict__ vis,
+                                                      const void* __restrict__ irr, const void* __restrict__ dep,
+                                                      int bounce, float4* __restrict__ rec, float* __restrict__ lum)
+{
+    __shared__ int s_lo, s_hi;
+    block_range(V, Rs, &s_lo, &s_hi);
+    const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= Rs.n) return;
+    int2 hv = hit[r];
+    uint32_t h = (uint32_t)hv.x;
+    float4 out;
+    float lo = 0.0f;
+    if (h == kMiss) {
+        lo = fa(fa(fm(kLumR, F.sky[0]), fm(kLumG, F.sky[1])), fm(kLumB, F.sky[2]));
+        out = make_float4(F.sky[0], F.sky[1], F.sky[2], V.depth_max);
+    } else {
+        float t = __int_as_float(hv.y);
+        float depth = fminf(t, V.depth_max);
+        float3 o, d;
+        if ((h & kBackBit) || !ray_of(V, F, Rs, r, s_lo, s_hi, o, d)) {
+            out = make_float4(0.f, 0.f, 0.f, depth);
+        } else {
+            int tri = (int)h;
+            float3 n = tri_normal(S, tri);
+            float3 x = make_float3(fa(o.x, fm(t, d.x)), fa(o.y, fm(t, d.y)), fa(o.z, fm(t, d.z)));
+            unsigned long long vm = vis[r];
+            float E0 = 0.f, E1 = 0.f, E2 = 0.f;
+            for (int l = 0; l < L.n; ++l) {
+                if (!((vm >> l) & 1ull)) continue;
+                const Light& Li = L.l[l];
+                float g;
+                if (Li.kind == 0) {
+                    float dx = fs(Li.v[0], x.x), dy = fs(Li.v[1], x.y), dz = fs(Li.v[2], x.z);
+                    float d2 = dot3x(dx, dy, dz, dx, dy, dz);
+                    float nd = dot3x(n.x, n.y, n.z, dx, dy, dz);
+                    g = nd > 0.0f ? fd(nd, fm(d2, fsq(d2))) : 0.0f;
+                } else {
+                    float ndD = dot3x(n.x, n.y, n.z, -Li.v[0], -Li.v[1], -Li.v[2]);
+                    float l2 = dot3x(Li.v[0], Li.v[1], Li.v[2], Li.v[0], Li.v[1], Li.v[2]);
+                    g = fd(ndD, fsq(l2));
+                }
+                E0 = fa(E0, fm(Li.rgb[0], g));
+                E1 = fa(E1, fm(Li.rgb[1], g));
+                E2 = fa(E2, fm(Li.rgb[2], g));
+            }
+            const float a0 = __ldg(S.albedo + 3 * (size_t)tri), a1 = __ldg(S.albedo + 3 * (size_t)tri + 1),
+                        a2 = __ldg(S.albedo + 3 * (size_t)tri + 2);
+            float r0 = fm(fm(a0, kInvPi), E0), r1 = fm(fm(a1, kInvPi), E1), r2 = fm(fm(a2, kInvPi), E2);
+            lo = fa(fa(fm(kLumR, r0), fm(kLumG, r1)), fm(kLumB, r2));
+            if (bounce) {
+                float3 Q = query_irr_hit(V, irr, dep, o, t, d, n);
+                r0 += a0 * Q.x;
+                r1 += a1 * Q.y;
+                r2 += a2 * Q.z;
+            }
+            out = make_float4(r0, r1, r2, depth);
+        }
+    }
+    rec[r] = out;
+    if (lum) lum[r] = lo;
+}
+
+}  // namespace
+
+unsigned shadow_grid_blocks()
+{
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_shadow, 128, 0);
+    if (sms <= 0) sms = 152;
+    if (per <= 0) per = 4;
+    return (unsigned)(sms * per);
+}
+
+cudaError_t launch_shade(const VolConst& V, const FrameConst& F, const LightSet& L, const SceneDev& S, int mode,
+                         uint32_t n_rays, const uint32_t* off, const float4* sf, const void* irr, const void* dep,
+                         const int2* hit, float4* rec, float* lum, int bounce, const ShadeWork& W, cudaStream_t s)
+{
+    if (n_rays == 0) return cudaSuccess;
+    RaySet Rs{mode, n_rays, off, sf};
+    const unsigned nb = (n_rays + 127) / 128;
+    cudaError_t e = cudaMemsetAsync(W.job_count, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    k_shade_prep<<<nb, 128, 0, s>>>(V, F, L, S, Rs, hit, W.vis, W.jobs, W.job_light, W.job_count, W.job_cap);
+    count_launches(1);
+    if (L.n > 0) {
+        k_shadow<<<W.shadow_blocks, 128, 0, s>>>(L, S, W.jobs, W.job_light, W.job_count, W.job_cap, W.vis,
+                                                 W.shadow_ctr);
+        count_launches(1);
+    }
+    k_shade_finish<<<nb, 128, 0, s>>>(V, F, L, S, Rs, hit, W.vis, irr, dep, bounce, rec, lum);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+}  // namespace adgi

@@ -78,136 +78,6 @@ __global__ void __launch_bounds__(128) k_main_trace(VolConst V, FrameConst F, Sc
     hit[r] = make_int2((int)h, __float_as_int(t));
 }
 
-constexpr float kInvPi = 0.31830987f;
-constexpr float kLumR = 0.2126f, kLumG = 0.7152f, kLumB = 0.0722f;
-
-// Shade one ray given its hit.  Writes {rgb, depth} and the FP32 luminance of
-// the direct-only radiance (f_r input).  Light visibility and the lit test are
-// exact FP32 decisions.
-__device__ __forceinline__ float4 shade(const VolConst& V, const FrameConst& F, const LightSet& L, const SceneDev& S,
-                                        const void* irr, const void* dep, float3 o, float3 d, int2 hv, bool bounce,
-                                        float* lum_out, unsigned* n_shadow)
-{
-    uint32_t h = (uint32_t)hv.x;
-    if (h == kMiss) {
-        *lum_out = fa(fa(fm(kLumR, F.sky[0]), fm(kLumG, F.sky[1])), fm(kLumB, F.sky[2]));
-        return make_float4(F.sky[0], F.sky[1], F.sky[2], V.depth_max);
-    }
-    float t = __int_as_float(hv.y);
-    float depth = fminf(t, V.depth_max);
-    if (h & kBackBit) {
-        *lum_out = 0.0f;
-        return make_float4(0.f, 0.f, 0.f, depth);
-    }
-    int tri = (int)h;
-    float4 A = __ldg(S.tri_orig + 3 * (size_t)tri), B = __ldg(S.tri_orig + 3 * (size_t)tri + 1),
-           C = __ldg(S.tri_orig + 3 * (size_t)tri + 2);
-    float e1x = fs(B.x, A.x), e1y = fs(B.y, A.y), e1z = fs(B.z, A.z);
-    float e2x = fs(C.x, A.x), e2y = fs(C.y, A.y), e2z = fs(C.z, A.z);
-    float cx = fs(fm(e1y, e2z), fm(e1z, e2y));
-    float cy = fs(fm(e1z, e2x), fm(e1x, e2z));
-    float cz = fs(fm(e1x, e2y), fm(e1y, e2x));
-    float cl = fsq(dot3x(cx, cy, cz, cx, cy, cz));
-    float3 n = cl > 0.0f ? make_float3(fd(cx, cl), fd(cy, cl), fd(cz, cl)) : make_float3(0.f, 0.f, 1.f);
-    float3 x = make_float3(fa(o.x, fm(t, d.x)), fa(o.y, fm(t, d.y)), fa(o.z, fm(t, d.z)));
-    float3 xs = make_float3(fa(x.x, fm(V.tmin, n.x)), fa(x.y, fm(V.tmin, n.y)), fa(x.z, fm(V.tmin, n.z)));
-    float E0 = 0.f, E1 = 0.f, E2 = 0.f;
-    for (int l = 0; l < L.n; ++l) {
-        const Light& Li = L.l[l];
-        float3 D;
-        float thi;
-        if (Li.kind == 0) {
-            D = make_float3(fs(Li.v[0], xs.x), fs(Li.v[1], xs.y), fs(Li.v[2], xs.z));
-            thi = 1.0f;
-        } else {
-            D = make_float3(-Li.v[0], -Li.v[1], -Li.v[2]);
-            thi = __int_as_float(0x7F800000);
-        }
-        float ndD = dot3x(n.x, n.y, n.z, D.x, D.y, D.z);
-        if (!(ndD > 0.0f)) continue;
-        ++*n_shadow;
-        if (trace_any(S, xs, D, 0.0f, thi)) continue;
-        float g;
-        if (Li.kind == 0) {
-            float dx = fs(Li.v[0], x.x), dy = fs(Li.v[1], x.y), dz = fs(Li.v[2], x.z);
-            float d2 = dot3x(dx, dy, dz, dx, dy, dz);
-            float nd = dot3x(n.x, n.y, n.z, dx, dy, dz);
-            g = nd > 0.0f ? fd(nd, fm(d2, fsq(d2))) : 0.0f;
-        } else {
-            float l2 = dot3x(Li.v[0], Li.v[1], Li.v[2], Li.v[0], Li.v[1], Li.v[2]);
-            g = fd(ndD, fsq(l2));
-        }
-        E0 = fa(E0, fm(Li.rgb[0], g));
-        E1 = fa(E1, fm(Li.rgb[1], g));
-        E2 = fa(E2, fm(Li.rgb[2], g));
-    }
-    const float a0 = __ldg(S.albedo + 3 * (size_t)tri), a1 = __ldg(S.albedo + 3 * (size_t)tri + 1),
-                a2 = __ldg(S.albedo + 3 * (size_t)tri + 2);
-    float r0 = fm(fm(a0, kInvPi), E0), r1 = fm(fm(a1, kInvPi), E1), r2 = fm(fm(a2, kInvPi), E2);
-    *lum_out = fa(fa(fm(kLumR, r0), fm(kLumG, r1)), fm(kLumB, r2));
-    if (bounce) {
-        float3 Q = query_irr_hit(V, irr, dep, o, t, d, n);
-        r0 += a0 * Q.x;
-        r1 += a1 * Q.y;
-        r2 += a2 * Q.z;
-    }
-    return make_float4(r0, r1, r2, depth);
-}
-
-__device__ __forceinline__ void count_shadow(unsigned n, unsigned long long* counter)
-{
-    unsigned tot = __reduce_add_sync(0xFFFFFFFFu, n);
-    if ((threadIdx.x & 31) == 0 && tot) atomicAdd(counter, (unsigned long long)tot);
-}
-
-__global__ void __launch_bounds__(128) k_pilot_shade(VolConst V, FrameConst F, const __grid_constant__ LightSet L,
-                                                     SceneDev S, const void* __restrict__ irr,
-                                                     const void* __restrict__ dep, const int2* __restrict__ hit,
-                                                     float4* __restrict__ rec, float* __restrict__ lum,
-                                                     unsigned long long* counter)
-{
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    unsigned ns = 0;
-    if (i < V.P * kPilots) {
-        int p = i >> 3, o = i & 7;
-        float3 org = probe_pos(V, p);
-        float3 d = pilot_dir(F.pilot_key, (uint32_t)p, o);
-        float l;
-        rec[i] = shade(V, F, L, S, irr, dep, org, d, hit[i], F.even != 0, &l, &ns);
-        lum[i] = l;
-    }
-    count_shadow(ns, counter);
-}
-
-__global__ void __launch_bounds__(128) k_main_shade(VolConst V, FrameConst F, const __grid_constant__ LightSet L,
-                                                    SceneDev S, const void* __restrict__ irr,
-                                                    const void* __restrict__ dep, const uint32_t* __restrict__ off,
-                                                    const float4* __restrict__ sf, uint32_t R,
-                                                    const int2* __restrict__ hit, float4* __restrict__ rec,
-                                                    unsigned long long* counter)
-{
-    __shared__ int s_lo, s_hi;
-    uint32_t r0 = blockIdx.x * blockDim.x;
-    uint32_t r1 = min(R - 1, r0 + blockDim.x - 1);
-    block_probe_range(off, V.P, r0, r1, &s_lo, &s_hi);
-    uint32_t r = r0 + threadIdx.x;
-    unsigned ns = 0;
-    if (r < R) {
-        int p = probe_of_ray(off, r, s_lo, s_hi);
-        uint32_t base = __ldg(off + p);
-        uint32_t m = __ldg(off + p + 1) - base;
-        if (m > (uint32_t)(V.rays_max - kPilots) || r - base >= m) {
-            atomicOr(V.err, kErrRayRange);
-        } else {
-            float3 org = probe_pos(V, p);
-            float3 d = main_dir(F, sf, m, r - base);
-            float l;
-            rec[r] = shade(V, F, L, S, irr, dep, org, d, hit[r], true, &l, &ns);
-        }
-    }
-    count_shadow(ns, counter);
-}
-
 // Re-trace the last update's rays with work counters (roofline accounting).
 __global__ void __launch_bounds__(128) k_count(VolConst V, FrameConst F, const __grid_constant__ LightSet L, SceneDev S,
                                                const uint32_t* __restrict__ off, const float4* __restrict__ sf,
@@ -312,26 +182,6 @@ cudaError_t launch_main_trace(const VolConst& V, const FrameConst& F, const Scen
 {
     if (R == 0) return cudaSuccess;
     k_main_trace<<<(R + 127) / 128, 128, 0, s>>>(V, F, S, off, sf, R, hit);
-    count_launches(1);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_pilot_shade(const VolConst& V, const FrameConst& F, const LightSet& L, const SceneDev& S,
-                               const void* irr, const void* dep, const int2* hit, float4* rec, float* lum,
-                               unsigned long long* counter, cudaStream_t s)
-{
-    int n = V.P * kPilots;
-    k_pilot_shade<<<(n + 127) / 128, 128, 0, s>>>(V, F, L, S, irr, dep, hit, rec, lum, counter);
-    count_launches(1);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_main_shade(const VolConst& V, const FrameConst& F, const LightSet& L, const SceneDev& S,
-                              const void* irr, const void* dep, const uint32_t* off, const float4* sf, uint32_t R,
-                              const int2* hit, float4* rec, unsigned long long* counter, cudaStream_t s)
-{
-    if (R == 0) return cudaSuccess;
-    k_main_shade<<<(R + 127) / 128, 128, 0, s>>>(V, F, L, S, irr, dep, off, sf, R, hit, rec, counter);
     count_launches(1);
     return cudaGetLastError();
 }
