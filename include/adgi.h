@@ -185,9 +185,15 @@ int adgi_enable_timing(adgi_volume vol, int32_t enable);
  *   ADGI_STATE_DEP      float[P][Td][Td][2] {mean, mean^2} (half[...][2] when atlas_fp16)
  *   ADGI_STATE_DEP_N    uint8[P][Td][Td]  depth sample counts
  *   ADGI_STATE_ROT      float[9]          main-ray rotation of the last update
- *   ADGI_STATE_BVH_NODES bytes[max(T-1,1)][64]  BVH nodes of the current scene (T triangles;
- *                       layout of adgi_build_bvh)
- *   ADGI_STATE_BVH_TRIS  float[T][3][4]    triangles in BVH order (layout of adgi_build_bvh)
+ *   ADGI_STATE_BVH_NODES bytes[max(T-1,1)][64]  nodes of the static part's BVH (T static
+ *                       triangles; layout of adgi_build_bvh; zeros when T < 2)
+ *   ADGI_STATE_BVH_TRIS  float[T][3][4]    static triangles in BVH order (layout of adgi_build_bvh)
+ *   ADGI_STATE_MOVING_BVH_NODES / _TRIS    the same for the moving part (triangles that touch a
+ *                       vertex passed to adgi_move_vertices), a linear BVH rebuilt after moves
+ * The scene is traced as two parts: triangles that touch any vertex ever passed
+ * to adgi_move_vertices form the moving part (linear BVH, rebuilt at the next
+ * update after each move); the others form the static part (agglomerative
+ * PLOC BVH, rebuilt only when the moving set grows).
  */
 enum {
     ADGI_STATE_W = 0,
@@ -207,7 +213,9 @@ enum {
     ADGI_STATE_DEP_N = 14,
     ADGI_STATE_ROT = 15,
     ADGI_STATE_BVH_NODES = 16,
-    ADGI_STATE_BVH_TRIS = 17
+    ADGI_STATE_BVH_TRIS = 17,
+    ADGI_STATE_MOVING_BVH_NODES = 18,
+    ADGI_STATE_MOVING_BVH_TRIS = 19
 };
 int adgi_state_bytes(adgi_volume vol, int32_t which, uint64_t* bytes);
 int adgi_read_state(adgi_volume vol, int32_t which, void* dst_host, uint64_t bytes);
@@ -234,12 +242,14 @@ int adgi_trace_closest(adgi_volume vol, const float* o, const float* d, int32_t 
  * stream.  Errors: INVALID_ARG, NO_SCENE, CUDA. */
 int adgi_count_traversal(adgi_volume vol, const adgi_frame* frame, uint64_t* counts);
 
-/* Build the update's software BVH (Morton codes, stable radix sort, radix
- * tree, bottom-up child boxes enlarged by eps) for caller triangles into
- * caller buffers -- the structure adgi_update() traces against.
+/* Build the linear BVH (Morton codes, stable radix sort, radix tree,
+ * bottom-up child boxes enlarged by eps) for caller triangles into caller
+ * buffers -- the structure adgi_update() uses for the moving part of a scene.
  *   verts:     device float[3*n_verts];  tri_idx: device int32[3*n_tris]
  *   eps:       absolute box enlargement (adgi_set_scene uses 1e-5 x the
- *              larger of the scene extent and the largest |coordinate|)
+ *              larger of the scene extent and the largest |coordinate|); a
+ *              triangle's box is enlarged by at least 1e-5 x its own largest
+ *              |coordinate|
  *   nodes_out: device buffer of max(n_tris-1, 1) * 64 bytes; node i holds
  *              float[12] child boxes {lo0.xyz, hi0.xyz, lo1.xyz, hi1.xyz} then
  *              int32[4] {left, right, 0, 0}: a child c >= 0 is node c, c < 0 is

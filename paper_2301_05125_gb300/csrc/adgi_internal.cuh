@@ -36,15 +36,25 @@ struct __align__(16) BNode {
     int4 d;    // left, right, -, -
 };
 
+// One BVH over a subset of the scene's triangles.
+struct SubBvh {
+    int n_tris;
+    int root_leaf;          // n_tris == 1: the single triangle slot
+    const float4* tri_v;    // [n_tris*3] vertices in BVH order, .w of v0 = original index
+    const BNode* nodes;     // [n_tris-1]
+    int max_iter;           // traversal step limit (a correct tree needs < n_tris steps)
+};
+
+// The scene: a static part (quality BVH, built once) and a moving part
+// (linear BVH, rebuilt when vertices move).  Hits are ranked over both by
+// (t, original triangle index).
 struct SceneDev {
+    SubBvh part[2];
+    int n_parts;
     int n_tris;
     int n_verts;
-    const float4* tri_v;    // [n_tris*3] vertices in BVH order, .w of v0 = original index
     const float4* tri_orig; // [n_tris*3] vertices in original order (shading normal)
     const float* albedo;    // [n_tris*3]
-    const BNode* nodes;     // [n_tris-1] (>= 1 node)
-    int root_leaf;          // n_tris == 1: the single triangle slot
-    int max_iter;           // traversal step limit (a correct tree needs < n_tris steps)
     int* err;               // anomaly flags (kErr*), 0 when all is well
 };
 
@@ -252,8 +262,14 @@ __device__ __forceinline__ bool slab(float lox, float loy, float loz, float hix,
 }
 
 constexpr float kBoxSlack = 1.0001f;  // pruning slack on the best t (conservative)
-// LBVH depth is at most 95 (63 key bits + 32 index bits), so 96 entries never overflow.
+// LBVH depth is at most 95 (63 key bits + 32 index bits); a PLOC tree can be
+// deeper, so its builder checks the depth against this bound.
 constexpr int kStack = 96;
+
+// Traversal of the two-part scene as one flat loop over one stack: an entry
+// is an internal node of part 0 (bit 30 clear) or part 1 (bit 30 set).  The
+// loop has no early exit, so the lanes of a warp reconverge every iteration.
+constexpr int kPartBit = 1 << 30;
 
 // nearest hit with t in (tmin, tmax]; (t, original index) lexicographic
 __device__ __forceinline__ void trace_closest(const SceneDev& S, float3 o, float3 d, float tmin, float tmax,
@@ -263,69 +279,89 @@ __device__ __forceinline__ void trace_closest(const SceneDev& S, float3 o, float
     t_best = tmax;
     hit_best = kMiss;
     if (S.n_tris == 0) return;
-    WRay wr = wray(o, d);
-    float3 inv = make_float3(1.0f / d.x, 1.0f / d.y, 1.0f / d.z);
+    const WRay wr = wray(o, d);
+    const float3 inv = make_float3(1.0f / d.x, 1.0f / d.y, 1.0f / d.z);
     int best_orig = 0x7FFFFFFF;
     float best_det = 0.0f;
     bool found = false;
-    auto test_tri = [&](int slot) {
-        if (ntri) ++*ntri;
-        const float4* tv = S.tri_v + 3 * (size_t)slot;
-        float4 A = __ldg(tv), B = __ldg(tv + 1), C = __ldg(tv + 2);
-        float tt, det;
-        if (!wtri(wr, A, B, C, tt, det)) return;
-        if (!(tt > tmin)) return;
-        int orig = __float_as_int(A.w);
-        bool better = found ? (tt < t_best || (tt == t_best && orig < best_orig)) : (tt <= tmax);
-        if (!better) return;
-        found = true;
-        t_best = tt;
-        best_orig = orig;
-        best_det = det;
-    };
-    if (S.root_leaf >= 0) {
-        test_tri(S.root_leaf);
-    } else {
-        int stack[kStack];
-        int sp = 0;
-        int node = 0;
-        for (int iter = 0;; ++iter) {
-            if (iter > S.max_iter) {
+    int stack[kStack + 2];
+    int sp = 0;
+    int iter = 0;
+    const int max_iter = S.part[0].max_iter + S.part[1].max_iter;
+    // single-triangle parts are tested up front; trees are pushed
+    for (int pi = 1; pi >= 0; --pi) {
+        const int nt = pi ? S.part[1].n_tris : S.part[0].n_tris;
+        const int rl = pi ? S.part[1].root_leaf : S.part[0].root_leaf;
+        if (nt >= 2) stack[sp++] = pi ? kPartBit : 0;
+        else if (nt == 1) {
+            const float4* tv = (pi ? S.part[1].tri_v : S.part[0].tri_v) + 3 * (size_t)rl;
+            float4 A = __ldg(tv), Bv = __ldg(tv + 1), C = __ldg(tv + 2);
+            float tt, det;
+            if (ntri) ++*ntri;
+            if (wtri(wr, A, Bv, C, tt, det) && tt > tmin) {
+                int orig = __float_as_int(A.w);
+                bool better = found ? (tt < t_best || (tt == t_best && orig < best_orig)) : (tt <= tmax);
+                if (better) {
+                    found = true;
+                    t_best = tt;
+                    best_orig = orig;
+                    best_det = det;
+                }
+            }
+        }
+    }
+    while (sp > 0) {
+        if (++iter > max_iter) {
+            atomicOr(S.err, kErrTraversal);
+            break;
+        }
+        if (nvis) ++*nvis;
+        const int e = stack[--sp];
+        const int part = e & kPartBit;
+        const BNode* nodes = part ? S.part[1].nodes : S.part[0].nodes;
+        const float4* tris = part ? S.part[1].tri_v : S.part[0].tri_v;
+        const BNode* nd = nodes + (e & ~kPartBit);
+        float4 a = __ldg(&nd->a), b = __ldg(&nd->b), c = __ldg(&nd->c);
+        int4 ch = __ldg(&nd->d);
+        float lim = t_best * kBoxSlack;
+        float t0, t1;
+        bool h0 = slab(a.x, a.y, a.z, a.w, b.x, b.y, o, inv, lim, t0);
+        bool h1 = slab(b.z, b.w, c.x, c.y, c.z, c.w, o, inv, lim, t1);
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const bool hk = k ? h1 : h0;
+            const int ck = k ? ch.y : ch.x;
+            if (hk && ck < 0) {
+                if (ntri) ++*ntri;
+                const float4* tv = tris + 3 * (size_t)(~ck);
+                float4 A = __ldg(tv), Bv = __ldg(tv + 1), C = __ldg(tv + 2);
+                float tt, det;
+                if (wtri(wr, A, Bv, C, tt, det) && tt > tmin) {
+                    int orig = __float_as_int(A.w);
+                    bool better = found ? (tt < t_best || (tt == t_best && orig < best_orig)) : (tt <= tmax);
+                    if (better) {
+                        found = true;
+                        t_best = tt;
+                        best_orig = orig;
+                        best_det = det;
+                    }
+                }
+            }
+        }
+        const bool i0 = h0 && ch.x >= 0, i1 = h1 && ch.y >= 0;
+        if (i0 && i1) {  // far child below the near one
+            const bool first0 = t0 <= t1;
+            if (sp + 2 <= kStack + 2) {
+                stack[sp++] = (first0 ? ch.y : ch.x) | part;
+                stack[sp++] = (first0 ? ch.x : ch.y) | part;
+            } else {
+                atomicOr(S.err, kErrTraversal);  // cannot happen: depths are bounded by the builders
+            }
+        } else if (i0 || i1) {
+            if (sp < kStack + 2)
+                stack[sp++] = (i0 ? ch.x : ch.y) | part;
+            else
                 atomicOr(S.err, kErrTraversal);
-                break;
-            }
-            if (nvis) ++*nvis;
-            const BNode* nd = S.nodes + node;
-            float4 a = __ldg(&nd->a), b = __ldg(&nd->b), c = __ldg(&nd->c);
-            int4 ch = __ldg(&nd->d);
-            float lim = t_best * kBoxSlack;
-            float t0, t1;
-            bool h0 = slab(a.x, a.y, a.z, a.w, b.x, b.y, o, inv, lim, t0);
-            bool h1 = slab(b.z, b.w, c.x, c.y, c.z, c.w, o, inv, lim, t1);
-            int next = -1;
-            if (h0 && ch.x < 0) {
-                test_tri(~ch.x);
-                h0 = false;
-            }
-            if (h1 && ch.y < 0) {
-                test_tri(~ch.y);
-                h1 = false;
-            }
-            if (h0 && h1) {
-                int nearc = t0 <= t1 ? ch.x : ch.y;
-                int farc = t0 <= t1 ? ch.y : ch.x;
-                if (sp < kStack) stack[sp++] = farc;
-                next = nearc;
-            } else if (h0) {
-                next = ch.x;
-            } else if (h1) {
-                next = ch.y;
-            }
-            if (next < 0) {
-                if (sp == 0) break;
-                next = stack[--sp];
-            }
-            node = next;
         }
     }
     if (found) hit_best = (uint32_t)best_orig | (best_det < 0.0f ? kBackBit : 0u);
@@ -336,57 +372,73 @@ __device__ __forceinline__ bool trace_any(const SceneDev& S, float3 o, float3 d,
                                           uint32_t* nvis = nullptr, uint32_t* ntri = nullptr)
 {
     if (S.n_tris == 0) return false;
-    WRay wr = wray(o, d);
-    float3 inv = make_float3(1.0f / d.x, 1.0f / d.y, 1.0f / d.z);
-    float lim = isinf(thi) ? thi : thi * kBoxSlack;
-    auto test_tri = [&](int slot) -> bool {
-        if (ntri) ++*ntri;
-        const float4* tv = S.tri_v + 3 * (size_t)slot;
-        float4 A = __ldg(tv), B = __ldg(tv + 1), C = __ldg(tv + 2);
-        float tt, det;
-        if (!wtri(wr, A, B, C, tt, det)) return false;
-        return tt > tlo && tt < thi;
-    };
-    if (S.root_leaf >= 0) return test_tri(S.root_leaf);
-    int stack[kStack];
+    const WRay wr = wray(o, d);
+    const float3 inv = make_float3(1.0f / d.x, 1.0f / d.y, 1.0f / d.z);
+    const float lim = isinf(thi) ? thi : thi * kBoxSlack;
+    bool hit = false;
+    int stack[kStack + 2];
     int sp = 0;
-    int node = 0;
-    for (int iter = 0;; ++iter) {
-        if (iter > S.max_iter) {
+    int iter = 0;
+    const int max_iter = S.part[0].max_iter + S.part[1].max_iter;
+    for (int pi = 1; pi >= 0; --pi) {
+        const int nt = pi ? S.part[1].n_tris : S.part[0].n_tris;
+        const int rl = pi ? S.part[1].root_leaf : S.part[0].root_leaf;
+        if (nt >= 2) stack[sp++] = pi ? kPartBit : 0;
+        else if (nt == 1) {
+            const float4* tv = (pi ? S.part[1].tri_v : S.part[0].tri_v) + 3 * (size_t)rl;
+            float4 A = __ldg(tv), Bv = __ldg(tv + 1), C = __ldg(tv + 2);
+            float tt, det;
+            if (ntri) ++*ntri;
+            if (wtri(wr, A, Bv, C, tt, det) && tt > tlo && tt < thi) hit = true;
+        }
+    }
+    if (hit) sp = 0;
+    while (sp > 0) {
+        if (++iter > max_iter) {
             atomicOr(S.err, kErrTraversal);
             break;
         }
         if (nvis) ++*nvis;
-        const BNode* nd = S.nodes + node;
+        const int e = stack[--sp];
+        const int part = e & kPartBit;
+        const BNode* nodes = part ? S.part[1].nodes : S.part[0].nodes;
+        const float4* tris = part ? S.part[1].tri_v : S.part[0].tri_v;
+        const BNode* nd = nodes + (e & ~kPartBit);
         float4 a = __ldg(&nd->a), b = __ldg(&nd->b), c = __ldg(&nd->c);
         int4 ch = __ldg(&nd->d);
         float t0, t1;
         bool h0 = slab(a.x, a.y, a.z, a.w, b.x, b.y, o, inv, lim, t0);
         bool h1 = slab(b.z, b.w, c.x, c.y, c.z, c.w, o, inv, lim, t1);
-        if (h0 && ch.x < 0) {
-            if (test_tri(~ch.x)) return true;
-            h0 = false;
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const bool hk = k ? h1 : h0;
+            const int ck = k ? ch.y : ch.x;
+            if (hk && ck < 0) {
+                if (ntri) ++*ntri;
+                const float4* tv = tris + 3 * (size_t)(~ck);
+                float4 A = __ldg(tv), Bv = __ldg(tv + 1), C = __ldg(tv + 2);
+                float tt, det;
+                if (wtri(wr, A, Bv, C, tt, det) && tt > tlo && tt < thi) hit = true;
+            }
         }
-        if (h1 && ch.y < 0) {
-            if (test_tri(~ch.y)) return true;
-            h1 = false;
+        const bool i0 = h0 && ch.x >= 0, i1 = h1 && ch.y >= 0;
+        if (i0 && i1) {  // nearer child first: blockers near the origin end the search sooner
+            const bool first0 = t0 <= t1;
+            if (sp + 2 <= kStack + 2) {
+                stack[sp++] = (first0 ? ch.y : ch.x) | part;
+                stack[sp++] = (first0 ? ch.x : ch.y) | part;
+            } else {
+                atomicOr(S.err, kErrTraversal);  // cannot happen: depths are bounded by the builders
+            }
+        } else if (i0 || i1) {
+            if (sp < kStack + 2)
+                stack[sp++] = (i0 ? ch.x : ch.y) | part;
+            else
+                atomicOr(S.err, kErrTraversal);
         }
-        int next = -1;
-        if (h0 && h1) {
-            if (sp < kStack) stack[sp++] = ch.y;
-            next = ch.x;
-        } else if (h0) {
-            next = ch.x;
-        } else if (h1) {
-            next = ch.y;
-        }
-        if (next < 0) {
-            if (sp == 0) break;
-            next = stack[--sp];
-        }
-        node = next;
+        if (hit) sp = 0;
     }
-    return false;
+    return hit;
 }
 
 // ----------------------------------------------------------------- atlas access

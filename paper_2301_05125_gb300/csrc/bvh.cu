@@ -27,14 +27,25 @@ __device__ __forceinline__ uint32_t f2ord(float f)
 }
 __device__ __forceinline__ float ord2f(uint32_t u) { return __uint_as_float((u & 0x80000000u) ? (u & 0x7FFFFFFFu) : ~u); }
 
+// box enlargement of one triangle: the scene's eps, or 1e-5 of the triangle's
+// largest |coordinate| if that is larger (geometry moved far from where eps
+// was measured); keeps box tests conservative for the watertight test
+__device__ __forceinline__ float tri_eps(float eps, float4 A, float4 B, float4 C)
+{
+    float m = fmaxf(fmaxf(fmaxf(fabsf(A.x), fabsf(A.y)), fmaxf(fabsf(A.z), fabsf(B.x))),
+                    fmaxf(fmaxf(fabsf(B.y), fabsf(B.z)), fmaxf(fmaxf(fabsf(C.x), fabsf(C.y)), fabsf(C.z))));
+    return fmaxf(eps, 1e-5f * m);
+}
+
 __global__ void k_init_bounds(uint32_t* __restrict__ bounds)
 {
     if (threadIdx.x < 3) bounds[threadIdx.x] = 0xFFFFFFFFu;
     else if (threadIdx.x < 6) bounds[threadIdx.x] = 0u;
 }
 
-__global__ void k_tri_prep(const float* __restrict__ verts, const int* __restrict__ idx, int nt, int nv,
-                           float4* __restrict__ tri_orig, uint32_t* __restrict__ bounds, int* __restrict__ err)
+__global__ void k_tri_prep(const float* __restrict__ verts, const int* __restrict__ idx, const int* __restrict__ list,
+                           int nt, int nv, float4* __restrict__ tri_in, uint32_t* __restrict__ bounds,
+                           int* __restrict__ err)
 {
     __shared__ uint32_t s_lo[3], s_hi[3];
     if (threadIdx.x < 3) {
@@ -42,8 +53,9 @@ __global__ void k_tri_prep(const float* __restrict__ verts, const int* __restric
         s_hi[threadIdx.x] = 0u;
     }
     __syncthreads();
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < nt) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nt) {
+        const int t = list ? list[i] : i;
         float c[3] = {0.f, 0.f, 0.f};
         for (int v = 0; v < 3; ++v) {
             int vi = idx[3 * (size_t)t + v];
@@ -52,7 +64,7 @@ __global__ void k_tri_prep(const float* __restrict__ verts, const int* __restric
                 vi = 0;
             }
             float x = verts[3 * (size_t)vi], y = verts[3 * (size_t)vi + 1], z = verts[3 * (size_t)vi + 2];
-            tri_orig[3 * (size_t)t + v] = make_float4(x, y, z, 0.f);
+            tri_in[3 * (size_t)i + v] = make_float4(x, y, z, v == 0 ? __int_as_float(t) : 0.f);
             c[0] += x;
             c[1] += y;
             c[2] += z;
@@ -70,6 +82,21 @@ __global__ void k_tri_prep(const float* __restrict__ verts, const int* __restric
     }
 }
 
+// vertices of the listed triangles into an original-order array (shading)
+__global__ void k_fill_orig(const float* __restrict__ verts, const int* __restrict__ idx, const int* __restrict__ list,
+                            int nt, int nv, float4* __restrict__ tri_orig)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nt) return;
+    const int t = list ? list[i] : i;
+    for (int v = 0; v < 3; ++v) {
+        int vi = idx[3 * (size_t)t + v];
+        vi = (vi < 0 || vi >= nv) ? 0 : vi;
+        tri_orig[3 * (size_t)t + v] =
+            make_float4(verts[3 * (size_t)vi], verts[3 * (size_t)vi + 1], verts[3 * (size_t)vi + 2], 0.f);
+    }
+}
+
 __device__ __forceinline__ uint64_t spread21(uint32_t v)
 {
     uint64_t x = v & 0x1FFFFFu;
@@ -81,7 +108,7 @@ __device__ __forceinline__ uint64_t spread21(uint32_t v)
     return x;
 }
 
-__global__ void k_morton(const float4* __restrict__ tri_orig, int nt, const uint32_t* __restrict__ bounds,
+__global__ void k_morton(const float4* __restrict__ tri_in, int nt, const uint32_t* __restrict__ bounds,
                          uint64_t* __restrict__ keys, uint32_t* __restrict__ vals)
 {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -92,7 +119,7 @@ __global__ void k_morton(const float4* __restrict__ tri_orig, int nt, const uint
         float hi = ord2f(bounds[3 + k]);
         ext[k] = fmaxf(hi - lo[k], 1e-30f);
     }
-    float4 A = tri_orig[3 * (size_t)t], B = tri_orig[3 * (size_t)t + 1], C = tri_orig[3 * (size_t)t + 2];
+    float4 A = tri_in[3 * (size_t)t], B = tri_in[3 * (size_t)t + 1], C = tri_in[3 * (size_t)t + 2];
     float c[3] = {(A.x + B.x + C.x) * (1.0f / 3.0f), (A.y + B.y + C.y) * (1.0f / 3.0f),
                   (A.z + B.z + C.z) * (1.0f / 3.0f)};
     uint32_t q[3];
@@ -183,17 +210,15 @@ __global__ void k_scatter(const uint64_t* __restrict__ kin, const uint32_t* __re
     }
 }
 
-__global__ void k_tri_order(const float4* __restrict__ tri_orig, const uint32_t* __restrict__ order, int nt,
+__global__ void k_tri_order(const float4* __restrict__ tri_in, const uint32_t* __restrict__ order, int nt,
                             float4* __restrict__ tri_v)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nt) return;
     uint32_t t = order[i];
-    float4 A = tri_orig[3 * (size_t)t], B = tri_orig[3 * (size_t)t + 1], C = tri_orig[3 * (size_t)t + 2];
-    A.w = __int_as_float((int)t);
-    tri_v[3 * (size_t)i] = A;
-    tri_v[3 * (size_t)i + 1] = B;
-    tri_v[3 * (size_t)i + 2] = C;
+    tri_v[3 * (size_t)i] = tri_in[3 * (size_t)t];
+    tri_v[3 * (size_t)i + 1] = tri_in[3 * (size_t)t + 1];
+    tri_v[3 * (size_t)i + 2] = tri_in[3 * (size_t)t + 2];
 }
 
 __device__ __forceinline__ int delta(const uint64_t* keys, int n, int i, int j)
@@ -248,6 +273,7 @@ __global__ void k_bounds(const float4* __restrict__ tri_v, int n, BNode* nodes, 
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     float4 A = tri_v[3 * (size_t)i], B = tri_v[3 * (size_t)i + 1], C = tri_v[3 * (size_t)i + 2];
+    eps = tri_eps(eps, A, B, C);
     float lo[3] = {fminf(fminf(A.x, B.x), C.x) - eps, fminf(fminf(A.y, B.y), C.y) - eps,
                    fminf(fminf(A.z, B.z), C.z) - eps};
     float hi[3] = {fmaxf(fmaxf(A.x, B.x), C.x) + eps, fmaxf(fmaxf(A.y, B.y), C.y) + eps,
@@ -280,6 +306,198 @@ __global__ void k_bounds(const float4* __restrict__ tri_v, int n, BNode* nodes, 
     }
 }
 
+// ---------------------------------------------------------------- PLOC
+// Parallel locally-ordered clustering (Meister & Bittner, TVCG 2018): clusters
+// in Morton order; each finds its nearest neighbour by the surface area of the
+// merged box within +-kPlocR positions; mutual nearest neighbours merge into a
+// new node; the cluster array is compacted; repeat until one cluster is left.
+constexpr int kPlocR = 16;
+constexpr int kPlocT = 256;
+
+__device__ __forceinline__ float box_area(float4 lo, float4 hi)
+{
+    float dx = hi.x - lo.x, dy = hi.y - lo.y, dz = hi.z - lo.z;
+    return 2.0f * (dx * dy + dy * dz + dz * dx);
+}
+
+__global__ void k_ploc_init(const float4* __restrict__ tri_v, int n, float eps, int* __restrict__ cid,
+                            float4* __restrict__ blo, float4* __restrict__ bhi)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float4 A = tri_v[3 * (size_t)i], B = tri_v[3 * (size_t)i + 1], C = tri_v[3 * (size_t)i + 2];
+    eps = tri_eps(eps, A, B, C);
+    blo[i] = make_float4(fminf(fminf(A.x, B.x), C.x) - eps, fminf(fminf(A.y, B.y), C.y) - eps,
+                         fminf(fminf(A.z, B.z), C.z) - eps, 0.f);
+    bhi[i] = make_float4(fmaxf(fmaxf(A.x, B.x), C.x) + eps, fmaxf(fmaxf(A.y, B.y), C.y) + eps,
+                         fmaxf(fmaxf(A.z, B.z), C.z) + eps, 0.f);
+    cid[i] = ~i;
+}
+
+__global__ void __launch_bounds__(kPlocT) k_ploc_nn(int count, const float4* __restrict__ blo,
+                                                    const float4* __restrict__ bhi, int* __restrict__ nn)
+{
+    __shared__ float4 slo[kPlocT + 2 * kPlocR], shi[kPlocT + 2 * kPlocR];
+    const int base = blockIdx.x * kPlocT - kPlocR;
+    for (int k = threadIdx.x; k < kPlocT + 2 * kPlocR; k += kPlocT) {
+        int j = base + k;
+        if (j >= 0 && j < count) {
+            slo[k] = blo[j];
+            shi[k] = bhi[j];
+        }
+    }
+    __syncthreads();
+    const int i = blockIdx.x * kPlocT + threadIdx.x;
+    if (i >= count) return;
+    const int me = threadIdx.x + kPlocR;
+    float4 lo = slo[me], hi = shi[me];
+    float best = __int_as_float(0x7F800000);
+    int bj = i;
+    for (int k = -kPlocR; k <= kPlocR; ++k) {
+        int j = i + k;
+        if (k == 0 || j < 0 || j >= count) continue;
+        float4 l2 = slo[me + k], h2 = shi[me + k];
+        float a = box_area(make_float4(fminf(lo.x, l2.x), fminf(lo.y, l2.y), fminf(lo.z, l2.z), 0.f),
+                           make_float4(fmaxf(hi.x, h2.x), fmaxf(hi.y, h2.y), fmaxf(hi.z, h2.z), 0.f));
+        if (a < best) {  // scanning j upwards: ties keep the smaller index
+            best = a;
+            bj = j;
+        }
+    }
+    nn[i] = bj;
+}
+
+// flags of cluster i packed for one scan: keep (high word), creates a node (low word)
+__global__ void k_ploc_flags(int count, const int* __restrict__ nn, uint64_t* __restrict__ fl)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    int j = nn[i];
+    bool mutual = j != i && nn[j] == i;
+    uint64_t keep = !(mutual && j < i);
+    uint64_t mrg = mutual && i < j;
+    fl[i] = (keep << 32) | mrg;
+}
+
+__global__ void k_ploc_merge(int count, const int* __restrict__ nn, const uint64_t* __restrict__ pre,
+                             const int* __restrict__ cid, const float4* __restrict__ blo,
+                             const float4* __restrict__ bhi, int node_top, int* __restrict__ cid2,
+                             float4* __restrict__ blo2, float4* __restrict__ bhi2, BNode* __restrict__ nodes,
+                             int* __restrict__ par_int, int* __restrict__ par_leaf)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    int j = nn[i];
+    bool mutual = j != i && nn[j] == i;
+    if (mutual && j < i) return;  // merged into cluster j
+    uint64_t p = pre[i];
+    int pos = (int)(p >> 32);
+    if (mutual) {
+        int node = node_top - 1 - (int)(p & 0xFFFFFFFFu);
+        float4 la = blo[i], ha = bhi[i], lb = blo[j], hb = bhi[j];
+        BNode b;
+        b.a = make_float4(la.x, la.y, la.z, ha.x);
+        b.b = make_float4(ha.y, ha.z, lb.x, lb.y);
+        b.c = make_float4(lb.z, hb.x, hb.y, hb.z);
+        b.d = make_int4(cid[i], cid[j], 0, 0);
+        nodes[node] = b;
+        for (int c2 : {cid[i], cid[j]}) {
+            if (c2 < 0)
+                par_leaf[~c2] = node;
+            else
+                par_int[c2] = node;
+        }
+        cid2[pos] = node;
+        blo2[pos] = make_float4(fminf(la.x, lb.x), fminf(la.y, lb.y), fminf(la.z, lb.z), 0.f);
+        bhi2[pos] = make_float4(fmaxf(ha.x, hb.x), fmaxf(ha.y, hb.y), fmaxf(ha.z, hb.z), 0.f);
+    } else {
+        cid2[pos] = cid[i];
+        blo2[pos] = blo[i];
+        bhi2[pos] = bhi[i];
+    }
+}
+
+// depth of every leaf below the root (node 0), bounded walk; max into *depth
+__global__ void k_leaf_depth(int n, const int* __restrict__ par_int, const int* __restrict__ par_leaf,
+                             int* __restrict__ depth)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int d = 1, x = par_leaf[i];
+    while (x != 0 && d < 4096) {
+        x = par_int[x];
+        ++d;
+    }
+    atomicMax(depth, d);
+}
+
+// ---------------------------------------------------------------- 64-bit scan
+// exclusive scan in three phases: per-block scans of 1024 values, a scan of
+// the block totals (one block), and the add-back.
+constexpr int kScanT = 256, kScanItems = 4, kScanBlock = kScanT * kScanItems;
+
+__global__ void __launch_bounds__(kScanT) k_scan64_block(const uint64_t* __restrict__ in, uint64_t* __restrict__ out,
+                                                         uint64_t* __restrict__ sums, int n)
+{
+    __shared__ uint64_t wsum[kScanT / 32];
+    const int base = blockIdx.x * kScanBlock + threadIdx.x * kScanItems;
+    uint64_t v[kScanItems], run = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        v[k] = base + k < n ? in[base + k] : 0ull;
+        run += v[k];
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint64_t x = run;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint64_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[w] = x;
+    __syncthreads();
+    uint64_t wbase = 0;
+    for (int k = 0; k < w; ++k) wbase += wsum[k];
+    uint64_t pre = wbase + x - run;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        if (base + k < n) out[base + k] = pre;
+        pre += v[k];
+    }
+    if (threadIdx.x == kScanT - 1) sums[blockIdx.x] = wbase + x;
+}
+
+__global__ void k_scan64_small(uint64_t* __restrict__ a, int n, uint64_t* __restrict__ total)
+{
+    __shared__ uint64_t part[1024];
+    int tid = threadIdx.x;
+    int per = (n + 1023) / 1024;
+    int s0 = tid * per, s1 = min(n, s0 + per);
+    uint64_t sum = 0;
+    for (int i = s0; i < s1; ++i) sum += a[i];
+    part[tid] = sum;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+        uint64_t v = tid >= off ? part[tid - off] : 0ull;
+        __syncthreads();
+        part[tid] += v;
+        __syncthreads();
+    }
+    uint64_t run = part[tid] - sum;
+    for (int i = s0; i < s1; ++i) {
+        uint64_t v = a[i];
+        a[i] = run;
+        run += v;
+    }
+    if (tid == 1023) *total = part[1023];
+}
+
+__global__ void k_scan64_add(uint64_t* __restrict__ out, const uint64_t* __restrict__ sums, int n)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] += sums[i / kScanBlock];
+}
+
 }  // namespace
 
 size_t Bvh::bytes() const { return bytes_; }
@@ -290,8 +508,9 @@ size_t bvh_scratch_bytes(int nt)
     return carve_bvh_scratch(nullptr, nt, B);
 }
 
-// Carve the scratch buffers of a build for nt triangles out of one block
-// (base may be null to only compute the size); every piece 256-byte aligned.
+// Carve the scratch buffers of a linear build for nt triangles out of one
+// block (base may be null to only compute the size); every piece 256-byte
+// aligned.
 size_t carve_bvh_scratch(void* base, int nt, BvhBufs& B)
 {
     const size_t n = (size_t)(nt > 0 ? nt : 1);
@@ -302,7 +521,7 @@ size_t carve_bvh_scratch(void* base, int nt, BvhBufs& B)
         off += (bytes + 255) & ~(size_t)255;
         return p;
     };
-    B.tri_orig = (float4*)take(sizeof(float4) * 3 * n);
+    B.tri_in = (float4*)take(sizeof(float4) * 3 * n);
     B.par_int = (int*)take(sizeof(int) * n);
     B.par_leaf = (int*)take(sizeof(int) * n);
     B.flags = (int*)take(sizeof(int) * n);
@@ -316,21 +535,16 @@ size_t carve_bvh_scratch(void* base, int nt, BvhBufs& B)
     return off;
 }
 
-// The build itself: every buffer comes from B (scratch) or the outputs
-// B.tri_v / B.nodes.  All work is ordered on stream s; nothing is allocated.
-cudaError_t build_lbvh(const BvhBufs& B, const float* d_verts, const int* d_idx, int nv, int nt, float eps, int* err,
-                       cudaStream_t s, int* root_leaf)
+// Morton order of the listed triangles into B.tri_v (all builds start here)
+static cudaError_t morton_order(const BvhBufs& B, const float* d_verts, const int* d_idx, const int* list, int nv,
+                                int nt, int* err, cudaStream_t s, int* cur_out)
 {
-    if (nt <= 0) {
-        *root_leaf = -1;
-        return cudaSuccess;
-    }
     const int T = 256;
     k_init_bounds<<<1, 32, 0, s>>>(B.bounds);
     count_launches(1);
-    k_tri_prep<<<(nt + T - 1) / T, T, 0, s>>>(d_verts, d_idx, nt, nv, B.tri_orig, B.bounds, err);
+    k_tri_prep<<<(nt + T - 1) / T, T, 0, s>>>(d_verts, d_idx, list, nt, nv, B.tri_in, B.bounds, err);
     count_launches(1);
-    k_morton<<<(nt + T - 1) / T, T, 0, s>>>(B.tri_orig, nt, B.bounds, B.keys[0], B.vals[0]);
+    k_morton<<<(nt + T - 1) / T, T, 0, s>>>(B.tri_in, nt, B.bounds, B.keys[0], B.vals[0]);
     count_launches(1);
     int nb = (nt + kSortTile - 1) / kSortTile;
     int cur = 0;
@@ -344,14 +558,32 @@ cudaError_t build_lbvh(const BvhBufs& B, const float* d_verts, const int* d_idx,
         count_launches(1);
         cur ^= 1;
     }
-    k_tri_order<<<(nt + T - 1) / T, T, 0, s>>>(B.tri_orig, B.vals[cur], nt, B.tri_v);
+    k_tri_order<<<(nt + T - 1) / T, T, 0, s>>>(B.tri_in, B.vals[cur], nt, B.tri_v);
     count_launches(1);
+    *cur_out = cur;
+    return cudaGetLastError();
+}
+
+// Linear BVH (Karras 2012) of the listed triangles (list = null: all).  Every
+// buffer comes from B (scratch) or the outputs B.tri_v / B.nodes; all work is
+// ordered on stream s; nothing is allocated.
+cudaError_t build_lbvh(const BvhBufs& B, const float* d_verts, const int* d_idx, int nv, int nt, float eps, int* err,
+                       cudaStream_t s, int* root_leaf, const int* list)
+{
+    if (nt <= 0) {
+        *root_leaf = -1;
+        return cudaSuccess;
+    }
+    const int T = 256;
+    int cur = 0;
+    cudaError_t e = morton_order(B, d_verts, d_idx, list, nv, nt, err, s, &cur);
+    if (e != cudaSuccess) return e;
     if (nt == 1) {
         *root_leaf = 0;
         return cudaGetLastError();
     }
     *root_leaf = -1;
-    cudaError_t e = cudaMemsetAsync(B.flags, 0, sizeof(int) * (size_t)nt, s);
+    e = cudaMemsetAsync(B.flags, 0, sizeof(int) * (size_t)nt, s);
     if (e != cudaSuccess) return e;
     k_hierarchy<<<(nt - 1 + T - 1) / T, T, 0, s>>>(B.keys[cur], nt, B.nodes, B.par_int, B.par_leaf);
     count_launches(1);
@@ -360,19 +592,177 @@ cudaError_t build_lbvh(const BvhBufs& B, const float* d_verts, const int* d_idx,
     return cudaGetLastError();
 }
 
+// PLOC build of the listed triangles: Morton order as for the linear BVH,
+// then agglomerative clustering.  The host reads the cluster count after each
+// round (one synchronisation per round); meant for geometry that changes
+// rarely.  Nodes are numbered from the top so that the final merge is node 0.
+cudaError_t build_ploc(const BvhBufs& B, const PlocBufs& Q, const float* d_verts, const int* d_idx, int nv, int nt,
+                       float eps, int* err, cudaStream_t s, int* root_leaf, const int* list)
+{
+    if (nt <= 0) {
+        *root_leaf = -1;
+        return cudaSuccess;
+    }
+    int cur = 0;
+    cudaError_t e = morton_order(B, d_verts, d_idx, list, nv, nt, err, s, &cur);
+    if (e != cudaSuccess) return e;
+    if (nt == 1) {
+        *root_leaf = 0;
+        return cudaGetLastError();
+    }
+    *root_leaf = -1;
+    const int T = 256;
+    k_ploc_init<<<(nt + T - 1) / T, T, 0, s>>>(B.tri_v, nt, eps, Q.cid[0], Q.blo[0], Q.bhi[0]);
+    count_launches(1);
+    int count = nt, node_top = nt - 1, c = 0;
+    for (int round = 0; count > 1; ++round) {
+        if (round > 4 * 64 + nt) return cudaErrorUnknown;  // no progress: cannot happen with strict ties
+        const int nb = (count + kPlocT - 1) / kPlocT;
+        k_ploc_nn<<<nb, kPlocT, 0, s>>>(count, Q.blo[c], Q.bhi[c], Q.nn);
+        count_launches(1);
+        k_ploc_flags<<<nb, kPlocT, 0, s>>>(count, Q.nn, Q.flags);
+        count_launches(1);
+        const int sb = (count + kScanBlock - 1) / kScanBlock;
+        k_scan64_block<<<sb, kScanT, 0, s>>>(Q.flags, Q.pre, Q.sums, count);
+        count_launches(1);
+        k_scan64_small<<<1, 1024, 0, s>>>(Q.sums, sb, Q.total);
+        count_launches(1);
+        k_scan64_add<<<(count + T - 1) / T, T, 0, s>>>(Q.pre, Q.sums, count);
+        count_launches(1);
+        k_ploc_merge<<<nb, kPlocT, 0, s>>>(count, Q.nn, Q.pre, Q.cid[c], Q.blo[c], Q.bhi[c], node_top, Q.cid[c ^ 1],
+                                           Q.blo[c ^ 1], Q.bhi[c ^ 1], B.nodes, B.par_int, B.par_leaf);
+        count_launches(1);
+        uint64_t tot = 0;
+        e = cudaMemcpyAsync(&tot, Q.total, sizeof(tot), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return e;
+        int keeps = (int)(tot >> 32), merges = (int)(tot & 0xFFFFFFFFu);
+        if (merges <= 0 || keeps != count - merges) return cudaErrorUnknown;
+        count = keeps;
+        node_top -= merges;
+        c ^= 1;
+    }
+    if (node_top != 0) return cudaErrorUnknown;
+    // the traversal stack holds at most depth-1 entries: a deeper tree is
+    // replaced by the linear BVH (depth <= 95 by construction)
+    e = cudaMemsetAsync(Q.total, 0, sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    k_leaf_depth<<<(nt + T - 1) / T, T, 0, s>>>(nt, B.par_int, B.par_leaf, (int*)Q.total);
+    count_launches(1);
+    int depth = 0;
+    e = cudaMemcpyAsync(&depth, Q.total, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return e;
+    if (depth >= kStack) return build_lbvh(B, d_verts, d_idx, nv, nt, eps, err, s, root_leaf, list);
+    return cudaGetLastError();
+}
+
+size_t ploc_scratch_bytes(int nt)
+{
+    PlocBufs Q;
+    return carve_ploc_scratch(nullptr, nt, Q);
+}
+
+size_t carve_ploc_scratch(void* base, int nt, PlocBufs& Q)
+{
+    const size_t n = (size_t)(nt > 0 ? nt : 1);
+    size_t off = 0;
+    auto take = [&](size_t bytes) -> void* {
+        void* p = base ? (void*)((char*)base + off) : nullptr;
+        off += (bytes + 255) & ~(size_t)255;
+        return p;
+    };
+    for (int k = 0; k < 2; ++k) {
+        Q.cid[k] = (int*)take(sizeof(int) * n);
+        Q.blo[k] = (float4*)take(sizeof(float4) * n);
+        Q.bhi[k] = (float4*)take(sizeof(float4) * n);
+    }
+    Q.nn = (int*)take(sizeof(int) * n);
+    Q.flags = (uint64_t*)take(sizeof(uint64_t) * n);
+    Q.pre = (uint64_t*)take(sizeof(uint64_t) * n);
+    Q.sums = (uint64_t*)take(sizeof(uint64_t) * ((n + kScanBlock - 1) / kScanBlock + 1));
+    Q.total = (uint64_t*)take(sizeof(uint64_t));
+    return off;
+}
+
+__global__ void k_classify(const int* __restrict__ idx, const uint8_t* __restrict__ vmoved, int nt, int nv,
+                           uint64_t* __restrict__ fl)
+{
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nt) return;
+    bool mv = false;
+    for (int v = 0; v < 3; ++v) {
+        int vi = idx[3 * (size_t)t + v];
+        if (vi >= 0 && vi < nv && vmoved[vi]) mv = true;
+    }
+    fl[t] = mv ? 1ull : (1ull << 32);  // static count high, moving count low
+}
+
+__global__ void k_split(const uint64_t* __restrict__ fl, const uint64_t* __restrict__ pre, int nt,
+                        int* __restrict__ slist, int* __restrict__ dlist)
+{
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nt) return;
+    uint64_t p = pre[t];
+    if (fl[t] >> 32)
+        slist[p >> 32] = t;
+    else
+        dlist[p & 0xFFFFFFFFu] = t;
+}
+
+// Split the triangles into static (no moved vertex) and moving ones, keeping
+// index order in both lists; returns the counts (synchronises the stream).
+cudaError_t split_static_moving(const int* d_idx, const uint8_t* vmoved, int nt, int nv, const PlocBufs& Q,
+                                int* slist, int* dlist, int* ns, int* nd, cudaStream_t s)
+{
+    *ns = 0;
+    *nd = 0;
+    if (nt <= 0) return cudaSuccess;
+    const int T = 256;
+    k_classify<<<(nt + T - 1) / T, T, 0, s>>>(d_idx, vmoved, nt, nv, Q.flags);
+    count_launches(1);
+    const int sb = (nt + kScanBlock - 1) / kScanBlock;
+    k_scan64_block<<<sb, kScanT, 0, s>>>(Q.flags, Q.pre, Q.sums, nt);
+    count_launches(1);
+    k_scan64_small<<<1, 1024, 0, s>>>(Q.sums, sb, Q.total);
+    count_launches(1);
+    k_scan64_add<<<(nt + T - 1) / T, T, 0, s>>>(Q.pre, Q.sums, nt);
+    count_launches(1);
+    k_split<<<(nt + T - 1) / T, T, 0, s>>>(Q.flags, Q.pre, nt, slist, dlist);
+    count_launches(1);
+    uint64_t tot = 0;
+    cudaError_t e = cudaMemcpyAsync(&tot, Q.total, sizeof(tot), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return e;
+    *ns = (int)(tot >> 32);
+    *nd = (int)(tot & 0xFFFFFFFFu);
+    return cudaSuccess;
+}
+
+cudaError_t fill_tri_orig(const float* d_verts, const int* d_idx, const int* list, int nv, int nt, float4* tri_orig,
+                          cudaStream_t s)
+{
+    if (nt <= 0) return cudaSuccess;
+    k_fill_orig<<<(nt + 255) / 256, 256, 0, s>>>(d_verts, d_idx, list, nt, nv, tri_orig);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
 void Bvh::release()
 {
     cudaFree(scratch);
+    cudaFree(pscratch);
     cudaFree(tri_v);
     cudaFree(nodes);
     *this = Bvh();
 }
 
-cudaError_t Bvh::reserve(int nt)
+cudaError_t Bvh::reserve(int nt, bool ploc)
 {
-    if (nt <= cap_) return cudaSuccess;
+    if (nt <= cap_ && (!ploc || pscratch)) return cudaSuccess;
+    int n = nt > cap_ ? nt : cap_;
     release();
-    int n = nt > 0 ? nt : 1;
+    n = n > 0 ? n : 1;
     size_t sb = bvh_scratch_bytes(n);
     cudaError_t e = cudaMalloc(&scratch, sb);
     if (e != cudaSuccess) return e;
@@ -380,40 +770,42 @@ cudaError_t Bvh::reserve(int nt)
     if (e != cudaSuccess) return e;
     e = cudaMalloc((void**)&nodes, sizeof(BNode) * (size_t)n);
     if (e != cudaSuccess) return e;
+    size_t pb = 0;
+    if (ploc) {
+        pb = ploc_scratch_bytes(n);
+        e = cudaMalloc(&pscratch, pb);
+        if (e != cudaSuccess) return e;
+        carve_ploc_scratch(pscratch, n, pbufs);
+    }
     carve_bvh_scratch(scratch, n, bufs);
     bufs.tri_v = tri_v;
     bufs.nodes = nodes;
-    tri_orig = bufs.tri_orig;
     cap_ = n;
-    bytes_ = sb + sizeof(float4) * 3 * (size_t)n + sizeof(BNode) * (size_t)n;
+    bytes_ = sb + pb + sizeof(float4) * 3 * (size_t)n + sizeof(BNode) * (size_t)n;
     return cudaSuccess;
 }
 
-// Host-side: scene extent -> enlargement eps (1e-5 of the larger of the extent
-// and the largest coordinate magnitude).
-cudaError_t Bvh::build(const float* d_verts, const int* d_idx, int nv, int nt, float eps, int* err, cudaStream_t s)
+cudaError_t Bvh::build(const float* d_verts, const int* d_idx, int nv, int nt, float eps, int* err, cudaStream_t s,
+                       const int* list, bool ploc)
 {
     n_tris = 0;
     if (nt == 0) return cudaSuccess;
-    cudaError_t e = reserve(nt);  // may reset every member
+    cudaError_t e = reserve(nt, ploc);  // may reset every member
     if (e != cudaSuccess) return e;
     n_tris = nt;
-    return build_lbvh(bufs, d_verts, d_idx, nv, nt, eps, err, s, &root_leaf);
+    return ploc ? build_ploc(bufs, pbufs, d_verts, d_idx, nv, nt, eps, err, s, &root_leaf, list)
+                : build_lbvh(bufs, d_verts, d_idx, nv, nt, eps, err, s, &root_leaf, list);
 }
 
-SceneDev Bvh::view(const float* albedo, int nv, int* err) const
+SubBvh Bvh::part() const
 {
-    SceneDev S;
-    S.max_iter = 2 * n_tris + 16;
-    S.err = err;
-    S.n_tris = n_tris;
-    S.n_verts = nv;
-    S.tri_v = tri_v;
-    S.tri_orig = tri_orig;
-    S.albedo = albedo;
-    S.nodes = nodes;
-    S.root_leaf = root_leaf;
-    return S;
+    SubBvh P;
+    P.n_tris = n_tris;
+    P.root_leaf = root_leaf;
+    P.tri_v = tri_v;
+    P.nodes = nodes;
+    P.max_iter = 2 * n_tris + 16;
+    return P;
 }
 
 }  // namespace adgi

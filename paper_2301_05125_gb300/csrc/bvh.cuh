@@ -10,7 +10,7 @@ namespace adgi {
 struct BvhBufs {
     float4* tri_v = nullptr;     // [3*n] output: BVH order, v0.w = original index
     BNode* nodes = nullptr;      // [n-1] output
-    float4* tri_orig = nullptr;  // [3*n] scratch (kept by volumes for shading normals)
+    float4* tri_in = nullptr;    // [3*n] scratch: the listed triangles, v0.w = original index
     int* par_int = nullptr;
     int* par_leaf = nullptr;
     int* flags = nullptr;
@@ -21,27 +21,50 @@ struct BvhBufs {
     int* err = nullptr;
 };
 
+// extra scratch of the PLOC build
+struct PlocBufs {
+    int* cid[2] = {nullptr, nullptr};
+    float4* blo[2] = {nullptr, nullptr};
+    float4* bhi[2] = {nullptr, nullptr};
+    int* nn = nullptr;
+    uint64_t* flags = nullptr;
+    uint64_t* pre = nullptr;
+    uint64_t* sums = nullptr;
+    uint64_t* total = nullptr;
+};
+
 size_t bvh_scratch_bytes(int nt);
 size_t carve_bvh_scratch(void* base, int nt, BvhBufs& B);
+size_t ploc_scratch_bytes(int nt);
+size_t carve_ploc_scratch(void* base, int nt, PlocBufs& Q);
 cudaError_t build_lbvh(const BvhBufs& B, const float* d_verts, const int* d_idx, int nv, int nt, float eps, int* err,
-                       cudaStream_t s, int* root_leaf);
+                       cudaStream_t s, int* root_leaf, const int* list = nullptr);
+cudaError_t build_ploc(const BvhBufs& B, const PlocBufs& Q, const float* d_verts, const int* d_idx, int nv, int nt,
+                       float eps, int* err, cudaStream_t s, int* root_leaf, const int* list = nullptr);
+cudaError_t split_static_moving(const int* d_idx, const uint8_t* vmoved, int nt, int nv, const PlocBufs& Q,
+                                int* slist, int* dlist, int* ns, int* nd, cudaStream_t s);
+cudaError_t fill_tri_orig(const float* d_verts, const int* d_idx, const int* list, int nv, int nt, float4* tri_orig,
+                          cudaStream_t s);
 
+// A BVH owned by a volume (static part: PLOC; moving part: linear BVH).
 struct Bvh {
     int n_tris = 0;
     int root_leaf = -1;
-    float4* tri_orig = nullptr;  // [3*n] original order (inside scratch)
-    float4* tri_v = nullptr;     // [3*n] BVH order, v0.w = original index
-    BNode* nodes = nullptr;      // [n-1]
+    float4* tri_v = nullptr;  // [3*n] BVH order, v0.w = original index
+    BNode* nodes = nullptr;   // [n-1]
     void* scratch = nullptr;
+    void* pscratch = nullptr;
     BvhBufs bufs;
+    PlocBufs pbufs;
     int cap_ = 0;
     size_t bytes_ = 0;
 
-    cudaError_t reserve(int nt);
-    cudaError_t build(const float* d_verts, const int* d_idx, int nv, int nt, float eps, int* err, cudaStream_t s);
+    cudaError_t reserve(int nt, bool ploc);
+    cudaError_t build(const float* d_verts, const int* d_idx, int nv, int nt, float eps, int* err, cudaStream_t s,
+                      const int* list, bool ploc);
     void release();
     size_t bytes() const;
-    SceneDev view(const float* albedo, int nv, int* err) const;
+    SubBvh part() const;
 };
 
 }  // namespace adgi

@@ -155,9 +155,19 @@ struct adgi_volume_s {
     int* idx = nullptr;
     float* albedo = nullptr;
     int nv = 0, nt = 0;
-    bool has_scene = false, bvh_dirty = false;
+    bool has_scene = false;
     float eps = 0.f;
-    Bvh bvh;
+    // two-part scene: triangles that touch a moved vertex form the moving part
+    Bvh sbvh, dbvh;               // static part (PLOC, built once) and moving part (linear, per move)
+    float4* tri_orig = nullptr;   // [3*nt] vertices in original order (shading normals)
+    uint8_t* vmoved = nullptr;    // [nv] 1: vertex has been moved
+    int* slist = nullptr;         // static triangles
+    int* dlist = nullptr;         // moving triangles
+    int ns = 0, nd = 0;
+    size_t scene_cap_v = 0, scene_cap_t = 0;
+    std::vector<std::pair<int, int>> moved;  // union of moved vertex ranges [a, b)
+    bool split_dirty = false;     // the moved set grew: split and rebuild the static part
+    bool dyn_dirty = false;       // moving vertices changed: rebuild the moving part
     // frame bookkeeping
     int64_t last_even = -2;
     uint64_t frames = 0;
@@ -183,7 +193,12 @@ void free_volume(adgi_volume v)
                     v->vis,     v->jobs,    v->job_light, v->job_count};
     for (void* p : ptrs)
         if (p) cudaFree(p);
-    v->bvh.release();
+    v->sbvh.release();
+    v->dbvh.release();
+    cudaFree(v->tri_orig);
+    cudaFree(v->vmoved);
+    cudaFree(v->slist);
+    cudaFree(v->dlist);
     if (v->ev0) cudaEventDestroy(v->ev0);
     if (v->ev1) cudaEventDestroy(v->ev1);
     for (cudaEvent_t e : v->ph)
@@ -429,17 +444,26 @@ int adgi_set_scene(adgi_volume v, const float* verts, int32_t nv, const int32_t*
         mag = std::fmax(mag, std::fmax(std::fabs(lo[c]), std::fabs(hi3[c])));
     }
     v->eps = (float)(1e-5 * std::fmax(ext, mag) + 1e-30);
-    if (nv > v->nv || nt > v->nt || !v->verts) {
-        cudaFree(v->verts);
-        cudaFree(v->idx);
-        cudaFree(v->albedo);
+    if ((size_t)nv > v->scene_cap_v || (size_t)nt > v->scene_cap_t || !v->verts) {
+        for (void* p : {(void*)v->verts, (void*)v->idx, (void*)v->albedo, (void*)v->tri_orig, (void*)v->vmoved,
+                        (void*)v->slist, (void*)v->dlist})
+            cudaFree(p);
         v->verts = nullptr;
         v->idx = nullptr;
         v->albedo = nullptr;
+        v->tri_orig = nullptr;
+        v->vmoved = nullptr;
+        v->slist = nullptr;
+        v->dlist = nullptr;
         size_t dummy = 0;
         if (dalloc(&v->verts, 3 * (size_t)nv, &dummy) != cudaSuccess || dalloc(&v->idx, 3 * (size_t)nt, &dummy) != cudaSuccess ||
-            dalloc(&v->albedo, 3 * (size_t)nt, &dummy) != cudaSuccess)
+            dalloc(&v->albedo, 3 * (size_t)nt, &dummy) != cudaSuccess ||
+            dalloc(&v->tri_orig, 3 * (size_t)nt, &dummy) != cudaSuccess ||
+            dalloc(&v->vmoved, (size_t)nv, &dummy) != cudaSuccess || dalloc(&v->slist, (size_t)nt, &dummy) != cudaSuccess ||
+            dalloc(&v->dlist, (size_t)nt, &dummy) != cudaSuccess)
             return fail(ADGI_ERR_OOM, "scene allocation");
+        v->scene_cap_v = (size_t)nv;
+        v->scene_cap_t = (size_t)nt;
     }
     cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     if (nv) CK(cudaMemcpyAsync(v->verts, verts, sizeof(float) * 3 * (size_t)nv, k, s));
@@ -447,12 +471,20 @@ int adgi_set_scene(adgi_volume v, const float* verts, int32_t nv, const int32_t*
         CK(cudaMemcpyAsync(v->idx, idx, sizeof(int) * 3 * (size_t)nt, k, s));
         CK(cudaMemcpyAsync(v->albedo, albedo, sizeof(float) * 3 * (size_t)nt, k, s));
     }
+    if (nv) CK(cudaMemsetAsync(v->vmoved, 0, (size_t)nv, s));
     v->nv = nv;
     v->nt = nt;
     if (!on_device) CK(cudaStreamSynchronize(s));  // pageable sources are read before return anyway
-    CK(v->bvh.build(v->verts, v->idx, nv, nt, v->eps, v->err, s));
+    // every triangle is static until some of its vertices move
+    v->moved.clear();
+    v->ns = nt;
+    v->nd = 0;
+    v->dbvh.n_tris = 0;
+    CK(fill_tri_orig(v->verts, v->idx, nullptr, nv, nt, v->tri_orig, s));
+    CK(v->sbvh.build(v->verts, v->idx, nv, nt, v->eps, v->err, s, nullptr, true));
     v->has_scene = true;
-    v->bvh_dirty = false;
+    v->split_dirty = false;
+    v->dyn_dirty = false;
     return ADGI_OK;
 }
 
@@ -465,9 +497,63 @@ int adgi_move_vertices(adgi_volume v, int32_t first, int32_t count, const float*
     if (count == 0) return ADGI_OK;
     CK(cudaMemcpyAsync(v->verts + 3 * (size_t)first, verts, sizeof(float) * 3 * (size_t)count,
                        on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, v->stream));
-    v->bvh_dirty = true;
+    // a range not yet known to move makes its triangles part of the moving set
+    bool covered = false;
+    for (auto& r : v->moved)
+        if (r.first <= first && first + count <= r.second) covered = true;
+    if (!covered) {
+        v->moved.push_back({first, first + count});
+        std::sort(v->moved.begin(), v->moved.end());
+        std::vector<std::pair<int, int>> merged;
+        for (auto& r : v->moved) {
+            if (!merged.empty() && r.first <= merged.back().second)
+                merged.back().second = std::max(merged.back().second, r.second);
+            else
+                merged.push_back(r);
+        }
+        v->moved.swap(merged);
+        CK(cudaMemsetAsync(v->vmoved + first, 1, (size_t)count, v->stream));
+        v->split_dirty = true;
+    }
+    v->dyn_dirty = true;
     return ADGI_OK;
 }
+
+namespace {
+// Bring both BVH parts up to date: re-split and rebuild the static part when
+// the moving set grew, rebuild the moving part when its vertices moved.
+int ensure_bvh(adgi_volume v, cudaStream_t s)
+{
+    if (v->split_dirty) {
+        CK(v->sbvh.reserve(v->nt, true));
+        if (!v->sbvh.pscratch) return fail(ADGI_ERR_OOM, "split scratch");
+        CK(split_static_moving(v->idx, v->vmoved, v->nt, v->nv, v->sbvh.pbufs, v->slist, v->dlist, &v->ns, &v->nd, s));
+        CK(v->sbvh.build(v->verts, v->idx, v->nv, v->ns, v->eps, v->err, s, v->slist, true));
+        v->split_dirty = false;
+        v->dyn_dirty = true;
+    }
+    if (v->dyn_dirty) {
+        CK(fill_tri_orig(v->verts, v->idx, v->dlist, v->nv, v->nd, v->tri_orig, s));
+        CK(v->dbvh.build(v->verts, v->idx, v->nv, v->nd, v->eps, v->err, s, v->dlist, false));
+        v->dyn_dirty = false;
+    }
+    return ADGI_OK;
+}
+
+SceneDev scene_view(adgi_volume v)
+{
+    SceneDev S;
+    S.part[0] = v->sbvh.part();
+    S.part[1] = v->dbvh.part();
+    S.n_parts = 2;
+    S.n_tris = v->nt;
+    S.n_verts = v->nv;
+    S.tri_orig = v->tri_orig;
+    S.albedo = v->albedo;
+    S.err = v->err;
+    return S;
+}
+}  // namespace
 
 int adgi_update(adgi_volume v, const adgi_frame* f)
 {
@@ -481,9 +567,9 @@ int adgi_update(adgi_volume v, const adgi_frame* f)
     if (v->timing) CK(cudaEventRecord(v->ph[i], s))
     if (v->timing) CK(cudaEventRecord(v->ev0, s));
     PHASE(0);
-    if (v->bvh_dirty) {
-        CK(v->bvh.build(v->verts, v->idx, v->nv, v->nt, v->eps, v->err, s));
-        v->bvh_dirty = false;
+    {
+        int rc = ensure_bvh(v, s);
+        if (rc) return rc;
     }
     FrameConst F = frame_const(v, f);
     LightSet L;
@@ -495,7 +581,7 @@ int adgi_update(adgi_volume v, const adgi_frame* f)
             L.l[i].rgb[k] = f->lights[i].rgb[k];
         }
     }
-    SceneDev S = v->bvh.view(v->albedo, v->nv, v->err);
+    SceneDev S = scene_view(v);
     CK(cudaMemsetAsync(v->shadow_ctr, 0, 8, s));
     // shadow-job capacity: one job per lit light of every ray of the larger set
     {
@@ -589,9 +675,9 @@ int adgi_get_stats(adgi_volume v, adgi_stats* out)
     int ef = 0;
     CK(cudaMemcpy(&ef, v->err, 4, cudaMemcpyDeviceToHost));
     if (ef) return fail(ADGI_ERR_CUDA, "device anomaly flags set: " + std::to_string(ef));
-    out->bvh_nodes = v->nt > 1 ? (uint32_t)(v->nt - 1) : 0u;
+    out->bvh_nodes = (uint32_t)((v->ns > 1 ? v->ns - 1 : 0) + (v->nd > 1 ? v->nd - 1 : 0));
     out->n_tris = (uint32_t)v->nt;
-    out->device_bytes = v->bytes + v->bvh.bytes();
+    out->device_bytes = v->bytes + v->sbvh.bytes() + v->dbvh.bytes();
     out->kernels_launched = adgi::kernels_launched();
     if (v->timed_pending) {
         float ms = 0.f;
@@ -605,6 +691,11 @@ int adgi_get_stats(adgi_volume v, adgi_stats* out)
 int adgi_state_bytes(adgi_volume v, int32_t which, uint64_t* bytes)
 {
     if (!v || !bytes) return fail(ADGI_ERR_INVALID_ARG, "NULL argument");
+    if ((which == ADGI_STATE_BVH_NODES || which == ADGI_STATE_BVH_TRIS || which == ADGI_STATE_MOVING_BVH_NODES ||
+         which == ADGI_STATE_MOVING_BVH_TRIS) && v->has_scene) {
+        int rc = ensure_bvh(v, v->stream);  // sizes depend on the static/moving split
+        if (rc) return rc;
+    }
     const uint64_t P = (uint64_t)v->V.P, R = v->R_main;
     const uint64_t ti2 = (uint64_t)v->V.Ti * v->V.Ti, td2 = (uint64_t)v->V.Td * v->V.Td;
     switch (which) {
@@ -624,8 +715,10 @@ int adgi_state_bytes(adgi_volume v, int32_t which, uint64_t* bytes)
     case ADGI_STATE_DEP: *bytes = P * td2 * (v->V.fp16 ? 4 : 8); break;
     case ADGI_STATE_DEP_N: *bytes = P * td2; break;
     case ADGI_STATE_ROT: *bytes = 36; break;
-    case ADGI_STATE_BVH_NODES: *bytes = 64 * (uint64_t)(v->nt > 1 ? v->nt - 1 : 1); break;
-    case ADGI_STATE_BVH_TRIS: *bytes = 48 * (uint64_t)v->nt; break;
+    case ADGI_STATE_BVH_NODES: *bytes = 64 * (uint64_t)(v->ns > 1 ? v->ns - 1 : 1); break;
+    case ADGI_STATE_BVH_TRIS: *bytes = 48 * (uint64_t)v->ns; break;
+    case ADGI_STATE_MOVING_BVH_NODES: *bytes = 64 * (uint64_t)(v->nd > 1 ? v->nd - 1 : 1); break;
+    case ADGI_STATE_MOVING_BVH_TRIS: *bytes = 48 * (uint64_t)v->nd; break;
     default: return fail(ADGI_ERR_INVALID_ARG, "unknown state");
     }
     return ADGI_OK;
@@ -633,6 +726,11 @@ int adgi_state_bytes(adgi_volume v, int32_t which, uint64_t* bytes)
 
 int adgi_read_state(adgi_volume v, int32_t which, void* dst, uint64_t bytes)
 {
+    if (v && (which == ADGI_STATE_BVH_NODES || which == ADGI_STATE_BVH_TRIS || which == ADGI_STATE_MOVING_BVH_NODES ||
+              which == ADGI_STATE_MOVING_BVH_TRIS) && v->has_scene) {
+        int rc = ensure_bvh(v, v->stream);
+        if (rc) return rc;
+    }
     uint64_t need = 0;
     int rc = adgi_state_bytes(v, which, &need);
     if (rc) return rc;
@@ -643,6 +741,7 @@ int adgi_read_state(adgi_volume v, int32_t which, void* dst, uint64_t bytes)
         return ADGI_OK;
     }
     const void* src = nullptr;
+    int count_tris = -1;
     switch (which) {
     case ADGI_STATE_W: src = v->W; break;
     case ADGI_STATE_N: src = v->n; break;
@@ -659,14 +758,15 @@ int adgi_read_state(adgi_volume v, int32_t which, void* dst, uint64_t bytes)
     case ADGI_STATE_IRR: src = v->irr; break;
     case ADGI_STATE_DEP: src = v->dep; break;
     case ADGI_STATE_DEP_N: src = v->dep_n; break;
-    case ADGI_STATE_BVH_NODES: src = v->bvh.nodes; break;
-    case ADGI_STATE_BVH_TRIS: src = v->bvh.tri_v; break;
+    case ADGI_STATE_BVH_NODES: src = v->sbvh.nodes; count_tris = v->ns; break;
+    case ADGI_STATE_BVH_TRIS: src = v->sbvh.tri_v; count_tris = v->ns; break;
+    case ADGI_STATE_MOVING_BVH_NODES: src = v->dbvh.nodes; count_tris = v->nd; break;
+    case ADGI_STATE_MOVING_BVH_TRIS: src = v->dbvh.tri_v; count_tris = v->nd; break;
     }
-    if ((which == ADGI_STATE_BVH_NODES && v->nt < 2) || (which == ADGI_STATE_BVH_TRIS && v->nt == 0) ||
-        (which == ADGI_STATE_BVH_NODES && v->bvh_dirty)) {
-        std::memset(dst, 0, bytes);
-        if (!(which == ADGI_STATE_BVH_NODES && v->bvh_dirty)) return ADGI_OK;
-        return fail(ADGI_ERR_INVALID_ARG, "BVH is rebuilt at the next update");
+    bool nodes = which == ADGI_STATE_BVH_NODES || which == ADGI_STATE_MOVING_BVH_NODES;
+    if (count_tris >= 0 && (count_tris == 0 || (nodes && count_tris < 2))) {
+        std::memset(dst, 0, bytes);  // no tree (0 or 1 triangle)
+        return ADGI_OK;
     }
     if (bytes) CK(cudaMemcpy(dst, src, bytes, cudaMemcpyDeviceToHost));
     return ADGI_OK;
@@ -697,11 +797,11 @@ int adgi_trace_closest(adgi_volume v, const float* o, const float* d, int32_t n,
 {
     if (!v || n < 0 || (n > 0 && (!o || !d || !t_out || !tri_out))) return fail(ADGI_ERR_INVALID_ARG, "bad arguments");
     if (!v->has_scene) return fail(ADGI_ERR_NO_SCENE, "no scene");
-    if (v->bvh_dirty) {
-        CK(v->bvh.build(v->verts, v->idx, v->nv, v->nt, v->eps, v->err, v->stream));
-        v->bvh_dirty = false;
+    {
+        int rc = ensure_bvh(v, v->stream);
+        if (rc) return rc;
     }
-    SceneDev S = v->bvh.view(v->albedo, v->nv, v->err);
+    SceneDev S = scene_view(v);
     CK(launch_trace_list(S, o, d, n, tmin, tmax, t_out, tri_out, v->stream));
     return ADGI_OK;
 }
@@ -732,7 +832,7 @@ int adgi_count_traversal(adgi_volume v, const adgi_frame* f, uint64_t* counts)
     size_t dummy = 0;
     if (dalloc(&d, 8, &dummy) != cudaSuccess) return fail(ADGI_ERR_OOM, "counter buffer");
     cudaError_t e = cudaMemsetAsync(d, 0, 64, s);
-    if (e == cudaSuccess) e = launch_count(v->V, F, L, v->bvh.view(v->albedo, v->nv, v->err), v->off, v->sf, v->R_main, d, s);
+    if (e == cudaSuccess) e = launch_count(v->V, F, L, scene_view(v), v->off, v->sf, v->R_main, d, s);
     unsigned long long h[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     if (e == cudaSuccess) e = cudaMemcpyAsync(h, d, 64, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -759,7 +859,7 @@ int adgi_build_bvh(const float* verts, int32_t nv, const int32_t* idx, int32_t n
     B.nodes = (BNode*)nodes_out;
     int root = -1;
     e = cudaMemsetAsync(B.err, 0, sizeof(int), s);
-    if (e == cudaSuccess) e = build_lbvh(B, verts, idx, nv, nt, eps, B.err, s, &root);
+    if (e == cudaSuccess) e = build_lbvh(B, verts, idx, nv, nt, eps, B.err, s, &root, nullptr);
     int herr = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, B.err, sizeof(int), cudaMemcpyDeviceToHost, s);
     cudaError_t e2 = cudaFreeAsync(scratch, s);

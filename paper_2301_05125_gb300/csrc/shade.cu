@@ -148,14 +148,23 @@ __global__ void __launch_bounds__(128) k_shadow(const __grid_constant__ LightSet
 {
     const unsigned total = min(*job_count, job_cap);
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(shadow_ctr, (unsigned long long)total);
-    for (unsigned j = blockIdx.x * blockDim.x + threadIdx.x; j < total; j += gridDim.x * blockDim.x) {
-        uint4 jb = jobs[j];
-        int l = job_light[j];
-        const Light& Li = L.l[l];
-        float3 xs = make_float3(__uint_as_float(jb.x), __uint_as_float(jb.y), __uint_as_float(jb.z));
-        float3 D = shadow_dir(Li, xs);
-        float thi = Li.kind == 0 ? 1.0f : __int_as_float(0x7F800000);
-        if (!trace_any(S, xs, D, 0.0f, thi)) atomicOr(vis + jb.w, 1ull << l);
+    // rounds of one job per lane with a uniform trip count per warp, and an
+    // explicit reconvergence per round: lanes that finish early wait instead
+    // of running ahead into their next job on their own
+    const unsigned stride = gridDim.x * blockDim.x;
+    const unsigned warp0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31u);
+    for (unsigned base = warp0; base < total; base += stride) {
+        const unsigned j = base + (threadIdx.x & 31u);
+        if (j < total) {
+            uint4 jb = jobs[j];
+            int l = job_light[j];
+            const Light& Li = L.l[l];
+            float3 xs = make_float3(__uint_as_float(jb.x), __uint_as_float(jb.y), __uint_as_float(jb.z));
+            float3 D = shadow_dir(Li, xs);
+            float thi = Li.kind == 0 ? 1.0f : __int_as_float(0x7F800000);
+            if (!trace_any(S, xs, D, 0.0f, thi)) atomicOr(vis + jb.w, 1ull << l);
+        }
+        __syncwarp();
     }
 }
 

@@ -276,6 +276,9 @@ def test_build_bvh_matches_volume_bvh(adgi, scene):
         w = S.Workload(scene, 0, v, np.array([[0, 1, 2], [1, 2, 3]], np.int32)[:nt], np.ones((nt, 3), np.float32),
                        S.box_room(1).volume, 1, (0, 0, 0), lambda f: [])
     gv = gpu_volume(adgi, w)
+    # moving every vertex (to where it is) makes every triangle part of the
+    # moving set, whose BVH is the linear one adgi_build_bvh builds
+    gv.move_vertices(0, w.verts)
     dev = torch.device("cuda")
     nt = w.n_tris
     V = torch.from_numpy(w.verts).to(dev)
@@ -283,8 +286,8 @@ def test_build_bvh_matches_volume_bvh(adgi, scene):
     nodes = torch.zeros(max(nt - 1, 1) * 16, dtype=torch.int32, device=dev)
     tris = torch.zeros(nt * 12, dtype=torch.float32, device=dev)
     adgi.adgi_build_bvh(V, I, adgi.scene_eps(w.verts), nodes, tris, torch.cuda.current_stream().cuda_stream)
-    ref_nodes = gv.state("BVH_NODES", np.int32)
-    ref_tris = gv.state("BVH_TRIS", np.int32)
+    ref_nodes = gv.state("MOVING_BVH_NODES", np.int32)
+    ref_tris = gv.state("MOVING_BVH_TRIS", np.int32)
     if nt > 1:
         np.testing.assert_array_equal(nodes.cpu().numpy(), ref_nodes)
     np.testing.assert_array_equal(tris.cpu().numpy().view(np.int32), ref_tris)
