@@ -72,7 +72,8 @@ typedef struct {
     int32_t rays_max;       /* per-probe cap, <= 4096 */
     float hysteresis;       /* h of the moving average, in [0, 1) (Table cacheDetails: 0.98 / 0.91) */
     float depth_max;        /* depth clamp and miss depth; <= 0 selects 1.5 * voxel diagonal */
-    int32_t atlas_fp16;     /* 1: atlases stored as half, blended in FP32 */
+    int32_t atlas_fp16;     /* 0: FP32 atlases; 1: half, blended in FP32, stored round-to-nearest;
+                               2: half with seeded stochastic rounding (unbiased EMA steps) */
     int32_t tr_theta;       /* trigger decay length theta in frames (Fig. TrCam(a)), >= 1, <= 255 */
 } adgi_volume_desc;
 
@@ -182,7 +183,8 @@ int adgi_enable_timing(adgi_volume vol, int32_t enable);
  *   ADGI_STATE_MAIN_HIT int32[R][2]      as PILOT_HIT, rays in probe order
  *   ADGI_STATE_MAIN_REC float[R][4]
  *   ADGI_STATE_IRR      float[P][Ti][Ti][4] {r,g,b,count} (half[...][4] when atlas_fp16)
- *   ADGI_STATE_DEP      float[P][Td][Td][2] {mean, mean^2} (half[...][2] when atlas_fp16)
+ *   ADGI_STATE_DEP      float[P][Td][Td][2] {mean, variance} of the depth samples (the
+ *                       second moment is variance + mean^2); half[...][2] when atlas_fp16
  *   ADGI_STATE_DEP_N    uint8[P][Td][Td]  depth sample counts
  *   ADGI_STATE_ROT      float[9]          main-ray rotation of the last update
  *   ADGI_STATE_BVH_NODES bytes[max(T-1,1)][64]  nodes of the static part's BVH (T static

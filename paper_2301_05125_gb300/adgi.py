@@ -384,6 +384,12 @@ class Volume:
         dt = np.float16 if self.fp16 else np.float32
         return self.state("DEP", dt).reshape(self.P, self.Td, self.Td, 2).astype(np.float32)
 
+    def dep_moments(self):
+        """depth atlas as {mean, mean^2} (the library stores {mean, variance})."""
+        d = self.dep().astype(np.float64)
+        d[..., 1] = d[..., 1] + d[..., 0] * d[..., 0]
+        return d
+
     def dep_n(self):
         return self.state("DEP_N", np.uint8).reshape(self.P, self.Td, self.Td)
 

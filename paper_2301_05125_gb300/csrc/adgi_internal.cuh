@@ -504,6 +504,20 @@ __device__ __forceinline__ float local_offset(float o, float pb, float t, float 
     return fa(s, fa(e, err));
 }
 
+// Bilinear filter of depth texels {mean, variance}: filtered mean, and the
+// filtered variance sum w var_t + sum w (mean_t - mean)^2 -- the variance of
+// the filtered {d, d^2} moments, formed without cancellation.
+__device__ __forceinline__ void filter_moments(float w00, float w01, float w10, float w11, float2 v00, float2 v01,
+                                               float2 v10, float2 v11, float* mom)
+{
+    float mu = w00 * v00.x + w01 * v01.x + w10 * v10.x + w11 * v11.x;
+    float d00 = v00.x - mu, d01 = v01.x - mu, d10 = v10.x - mu, d11 = v11.x - mu;
+    float var = w00 * (v00.y + d00 * d00) + w01 * (v01.y + d01 * d01) + w10 * (v10.y + d10 * d10) +
+                w11 * (v11.y + d11 * d11);
+    mom[0] = mu;
+    mom[1] = var;
+}
+
 // Depth moments of probe tile p at the direction of dv (not normalised:
 // the octahedral map is scale invariant), FP32 bilinear fractions.
 __device__ __forceinline__ void depth_moments(const VolConst& V, const void* dep, size_t tile, float dx, float dy,
@@ -528,12 +542,12 @@ __device__ __forceinline__ void depth_moments(const VolConst& V, const void* dep
     float2 v00 = dep_load(dep, i00, V.fp16), v01 = dep_load(dep, i00 + 1, V.fp16);
     float2 v10 = dep_load(dep, i00 + T, V.fp16), v11 = dep_load(dep, i00 + T + 1, V.fp16);
     float w00 = (1.f - ax) * (1.f - ay), w01 = ax * (1.f - ay), w10 = (1.f - ax) * ay, w11 = ax * ay;
-    mom[0] = w00 * v00.x + w01 * v01.x + w10 * v10.x + w11 * v11.x;
-    mom[1] = w00 * v00.y + w01 * v01.y + w10 * v10.y + w11 * v11.y;
-    // conditioning of the filtered variance against the fractions: the spread
-    // of the footprint's means (squared) over the floored variance
-    float var = fmaxf(mom[1] - mom[0] * mom[0], fmaxf(1e-3f * mom[1], V.var_min));
-    float s2 = fmaxf(fmaxf(fabsf(v00.y - mom[1]), fabsf(v01.y - mom[1])), fmaxf(fabsf(v10.y - mom[1]), fabsf(v11.y - mom[1])));
+    filter_moments(w00, w01, w10, w11, v00, v01, v10, v11, mom);
+    // conditioning of the filtered variance against the fractions: what a
+    // texel adds to the variance per unit weight, over the floored variance
+    float var = fmaxf(mom[1], fmaxf(1e-3f * (mom[1] + mom[0] * mom[0]), V.var_min));
+    float d00 = v00.x - mom[0], d01 = v01.x - mom[0], d10 = v10.x - mom[0], d11 = v11.x - mom[0];
+    float s2 = fmaxf(fmaxf(v00.y + d00 * d00, v01.y + d01 * d01), fmaxf(v10.y + d10 * d10, v11.y + d11 * d11));
     *cond = s2 / var;
 }
 
@@ -620,8 +634,7 @@ static __device__ __noinline__ void depth_moments_precise(const VolConst& V, con
     float2 v00 = dep_load(dep, i00, V.fp16), v01 = dep_load(dep, i00 + 1, V.fp16);
     float2 v10 = dep_load(dep, i00 + T, V.fp16), v11 = dep_load(dep, i00 + T + 1, V.fp16);
     float w00 = bx * by, w01 = ax * by, w10 = bx * ay, w11 = ax * ay;
-    mom[0] = w00 * v00.x + w01 * v01.x + w10 * v10.x + w11 * v11.x;
-    mom[1] = w00 * v00.y + w01 * v01.y + w10 * v10.y + w11 * v11.y;
+    filter_moments(w00, w01, w10, w11, v00, v01, v10, v11, mom);
 }
 
 // 8-probe trilinear x Chebyshev irradiance query at x = o + t*d (the public
@@ -678,9 +691,9 @@ __device__ __forceinline__ float3 query_irr_at(const VolConst& V, const void* ir
         }
         float wc = 1.f;
         if (dist > mom[0]) {
-            // minimum variance: max(1e-3 mu2, 1e-6 s^2) keeps the weight well
-            // conditioned at the precision of the stored moments
-            float var = fmaxf(mom[1] - mom[0] * mom[0], fmaxf(1e-3f * mom[1], V.var_min));
+            // minimum variance: max(1e-3 mu2, 1e-6 s^2), mu2 = var + mean^2,
+            // keeps the weight well conditioned at the precision of the moments
+            float var = fmaxf(mom[1], fmaxf(1e-3f * (mom[1] + mom[0] * mom[0]), V.var_min));
             float dd = dist - mom[0];
             wc = var / (var + dd * dd);
         }

@@ -224,6 +224,7 @@ int validate_desc(const adgi_volume_desc* d)
         return fail(ADGI_ERR_INVALID_ARG, "need max(rays_min, 8) <= rays_avg <= rays_max <= 4096");
     if (!(d->hysteresis >= 0.0f && d->hysteresis < 1.0f)) return fail(ADGI_ERR_INVALID_ARG, "hysteresis in [0,1)");
     if (d->tr_theta < 1 || d->tr_theta > 255) return fail(ADGI_ERR_INVALID_ARG, "tr_theta in [1,255]");
+    if (d->atlas_fp16 < 0 || d->atlas_fp16 > 2) return fail(ADGI_ERR_INVALID_ARG, "atlas_fp16 in {0,1,2}");
     int64_t P = (int64_t)d->dims[0] * d->dims[1] * d->dims[2];
     if (P * (int64_t)d->rays_avg >= (int64_t)1 << 31) return fail(ADGI_ERR_INVALID_ARG, "ray budget too large");
     return ADGI_OK;
@@ -285,7 +286,7 @@ int adgi_create_volume(const adgi_volume_desc* desc, void* cuda_stream, adgi_vol
     V.m0 = d.rays_min > 8 ? d.rays_min : 8;
     V.rays_max = d.rays_max;
     V.rays_avg = d.rays_avg;
-    V.fp16 = d.atlas_fp16 ? 1 : 0;
+    V.fp16 = d.atlas_fp16 == 2 ? 2 : (d.atlas_fp16 ? 1 : 0);
     const size_t P = (size_t)V.P;
     v->R_main = (uint32_t)((size_t)(d.rays_avg - 8) * P);
     size_t& B = v->bytes;

@@ -260,6 +260,27 @@ __global__ void __launch_bounds__(kAllocThreads) k_allocate(const uint32_t* __re
 // border is refreshed, and the tiles are written back with coalesced stores.
 constexpr int kBlendThreads = 128;
 
+// float -> half with stochastic rounding: round toward zero, then step one
+// half ulp away from zero with probability equal to the remaining fraction
+// (unbiased in expectation; u is a uniform 32-bit hash).  Round-to-nearest
+// cannot move an EMA value by less than half an ulp, so with weight 1-h the
+// stored value would stop short of the target by up to ulp/(2(1-h)).
+__device__ __forceinline__ __half half_sr(float v, uint32_t u)
+{
+    __half h = __float2half_rz(v);
+    float hf = __half2float(h);
+    if (hf == v || !(fabsf(v) < 65504.0f)) return __float2half_rn(v);
+    __half n = __ushort_as_half((unsigned short)(__half_as_ushort(h) + 1));
+    float nf = __half2float(n);
+    float frac = (v - hf) / (nf - hf);
+    return (float)u * 2.3283064365386963e-10f < frac ? n : h;
+}
+
+__device__ __forceinline__ uint32_t sr_bits(uint64_t key, int p, int t, int c)
+{
+    return (uint32_t)splitmix(key ^ ((uint64_t)p << 24) ^ ((uint64_t)t << 4) ^ (uint64_t)c);
+}
+
 __device__ __forceinline__ void border_src(int i, int j, int n, int& si, int& sj)
 {
     if (i == 0 && j == 0) {
@@ -362,12 +383,20 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend(VolConst V, FrameConst 
     for (int t = tid; t < td2; t += kBlendThreads) {
         float k = acc_d[3 * t + 2];
         if (k > 0.f) {
+            // the texel stores {mean, variance}; with batch mean m and batch
+            // variance vb the moving average of {d, d^2} becomes
+            //   mean' = mean + w (m - mean)
+            //   var'  = (1-w) var + w vb + w (1-w) (m - mean)^2
+            // (every term non-negative: no cancellation in storage)
             float2 v = tile_d[t];
             float c = (float)cnt_d[t];
             float w = fmaxf(omh, k / (c + k));
             float ik = 1.0f / k;
-            v.x += w * (acc_d[3 * t] * ik - v.x);
-            v.y += w * (acc_d[3 * t + 1] * ik - v.y);
+            float m = acc_d[3 * t] * ik;
+            float vb = fmaxf(acc_d[3 * t + 1] * ik - m * m, 0.0f);
+            float dm = m - v.x;
+            v.y = (1.0f - w) * v.y + w * vb + w * (1.0f - w) * dm * dm;
+            v.x += w * dm;
             tile_d[t] = v;
             cnt_d[t] = (uint32_t)fminf(c + k, 255.0f);
         }
@@ -390,7 +419,18 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend(VolConst V, FrameConst 
         cnt_d[t] = cnt_d[si * Td + sj];
     }
     __syncthreads();
-    if (V.fp16) {
+    if (V.fp16 == 2) {  // stochastic rounding, seeded by the frame, probe, texel and channel
+        const uint64_t key = F.pilot_key ^ (F.even ? 0x5352ull : 0x5353ull);
+        __half2* hi = reinterpret_cast<__half2*>(B.irr) + 2 * io;
+        for (int t = tid; t < ti2; t += kBlendThreads) {
+            float4 v = tile_i[t];
+            hi[2 * t] = __halves2half2(half_sr(v.x, sr_bits(key, p, t, 0)), half_sr(v.y, sr_bits(key, p, t, 1)));
+            hi[2 * t + 1] = __halves2half2(half_sr(v.z, sr_bits(key, p, t, 2)), __float2half_rn(v.w));
+        }
+        __half2* hd = reinterpret_cast<__half2*>(B.dep) + dof;
+        for (int t = tid; t < td2; t += kBlendThreads)
+            hd[t] = __halves2half2(half_sr(tile_d[t].x, sr_bits(key, p, t, 4)), half_sr(tile_d[t].y, sr_bits(key, p, t, 5)));
+    } else if (V.fp16) {
         __half2* hi = reinterpret_cast<__half2*>(B.irr) + 2 * io;
         for (int t = tid; t < ti2; t += kBlendThreads) {
             float4 v = tile_i[t];
