@@ -230,6 +230,87 @@ def run_reference(args):
     return 0
 
 
+def _batched_section(args, adgi, torch, dev):
+    """Batched form: 24 volumes of uneven size over 6 scenes.  Plain FP32
+    per-volume updates (one after another on one stream) against FP16 atlases
+    updated by one captured graph per tick with autotuned block shapes."""
+    from paper_2301_05125_gb300 import scenegen as S
+
+    ticks = max(3, min(args.steps, 20))
+    out = {}
+    for label, fp16, batched in (("per_volume_fp32", 0, False), ("batched_fp16_graph", 1, True)):
+        ws = S.batched(args.seed, fp16=fp16)
+        stream = torch.cuda.Stream(device=dev)
+        vols = []
+        for w in ws:
+            v = adgi.Volume(stream=stream.cuda_stream, **w.volume)
+            v.set_scene(w.verts, w.idx, w.albedo)
+            vols.append(v)
+        dyn = [torch.from_numpy(np.stack([w.dyn_at(f) for f in range(ticks + 8)]).astype(np.float32)).to(dev)
+               for w in ws]
+        rays = sum(w.rays_per_update for w in ws)
+
+        def frames_of(f):
+            return [adgi.make_frame(f, w.seed, w.lights_at(f), w.sky) for w in ws]
+
+        def move(f):
+            for v, w, d in zip(vols, ws, dyn):
+                v.move_vertices(w.dyn_first, d[f])
+
+        with torch.cuda.stream(stream):
+            move(0)
+            for v, fr in zip(vols, frames_of(0)):
+                adgi.adgi_update(v.h, fr)
+        tuned = []
+        B = None
+        if batched:
+            for v, w in zip(vols, ws):
+                t = adgi.adgi_autotune(v.h, adgi.make_frame(0, w.seed, w.lights_at(0), w.sky), 2)
+                tuned.append([t.trace_block, t.shade_block, t.shadow_blocks_per_sm, t.blend_block])
+            B = adgi.Batch(vols, stream.cuda_stream)
+        f = 1
+        for _ in range(2):  # warm-up ticks (the first one captures the graph)
+            move(f)
+            if batched:
+                B.update(frames_of(f))
+            else:
+                for v, fr in zip(vols, frames_of(f)):
+                    adgi.adgi_update(v.h, fr)
+            f += 1
+        stream.synchronize()
+        ms = []
+        for _ in range(ticks):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            fr = frames_of(f)
+            e0.record(stream)
+            move(f)
+            if batched:
+                B.update(fr)
+            else:
+                for v, x in zip(vols, fr):
+                    adgi.adgi_update(v.h, x)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            f += 1
+        for v in vols:
+            v.stats()
+        if B is not None:
+            B.close()
+        for v in vols:
+            v.close()
+        out[label] = {"rays_per_tick": rays, "ms_per_tick": float(np.mean(ms)), "rays_per_s": rays / (np.mean(ms) / 1e3),
+                      "p50_ms": float(np.percentile(ms, 50)), "p99_ms": float(np.percentile(ms, 99)), "ticks": ticks}
+        if tuned:
+            out[label]["tuning_trace_shade_shadowPerSM_blend"] = tuned
+    out["volumes"] = len(S.batched(args.seed))
+    out["speedup_batched_fp16_vs_per_volume_fp32"] = (out["batched_fp16_graph"]["rays_per_s"] /
+                                                      out["per_volume_fp32"]["rays_per_s"])
+    out["fp16_error_vs_fp64_oracle"] = "see tests/test_gpu_fp16.py: mean 1-4e-4, max 2-4e-3 (atlases), 2.5e-3 (queries)"
+    return out
+
+
 def run_ours(args):
     import torch
 
@@ -376,6 +457,9 @@ def run_ours(args):
                "d2h_bytes_per_step": nq * 12, "ms_per_step": float(np.mean(e2e_ms)),
                "includes": "host->device occluder vertices + 65536-point shading query (positions, normals) "
                            "from pinned memory, update, query results back to the host"}
+    batched = None
+    if rank == 0 and not args.no_batched:
+        batched = _batched_section(args, adgi, torch, dev)
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         times, cores = _cpu_baseline(w, budget_s=args.cpu_budget)
@@ -402,6 +486,7 @@ def run_ours(args):
             "roofline_blend": roof_blend,
             "cpu_baseline": cpu,
             "e2e": e2e,
+            "batched": batched,
             "gpu_launches": int(launches),
             "clocks": clk,
             "wall_s": wall,
@@ -424,6 +509,7 @@ def main():
     ap.add_argument("--fp16", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)

@@ -162,6 +162,48 @@ int adgi_destroy(adgi_volume vol);
  * Additional entry points.
  * ------------------------------------------------------------------------- */
 
+/* adgi_update with the device work as a CUDA graph: the first call (and any
+ * call after the scene, the moving set, the shadow-job capacity or the tuning
+ * changed) captures the update on the volume's stream and instantiates it;
+ * later calls only rewrite the frame-descriptor node's parameters and launch
+ * the graph.  Results are those of adgi_update.  No phase timing. */
+int adgi_update_graph(adgi_volume vol, const adgi_frame* frame);
+
+/* Batched update of several volumes (the batched form of the update): one
+ * CUDA graph launch per tick covers every volume of the batch, each volume on
+ * its own branch of the graph so that their kernels overlap on the device.
+ * The graph is captured on the first tick (and again when a volume's scene,
+ * moving set, shadow-job capacity or tuning changed); later ticks rewrite each
+ * volume's frame-descriptor node and launch the graph once on cuda_stream.
+ * A volume may belong to one live batch at a time; while a batch tick may be
+ * running, order other calls on its volumes after cuda_stream (e.g. by
+ * synchronising it).  Errors: INVALID_ARG (NULL, duplicates), CUDA. */
+typedef struct adgi_batch_s* adgi_batch;
+int adgi_batch_create(const adgi_volume* vols, int32_t n, void* cuda_stream, adgi_batch* out);
+/* frames: host array of n frames, frames[i] for vols[i]. */
+int adgi_batch_update(adgi_batch batch, const adgi_frame* frames);
+int adgi_batch_destroy(adgi_batch batch);
+
+/* Block shapes of a volume's kernels.  adgi_autotune times candidate shapes
+ * of the nearest-hit traversal (64/128/256 threads), the shading wavefront
+ * (prep/finish blocks 64/128/256 x shadow grid of 0 = occupancy, 2, 4, 8
+ * blocks per SM) and the blend (64/128/256 threads per probe tile) on the
+ * volume's own data and keeps the fastest; results do not depend on the
+ * shapes.  It needs one update first, uses that update's rays (reps timed
+ * repetitions per candidate), leaves the atlases and the heuristic state as
+ * they were (blend trials run on the live atlases, restored afterwards) and
+ * recomputes the last update's ray records.  Synchronises the stream. */
+typedef struct {
+    int32_t trace_block;
+    int32_t shade_block;
+    int32_t shadow_blocks_per_sm; /* 0: occupancy limit */
+    int32_t blend_block;
+    float ms_trace, ms_shade, ms_blend; /* best times found by adgi_autotune */
+} adgi_tuning;
+int adgi_autotune(adgi_volume vol, const adgi_frame* frame, int32_t reps, adgi_tuning* out);
+int adgi_set_tuning(adgi_volume vol, const adgi_tuning* tuning);
+int adgi_get_tuning(adgi_volume vol, adgi_tuning* tuning);
+
 /* Use another stream for all later work of the volume (cudaStream_t). */
 int adgi_set_stream(adgi_volume vol, void* cuda_stream);
 

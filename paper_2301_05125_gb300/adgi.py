@@ -61,6 +61,11 @@ class adgi_frame(C.Structure):
     ]
 
 
+class adgi_tuning(C.Structure):
+    _fields_ = [("trace_block", C.c_int32), ("shade_block", C.c_int32), ("shadow_blocks_per_sm", C.c_int32),
+                ("blend_block", C.c_int32), ("ms_trace", C.c_float), ("ms_shade", C.c_float), ("ms_blend", C.c_float)]
+
+
 class adgi_stats(C.Structure):
     _fields_ = [
         ("frames", C.c_uint64),
@@ -82,7 +87,9 @@ PHASES = ["bvh", "pilot_trace", "pilot_shade", "heuristics", "allocation", "trac
 EXPORTED = ["adgi_create_volume", "adgi_set_scene", "adgi_move_vertices", "adgi_update", "adgi_query_irradiance",
             "adgi_get_stats", "adgi_destroy", "adgi_set_stream", "adgi_enable_timing", "adgi_state_bytes",
             "adgi_read_state", "adgi_write_atlas", "adgi_trace_closest", "adgi_count_traversal", "adgi_build_bvh",
-            "adgi_build_bvh_noalloc", "adgi_allocate_rays", "adgi_last_error"]
+            "adgi_build_bvh_noalloc", "adgi_allocate_rays", "adgi_update_graph", "adgi_batch_create",
+            "adgi_batch_update", "adgi_batch_destroy", "adgi_autotune", "adgi_set_tuning", "adgi_get_tuning",
+            "adgi_last_error"]
 
 BVH_NOALLOC_MAX_TRIS = 32768
 
@@ -115,6 +122,13 @@ def load(path: str = LIB_PATH):
     L.adgi_count_traversal.argtypes = [vp, C.POINTER(adgi_frame), C.POINTER(C.c_uint64)]
     L.adgi_build_bvh.argtypes = [vp, i32, vp, i32, C.c_float, vp, vp, vp]
     L.adgi_build_bvh_noalloc.argtypes = [vp, i32, vp, i32, C.c_float, vp, vp, vp]
+    L.adgi_update_graph.argtypes = [vp, C.POINTER(adgi_frame)]
+    L.adgi_batch_create.argtypes = [C.POINTER(vp), i32, vp, C.POINTER(vp)]
+    L.adgi_batch_update.argtypes = [vp, C.POINTER(adgi_frame)]
+    L.adgi_batch_destroy.argtypes = [vp]
+    L.adgi_autotune.argtypes = [vp, C.POINTER(adgi_frame), i32, C.POINTER(adgi_tuning)]
+    L.adgi_set_tuning.argtypes = [vp, C.POINTER(adgi_tuning)]
+    L.adgi_get_tuning.argtypes = [vp, C.POINTER(adgi_tuning)]
     L.adgi_last_error.restype = C.c_char_p
     for name in EXPORTED[:-1]:
         getattr(L, name).restype = C.c_int
@@ -248,6 +262,42 @@ def adgi_allocate_rays(W, rays_avg, rays_min, rays_max, n_out, off_out, stream=N
                                      _ptr(n_out), _ptr(off_out), stream))
 
 
+def adgi_update_graph(vol, frame: adgi_frame):
+    _check(load().adgi_update_graph(vol, C.byref(frame)))
+
+
+def adgi_batch_create(vols, stream=None):
+    arr = (C.c_void_p * len(vols))(*[v.value if isinstance(v, C.c_void_p) else v for v in vols])
+    h = C.c_void_p()
+    _check(load().adgi_batch_create(arr, len(vols), stream, C.byref(h)))
+    return h
+
+
+def adgi_batch_update(batch, frames):
+    arr = (adgi_frame * len(frames))(*frames)
+    _check(load().adgi_batch_update(batch, arr))
+
+
+def adgi_batch_destroy(batch):
+    _check(load().adgi_batch_destroy(batch))
+
+
+def adgi_autotune(vol, frame: adgi_frame, reps=3) -> adgi_tuning:
+    t = adgi_tuning()
+    _check(load().adgi_autotune(vol, C.byref(frame), int(reps), C.byref(t)))
+    return t
+
+
+def adgi_set_tuning(vol, t: adgi_tuning):
+    _check(load().adgi_set_tuning(vol, C.byref(t)))
+
+
+def adgi_get_tuning(vol) -> adgi_tuning:
+    t = adgi_tuning()
+    _check(load().adgi_get_tuning(vol, C.byref(t)))
+    return t
+
+
 def adgi_last_error() -> str:
     return load().adgi_last_error().decode(errors="replace")
 
@@ -325,6 +375,12 @@ class Volume:
     def update(self, frame, seed, lights, sky=(0, 0, 0), camera=None):
         adgi_update(self.h, make_frame(frame, seed, lights, sky, camera))
 
+    def update_graph(self, frame, seed, lights, sky=(0, 0, 0), camera=None):
+        adgi_update_graph(self.h, make_frame(frame, seed, lights, sky, camera))
+
+    def autotune(self, frame, seed, lights, sky=(0, 0, 0), reps=3):
+        return adgi_autotune(self.h, make_frame(frame, seed, lights, sky), reps)
+
     def query(self, pos, nrm, out=None):
         if isinstance(pos, np.ndarray):
             pos = np.ascontiguousarray(pos, np.float32)
@@ -401,6 +457,30 @@ class Volume:
         adgi_write_atlas(self.h, None if irr is None else np.ascontiguousarray(irr, dt),
                          None if dep is None else np.ascontiguousarray(dep, dt),
                          None if dep_n is None else np.ascontiguousarray(dep_n, np.uint8))
+
+
+class Batch:
+    """Owning wrapper of an adgi_batch: one graph launch per tick for all volumes."""
+
+    def __init__(self, volumes, stream=None):
+        self.volumes = list(volumes)
+        self.h = adgi_batch_create([v.h for v in self.volumes], stream)
+
+    def update(self, frames):
+        """frames: list of adgi_frame (make_frame), one per volume."""
+        self._keep = frames
+        adgi_batch_update(self.h, frames)
+
+    def close(self):
+        if self.h:
+            adgi_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def hit_tri(hit):

@@ -143,6 +143,14 @@ struct adgi_volume_s {
     float4* m_rec = nullptr;
     unsigned long long* shadow_ctr = nullptr;
     int* err = nullptr;  // device anomaly flags
+    FrameDev* fdev = nullptr;  // per-frame descriptor read by the kernels
+    Tuning tune;               // block shapes (autotuner)
+    // captured graph of the update (adgi_update_graph)
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    cudaGraphNode_t gset = nullptr;
+    bool graph_ok = false;
+    cudaStream_t cap_stream = nullptr;  // private stream the graph is captured on
     // shading wavefront
     unsigned long long* vis = nullptr;
     uint4* jobs = nullptr;
@@ -190,7 +198,7 @@ void free_volume(adgi_volume v)
                     v->qv_even, v->qr_even, v->amp_v,  v->amp_r, v->trv,     v->trr,     v->age_v,  v->age_r,
                     v->G,       v->W,       v->n,      v->off,   v->pil_hit, v->pil_rec, v->pil_lum, v->m_hit,
                     v->m_rec,   v->shadow_ctr, v->verts, v->idx, v->albedo,  v->q_buf, v->err,
-                    v->vis,     v->jobs,    v->job_light, v->job_count};
+                    v->vis,     v->jobs,    v->job_light, v->job_count, v->fdev};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     v->sbvh.release();
@@ -203,6 +211,9 @@ void free_volume(adgi_volume v)
     if (v->ev1) cudaEventDestroy(v->ev1);
     for (cudaEvent_t e : v->ph)
         if (e) cudaEventDestroy(e);
+    if (v->gexec) cudaGraphExecDestroy(v->gexec);
+    if (v->graph) cudaGraphDestroy(v->graph);
+    if (v->cap_stream) cudaStreamDestroy(v->cap_stream);
     delete v;
 }
 
@@ -343,6 +354,7 @@ int adgi_create_volume(const adgi_volume_desc* desc, void* cuda_stream, adgi_vol
     DA(v->m_rec, (size_t)v->R_main);
     DA(v->shadow_ctr, 1);
     DA(v->err, 1);
+    DA(v->fdev, 1);
     DA(v->vis, std::max<size_t>(P * 8, (size_t)v->R_main));
     DA(v->job_count, 1);
 #undef DA
@@ -370,7 +382,7 @@ int adgi_create_volume(const adgi_volume_desc* desc, void* cuda_stream, adgi_vol
     CKV(cudaMemsetAsync(v->W, 0, P * 4, s));
     CKV(cudaMemsetAsync(v->shadow_ctr, 0, 8, s));
     CKV(cudaMemsetAsync(v->err, 0, 4, s));
-    v->shadow_blocks = shadow_grid_blocks();
+    v->shadow_blocks = shadow_grid_blocks(0);
     CKV(cudaEventCreate(&v->ev0));
     CKV(cudaEventCreate(&v->ev1));
     for (cudaEvent_t& e : v->ph) CKV(cudaEventCreate(&e));
@@ -486,6 +498,7 @@ int adgi_set_scene(adgi_volume v, const float* verts, int32_t nv, const int32_t*
     v->has_scene = true;
     v->split_dirty = false;
     v->dyn_dirty = false;
+    v->graph_ok = false;
     return ADGI_OK;
 }
 
@@ -523,7 +536,7 @@ int adgi_move_vertices(adgi_volume v, int32_t first, int32_t count, const float*
 namespace {
 // Bring both BVH parts up to date: re-split and rebuild the static part when
 // the moving set grew, rebuild the moving part when its vertices moved.
-int ensure_bvh(adgi_volume v, cudaStream_t s)
+int ensure_bvh(adgi_volume v, cudaStream_t s, bool moving_too = true)
 {
     if (v->split_dirty) {
         CK(v->sbvh.reserve(v->nt, true));
@@ -533,7 +546,7 @@ int ensure_bvh(adgi_volume v, cudaStream_t s)
         v->split_dirty = false;
         v->dyn_dirty = true;
     }
-    if (v->dyn_dirty) {
+    if (v->dyn_dirty && moving_too) {
         CK(fill_tri_orig(v->verts, v->idx, v->dlist, v->nv, v->nd, v->tri_orig, s));
         CK(v->dbvh.build(v->verts, v->idx, v->nv, v->nd, v->eps, v->err, s, v->dlist, false));
         v->dyn_dirty = false;
@@ -556,7 +569,13 @@ SceneDev scene_view(adgi_volume v)
 }
 }  // namespace
 
-int adgi_update(adgi_volume v, const adgi_frame* f)
+namespace {
+
+// Host side of an update: validate, bring the BVH parts up to date (may
+// synchronise: never inside a capture), build the frame descriptor, and make
+// room for the shadow jobs.  Sets *graph_stale when a captured graph of this
+// volume can no longer be replayed.
+int prepare_update(adgi_volume v, const adgi_frame* f, FrameDev& fd, bool* graph_stale)
 {
     if (!v || !f) return fail(ADGI_ERR_INVALID_ARG, "NULL argument");
     if (!v->has_scene) return fail(ADGI_ERR_NO_SCENE, "no scene");
@@ -564,74 +583,425 @@ int adgi_update(adgi_volume v, const adgi_frame* f)
         return fail(ADGI_ERR_INVALID_ARG, "bad light list");
     cudaStream_t s = v->stream;
     const VolConst& V = v->V;
-#define PHASE(i) \
-    if (v->timing) CK(cudaEventRecord(v->ph[i], s))
-    if (v->timing) CK(cudaEventRecord(v->ev0, s));
-    PHASE(0);
+    bool stale = false;
+    if (v->split_dirty) stale = true;
     {
-        int rc = ensure_bvh(v, s);
+        int rc = ensure_bvh(v, s, false);  // the moving part is rebuilt inside the update itself
         if (rc) return rc;
     }
-    FrameConst F = frame_const(v, f);
-    LightSet L;
-    L.n = f->n_lights;
+    if (v->nd > 0) CK(v->dbvh.reserve(v->nd, false));  // no allocation inside a captured update
+    const unsigned sb = shadow_grid_blocks(v->tune.shadow_mult);
+    if (sb != v->shadow_blocks) {
+        v->shadow_blocks = sb;
+        stale = true;
+    }
+    fd.F = frame_const(v, f);
+    fd.L.n = f->n_lights;
     for (int i = 0; i < f->n_lights; ++i) {
-        L.l[i].kind = f->lights[i].kind;
+        fd.L.l[i].kind = f->lights[i].kind;
         for (int k = 0; k < 3; ++k) {
-            L.l[i].v[k] = f->lights[i].pos_or_dir[k];
-            L.l[i].rgb[k] = f->lights[i].rgb[k];
+            fd.L.l[i].v[k] = f->lights[i].pos_or_dir[k];
+            fd.L.l[i].rgb[k] = f->lights[i].rgb[k];
         }
     }
-    SceneDev S = scene_view(v);
-    CK(cudaMemsetAsync(v->shadow_ctr, 0, 8, s));
     // shadow-job capacity: one job per lit light of every ray of the larger set
-    {
-        size_t need = (size_t)f->n_lights * std::max<size_t>((size_t)V.P * kPilots, (size_t)v->R_main);
-        if (need > v->job_cap) {
-            cudaFree(v->jobs);
-            cudaFree(v->job_light);
-            v->jobs = nullptr;
-            v->job_light = nullptr;
-            v->job_cap = 0;
-            size_t dummy = 0;
-            if (dalloc(&v->jobs, need, &dummy) != cudaSuccess || dalloc(&v->job_light, need, &dummy) != cudaSuccess)
-                return fail(ADGI_ERR_OOM, "shadow job buffer");
-            v->job_cap = need;
-        }
+    size_t need = (size_t)f->n_lights * std::max<size_t>((size_t)V.P * kPilots, (size_t)v->R_main);
+    if (need > v->job_cap) {
+        cudaFree(v->jobs);
+        cudaFree(v->job_light);
+        v->jobs = nullptr;
+        v->job_light = nullptr;
+        v->job_cap = 0;
+        size_t dummy = 0;
+        if (dalloc(&v->jobs, need, &dummy) != cudaSuccess || dalloc(&v->job_light, need, &dummy) != cudaSuccess)
+            return fail(ADGI_ERR_OOM, "shadow job buffer");
+        v->job_cap = need;
+        stale = true;
     }
+    if (graph_stale) *graph_stale = stale;
+    return ADGI_OK;
+}
+
+// The device work of one update, in order, on stream s (capturable).  The
+// frame descriptor fd is written to the device by the first kernel; when
+// set_node is given, the captured node of that kernel is returned there.
+int enqueue_update(adgi_volume v, const FrameDev& fd, cudaStream_t s, bool phases, cudaGraphNode_t* set_node)
+{
+    const VolConst& V = v->V;
+    const Tuning& T = v->tune;
+#define PHASE(i) \
+    if (phases) CK(cudaEventRecord(v->ph[i], s))
+    if (phases) CK(cudaEventRecord(v->ev0, s));
+    CK(launch_set_frame(v->fdev, fd, s));
+    if (set_node) {
+        cudaStreamCaptureStatus st;
+        const cudaGraphNode_t* deps = nullptr;
+        size_t nd = 0;
+        CK(cudaStreamGetCaptureInfo(s, &st, nullptr, nullptr, &deps, nullptr, &nd));
+        if (st != cudaStreamCaptureStatusActive || nd != 1) return fail(ADGI_ERR_CUDA, "capture: set-frame node");
+        *set_node = deps[0];
+    }
+    PHASE(0);
+    // the moving part of the scene: refresh its vertices and rebuild its BVH
+    if (v->nd > 0 && (v->dyn_dirty || set_node)) {
+        CK(fill_tri_orig(v->verts, v->idx, v->dlist, v->nv, v->nd, v->tri_orig, s));
+        CK(v->dbvh.build(v->verts, v->idx, v->nv, v->nd, v->eps, v->err, s, v->dlist, false));
+    }
+    if (!set_node) v->dyn_dirty = false;
+    SceneDev S = scene_view(v);
+    const FrameDev* FD = v->fdev;
+    CK(cudaMemsetAsync(v->shadow_ctr, 0, 8, s));
     ShadeWork W{v->vis, v->jobs, v->job_light, v->job_count, (unsigned)std::min<size_t>(v->job_cap, 0xFFFFFFFFu),
                 v->shadow_blocks, v->shadow_ctr};
     // 1. pilot rays (trace + shade; the shading reads the previous atlases)
     PHASE(1);
-    CK(launch_pilot_trace(V, F, S, v->pil_hit, s));
+    CK(launch_pilot_trace(V, FD, S, v->pil_hit, T, s));
     PHASE(2);
-    CK(launch_shade(V, F, L, S, 0, (uint32_t)V.P * kPilots, nullptr, nullptr, v->irr, v->dep, v->pil_hit, v->pil_rec,
-                    v->pil_lum, F.even, W, s));
+    CK(launch_shade(V, FD, S, 0, (uint32_t)V.P * kPilots, nullptr, nullptr, v->irr, v->dep, v->pil_hit, v->pil_rec,
+                    v->pil_lum, W, T, s));
     // 2. heuristics -> W_p
     PHASE(3);
     ChangeBufs C{v->pil_hit, v->pil_lum, v->lut_v, v->lut_c, v->qv,  v->qr,  v->qv_even, v->qr_even,
                  v->amp_v,   v->amp_r,   v->age_v, v->age_r, v->trv, v->trr, v->G,       v->W};
-    CK(launch_change(V, F, C, s));
+    CK(launch_change(V, FD, C, s));
     // 3. allocation
     PHASE(4);
     CK(launch_allocate(v->W, V.P, V.rays_avg, V.m0, V.rays_max, v->n, v->off, s));
     // 4-5. adaptive rays: trace, shade
     PHASE(5);
-    CK(launch_main_trace(V, F, S, v->off, v->sf, v->R_main, v->m_hit, s));
+    CK(launch_main_trace(V, FD, S, v->off, v->sf, v->R_main, v->m_hit, T, s));
     PHASE(6);
-    CK(launch_shade(V, F, L, S, 1, v->R_main, v->off, v->sf, v->irr, v->dep, v->m_hit, v->m_rec, nullptr, 1, W, s));
+    CK(launch_shade(V, FD, S, 1, v->R_main, v->off, v->sf, v->irr, v->dep, v->m_hit, v->m_rec, nullptr, W, T, s));
     // 6. blend (after every read of the previous atlases)
     PHASE(7);
     BlendBufs Bb{v->off, v->sf, v->pil_rec, v->m_rec, v->irr, v->dep, v->dep_n};
-    CK(launch_blend(V, F, Bb, s));
+    CK(launch_blend(V, FD, Bb, T, s));
     PHASE(8);
 #undef PHASE
-    if (v->timing) {
+    if (phases) {
         CK(cudaEventRecord(v->ev1, s));
         v->timed_pending = true;
     }
-    if (F.even) v->last_even = (int64_t)f->frame;
+    return ADGI_OK;
+}
+
+void finish_update(adgi_volume v, const FrameDev& fd, const adgi_frame* f)
+{
+    if (fd.F.even) v->last_even = (int64_t)f->frame;
     v->frames += 1;
+}
+
+}  // namespace
+
+int adgi_update(adgi_volume v, const adgi_frame* f)
+{
+    FrameDev fd;
+    int rc = prepare_update(v, f, fd, nullptr);
+    if (rc) return rc;
+    rc = enqueue_update(v, fd, v->stream, v->timing, nullptr);
+    if (rc) return rc;
+    finish_update(v, fd, f);
+    return ADGI_OK;
+}
+
+namespace {
+
+cudaError_t capture_end(cudaStream_t s, cudaGraph_t* g)
+{
+    cudaGraph_t tmp = nullptr;
+    cudaError_t e = cudaStreamEndCapture(s, &tmp);
+    *g = tmp;
+    return e;
+}
+
+}  // namespace
+
+int adgi_update_graph(adgi_volume v, const adgi_frame* f)
+{
+    FrameDev fd;
+    bool stale = false;
+    int rc = prepare_update(v, f, fd, &stale);
+    if (rc) return rc;
+    cudaStream_t s = v->stream;
+    if (stale || !v->graph_ok) {
+        if (v->gexec) cudaGraphExecDestroy(v->gexec);
+        if (v->graph) cudaGraphDestroy(v->graph);
+        v->gexec = nullptr;
+        v->graph = nullptr;
+        v->graph_ok = false;
+        if (!v->cap_stream) CK(cudaStreamCreateWithFlags(&v->cap_stream, cudaStreamNonBlocking));
+        CK(cudaStreamSynchronize(s));  // preparation work queued on the volume's stream
+        CK(cudaStreamBeginCapture(v->cap_stream, cudaStreamCaptureModeThreadLocal));
+        rc = enqueue_update(v, fd, v->cap_stream, false, &v->gset);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = capture_end(v->cap_stream, &g);
+        if (rc) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+        if (e != cudaSuccess) return fail(ADGI_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(e));
+        v->graph = g;
+        CK(cudaGraphInstantiate(&v->gexec, v->graph, 0));
+        v->graph_ok = true;
+    } else {
+        cudaKernelNodeParams kp;
+        void* args[2];
+        FrameDev* dst = v->fdev;
+        set_frame_node_params(&dst, &fd, &kp, args);
+        CK(cudaGraphExecKernelNodeSetParams(v->gexec, v->gset, &kp));
+    }
+    CK(cudaGraphLaunch(v->gexec, s));
+    finish_update(v, fd, f);
+    v->dyn_dirty = false;
+    return ADGI_OK;
+}
+
+struct adgi_batch_s {
+    std::vector<adgi_volume> vols;
+    cudaStream_t stream = nullptr;
+    std::vector<cudaStream_t> side;
+    cudaEvent_t fork = nullptr;
+    std::vector<cudaEvent_t> join;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<cudaGraphNode_t> setn;
+    bool ok = false;
+};
+
+namespace {
+void free_batch(adgi_batch b)
+{
+    if (!b) return;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    for (cudaStream_t st : b->side)
+        if (st) cudaStreamDestroy(st);
+    for (cudaEvent_t e : b->join)
+        if (e) cudaEventDestroy(e);
+    if (b->fork) cudaEventDestroy(b->fork);
+    delete b;
+}
+}  // namespace
+
+int adgi_batch_create(const adgi_volume* vols, int32_t n, void* cuda_stream, adgi_batch* out)
+{
+    if (!out || !vols || n <= 0 || n > 4096) return fail(ADGI_ERR_INVALID_ARG, "bad batch arguments");
+    *out = nullptr;
+    for (int i = 0; i < n; ++i) {
+        if (!vols[i]) return fail(ADGI_ERR_INVALID_ARG, "NULL volume in batch");
+        for (int j = 0; j < i; ++j)
+            if (vols[j] == vols[i]) return fail(ADGI_ERR_INVALID_ARG, "a volume appears twice in the batch");
+    }
+    adgi_batch b = new adgi_batch_s();
+    b->vols.assign(vols, vols + n);
+    b->stream = (cudaStream_t)cuda_stream;
+    b->side.assign(n, nullptr);
+    b->join.assign(n, nullptr);
+    b->setn.assign(n, nullptr);
+    cudaError_t e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+    for (int i = 0; i < n && e == cudaSuccess; ++i) {
+        e = cudaStreamCreateWithFlags(&b->side[i], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join[i], cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) {
+        free_batch(b);
+        return fail(ADGI_ERR_CUDA, std::string("batch: ") + cudaGetErrorString(e));
+    }
+    *out = b;
+    return ADGI_OK;
+}
+
+int adgi_batch_update(adgi_batch b, const adgi_frame* frames)
+{
+    if (!b || !frames) return fail(ADGI_ERR_INVALID_ARG, "NULL argument");
+    const int n = (int)b->vols.size();
+    std::vector<FrameDev> fd(n);
+    bool stale = !b->ok;
+    for (int i = 0; i < n; ++i) {
+        bool st = false;
+        int rc = prepare_update(b->vols[i], &frames[i], fd[i], &st);
+        if (rc) return rc;
+        stale = stale || st;
+    }
+    if (stale) {
+        // a static-part rebuild may have been queued on a volume's own stream
+        for (int i = 0; i < n; ++i) CK(cudaStreamSynchronize(b->vols[i]->stream));
+        if (b->exec) cudaGraphExecDestroy(b->exec);
+        if (b->graph) cudaGraphDestroy(b->graph);
+        b->exec = nullptr;
+        b->graph = nullptr;
+        b->ok = false;
+        CK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+        int rc = ADGI_OK;
+        cudaError_t e = cudaEventRecord(b->fork, b->stream);
+        for (int i = 0; i < n && !rc && e == cudaSuccess; ++i) {
+            e = cudaStreamWaitEvent(b->side[i], b->fork, 0);
+            if (e == cudaSuccess) rc = enqueue_update(b->vols[i], fd[i], b->side[i], false, &b->setn[i]);
+            if (!rc && e == cudaSuccess) e = cudaEventRecord(b->join[i], b->side[i]);
+            if (!rc && e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->join[i], 0);
+        }
+        cudaGraph_t g = nullptr;
+        cudaError_t e2 = capture_end(b->stream, &g);
+        if (rc || e != cudaSuccess || e2 != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            if (rc) return rc;
+            return fail(ADGI_ERR_CUDA, std::string("batch capture: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
+        }
+        b->graph = g;
+        CK(cudaGraphInstantiate(&b->exec, b->graph, 0));
+        b->ok = true;
+    } else {
+        for (int i = 0; i < n; ++i) {
+            cudaKernelNodeParams kp;
+            void* args[2];
+            FrameDev* dst = b->vols[i]->fdev;
+            set_frame_node_params(&dst, &fd[i], &kp, args);
+            CK(cudaGraphExecKernelNodeSetParams(b->exec, b->setn[i], &kp));
+        }
+    }
+    CK(cudaGraphLaunch(b->exec, b->stream));
+    for (int i = 0; i < n; ++i) {
+        finish_update(b->vols[i], fd[i], &frames[i]);
+        b->vols[i]->dyn_dirty = false;
+    }
+    return ADGI_OK;
+}
+
+int adgi_batch_destroy(adgi_batch b)
+{
+    if (!b) return ADGI_OK;
+    cudaStreamSynchronize(b->stream);
+    free_batch(b);
+    return ADGI_OK;
+}
+
+int adgi_set_tuning(adgi_volume v, const adgi_tuning* t)
+{
+    if (!v || !t) return fail(ADGI_ERR_INVALID_ARG, "NULL argument");
+    auto okb = [](int x) { return x == 32 || x == 64 || x == 128 || x == 256; };
+    if (!okb(t->trace_block) || !okb(t->shade_block) || !okb(t->blend_block) || t->shadow_blocks_per_sm < 0 ||
+        t->shadow_blocks_per_sm > 64)
+        return fail(ADGI_ERR_INVALID_ARG, "block sizes must be 32, 64, 128 or 256");
+    v->tune.trace_block = t->trace_block;
+    v->tune.shade_block = t->shade_block;
+    v->tune.blend_block = t->blend_block;
+    v->tune.shadow_mult = t->shadow_blocks_per_sm;
+    v->graph_ok = false;
+    return ADGI_OK;
+}
+
+int adgi_get_tuning(adgi_volume v, adgi_tuning* t)
+{
+    if (!v || !t) return fail(ADGI_ERR_INVALID_ARG, "NULL argument");
+    std::memset(t, 0, sizeof(*t));
+    t->trace_block = v->tune.trace_block;
+    t->shade_block = v->tune.shade_block;
+    t->blend_block = v->tune.blend_block;
+    t->shadow_blocks_per_sm = v->tune.shadow_mult;
+    return ADGI_OK;
+}
+
+int adgi_autotune(adgi_volume v, const adgi_frame* f, int32_t reps, adgi_tuning* out)
+{
+    if (!v || !f) return fail(ADGI_ERR_INVALID_ARG, "NULL argument");
+    if (v->frames == 0) return fail(ADGI_ERR_INVALID_ARG, "autotune needs one update first");
+    if (reps < 1) reps = 1;
+    FrameDev fd;
+    int rc = prepare_update(v, f, fd, nullptr);
+    if (rc) return rc;
+    cudaStream_t s = v->stream;
+    const VolConst& V = v->V;
+    SceneDev S = scene_view(v);
+    CK(launch_set_frame(v->fdev, fd, s));
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    auto timed = [&](auto&& body, float* ms) -> int {
+        cudaError_t e = cudaEventRecord(e0, s);
+        for (int r = 0; r < reps && e == cudaSuccess; ++r) e = body();
+        if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(ms, e0, e1);
+        if (e != cudaSuccess) return fail(ADGI_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(e));
+        *ms /= (float)reps;
+        return ADGI_OK;
+    };
+    const int blocks[3] = {64, 128, 256};
+    Tuning best = v->tune;
+    float t_trace = 1e30f, t_shade = 1e30f, t_blend = 1e30f;
+    for (int b : blocks) {  // nearest-hit traversal
+        Tuning T = best;
+        T.trace_block = b;
+        float ms = 0.f;
+        rc = timed([&] { return launch_main_trace(V, v->fdev, S, v->off, v->sf, v->R_main, v->m_hit, T, s); }, &ms);
+        if (rc) break;
+        if (ms < t_trace) {
+            t_trace = ms;
+            best.trace_block = b;
+        }
+    }
+    const int mults[4] = {0, 2, 4, 8};
+    for (int b : blocks) {  // shading wavefront (shadow grid per SM, prep/finish blocks)
+        for (int m : mults) {
+            if (rc) break;
+            Tuning T = best;
+            T.shade_block = b;
+            T.shadow_mult = m;
+            ShadeWork W{v->vis, v->jobs, v->job_light, v->job_count, (unsigned)std::min<size_t>(v->job_cap, 0xFFFFFFFFu),
+                        shadow_grid_blocks(m), v->shadow_ctr};
+            float ms = 0.f;
+            rc = timed([&] {
+                return launch_shade(V, v->fdev, S, 1, v->R_main, v->off, v->sf, v->irr, v->dep, v->m_hit, v->m_rec,
+                                    nullptr, W, T, s);
+            }, &ms);
+            if (!rc && ms < t_shade) {
+                t_shade = ms;
+                best.shade_block = b;
+                best.shadow_mult = m;
+            }
+        }
+    }
+    // blend: trials run on the live atlases, which are restored afterwards
+    uint64_t bi = 0, bd = 0, bn = 0;
+    adgi_state_bytes(v, ADGI_STATE_IRR, &bi);
+    adgi_state_bytes(v, ADGI_STATE_DEP, &bd);
+    adgi_state_bytes(v, ADGI_STATE_DEP_N, &bn);
+    void* keep = nullptr;
+    if (!rc && cudaMalloc(&keep, bi + bd + bn) != cudaSuccess) rc = fail(ADGI_ERR_OOM, "autotune snapshot");
+    if (!rc) {
+        char* k = (char*)keep;
+        CK(cudaMemcpyAsync(k, v->irr, bi, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(k + bi, v->dep, bd, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(k + bi + bd, v->dep_n, bn, cudaMemcpyDeviceToDevice, s));
+        BlendBufs Bb{v->off, v->sf, v->pil_rec, v->m_rec, v->irr, v->dep, v->dep_n};
+        for (int b : blocks) {
+            if (rc) break;
+            Tuning T = best;
+            T.blend_block = b;
+            float ms = 0.f;
+            rc = timed([&] { return launch_blend(V, v->fdev, Bb, T, s); }, &ms);
+            if (!rc && ms < t_blend) {
+                t_blend = ms;
+                best.blend_block = b;
+            }
+        }
+        cudaMemcpyAsync(v->irr, k, bi, cudaMemcpyDeviceToDevice, s);
+        cudaMemcpyAsync(v->dep, k + bi, bd, cudaMemcpyDeviceToDevice, s);
+        cudaMemcpyAsync(v->dep_n, k + bi + bd, bn, cudaMemcpyDeviceToDevice, s);
+        cudaStreamSynchronize(s);
+    }
+    if (keep) cudaFree(keep);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    v->tune = best;
+    v->graph_ok = false;
+    if (out) {
+        adgi_get_tuning(v, out);
+        out->ms_trace = t_trace;
+        out->ms_shade = t_shade;
+        out->ms_blend = t_blend;
+    }
     return ADGI_OK;
 }
 
@@ -817,23 +1187,26 @@ int adgi_count_traversal(adgi_volume v, const adgi_frame* f, uint64_t* counts)
     float Rsave[9];
     std::memcpy(Rsave, v->R, sizeof(Rsave));
     int64_t le = v->last_even;
-    FrameConst F = frame_const(v, f);
+    // the last update's pair state: the frame after an even frame saw it
+    if ((f->frame & 1u) == 1u && v->last_even == (int64_t)f->frame) v->last_even = (int64_t)f->frame - 1;
+    FrameDev fd;
+    fd.F = frame_const(v, f);
     v->last_even = le;
     std::memcpy(v->R, Rsave, sizeof(Rsave));
-    LightSet L;
-    L.n = f->n_lights;
+    fd.L.n = f->n_lights;
     for (int i = 0; i < f->n_lights; ++i) {
-        L.l[i].kind = f->lights[i].kind;
+        fd.L.l[i].kind = f->lights[i].kind;
         for (int k = 0; k < 3; ++k) {
-            L.l[i].v[k] = f->lights[i].pos_or_dir[k];
-            L.l[i].rgb[k] = f->lights[i].rgb[k];
+            fd.L.l[i].v[k] = f->lights[i].pos_or_dir[k];
+            fd.L.l[i].rgb[k] = f->lights[i].rgb[k];
         }
     }
     unsigned long long* d = nullptr;
     size_t dummy = 0;
     if (dalloc(&d, 8, &dummy) != cudaSuccess) return fail(ADGI_ERR_OOM, "counter buffer");
     cudaError_t e = cudaMemsetAsync(d, 0, 64, s);
-    if (e == cudaSuccess) e = launch_count(v->V, F, L, scene_view(v), v->off, v->sf, v->R_main, d, s);
+    if (e == cudaSuccess) e = launch_set_frame(v->fdev, fd, s);
+    if (e == cudaSuccess) e = launch_count(v->V, v->fdev, scene_view(v), v->off, v->sf, v->R_main, d, s);
     unsigned long long h[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     if (e == cudaSuccess) e = cudaMemcpyAsync(h, d, 64, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);

@@ -15,6 +15,21 @@ struct LightSet {
     Light l[kMaxLights];
 };
 
+// Per-frame inputs of one update, kept in device memory so that a captured
+// graph of the update reads each tick's values (written by k_set_frame).
+struct FrameDev {
+    FrameConst F;
+    LightSet L;
+};
+
+// Block shapes of the launch wrappers (picked per volume by the autotuner).
+struct Tuning {
+    int trace_block = 128;   // pilot/adaptive nearest-hit kernels
+    int shade_block = 128;   // shading prep/finish kernels
+    int shadow_mult = 0;     // shadow-ray grid: blocks per SM (0: occupancy)
+    int blend_block = 128;   // blend kernel threads per probe tile
+};
+
 struct ChangeBufs {
     const int2* pil_hit;
     const float* pil_lum;
@@ -55,22 +70,25 @@ struct BlendBufs {
     uint8_t* dep_n;
 };
 
-cudaError_t launch_pilot_trace(const VolConst& V, const FrameConst& F, const SceneDev& S, int2* hit, cudaStream_t s);
-cudaError_t launch_main_trace(const VolConst& V, const FrameConst& F, const SceneDev& S, const uint32_t* off,
-                              const float4* sf, uint32_t R, int2* hit, cudaStream_t s);
-cudaError_t launch_shade(const VolConst& V, const FrameConst& F, const LightSet& L, const SceneDev& S, int mode,
-                         uint32_t n_rays, const uint32_t* off, const float4* sf, const void* irr, const void* dep,
-                         const int2* hit, float4* rec, float* lum, int bounce, const ShadeWork& W, cudaStream_t s);
-unsigned shadow_grid_blocks();
-cudaError_t launch_count(const VolConst& V, const FrameConst& F, const LightSet& L, const SceneDev& S,
-                         const uint32_t* off, const float4* sf, uint32_t R, unsigned long long* out, cudaStream_t s);
+cudaError_t launch_set_frame(FrameDev* dst, const FrameDev& src, cudaStream_t s);
+void set_frame_node_params(FrameDev** dst_slot, const FrameDev* src, cudaKernelNodeParams* kp, void** args);
+cudaError_t launch_pilot_trace(const VolConst& V, const FrameDev* FD, const SceneDev& S, int2* hit, const Tuning& T,
+                               cudaStream_t s);
+cudaError_t launch_main_trace(const VolConst& V, const FrameDev* FD, const SceneDev& S, const uint32_t* off,
+                              const float4* sf, uint32_t R, int2* hit, const Tuning& T, cudaStream_t s);
+cudaError_t launch_shade(const VolConst& V, const FrameDev* FD, const SceneDev& S, int mode, uint32_t n_rays,
+                         const uint32_t* off, const float4* sf, const void* irr, const void* dep, const int2* hit,
+                         float4* rec, float* lum, const ShadeWork& W, const Tuning& T, cudaStream_t s);
+unsigned shadow_grid_blocks(int mult);
+cudaError_t launch_count(const VolConst& V, const FrameDev* FD, const SceneDev& S, const uint32_t* off,
+                         const float4* sf, uint32_t R, unsigned long long* out, cudaStream_t s);
 cudaError_t launch_trace_list(const SceneDev& S, const float* o, const float* d, int n, float tmin, float tmax,
                               float* t_out, int* tri_out, cudaStream_t s);
 
-cudaError_t launch_change(const VolConst& V, const FrameConst& F, const ChangeBufs& B, cudaStream_t s);
+cudaError_t launch_change(const VolConst& V, const FrameDev* FD, const ChangeBufs& B, cudaStream_t s);
 cudaError_t launch_allocate(const uint32_t* W, int P, int avg, int m0, int rmax, uint32_t* n_out, uint32_t* off_out,
                             cudaStream_t s);
-cudaError_t launch_blend(const VolConst& V, const FrameConst& F, const BlendBufs& B, cudaStream_t s);
+cudaError_t launch_blend(const VolConst& V, const FrameDev* FD, const BlendBufs& B, const Tuning& T, cudaStream_t s);
 cudaError_t launch_query(const VolConst& V, const void* irr, const void* dep, const float* pos, const float* nrm, int n,
                          float* out, cudaStream_t s);
 

@@ -93,12 +93,14 @@ __device__ __forceinline__ float3 shadow_dir(const Light& Li, float3 xs)
                         : make_float3(-Li.v[0], -Li.v[1], -Li.v[2]);
 }
 
-__global__ void __launch_bounds__(128) k_shade_prep(VolConst V, FrameConst F, const __grid_constant__ LightSet L,
-                                                    SceneDev S, RaySet Rs, const int2* __restrict__ hit,
+__global__ void __launch_bounds__(256) k_shade_prep(VolConst V, const FrameDev* __restrict__ FD, SceneDev S,
+                                                    RaySet Rs, const int2* __restrict__ hit,
                                                     unsigned long long* __restrict__ vis, uint4* __restrict__ jobs,
                                                     uint8_t* __restrict__ job_light, unsigned* __restrict__ job_count,
                                                     unsigned job_cap)
 {
+    const FrameConst& F = FD->F;
+    const LightSet& L = FD->L;
     __shared__ int s_lo, s_hi;
     block_range(V, Rs, &s_lo, &s_hi);
     const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
@@ -141,11 +143,12 @@ __global__ void __launch_bounds__(128) k_shade_prep(VolConst V, FrameConst F, co
     }
 }
 
-__global__ void __launch_bounds__(128) k_shadow(const __grid_constant__ LightSet L, SceneDev S,
+__global__ void __launch_bounds__(128) k_shadow(const FrameDev* __restrict__ FD, SceneDev S,
                                                 const uint4* __restrict__ jobs, const uint8_t* __restrict__ job_light,
                                                 const unsigned* __restrict__ job_count, unsigned job_cap,
                                                 unsigned long long* __restrict__ vis, unsigned long long* shadow_ctr)
 {
+    const LightSet& L = FD->L;
     const unsigned total = min(*job_count, job_cap);
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(shadow_ctr, (unsigned long long)total);
     // rounds of one job per lane with a uniform trip count per warp, and an
@@ -168,12 +171,17 @@ __global__ void __launch_bounds__(128) k_shadow(const __grid_constant__ LightSet
     }
 }
 
-__global__ void __launch_bounds__(128) k_shade_finish(VolConst V, FrameConst F, const __grid_constant__ LightSet L,
-                                                      SceneDev S, RaySet Rs, const int2* __restrict__ hit,
+__global__ void __launch_bounds__(256) k_shade_finish(VolConst V, const FrameDev* __restrict__ FD, SceneDev S,
+                                                      RaySet Rs, const int2* __restrict__ hit,
                                                       const unsigned long long* __restrict__ vis,
                                                       const void* __restrict__ irr, const void* __restrict__ dep,
-                                                      int bounce, float4* __restrict__ rec, float* __restrict__ lum)
+                                                      float4* __restrict__ rec, float* __restrict__ lum)
 {
+    const FrameConst& F = FD->F;
+    const LightSet& L = FD->L;
+    // adaptive rays always carry the multi-bounce term; pilot records are
+    // blended (so need it) only on the first frame of a pair
+    const int bounce = Rs.mode == 1 || F.even;
     __shared__ int s_lo, s_hi;
     block_range(V, Rs, &s_lo, &s_hi);
     const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
@@ -234,7 +242,7 @@ __global__ void __launch_bounds__(128) k_shade_finish(VolConst V, FrameConst F, 
 
 }  // namespace
 
-unsigned shadow_grid_blocks()
+unsigned shadow_grid_blocks(int mult)
 {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
@@ -242,26 +250,26 @@ unsigned shadow_grid_blocks()
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_shadow, 128, 0);
     if (sms <= 0) sms = 152;
     if (per <= 0) per = 4;
+    if (mult > 0 && mult < per) per = mult;
     return (unsigned)(sms * per);
 }
 
-cudaError_t launch_shade(const VolConst& V, const FrameConst& F, const LightSet& L, const SceneDev& S, int mode,
-                         uint32_t n_rays, const uint32_t* off, const float4* sf, const void* irr, const void* dep,
-                         const int2* hit, float4* rec, float* lum, int bounce, const ShadeWork& W, cudaStream_t s)
+cudaError_t launch_shade(const VolConst& V, const FrameDev* FD, const SceneDev& S, int mode, uint32_t n_rays,
+                         const uint32_t* off, const float4* sf, const void* irr, const void* dep, const int2* hit,
+                         float4* rec, float* lum, const ShadeWork& W, const Tuning& T, cudaStream_t s)
 {
     if (n_rays == 0) return cudaSuccess;
     RaySet Rs{mode, n_rays, off, sf};
-    const unsigned nb = (n_rays + 127) / 128;
+    const unsigned b = (unsigned)T.shade_block;
+    const unsigned nb = (n_rays + b - 1) / b;
     cudaError_t e = cudaMemsetAsync(W.job_count, 0, sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
-    k_shade_prep<<<nb, 128, 0, s>>>(V, F, L, S, Rs, hit, W.vis, W.jobs, W.job_light, W.job_count, W.job_cap);
+    k_shade_prep<<<nb, b, 0, s>>>(V, FD, S, Rs, hit, W.vis, W.jobs, W.job_light, W.job_count, W.job_cap);
     count_launches(1);
-    if (L.n > 0) {
-        k_shadow<<<W.shadow_blocks, 128, 0, s>>>(L, S, W.jobs, W.job_light, W.job_count, W.job_cap, W.vis,
-                                                 W.shadow_ctr);
-        count_launches(1);
-    }
-    k_shade_finish<<<nb, 128, 0, s>>>(V, F, L, S, Rs, hit, W.vis, irr, dep, bounce, rec, lum);
+    k_shadow<<<W.shadow_blocks, 128, 0, s>>>(FD, S, W.jobs, W.job_light, W.job_count, W.job_cap, W.vis,
+                                             W.shadow_ctr);
+    count_launches(1);
+    k_shade_finish<<<nb, b, 0, s>>>(V, FD, S, Rs, hit, W.vis, irr, dep, rec, lum);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -39,8 +39,17 @@ __device__ __forceinline__ float3 main_dir(const FrameConst& F, const float4* __
     return rotate(F.R, s);
 }
 
-__global__ void __launch_bounds__(128) k_pilot_trace(VolConst V, FrameConst F, SceneDev S, int2* __restrict__ hit)
+__global__ void k_set_frame(FrameDev* __restrict__ dst, const __grid_constant__ FrameDev src)
 {
+    const int* a = reinterpret_cast<const int*>(&src);
+    int* b = reinterpret_cast<int*>(dst);
+    for (int i = threadIdx.x; i < (int)(sizeof(FrameDev) / sizeof(int)); i += blockDim.x) b[i] = a[i];
+}
+
+__global__ void __launch_bounds__(256) k_pilot_trace(VolConst V, const FrameDev* __restrict__ FD, SceneDev S,
+                                                     int2* __restrict__ hit)
+{
+    const FrameConst& F = FD->F;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= V.P * kPilots) return;
     int p = i >> 3, o = i & 7;
@@ -52,10 +61,11 @@ __global__ void __launch_bounds__(128) k_pilot_trace(VolConst V, FrameConst F, S
     hit[i] = make_int2((int)h, __float_as_int(t));
 }
 
-__global__ void __launch_bounds__(128) k_main_trace(VolConst V, FrameConst F, SceneDev S,
+__global__ void __launch_bounds__(256) k_main_trace(VolConst V, const FrameDev* __restrict__ FD, SceneDev S,
                                                     const uint32_t* __restrict__ off, const float4* __restrict__ sf,
                                                     uint32_t R, int2* __restrict__ hit)
 {
+    const FrameConst& F = FD->F;
     __shared__ int s_lo, s_hi;
     uint32_t r0 = blockIdx.x * blockDim.x;
     uint32_t r1 = min(R - 1, r0 + blockDim.x - 1);
@@ -79,10 +89,12 @@ __global__ void __launch_bounds__(128) k_main_trace(VolConst V, FrameConst F, Sc
 }
 
 // Re-trace the last update's rays with work counters (roofline accounting).
-__global__ void __launch_bounds__(128) k_count(VolConst V, FrameConst F, const __grid_constant__ LightSet L, SceneDev S,
+__global__ void __launch_bounds__(128) k_count(VolConst V, const FrameDev* __restrict__ FD, SceneDev S,
                                                const uint32_t* __restrict__ off, const float4* __restrict__ sf,
                                                uint32_t R, unsigned long long* __restrict__ out)
 {
+    const FrameConst& F = FD->F;
+    const LightSet& L = FD->L;
     __shared__ int s_lo, s_hi;
     const uint32_t NP = (uint32_t)V.P * kPilots;
     uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
@@ -169,28 +181,50 @@ __global__ void k_trace_list(SceneDev S, const float* __restrict__ o, const floa
 
 }  // namespace
 
-cudaError_t launch_pilot_trace(const VolConst& V, const FrameConst& F, const SceneDev& S, int2* hit, cudaStream_t s)
+// kernel-node parameters of k_set_frame (args[0] -> *dst_slot, args[1] -> src)
+void set_frame_node_params(FrameDev** dst_slot, const FrameDev* src, cudaKernelNodeParams* kp, void** args)
 {
-    int n = V.P * kPilots;
-    k_pilot_trace<<<(n + 127) / 128, 128, 0, s>>>(V, F, S, hit);
+    args[0] = (void*)dst_slot;
+    args[1] = (void*)src;
+    kp->func = (void*)k_set_frame;
+    kp->gridDim = dim3(1, 1, 1);
+    kp->blockDim = dim3(256, 1, 1);
+    kp->sharedMemBytes = 0;
+    kp->kernelParams = args;
+    kp->extra = nullptr;
+}
+
+cudaError_t launch_set_frame(FrameDev* dst, const FrameDev& src, cudaStream_t s)
+{
+    k_set_frame<<<1, 256, 0, s>>>(dst, src);
     count_launches(1);
     return cudaGetLastError();
 }
 
-cudaError_t launch_main_trace(const VolConst& V, const FrameConst& F, const SceneDev& S, const uint32_t* off,
-                              const float4* sf, uint32_t R, int2* hit, cudaStream_t s)
+cudaError_t launch_pilot_trace(const VolConst& V, const FrameDev* FD, const SceneDev& S, int2* hit, const Tuning& T,
+                               cudaStream_t s)
+{
+    int n = V.P * kPilots, b = T.trace_block;
+    k_pilot_trace<<<(n + b - 1) / b, b, 0, s>>>(V, FD, S, hit);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_main_trace(const VolConst& V, const FrameDev* FD, const SceneDev& S, const uint32_t* off,
+                              const float4* sf, uint32_t R, int2* hit, const Tuning& T, cudaStream_t s)
 {
     if (R == 0) return cudaSuccess;
-    k_main_trace<<<(R + 127) / 128, 128, 0, s>>>(V, F, S, off, sf, R, hit);
+    const unsigned b = (unsigned)T.trace_block;
+    k_main_trace<<<(R + b - 1) / b, b, 0, s>>>(V, FD, S, off, sf, R, hit);
     count_launches(1);
     return cudaGetLastError();
 }
 
-cudaError_t launch_count(const VolConst& V, const FrameConst& F, const LightSet& L, const SceneDev& S,
-                         const uint32_t* off, const float4* sf, uint32_t R, unsigned long long* out, cudaStream_t s)
+cudaError_t launch_count(const VolConst& V, const FrameDev* FD, const SceneDev& S, const uint32_t* off,
+                         const float4* sf, uint32_t R, unsigned long long* out, cudaStream_t s)
 {
     uint32_t n = (uint32_t)V.P * kPilots + R;
-    k_count<<<(n + 127) / 128, 128, 0, s>>>(V, F, L, S, off, sf, R, out);
+    k_count<<<(n + 127) / 128, 128, 0, s>>>(V, FD, S, off, sf, R, out);
     count_launches(1);
     return cudaGetLastError();
 }

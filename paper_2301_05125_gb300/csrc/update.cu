@@ -32,8 +32,9 @@ __device__ __forceinline__ uint16_t trigger(uint16_t& amp, uint8_t& age, int del
     return (uint16_t)cur;
 }
 
-__global__ void __launch_bounds__(128) k_change_state(VolConst V, FrameConst F, ChangeBufs B)
+__global__ void __launch_bounds__(128) k_change_state(VolConst V, const FrameDev* __restrict__ FD, ChangeBufs B)
 {
+    const FrameConst& F = FD->F;
     int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= V.P) return;
     uint32_t yv[8], yr[8];
@@ -82,8 +83,9 @@ __global__ void __launch_bounds__(128) k_change_state(VolConst V, FrameConst F, 
 
 // 5x5x5 box sum of G (clipped to the grid) and composition (Eq. priorDynamic,
 // mu = 2, f_c from Eq. cameraD): W_p = min(sum_o (q_c q_v F) >> 20, 2^24-1).
-__global__ void __launch_bounds__(128) k_change_weight(VolConst V, FrameConst F, ChangeBufs B)
+__global__ void __launch_bounds__(128) k_change_weight(VolConst V, const FrameDev* __restrict__ FD, ChangeBufs B)
 {
+    const FrameConst& F = FD->F;
     int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= V.P) return;
     const int X = V.dims[0], Y = V.dims[1], Z = V.dims[2];
@@ -258,7 +260,6 @@ __global__ void __launch_bounds__(kAllocThreads) k_allocate(const uint32_t* __re
 // the probe's samples are binned to their nearest texel in shared memory, the
 // touched texels are blended with w = max(1 - h, k/(n+k)), the octahedral
 // border is refreshed, and the tiles are written back with coalesced stores.
-constexpr int kBlendThreads = 128;
 
 // float -> half with stochastic rounding: round toward zero, then step one
 // half ulp away from zero with probability equal to the remaining fraction
@@ -310,8 +311,10 @@ __device__ __forceinline__ void border_src(int i, int j, int n, int& si, int& sj
     }
 }
 
-__global__ void __launch_bounds__(kBlendThreads) k_blend(VolConst V, FrameConst F, BlendBufs B)
+__global__ void __launch_bounds__(256) k_blend(VolConst V, const FrameDev* __restrict__ FD, BlendBufs B)
 {
+    const FrameConst& F = FD->F;
+    const int nthr = blockDim.x;
     extern __shared__ float4 smem4[];
     const int p = blockIdx.x;
     const uint32_t base = __ldg(B.off + p);
@@ -331,10 +334,10 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend(VolConst V, FrameConst 
     float* acc_d = reinterpret_cast<float*>(tile_d + td2);         // [td2*3]
     uint32_t* cnt_d = reinterpret_cast<uint32_t*>(acc_d + 3 * td2);  // [td2]
     const int tid = threadIdx.x;
-    for (int t = tid; t < ti2; t += kBlendThreads) acc_i[t] = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int t = tid; t < 3 * td2; t += kBlendThreads) acc_d[t] = 0.f;
+    for (int t = tid; t < ti2; t += nthr) acc_i[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int t = tid; t < 3 * td2; t += nthr) acc_d[t] = 0.f;
     __syncthreads();
-    for (int j = tid; j < total; j += kBlendThreads) {
+    for (int j = tid; j < total; j += nthr) {
         float3 d;
         float4 rec;
         if (j < npil) {
@@ -360,14 +363,14 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend(VolConst V, FrameConst 
     }
     // stage the old tiles
     const size_t io = (size_t)p * ti2, dof = (size_t)p * td2;
-    for (int t = tid; t < ti2; t += kBlendThreads) tile_i[t] = irr_load(B.irr, io + t, V.fp16);
-    for (int t = tid; t < td2; t += kBlendThreads) {
+    for (int t = tid; t < ti2; t += nthr) tile_i[t] = irr_load(B.irr, io + t, V.fp16);
+    for (int t = tid; t < td2; t += nthr) {
         tile_d[t] = dep_load(B.dep, dof + t, V.fp16);
         cnt_d[t] = B.dep_n[dof + t];
     }
     __syncthreads();
     const float omh = 1.0f - V.hyst;
-    for (int t = tid; t < ti2; t += kBlendThreads) {
+    for (int t = tid; t < ti2; t += nthr) {
         float4 a = acc_i[t];
         if (a.w > 0.f) {
             float4 v = tile_i[t];
@@ -380,7 +383,7 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend(VolConst V, FrameConst 
             tile_i[t] = v;
         }
     }
-    for (int t = tid; t < td2; t += kBlendThreads) {
+    for (int t = tid; t < td2; t += nthr) {
         float k = acc_d[3 * t + 2];
         if (k > 0.f) {
             // the texel stores {mean, variance}; with batch mean m and batch
@@ -403,14 +406,14 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend(VolConst V, FrameConst 
     }
     __syncthreads();
     // border texels copy their octahedral fold partners (interior, updated)
-    for (int t = tid; t < ti2; t += kBlendThreads) {
+    for (int t = tid; t < ti2; t += nthr) {
         int i = t / Ti, j = t - i * Ti;
         if (i >= 1 && i <= ni && j >= 1 && j <= ni) continue;
         int si, sj;
         border_src(i, j, ni, si, sj);
         tile_i[t] = tile_i[si * Ti + sj];
     }
-    for (int t = tid; t < td2; t += kBlendThreads) {
+    for (int t = tid; t < td2; t += nthr) {
         int i = t / Td, j = t - i * Td;
         if (i >= 1 && i <= nd && j >= 1 && j <= nd) continue;
         int si, sj;
@@ -422,30 +425,30 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend(VolConst V, FrameConst 
     if (V.fp16 == 2) {  // stochastic rounding, seeded by the frame, probe, texel and channel
         const uint64_t key = F.pilot_key ^ (F.even ? 0x5352ull : 0x5353ull);
         __half2* hi = reinterpret_cast<__half2*>(B.irr) + 2 * io;
-        for (int t = tid; t < ti2; t += kBlendThreads) {
+        for (int t = tid; t < ti2; t += nthr) {
             float4 v = tile_i[t];
             hi[2 * t] = __halves2half2(half_sr(v.x, sr_bits(key, p, t, 0)), half_sr(v.y, sr_bits(key, p, t, 1)));
             hi[2 * t + 1] = __halves2half2(half_sr(v.z, sr_bits(key, p, t, 2)), __float2half_rn(v.w));
         }
         __half2* hd = reinterpret_cast<__half2*>(B.dep) + dof;
-        for (int t = tid; t < td2; t += kBlendThreads)
+        for (int t = tid; t < td2; t += nthr)
             hd[t] = __halves2half2(half_sr(tile_d[t].x, sr_bits(key, p, t, 4)), half_sr(tile_d[t].y, sr_bits(key, p, t, 5)));
     } else if (V.fp16) {
         __half2* hi = reinterpret_cast<__half2*>(B.irr) + 2 * io;
-        for (int t = tid; t < ti2; t += kBlendThreads) {
+        for (int t = tid; t < ti2; t += nthr) {
             float4 v = tile_i[t];
             hi[2 * t] = __floats2half2_rn(v.x, v.y);
             hi[2 * t + 1] = __floats2half2_rn(v.z, v.w);
         }
         __half2* hd = reinterpret_cast<__half2*>(B.dep) + dof;
-        for (int t = tid; t < td2; t += kBlendThreads) hd[t] = __floats2half2_rn(tile_d[t].x, tile_d[t].y);
+        for (int t = tid; t < td2; t += nthr) hd[t] = __floats2half2_rn(tile_d[t].x, tile_d[t].y);
     } else {
         float4* gi = reinterpret_cast<float4*>(B.irr) + io;
-        for (int t = tid; t < ti2; t += kBlendThreads) gi[t] = tile_i[t];
+        for (int t = tid; t < ti2; t += nthr) gi[t] = tile_i[t];
         float2* gd = reinterpret_cast<float2*>(B.dep) + dof;
-        for (int t = tid; t < td2; t += kBlendThreads) gd[t] = tile_d[t];
+        for (int t = tid; t < td2; t += nthr) gd[t] = tile_d[t];
     }
-    for (int t = tid; t < td2; t += kBlendThreads) B.dep_n[dof + t] = (uint8_t)cnt_d[t];
+    for (int t = tid; t < td2; t += nthr) B.dep_n[dof + t] = (uint8_t)cnt_d[t];
 }
 
 // ============================================================== query
@@ -471,11 +474,11 @@ size_t blend_smem_bytes(const VolConst& V)
     return ti2 * 16 * 2 + td2 * 8 + td2 * 12 + td2 * 4;
 }
 
-cudaError_t launch_change(const VolConst& V, const FrameConst& F, const ChangeBufs& B, cudaStream_t s)
+cudaError_t launch_change(const VolConst& V, const FrameDev* FD, const ChangeBufs& B, cudaStream_t s)
 {
-    k_change_state<<<(V.P + 127) / 128, 128, 0, s>>>(V, F, B);
+    k_change_state<<<(V.P + 127) / 128, 128, 0, s>>>(V, FD, B);
     count_launches(1);
-    k_change_weight<<<(V.P + 127) / 128, 128, 0, s>>>(V, F, B);
+    k_change_weight<<<(V.P + 127) / 128, 128, 0, s>>>(V, FD, B);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -488,14 +491,14 @@ cudaError_t launch_allocate(const uint32_t* W, int P, int avg, int m0, int rmax,
     return cudaGetLastError();
 }
 
-cudaError_t launch_blend(const VolConst& V, const FrameConst& F, const BlendBufs& B, cudaStream_t s)
+cudaError_t launch_blend(const VolConst& V, const FrameDev* FD, const BlendBufs& B, const Tuning& T, cudaStream_t s)
 {
     size_t sm = blend_smem_bytes(V);
     if (sm > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k_blend, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
     }
-    k_blend<<<V.P, kBlendThreads, sm, s>>>(V, F, B);
+    k_blend<<<V.P, T.blend_block, sm, s>>>(V, FD, B);
     count_launches(1);
     return cudaGetLastError();
 }

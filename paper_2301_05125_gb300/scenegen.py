@@ -315,3 +315,36 @@ def small_city(seed: int = 1, n_boxes: int = 600, dims=(8, 4, 8), rays_avg=48) -
     """A reduced tunnel+city (same generator) that the oracle finishes in
     seconds while still spanning many probes, tiles and a ragged tail."""
     return _city(seed, n_boxes, 20, dims, (-30.0, 1.0, -30.0), (8.0, 8.0, 8.0), rays_avg, 8, 160, 4, "small_city")
+
+
+def batched(seed: int = 1, n_volumes: int = 24, n_scenes: int = 6, tri_lo: float = 20e3, tri_hi: float = 500e3,
+            dims_lo=(8, 8, 8), dims_hi=(48, 16, 48), rays_avg: int = 64, fp16: int = 1) -> List[Workload]:
+    """Batched volumes: n_volumes probe volumes of uneven size (dims log-uniform
+    between dims_lo and dims_hi) over n_scenes seeded city scenes whose
+    triangle counts are log-uniform in [tri_lo, tri_hi]; every volume has its
+    own light phase and occluder motion; FP16 atlases."""
+    rng = np.random.default_rng(seed)
+    tris = np.exp(rng.uniform(np.log(tri_lo), np.log(tri_hi), n_scenes))
+    scenes = []
+    for k in range(n_scenes):
+        # fixed part: ground 2048 + tunnel 64x40x2 + occluders 240 triangles;
+        # about 3% of the boxes fall in the tunnel corridor and are dropped
+        n_boxes = max(100, int((tris[k] - 7408) / 12 / 0.97))
+        scenes.append(_city(seed * 100 + k, n_boxes, 40, (2, 2, 2), (0.0, 1.0, 0.0), (4.0, 4.0, 4.0), 64, 8, 256, 1,
+                            "scene%d" % k))
+    out = []
+    for i in range(n_volumes):
+        base = scenes[i % n_scenes]
+        dims = tuple(int(round(np.exp(rng.uniform(np.log(lo), np.log(hi))))) for lo, hi in zip(dims_lo, dims_hi))
+        spacing = 3.0 + 2.0 * rng.random()
+        origin = (-dims[0] * spacing / 2 + rng.uniform(-20, 20), 1.0, -dims[2] * spacing / 2 + rng.uniform(-20, 20))
+        phase = 7 * i
+        vol = dict(origin=origin, spacing=(spacing, spacing, spacing), dims=dims, irr_interior=6, depth_interior=14,
+                   rays_avg=rays_avg, rays_min=8, rays_max=256, hysteresis=0.97, depth_max=0.0, atlas_fp16=fp16,
+                   tr_theta=16)
+        w = Workload("batched%d" % i, seed * 1000 + i, base.verts, base.idx, base.albedo, vol, 30, base.sky,
+                     (lambda f, b=base, ph=phase: b.lights_at(f + ph)), dyn_first=base.dyn_first,
+                     dyn_count=base.dyn_count, dyn_at=(lambda f, b=base, ph=phase: b.dyn_at(f + ph)),
+                     meta=dict(scene=i % n_scenes, scene_tris=int(base.n_tris)))
+        out.append(w)
+    return out
