@@ -130,6 +130,24 @@ def _dist():
     return ws, rank
 
 
+def _replica_seed(seed, rank):
+    """Replicas: every rank updates its own volume of the same workload with
+    its own seed; nothing is exchanged on the data path."""
+    return seed + rank
+
+
+def _job_ms(ms_step, ws, device):
+    """Whole-job step time: the maximum over ranks (every rank calls this)."""
+    if ws == 1:
+        return float(ms_step)
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(ms_step)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def _workload(name, seed):
     from paper_2301_05125_gb300 import scenegen as S
 
@@ -311,6 +329,103 @@ def _batched_section(args, adgi, torch, dev):
     return out
 
 
+def _serve_trace(args, adgi, ws, sched_t, sched_c, fp16, streams, graph):
+    """Replay one Poisson arrival trace through an adgi server; returns the
+    served/superseded counts, latencies and rays/s."""
+    srv = adgi.Server(streams=streams, hbm_budget_bytes=args.serve_budget_gb << 30, coalesce=True, graph=graph)
+    vids = []
+    for w in ws:
+        vd = dict(w.volume)
+        vd["atlas_fp16"] = fp16
+        vids.append(srv.add_volume(w.verts, w.idx, w.albedo, **vd))
+    n_frames = int(np.bincount(sched_c, minlength=len(ws)).max()) + 2
+    # occluder vertices per client and frame, made before the clock starts
+    dyn = [[np.ascontiguousarray(w.dyn_at(f), np.float32) for f in range(n_frames)] for w in ws]
+
+    def submit(i, f):
+        w = ws[i]
+        return srv.submit(vids[i], f, w.seed, w.lights_at(f), w.sky, move_first=w.dyn_first, move_verts=dyn[i][f])
+
+    t0 = time.perf_counter()
+    for i in range(len(ws)):  # admission, first-frame set-up and graph capture: untimed
+        submit(i, 0)
+    srv.drain(1200.0)
+    srv.poll(1 << 16)
+    setup_s = time.perf_counter() - t0
+    info0 = srv.info()
+    frame = [1] * len(ws)
+    results = []
+    start = time.perf_counter()
+    for t, c in zip(sched_t, sched_c):
+        while True:
+            dt = start + float(t) - time.perf_counter()
+            if dt <= 0:
+                break
+            if dt > 2e-3:
+                results += srv.poll(1 << 14)
+            time.sleep(min(dt, 1e-3))
+        submit(int(c), frame[c])
+        frame[c] += 1
+    srv.drain(1200.0)
+    results += srv.poll(1 << 16)
+    info = srv.info()
+    srv.close()
+    served = [r for r in results if r.status == 0]
+    bad = [r for r in results if r.status < 0]
+    lat = np.array([r.t_done_s - r.t_submit_s for r in served]) * 1e3
+    # what a client sees: a superseded request is answered by the next served
+    # update of its volume (a newer frame), so its latency runs to that one
+    eff = []
+    by_vol = {}
+    for r in results:
+        by_vol.setdefault(r.volume, []).append(r)
+    for rs in by_vol.values():
+        rs.sort(key=lambda r: r.request_id)
+        t_next = None
+        for r in reversed(rs):
+            if r.status == 0:
+                t_next = r.t_done_s
+            if r.status >= 0 and t_next is not None:
+                eff.append(t_next - r.t_submit_s)
+    eff = np.array(eff) * 1e3
+    t_first = min(r.t_submit_s for r in results)
+    t_last = max(r.t_done_s for r in results)
+    rays = sum(int(r.rays) for r in served)
+    return {"requests": len(results), "served": len(served), "superseded": len(results) - len(served) - len(bad),
+            "failed": len(bad), "rays_per_s": rays / (t_last - t_first),
+            "p50_ms": float(np.percentile(eff, 50)), "p99_ms": float(np.percentile(eff, 99)),
+            "mean_ms": float(eff.mean()), "served_p50_ms": float(np.percentile(lat, 50)),
+            "served_p99_ms": float(np.percentile(lat, 99)), "span_s": t_last - t_first,
+            "streams": streams, "graph": graph, "atlas": "fp16" if fp16 else "fp32",
+            "resident_volumes": info["resident"], "waiting_volumes": info["waiting"],
+            "device_bytes_resident": info0["used_bytes"], "setup_s": setup_s}
+
+
+def _serving_section(args, adgi, torch, dev):
+    """Serving form: 64 clients, Poisson arrivals at 60 Hz each, volumes of
+    512-65536 probes over scenes of 50k-1M triangles, admission under a 120 GB
+    budget; the served path (FP16 atlases, 8 streams, graph replays) against
+    the plain FP32 per-volume path (one stream, plain updates), same trace and
+    the same latest-frame-wins policy."""
+    from paper_2301_05125_gb300 import scenegen as S
+
+    n_req = args.serve_requests
+    sched_t, sched_c = S.poisson_schedule(args.seed, 64, 60.0, n_req)
+    out = {"clients": 64, "rate_hz_per_client": 60.0, "requests_offered": n_req,
+           "budget_gb": args.serve_budget_gb, "offered_s": float(sched_t[-1])}
+    ws16 = S.serving(args.seed, fp16=1)
+    out["probes_min_max_mean"] = [min(w.n_probes for w in ws16), max(w.n_probes for w in ws16),
+                                  float(np.mean([w.n_probes for w in ws16]))]
+    out["scene_triangles"] = sorted(set(int(w.n_tris) for w in ws16))
+    out["served_fp16"] = _serve_trace(args, adgi, ws16, sched_t, sched_c, 1, args.serve_streams, True)
+    out["plain_fp32"] = _serve_trace(args, adgi, ws16, sched_t, sched_c, 0, 1, False)
+    out["speedup_rays_per_s"] = out["served_fp16"]["rays_per_s"] / out["plain_fp32"]["rays_per_s"]
+    out["policy"] = ("a client's queued request is superseded when a newer one of the same volume is dispatched; "
+                     "p50/p99 = latency of every request until its volume's next completed update (the one that "
+                     "served it or a newer frame); served_p50/p99 = completion - submission of served requests")
+    return out
+
+
 def run_ours(args):
     import torch
 
@@ -331,7 +446,7 @@ def run_ours(args):
     adgi.load()
     dev = torch.device("cuda", local)
     # replicas: every rank updates its own volume (independent seeds); no data-path collective
-    w = _workload(args.workload, args.seed + rank)
+    w = _workload(args.workload, _replica_seed(args.seed, rank))
     vd = dict(w.volume)
     if args.fp16:
         vd["atlas_fp16"] = 1
@@ -394,11 +509,7 @@ def run_ours(args):
     launches = vol.stats().kernels_launched - launches0
     last_frame = frames[args.warmup + args.steps - 1]
     counts = adgi.adgi_count_traversal(vol.h, last_frame)
-    ms_step = float(np.mean(dev_ms))
-    if ws > 1:
-        t = torch.tensor([ms_step], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
+    ms_step = _job_ms(float(np.mean(dev_ms)), ws, dev)
     rays = w.rays_per_update
     value = ws * rays / (ms_step / 1e3)
     hbm, smax_nominal, peak_src = _peaks()
@@ -460,6 +571,9 @@ def run_ours(args):
     batched = None
     if rank == 0 and not args.no_batched:
         batched = _batched_section(args, adgi, torch, dev)
+    serving = None
+    if rank == 0 and not args.no_serving:
+        serving = _serving_section(args, adgi, torch, dev)
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         times, cores = _cpu_baseline(w, budget_s=args.cpu_budget)
@@ -487,6 +601,7 @@ def run_ours(args):
             "cpu_baseline": cpu,
             "e2e": e2e,
             "batched": batched,
+            "serving": serving,
             "gpu_launches": int(launches),
             "clocks": clk,
             "wall_s": wall,
@@ -510,6 +625,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=10000)
+    ap.add_argument("--serve-streams", type=int, default=8)
+    ap.add_argument("--serve-budget-gb", type=int, default=120)
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)

@@ -338,6 +338,71 @@ int adgi_build_bvh_noalloc(const float* verts, int32_t n_verts, const int32_t* t
 int adgi_allocate_rays(const uint32_t* W, int32_t P, int32_t rays_avg, int32_t rays_min, int32_t rays_max,
                        uint32_t* n_out, uint32_t* off_out, void* cuda_stream);
 
+/* ---------------------------------------------------------------------------
+ * Serving: a continuous-batching request loop over many resident volumes.
+ * The paper updates one volume per frame inside one renderer; this loop is
+ * the server form of that update for many clients, with no counterpart in
+ * the paper.
+ *
+ * adgi_server_create starts a worker thread on the current device with
+ * `streams` CUDA streams ("slots", 1..64) and a device-memory budget in bytes.
+ * Volumes are registered with adgi_server_add_volume (desc, scene: host
+ * arrays as for adgi_create_volume / adgi_set_scene, copied); the worker
+ * creates and uploads them -- "admits" them -- in registration order while
+ * the sum of their device footprints (estimated before creation, the true
+ * figure of adgi_stats.device_bytes after) stays within the budget; a
+ * volume that does not fit waits until adgi_server_remove_volume releases
+ * enough memory.  adgi_server_submit queues one frame update for a volume
+ * (host data copied; optional vertex move as adgi_move_vertices, applied
+ * before the update).  Whenever a slot is free the worker starts the oldest
+ * queued request of an idle admitted volume on it -- requests of one volume
+ * run in submission order, those of different volumes overlap on the
+ * device, and a request never waits for a batch boundary.  Each update is a
+ * replay of the volume's captured update graph (adgi_update_graph), or a
+ * plain adgi_update with ADGI_SERVER_NO_GRAPH.  With ADGI_SERVER_COALESCE a
+ * request that is still queued when a newer one of the same volume is
+ * dispatched is dropped and reported with status 1 (superseded): a renderer
+ * wants its latest frame, not a backlog.  Results are identical to those of
+ * the same requests run on a lone volume with adgi_update.
+ *
+ * adgi_server_poll moves up to `max` finished results into out (host
+ * array), *n = count; times are seconds of a monotonic host clock (submit,
+ * start on a slot, completion seen by the worker).  It returns CUDA with the
+ * message of the worker's last failure once one happened.
+ * adgi_server_drain waits until no request is queued or running (TIMEOUT
+ * after timeout_s seconds).  adgi_server_volume hands out the handle of an
+ * admitted, idle volume for queries and state reads (INVALID_ARG if it is
+ * busy or not admitted); the caller must submit nothing to that volume while
+ * it uses the handle.  adgi_server_destroy stops the worker, waits for the
+ * streams and destroys every volume.  Errors: INVALID_ARG (NULL, unknown
+ * volume, streams outside 1..64, unknown flags), OVER_BUDGET (a volume larger
+ * than the whole budget), CUDA.
+ * ------------------------------------------------------------------------- */
+typedef struct adgi_server_s* adgi_server;
+#define ADGI_SERVER_COALESCE 1
+#define ADGI_SERVER_NO_GRAPH 2
+typedef struct {
+    uint64_t request_id; /* as returned by adgi_server_submit (from 1) */
+    int32_t volume;      /* volume id */
+    int32_t status;      /* ADGI_OK, 1 = superseded, or a negative ADGI_ERR_* */
+    double t_submit_s, t_start_s, t_done_s;
+    uint64_t rays;       /* rays of the update: rays_avg * probes (0 if superseded) */
+} adgi_result;
+int adgi_server_create(int32_t streams, uint64_t hbm_budget_bytes, int32_t flags, adgi_server* out);
+int adgi_server_add_volume(adgi_server s, const adgi_volume_desc* desc, const float* verts_xyz, int32_t n_verts,
+                           const int32_t* tri_idx, int32_t n_tris, const float* tri_albedo_rgb, int32_t* id_out);
+int adgi_server_submit(adgi_server s, int32_t volume, const adgi_frame* frame, int32_t move_first,
+                       int32_t move_count, const float* move_verts_xyz, uint64_t* request_id);
+int adgi_server_poll(adgi_server s, adgi_result* out, int32_t max, int32_t* n);
+int adgi_server_drain(adgi_server s, double timeout_s);
+int adgi_server_volume(adgi_server s, int32_t volume, adgi_volume* out);
+int adgi_server_remove_volume(adgi_server s, int32_t volume);
+/* used: bytes charged to admitted volumes; superseded: requests dropped so
+ * far; resident / waiting: admitted volumes and volumes waiting for memory. */
+int adgi_server_info(adgi_server s, uint64_t* used_bytes, uint64_t* superseded, int32_t* resident,
+                     int32_t* waiting);
+int adgi_server_destroy(adgi_server s);
+
 /* Message of the calling thread's last error ("" if none). */
 const char* adgi_last_error(void);
 

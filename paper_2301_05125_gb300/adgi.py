@@ -66,6 +66,15 @@ class adgi_tuning(C.Structure):
                 ("blend_block", C.c_int32), ("ms_trace", C.c_float), ("ms_shade", C.c_float), ("ms_blend", C.c_float)]
 
 
+class adgi_result(C.Structure):
+    _fields_ = [("request_id", C.c_uint64), ("volume", C.c_int32), ("status", C.c_int32), ("t_submit_s", C.c_double),
+                ("t_start_s", C.c_double), ("t_done_s", C.c_double), ("rays", C.c_uint64)]
+
+
+SERVER_COALESCE = 1
+SERVER_NO_GRAPH = 2
+
+
 class adgi_stats(C.Structure):
     _fields_ = [
         ("frames", C.c_uint64),
@@ -89,7 +98,9 @@ EXPORTED = ["adgi_create_volume", "adgi_set_scene", "adgi_move_vertices", "adgi_
             "adgi_read_state", "adgi_write_atlas", "adgi_trace_closest", "adgi_count_traversal", "adgi_build_bvh",
             "adgi_build_bvh_noalloc", "adgi_allocate_rays", "adgi_update_graph", "adgi_batch_create",
             "adgi_batch_update", "adgi_batch_destroy", "adgi_autotune", "adgi_set_tuning", "adgi_get_tuning",
-            "adgi_last_error"]
+            "adgi_server_create", "adgi_server_add_volume", "adgi_server_submit", "adgi_server_poll",
+            "adgi_server_drain", "adgi_server_volume", "adgi_server_remove_volume", "adgi_server_info",
+            "adgi_server_destroy", "adgi_last_error"]
 
 BVH_NOALLOC_MAX_TRIS = 32768
 
@@ -129,6 +140,15 @@ def load(path: str = LIB_PATH):
     L.adgi_autotune.argtypes = [vp, C.POINTER(adgi_frame), i32, C.POINTER(adgi_tuning)]
     L.adgi_set_tuning.argtypes = [vp, C.POINTER(adgi_tuning)]
     L.adgi_get_tuning.argtypes = [vp, C.POINTER(adgi_tuning)]
+    L.adgi_server_create.argtypes = [i32, u64, i32, C.POINTER(vp)]
+    L.adgi_server_add_volume.argtypes = [vp, C.POINTER(adgi_volume_desc), vp, i32, vp, i32, vp, C.POINTER(i32)]
+    L.adgi_server_submit.argtypes = [vp, i32, C.POINTER(adgi_frame), i32, i32, vp, C.POINTER(u64)]
+    L.adgi_server_poll.argtypes = [vp, C.POINTER(adgi_result), i32, C.POINTER(i32)]
+    L.adgi_server_drain.argtypes = [vp, C.c_double]
+    L.adgi_server_volume.argtypes = [vp, i32, C.POINTER(vp)]
+    L.adgi_server_remove_volume.argtypes = [vp, i32]
+    L.adgi_server_info.argtypes = [vp, C.POINTER(u64), C.POINTER(u64), C.POINTER(i32), C.POINTER(i32)]
+    L.adgi_server_destroy.argtypes = [vp]
     L.adgi_last_error.restype = C.c_char_p
     for name in EXPORTED[:-1]:
         getattr(L, name).restype = C.c_int
@@ -298,6 +318,68 @@ def adgi_get_tuning(vol) -> adgi_tuning:
     return t
 
 
+def adgi_server_create(streams, hbm_budget_bytes, flags=0):
+    h = C.c_void_p()
+    _check(load().adgi_server_create(int(streams), int(hbm_budget_bytes), int(flags), C.byref(h)))
+    return h
+
+
+def adgi_server_add_volume(server, desc: adgi_volume_desc, verts, idx, albedo) -> int:
+    verts = np.ascontiguousarray(verts, np.float32)
+    idx = np.ascontiguousarray(idx, np.int32)
+    albedo = np.ascontiguousarray(albedo, np.float32)
+    vid = C.c_int32()
+    _check(load().adgi_server_add_volume(server, C.byref(desc), _ptr(verts), verts.size // 3, _ptr(idx),
+                                         idx.size // 3, _ptr(albedo), C.byref(vid)))
+    return int(vid.value)
+
+
+def adgi_server_submit(server, volume, frame: adgi_frame, move_first=0, move_verts=None) -> int:
+    rid = C.c_uint64()
+    mv = None if move_verts is None else np.ascontiguousarray(move_verts, np.float32)
+    _check(load().adgi_server_submit(server, int(volume), C.byref(frame), int(move_first),
+                                     0 if mv is None else mv.size // 3, _ptr(mv), C.byref(rid)))
+    return int(rid.value)
+
+
+_poll_bufs = {}
+
+
+def adgi_server_poll(server, max_results=4096):
+    buf = _poll_bufs.get(max_results)
+    if buf is None:
+        buf = _poll_bufs[max_results] = (adgi_result * max_results)()
+    n = C.c_int32()
+    _check(load().adgi_server_poll(server, buf, max_results, C.byref(n)))
+    return [adgi_result.from_buffer_copy(buf[i]) for i in range(n.value)]
+
+
+def adgi_server_drain(server, timeout_s=600.0):
+    _check(load().adgi_server_drain(server, float(timeout_s)))
+
+
+def adgi_server_volume(server, volume):
+    h = C.c_void_p()
+    _check(load().adgi_server_volume(server, int(volume), C.byref(h)))
+    return h
+
+
+def adgi_server_remove_volume(server, volume):
+    _check(load().adgi_server_remove_volume(server, int(volume)))
+
+
+def adgi_server_info(server):
+    used, sup = C.c_uint64(), C.c_uint64()
+    res, wait = C.c_int32(), C.c_int32()
+    _check(load().adgi_server_info(server, C.byref(used), C.byref(sup), C.byref(res), C.byref(wait)))
+    return dict(used_bytes=int(used.value), superseded=int(sup.value), resident=int(res.value),
+                waiting=int(wait.value))
+
+
+def adgi_server_destroy(server):
+    _check(load().adgi_server_destroy(server))
+
+
 def adgi_last_error() -> str:
     return load().adgi_last_error().decode(errors="replace")
 
@@ -349,10 +431,20 @@ class Volume:
         self.Ti, self.Td = d.irr_interior + 2, d.depth_interior + 2
         self.fp16 = bool(d.atlas_fp16)
 
+    @classmethod
+    def borrow(cls, h, desc):
+        """view of a handle owned elsewhere (a server volume): never destroyed here"""
+        v = cls.__new__(cls)
+        v.desc, v.h, v._borrowed = desc, h, True
+        v.P = desc.dims[0] * desc.dims[1] * desc.dims[2]
+        v.Ti, v.Td = desc.irr_interior + 2, desc.depth_interior + 2
+        v.fp16 = bool(desc.atlas_fp16)
+        return v
+
     def close(self):
-        if self.h:
+        if self.h and not getattr(self, "_borrowed", False):
             adgi_destroy(self.h)
-            self.h = None
+        self.h = None
 
     def __del__(self):
         try:
@@ -457,6 +549,52 @@ class Volume:
         adgi_write_atlas(self.h, None if irr is None else np.ascontiguousarray(irr, dt),
                          None if dep is None else np.ascontiguousarray(dep, dt),
                          None if dep_n is None else np.ascontiguousarray(dep_n, np.uint8))
+
+
+class Server:
+    """Owning wrapper of an adgi_server (continuous-batching request loop)."""
+
+    def __init__(self, streams=4, hbm_budget_bytes=120 << 30, coalesce=False, graph=True):
+        flags = (SERVER_COALESCE if coalesce else 0) | (0 if graph else SERVER_NO_GRAPH)
+        self.h = adgi_server_create(streams, hbm_budget_bytes, flags)
+        self.descs = {}
+
+    def add_volume(self, verts, idx, albedo, **desc):
+        d = make_desc(**desc)
+        vid = adgi_server_add_volume(self.h, d, verts, idx, albedo)
+        self.descs[vid] = d
+        return vid
+
+    def submit(self, volume, frame, seed, lights, sky=(0, 0, 0), camera=None, move_first=0, move_verts=None):
+        return adgi_server_submit(self.h, volume, make_frame(frame, seed, lights, sky, camera), move_first,
+                                  move_verts)
+
+    def poll(self, max_results=4096):
+        return adgi_server_poll(self.h, max_results)
+
+    def drain(self, timeout_s=600.0):
+        adgi_server_drain(self.h, timeout_s)
+
+    def volume(self, vid):
+        """a non-owning Volume view of an admitted, idle volume"""
+        return Volume.borrow(adgi_server_volume(self.h, vid), self.descs[vid])
+
+    def remove_volume(self, vid):
+        adgi_server_remove_volume(self.h, vid)
+
+    def info(self):
+        return adgi_server_info(self.h)
+
+    def close(self):
+        if self.h:
+            adgi_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Batch:

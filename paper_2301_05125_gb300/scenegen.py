@@ -348,3 +348,46 @@ def batched(seed: int = 1, n_volumes: int = 24, n_scenes: int = 6, tri_lo: float
                      meta=dict(scene=i % n_scenes, scene_tris=int(base.n_tris)))
         out.append(w)
     return out
+
+
+def serving(seed: int = 1, n_clients: int = 64, n_scenes: int = 8, tri_lo: float = 50e3, tri_hi: float = 1e6,
+            probes_lo: int = 512, probes_hi: int = 65536, rays_avg: int = 64, fp16: int = 1) -> List[Workload]:
+    """Serving mix: n_clients volumes, each owned by one client, whose probe
+    counts are log-uniform in [probes_lo, probes_hi] (grids 2a x a x 2a) over
+    n_scenes seeded city scenes of log-uniform triangle count in [tri_lo,
+    tri_hi]; every volume has its own light phase and occluder motion."""
+    rng = np.random.default_rng(seed)
+    tris = np.exp(rng.uniform(np.log(tri_lo), np.log(tri_hi), n_scenes))
+    scenes = []
+    for k in range(n_scenes):
+        n_boxes = max(100, int((tris[k] - 7408) / 12 / 0.97))
+        scenes.append(_city(seed * 100 + 50 + k, n_boxes, 40, (2, 2, 2), (0.0, 1.0, 0.0), (4.0, 4.0, 4.0), 64, 8,
+                            256, 1, "scene%d" % k))
+    out = []
+    for i in range(n_clients):
+        base = scenes[i % n_scenes]
+        P = np.exp(rng.uniform(np.log(probes_lo), np.log(probes_hi)))
+        a = max(4, int(round((P / 4.0) ** (1.0 / 3.0))))
+        dims = (2 * a, a, 2 * a)
+        spacing = float(np.clip(160.0 / (2 * a), 2.0, 8.0))
+        origin = (-a * spacing + rng.uniform(-30, 30), 1.0, -a * spacing + rng.uniform(-30, 30))
+        phase = 5 * i
+        vol = dict(origin=origin, spacing=(spacing, spacing, spacing), dims=dims, irr_interior=6, depth_interior=14,
+                   rays_avg=rays_avg, rays_min=8, rays_max=256, hysteresis=0.97, depth_max=0.0, atlas_fp16=fp16,
+                   tr_theta=16)
+        out.append(Workload("client%d" % i, seed * 1000 + i, base.verts, base.idx, base.albedo, vol, 0, base.sky,
+                            (lambda f, b=base, ph=phase: b.lights_at(f + ph)), dyn_first=base.dyn_first,
+                            dyn_count=base.dyn_count, dyn_at=(lambda f, b=base, ph=phase: b.dyn_at(f + ph)),
+                            meta=dict(scene=i % n_scenes, scene_tris=int(base.n_tris))))
+    return out
+
+
+def poisson_schedule(seed: int, n_clients: int, rate_hz: float, n_requests: int):
+    """Arrival times (s) and client ids of the first n_requests arrivals of
+    n_clients independent Poisson processes of rate rate_hz each."""
+    rng = np.random.default_rng(seed)
+    per = int(np.ceil(n_requests / n_clients * 1.5)) + 16
+    t = np.cumsum(rng.exponential(1.0 / rate_hz, (n_clients, per)), axis=1)
+    cid = np.repeat(np.arange(n_clients), per)
+    order = np.argsort(t.ravel(), kind="stable")[:n_requests]
+    return t.ravel()[order], cid[order]
