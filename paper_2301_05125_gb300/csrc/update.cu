@@ -256,10 +256,17 @@ __global__ void __launch_bounds__(kAllocThreads) k_allocate(const uint32_t* __re
 }
 
 // ============================================================== blend
-// One CTA per probe tile (Alg. ApproxAlgo + Alg. MovingAvgUpdate, batched):
-// the probe's samples are binned to their nearest texel in shared memory, the
-// touched texels are blended with w = max(1 - h, k/(n+k)), the octahedral
-// border is refreshed, and the tiles are written back with coalesced stores.
+// One CTA per probe tile (Alg. ApproxAlgo + Alg. MovingAvgUpdate, batched).
+//  1. one thread stages the probe's ray records and its old atlas tiles into
+//     shared memory with bulk asynchronous copies (cp.async.bulk, completion
+//     counted on an mbarrier) while the CTA bins every sample direction to its
+//     nearest irradiance and depth texel;
+//  2. a stable counting sort in shared memory groups the samples of each
+//     texel in sample order, so each texel's sum is taken by one thread in a
+//     fixed order: the blend is deterministic (no floating-point atomics);
+//  3. touched texels are blended with w = max(1 - h, k/(n+k)), the octahedral
+//     border is refreshed from the updated interior, and the tiles are
+//     written back with coalesced 16-byte stores.
 
 // float -> half with stochastic rounding: round toward zero, then step one
 // half ulp away from zero with probability equal to the remaining fraction
@@ -311,16 +318,114 @@ __device__ __forceinline__ void border_src(int i, int j, int n, int& si, int& sj
     }
 }
 
+
+constexpr int kErrWait = 16;  // a bulk copy did not complete within the wait limit
+
+// shared-memory layout of k_blend for samples <= smax (byte offsets, 16-aligned)
+struct BlendLayout {
+    uint32_t rec, irr_raw, dep_raw, dn_raw, irr_new, dep_new, dn_new, key_i, key_d, ord_i, ord_d, beg_i, beg_d, cur_i,
+        cur_d, total;
+};
+
+__host__ __device__ inline uint32_t al16(uint32_t x) { return (x + 15u) & ~15u; }
+
+__host__ __device__ inline BlendLayout blend_layout(int smax, int Ti, int Td)
+{
+    const uint32_t ti2 = (uint32_t)(Ti * Ti), td2 = (uint32_t)(Td * Td), S = (uint32_t)smax;
+    BlendLayout L;
+    uint32_t o = 16;  // mbarrier
+    L.rec = o, o += al16(16 * S);
+    L.irr_raw = o, o += al16(16 * ti2);
+    L.dep_raw = o, o += al16(8 * td2);
+    L.dn_raw = o, o += al16(td2);
+    L.irr_new = o, o += al16(16 * ti2);
+    L.dep_new = o, o += al16(8 * td2);
+    L.dn_new = o, o += al16(td2);
+    L.key_i = o, o += al16(2 * S);
+    L.key_d = o, o += al16(2 * S);
+    L.ord_i = o, o += al16(2 * S);
+    L.ord_d = o, o += al16(2 * S);
+    L.beg_i = o, o += al16(4 * (ti2 + 1));
+    L.beg_d = o, o += al16(4 * (td2 + 1));
+    L.cur_i = o, o += al16(4 * ti2);
+    L.cur_d = o, o += al16(4 * td2);
+    L.total = o;
+    return L;
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint32_t bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred P;\n mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n selp.u32 %0, 1, 0, P;\n}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// exclusive scan of cnt[0..n) into beg[0..n] (beg[n] = total) and cur, by one warp
+__device__ __forceinline__ void warp_scan_bins(const uint32_t* cnt, uint32_t* beg, uint32_t* cur, int n, int lane)
+{
+    uint32_t carry = 0;
+    for (int b0 = 0; b0 < n; b0 += 32) {
+        const int b = b0 + lane;
+        uint32_t c = b < n ? cnt[b] : 0u, x = c;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
+            if (lane >= d) x += y;
+        }
+        if (b < n) {
+            beg[b] = carry + x - c;
+            cur[b] = carry + x - c;
+        }
+        carry += __shfl_sync(0xffffffffu, x, 31);
+    }
+    if (lane == 0) beg[n] = carry;
+}
+
+// stable scatter of sample indices by key (sample order kept inside a key), by one warp
+__device__ __forceinline__ void warp_stable_scatter(const uint16_t* key, uint32_t* cur, uint16_t* ord, int total,
+                                                    int lane)
+{
+    const uint32_t lt = (1u << lane) - 1u;
+    for (int c0 = 0; c0 < total; c0 += 32) {
+        const int j = c0 + lane;
+        const bool valid = j < total;
+        const uint32_t k = valid ? (uint32_t)key[j] : 0x10000u + (uint32_t)lane;  // invalid lanes match nobody
+        const uint32_t mask = __match_any_sync(0xffffffffu, k);
+        uint32_t pos = 0;
+        if (valid) pos = cur[k] + (uint32_t)__popc(mask & lt);
+        __syncwarp();
+        if (valid) {
+            ord[pos] = (uint16_t)j;
+            if ((mask & lt) == 0u) cur[k] += (uint32_t)__popc(mask);  // lowest lane of the group advances the cursor
+        }
+        __syncwarp();
+    }
+}
+
 __global__ void __launch_bounds__(256) k_blend(VolConst V, const FrameDev* __restrict__ FD, BlendBufs B)
 {
     const FrameConst& F = FD->F;
-    const int nthr = blockDim.x;
-    extern __shared__ float4 smem4[];
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int nthr = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int p = blockIdx.x;
     const uint32_t base = __ldg(B.off + p);
     uint32_t m = __ldg(B.off + p + 1) - base;
     if (m > (uint32_t)(V.rays_max - kPilots) || base > V.R_main || m > V.R_main - base) {
-        if (threadIdx.x == 0) atomicOr(V.err, kErrRayRange);
+        if (tid == 0) atomicOr(V.err, kErrRayRange);
         m = 0;
     }
     const int npil = F.even ? kPilots : 0;
@@ -328,127 +433,212 @@ __global__ void __launch_bounds__(256) k_blend(VolConst V, const FrameDev* __res
     if (total == 0) return;  // untouched tile: nothing to read or write
     const int Ti = V.Ti, Td = V.Td, ni = V.n_irr, nd = V.n_dep;
     const int ti2 = Ti * Ti, td2 = Td * Td;
-    float4* tile_i = smem4;                                        // [ti2]
-    float4* acc_i = tile_i + ti2;                                  // [ti2] sum rgb, k
-    float2* tile_d = reinterpret_cast<float2*>(acc_i + ti2);       // [td2]
-    float* acc_d = reinterpret_cast<float*>(tile_d + td2);         // [td2*3]
-    uint32_t* cnt_d = reinterpret_cast<uint32_t*>(acc_d + 3 * td2);  // [td2]
-    const int tid = threadIdx.x;
-    for (int t = tid; t < ti2; t += nthr) acc_i[t] = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int t = tid; t < 3 * td2; t += nthr) acc_d[t] = 0.f;
+    const BlendLayout L = blend_layout(V.rays_max, Ti, Td);
+    float4* rec = reinterpret_cast<float4*>(smem + L.rec);
+    unsigned char* irr_raw = smem + L.irr_raw;
+    unsigned char* dep_raw = smem + L.dep_raw;
+    uint8_t* dn_raw = smem + L.dn_raw;
+    float4* irr_new = reinterpret_cast<float4*>(smem + L.irr_new);
+    float2* dep_new = reinterpret_cast<float2*>(smem + L.dep_new);
+    uint8_t* dn_new = smem + L.dn_new;
+    uint16_t* key_i = reinterpret_cast<uint16_t*>(smem + L.key_i);
+    uint16_t* key_d = reinterpret_cast<uint16_t*>(smem + L.key_d);
+    uint16_t* ord_i = reinterpret_cast<uint16_t*>(smem + L.ord_i);
+    uint16_t* ord_d = reinterpret_cast<uint16_t*>(smem + L.ord_d);
+    uint32_t* beg_i = reinterpret_cast<uint32_t*>(smem + L.beg_i);
+    uint32_t* beg_d = reinterpret_cast<uint32_t*>(smem + L.beg_d);
+    uint32_t* cur_i = reinterpret_cast<uint32_t*>(smem + L.cur_i);
+    uint32_t* cur_d = reinterpret_cast<uint32_t*>(smem + L.cur_d);
+    const uint32_t bar = smem_u32(smem);
+
+    // 1. stage records (always 16-byte multiples) and, when their sizes allow
+    //    16-byte bulk copies, the old tiles
+    const uint32_t irr_b = (uint32_t)ti2 * (V.fp16 ? 8u : 16u), dep_b = (uint32_t)td2 * (V.fp16 ? 4u : 8u);
+    const uint32_t dn_b = (uint32_t)td2;
+    const bool tiles_bulk = (irr_b % 16u) == 0u && (dep_b % 16u) == 0u && (dn_b % 16u) == 0u;
+    const unsigned char* g_irr = reinterpret_cast<const unsigned char*>(B.irr) + (size_t)p * irr_b;
+    const unsigned char* g_dep = reinterpret_cast<const unsigned char*>(B.dep) + (size_t)p * dep_b;
+    const uint8_t* g_dn = B.dep_n + (size_t)p * dn_b;
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    for (int t = tid; t < ti2; t += nthr) cur_i[t] = 0u;
+    for (int t = tid; t < td2; t += nthr) cur_d[t] = 0u;
     __syncthreads();
-    for (int j = tid; j < total; j += nthr) {
-        float3 d;
-        float4 rec;
-        if (j < npil) {
-            d = pilot_dir(F.pilot_key, (uint32_t)p, j);
-            rec = B.pil_rec[(size_t)p * kPilots + j];
-        } else {
-            uint32_t i = (uint32_t)(j - npil);
-            float4 s = __ldg(B.sf + (size_t)m * (m - 1) / 2 + i);
-            d = rotate(F.R, s);
-            rec = B.main_rec[base + i];
+    if (tid == 0) {
+        const uint32_t tx = 16u * (uint32_t)total + (tiles_bulk ? irr_b + dep_b + dn_b : 0u);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(tx) : "memory");
+        if (npil) bulk_g2s(rec, B.pil_rec + (size_t)p * kPilots, 16u * kPilots, bar);
+        if (m) bulk_g2s(rec + npil, B.main_rec + base, 16u * m, bar);
+        if (tiles_bulk) {
+            bulk_g2s(irr_raw, g_irr, irr_b, bar);
+            bulk_g2s(dep_raw, g_dep, dep_b, bar);
+            bulk_g2s(dn_raw, g_dn, dn_b, bar);
         }
-        float2 e = oct_encode_x(d);
-        int ti = texel_of(e, ni);
-        int td = texel_of(e, nd);
-        float* ai = reinterpret_cast<float*>(acc_i + ti);
-        atomicAdd(ai + 0, rec.x);
-        atomicAdd(ai + 1, rec.y);
-        atomicAdd(ai + 2, rec.z);
-        atomicAdd(ai + 3, 1.0f);
-        atomicAdd(acc_d + 3 * td + 0, rec.w);
-        atomicAdd(acc_d + 3 * td + 1, rec.w * rec.w);
-        atomicAdd(acc_d + 3 * td + 2, 1.0f);
     }
-    // stage the old tiles
-    const size_t io = (size_t)p * ti2, dof = (size_t)p * td2;
-    for (int t = tid; t < ti2; t += nthr) tile_i[t] = irr_load(B.irr, io + t, V.fp16);
-    for (int t = tid; t < td2; t += nthr) {
-        tile_d[t] = dep_load(B.dep, dof + t, V.fp16);
-        cnt_d[t] = B.dep_n[dof + t];
+    if (!tiles_bulk) {  // odd tile sizes: plain loads (4-byte words; the counts bytewise)
+        for (uint32_t t = tid; t < irr_b / 4u; t += nthr)
+            reinterpret_cast<uint32_t*>(irr_raw)[t] = reinterpret_cast<const uint32_t*>(g_irr)[t];
+        for (uint32_t t = tid; t < dep_b / 4u; t += nthr)
+            reinterpret_cast<uint32_t*>(dep_raw)[t] = reinterpret_cast<const uint32_t*>(g_dep)[t];
+        for (uint32_t t = tid; t < dn_b; t += nthr) dn_raw[t] = g_dn[t];
+    }
+    // sample directions -> nearest texels (the copies are in flight meanwhile)
+    const float4* sfm = B.sf + (size_t)m * (m - 1) / 2;
+    for (int j = tid; j < total; j += nthr) {
+        float3 d = j < npil ? pilot_dir(F.pilot_key, (uint32_t)p, j) : rotate(F.R, __ldg(sfm + (j - npil)));
+        float2 e = oct_encode_x(d);
+        const int ki = texel_of(e, ni), kd = texel_of(e, nd);
+        key_i[j] = (uint16_t)ki;
+        key_d[j] = (uint16_t)kd;
+        atomicAdd(cur_i + ki, 1u);  // integer counts: order-independent
+        atomicAdd(cur_d + kd, 1u);
     }
     __syncthreads();
+    // 2. per-texel buckets in sample order
+    const int wd = nthr > 32 ? 1 : 0;  // the warp that sorts the depth keys
+    if (warp == 0) warp_scan_bins(cur_i, beg_i, cur_i, ti2, lane);
+    if (warp == wd) warp_scan_bins(cur_d, beg_d, cur_d, td2, lane);
+    __syncthreads();
+    if (warp == 0) warp_stable_scatter(key_i, cur_i, ord_i, total, lane);
+    if (warp == wd) warp_stable_scatter(key_d, cur_d, ord_d, total, lane);
+    // the staged data must have landed (bounded wait; on time-out the CTA
+    // flags the volume and leaves the tiles as they were)
+    bool ok = false;
+    for (int it = 0; it < (1 << 22) && !ok; ++it) ok = mbar_try_wait(bar, 0u);
+    if (__syncthreads_or(!ok)) {
+        if (tid == 0) atomicOr(V.err, kErrWait);
+        for (int it = 0; it < (1 << 22) && !ok; ++it) ok = mbar_try_wait(bar, 0u);
+        return;
+    }
+    // 3. blend the touched interior texels
     const float omh = 1.0f - V.hyst;
     for (int t = tid; t < ti2; t += nthr) {
-        float4 a = acc_i[t];
-        if (a.w > 0.f) {
-            float4 v = tile_i[t];
-            float w = fmaxf(omh, a.w / (v.w + a.w));
-            float ik = 1.0f / a.w;
-            v.x += w * (a.x * ik - v.x);
-            v.y += w * (a.y * ik - v.y);
-            v.z += w * (a.z * ik - v.z);
-            v.w = fminf(v.w + a.w, 255.0f);
-            tile_i[t] = v;
+        const int i = t / Ti, jj = t - i * Ti;
+        if (i < 1 || i > ni || jj < 1 || jj > ni) continue;
+        float4 v;
+        if (V.fp16) {
+            const __half2* h = reinterpret_cast<const __half2*>(irr_raw) + 2 * t;
+            float2 a = __half22float2(h[0]), b2 = __half22float2(h[1]);
+            v = make_float4(a.x, a.y, b2.x, b2.y);
+        } else {
+            v = reinterpret_cast<const float4*>(irr_raw)[t];
         }
+        const uint32_t b0 = beg_i[t], b1 = beg_i[t + 1];
+        if (b1 > b0) {
+            float sx = 0.f, sy = 0.f, sz = 0.f;
+            for (uint32_t q = b0; q < b1; ++q) {
+                const float4 r = rec[ord_i[q]];
+                sx += r.x;
+                sy += r.y;
+                sz += r.z;
+            }
+            const float k = (float)(b1 - b0);
+            const float w = fmaxf(omh, k / (v.w + k));
+            const float ik = 1.0f / k;
+            v.x += w * (sx * ik - v.x);
+            v.y += w * (sy * ik - v.y);
+            v.z += w * (sz * ik - v.z);
+            v.w = fminf(v.w + k, 255.0f);
+        }
+        irr_new[t] = v;
     }
     for (int t = tid; t < td2; t += nthr) {
-        float k = acc_d[3 * t + 2];
-        if (k > 0.f) {
+        const int i = t / Td, jj = t - i * Td;
+        if (i < 1 || i > nd || jj < 1 || jj > nd) continue;
+        float2 v = V.fp16 ? __half22float2(reinterpret_cast<const __half2*>(dep_raw)[t])
+                          : reinterpret_cast<const float2*>(dep_raw)[t];
+        uint32_t c = dn_raw[t];
+        const uint32_t b0 = beg_d[t], b1 = beg_d[t + 1];
+        if (b1 > b0) {
             // the texel stores {mean, variance}; with batch mean m and batch
             // variance vb the moving average of {d, d^2} becomes
             //   mean' = mean + w (m - mean)
             //   var'  = (1-w) var + w vb + w (1-w) (m - mean)^2
             // (every term non-negative: no cancellation in storage)
-            float2 v = tile_d[t];
-            float c = (float)cnt_d[t];
-            float w = fmaxf(omh, k / (c + k));
-            float ik = 1.0f / k;
-            float m = acc_d[3 * t] * ik;
-            float vb = fmaxf(acc_d[3 * t + 1] * ik - m * m, 0.0f);
-            float dm = m - v.x;
+            float s1 = 0.f, s2 = 0.f;
+            for (uint32_t q = b0; q < b1; ++q) {
+                const float d = rec[ord_d[q]].w;
+                s1 += d;
+                s2 += d * d;
+            }
+            const float k = (float)(b1 - b0);
+            const float w = fmaxf(omh, k / ((float)c + k));
+            const float ik = 1.0f / k;
+            const float mb = s1 * ik;
+            const float vb = fmaxf(s2 * ik - mb * mb, 0.0f);
+            const float dm = mb - v.x;
             v.y = (1.0f - w) * v.y + w * vb + w * (1.0f - w) * dm * dm;
             v.x += w * dm;
-            tile_d[t] = v;
-            cnt_d[t] = (uint32_t)fminf(c + k, 255.0f);
+            c = (uint32_t)fminf((float)c + k, 255.0f);
         }
+        dep_new[t] = v;
+        dn_new[t] = (uint8_t)c;
     }
     __syncthreads();
-    // border texels copy their octahedral fold partners (interior, updated)
+    // 4. every texel (border ones from their octahedral fold partner) in the
+    //    storage format, into the staging buffers
+    const uint64_t srkey = F.pilot_key ^ (F.even ? 0x5352ull : 0x5353ull);
     for (int t = tid; t < ti2; t += nthr) {
-        int i = t / Ti, j = t - i * Ti;
-        if (i >= 1 && i <= ni && j >= 1 && j <= ni) continue;
-        int si, sj;
-        border_src(i, j, ni, si, sj);
-        tile_i[t] = tile_i[si * Ti + sj];
+        const int i = t / Ti, jj = t - i * Ti;
+        int src = t;
+        if (i < 1 || i > ni || jj < 1 || jj > ni) {
+            int si, sj;
+            border_src(i, jj, ni, si, sj);
+            src = si * Ti + sj;
+        }
+        const float4 v = irr_new[src];
+        if (V.fp16 == 2) {
+            __half2* h = reinterpret_cast<__half2*>(irr_raw) + 2 * t;
+            h[0] = __halves2half2(half_sr(v.x, sr_bits(srkey, p, t, 0)), half_sr(v.y, sr_bits(srkey, p, t, 1)));
+            h[1] = __halves2half2(half_sr(v.z, sr_bits(srkey, p, t, 2)), __float2half_rn(v.w));
+        } else if (V.fp16) {
+            __half2* h = reinterpret_cast<__half2*>(irr_raw) + 2 * t;
+            h[0] = __floats2half2_rn(v.x, v.y);
+            h[1] = __floats2half2_rn(v.z, v.w);
+        } else {
+            reinterpret_cast<float4*>(irr_raw)[t] = v;
+        }
     }
     for (int t = tid; t < td2; t += nthr) {
-        int i = t / Td, j = t - i * Td;
-        if (i >= 1 && i <= nd && j >= 1 && j <= nd) continue;
-        int si, sj;
-        border_src(i, j, nd, si, sj);
-        tile_d[t] = tile_d[si * Td + sj];
-        cnt_d[t] = cnt_d[si * Td + sj];
+        const int i = t / Td, jj = t - i * Td;
+        int src = t;
+        if (i < 1 || i > nd || jj < 1 || jj > nd) {
+            int si, sj;
+            border_src(i, jj, nd, si, sj);
+            src = si * Td + sj;
+        }
+        const float2 v = dep_new[src];
+        if (V.fp16 == 2)
+            reinterpret_cast<__half2*>(dep_raw)[t] =
+                __halves2half2(half_sr(v.x, sr_bits(srkey, p, t, 4)), half_sr(v.y, sr_bits(srkey, p, t, 5)));
+        else if (V.fp16)
+            reinterpret_cast<__half2*>(dep_raw)[t] = __floats2half2_rn(v.x, v.y);
+        else
+            reinterpret_cast<float2*>(dep_raw)[t] = v;
+        dn_raw[t] = dn_new[src];
     }
     __syncthreads();
-    if (V.fp16 == 2) {  // stochastic rounding, seeded by the frame, probe, texel and channel
-        const uint64_t key = F.pilot_key ^ (F.even ? 0x5352ull : 0x5353ull);
-        __half2* hi = reinterpret_cast<__half2*>(B.irr) + 2 * io;
-        for (int t = tid; t < ti2; t += nthr) {
-            float4 v = tile_i[t];
-            hi[2 * t] = __halves2half2(half_sr(v.x, sr_bits(key, p, t, 0)), half_sr(v.y, sr_bits(key, p, t, 1)));
-            hi[2 * t + 1] = __halves2half2(half_sr(v.z, sr_bits(key, p, t, 2)), __float2half_rn(v.w));
-        }
-        __half2* hd = reinterpret_cast<__half2*>(B.dep) + dof;
-        for (int t = tid; t < td2; t += nthr)
-            hd[t] = __halves2half2(half_sr(tile_d[t].x, sr_bits(key, p, t, 4)), half_sr(tile_d[t].y, sr_bits(key, p, t, 5)));
-    } else if (V.fp16) {
-        __half2* hi = reinterpret_cast<__half2*>(B.irr) + 2 * io;
-        for (int t = tid; t < ti2; t += nthr) {
-            float4 v = tile_i[t];
-            hi[2 * t] = __floats2half2_rn(v.x, v.y);
-            hi[2 * t + 1] = __floats2half2_rn(v.z, v.w);
-        }
-        __half2* hd = reinterpret_cast<__half2*>(B.dep) + dof;
-        for (int t = tid; t < td2; t += nthr) hd[t] = __floats2half2_rn(tile_d[t].x, tile_d[t].y);
+    // 5. coalesced write-back: 16-byte stores when the tile sizes allow
+    unsigned char* o_irr = reinterpret_cast<unsigned char*>(B.irr) + (size_t)p * irr_b;
+    unsigned char* o_dep = reinterpret_cast<unsigned char*>(B.dep) + (size_t)p * dep_b;
+    uint8_t* o_dn = B.dep_n + (size_t)p * dn_b;
+    if (tiles_bulk) {
+        for (uint32_t t = tid; t < irr_b / 16u; t += nthr)
+            reinterpret_cast<uint4*>(o_irr)[t] = reinterpret_cast<const uint4*>(irr_raw)[t];
+        for (uint32_t t = tid; t < dep_b / 16u; t += nthr)
+            reinterpret_cast<uint4*>(o_dep)[t] = reinterpret_cast<const uint4*>(dep_raw)[t];
+        for (uint32_t t = tid; t < dn_b / 16u; t += nthr)
+            reinterpret_cast<uint4*>(o_dn)[t] = reinterpret_cast<const uint4*>(dn_raw)[t];
     } else {
-        float4* gi = reinterpret_cast<float4*>(B.irr) + io;
-        for (int t = tid; t < ti2; t += nthr) gi[t] = tile_i[t];
-        float2* gd = reinterpret_cast<float2*>(B.dep) + dof;
-        for (int t = tid; t < td2; t += nthr) gd[t] = tile_d[t];
+        for (uint32_t t = tid; t < irr_b / 4u; t += nthr)
+            reinterpret_cast<uint32_t*>(o_irr)[t] = reinterpret_cast<const uint32_t*>(irr_raw)[t];
+        for (uint32_t t = tid; t < dep_b / 4u; t += nthr)
+            reinterpret_cast<uint32_t*>(o_dep)[t] = reinterpret_cast<const uint32_t*>(dep_raw)[t];
+        for (uint32_t t = tid; t < dn_b; t += nthr) o_dn[t] = dn_raw[t];
     }
-    for (int t = tid; t < td2; t += nthr) B.dep_n[dof + t] = (uint8_t)cnt_d[t];
 }
 
 // ============================================================== query
@@ -468,11 +658,7 @@ __global__ void __launch_bounds__(128) k_query(VolConst V, const void* __restric
 
 }  // namespace
 
-size_t blend_smem_bytes(const VolConst& V)
-{
-    size_t ti2 = (size_t)V.Ti * V.Ti, td2 = (size_t)V.Td * V.Td;
-    return ti2 * 16 * 2 + td2 * 8 + td2 * 12 + td2 * 4;
-}
+size_t blend_smem_bytes(const VolConst& V) { return blend_layout(V.rays_max, V.Ti, V.Td).total; }
 
 cudaError_t launch_change(const VolConst& V, const FrameDev* FD, const ChangeBufs& B, cudaStream_t s)
 {
