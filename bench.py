@@ -31,11 +31,11 @@ if ROOT not in sys.path:
 import numpy as np  # noqa: E402
 
 # FP32 lane operations per unit of traversal work (counted from the kernels'
-# arithmetic): one BVH node visit tests two child boxes (6 sub, 6 mul,
-# 8 min/max, 2 compare each = 22, so 44); one watertight triangle test is
-# 9 sub + 6 mul/sub pairs + 6 mul + 3 sub + 2 add (det) + 3 mul + 4 (T) +
-# 1 div (counted 8) + 6 compares = 55.
-OPS_NODE = 44
+# arithmetic): one child-box slab test is 6 sub, 6 mul, 8 min/max and 2
+# compares = 22 (a node visit tests both child boxes); one watertight triangle
+# test is 9 sub + 6 mul/sub pairs + 6 mul + 3 sub + 2 add (det) + 3 mul +
+# 4 (T) + 1 div (counted 8) + 6 compares = 55.
+OPS_BOX = 22
 OPS_TRI = 55
 # algorithmic blend bytes per touched probe tile: read + write of the
 # irradiance tile (8x8 float4 = 1024 B), depth tile (16x16 float2 = 2048 B)
@@ -472,6 +472,8 @@ def run_ours(args):
             step(f)
     torch.cuda.synchronize()
     phases = {k: [] for k in adgi.PHASES}
+    shadow_ms = [[], []]
+    plan_ms = []
     dev_ms, host_ms = [], []
     tiles_touched, rays_blended = [], []
     clocks = Clocks()
@@ -498,6 +500,9 @@ def run_ours(args):
         st = vol.stats()
         for i, name in enumerate(adgi.PHASES):
             phases[name].append(st.ms_phase[i])
+        for i in range(2):
+            shadow_ms[i].append(st.ms_shadow[i])
+        plan_ms.append(st.ms_blend_plan)
         n = vol.n()
         m = n.astype(np.int64) - 8
         even = f % 2 == 0
@@ -514,32 +519,37 @@ def run_ours(args):
     value = ws * rays / (ms_step / 1e3)
     hbm, smax_nominal, peak_src = _peaks()
     mean_ph = {k: float(np.mean(v)) for k, v in phases.items()}
-    dominant = max(mean_ph, key=mean_ph.get)
+    # per-kernel device times (CUDA events on the volume's stream around each
+    # kernel) and the counted traversal work of each traversal kernel
+    kern_ms = {"k_main_trace": mean_ph["trace"], "k_shadow (adaptive rays)": float(np.mean(shadow_ms[1])),
+               "k_pilot_trace": mean_ph["pilot_trace"], "k_shadow (pilot rays)": float(np.mean(shadow_ms[0])),
+               "k_blend": mean_ph["blend"], "k_blend_plan (side stream, overlapped)": float(np.mean(plan_ms))}
+    work = {
+        "k_pilot_trace": OPS_BOX * counts[0] + OPS_TRI * counts[1],
+        "k_shadow (pilot rays)": OPS_BOX * counts[2] + OPS_TRI * counts[3],
+        "k_main_trace": OPS_BOX * counts[4] + OPS_TRI * counts[5],
+        "k_shadow (adaptive rays)": OPS_BOX * counts[6] + OPS_TRI * counts[7],
+    }
+    dominant = max((k for k in kern_ms if "side stream" not in k), key=kern_ms.get)
     # ALU roofline of a traversal kernel: counted FP32 lane ops / time vs
     # 152 SMs x 128 FP32 lanes x max SM clock
     alu_peak = 152 * 128 * smax_nominal * 1e6 / 1e12  # T lane-ops/s
-    work = {
-        "pilot_trace": OPS_NODE * counts[0] + OPS_TRI * counts[1],
-        "pilot_shade": OPS_NODE * counts[2] + OPS_TRI * counts[3],
-        "trace": OPS_NODE * counts[4] + OPS_TRI * counts[5],
-        "shade": OPS_NODE * counts[6] + OPS_TRI * counts[7],
-    }
     tile_bytes = TILE_BYTES_FP32 if not args.fp16 else 2 * (8 * 8 * 8 + 16 * 16 * 4 + 16 * 16)
     blend_bytes = float(np.mean(tiles_touched)) * tile_bytes + float(np.mean(rays_blended)) * REC_BYTES
     blend_ach = blend_bytes / (mean_ph["blend"] / 1e3) / 1e9
-    kname = {"trace": "k_main_trace", "shade": "k_main_shade", "pilot_trace": "k_pilot_trace",
-             "pilot_shade": "k_pilot_shade", "blend": "k_blend", "bvh": "k_scatter"}
     if dominant in work:
-        ach = work[dominant] / (mean_ph[dominant] / 1e3) / 1e12
+        ach = work[dominant] / (kern_ms[dominant] / 1e3) / 1e12
+        kbase = dominant.split(" ")[0]
         roof = {"bound": "alu", "achieved": ach, "peak": alu_peak, "unit": "Tops/s (FP32 lane ops)",
-                "frac": ach / alu_peak, "traffic": _ncu_traffic(kname.get(dominant, dominant)),
-                "kernel": kname.get(dominant, dominant), "ms": mean_ph[dominant],
-                "peak_source": "152 SMs x 128 FP32 lanes x %.0f MHz" % smax_nominal}
+                "frac": ach / alu_peak, "traffic": _ncu_traffic(kbase), "kernel": dominant,
+                "ms": kern_ms[dominant], "work_lane_ops": work[dominant],
+                "peak_source": "152 SMs x 128 FP32 lanes x %.0f MHz (nominal max clock)" % smax_nominal}
     else:
         roof = {"bound": "hbm", "achieved": blend_ach, "peak": hbm, "unit": "GB/s", "frac": blend_ach / hbm,
                 "traffic": _ncu_traffic("k_blend"), "kernel": "k_blend", "ms": mean_ph["blend"]}
     roof_blend = {"bound": "hbm", "achieved": blend_ach, "peak": hbm, "unit": "GB/s", "frac": blend_ach / hbm,
                   "traffic": _ncu_traffic("k_blend"), "algorithmic_bytes": blend_bytes, "ms": mean_ph["blend"],
+                  "kernel": "k_blend (the per-frame plan runs beforehand on a side stream, see kernels_ms)",
                   "peak_source": "%s hbm_gbs" % peak_src}
     # end to end through the C ABI with host buffers
     e2e = None
@@ -592,9 +602,10 @@ def run_ours(args):
             "latency_ms": {"device_p50": float(np.percentile(dev_ms, 50)), "device_p99": float(np.percentile(dev_ms, 99)),
                            "host_p50": float(np.percentile(host_ms, 50)), "host_p99": float(np.percentile(host_ms, 99))},
             "phases_ms": mean_ph,
-            "traversal_counts": {"pilot_nodes": counts[0], "pilot_tris": counts[1], "pilot_shadow_nodes": counts[2],
-                                 "pilot_shadow_tris": counts[3], "nodes": counts[4], "tris": counts[5],
-                                 "shadow_nodes": counts[6], "shadow_tris": counts[7]},
+            "kernels_ms": kern_ms,
+            "traversal_counts": {"pilot_boxes": counts[0], "pilot_tris": counts[1], "pilot_shadow_boxes": counts[2],
+                                 "pilot_shadow_tris": counts[3], "boxes": counts[4], "tris": counts[5],
+                                 "shadow_boxes": counts[6], "shadow_tris": counts[7]},
             "rays_incl_shadow_per_s": ws * (rays + vol.stats().shadow_rays) / (ms_step / 1e3),
             "roofline": roof,
             "roofline_blend": roof_blend,

@@ -111,6 +111,9 @@ typedef struct {
                                  0 BVH rebuild, 1 pilot trace, 2 pilot shade, 3 heuristics,
                                  4 allocation, 5 adaptive trace, 6 adaptive shade, 7 blend */
     uint64_t kernels_launched; /* kernels this library has launched in the process so far */
+    float ms_shadow[2];        /* device time of the shadow-ray kernel inside phases 2 and 6 (timing enabled) */
+    float ms_blend_plan;       /* device time of the per-frame blend plan, which runs on a side stream
+                                  beside phases 1-6 (timing enabled) */
 } adgi_stats;
 
 /* Create a volume on the current CUDA device.  desc: host pointer, copied.
@@ -187,7 +190,8 @@ int adgi_batch_destroy(adgi_batch batch);
 /* Block shapes of a volume's kernels.  adgi_autotune times candidate shapes
  * of the nearest-hit traversal (64/128/256 threads), the shading wavefront
  * (prep/finish blocks 64/128/256 x shadow grid of 0 = occupancy, 2, 4, 8
- * blocks per SM) and the blend (64/128/256 threads per probe tile) on the
+ * blocks per SM) and the blend (32/64/128 threads per CTA: one warp per probe
+ * tile, so 1, 2 or 4 tiles per CTA) on the
  * volume's own data and keeps the fastest; results do not depend on the
  * shapes.  It needs one update first, uses that update's rays (reps timed
  * repetitions per candidate), leaves the atlases and the heuristic state as
@@ -281,9 +285,10 @@ int adgi_trace_closest(adgi_volume vol, const float* o, const float* d, int32_t 
  * last update's pilot and adaptive rays (and their shadow rays for the lights
  * of *frame, which must be the last update's frame) with counters, without
  * changing any state.  counts (host uint64[8]) receives, for the pilot rays
- * then for the adaptive rays: nearest-hit node visits, nearest-hit triangle
- * tests, shadow-ray node visits, shadow-ray triangle tests.  Synchronises the
- * stream.  Errors: INVALID_ARG, NO_SCENE, CUDA. */
+ * then for the adaptive rays: nearest-hit box tests, nearest-hit triangle
+ * tests, shadow-ray box tests, shadow-ray triangle tests (a BVH node visit
+ * tests the boxes of both children: 2 box tests).  Synchronises the stream.
+ * Errors: INVALID_ARG, NO_SCENE, CUDA. */
 int adgi_count_traversal(adgi_volume vol, const adgi_frame* frame, uint64_t* counts);
 
 /* Build the linear BVH (Morton codes, stable radix sort, radix tree,

@@ -87,6 +87,8 @@ class adgi_stats(C.Structure):
         ("ms_last_update", C.c_float),
         ("ms_phase", C.c_float * 8),
         ("kernels_launched", C.c_uint64),
+        ("ms_shadow", C.c_float * 2),
+        ("ms_blend_plan", C.c_float),
     ]
 
 

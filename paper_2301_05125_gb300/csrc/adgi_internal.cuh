@@ -263,183 +263,152 @@ __device__ __forceinline__ bool slab(float lox, float loy, float loz, float hix,
 
 constexpr float kBoxSlack = 1.0001f;  // pruning slack on the best t (conservative)
 // LBVH depth is at most 95 (63 key bits + 32 index bits); a PLOC tree can be
-// deeper, so its builder checks the depth against this bound.
-constexpr int kStack = 96;
+// deeper, so its builder checks the depth against kMaxDepth.  The near-first
+// traversal stack holds at most one pending entry per level.
+constexpr int kMaxDepth = 96;
+constexpr int kStack = kMaxDepth;
 
 // Traversal of the two-part scene as one flat loop over one stack: an entry
 // is an internal node of part 0 (bit 30 clear) or part 1 (bit 30 set).  The
 // loop has no early exit, so the lanes of a warp reconverge every iteration.
 constexpr int kPartBit = 1 << 30;
 
-// nearest hit with t in (tmin, tmax]; (t, original index) lexicographic
-__device__ __forceinline__ void trace_closest(const SceneDev& S, float3 o, float3 d, float tmin, float tmax,
-                                              float& t_best, uint32_t& hit_best, uint32_t* nvis = nullptr,
-                                              uint32_t* ntri = nullptr)
+// One traversal in flight.  Closest hit: t in (tmin, tmax], ranked by
+// (t, original index) -- a strict order, so the result does not depend on
+// the traversal order.  Any hit: t in (tmin, tmax), stops at the first.
+// The state is scalars only, so it can live in registers; the node stack is
+// a separate local array.
+struct Trav {
+    WRay wr;
+    float3 o, inv;
+    float tmin, tmax, lim;  // lim: box pruning bound
+    float t_best, best_det;
+    int best_orig;
+    bool found;
+    int sp, iter;
+};
+
+__device__ __forceinline__ void trav_tri(Trav& T, const float4* tv, bool any, uint32_t* ntri)
 {
-    t_best = tmax;
-    hit_best = kMiss;
-    if (S.n_tris == 0) return;
-    const WRay wr = wray(o, d);
-    const float3 inv = make_float3(1.0f / d.x, 1.0f / d.y, 1.0f / d.z);
-    int best_orig = 0x7FFFFFFF;
-    float best_det = 0.0f;
-    bool found = false;
-    int stack[kStack + 2];
-    int sp = 0;
-    int iter = 0;
-    const int max_iter = S.part[0].max_iter + S.part[1].max_iter;
-    // single-triangle parts are tested up front; trees are pushed
-    for (int pi = 1; pi >= 0; --pi) {
-        const int nt = pi ? S.part[1].n_tris : S.part[0].n_tris;
-        const int rl = pi ? S.part[1].root_leaf : S.part[0].root_leaf;
-        if (nt >= 2) stack[sp++] = pi ? kPartBit : 0;
-        else if (nt == 1) {
-            const float4* tv = (pi ? S.part[1].tri_v : S.part[0].tri_v) + 3 * (size_t)rl;
-            float4 A = __ldg(tv), Bv = __ldg(tv + 1), C = __ldg(tv + 2);
-            float tt, det;
-            if (ntri) ++*ntri;
-            if (wtri(wr, A, Bv, C, tt, det) && tt > tmin) {
-                int orig = __float_as_int(A.w);
-                bool better = found ? (tt < t_best || (tt == t_best && orig < best_orig)) : (tt <= tmax);
-                if (better) {
-                    found = true;
-                    t_best = tt;
-                    best_orig = orig;
-                    best_det = det;
-                }
-            }
-        }
+    if (ntri) ++*ntri;
+    float4 A = __ldg(tv), Bv = __ldg(tv + 1), C = __ldg(tv + 2);
+    float tt, det;
+    if (!wtri(T.wr, A, Bv, C, tt, det) || !(tt > T.tmin)) return;
+    if (any) {
+        if (tt < T.tmax) T.found = true;
+        return;
     }
-    while (sp > 0) {
-        if (++iter > max_iter) {
-            atomicOr(S.err, kErrTraversal);
-            break;
-        }
-        if (nvis) ++*nvis;
-        const int e = stack[--sp];
-        const int part = e & kPartBit;
-        const BNode* nodes = part ? S.part[1].nodes : S.part[0].nodes;
-        const float4* tris = part ? S.part[1].tri_v : S.part[0].tri_v;
-        const BNode* nd = nodes + (e & ~kPartBit);
-        float4 a = __ldg(&nd->a), b = __ldg(&nd->b), c = __ldg(&nd->c);
-        int4 ch = __ldg(&nd->d);
-        float lim = t_best * kBoxSlack;
-        float t0, t1;
-        bool h0 = slab(a.x, a.y, a.z, a.w, b.x, b.y, o, inv, lim, t0);
-        bool h1 = slab(b.z, b.w, c.x, c.y, c.z, c.w, o, inv, lim, t1);
-#pragma unroll
-        for (int k = 0; k < 2; ++k) {
-            const bool hk = k ? h1 : h0;
-            const int ck = k ? ch.y : ch.x;
-            if (hk && ck < 0) {
-                if (ntri) ++*ntri;
-                const float4* tv = tris + 3 * (size_t)(~ck);
-                float4 A = __ldg(tv), Bv = __ldg(tv + 1), C = __ldg(tv + 2);
-                float tt, det;
-                if (wtri(wr, A, Bv, C, tt, det) && tt > tmin) {
-                    int orig = __float_as_int(A.w);
-                    bool better = found ? (tt < t_best || (tt == t_best && orig < best_orig)) : (tt <= tmax);
-                    if (better) {
-                        found = true;
-                        t_best = tt;
-                        best_orig = orig;
-                        best_det = det;
-                    }
-                }
-            }
-        }
-        const bool i0 = h0 && ch.x >= 0, i1 = h1 && ch.y >= 0;
-        if (i0 && i1) {  // far child below the near one
-            const bool first0 = t0 <= t1;
-            if (sp + 2 <= kStack + 2) {
-                stack[sp++] = (first0 ? ch.y : ch.x) | part;
-                stack[sp++] = (first0 ? ch.x : ch.y) | part;
-            } else {
-                atomicOr(S.err, kErrTraversal);  // cannot happen: depths are bounded by the builders
-            }
-        } else if (i0 || i1) {
-            if (sp < kStack + 2)
-                stack[sp++] = (i0 ? ch.x : ch.y) | part;
-            else
-                atomicOr(S.err, kErrTraversal);
-        }
+    const int orig = __float_as_int(A.w);
+    const bool better = T.found ? (tt < T.t_best || (tt == T.t_best && orig < T.best_orig)) : (tt <= T.tmax);
+    if (better) {
+        T.found = true;
+        T.t_best = tt;
+        T.best_orig = orig;
+        T.best_det = det;
     }
-    if (found) hit_best = (uint32_t)best_orig | (best_det < 0.0f ? kBackBit : 0u);
 }
 
-// any hit with t strictly inside (tlo, thi)
-__device__ __forceinline__ bool trace_any(const SceneDev& S, float3 o, float3 d, float tlo, float thi,
-                                          uint32_t* nvis = nullptr, uint32_t* ntri = nullptr)
+// set up a traversal; single-triangle parts are tested here, trees pushed
+__device__ __forceinline__ void trav_init(Trav& T, int* stack, const SceneDev& S, float3 o, float3 d, float tmin,
+                                          float tmax, bool any, uint32_t* ntri = nullptr)
 {
-    if (S.n_tris == 0) return false;
-    const WRay wr = wray(o, d);
-    const float3 inv = make_float3(1.0f / d.x, 1.0f / d.y, 1.0f / d.z);
-    const float lim = isinf(thi) ? thi : thi * kBoxSlack;
-    bool hit = false;
-    int stack[kStack + 2];
-    int sp = 0;
-    int iter = 0;
-    const int max_iter = S.part[0].max_iter + S.part[1].max_iter;
+    T.wr = wray(o, d);
+    T.o = o;
+    T.inv = make_float3(1.0f / d.x, 1.0f / d.y, 1.0f / d.z);
+    T.tmin = tmin;
+    T.tmax = tmax;
+    T.lim = any ? (isinf(tmax) ? tmax : tmax * kBoxSlack) : tmax * kBoxSlack;
+    T.t_best = tmax;
+    T.best_det = 0.0f;
+    T.best_orig = 0x7FFFFFFF;
+    T.found = false;
+    T.sp = 0;
+    T.iter = 0;
+    if (S.n_tris == 0) return;
     for (int pi = 1; pi >= 0; --pi) {
         const int nt = pi ? S.part[1].n_tris : S.part[0].n_tris;
         const int rl = pi ? S.part[1].root_leaf : S.part[0].root_leaf;
-        if (nt >= 2) stack[sp++] = pi ? kPartBit : 0;
-        else if (nt == 1) {
-            const float4* tv = (pi ? S.part[1].tri_v : S.part[0].tri_v) + 3 * (size_t)rl;
-            float4 A = __ldg(tv), Bv = __ldg(tv + 1), C = __ldg(tv + 2);
-            float tt, det;
-            if (ntri) ++*ntri;
-            if (wtri(wr, A, Bv, C, tt, det) && tt > tlo && tt < thi) hit = true;
-        }
+        if (nt >= 2)
+            stack[T.sp++] = pi ? kPartBit : 0;
+        else if (nt == 1)
+            trav_tri(T, (pi ? S.part[1].tri_v : S.part[0].tri_v) + 3 * (size_t)rl, any, ntri);
     }
-    if (hit) sp = 0;
-    while (sp > 0) {
-        if (++iter > max_iter) {
-            atomicOr(S.err, kErrTraversal);
-            break;
-        }
-        if (nvis) ++*nvis;
-        const int e = stack[--sp];
-        const int part = e & kPartBit;
-        const BNode* nodes = part ? S.part[1].nodes : S.part[0].nodes;
-        const float4* tris = part ? S.part[1].tri_v : S.part[0].tri_v;
-        const BNode* nd = nodes + (e & ~kPartBit);
-        float4 a = __ldg(&nd->a), b = __ldg(&nd->b), c = __ldg(&nd->c);
-        int4 ch = __ldg(&nd->d);
-        float t0, t1;
-        bool h0 = slab(a.x, a.y, a.z, a.w, b.x, b.y, o, inv, lim, t0);
-        bool h1 = slab(b.z, b.w, c.x, c.y, c.z, c.w, o, inv, lim, t1);
-#pragma unroll
-        for (int k = 0; k < 2; ++k) {
-            const bool hk = k ? h1 : h0;
-            const int ck = k ? ch.y : ch.x;
-            if (hk && ck < 0) {
-                if (ntri) ++*ntri;
-                const float4* tv = tris + 3 * (size_t)(~ck);
-                float4 A = __ldg(tv), Bv = __ldg(tv + 1), C = __ldg(tv + 2);
-                float tt, det;
-                if (wtri(wr, A, Bv, C, tt, det) && tt > tlo && tt < thi) hit = true;
-            }
-        }
-        const bool i0 = h0 && ch.x >= 0, i1 = h1 && ch.y >= 0;
-        if (i0 && i1) {  // nearer child first: blockers near the origin end the search sooner
-            const bool first0 = t0 <= t1;
-            if (sp + 2 <= kStack + 2) {
-                stack[sp++] = (first0 ? ch.y : ch.x) | part;
-                stack[sp++] = (first0 ? ch.x : ch.y) | part;
-            } else {
-                atomicOr(S.err, kErrTraversal);  // cannot happen: depths are bounded by the builders
-            }
-        } else if (i0 || i1) {
-            if (sp < kStack + 2)
-                stack[sp++] = (i0 ? ch.x : ch.y) | part;
-            else
-                atomicOr(S.err, kErrTraversal);
-        }
-        if (hit) sp = 0;
-    }
-    return hit;
+    if (any && T.found) T.sp = 0;
 }
+
+// one node visit; false once the traversal is over
+__device__ __forceinline__ bool trav_step(Trav& T, int* stack, const SceneDev& S, bool any,
+                                          uint32_t* nbox = nullptr, uint32_t* ntri = nullptr)
+{
+    if (T.sp <= 0) return false;
+    if (++T.iter > S.part[0].max_iter + S.part[1].max_iter) {
+        atomicOr(S.err, kErrTraversal);
+        T.sp = 0;
+        return false;
+    }
+    if (nbox) *nbox += 2;
+    const int e = stack[--T.sp];
+    const int part = e & kPartBit;
+    const BNode* nd = (part ? S.part[1].nodes : S.part[0].nodes) + (e & ~kPartBit);
+    const float4* tris = part ? S.part[1].tri_v : S.part[0].tri_v;
+    float4 a = __ldg(&nd->a), b = __ldg(&nd->b), c = __ldg(&nd->c);
+    int4 ch = __ldg(&nd->d);
+    const float lim = any ? T.lim : T.t_best * kBoxSlack;
+    float t0, t1;
+    const bool h0 = slab(a.x, a.y, a.z, a.w, b.x, b.y, T.o, T.inv, lim, t0);
+    const bool h1 = slab(b.z, b.w, c.x, c.y, c.z, c.w, T.o, T.inv, lim, t1);
+    if (h0 && ch.x < 0) trav_tri(T, tris + 3 * (size_t)(~ch.x), any, ntri);
+    if (h1 && ch.y < 0) trav_tri(T, tris + 3 * (size_t)(~ch.y), any, ntri);
+    const bool i0 = h0 && ch.x >= 0, i1 = h1 && ch.y >= 0;
+    if (i0 && i1) {  // far child below the near one
+        const bool first0 = t0 <= t1;
+        if (T.sp + 2 <= kStack + 2) {
+            stack[T.sp++] = (first0 ? ch.y : ch.x) | part;
+            stack[T.sp++] = (first0 ? ch.x : ch.y) | part;
+        } else {
+            atomicOr(S.err, kErrTraversal);  // cannot happen: depths are bounded by the builders
+        }
+    } else if (i0 || i1) {
+        if (T.sp < kStack + 2)
+            stack[T.sp++] = (i0 ? ch.x : ch.y) | part;
+        else
+            atomicOr(S.err, kErrTraversal);
+    }
+    if (any && T.found) T.sp = 0;  // a blocker ends a shadow ray
+    return T.sp > 0;
+}
+
+__device__ __forceinline__ uint32_t trav_hit(const Trav& T)
+{
+    return T.found ? ((uint32_t)T.best_orig | (T.best_det < 0.0f ? kBackBit : 0u)) : kMiss;
+}
+
+// nearest hit with t in (tmin, tmax] (one thread, one ray)
+__device__ __forceinline__ void trace_closest(const SceneDev& S, float3 o, float3 d, float tmin, float tmax,
+                                              float& t_best, uint32_t& hit_best, uint32_t* nbox = nullptr,
+                                              uint32_t* ntri = nullptr)
+{
+    Trav T;
+    int stack[kStack + 2];
+    trav_init(T, stack, S, o, d, tmin, tmax, false, ntri);
+    while (trav_step(T, stack, S, false, nbox, ntri)) {
+    }
+    t_best = T.t_best;
+    hit_best = trav_hit(T);
+}
+
+// any hit with t in (tlo, thi): shadow visibility (one thread, one ray)
+__device__ __forceinline__ bool trace_any(const SceneDev& S, float3 o, float3 d, float tlo, float thi,
+                                          uint32_t* nbox = nullptr, uint32_t* ntri = nullptr)
+{
+    Trav T;
+    int stack[kStack + 2];
+    trav_init(T, stack, S, o, d, tlo, thi, true, ntri);
+    while (trav_step(T, stack, S, true, nbox, ntri)) {
+    }
+    return T.found;
+}
+
 
 // ----------------------------------------------------------------- atlas access
 __device__ __forceinline__ float4 irr_load(const void* irr, size_t idx, int fp16)

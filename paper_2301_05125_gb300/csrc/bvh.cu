@@ -653,7 +653,7 @@ cudaError_t build_ploc(const BvhBufs& B, const PlocBufs& Q, const float* d_verts
     e = cudaMemcpyAsync(&depth, Q.total, sizeof(int), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return e;
-    if (depth >= kStack) return build_lbvh(B, d_verts, d_idx, nv, nt, eps, err, s, root_leaf, list);
+    if (depth >= kMaxDepth) return build_lbvh(B, d_verts, d_idx, nv, nt, eps, err, s, root_leaf, list);
     return cudaGetLastError();
 }
 

@@ -53,21 +53,59 @@ int fail(int code, const std::string& msg)
 const double kGaCos = -0.7373688780783197;  // cos(pi (3 - sqrt 5))
 const double kGaSin = 0.6754902942615238;   // sin(pi (3 - sqrt 5))
 
+// Spherical Fibonacci sets SF_m, m = 1..M, one row of m points per m.  Row m
+// lists its points in the order of a Morton curve over their octahedral
+// coordinates, and .w holds each point's SF index i (int bits): a warp that
+// takes 32 consecutive positions traces a compact cone of directions, while
+// every result is still stored under its SF index.
 void build_sf(int M, std::vector<float4>& out)
 {
     out.resize((size_t)M * (M + 1) / 2 + 1);
+    std::vector<float4> pts;
+    std::vector<std::pair<uint32_t, int>> order;
+    auto spread = [](uint32_t x) {  // 10 bits -> every second bit
+        x &= 0x3FFu;
+        x = (x | (x << 8)) & 0x00FF00FFu;
+        x = (x | (x << 4)) & 0x0F0F0F0Fu;
+        x = (x | (x << 2)) & 0x33333333u;
+        x = (x | (x << 1)) & 0x55555555u;
+        return x;
+    };
     for (int m = 1; m <= M; ++m) {
         float4* dst = out.data() + (size_t)m * (m - 1) / 2;
+        pts.resize((size_t)m);
+        order.resize((size_t)m);
         double c = 1.0, s = 0.0;
         for (int i = 0; i < m; ++i) {
             double z = 1.0 - (2.0 * (double)i + 1.0) / (double)m;
             double r2 = 1.0 - z * z;
             double r = r2 > 0.0 ? std::sqrt(r2) : 0.0;
-            dst[i] = make_float4((float)(r * c), (float)(r * s), (float)z, 0.0f);
+            double x = r * c, y = r * s;
+            pts[(size_t)i] = make_float4((float)x, (float)y, (float)z, 0.0f);
+            // octahedral coordinates in [-1,1]^2 (any order would do: this one
+            // only groups nearby directions)
+            double l1 = std::fabs(x) + std::fabs(y) + std::fabs(z);
+            double u = x / l1, v = y / l1;
+            if (z < 0.0) {
+                double uu = (1.0 - std::fabs(v)) * (u >= 0.0 ? 1.0 : -1.0);
+                double vv = (1.0 - std::fabs(u)) * (v >= 0.0 ? 1.0 : -1.0);
+                u = uu;
+                v = vv;
+            }
+            uint32_t qu = (uint32_t)std::min(1023.0, std::max(0.0, (u + 1.0) * 512.0));
+            uint32_t qv = (uint32_t)std::min(1023.0, std::max(0.0, (v + 1.0) * 512.0));
+            order[(size_t)i] = {spread(qu) | (spread(qv) << 1), i};
             double cn = c * kGaCos - s * kGaSin;
             double sn = s * kGaCos + c * kGaSin;
             c = cn;
             s = sn;
+        }
+        std::sort(order.begin(), order.end());
+        for (int k = 0; k < m; ++k) {
+            const int i = order[(size_t)k].second;
+            float4 q = pts[(size_t)i];
+            std::memcpy(&q.w, &i, sizeof(int));
+            dst[k] = q;
         }
     }
 }
@@ -122,6 +160,8 @@ struct adgi_volume_s {
     size_t bytes = 0;
     // tables
     float4* sf = nullptr;
+    uint16_t* plan = nullptr;  // per-frame blend plan (BlendPlan)
+    uint16_t* tex_src = nullptr;  // per texel: itself, or a border texel's octahedral fold partner
     uint16_t* lut_v = nullptr;
     uint16_t* lut_c = nullptr;
     // atlases
@@ -183,6 +223,10 @@ struct adgi_volume_s {
     bool timing = false;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     cudaEvent_t ph[9] = {};  // phase boundaries of the last timed update
+    cudaEvent_t shq[4] = {};  // around the shadow-ray kernel: pilot, adaptive
+    cudaStream_t side = nullptr;  // the blend plan runs here, beside the traces
+    cudaEvent_t fork = nullptr, join = nullptr;
+    cudaEvent_t plq[2] = {};  // around the blend plan (timing)
     bool timed_pending = false;
     // query scratch for host pointers
     float* q_buf = nullptr;
@@ -194,7 +238,7 @@ namespace {
 void free_volume(adgi_volume v)
 {
     if (!v) return;
-    void* ptrs[] = {v->sf,      v->lut_v,   v->lut_c,  v->irr,   v->dep,     v->dep_n,   v->qv,     v->qr,
+    void* ptrs[] = {v->sf,      v->plan,    v->tex_src, v->lut_v,   v->lut_c,  v->irr,   v->dep,     v->dep_n,   v->qv,     v->qr,
                     v->qv_even, v->qr_even, v->amp_v,  v->amp_r, v->trv,     v->trr,     v->age_v,  v->age_r,
                     v->G,       v->W,       v->n,      v->off,   v->pil_hit, v->pil_rec, v->pil_lum, v->m_hit,
                     v->m_rec,   v->shadow_ctr, v->verts, v->idx, v->albedo,  v->q_buf, v->err,
@@ -211,6 +255,13 @@ void free_volume(adgi_volume v)
     if (v->ev1) cudaEventDestroy(v->ev1);
     for (cudaEvent_t e : v->ph)
         if (e) cudaEventDestroy(e);
+    for (cudaEvent_t e : v->shq)
+        if (e) cudaEventDestroy(e);
+    for (cudaEvent_t e : v->plq)
+        if (e) cudaEventDestroy(e);
+    if (v->fork) cudaEventDestroy(v->fork);
+    if (v->join) cudaEventDestroy(v->join);
+    if (v->side) cudaStreamDestroy(v->side);
     if (v->gexec) cudaGraphExecDestroy(v->gexec);
     if (v->graph) cudaGraphDestroy(v->graph);
     if (v->cap_stream) cudaStreamDestroy(v->cap_stream);
@@ -315,6 +366,28 @@ int adgi_create_volume(const adgi_volume_desc* desc, void* cuda_stream, adgi_vol
     std::vector<float4> sf;
     build_sf(M > 0 ? M : 0, sf);
     DA(v->sf, sf.size());
+    DA(v->plan, blend_plan_elems(M > 0 ? M : 0));
+    DA(v->tex_src, (size_t)V.Ti * V.Ti + (size_t)V.Td * V.Td);
+    std::vector<uint16_t> tsrc;
+    for (int n : {V.n_irr, V.n_dep}) {  // octahedral border fold of a tile with n x n interior
+        const int T = n + 2;
+        for (int i = 0; i < T; ++i)
+            for (int j = 0; j < T; ++j) {
+                int si = i, sj = j;
+                const bool top = i == 0, bot = i == n + 1, lef = j == 0, rig = j == n + 1;
+                if ((top || bot) && (lef || rig)) {  // corners: the diagonally opposite interior corner
+                    si = top ? n : 1;
+                    sj = lef ? n : 1;
+                } else if (top || bot) {
+                    si = top ? 1 : n;
+                    sj = n + 1 - j;
+                } else if (lef || rig) {
+                    si = n + 1 - i;
+                    sj = lef ? 1 : n;
+                }
+                tsrc.push_back((uint16_t)(si * T + sj));
+            }
+    }
     DA(v->lut_v, 4096);
     DA(v->lut_c, 4096);
     std::vector<uint16_t> lv(4096), lc(4096);
@@ -370,6 +443,7 @@ int adgi_create_volume(const adgi_volume_desc* desc, void* cuda_stream, adgi_vol
         }                                                                                                \
     } while (0)
     CKV(cudaMemcpyAsync(v->sf, sf.data(), sizeof(float4) * sf.size(), cudaMemcpyHostToDevice, s));
+    CKV(cudaMemcpyAsync(v->tex_src, tsrc.data(), sizeof(uint16_t) * tsrc.size(), cudaMemcpyHostToDevice, s));
     CKV(cudaMemcpyAsync(v->lut_v, lv.data(), 2 * 4096, cudaMemcpyHostToDevice, s));
     CKV(cudaMemcpyAsync(v->lut_c, lc.data(), 2 * 4096, cudaMemcpyHostToDevice, s));
     CKV(cudaMemsetAsync(v->irr, 0, irr_bytes, s));
@@ -386,6 +460,11 @@ int adgi_create_volume(const adgi_volume_desc* desc, void* cuda_stream, adgi_vol
     CKV(cudaEventCreate(&v->ev0));
     CKV(cudaEventCreate(&v->ev1));
     for (cudaEvent_t& e : v->ph) CKV(cudaEventCreate(&e));
+    for (cudaEvent_t& e : v->shq) CKV(cudaEventCreate(&e));
+    for (cudaEvent_t& e : v->plq) CKV(cudaEventCreate(&e));
+    CKV(cudaEventCreateWithFlags(&v->fork, cudaEventDisableTiming));
+    CKV(cudaEventCreateWithFlags(&v->join, cudaEventDisableTiming));
+    CKV(cudaStreamCreateWithFlags(&v->side, cudaStreamNonBlocking));
     // the host vectors die at return: wait for the copies
     CKV(cudaStreamSynchronize(s));
 #undef CKV
@@ -648,6 +727,16 @@ int enqueue_update(adgi_volume v, const FrameDev& fd, cudaStream_t s, bool phase
         CK(v->dbvh.build(v->verts, v->idx, v->nv, v->nd, v->eps, v->err, s, v->dlist, false));
     }
     if (!set_node) v->dyn_dirty = false;
+    // the blend plan needs only the frame descriptor: run it on the side
+    // stream, beside the traversals, and join before the blend
+    BlendBufs Bb{v->off,  v->sf,  v->pil_rec, v->m_rec,
+                 v->irr,  v->dep, v->dep_n,   carve_blend_plan(v->plan, V.rays_max - 8), v->tex_src};
+    CK(cudaEventRecord(v->fork, s));
+    CK(cudaStreamWaitEvent(v->side, v->fork, 0));
+    if (phases) CK(cudaEventRecord(v->plq[0], v->side));
+    CK(launch_blend_plan(V, v->fdev, v->sf, Bb.plan, v->side));
+    if (phases) CK(cudaEventRecord(v->plq[1], v->side));
+    CK(cudaEventRecord(v->join, v->side));
     SceneDev S = scene_view(v);
     const FrameDev* FD = v->fdev;
     CK(cudaMemsetAsync(v->shadow_ctr, 0, 8, s));
@@ -658,7 +747,7 @@ int enqueue_update(adgi_volume v, const FrameDev& fd, cudaStream_t s, bool phase
     CK(launch_pilot_trace(V, FD, S, v->pil_hit, T, s));
     PHASE(2);
     CK(launch_shade(V, FD, S, 0, (uint32_t)V.P * kPilots, nullptr, nullptr, v->irr, v->dep, v->pil_hit, v->pil_rec,
-                    v->pil_lum, W, T, s));
+                    v->pil_lum, W, T, s, phases ? v->shq : nullptr));
     // 2. heuristics -> W_p
     PHASE(3);
     ChangeBufs C{v->pil_hit, v->pil_lum, v->lut_v, v->lut_c, v->qv,  v->qr,  v->qv_even, v->qr_even,
@@ -671,10 +760,11 @@ int enqueue_update(adgi_volume v, const FrameDev& fd, cudaStream_t s, bool phase
     PHASE(5);
     CK(launch_main_trace(V, FD, S, v->off, v->sf, v->R_main, v->m_hit, T, s));
     PHASE(6);
-    CK(launch_shade(V, FD, S, 1, v->R_main, v->off, v->sf, v->irr, v->dep, v->m_hit, v->m_rec, nullptr, W, T, s));
+    CK(launch_shade(V, FD, S, 1, v->R_main, v->off, v->sf, v->irr, v->dep, v->m_hit, v->m_rec, nullptr, W, T, s,
+                    phases ? v->shq + 2 : nullptr));
     // 6. blend (after every read of the previous atlases)
     PHASE(7);
-    BlendBufs Bb{v->off, v->sf, v->pil_rec, v->m_rec, v->irr, v->dep, v->dep_n};
+    CK(cudaStreamWaitEvent(s, v->join, 0));
     CK(launch_blend(V, FD, Bb, T, s));
     PHASE(8);
 #undef PHASE
@@ -973,8 +1063,10 @@ int adgi_autotune(adgi_volume v, const adgi_frame* f, int32_t reps, adgi_tuning*
         CK(cudaMemcpyAsync(k, v->irr, bi, cudaMemcpyDeviceToDevice, s));
         CK(cudaMemcpyAsync(k + bi, v->dep, bd, cudaMemcpyDeviceToDevice, s));
         CK(cudaMemcpyAsync(k + bi + bd, v->dep_n, bn, cudaMemcpyDeviceToDevice, s));
-        BlendBufs Bb{v->off, v->sf, v->pil_rec, v->m_rec, v->irr, v->dep, v->dep_n};
-        for (int b : blocks) {
+        BlendBufs Bb{v->off,  v->sf,  v->pil_rec, v->m_rec,
+                 v->irr,  v->dep, v->dep_n,   carve_blend_plan(v->plan, V.rays_max - 8), v->tex_src};
+        const int wblocks[3] = {32, 64, 128};  // 1, 2 or 4 probe tiles (warps) per CTA
+        for (int b : wblocks) {
             if (rc) break;
             Tuning T = best;
             T.blend_block = b;
@@ -1055,6 +1147,8 @@ int adgi_get_stats(adgi_volume v, adgi_stats* out)
         CK(cudaEventElapsedTime(&ms, v->ev0, v->ev1));
         out->ms_last_update = ms;
         for (int i = 0; i < 8; ++i) CK(cudaEventElapsedTime(&out->ms_phase[i], v->ph[i], v->ph[i + 1]));
+        for (int i = 0; i < 2; ++i) CK(cudaEventElapsedTime(&out->ms_shadow[i], v->shq[2 * i], v->shq[2 * i + 1]));
+        CK(cudaEventElapsedTime(&out->ms_blend_plan, v->plq[0], v->plq[1]));
     }
     return ADGI_OK;
 }

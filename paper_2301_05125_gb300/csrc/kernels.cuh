@@ -27,7 +27,7 @@ struct Tuning {
     int trace_block = 128;   // pilot/adaptive nearest-hit kernels
     int shade_block = 128;   // shading prep/finish kernels
     int shadow_mult = 0;     // shadow-ray grid: blocks per SM (0: occupancy)
-    int blend_block = 128;   // blend kernel threads per probe tile
+    int blend_block = 64;    // blend kernel threads per CTA: one warp per probe tile
 };
 
 struct ChangeBufs {
@@ -60,6 +60,17 @@ struct ShadeWork {
     unsigned long long* shadow_ctr;
 };
 
+// Per-frame blend plan, shared by every probe with the same adaptive ray
+// count m: the irradiance and depth texel of every point of every row of the
+// SF table under this frame's rotation.  key_* [M(M+1)/2], row m at
+// m(m-1)/2, entry i = SF index i.
+struct BlendPlan {
+    uint16_t* key_i;
+    uint16_t* key_d;
+};
+size_t blend_plan_elems(int M);  // uint16 elements of the plan
+BlendPlan carve_blend_plan(uint16_t* base, int M);
+
 struct BlendBufs {
     const uint32_t* off;
     const float4* sf;
@@ -68,6 +79,8 @@ struct BlendBufs {
     void* irr;
     void* dep;
     uint8_t* dep_n;
+    BlendPlan plan;
+    const uint16_t* src;  // [Ti^2 + Td^2]: the texel each texel copies (itself, or a border's fold partner)
 };
 
 cudaError_t launch_set_frame(FrameDev* dst, const FrameDev& src, cudaStream_t s);
@@ -78,7 +91,8 @@ cudaError_t launch_main_trace(const VolConst& V, const FrameDev* FD, const Scene
                               const float4* sf, uint32_t R, int2* hit, const Tuning& T, cudaStream_t s);
 cudaError_t launch_shade(const VolConst& V, const FrameDev* FD, const SceneDev& S, int mode, uint32_t n_rays,
                          const uint32_t* off, const float4* sf, const void* irr, const void* dep, const int2* hit,
-                         float4* rec, float* lum, const ShadeWork& W, const Tuning& T, cudaStream_t s);
+                         float4* rec, float* lum, const ShadeWork& W, const Tuning& T, cudaStream_t s,
+                         cudaEvent_t* ev_shadow = nullptr);
 unsigned shadow_grid_blocks(int mult);
 cudaError_t launch_count(const VolConst& V, const FrameDev* FD, const SceneDev& S, const uint32_t* off,
                          const float4* sf, uint32_t R, unsigned long long* out, cudaStream_t s);
@@ -88,6 +102,10 @@ cudaError_t launch_trace_list(const SceneDev& S, const float* o, const float* d,
 cudaError_t launch_change(const VolConst& V, const FrameDev* FD, const ChangeBufs& B, cudaStream_t s);
 cudaError_t launch_allocate(const uint32_t* W, int P, int avg, int m0, int rmax, uint32_t* n_out, uint32_t* off_out,
                             cudaStream_t s);
+// this frame's blend plan (needs only the frame rotation: may run beside the traces)
+cudaError_t launch_blend_plan(const VolConst& V, const FrameDev* FD, const float4* sf, const BlendPlan& plan,
+                              cudaStream_t s);
+// the tiles (after the plan and every read of the previous atlases)
 cudaError_t launch_blend(const VolConst& V, const FrameDev* FD, const BlendBufs& B, const Tuning& T, cudaStream_t s);
 cudaError_t launch_query(const VolConst& V, const void* irr, const void* dep, const float* pos, const float* nrm, int n,
                          float* out, cudaStream_t s);

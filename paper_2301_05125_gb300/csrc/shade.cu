@@ -54,12 +54,16 @@ __device__ __forceinline__ void block_range(const VolConst& V, const RaySet& Rs,
     __syncthreads();
 }
 
-// origin and direction of ray r; false if the ray range is inconsistent
+// The ray a thread handles: thread r takes position r of the set; a pilot ray
+// is stored at slot r, an adaptive ray at base + (SF index of row position
+// r - base), so that a warp works on nearby directions.  Gives the slot,
+// origin and direction; false if the ray range is inconsistent.
 __device__ __forceinline__ bool ray_of(const VolConst& V, const FrameConst& F, const RaySet& Rs, uint32_t r, int lo,
-                                       int hi, float3& o, float3& d)
+                                       int hi, uint32_t& slot, float3& o, float3& d)
 {
     if (Rs.mode == 0) {
         int p = (int)(r >> 3);
+        slot = r;
         o = probe_pos(V, p);
         d = pilot_dir(F.pilot_key, (uint32_t)p, (int)(r & 7));
         return true;
@@ -69,6 +73,9 @@ __device__ __forceinline__ bool ray_of(const VolConst& V, const FrameConst& F, c
     if (m > (uint32_t)(V.rays_max - kPilots) || r - base >= m) return false;
     o = probe_pos(V, p);
     float4 s = __ldg(Rs.sf + (size_t)m * (m - 1) / 2 + (r - base));
+    const uint32_t i = (uint32_t)__float_as_int(s.w);
+    if (i >= m) return false;
+    slot = base + i;
     d = rotate(F.R, s);
     return true;
 }
@@ -106,12 +113,13 @@ __global__ void __launch_bounds__(256) k_shade_prep(VolConst V, const FrameDev* 
     const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
     bool front = false;
     float3 xs = make_float3(0.f, 0.f, 0.f), n = make_float3(0.f, 0.f, 1.f);
-    if (r < Rs.n) {
-        vis[r] = 0ull;
-        int2 hv = hit[r];
+    uint32_t slot = r;
+    float3 o, d;
+    if (r < Rs.n && ray_of(V, F, Rs, r, s_lo, s_hi, slot, o, d)) {
+        vis[slot] = 0ull;
+        int2 hv = hit[slot];
         uint32_t h = (uint32_t)hv.x;
-        float3 o, d;
-        if (h != kMiss && !(h & kBackBit) && ray_of(V, F, Rs, r, s_lo, s_hi, o, d)) {
+        if (h != kMiss && !(h & kBackBit)) {
             float t = __int_as_float(hv.y);
             n = tri_normal(S, (int)h);
             float3 x = make_float3(fa(o.x, fm(t, d.x)), fa(o.y, fm(t, d.y)), fa(o.z, fm(t, d.z)));
@@ -132,10 +140,10 @@ __global__ void __launch_bounds__(256) k_shade_prep(VolConst V, const FrameDev* 
         if (lane == 0) base = atomicAdd(job_count, (unsigned)__popc(mask));
         base = __shfl_sync(0xFFFFFFFFu, base, 0);
         if (want) {
-            unsigned slot = base + __popc(mask & ((1u << lane) - 1u));
-            if (slot < job_cap) {
-                jobs[slot] = make_uint4(__float_as_uint(xs.x), __float_as_uint(xs.y), __float_as_uint(xs.z), r);
-                job_light[slot] = (uint8_t)l;
+            unsigned js = base + __popc(mask & ((1u << lane) - 1u));
+            if (js < job_cap) {
+                jobs[js] = make_uint4(__float_as_uint(xs.x), __float_as_uint(xs.y), __float_as_uint(xs.z), slot);
+                job_light[js] = (uint8_t)l;
             } else {
                 atomicOr(V.err, kErrRayRange);
             }
@@ -186,7 +194,10 @@ __global__ void __launch_bounds__(256) k_shade_finish(VolConst V, const FrameDev
     block_range(V, Rs, &s_lo, &s_hi);
     const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= Rs.n) return;
-    int2 hv = hit[r];
+    uint32_t slot;
+    float3 o, d;
+    if (!ray_of(V, F, Rs, r, s_lo, s_hi, slot, o, d)) return;  // flagged by the trace kernel
+    int2 hv = hit[slot];
     uint32_t h = (uint32_t)hv.x;
     float4 out;
     float lo = 0.0f;
@@ -196,14 +207,13 @@ __global__ void __launch_bounds__(256) k_shade_finish(VolConst V, const FrameDev
     } else {
         float t = __int_as_float(hv.y);
         float depth = fminf(t, V.depth_max);
-        float3 o, d;
-        if ((h & kBackBit) || !ray_of(V, F, Rs, r, s_lo, s_hi, o, d)) {
+        if (h & kBackBit) {
             out = make_float4(0.f, 0.f, 0.f, depth);
         } else {
             int tri = (int)h;
             float3 n = tri_normal(S, tri);
             float3 x = make_float3(fa(o.x, fm(t, d.x)), fa(o.y, fm(t, d.y)), fa(o.z, fm(t, d.z)));
-            unsigned long long vm = vis[r];
+            unsigned long long vm = vis[slot];
             float E0 = 0.f, E1 = 0.f, E2 = 0.f;
             for (int l = 0; l < L.n; ++l) {
                 if (!((vm >> l) & 1ull)) continue;
@@ -236,8 +246,8 @@ __global__ void __launch_bounds__(256) k_shade_finish(VolConst V, const FrameDev
             out = make_float4(r0, r1, r2, depth);
         }
     }
-    rec[r] = out;
-    if (lum) lum[r] = lo;
+    rec[slot] = out;
+    if (lum) lum[slot] = lo;
 }
 
 }  // namespace
@@ -256,7 +266,8 @@ unsigned shadow_grid_blocks(int mult)
 
 cudaError_t launch_shade(const VolConst& V, const FrameDev* FD, const SceneDev& S, int mode, uint32_t n_rays,
                          const uint32_t* off, const float4* sf, const void* irr, const void* dep, const int2* hit,
-                         float4* rec, float* lum, const ShadeWork& W, const Tuning& T, cudaStream_t s)
+                         float4* rec, float* lum, const ShadeWork& W, const Tuning& T, cudaStream_t s,
+                         cudaEvent_t* ev_shadow)
 {
     if (n_rays == 0) return cudaSuccess;
     RaySet Rs{mode, n_rays, off, sf};
@@ -266,9 +277,11 @@ cudaError_t launch_shade(const VolConst& V, const FrameDev* FD, const SceneDev& 
     if (e != cudaSuccess) return e;
     k_shade_prep<<<nb, b, 0, s>>>(V, FD, S, Rs, hit, W.vis, W.jobs, W.job_light, W.job_count, W.job_cap);
     count_launches(1);
+    if (ev_shadow && (e = cudaEventRecord(ev_shadow[0], s)) != cudaSuccess) return e;
     k_shadow<<<W.shadow_blocks, 128, 0, s>>>(FD, S, W.jobs, W.job_light, W.job_count, W.job_cap, W.vis,
                                              W.shadow_ctr);
     count_launches(1);
+    if (ev_shadow && (e = cudaEventRecord(ev_shadow[1], s)) != cudaSuccess) return e;
     k_shade_finish<<<nb, b, 0, s>>>(V, FD, S, Rs, hit, W.vis, irr, dep, rec, lum);
     count_launches(1);
     return cudaGetLastError();

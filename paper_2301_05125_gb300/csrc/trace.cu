@@ -33,9 +33,12 @@ __device__ __forceinline__ void block_probe_range(const uint32_t* __restrict__ o
     __syncthreads();
 }
 
-__device__ __forceinline__ float3 main_dir(const FrameConst& F, const float4* __restrict__ sf, uint32_t m, uint32_t i)
+// direction at position k of the SF row of m points, and its SF index *i
+__device__ __forceinline__ float3 main_dir(const FrameConst& F, const float4* __restrict__ sf, uint32_t m, uint32_t k,
+                                           uint32_t* i)
 {
-    float4 s = __ldg(sf + (size_t)m * (m - 1) / 2 + i);
+    float4 s = __ldg(sf + (size_t)m * (m - 1) / 2 + k);
+    *i = (uint32_t)__float_as_int(s.w);
     return rotate(F.R, s);
 }
 
@@ -61,6 +64,9 @@ __global__ void __launch_bounds__(256) k_pilot_trace(VolConst V, const FrameDev*
     hit[i] = make_int2((int)h, __float_as_int(t));
 }
 
+// Thread r takes row position r - off[p] of probe p, whose SF index i names
+// the slot off[p] + i of the result: the threads of a warp trace nearby
+// directions (the rows are in a spatial order).
 __global__ void __launch_bounds__(256) k_main_trace(VolConst V, const FrameDev* __restrict__ FD, SceneDev S,
                                                     const uint32_t* __restrict__ off, const float4* __restrict__ sf,
                                                     uint32_t R, int2* __restrict__ hit)
@@ -77,15 +83,19 @@ __global__ void __launch_bounds__(256) k_main_trace(VolConst V, const FrameDev* 
     uint32_t m = __ldg(off + p + 1) - base;
     if (m > (uint32_t)(V.rays_max - kPilots) || r - base >= m) {
         atomicOr(V.err, kErrRayRange);
-        hit[r] = make_int2((int)kMiss, 0);
         return;
     }
     float3 org = probe_pos(V, p);
-    float3 d = main_dir(F, sf, m, r - base);
+    uint32_t i;
+    float3 d = main_dir(F, sf, m, r - base, &i);
+    if (i >= m) {
+        atomicOr(V.err, kErrRayRange);
+        return;
+    }
     float t;
     uint32_t h;
     trace_closest(S, org, d, V.tmin, __int_as_float(0x7F800000), t, h);
-    hit[r] = make_int2((int)h, __float_as_int(t));
+    hit[base + i] = make_int2((int)h, __float_as_int(t));
 }
 
 // Re-trace the last update's rays with work counters (roofline accounting).
@@ -117,7 +127,8 @@ __global__ void __launch_bounds__(128) k_count(VolConst V, const FrameDev* __res
             uint32_t base = __ldg(off + p), m = __ldg(off + p + 1) - base;
             ok = m <= (uint32_t)(V.rays_max - kPilots) && q - base < m;
             org = probe_pos(V, p);
-            if (ok) d = main_dir(F, sf, m, q - base);
+            uint32_t i;
+            if (ok) d = main_dir(F, sf, m, q - base, &i);
         }
         if (ok) {
             float t;

@@ -1,4 +1,6 @@
 // update.cu -- heuristics, ray allocation, blend and query kernels (sm_103a).
+#include <algorithm>
+
 #include "adgi_internal.cuh"
 #include "kernels.cuh"
 
@@ -256,17 +258,21 @@ __global__ void __launch_bounds__(kAllocThreads) k_allocate(const uint32_t* __re
 }
 
 // ============================================================== blend
-// One CTA per probe tile (Alg. ApproxAlgo + Alg. MovingAvgUpdate, batched).
-//  1. one thread stages the probe's ray records and its old atlas tiles into
-//     shared memory with bulk asynchronous copies (cp.async.bulk, completion
-//     counted on an mbarrier) while the CTA bins every sample direction to its
-//     nearest irradiance and depth texel;
-//  2. a stable counting sort in shared memory groups the samples of each
-//     texel in sample order, so each texel's sum is taken by one thread in a
-//     fixed order: the blend is deterministic (no floating-point atomics);
-//  3. touched texels are blended with w = max(1 - h, k/(n+k)), the octahedral
-//     border is refreshed from the updated interior, and the tiles are
-//     written back with coalesced 16-byte stores.
+// Alg. ApproxAlgo + Alg. MovingAvgUpdate, batched per texel, in two kernels.
+//  plan  (once per frame): the irradiance and depth texel of every point of
+//        every row of the SF table under this frame's rotation -- every probe
+//        with m adaptive rays shares row m, so binning is done once per
+//        direction, not once per ray;
+//  blend (one warp per probe tile): the probe's ray records stream through
+//        shared memory 32 at a time (cp.async, double buffered) and the old
+//        tiles are staged beside them; within each group of 32 samples, the
+//        lanes that fall in the same texel are found with match_any and the
+//        group's lowest lane adds them in lane order, so every texel sums its
+//        samples in sample order (pilots, then SF index order): the result is
+//        deterministic, with no floating-point atomics.  Touched texels are
+//        blended with w = max(1 - h, k/(n+k)), and every texel -- border
+//        texels from their octahedral fold partner -- is written back with
+//        coalesced stores in texel order.
 
 // float -> half with stochastic rounding: round toward zero, then step one
 // half ulp away from zero with probability equal to the remaining fraction
@@ -289,355 +295,290 @@ __device__ __forceinline__ uint32_t sr_bits(uint64_t key, int p, int t, int c)
     return (uint32_t)splitmix(key ^ ((uint64_t)p << 24) ^ ((uint64_t)t << 4) ^ (uint64_t)c);
 }
 
-__device__ __forceinline__ void border_src(int i, int j, int n, int& si, int& sj)
+
+
+
+// 16-byte asynchronous copy global -> shared (both 16-byte aligned)
+__device__ __forceinline__ void cp_async16(void* dst, const void* src)
 {
-    if (i == 0 && j == 0) {
-        si = n;
-        sj = n;
-    } else if (i == 0 && j == n + 1) {
-        si = n;
-        sj = 1;
-    } else if (i == n + 1 && j == 0) {
-        si = 1;
-        sj = n;
-    } else if (i == n + 1 && j == n + 1) {
-        si = 1;
-        sj = 1;
-    } else if (i == 0) {
-        si = 1;
-        sj = n + 1 - j;
-    } else if (i == n + 1) {
-        si = n;
-        sj = n + 1 - j;
-    } else if (j == 0) {
-        si = n + 1 - i;
-        sj = 1;
-    } else {
-        si = n + 1 - i;
-        sj = n;
-    }
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
+// Plan of this frame: thread e handles entry e of the flat table (row m,
+// SF index i).
+__global__ void __launch_bounds__(256) k_blend_plan(VolConst V, const FrameDev* __restrict__ FD,
+                                                    const float4* __restrict__ sf, BlendPlan Pl, uint32_t n_entries)
+{
+    const FrameConst& F = FD->F;
+    const uint32_t e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n_entries) return;
+    // row m holds SF indices in a spatial order; position e - row start is
+    // SF index .w of that point
+    const uint32_t m = (uint32_t)((sqrtf(8.0f * (float)e + 1.0f) + 1.0f) * 0.5f);  // first guess of the row
+    uint32_t mm = m;
+    while (mm > 1 && (size_t)mm * (mm - 1) / 2 > e) --mm;  // m(m-1)/2 <= e < m(m+1)/2
+    while ((size_t)(mm + 1) * mm / 2 <= e) ++mm;
+    const size_t row = (size_t)mm * (mm - 1) / 2;
+    const float4 s4 = __ldg(sf + e);
+    const uint32_t i = (uint32_t)__float_as_int(s4.w);
+    if (i >= mm) {
+        atomicOr(V.err, kErrIndex);
+        return;
+    }
+    const float2 oe = oct_encode_x(rotate(F.R, s4));
+    Pl.key_i[row + i] = (uint16_t)texel_of(oe, V.n_irr);
+    Pl.key_d[row + i] = (uint16_t)texel_of(oe, V.n_dep);
+}
 
-constexpr int kErrWait = 16;  // a bulk copy did not complete within the wait limit
-
-// shared-memory layout of k_blend for samples <= smax (byte offsets, 16-aligned)
+// shared memory of one probe (one warp) of k_blend: two 32-record buffers,
+// the pilot records and bins, the old tiles as stored, per-texel running
+// sums and counts, and the updated depth counts
 struct BlendLayout {
-    uint32_t rec, irr_raw, dep_raw, dn_raw, irr_new, dep_new, dn_new, key_i, key_d, ord_i, ord_d, beg_i, beg_d, cur_i,
-        cur_d, total;
+    uint32_t rb, prec, pkey, irr_raw, dep_raw, dn_raw, acc_i, acc_d, cnt_d, dn_new, total;
 };
 
 __host__ __device__ inline uint32_t al16(uint32_t x) { return (x + 15u) & ~15u; }
 
-__host__ __device__ inline BlendLayout blend_layout(int smax, int Ti, int Td)
+__host__ __device__ inline BlendLayout blend_layout(int Ti, int Td)
 {
-    const uint32_t ti2 = (uint32_t)(Ti * Ti), td2 = (uint32_t)(Td * Td), S = (uint32_t)smax;
+    const uint32_t ti2 = (uint32_t)(Ti * Ti), td2 = (uint32_t)(Td * Td);
     BlendLayout L;
-    uint32_t o = 16;  // mbarrier
-    L.rec = o, o += al16(16 * S);
+    uint32_t o = 0;
+    L.rb = o, o += 2 * 32 * 16;
+    L.prec = o, o += 16 * kPilots;
+    L.pkey = o, o += 4 * 2 * kPilots;
     L.irr_raw = o, o += al16(16 * ti2);
     L.dep_raw = o, o += al16(8 * td2);
     L.dn_raw = o, o += al16(td2);
-    L.irr_new = o, o += al16(16 * ti2);
-    L.dep_new = o, o += al16(8 * td2);
+    L.acc_i = o, o += al16(16 * ti2);
+    L.acc_d = o, o += al16(8 * td2);
+    L.cnt_d = o, o += al16(2 * td2);
     L.dn_new = o, o += al16(td2);
-    L.key_i = o, o += al16(2 * S);
-    L.key_d = o, o += al16(2 * S);
-    L.ord_i = o, o += al16(2 * S);
-    L.ord_d = o, o += al16(2 * S);
-    L.beg_i = o, o += al16(4 * (ti2 + 1));
-    L.beg_d = o, o += al16(4 * (td2 + 1));
-    L.cur_i = o, o += al16(4 * ti2);
-    L.cur_d = o, o += al16(4 * td2);
     L.total = o;
     return L;
 }
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint32_t bar)
-{
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     smem_u32(dst)),
-                 "l"(src), "r"(bytes), "r"(bar)
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
-{
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred P;\n mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n selp.u32 %0, 1, 0, P;\n}"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// exclusive scan of cnt[0..n) into beg[0..n] (beg[n] = total) and cur, by one warp
-__device__ __forceinline__ void warp_scan_bins(const uint32_t* cnt, uint32_t* beg, uint32_t* cur, int n, int lane)
-{
-    uint32_t carry = 0;
-    for (int b0 = 0; b0 < n; b0 += 32) {
-        const int b = b0 + lane;
-        uint32_t c = b < n ? cnt[b] : 0u, x = c;
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
-            if (lane >= d) x += y;
-        }
-        if (b < n) {
-            beg[b] = carry + x - c;
-            cur[b] = carry + x - c;
-        }
-        carry += __shfl_sync(0xffffffffu, x, 31);
-    }
-    if (lane == 0) beg[n] = carry;
-}
-
-// stable scatter of sample indices by key (sample order kept inside a key), by one warp
-__device__ __forceinline__ void warp_stable_scatter(const uint16_t* key, uint32_t* cur, uint16_t* ord, int total,
-                                                    int lane)
-{
-    const uint32_t lt = (1u << lane) - 1u;
-    for (int c0 = 0; c0 < total; c0 += 32) {
-        const int j = c0 + lane;
-        const bool valid = j < total;
-        const uint32_t k = valid ? (uint32_t)key[j] : 0x10000u + (uint32_t)lane;  // invalid lanes match nobody
-        const uint32_t mask = __match_any_sync(0xffffffffu, k);
-        uint32_t pos = 0;
-        if (valid) pos = cur[k] + (uint32_t)__popc(mask & lt);
-        __syncwarp();
-        if (valid) {
-            ord[pos] = (uint16_t)j;
-            if ((mask & lt) == 0u) cur[k] += (uint32_t)__popc(mask);  // lowest lane of the group advances the cursor
-        }
-        __syncwarp();
-    }
-}
+// row of texel t in a tile of width T (t < 1024, T <= 32: the product is
+// never within 2^-7 of an integer, so single-precision rounding is harmless)
+__device__ __forceinline__ int tile_row(int t, float rT) { return (int)(((float)t + 0.5f) * rT); }
 
 __global__ void __launch_bounds__(256) k_blend(VolConst V, const FrameDev* __restrict__ FD, BlendBufs B)
 {
     const FrameConst& F = FD->F;
     extern __shared__ __align__(16) unsigned char smem[];
-    const int nthr = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int p = blockIdx.x;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const uint32_t lt = (1u << lane) - 1u;
+    const int p = blockIdx.x * (blockDim.x >> 5) + wib;
+    if (p >= V.P) return;  // the whole warp
     const uint32_t base = __ldg(B.off + p);
     uint32_t m = __ldg(B.off + p + 1) - base;
     if (m > (uint32_t)(V.rays_max - kPilots) || base > V.R_main || m > V.R_main - base) {
-        if (tid == 0) atomicOr(V.err, kErrRayRange);
+        if (lane == 0) atomicOr(V.err, kErrRayRange);
         m = 0;
     }
     const int npil = F.even ? kPilots : 0;
-    const int total = (int)m + npil;
-    if (total == 0) return;  // untouched tile: nothing to read or write
+    if ((int)m + npil == 0) return;  // untouched tile: nothing to read or write
     const int Ti = V.Ti, Td = V.Td, ni = V.n_irr, nd = V.n_dep;
     const int ti2 = Ti * Ti, td2 = Td * Td;
-    const BlendLayout L = blend_layout(V.rays_max, Ti, Td);
-    float4* rec = reinterpret_cast<float4*>(smem + L.rec);
-    unsigned char* irr_raw = smem + L.irr_raw;
-    unsigned char* dep_raw = smem + L.dep_raw;
-    uint8_t* dn_raw = smem + L.dn_raw;
-    float4* irr_new = reinterpret_cast<float4*>(smem + L.irr_new);
-    float2* dep_new = reinterpret_cast<float2*>(smem + L.dep_new);
-    uint8_t* dn_new = smem + L.dn_new;
-    uint16_t* key_i = reinterpret_cast<uint16_t*>(smem + L.key_i);
-    uint16_t* key_d = reinterpret_cast<uint16_t*>(smem + L.key_d);
-    uint16_t* ord_i = reinterpret_cast<uint16_t*>(smem + L.ord_i);
-    uint16_t* ord_d = reinterpret_cast<uint16_t*>(smem + L.ord_d);
-    uint32_t* beg_i = reinterpret_cast<uint32_t*>(smem + L.beg_i);
-    uint32_t* beg_d = reinterpret_cast<uint32_t*>(smem + L.beg_d);
-    uint32_t* cur_i = reinterpret_cast<uint32_t*>(smem + L.cur_i);
-    uint32_t* cur_d = reinterpret_cast<uint32_t*>(smem + L.cur_d);
-    const uint32_t bar = smem_u32(smem);
-
-    // 1. stage records (always 16-byte multiples) and, when their sizes allow
-    //    16-byte bulk copies, the old tiles
+    const BlendLayout L = blend_layout(Ti, Td);
+    unsigned char* ws = smem + (size_t)wib * L.total;
+    float4* rb = reinterpret_cast<float4*>(ws + L.rb);  // [2][32]
+    float4* prs = reinterpret_cast<float4*>(ws + L.prec);
+    int* pk_i = reinterpret_cast<int*>(ws + L.pkey);
+    int* pk_d = pk_i + kPilots;
+    unsigned char* irr_raw = ws + L.irr_raw;
+    unsigned char* dep_raw = ws + L.dep_raw;
+    uint8_t* dn_raw = ws + L.dn_raw;
+    float4* acc_i = reinterpret_cast<float4*>(ws + L.acc_i);
+    float2* acc_d = reinterpret_cast<float2*>(ws + L.acc_d);
+    uint16_t* cnt_d = reinterpret_cast<uint16_t*>(ws + L.cnt_d);
+    uint8_t* dn_new = ws + L.dn_new;
+    const size_t io = (size_t)p * ti2, dof = (size_t)p * td2;
+    const float4* mrec = B.main_rec + base;
+    // old tiles: asynchronous copies when the tile sizes are 16-byte multiples
     const uint32_t irr_b = (uint32_t)ti2 * (V.fp16 ? 8u : 16u), dep_b = (uint32_t)td2 * (V.fp16 ? 4u : 8u);
     const uint32_t dn_b = (uint32_t)td2;
-    const bool tiles_bulk = (irr_b % 16u) == 0u && (dep_b % 16u) == 0u && (dn_b % 16u) == 0u;
+    const bool tiles_async = (irr_b % 16u) == 0u && (dep_b % 16u) == 0u && (dn_b % 16u) == 0u;
     const unsigned char* g_irr = reinterpret_cast<const unsigned char*>(B.irr) + (size_t)p * irr_b;
     const unsigned char* g_dep = reinterpret_cast<const unsigned char*>(B.dep) + (size_t)p * dep_b;
-    const uint8_t* g_dn = B.dep_n + (size_t)p * dn_b;
-    if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    const uint8_t* g_dn = B.dep_n + dof;
+    if (tiles_async) {
+        for (uint32_t c = lane; c < irr_b / 16u; c += 32) cp_async16(irr_raw + 16 * c, g_irr + 16 * c);
+        for (uint32_t c = lane; c < dep_b / 16u; c += 32) cp_async16(dep_raw + 16 * c, g_dep + 16 * c);
+        for (uint32_t c = lane; c < dn_b / 16u; c += 32) cp_async16(dn_raw + 16 * c, g_dn + 16 * c);
+    } else {
+        for (uint32_t c = lane; c < irr_b / 4u; c += 32)
+            reinterpret_cast<uint32_t*>(irr_raw)[c] = reinterpret_cast<const uint32_t*>(g_irr)[c];
+        for (uint32_t c = lane; c < dep_b / 4u; c += 32)
+            reinterpret_cast<uint32_t*>(dep_raw)[c] = reinterpret_cast<const uint32_t*>(g_dep)[c];
+        for (uint32_t c = lane; c < dn_b; c += 32) dn_raw[c] = g_dn[c];
     }
-    for (int t = tid; t < ti2; t += nthr) cur_i[t] = 0u;
-    for (int t = tid; t < td2; t += nthr) cur_d[t] = 0u;
-    __syncthreads();
-    if (tid == 0) {
-        const uint32_t tx = 16u * (uint32_t)total + (tiles_bulk ? irr_b + dep_b + dn_b : 0u);
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(tx) : "memory");
-        if (npil) bulk_g2s(rec, B.pil_rec + (size_t)p * kPilots, 16u * kPilots, bar);
-        if (m) bulk_g2s(rec + npil, B.main_rec + base, 16u * m, bar);
-        if (tiles_bulk) {
-            bulk_g2s(irr_raw, g_irr, irr_b, bar);
-            bulk_g2s(dep_raw, g_dep, dep_b, bar);
-            bulk_g2s(dn_raw, g_dn, dn_b, bar);
+    cp_async_commit();  // group: tiles
+    // records of rounds 0 and 1 (32 samples each)
+    const uint32_t rounds = (m + 31u) / 32u;
+    if (lane < m) cp_async16(rb + lane, mrec + lane);
+    cp_async_commit();  // group: round 0
+    if (32u + lane < m) cp_async16(rb + 32 + lane, mrec + 32 + lane);
+    cp_async_commit();  // group: round 1
+    // pilot samples (first in every texel's sum, in pilot order): records and
+    // bins, added by one lane
+    if (npil && lane < kPilots) {
+        prs[lane] = __ldg(B.pil_rec + (size_t)p * kPilots + lane);
+        const float2 e = oct_encode_x(pilot_dir(F.pilot_key, (uint32_t)p, lane));
+        pk_i[lane] = texel_of(e, ni);
+        pk_d[lane] = texel_of(e, nd);
+    }
+    for (int t = lane; t < ti2; t += 32) acc_i[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int t = lane; t < td2; t += 32) {
+        acc_d[t] = make_float2(0.f, 0.f);
+        cnt_d[t] = 0;
+    }
+    __syncwarp();
+    if (lane == 0)
+        for (int o = 0; o < npil; ++o) {
+            const float4 r = prs[o];
+            float4& ai = acc_i[pk_i[o]];
+            ai.x += r.x;
+            ai.y += r.y;
+            ai.z += r.z;
+            ai.w += 1.0f;
+            float2& ad = acc_d[pk_d[o]];
+            ad.x += r.w;
+            ad.y += r.w * r.w;
+            cnt_d[pk_d[o]] += 1;
         }
+    // adaptive samples, 32 per round in SF index order
+    const size_t row = m ? (size_t)m * (m - 1) / 2 : 0;
+    uint32_t ki = 0, kd = 0;
+    if (lane < m) {
+        ki = __ldg(B.plan.key_i + row + lane);
+        kd = __ldg(B.plan.key_d + row + lane);
     }
-    if (!tiles_bulk) {  // odd tile sizes: plain loads (4-byte words; the counts bytewise)
-        for (uint32_t t = tid; t < irr_b / 4u; t += nthr)
-            reinterpret_cast<uint32_t*>(irr_raw)[t] = reinterpret_cast<const uint32_t*>(g_irr)[t];
-        for (uint32_t t = tid; t < dep_b / 4u; t += nthr)
-            reinterpret_cast<uint32_t*>(dep_raw)[t] = reinterpret_cast<const uint32_t*>(g_dep)[t];
-        for (uint32_t t = tid; t < dn_b; t += nthr) dn_raw[t] = g_dn[t];
-    }
-    // sample directions -> nearest texels (the copies are in flight meanwhile)
-    const float4* sfm = B.sf + (size_t)m * (m - 1) / 2;
-    for (int j = tid; j < total; j += nthr) {
-        float3 d = j < npil ? pilot_dir(F.pilot_key, (uint32_t)p, j) : rotate(F.R, __ldg(sfm + (j - npil)));
-        float2 e = oct_encode_x(d);
-        const int ki = texel_of(e, ni), kd = texel_of(e, nd);
-        key_i[j] = (uint16_t)ki;
-        key_d[j] = (uint16_t)kd;
-        atomicAdd(cur_i + ki, 1u);  // integer counts: order-independent
-        atomicAdd(cur_d + kd, 1u);
-    }
-    __syncthreads();
-    // 2. per-texel buckets in sample order
-    const int wd = nthr > 32 ? 1 : 0;  // the warp that sorts the depth keys
-    if (warp == 0) warp_scan_bins(cur_i, beg_i, cur_i, ti2, lane);
-    if (warp == wd) warp_scan_bins(cur_d, beg_d, cur_d, td2, lane);
-    __syncthreads();
-    if (warp == 0) warp_stable_scatter(key_i, cur_i, ord_i, total, lane);
-    if (warp == wd) warp_stable_scatter(key_d, cur_d, ord_d, total, lane);
-    // the staged data must have landed (bounded wait; on time-out the CTA
-    // flags the volume and leaves the tiles as they were)
-    bool ok = false;
-    for (int it = 0; it < (1 << 22) && !ok; ++it) ok = mbar_try_wait(bar, 0u);
-    if (__syncthreads_or(!ok)) {
-        if (tid == 0) atomicOr(V.err, kErrWait);
-        for (int it = 0; it < (1 << 22) && !ok; ++it) ok = mbar_try_wait(bar, 0u);
-        return;
-    }
-    // 3. blend the touched interior texels
-    const float omh = 1.0f - V.hyst;
-    for (int t = tid; t < ti2; t += nthr) {
-        const int i = t / Ti, jj = t - i * Ti;
-        if (i < 1 || i > ni || jj < 1 || jj > ni) continue;
-        float4 v;
-        if (V.fp16) {
-            const __half2* h = reinterpret_cast<const __half2*>(irr_raw) + 2 * t;
-            float2 a = __half22float2(h[0]), b2 = __half22float2(h[1]);
-            v = make_float4(a.x, a.y, b2.x, b2.y);
-        } else {
-            v = reinterpret_cast<const float4*>(irr_raw)[t];
+    for (uint32_t r = 0; r < rounds; ++r) {
+        const uint32_t j = 32u * r + lane;
+        const bool valid = j < m;
+        uint32_t ki_n = 0, kd_n = 0;  // next round's bins, loaded early
+        if (j + 32u < m) {
+            ki_n = __ldg(B.plan.key_i + row + j + 32u);
+            kd_n = __ldg(B.plan.key_d + row + j + 32u);
         }
-        const uint32_t b0 = beg_i[t], b1 = beg_i[t + 1];
-        if (b1 > b0) {
-            float sx = 0.f, sy = 0.f, sz = 0.f;
-            for (uint32_t q = b0; q < b1; ++q) {
-                const float4 r = rec[ord_i[q]];
-                sx += r.x;
-                sy += r.y;
-                sz += r.z;
+        cp_async_wait<1>();  // this round's records have landed (the next round's may be in flight)
+        __syncwarp();
+        const float4* cur = rb + 32 * (r & 1u);
+        const uint32_t gi = __match_any_sync(0xffffffffu, valid ? ki : 0x10000u + lane);
+        if (valid && (gi & lt) == 0u) {  // lowest lane of its group: add the group in lane order
+            float4& a = acc_i[ki];
+            for (uint32_t g = gi; g; g &= g - 1u) {
+                const float4 x = cur[__ffs(g) - 1];
+                a.x += x.x;
+                a.y += x.y;
+                a.z += x.z;
             }
-            const float k = (float)(b1 - b0);
-            const float w = fmaxf(omh, k / (v.w + k));
-            const float ik = 1.0f / k;
-            v.x += w * (sx * ik - v.x);
-            v.y += w * (sy * ik - v.y);
-            v.z += w * (sz * ik - v.z);
-            v.w = fminf(v.w + k, 255.0f);
+            a.w += (float)__popc(gi);
         }
-        irr_new[t] = v;
+        const uint32_t gd = __match_any_sync(0xffffffffu, valid ? kd : 0x10000u + lane);
+        if (valid && (gd & lt) == 0u) {
+            float2& a = acc_d[kd];
+            for (uint32_t g = gd; g; g &= g - 1u) {
+                const float x = cur[__ffs(g) - 1].w;
+                a.x += x;
+                a.y += x * x;
+            }
+            cnt_d[kd] += (uint16_t)__popc(gd);
+        }
+        __syncwarp();
+        // refill the buffer just consumed with round r + 2
+        const uint32_t j2 = j + 64u;
+        if (j2 < m) cp_async16(rb + 32 * (r & 1u) + lane, mrec + j2);
+        cp_async_commit();
+        ki = ki_n;
+        kd = kd_n;
     }
-    for (int t = tid; t < td2; t += nthr) {
-        const int i = t / Td, jj = t - i * Td;
-        if (i < 1 || i > nd || jj < 1 || jj > nd) continue;
-        float2 v = V.fp16 ? __half22float2(reinterpret_cast<const __half2*>(dep_raw)[t])
-                          : reinterpret_cast<const float2*>(dep_raw)[t];
+    cp_async_wait<0>();
+    __syncwarp();
+    // blend the interior texels in place (untouched ones keep their value)
+    const float omh = 1.0f - V.hyst;
+    const float rni = 1.0f / (float)ni, rnd = 1.0f / (float)nd;
+    for (int q = lane; q < ni * ni; q += 32) {
+        const int r = tile_row(q, rni), t = (r + 1) * Ti + (q - r * ni) + 1;
+        const float4 a = acc_i[t];
+        float4 v = irr_load(irr_raw, (size_t)t, V.fp16);
+        if (a.w > 0.0f) {
+            const float kf = a.w;
+            const float w = fmaxf(omh, __fdividef(kf, v.w + kf));
+            const float ik = __frcp_rn(kf);
+            v.x += w * (a.x * ik - v.x);
+            v.y += w * (a.y * ik - v.y);
+            v.z += w * (a.z * ik - v.z);
+            v.w = fminf(v.w + kf, 255.0f);
+        }
+        acc_i[t] = v;
+    }
+    for (int q = lane; q < nd * nd; q += 32) {
+        const int r = tile_row(q, rnd), t = (r + 1) * Td + (q - r * nd) + 1;
+        const float2 a = acc_d[t];
+        float2 v = dep_load(dep_raw, (size_t)t, V.fp16);
         uint32_t c = dn_raw[t];
-        const uint32_t b0 = beg_d[t], b1 = beg_d[t + 1];
-        if (b1 > b0) {
+        const uint32_t k = cnt_d[t];
+        if (k) {
             // the texel stores {mean, variance}; with batch mean m and batch
             // variance vb the moving average of {d, d^2} becomes
             //   mean' = mean + w (m - mean)
             //   var'  = (1-w) var + w vb + w (1-w) (m - mean)^2
             // (every term non-negative: no cancellation in storage)
-            float s1 = 0.f, s2 = 0.f;
-            for (uint32_t q = b0; q < b1; ++q) {
-                const float d = rec[ord_d[q]].w;
-                s1 += d;
-                s2 += d * d;
-            }
-            const float k = (float)(b1 - b0);
-            const float w = fmaxf(omh, k / ((float)c + k));
-            const float ik = 1.0f / k;
-            const float mb = s1 * ik;
-            const float vb = fmaxf(s2 * ik - mb * mb, 0.0f);
+            const float kf = (float)k;
+            const float w = fmaxf(omh, __fdividef(kf, (float)c + kf));
+            const float ik = __frcp_rn(kf);
+            const float mb = a.x * ik;
+            const float vb = fmaxf(a.y * ik - mb * mb, 0.0f);
             const float dm = mb - v.x;
             v.y = (1.0f - w) * v.y + w * vb + w * (1.0f - w) * dm * dm;
             v.x += w * dm;
-            c = (uint32_t)fminf((float)c + k, 255.0f);
+            c = (uint32_t)fminf((float)c + kf, 255.0f);
         }
-        dep_new[t] = v;
+        acc_d[t] = v;
         dn_new[t] = (uint8_t)c;
     }
-    __syncthreads();
-    // 4. every texel (border ones from their octahedral fold partner) in the
-    //    storage format, into the staging buffers
+    __syncwarp();
+    // every texel (a border texel from its octahedral fold partner) in the
+    // storage format, stored in texel order (coalesced)
     const uint64_t srkey = F.pilot_key ^ (F.even ? 0x5352ull : 0x5353ull);
-    for (int t = tid; t < ti2; t += nthr) {
-        const int i = t / Ti, jj = t - i * Ti;
-        int src = t;
-        if (i < 1 || i > ni || jj < 1 || jj > ni) {
-            int si, sj;
-            border_src(i, jj, ni, si, sj);
-            src = si * Ti + sj;
-        }
-        const float4 v = irr_new[src];
+    for (int t = lane; t < ti2; t += 32) {
+        const float4 v = acc_i[__ldg(B.src + t)];
         if (V.fp16 == 2) {
-            __half2* h = reinterpret_cast<__half2*>(irr_raw) + 2 * t;
-            h[0] = __halves2half2(half_sr(v.x, sr_bits(srkey, p, t, 0)), half_sr(v.y, sr_bits(srkey, p, t, 1)));
-            h[1] = __halves2half2(half_sr(v.z, sr_bits(srkey, p, t, 2)), __float2half_rn(v.w));
+            __half2* h = reinterpret_cast<__half2*>(B.irr) + 2 * (io + t);
+            const __half2 h0 = __halves2half2(half_sr(v.x, sr_bits(srkey, p, t, 0)), half_sr(v.y, sr_bits(srkey, p, t, 1)));
+            const __half2 h1 = __halves2half2(half_sr(v.z, sr_bits(srkey, p, t, 2)), __float2half_rn(v.w));
+            *reinterpret_cast<uint2*>(h) = make_uint2(*reinterpret_cast<const uint32_t*>(&h0),
+                                                     *reinterpret_cast<const uint32_t*>(&h1));
         } else if (V.fp16) {
-            __half2* h = reinterpret_cast<__half2*>(irr_raw) + 2 * t;
-            h[0] = __floats2half2_rn(v.x, v.y);
-            h[1] = __floats2half2_rn(v.z, v.w);
+            __half2* h = reinterpret_cast<__half2*>(B.irr) + 2 * (io + t);
+            const __half2 h0 = __floats2half2_rn(v.x, v.y), h1 = __floats2half2_rn(v.z, v.w);
+            *reinterpret_cast<uint2*>(h) = make_uint2(*reinterpret_cast<const uint32_t*>(&h0),
+                                                     *reinterpret_cast<const uint32_t*>(&h1));
         } else {
-            reinterpret_cast<float4*>(irr_raw)[t] = v;
+            reinterpret_cast<float4*>(B.irr)[io + t] = v;
         }
     }
-    for (int t = tid; t < td2; t += nthr) {
-        const int i = t / Td, jj = t - i * Td;
-        int src = t;
-        if (i < 1 || i > nd || jj < 1 || jj > nd) {
-            int si, sj;
-            border_src(i, jj, nd, si, sj);
-            src = si * Td + sj;
-        }
-        const float2 v = dep_new[src];
+    for (int t = lane; t < td2; t += 32) {
+        const int src = __ldg(B.src + ti2 + t);
+        const float2 v = acc_d[src];
         if (V.fp16 == 2)
-            reinterpret_cast<__half2*>(dep_raw)[t] =
+            reinterpret_cast<__half2*>(B.dep)[dof + t] =
                 __halves2half2(half_sr(v.x, sr_bits(srkey, p, t, 4)), half_sr(v.y, sr_bits(srkey, p, t, 5)));
         else if (V.fp16)
-            reinterpret_cast<__half2*>(dep_raw)[t] = __floats2half2_rn(v.x, v.y);
+            reinterpret_cast<__half2*>(B.dep)[dof + t] = __floats2half2_rn(v.x, v.y);
         else
-            reinterpret_cast<float2*>(dep_raw)[t] = v;
-        dn_raw[t] = dn_new[src];
-    }
-    __syncthreads();
-    // 5. coalesced write-back: 16-byte stores when the tile sizes allow
-    unsigned char* o_irr = reinterpret_cast<unsigned char*>(B.irr) + (size_t)p * irr_b;
-    unsigned char* o_dep = reinterpret_cast<unsigned char*>(B.dep) + (size_t)p * dep_b;
-    uint8_t* o_dn = B.dep_n + (size_t)p * dn_b;
-    if (tiles_bulk) {
-        for (uint32_t t = tid; t < irr_b / 16u; t += nthr)
-            reinterpret_cast<uint4*>(o_irr)[t] = reinterpret_cast<const uint4*>(irr_raw)[t];
-        for (uint32_t t = tid; t < dep_b / 16u; t += nthr)
-            reinterpret_cast<uint4*>(o_dep)[t] = reinterpret_cast<const uint4*>(dep_raw)[t];
-        for (uint32_t t = tid; t < dn_b / 16u; t += nthr)
-            reinterpret_cast<uint4*>(o_dn)[t] = reinterpret_cast<const uint4*>(dn_raw)[t];
-    } else {
-        for (uint32_t t = tid; t < irr_b / 4u; t += nthr)
-            reinterpret_cast<uint32_t*>(o_irr)[t] = reinterpret_cast<const uint32_t*>(irr_raw)[t];
-        for (uint32_t t = tid; t < dep_b / 4u; t += nthr)
-            reinterpret_cast<uint32_t*>(o_dep)[t] = reinterpret_cast<const uint32_t*>(dep_raw)[t];
-        for (uint32_t t = tid; t < dn_b; t += nthr) o_dn[t] = dn_raw[t];
+            reinterpret_cast<float2*>(B.dep)[dof + t] = v;
+        B.dep_n[dof + t] = dn_new[src];
     }
 }
 
@@ -658,7 +599,23 @@ __global__ void __launch_bounds__(128) k_query(VolConst V, const void* __restric
 
 }  // namespace
 
-size_t blend_smem_bytes(const VolConst& V) { return blend_layout(V.rays_max, V.Ti, V.Td).total; }
+size_t blend_plan_elems(int M)
+{
+    const size_t m = (size_t)(M > 0 ? M : 0);
+    return 2 * (m * (m + 1) / 2) + 8;
+}
+
+BlendPlan carve_blend_plan(uint16_t* base, int M)
+{
+    const size_t m = (size_t)(M > 0 ? M : 0), tri = m * (m + 1) / 2;
+    BlendPlan P;
+    P.key_i = base;
+    P.key_d = base + tri;
+    return P;
+}
+
+// shared memory of one probe (one warp) of k_blend
+size_t blend_smem_bytes(const VolConst& V) { return blend_layout(V.Ti, V.Td).total; }
 
 cudaError_t launch_change(const VolConst& V, const FrameDev* FD, const ChangeBufs& B, cudaStream_t s)
 {
@@ -677,14 +634,28 @@ cudaError_t launch_allocate(const uint32_t* W, int P, int avg, int m0, int rmax,
     return cudaGetLastError();
 }
 
+cudaError_t launch_blend_plan(const VolConst& V, const FrameDev* FD, const float4* sf, const BlendPlan& plan,
+                              cudaStream_t s)
+{
+    const int M = V.rays_max - kPilots;
+    if (M <= 0) return cudaSuccess;
+    const uint32_t n = (uint32_t)((size_t)M * (M + 1) / 2);
+    k_blend_plan<<<(n + 255) / 256, 256, 0, s>>>(V, FD, sf, plan, n);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_blend(const VolConst& V, const FrameDev* FD, const BlendBufs& B, const Tuning& T, cudaStream_t s)
 {
-    size_t sm = blend_smem_bytes(V);
+    // probes per CTA (one warp each), as many as the tuning asks and 227 KB allow
+    const size_t per = blend_smem_bytes(V);
+    const int wpb = std::max(1, std::min(T.blend_block / 32, (int)((227u * 1024u) / per)));
+    const size_t sm = per * (size_t)wpb;
     if (sm > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k_blend, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
     }
-    k_blend<<<V.P, T.blend_block, sm, s>>>(V, FD, B);
+    k_blend<<<(V.P + wpb - 1) / wpb, 32 * wpb, sm, s>>>(V, FD, B);
     count_launches(1);
     return cudaGetLastError();
 }
