@@ -160,7 +160,7 @@ struct adgi_volume_s {
     size_t bytes = 0;
     // tables
     float4* sf = nullptr;
-    uint16_t* plan = nullptr;  // per-frame blend plan (BlendPlan)
+    void* plan = nullptr;  // per-frame blend plan (BlendPlan)
     uint16_t* tex_src = nullptr;  // per texel: itself, or a border texel's octahedral fold partner
     uint16_t* lut_v = nullptr;
     uint16_t* lut_c = nullptr;
@@ -366,7 +366,11 @@ int adgi_create_volume(const adgi_volume_desc* desc, void* cuda_stream, adgi_vol
     std::vector<float4> sf;
     build_sf(M > 0 ? M : 0, sf);
     DA(v->sf, sf.size());
-    DA(v->plan, blend_plan_elems(M > 0 ? M : 0));
+    {
+        uint8_t* pb;
+        DA(pb, blend_plan_bytes(M > 0 ? M : 0, V.Ti, V.Td));
+        v->plan = pb;
+    }
     DA(v->tex_src, (size_t)V.Ti * V.Ti + (size_t)V.Td * V.Td);
     std::vector<uint16_t> tsrc;
     for (int n : {V.n_irr, V.n_dep}) {  // octahedral border fold of a tile with n x n interior
@@ -730,7 +734,7 @@ int enqueue_update(adgi_volume v, const FrameDev& fd, cudaStream_t s, bool phase
     // the blend plan needs only the frame descriptor: run it on the side
     // stream, beside the traversals, and join before the blend
     BlendBufs Bb{v->off,  v->sf,  v->pil_rec, v->m_rec,
-                 v->irr,  v->dep, v->dep_n,   carve_blend_plan(v->plan, V.rays_max - 8), v->tex_src};
+                 v->irr,  v->dep, v->dep_n,   carve_blend_plan(v->plan, V.rays_max - 8, V.Ti, V.Td), v->tex_src};
     CK(cudaEventRecord(v->fork, s));
     CK(cudaStreamWaitEvent(v->side, v->fork, 0));
     if (phases) CK(cudaEventRecord(v->plq[0], v->side));
@@ -1064,7 +1068,7 @@ int adgi_autotune(adgi_volume v, const adgi_frame* f, int32_t reps, adgi_tuning*
         CK(cudaMemcpyAsync(k + bi, v->dep, bd, cudaMemcpyDeviceToDevice, s));
         CK(cudaMemcpyAsync(k + bi + bd, v->dep_n, bn, cudaMemcpyDeviceToDevice, s));
         BlendBufs Bb{v->off,  v->sf,  v->pil_rec, v->m_rec,
-                 v->irr,  v->dep, v->dep_n,   carve_blend_plan(v->plan, V.rays_max - 8), v->tex_src};
+                 v->irr,  v->dep, v->dep_n,   carve_blend_plan(v->plan, V.rays_max - 8, V.Ti, V.Td), v->tex_src};
         const int wblocks[3] = {32, 64, 128};  // 1, 2 or 4 probe tiles (warps) per CTA
         for (int b : wblocks) {
             if (rc) break;

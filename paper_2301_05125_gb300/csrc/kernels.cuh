@@ -61,15 +61,18 @@ struct ShadeWork {
 };
 
 // Per-frame blend plan, shared by every probe with the same adaptive ray
-// count m: the irradiance and depth texel of every point of every row of the
-// SF table under this frame's rotation.  key_* [M(M+1)/2], row m at
-// m(m-1)/2, entry i = SF index i.
+// count m: for row m of the SF table, its SF indices sorted by the texel
+// their point falls in under this frame's rotation (stable: index order
+// within a texel), and each texel's bucket start.  ord_* [M(M+1)/2] (row m
+// at m(m-1)/2); beg_i [M][Ti^2+1], beg_d [M][Td^2+1] (row m at m-1).
 struct BlendPlan {
-    uint16_t* key_i;
-    uint16_t* key_d;
+    uint16_t* ord_i;
+    uint16_t* ord_d;
+    uint16_t* beg_i;
+    uint16_t* beg_d;
 };
-size_t blend_plan_elems(int M);  // uint16 elements of the plan
-BlendPlan carve_blend_plan(uint16_t* base, int M);
+size_t blend_plan_bytes(int M, int Ti, int Td);
+BlendPlan carve_blend_plan(void* base, int M, int Ti, int Td);
 
 struct BlendBufs {
     const uint32_t* off;

@@ -259,20 +259,20 @@ __global__ void __launch_bounds__(kAllocThreads) k_allocate(const uint32_t* __re
 
 // ============================================================== blend
 // Alg. ApproxAlgo + Alg. MovingAvgUpdate, batched per texel, in two kernels.
-//  plan  (once per frame): the irradiance and depth texel of every point of
-//        every row of the SF table under this frame's rotation -- every probe
-//        with m adaptive rays shares row m, so binning is done once per
-//        direction, not once per ray;
-//  blend (one warp per probe tile): the probe's ray records stream through
-//        shared memory 32 at a time (cp.async, double buffered) and the old
-//        tiles are staged beside them; within each group of 32 samples, the
-//        lanes that fall in the same texel are found with match_any and the
-//        group's lowest lane adds them in lane order, so every texel sums its
-//        samples in sample order (pilots, then SF index order): the result is
-//        deterministic, with no floating-point atomics.  Touched texels are
-//        blended with w = max(1 - h, k/(n+k)), and every texel -- border
-//        texels from their octahedral fold partner -- is written back with
-//        coalesced stores in texel order.
+//  plan  (once per frame, one CTA per row m of the SF table): the rotated
+//        directions of row m are binned to their nearest irradiance and depth
+//        texels and sorted by texel with a stable counting sort; every probe
+//        with m adaptive rays shares this plan, because its directions are
+//        the same -- binning is done once per direction, not once per ray;
+//  blend (one warp per probe tile): L2 prefetch of the probe's records and
+//        old tiles (cp.async.bulk.prefetch); each lane takes whole texels and
+//        sums the texel's pilot samples (pilot order) and then its bucket of
+//        the plan (SF index order), i.e. in sample order, so the result is
+//        deterministic with no floating-point atomics; the texel is blended
+//        with w = max(1 - h, k/(n+k)) into shared memory, and every texel --
+//        border texels from their octahedral fold partner -- is written back
+//        with coalesced stores in texel order.  Shared memory per warp is
+//        kept small: the kernel is latency bound, so warps per SM count.
 
 // float -> half with stochastic rounding: round toward zero, then step one
 // half ulp away from zero with probability equal to the remaining fraction
@@ -298,51 +298,107 @@ __device__ __forceinline__ uint32_t sr_bits(uint64_t key, int p, int t, int c)
 
 
 
-// 16-byte asynchronous copy global -> shared (both 16-byte aligned)
-__device__ __forceinline__ void cp_async16(void* dst, const void* src)
+
+// exclusive scan of cnt[0..n) into beg[0..n] (beg[n] = total) and, in place,
+// cnt -> running cursors; by one warp
+__device__ __forceinline__ void warp_scan_bins(uint32_t* cnt, uint16_t* beg, int n, int lane)
 {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
-                 "l"(src)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait()
-{
-    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+    uint32_t carry = 0;
+    for (int b0 = 0; b0 < n; b0 += 32) {
+        const int b = b0 + lane;
+        uint32_t c = b < n ? cnt[b] : 0u, x = c;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
+            if (lane >= d) x += y;
+        }
+        if (b < n) {
+            beg[b] = (uint16_t)(carry + x - c);
+            cnt[b] = carry + x - c;
+        }
+        carry += __shfl_sync(0xffffffffu, x, 31);
+    }
+    if (lane == 0) beg[n] = (uint16_t)carry;
 }
 
-// Plan of this frame: thread e handles entry e of the flat table (row m,
-// SF index i).
+// stable scatter of indices 0..n-1 by key (index order kept inside a key), by one warp
+__device__ __forceinline__ void warp_stable_scatter(const uint16_t* key, uint32_t* cur, uint16_t* ord, int n,
+                                                    int lane)
+{
+    const uint32_t lt = (1u << lane) - 1u;
+    for (int c0 = 0; c0 < n; c0 += 32) {
+        const int j = c0 + lane;
+        const bool valid = j < n;
+        const uint32_t k = valid ? (uint32_t)key[j] : 0x10000u + (uint32_t)lane;  // invalid lanes match nobody
+        const uint32_t mask = __match_any_sync(0xffffffffu, k);
+        uint32_t pos = 0;
+        if (valid) pos = cur[k] + (uint32_t)__popc(mask & lt);
+        __syncwarp();
+        if (valid) {
+            ord[pos] = (uint16_t)j;
+            if ((mask & lt) == 0u) cur[k] += (uint32_t)__popc(mask);  // lowest lane of the group advances the cursor
+        }
+        __syncwarp();
+    }
+}
+
+// Plan of SF row m = blockIdx.x + 1 for this frame's rotation.
 __global__ void __launch_bounds__(256) k_blend_plan(VolConst V, const FrameDev* __restrict__ FD,
-                                                    const float4* __restrict__ sf, BlendPlan Pl, uint32_t n_entries)
+                                                    const float4* __restrict__ sf, BlendPlan Pl)
 {
     const FrameConst& F = FD->F;
-    const uint32_t e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= n_entries) return;
-    // row m holds SF indices in a spatial order; position e - row start is
-    // SF index .w of that point
-    const uint32_t m = (uint32_t)((sqrtf(8.0f * (float)e + 1.0f) + 1.0f) * 0.5f);  // first guess of the row
-    uint32_t mm = m;
-    while (mm > 1 && (size_t)mm * (mm - 1) / 2 > e) --mm;  // m(m-1)/2 <= e < m(m+1)/2
-    while ((size_t)(mm + 1) * mm / 2 <= e) ++mm;
-    const size_t row = (size_t)mm * (mm - 1) / 2;
-    const float4 s4 = __ldg(sf + e);
-    const uint32_t i = (uint32_t)__float_as_int(s4.w);
-    if (i >= mm) {
-        atomicOr(V.err, kErrIndex);
-        return;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int m = blockIdx.x + 1;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nthr = blockDim.x;
+    const int ti2 = V.Ti * V.Ti, td2 = V.Td * V.Td;
+    uint32_t* cnt_i = reinterpret_cast<uint32_t*>(smem);
+    uint32_t* cnt_d = cnt_i + ti2;
+    uint16_t* key_i = reinterpret_cast<uint16_t*>(cnt_d + td2);
+    uint16_t* key_d = key_i + m;
+    for (int t = tid; t < ti2; t += nthr) cnt_i[t] = 0u;
+    for (int t = tid; t < td2; t += nthr) cnt_d[t] = 0u;
+    __syncthreads();
+    const size_t row = (size_t)m * (m - 1) / 2;
+    for (int k = tid; k < m; k += nthr) {  // row position k holds SF index .w
+        const float4 s4 = __ldg(sf + row + k);
+        const int i = __float_as_int(s4.w);
+        if (i < 0 || i >= m) {
+            atomicOr(V.err, kErrIndex);
+            continue;
+        }
+        const float2 e = oct_encode_x(rotate(F.R, s4));
+        const int ki = texel_of(e, V.n_irr), kd = texel_of(e, V.n_dep);
+        key_i[i] = (uint16_t)ki;
+        key_d[i] = (uint16_t)kd;
+        atomicAdd(cnt_i + ki, 1u);  // integer counts: order-independent
+        atomicAdd(cnt_d + kd, 1u);
     }
-    const float2 oe = oct_encode_x(rotate(F.R, s4));
-    Pl.key_i[row + i] = (uint16_t)texel_of(oe, V.n_irr);
-    Pl.key_d[row + i] = (uint16_t)texel_of(oe, V.n_dep);
+    __syncthreads();
+    uint16_t* beg_i = Pl.beg_i + (size_t)(m - 1) * (ti2 + 1);
+    uint16_t* beg_d = Pl.beg_d + (size_t)(m - 1) * (td2 + 1);
+    if (warp == 0) {
+        warp_scan_bins(cnt_i, beg_i, ti2, lane);
+        __syncwarp();
+        warp_stable_scatter(key_i, cnt_i, Pl.ord_i + row, m, lane);
+    }
+    if (warp == (nthr > 32 ? 1 : 0)) {
+        warp_scan_bins(cnt_d, beg_d, td2, lane);
+        __syncwarp();
+        warp_stable_scatter(key_d, cnt_d, Pl.ord_d + row, m, lane);
+    }
 }
 
-// shared memory of one probe (one warp) of k_blend: two 32-record buffers,
-// the pilot records and bins, the old tiles as stored, per-texel running
-// sums and counts, and the updated depth counts
+size_t blend_plan_smem(const VolConst& V)
+{
+    const size_t M = (size_t)(V.rays_max - kPilots);
+    return 4 * ((size_t)V.Ti * V.Ti + (size_t)V.Td * V.Td) + 4 * M;
+}
+
+// shared memory of one probe (one warp) of k_blend: the pilot records and
+// bins, and the updated tiles (kept small: the kernel is latency bound, so
+// warps per SM matter more than staging)
 struct BlendLayout {
-    uint32_t rb, prec, pkey, irr_raw, dep_raw, dn_raw, acc_i, acc_d, cnt_d, dn_new, total;
+    uint32_t prec, pkey, irr_new, dep_new, dn_new, total;
 };
 
 __host__ __device__ inline uint32_t al16(uint32_t x) { return (x + 15u) & ~15u; }
@@ -352,15 +408,10 @@ __host__ __device__ inline BlendLayout blend_layout(int Ti, int Td)
     const uint32_t ti2 = (uint32_t)(Ti * Ti), td2 = (uint32_t)(Td * Td);
     BlendLayout L;
     uint32_t o = 0;
-    L.rb = o, o += 2 * 32 * 16;
     L.prec = o, o += 16 * kPilots;
     L.pkey = o, o += 4 * 2 * kPilots;
-    L.irr_raw = o, o += al16(16 * ti2);
-    L.dep_raw = o, o += al16(8 * td2);
-    L.dn_raw = o, o += al16(td2);
-    L.acc_i = o, o += al16(16 * ti2);
-    L.acc_d = o, o += al16(8 * td2);
-    L.cnt_d = o, o += al16(2 * td2);
+    L.irr_new = o, o += al16(16 * ti2);
+    L.dep_new = o, o += al16(8 * td2);
     L.dn_new = o, o += al16(td2);
     L.total = o;
     return L;
@@ -370,12 +421,17 @@ __host__ __device__ inline BlendLayout blend_layout(int Ti, int Td)
 // never within 2^-7 of an integer, so single-precision rounding is harmless)
 __device__ __forceinline__ int tile_row(int t, float rT) { return (int)(((float)t + 0.5f) * rT); }
 
-__global__ void __launch_bounds__(256) k_blend(VolConst V, const FrameDev* __restrict__ FD, BlendBufs B)
+// hint: bring [src, src+bytes) into L2 (16-byte aligned address and size)
+__device__ __forceinline__ void prefetch_l2(const void* src, uint32_t bytes)
+{
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+
+__global__ void __launch_bounds__(128) k_blend(VolConst V, const FrameDev* __restrict__ FD, BlendBufs B)
 {
     const FrameConst& F = FD->F;
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const uint32_t lt = (1u << lane) - 1u;
     const int p = blockIdx.x * (blockDim.x >> 5) + wib;
     if (p >= V.P) return;  // the whole warp
     const uint32_t base = __ldg(B.off + p);
@@ -390,144 +446,96 @@ __global__ void __launch_bounds__(256) k_blend(VolConst V, const FrameDev* __res
     const int ti2 = Ti * Ti, td2 = Td * Td;
     const BlendLayout L = blend_layout(Ti, Td);
     unsigned char* ws = smem + (size_t)wib * L.total;
-    float4* rb = reinterpret_cast<float4*>(ws + L.rb);  // [2][32]
     float4* prs = reinterpret_cast<float4*>(ws + L.prec);
     int* pk_i = reinterpret_cast<int*>(ws + L.pkey);
     int* pk_d = pk_i + kPilots;
-    unsigned char* irr_raw = ws + L.irr_raw;
-    unsigned char* dep_raw = ws + L.dep_raw;
-    uint8_t* dn_raw = ws + L.dn_raw;
-    float4* acc_i = reinterpret_cast<float4*>(ws + L.acc_i);
-    float2* acc_d = reinterpret_cast<float2*>(ws + L.acc_d);
-    uint16_t* cnt_d = reinterpret_cast<uint16_t*>(ws + L.cnt_d);
+    float4* irr_new = reinterpret_cast<float4*>(ws + L.irr_new);
+    float2* dep_new = reinterpret_cast<float2*>(ws + L.dep_new);
     uint8_t* dn_new = ws + L.dn_new;
     const size_t io = (size_t)p * ti2, dof = (size_t)p * td2;
     const float4* mrec = B.main_rec + base;
-    // old tiles: asynchronous copies when the tile sizes are 16-byte multiples
-    const uint32_t irr_b = (uint32_t)ti2 * (V.fp16 ? 8u : 16u), dep_b = (uint32_t)td2 * (V.fp16 ? 4u : 8u);
-    const uint32_t dn_b = (uint32_t)td2;
-    const bool tiles_async = (irr_b % 16u) == 0u && (dep_b % 16u) == 0u && (dn_b % 16u) == 0u;
-    const unsigned char* g_irr = reinterpret_cast<const unsigned char*>(B.irr) + (size_t)p * irr_b;
-    const unsigned char* g_dep = reinterpret_cast<const unsigned char*>(B.dep) + (size_t)p * dep_b;
-    const uint8_t* g_dn = B.dep_n + dof;
-    if (tiles_async) {
-        for (uint32_t c = lane; c < irr_b / 16u; c += 32) cp_async16(irr_raw + 16 * c, g_irr + 16 * c);
-        for (uint32_t c = lane; c < dep_b / 16u; c += 32) cp_async16(dep_raw + 16 * c, g_dep + 16 * c);
-        for (uint32_t c = lane; c < dn_b / 16u; c += 32) cp_async16(dn_raw + 16 * c, g_dn + 16 * c);
-    } else {
-        for (uint32_t c = lane; c < irr_b / 4u; c += 32)
-            reinterpret_cast<uint32_t*>(irr_raw)[c] = reinterpret_cast<const uint32_t*>(g_irr)[c];
-        for (uint32_t c = lane; c < dep_b / 4u; c += 32)
-            reinterpret_cast<uint32_t*>(dep_raw)[c] = reinterpret_cast<const uint32_t*>(g_dep)[c];
-        for (uint32_t c = lane; c < dn_b; c += 32) dn_raw[c] = g_dn[c];
+    if (lane == 0) {  // L2 prefetch of the records and the old tiles, gathered below
+        if (m) prefetch_l2(mrec, 16u * m);
+        const uint32_t irr_b = (uint32_t)ti2 * (V.fp16 ? 8u : 16u), dep_b = (uint32_t)td2 * (V.fp16 ? 4u : 8u);
+        if ((irr_b % 16u) == 0u) prefetch_l2(reinterpret_cast<const unsigned char*>(B.irr) + (size_t)p * irr_b, irr_b);
+        if ((dep_b % 16u) == 0u) prefetch_l2(reinterpret_cast<const unsigned char*>(B.dep) + (size_t)p * dep_b, dep_b);
+        if ((td2 % 16) == 0) prefetch_l2(B.dep_n + dof, (uint32_t)td2);
     }
-    cp_async_commit();  // group: tiles
-    // records of rounds 0 and 1 (32 samples each)
-    const uint32_t rounds = (m + 31u) / 32u;
-    if (lane < m) cp_async16(rb + lane, mrec + lane);
-    cp_async_commit();  // group: round 0
-    if (32u + lane < m) cp_async16(rb + 32 + lane, mrec + 32 + lane);
-    cp_async_commit();  // group: round 1
-    // pilot samples (first in every texel's sum, in pilot order): records and
-    // bins, added by one lane
+    // pilot samples: records and bins (pilots come first in every texel's sum)
     if (npil && lane < kPilots) {
         prs[lane] = __ldg(B.pil_rec + (size_t)p * kPilots + lane);
         const float2 e = oct_encode_x(pilot_dir(F.pilot_key, (uint32_t)p, lane));
         pk_i[lane] = texel_of(e, ni);
         pk_d[lane] = texel_of(e, nd);
     }
-    for (int t = lane; t < ti2; t += 32) acc_i[t] = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int t = lane; t < td2; t += 32) {
-        acc_d[t] = make_float2(0.f, 0.f);
-        cnt_d[t] = 0;
-    }
+    const uint16_t* ord_i = B.plan.ord_i + (m ? (size_t)m * (m - 1) / 2 : 0);
+    const uint16_t* ord_d = B.plan.ord_d + (m ? (size_t)m * (m - 1) / 2 : 0);
+    const uint16_t* beg_i = B.plan.beg_i + (size_t)(m ? m - 1 : 0) * (ti2 + 1);
+    const uint16_t* beg_d = B.plan.beg_d + (size_t)(m ? m - 1 : 0) * (td2 + 1);
     __syncwarp();
-    if (lane == 0)
-        for (int o = 0; o < npil; ++o) {
-            const float4 r = prs[o];
-            float4& ai = acc_i[pk_i[o]];
-            ai.x += r.x;
-            ai.y += r.y;
-            ai.z += r.z;
-            ai.w += 1.0f;
-            float2& ad = acc_d[pk_d[o]];
-            ad.x += r.w;
-            ad.y += r.w * r.w;
-            cnt_d[pk_d[o]] += 1;
-        }
-    // adaptive samples, 32 per round in SF index order
-    const size_t row = m ? (size_t)m * (m - 1) / 2 : 0;
-    uint32_t ki = 0, kd = 0;
-    if (lane < m) {
-        ki = __ldg(B.plan.key_i + row + lane);
-        kd = __ldg(B.plan.key_d + row + lane);
-    }
-    for (uint32_t r = 0; r < rounds; ++r) {
-        const uint32_t j = 32u * r + lane;
-        const bool valid = j < m;
-        uint32_t ki_n = 0, kd_n = 0;  // next round's bins, loaded early
-        if (j + 32u < m) {
-            ki_n = __ldg(B.plan.key_i + row + j + 32u);
-            kd_n = __ldg(B.plan.key_d + row + j + 32u);
-        }
-        cp_async_wait<1>();  // this round's records have landed (the next round's may be in flight)
-        __syncwarp();
-        const float4* cur = rb + 32 * (r & 1u);
-        const uint32_t gi = __match_any_sync(0xffffffffu, valid ? ki : 0x10000u + lane);
-        if (valid && (gi & lt) == 0u) {  // lowest lane of its group: add the group in lane order
-            float4& a = acc_i[ki];
-            for (uint32_t g = gi; g; g &= g - 1u) {
-                const float4 x = cur[__ffs(g) - 1];
-                a.x += x.x;
-                a.y += x.y;
-                a.z += x.z;
-            }
-            a.w += (float)__popc(gi);
-        }
-        const uint32_t gd = __match_any_sync(0xffffffffu, valid ? kd : 0x10000u + lane);
-        if (valid && (gd & lt) == 0u) {
-            float2& a = acc_d[kd];
-            for (uint32_t g = gd; g; g &= g - 1u) {
-                const float x = cur[__ffs(g) - 1].w;
-                a.x += x;
-                a.y += x * x;
-            }
-            cnt_d[kd] += (uint16_t)__popc(gd);
-        }
-        __syncwarp();
-        // refill the buffer just consumed with round r + 2
-        const uint32_t j2 = j + 64u;
-        if (j2 < m) cp_async16(rb + 32 * (r & 1u) + lane, mrec + j2);
-        cp_async_commit();
-        ki = ki_n;
-        kd = kd_n;
-    }
-    cp_async_wait<0>();
-    __syncwarp();
-    // blend the interior texels in place (untouched ones keep their value)
+    // each lane sums whole texels: the pilots of the texel in pilot order,
+    // then the texel's bucket of the plan in SF index order (the sample
+    // order), and blends the texel
     const float omh = 1.0f - V.hyst;
     const float rni = 1.0f / (float)ni, rnd = 1.0f / (float)nd;
     for (int q = lane; q < ni * ni; q += 32) {
         const int r = tile_row(q, rni), t = (r + 1) * Ti + (q - r * ni) + 1;
-        const float4 a = acc_i[t];
-        float4 v = irr_load(irr_raw, (size_t)t, V.fp16);
-        if (a.w > 0.0f) {
-            const float kf = a.w;
+        float sx = 0.f, sy = 0.f, sz = 0.f;
+        uint32_t k = 0;
+        for (int o = 0; o < npil; ++o)
+            if (pk_i[o] == t) {
+                const float4 x = prs[o];
+                sx += x.x;
+                sy += x.y;
+                sz += x.z;
+                ++k;
+            }
+        if (m) {
+            const uint32_t b0 = __ldg(beg_i + t), b1 = __ldg(beg_i + t + 1);
+            for (uint32_t u = b0; u < b1; ++u) {
+                const uint32_t i = min((uint32_t)__ldg(ord_i + u), m - 1);
+                const float4 x = __ldg(mrec + i);
+                sx += x.x;
+                sy += x.y;
+                sz += x.z;
+            }
+            k += b1 - b0;
+        }
+        float4 v = irr_load(B.irr, io + t, V.fp16);
+        if (k) {
+            const float kf = (float)k;
             const float w = fmaxf(omh, __fdividef(kf, v.w + kf));
             const float ik = __frcp_rn(kf);
-            v.x += w * (a.x * ik - v.x);
-            v.y += w * (a.y * ik - v.y);
-            v.z += w * (a.z * ik - v.z);
+            v.x += w * (sx * ik - v.x);
+            v.y += w * (sy * ik - v.y);
+            v.z += w * (sz * ik - v.z);
             v.w = fminf(v.w + kf, 255.0f);
         }
-        acc_i[t] = v;
+        irr_new[t] = v;
     }
     for (int q = lane; q < nd * nd; q += 32) {
         const int r = tile_row(q, rnd), t = (r + 1) * Td + (q - r * nd) + 1;
-        const float2 a = acc_d[t];
-        float2 v = dep_load(dep_raw, (size_t)t, V.fp16);
-        uint32_t c = dn_raw[t];
-        const uint32_t k = cnt_d[t];
+        float s1 = 0.f, s2 = 0.f;
+        uint32_t k = 0;
+        for (int o = 0; o < npil; ++o)
+            if (pk_d[o] == t) {
+                const float x = prs[o].w;
+                s1 += x;
+                s2 += x * x;
+                ++k;
+            }
+        if (m) {
+            const uint32_t b0 = __ldg(beg_d + t), b1 = __ldg(beg_d + t + 1);
+            for (uint32_t u = b0; u < b1; ++u) {
+                const uint32_t i = min((uint32_t)__ldg(ord_d + u), m - 1);
+                const float x = __ldg(mrec + i).w;
+                s1 += x;
+                s2 += x * x;
+            }
+            k += b1 - b0;
+        }
+        float2 v = dep_load(B.dep, dof + t, V.fp16);
+        uint32_t c = B.dep_n[dof + t];
         if (k) {
             // the texel stores {mean, variance}; with batch mean m and batch
             // variance vb the moving average of {d, d^2} becomes
@@ -537,14 +545,14 @@ __global__ void __launch_bounds__(256) k_blend(VolConst V, const FrameDev* __res
             const float kf = (float)k;
             const float w = fmaxf(omh, __fdividef(kf, (float)c + kf));
             const float ik = __frcp_rn(kf);
-            const float mb = a.x * ik;
-            const float vb = fmaxf(a.y * ik - mb * mb, 0.0f);
+            const float mb = s1 * ik;
+            const float vb = fmaxf(s2 * ik - mb * mb, 0.0f);
             const float dm = mb - v.x;
             v.y = (1.0f - w) * v.y + w * vb + w * (1.0f - w) * dm * dm;
             v.x += w * dm;
             c = (uint32_t)fminf((float)c + kf, 255.0f);
         }
-        acc_d[t] = v;
+        dep_new[t] = v;
         dn_new[t] = (uint8_t)c;
     }
     __syncwarp();
@@ -552,7 +560,7 @@ __global__ void __launch_bounds__(256) k_blend(VolConst V, const FrameDev* __res
     // storage format, stored in texel order (coalesced)
     const uint64_t srkey = F.pilot_key ^ (F.even ? 0x5352ull : 0x5353ull);
     for (int t = lane; t < ti2; t += 32) {
-        const float4 v = acc_i[__ldg(B.src + t)];
+        const float4 v = irr_new[__ldg(B.src + t)];
         if (V.fp16 == 2) {
             __half2* h = reinterpret_cast<__half2*>(B.irr) + 2 * (io + t);
             const __half2 h0 = __halves2half2(half_sr(v.x, sr_bits(srkey, p, t, 0)), half_sr(v.y, sr_bits(srkey, p, t, 1)));
@@ -570,7 +578,7 @@ __global__ void __launch_bounds__(256) k_blend(VolConst V, const FrameDev* __res
     }
     for (int t = lane; t < td2; t += 32) {
         const int src = __ldg(B.src + ti2 + t);
-        const float2 v = acc_d[src];
+        const float2 v = dep_new[src];
         if (V.fp16 == 2)
             reinterpret_cast<__half2*>(B.dep)[dof + t] =
                 __halves2half2(half_sr(v.x, sr_bits(srkey, p, t, 4)), half_sr(v.y, sr_bits(srkey, p, t, 5)));
@@ -599,18 +607,21 @@ __global__ void __launch_bounds__(128) k_query(VolConst V, const void* __restric
 
 }  // namespace
 
-size_t blend_plan_elems(int M)
-{
-    const size_t m = (size_t)(M > 0 ? M : 0);
-    return 2 * (m * (m + 1) / 2) + 8;
-}
-
-BlendPlan carve_blend_plan(uint16_t* base, int M)
+size_t blend_plan_bytes(int M, int Ti, int Td)
 {
     const size_t m = (size_t)(M > 0 ? M : 0), tri = m * (m + 1) / 2;
+    return sizeof(uint16_t) * (2 * tri + m * ((size_t)Ti * Ti + 1) + m * ((size_t)Td * Td + 1) + 8);
+}
+
+BlendPlan carve_blend_plan(void* base, int M, int Ti, int Td)
+{
+    const size_t m = (size_t)(M > 0 ? M : 0), tri = m * (m + 1) / 2;
+    uint16_t* b = reinterpret_cast<uint16_t*>(base);
     BlendPlan P;
-    P.key_i = base;
-    P.key_d = base + tri;
+    P.ord_i = b;
+    P.ord_d = b + tri;
+    P.beg_i = b + 2 * tri;
+    P.beg_d = P.beg_i + m * ((size_t)Ti * Ti + 1);
     return P;
 }
 
@@ -639,8 +650,12 @@ cudaError_t launch_blend_plan(const VolConst& V, const FrameDev* FD, const float
 {
     const int M = V.rays_max - kPilots;
     if (M <= 0) return cudaSuccess;
-    const uint32_t n = (uint32_t)((size_t)M * (M + 1) / 2);
-    k_blend_plan<<<(n + 255) / 256, 256, 0, s>>>(V, FD, sf, plan, n);
+    const size_t ps = blend_plan_smem(V);
+    if (ps > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_blend_plan, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ps);
+        if (e != cudaSuccess) return e;
+    }
+    k_blend_plan<<<M, 256, ps, s>>>(V, FD, sf, plan);
     count_launches(1);
     return cudaGetLastError();
 }
