@@ -490,18 +490,32 @@ __global__ void __launch_bounds__(128) k_blend(VolConst V, const FrameDev* __res
                 sz += x.z;
                 ++k;
             }
+        float4 v = irr_load(B.irr, io + t, V.fp16);  // issued early: independent of the sums
         if (m) {
             const uint32_t b0 = __ldg(beg_i + t), b1 = __ldg(beg_i + t + 1);
-            for (uint32_t u = b0; u < b1; ++u) {
-                const uint32_t i = min((uint32_t)__ldg(ord_i + u), m - 1);
-                const float4 x = __ldg(mrec + i);
+            uint32_t u = b0;
+            for (; u + 4 <= b1; u += 4) {  // four gathers in flight, added in order
+                uint32_t i4[4];
+#pragma unroll
+                for (int z = 0; z < 4; ++z) i4[z] = min((uint32_t)__ldg(ord_i + u + z), m - 1);
+                float4 x4[4];
+#pragma unroll
+                for (int z = 0; z < 4; ++z) x4[z] = __ldg(mrec + i4[z]);
+#pragma unroll
+                for (int z = 0; z < 4; ++z) {
+                    sx += x4[z].x;
+                    sy += x4[z].y;
+                    sz += x4[z].z;
+                }
+            }
+            for (; u < b1; ++u) {
+                const float4 x = __ldg(mrec + min((uint32_t)__ldg(ord_i + u), m - 1));
                 sx += x.x;
                 sy += x.y;
                 sz += x.z;
             }
             k += b1 - b0;
         }
-        float4 v = irr_load(B.irr, io + t, V.fp16);
         if (k) {
             const float kf = (float)k;
             const float w = fmaxf(omh, __fdividef(kf, v.w + kf));
@@ -524,18 +538,26 @@ __global__ void __launch_bounds__(128) k_blend(VolConst V, const FrameDev* __res
                 s2 += x * x;
                 ++k;
             }
+        float2 v = dep_load(B.dep, dof + t, V.fp16);  // issued early: independent of the sums
+        uint32_t c = B.dep_n[dof + t];
         if (m) {
             const uint32_t b0 = __ldg(beg_d + t), b1 = __ldg(beg_d + t + 1);
-            for (uint32_t u = b0; u < b1; ++u) {
-                const uint32_t i = min((uint32_t)__ldg(ord_d + u), m - 1);
-                const float x = __ldg(mrec + i).w;
+            uint32_t u = b0;
+            for (; u + 2 <= b1; u += 2) {  // two gathers in flight, added in order
+                const uint32_t i0 = min((uint32_t)__ldg(ord_d + u), m - 1), i1 = min((uint32_t)__ldg(ord_d + u + 1), m - 1);
+                const float x0 = __ldg(&mrec[i0].w), x1 = __ldg(&mrec[i1].w);
+                s1 += x0;
+                s2 += x0 * x0;
+                s1 += x1;
+                s2 += x1 * x1;
+            }
+            if (u < b1) {
+                const float x = __ldg(&mrec[min((uint32_t)__ldg(ord_d + u), m - 1)].w);
                 s1 += x;
                 s2 += x * x;
             }
             k += b1 - b0;
         }
-        float2 v = dep_load(B.dep, dof + t, V.fp16);
-        uint32_t c = B.dep_n[dof + t];
         if (k) {
             // the texel stores {mean, variance}; with batch mean m and batch
             // variance vb the moving average of {d, d^2} becomes
