@@ -782,6 +782,115 @@ EXPORT int orc_allocate(const uint32_t* W, int P, int avg, int rmin, int rmax, u
 }
 
 /* ------------------------------------------------------------------------ */
+/* Packed 32-bit atlases (Sec. "Probe irradiance cache", "Probe visibility   */
+/* cache", appendix "Probe compression").  A channel value v >= 0 is coded   */
+/* as u = min(ln(gamma v + 1), beta) / beta quantised to b bits by rounding  */
+/* down; decoding is (exp(beta u) - 1) / gamma.  Irradiance texel: R9 G9 B8 */
+/* (beta 5, gamma 15) and a 6-bit sample count N; visibility texel: the     */
+/* mean distance and mean squared distance, both divided by the probe cage  */
+/* diagonal s (and s^2), 13 bits each with (beta, gamma) = (5, 15) and      */
+/* (8, 20), and N.  The code is exact through its thresholds: code k stands */
+/* for t_k = (exp(beta k / (2^b - 1)) - 1) / gamma (FP64, rounded to FP32),  */
+/* and v codes to the largest k with t_k <= v -- rounding down of u, with    */
+/* the thresholds as the single definition of the boundaries.               */
+/* Sample updates follow Alg. MovingAvgUpdate one sample at a time (as the  */
+/* CAS loop of Alg. atmMvAvgUpd serialises them), in sample order:          */
+/* V = v / (n + 1) + (n o) / (n + 1) in FP32 on the decoded o, then coded   */
+/* again; N = min(n + 1, 63) (6 bits).                                      */
+/* ------------------------------------------------------------------------ */
+#define PK_NMAX 63u
+typedef struct {
+    int bits;
+    uint32_t kmax;
+    float t[8192];
+} codec_tab;
+
+static void codec_init(codec_tab* c, int bits, double beta, double gamma)
+{
+    c->bits = bits;
+    c->kmax = (1u << bits) - 1u;
+    for (uint32_t k = 0; k <= c->kmax; ++k)
+        c->t[k] = (float)((exp(beta * (double)k / (double)c->kmax) - 1.0) / gamma);
+}
+
+static uint32_t codec_enc(const codec_tab* c, float v)
+{
+    if (!(v > 0.0f)) return 0u; /* negatives, zero and NaN code to 0 */
+    uint32_t lo = 0, hi = c->kmax; /* t[lo] <= v */
+    while (lo < hi) {
+        uint32_t mid = (lo + hi + 1u) / 2u;
+        if (c->t[mid] <= v)
+            lo = mid;
+        else
+            hi = mid - 1u;
+    }
+    return lo;
+}
+
+static float codec_dec(const codec_tab* c, uint32_t k) { return c->t[k <= c->kmax ? k : c->kmax]; }
+
+/* one moving-average step on a decoded value (Alg. MovingAvgUpdate), FP32 */
+static float mav_step(float o, float v, uint32_t n)
+{
+    float n1 = (float)(n + 1u);
+    float a = v / n1;
+    float b = ((float)n * o) / n1;
+    return a + b;
+}
+
+static codec_tab g_c9, g_c8, g_c13m, g_c13q;
+static pthread_once_t g_codec_once = PTHREAD_ONCE_INIT;
+static void codec_tables_init(void)
+{
+    codec_init(&g_c9, 9, 5.0, 15.0);
+    codec_init(&g_c8, 8, 5.0, 15.0);
+    codec_init(&g_c13m, 13, 5.0, 15.0);
+    codec_init(&g_c13q, 13, 8.0, 20.0);
+}
+
+static const codec_tab* codec_of(int which)
+{
+    pthread_once(&g_codec_once, codec_tables_init);
+    switch (which) {
+    case 0: return &g_c9;
+    case 1: return &g_c8;
+    case 2: return &g_c13m;
+    default: return &g_c13q;
+    }
+}
+
+/* which: 0 = 9-bit irradiance, 1 = 8-bit irradiance, 2 = 13-bit mean
+   distance, 3 = 13-bit mean squared distance */
+EXPORT uint32_t orc_codec_enc(int which, float v) { return codec_enc(codec_of(which), v); }
+EXPORT float orc_codec_dec(int which, uint32_t k) { return codec_dec(codec_of(which), k); }
+EXPORT float orc_codec_mav(float o, float v, uint32_t n) { return mav_step(o, v, n); }
+
+/* packed texels: irradiance R bits 0-8, G 9-17, B 18-25, N 26-31;
+   visibility mean bits 0-12, mean square 13-25, N 26-31 */
+static uint32_t pk_irr_update(uint32_t code, const float v[3])
+{
+    const codec_tab *c9 = codec_of(0), *c8 = codec_of(1);
+    uint32_t n = code >> 26;
+    float o0 = codec_dec(c9, code & 511u), o1 = codec_dec(c9, (code >> 9) & 511u), o2 = codec_dec(c8, (code >> 18) & 255u);
+    uint32_t k0 = codec_enc(c9, mav_step(o0, v[0], n));
+    uint32_t k1 = codec_enc(c9, mav_step(o1, v[1], n));
+    uint32_t k2 = codec_enc(c8, mav_step(o2, v[2], n));
+    uint32_t nn = n + 1u < PK_NMAX ? n + 1u : PK_NMAX;
+    return k0 | (k1 << 9) | (k2 << 18) | (nn << 26);
+}
+
+static uint32_t pk_dep_update(uint32_t code, float x)
+{
+    const codec_tab *cm = codec_of(2), *cq = codec_of(3);
+    uint32_t n = code >> 26;
+    float om = codec_dec(cm, code & 8191u), oq = codec_dec(cq, (code >> 13) & 8191u);
+    uint32_t km = codec_enc(cm, mav_step(om, x, n));
+    uint32_t kq = codec_enc(cq, mav_step(oq, x * x, n));
+    uint32_t nn = n + 1u < PK_NMAX ? n + 1u : PK_NMAX;
+    return km | (kq << 13) | (nn << 26);
+}
+
+/* ------------------------------------------------------------------------ */
 /* Volume state                                                              */
 /* ------------------------------------------------------------------------ */
 typedef struct {
@@ -792,6 +901,7 @@ typedef struct {
     float hyst;           /* hysteresis h */
     float depth_max;      /* depth clamp; <= 0 selects 1.5 * voxel diagonal */
     int theta;            /* temporal trigger decay length (frames) */
+    int packed;           /* 1: 32-bit packed atlases (the paper's codecs) */
 } orc_desc;
 
 typedef struct {
@@ -825,6 +935,11 @@ typedef struct orc_vol {
     float* alb;
     cbvh bvh;
     int bvh_dirty;
+    /* packed atlases (desc.packed): the codes are the state; irr/dep
+       below then hold their decoded FP64 view, which the queries read */
+    uint32_t* irr_pk; /* P * Ti*Ti */
+    uint32_t* dep_pk; /* P * Td*Td */
+    float s_f;        /* (float) s: the visibility normaliser */
     /* atlases, FP64 */
     double* irr;    /* P * Ti*Ti * 3 */
     uint8_t* irr_n; /* P * Ti*Ti */
@@ -903,6 +1018,11 @@ EXPORT orc_vol* orc_create(const orc_desc* d, int nthreads)
         for (int m = 1; m <= v->sf_M; ++m) orc_sf_points(m, v->sf + 3 * ((size_t)m * (size_t)(m - 1) / 2));
     }
     size_t P = (size_t)v->P;
+    v->s_f = (float)v->s;
+    if (d->packed) {
+        v->irr_pk = (uint32_t*)calloc(P * v->Ti * v->Ti, 4);
+        v->dep_pk = (uint32_t*)calloc(P * v->Td * v->Td, 4);
+    }
     v->irr = (double*)calloc(P * v->Ti * v->Ti * 3, sizeof(double));
     v->irr_n = (uint8_t*)calloc(P * v->Ti * v->Ti, 1);
     v->dep = (double*)calloc(P * v->Td * v->Td * 2, sizeof(double));
@@ -950,6 +1070,8 @@ EXPORT void orc_destroy(orc_vol* v)
     free(v->irr_n);
     free(v->dep);
     free(v->dep_n);
+    free(v->irr_pk);
+    free(v->dep_pk);
     free(v->qv_even);
     free(v->qr_even);
     free(v->trv);
@@ -1296,6 +1418,88 @@ static void border_copy(double* tile, uint8_t* cnt, int n, int ch)
 #undef CP
 }
 
+/* octahedral border fold of a tile of codes (the same texel map as
+   border_copy) */
+static void border_copy_u32(uint32_t* tile, int n)
+{
+    int T = n + 2;
+    for (int j = 1; j <= n; ++j) {
+        tile[j] = tile[T + (n + 1 - j)];
+        tile[(n + 1) * T + j] = tile[n * T + (n + 1 - j)];
+    }
+    for (int i = 1; i <= n; ++i) {
+        tile[i * T] = tile[(n + 1 - i) * T + 1];
+        tile[i * T + n + 1] = tile[(n + 1 - i) * T + n];
+    }
+    tile[0] = tile[n * T + n];
+    tile[n + 1] = tile[n * T + 1];
+    tile[(n + 1) * T] = tile[T + n];
+    tile[(n + 1) * T + n + 1] = tile[T + 1];
+}
+
+/* the decoded view of probe p's packed tiles (what the queries read) */
+static void decode_probe(orc_vol* v, int p)
+{
+    const int Ti = v->Ti, Td = v->Td;
+    const codec_tab *c9 = codec_of(0), *c8 = codec_of(1), *cm = codec_of(2), *cq = codec_of(3);
+    const double s = (double)v->s_f;
+    for (int t = 0; t < Ti * Ti; ++t) {
+        uint32_t c = v->irr_pk[(size_t)p * Ti * Ti + t];
+        double* o = v->irr + ((size_t)p * Ti * Ti + t) * 3;
+        o[0] = codec_dec(c9, c & 511u);
+        o[1] = codec_dec(c9, (c >> 9) & 511u);
+        o[2] = codec_dec(c8, (c >> 18) & 255u);
+        v->irr_n[(size_t)p * Ti * Ti + t] = (uint8_t)(c >> 26);
+    }
+    for (int t = 0; t < Td * Td; ++t) {
+        uint32_t c = v->dep_pk[(size_t)p * Td * Td + t];
+        double* o = v->dep + ((size_t)p * Td * Td + t) * 2;
+        o[0] = (double)codec_dec(cm, c & 8191u) * s;
+        o[1] = (double)codec_dec(cq, (c >> 13) & 8191u) * s * s;
+        v->dep_n[(size_t)p * Td * Td + t] = (uint8_t)(c >> 26);
+    }
+}
+
+/* Packed blend: every sample, in sample order (pilots first, then SF index
+   order), updates its nearest irradiance and visibility texel with one
+   moving-average step on the codes; then the border fold. */
+static void blend_probe_packed(orc_vol* v, int p, int use_pilots)
+{
+    const int Ti = v->Ti, Td = v->Td, ni = v->d.n_irr, nd = v->d.n_dep;
+    uint32_t* irr = v->irr_pk + (size_t)p * Ti * Ti;
+    uint32_t* dep = v->dep_pk + (size_t)p * Td * Td;
+    const uint32_t mp = v->n[p] - 8u;
+    const int total = (int)mp + (use_pilots ? 8 : 0);
+    for (int j = 0; j < total; ++j) {
+        float d[3];
+        const double* rad;
+        double ds;
+        if (use_pilots && j < 8) {
+            const float* pd = v->pil_dir + ((size_t)p * 8 + (size_t)j) * 3;
+            d[0] = pd[0];
+            d[1] = pd[1];
+            d[2] = pd[2];
+            rad = v->pil_rad + ((size_t)p * 8 + (size_t)j) * 3;
+            ds = v->pil_dep[(size_t)p * 8 + (size_t)j];
+        } else {
+            int i = use_pilots ? j - 8 : j;
+            main_dir(v, (int)mp, i, d);
+            size_t r = (size_t)v->off[p] + (size_t)i;
+            rad = v->m_rad + r * 3;
+            ds = v->m_dep[r];
+        }
+        int ti = orc_texel_of_dir(d, ni);
+        int td = orc_texel_of_dir(d, nd);
+        float vr[3] = {(float)rad[0], (float)rad[1], (float)rad[2]};
+        irr[ti] = pk_irr_update(irr[ti], vr);
+        float x = (float)ds / v->s_f; /* distance in units of the cage diagonal */
+        dep[td] = pk_dep_update(dep[td], x);
+    }
+    border_copy_u32(irr, ni);
+    border_copy_u32(dep, nd);
+    decode_probe(v, p);
+}
+
 static void blend_probe(orc_vol* v, int p, int use_pilots, double h)
 {
     const int Ti = v->Ti, Td = v->Td, ni = v->d.n_irr, nd = v->d.n_dep;
@@ -1524,7 +1728,10 @@ static void* worker(void* arg)
         else if (j->phase == 1)
             main_probe(j->v, j->fr, p);
         else
-            blend_probe(j->v, p, (j->fr->frame & 1u) == 0, (double)j->v->d.hyst);
+            if (j->v->d.packed)
+                blend_probe_packed(j->v, p, (j->fr->frame & 1u) == 0);
+            else
+                blend_probe(j->v, p, (j->fr->frame & 1u) == 0, (double)j->v->d.hyst);
     }
     return NULL;
 }
@@ -1624,6 +1831,24 @@ EXPORT void orc_set_atlas(orc_vol* v, const double* irr, const uint8_t* irr_n, c
 }
 
 EXPORT void orc_border_copy(double* tile, uint8_t* cnt, int n, int ch) { border_copy(tile, cnt, n, ch); }
+
+/* packed atlases (NULL unless the volume was created packed) */
+EXPORT const uint32_t* orc_irr_packed(const orc_vol* v) { return v->irr_pk; }
+EXPORT const uint32_t* orc_dep_packed(const orc_vol* v) { return v->dep_pk; }
+EXPORT float orc_cage_diag(const orc_vol* v) { return v->s_f; }
+
+/* Test hook: blend given records of probe p into the packed atlases (the
+   probe's pilot directions, n_p and offsets from the last update). */
+EXPORT void orc_blend_packed_records(orc_vol* v, int p, int use_pilots, const double* pil_rad, const double* pil_dep,
+                                     const double* m_rad, const double* m_dep)
+{
+    size_t r0 = (size_t)v->off[p], m = (size_t)(v->n[p] - 8u);
+    if (pil_rad) memcpy(v->pil_rad + (size_t)p * 8 * 3, pil_rad, 8 * 3 * sizeof(double));
+    if (pil_dep) memcpy(v->pil_dep + (size_t)p * 8, pil_dep, 8 * sizeof(double));
+    if (m_rad) memcpy(v->m_rad + r0 * 3, m_rad, m * 3 * sizeof(double));
+    if (m_dep) memcpy(v->m_dep + r0, m_dep, m * sizeof(double));
+    blend_probe_packed(v, p, use_pilots);
+}
 
 /* Test hook: run the heuristics step (Sec. 4.1-4.2) on given pilot results. */
 EXPORT void orc_change_from_pilots(orc_vol* v, const orc_frame* fr, const float* pil_t, const int* pil_tri,

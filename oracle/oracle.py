@@ -26,6 +26,7 @@ class OrcDesc(C.Structure):
         ("hyst", C.c_float),
         ("depth_max", C.c_float),
         ("theta", C.c_int),
+        ("packed", C.c_int),
     ]
 
 
@@ -111,6 +112,18 @@ def lib():
         L.orc_set_atlas.argtypes = [vp, f64p, u8p, f64p, u8p]
         L.orc_border_copy.argtypes = [f64p, u8p, C.c_int, C.c_int]
         L.orc_change_from_pilots.argtypes = [vp, C.POINTER(OrcFrame), f32p, i32p, f32p]
+        L.orc_codec_enc.argtypes = [C.c_int, C.c_float]
+        L.orc_codec_enc.restype = C.c_uint32
+        L.orc_codec_dec.argtypes = [C.c_int, C.c_uint32]
+        L.orc_codec_dec.restype = C.c_float
+        L.orc_codec_mav.argtypes = [C.c_float, C.c_float, C.c_uint32]
+        L.orc_codec_mav.restype = C.c_float
+        for name in ("orc_irr_packed", "orc_dep_packed"):
+            getattr(L, name).argtypes = [vp]
+            getattr(L, name).restype = u32p
+        L.orc_cage_diag.argtypes = [vp]
+        L.orc_cage_diag.restype = C.c_float
+        L.orc_blend_packed_records.argtypes = [vp, C.c_int, C.c_int, f64p, f64p, f64p, f64p]
         _lib = L
     return _lib
 
@@ -132,6 +145,28 @@ def pilot_dir(seed: int, frame: int, probe: int, octant: int) -> np.ndarray:
     out = np.zeros(3, np.float32)
     lib().orc_pilot_dir(seed, frame, probe, octant, _p(out, C.c_float))
     return out
+
+
+# packed atlas codec: which = 0 (9-bit irradiance), 1 (8-bit irradiance),
+# 2 (13-bit mean distance), 3 (13-bit mean squared distance)
+CODEC_BITS = (9, 8, 13, 13)
+
+
+def codec_enc(which: int, v: float) -> int:
+    return int(lib().orc_codec_enc(int(which), float(v)))
+
+
+def codec_dec(which: int, k: int) -> float:
+    return float(lib().orc_codec_dec(int(which), int(k)))
+
+
+def codec_table(which: int) -> np.ndarray:
+    """decoded value of every code (FP32)"""
+    return np.array([codec_dec(which, k) for k in range(1 << CODEC_BITS[which])], np.float32)
+
+
+def codec_mav(o: float, v: float, n: int) -> float:
+    return float(lib().orc_codec_mav(float(o), float(v), int(n)))
 
 
 def frame_rotation(seed: int, frame: int) -> np.ndarray:
@@ -253,7 +288,7 @@ class OracleVolume:
     """FP64 oracle volume with the same five-call shape as the C-ABI."""
 
     def __init__(self, origin, spacing, dims, n_irr=6, n_dep=14, rays_avg=64, rays_min=8, rays_max=256,
-                 hysteresis=0.97, depth_max=0.0, theta=16, threads=None):
+                 hysteresis=0.97, depth_max=0.0, theta=16, threads=None, packed=False):
         d = OrcDesc()
         d.origin[:] = [float(x) for x in origin]
         d.spacing[:] = [float(x) for x in spacing]
@@ -263,6 +298,8 @@ class OracleVolume:
         d.hyst = float(hysteresis)
         d.depth_max = float(depth_max)
         d.theta = int(theta)
+        d.packed = int(bool(packed))
+        self.packed = bool(packed)
         self.desc = d
         if threads is None:
             threads = os.cpu_count() or 1
@@ -344,6 +381,25 @@ class OracleVolume:
 
     def dep_n(self):
         return self._arr("orc_dep_n", self.P * self.Td * self.Td, np.uint8, (self.P, self.Td, self.Td))
+
+    def irr_packed(self):
+        """packed irradiance codes (R bits 0-8, G 9-17, B 18-25, N 26-31)"""
+        return self._arr("orc_irr_packed", self.P * self.Ti * self.Ti, np.uint32, (self.P, self.Ti, self.Ti))
+
+    def dep_packed(self):
+        """packed visibility codes (mean 0-12, mean square 13-25, N 26-31)"""
+        return self._arr("orc_dep_packed", self.P * self.Td * self.Td, np.uint32, (self.P, self.Td, self.Td))
+
+    @property
+    def cage_diag(self):
+        return float(lib().orc_cage_diag(self.h))
+
+    def blend_packed_records(self, p, use_pilots, pil_rad=None, pil_dep=None, m_rad=None, m_dep=None):
+        def ptr(a):
+            return None if a is None else _p(np.ascontiguousarray(a, np.float64), C.c_double)
+        keep = [None if a is None else np.ascontiguousarray(a, np.float64) for a in (pil_rad, pil_dep, m_rad, m_dep)]
+        lib().orc_blend_packed_records(self.h, int(p), int(bool(use_pilots)),
+                                       *[None if a is None else _p(a, C.c_double) for a in keep])
 
     def W(self):
         return self._arr("orc_W", self.P, np.uint32)

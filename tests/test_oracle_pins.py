@@ -630,3 +630,90 @@ def test_query_chebyshev_weight():
         ref_w.append(w)
     ref_w = np.array(ref_w)
     np.testing.assert_allclose(q, (ref_w[:, None] * vals).sum(0) / ref_w.sum(), rtol=1e-12)
+
+
+# --------------------------------------------------------------- packed atlases
+# The paper's 32-bit atlas codec (Sec. "Probe irradiance cache", "Probe
+# visibility cache", appendix "Probe compression"): u = min(ln(gamma v + 1),
+# beta) / beta, rounded down to b bits, decoded by (exp(beta u) - 1) / gamma.
+CODECS = ((9, 5.0, 15.0), (8, 5.0, 15.0), (13, 5.0, 15.0), (13, 8.0, 20.0))
+
+
+@pytest.mark.parametrize("which", range(4))
+def test_codec_closed_form_and_round_down(which):
+    bits, beta, gamma = CODECS[which]
+    kmax = (1 << bits) - 1
+    tab = O.codec_table(which).astype(np.float64)
+    k = np.arange(kmax + 1)
+    # decode: the closed form at u = k / kmax (FP32 rounding of the FP64 value)
+    np.testing.assert_array_equal(tab.astype(np.float32), ((np.exp(beta * k / kmax) - 1.0) / gamma).astype(np.float32))
+    assert tab[0] == 0.0 and (np.diff(tab) > 0).all()
+    # every code decodes and codes back to itself
+    for kk in list(range(0, kmax + 1, max(1, kmax // 300))) + [kmax]:
+        assert O.codec_enc(which, tab[kk]) == kk
+    # rounding down: dec(enc(v)) <= v < dec(enc(v) + 1), and the closed form
+    # floor(u kmax) wherever v is not within FP32 rounding of a boundary
+    rng = np.random.default_rng(3 + which)
+    vals = np.concatenate([rng.exponential(0.3, 400), rng.uniform(0, tab[-1] * 1.2, 200), [0.0, -1.0, 1e9]])
+    for v in vals.astype(np.float32):
+        q = O.codec_enc(which, float(v))
+        if v <= 0:
+            assert q == 0
+            continue
+        assert tab[q] <= v
+        assert q == kmax or v < tab[q + 1]
+        u = min(math.log(gamma * float(v) + 1.0), beta) / beta * kmax
+        if abs(u - round(u)) > 1e-4:
+            assert q == min(int(math.floor(u)), kmax)
+    assert O.codec_enc(which, float("nan")) == 0
+
+
+def test_moving_average_step_and_floor_codec_dynamics():
+    # Alg. MovingAvgUpdate: V = v/(n+1) + n o/(n+1); the first sample is taken as is
+    assert O.codec_mav(0.25, 3.0, 0) == np.float32(3.0)
+    assert O.codec_mav(2.0, 4.0, 1) == np.float32(3.0)
+    # a constant stream settles at the code just below it and never above;
+    # a dark stream then drives the code to exactly 0 (the reason the paper
+    # rounds down: round-to-nearest could stall above zero)
+    tab = O.codec_table(0)
+    code, n = 0, 0
+    for _ in range(200):
+        code = O.codec_enc(0, O.codec_mav(tab[code], 1.7, n))
+        n = min(n + 1, 63)
+        assert tab[code] <= np.float32(1.7)
+    assert code == O.codec_enc(0, 1.7) or tab[code + 1] > np.float32(1.7) * (1 - 0.02)
+    steps = 0
+    while code and steps < 5000:
+        code = O.codec_enc(0, O.codec_mav(tab[code], 0.0, 63))
+        steps += 1
+    assert code == 0 and steps < 5000
+
+
+def test_packed_constant_environment():
+    # a constant sky radiance c: every touched irradiance texel decodes to the
+    # largest code value not above c (monotone approach from below), and the
+    # miss depth to the largest code value not above depth_max / s
+    v = O.OracleVolume((0, 0, 0), (1, 1, 1), (3, 3, 3), rays_avg=16, rays_min=8, rays_max=64, packed=True)
+    v.set_scene(np.zeros((3, 3), np.float32), np.zeros((0, 3), np.int32), np.zeros((0, 3), np.float32))
+    c = np.array((0.7, 1.3, 2.9), np.float32)
+    t9, t8 = O.codec_table(0), O.codec_table(1)
+    target = [t9[O.codec_enc(0, c[0])], t9[O.codec_enc(0, c[1])], t8[O.codec_enc(1, c[2])]]
+    for f in range(40):
+        v.update(f, 1, [], sky=tuple(c))
+    pk = v.irr_packed()
+    n = pk >> 26
+    touched = n > 0
+    assert touched.any() and (n[touched] >= 1).all() and n.max() >= 8
+    dec = v.irr()[touched]
+    assert (dec <= c.astype(np.float64) + 1e-7).all()
+    # the first sample codes c exactly; later steps stay within [dec(enc(c)), c]
+    # up to one FP32 rounding below
+    for ch, tb, which in ((0, t9, 0), (1, t9, 0), (2, t8, 1)):
+        codes = (pk[touched] >> (9 * ch)) & (511 if ch < 2 else 255)
+        assert (np.abs(codes.astype(int) - O.codec_enc(which, c[ch])) <= 1).all()
+    dpk = v.dep_packed()
+    dn = dpk >> 26
+    x = np.float32(v.depth_max) / np.float32(v.cage_diag)
+    km = O.codec_enc(2, x)
+    assert (np.abs((dpk[dn > 0] & 8191).astype(int) - km) <= 1).all()
+    v.close()
