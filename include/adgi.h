@@ -73,7 +73,13 @@ typedef struct {
     float hysteresis;       /* h of the moving average, in [0, 1) (Table cacheDetails: 0.98 / 0.91) */
     float depth_max;        /* depth clamp and miss depth; <= 0 selects 1.5 * voxel diagonal */
     int32_t atlas_fp16;     /* 0: FP32 atlases; 1: half, blended in FP32, stored round-to-nearest;
-                               2: half with seeded stochastic rounding (unbiased EMA steps) */
+                               2: half with seeded stochastic rounding (unbiased EMA steps);
+                               3: the paper's packed 32-bit texels (Sec. "Probe irradiance cache",
+                               "Probe visibility cache", appendix "Probe compression"): irradiance
+                               R9 G9 B8 + 6-bit count, visibility two 13-bit moments of the distance
+                               over the cage diagonal + count, log-coded and rounded down, updated by
+                               one moving-average step per sample (Alg. MovingAvgUpdate, count capped
+                               at 63) in sample order; hysteresis is not used */
     int32_t tr_theta;       /* trigger decay length theta in frames (Fig. TrCam(a)), >= 1, <= 255 */
 } adgi_volume_desc;
 
@@ -228,10 +234,13 @@ int adgi_enable_timing(adgi_volume vol, int32_t enable);
  *   ADGI_STATE_PILOT_LUM float[P][8]     FP32 luminance of the direct light (f_r input)
  *   ADGI_STATE_MAIN_HIT int32[R][2]      as PILOT_HIT, rays in probe order
  *   ADGI_STATE_MAIN_REC float[R][4]
- *   ADGI_STATE_IRR      float[P][Ti][Ti][4] {r,g,b,count} (half[...][4] when atlas_fp16)
+ *   ADGI_STATE_IRR      float[P][Ti][Ti][4] {r,g,b,count} (half[...][4] when atlas_fp16 is
+ *                       1 or 2; uint32[P][Ti][Ti] packed texels when it is 3)
  *   ADGI_STATE_DEP      float[P][Td][Td][2] {mean, variance} of the depth samples (the
  *                       second moment is variance + mean^2); half[...][2] when atlas_fp16
- *   ADGI_STATE_DEP_N    uint8[P][Td][Td]  depth sample counts
+ *                       is 1 or 2; uint32[P][Td][Td] packed texels when it is 3
+ *   ADGI_STATE_DEP_N    uint8[P][Td][Td]  depth sample counts (unused with packed texels,
+ *                       which carry their own count)
  *   ADGI_STATE_ROT      float[9]          main-ray rotation of the last update
  *   ADGI_STATE_BVH_NODES bytes[max(T-1,1)][64]  nodes of the static part's BVH (T static
  *                       triangles; layout of adgi_build_bvh; zeros when T < 2)

@@ -526,11 +526,23 @@ class Volume:
     def main_rec(self):
         return self.state("MAIN_REC", np.float32).reshape(-1, 4)
 
+    @property
+    def packed(self):
+        return int(self.desc.atlas_fp16) == 3
+
     def irr(self):
+        """irradiance atlas as float32 {r, g, b, count}; packed volumes: the
+        raw 32-bit codes (R bits 0-8, G 9-17, B 18-25, count 26-31)"""
+        if self.packed:
+            return self.state("IRR", np.uint32).reshape(self.P, self.Ti, self.Ti)
         dt = np.float16 if self.fp16 else np.float32
         return self.state("IRR", dt).reshape(self.P, self.Ti, self.Ti, 4).astype(np.float32)
 
     def dep(self):
+        """depth atlas as float32 {mean, variance}; packed volumes: the raw
+        32-bit codes (mean bits 0-12, mean square 13-25, count 26-31)"""
+        if self.packed:
+            return self.state("DEP", np.uint32).reshape(self.P, self.Td, self.Td)
         dt = np.float16 if self.fp16 else np.float32
         return self.state("DEP", dt).reshape(self.P, self.Td, self.Td, 2).astype(np.float32)
 

@@ -88,7 +88,9 @@ struct VolConst {
     float hyst;
     int theta;
     int m0, rays_max, rays_avg;
-    int fp16;
+    int fp16;               // atlas storage: 0 FP32, 1 FP16 (RN), 2 FP16 (SR), 3 packed 32-bit codes
+    const float* ctab;      // packed code values: [512] 9-bit, [256] 8-bit, [8192] 13-bit mean, [8192] 13-bit square
+    float s_f;              // (float) cage diagonal: the packed visibility normaliser
     uint32_t R_main;        // main-ray buffer length
     int* err;               // anomaly flags (kErr*)
 };
@@ -411,9 +413,30 @@ __device__ __forceinline__ bool trace_any(const SceneDev& S, float3 o, float3 d,
 
 
 // ----------------------------------------------------------------- atlas access
-__device__ __forceinline__ float4 irr_load(const void* irr, size_t idx, int fp16)
+// Packed texels (the paper's 32-bit codecs): irradiance R bits 0-8, G 9-17,
+// B 18-25, count 26-31; visibility mean bits 0-12, mean square 13-25, count
+// 26-31, both in units of the cage diagonal s.  A code stands for the value
+// of its table entry.
+constexpr int kCt9 = 0, kCt8 = 512, kCtM = 768, kCtQ = 768 + 8192, kCtSize = 768 + 2 * 8192;
+
+__device__ __forceinline__ float4 irr_unpack(const float* __restrict__ ct, uint32_t c)
 {
-    if (fp16) {
+    return make_float4(__ldg(ct + kCt9 + (c & 511u)), __ldg(ct + kCt9 + ((c >> 9) & 511u)),
+                       __ldg(ct + kCt8 + ((c >> 18) & 255u)), (float)(c >> 26));
+}
+
+// {mean, variance} in world units from a packed visibility texel
+__device__ __forceinline__ float2 dep_unpack(const float* __restrict__ ct, float s, uint32_t c)
+{
+    const float m = __ldg(ct + kCtM + (c & 8191u)) * s;
+    const float q = __ldg(ct + kCtQ + ((c >> 13) & 8191u)) * (s * s);
+    return make_float2(m, fmaxf(q - m * m, 0.0f));
+}
+
+__device__ __forceinline__ float4 irr_load(const VolConst& V, const void* irr, size_t idx)
+{
+    if (V.fp16 == 3) return irr_unpack(V.ctab, reinterpret_cast<const uint32_t*>(irr)[idx]);
+    if (V.fp16) {
         const __half2* h = reinterpret_cast<const __half2*>(irr) + 2 * idx;
         float2 a = __half22float2(h[0]), b = __half22float2(h[1]);
         return make_float4(a.x, a.y, b.x, b.y);
@@ -421,16 +444,18 @@ __device__ __forceinline__ float4 irr_load(const void* irr, size_t idx, int fp16
     return reinterpret_cast<const float4*>(irr)[idx];
 }
 
-__device__ __forceinline__ float2 dep_load(const void* dep, size_t idx, int fp16)
+// depth texel as {mean, variance}
+__device__ __forceinline__ float2 dep_load(const VolConst& V, const void* dep, size_t idx)
 {
-    if (fp16) return __half22float2(reinterpret_cast<const __half2*>(dep)[idx]);
+    if (V.fp16 == 3) return dep_unpack(V.ctab, V.s_f, reinterpret_cast<const uint32_t*>(dep)[idx]);
+    if (V.fp16) return __half22float2(reinterpret_cast<const __half2*>(dep)[idx]);
     return reinterpret_cast<const float2*>(dep)[idx];
 }
 
 // bilinear sample of a padded tile at direction w (octahedral coordinates)
 template <int CH>
-__device__ __forceinline__ void tile_bilinear(const void* base, size_t tile_off, int T, int n, float2 p, int fp16,
-                                              float* out)
+__device__ __forceinline__ void tile_bilinear(const VolConst& V, const void* base, size_t tile_off, int T, int n,
+                                              float2 p, float* out)
 {
     float fx = (1.0f + (p.x + 1.0f) * 0.5f * (float)n) - 0.5f;
     float fy = (1.0f + (p.y + 1.0f) * 0.5f * (float)n) - 0.5f;
@@ -440,14 +465,14 @@ __device__ __forceinline__ void tile_bilinear(const void* base, size_t tile_off,
     float ay = fminf(fmaxf(fy - (float)y0, 0.0f), 1.0f);
     size_t i00 = tile_off + (size_t)(y0 * T + x0);
     if (CH == 3) {
-        float4 v00 = irr_load(base, i00, fp16), v01 = irr_load(base, i00 + 1, fp16);
-        float4 v10 = irr_load(base, i00 + T, fp16), v11 = irr_load(base, i00 + T + 1, fp16);
+        float4 v00 = irr_load(V, base, i00), v01 = irr_load(V, base, i00 + 1);
+        float4 v10 = irr_load(V, base, i00 + T), v11 = irr_load(V, base, i00 + T + 1);
         out[0] = (1.0f - ay) * ((1.0f - ax) * v00.x + ax * v01.x) + ay * ((1.0f - ax) * v10.x + ax * v11.x);
         out[1] = (1.0f - ay) * ((1.0f - ax) * v00.y + ax * v01.y) + ay * ((1.0f - ax) * v10.y + ax * v11.y);
         out[2] = (1.0f - ay) * ((1.0f - ax) * v00.z + ax * v01.z) + ay * ((1.0f - ax) * v10.z + ax * v11.z);
     } else {
-        float2 v00 = dep_load(base, i00, fp16), v01 = dep_load(base, i00 + 1, fp16);
-        float2 v10 = dep_load(base, i00 + T, fp16), v11 = dep_load(base, i00 + T + 1, fp16);
+        float2 v00 = dep_load(V, base, i00), v01 = dep_load(V, base, i00 + 1);
+        float2 v10 = dep_load(V, base, i00 + T), v11 = dep_load(V, base, i00 + T + 1);
         out[0] = (1.0f - ay) * ((1.0f - ax) * v00.x + ax * v01.x) + ay * ((1.0f - ax) * v10.x + ax * v11.x);
         out[1] = (1.0f - ay) * ((1.0f - ax) * v00.y + ax * v01.y) + ay * ((1.0f - ax) * v10.y + ax * v11.y);
     }
@@ -508,8 +533,8 @@ __device__ __forceinline__ void depth_moments(const VolConst& V, const void* dep
     float ax = fminf(fmaxf(fx - (float)x0, 0.0f), 1.0f);
     float ay = fminf(fmaxf(fy - (float)y0, 0.0f), 1.0f);
     size_t i00 = tile + (size_t)(y0 * T + x0);
-    float2 v00 = dep_load(dep, i00, V.fp16), v01 = dep_load(dep, i00 + 1, V.fp16);
-    float2 v10 = dep_load(dep, i00 + T, V.fp16), v11 = dep_load(dep, i00 + T + 1, V.fp16);
+    float2 v00 = dep_load(V, dep, i00), v01 = dep_load(V, dep, i00 + 1);
+    float2 v10 = dep_load(V, dep, i00 + T), v11 = dep_load(V, dep, i00 + T + 1);
     float w00 = (1.f - ax) * (1.f - ay), w01 = ax * (1.f - ay), w10 = (1.f - ax) * ay, w11 = ax * ay;
     filter_moments(w00, w01, w10, w11, v00, v01, v10, v11, mom);
     // conditioning of the filtered variance against the fractions: what a
@@ -600,8 +625,8 @@ static __device__ __noinline__ void depth_moments_precise(const VolConst& V, con
     float bx = fminf(fmaxf(fs(fs((float)(x0 + 1), fx.h), fx.l), 0.0f), 1.0f);
     float by = fminf(fmaxf(fs(fs((float)(y0 + 1), fy.h), fy.l), 0.0f), 1.0f);
     size_t i00 = tile + (size_t)(y0 * T + x0);
-    float2 v00 = dep_load(dep, i00, V.fp16), v01 = dep_load(dep, i00 + 1, V.fp16);
-    float2 v10 = dep_load(dep, i00 + T, V.fp16), v11 = dep_load(dep, i00 + T + 1, V.fp16);
+    float2 v00 = dep_load(V, dep, i00), v01 = dep_load(V, dep, i00 + 1);
+    float2 v10 = dep_load(V, dep, i00 + T), v11 = dep_load(V, dep, i00 + T + 1);
     float w00 = bx * by, w01 = ax * by, w10 = bx * ay, w11 = ax * ay;
     filter_moments(w00, w01, w10, w11, v00, v01, v10, v11, mom);
 }
@@ -667,7 +692,7 @@ __device__ __forceinline__ float3 query_irr_at(const VolConst& V, const void* ir
             wc = var / (var + dd * dd);
         }
         float E[3];
-        tile_bilinear<3>(irr, (size_t)p * ti2, V.Ti, V.n_irr, pn, V.fp16, E);
+        tile_bilinear<3>(V, irr, (size_t)p * ti2, V.Ti, V.n_irr, pn, E);
         float w = wt * wc;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {

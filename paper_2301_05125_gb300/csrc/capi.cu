@@ -22,6 +22,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <tuple>
 
 namespace adgi {
 size_t blend_smem_bytes(const VolConst& V);
@@ -162,6 +163,7 @@ struct adgi_volume_s {
     float4* sf = nullptr;
     void* plan = nullptr;  // per-frame blend plan (BlendPlan)
     uint16_t* tex_src = nullptr;  // per texel: itself, or a border texel's octahedral fold partner
+    float* ctab = nullptr;        // values of the packed atlas codes
     uint16_t* lut_v = nullptr;
     uint16_t* lut_c = nullptr;
     // atlases
@@ -238,7 +240,7 @@ namespace {
 void free_volume(adgi_volume v)
 {
     if (!v) return;
-    void* ptrs[] = {v->sf,      v->plan,    v->tex_src, v->lut_v,   v->lut_c,  v->irr,   v->dep,     v->dep_n,   v->qv,     v->qr,
+    void* ptrs[] = {v->sf,      v->plan,    v->tex_src, v->ctab,    v->lut_v,   v->lut_c,  v->irr,   v->dep,     v->dep_n,   v->qv,     v->qr,
                     v->qv_even, v->qr_even, v->amp_v,  v->amp_r, v->trv,     v->trr,     v->age_v,  v->age_r,
                     v->G,       v->W,       v->n,      v->off,   v->pil_hit, v->pil_rec, v->pil_lum, v->m_hit,
                     v->m_rec,   v->shadow_ctr, v->verts, v->idx, v->albedo,  v->q_buf, v->err,
@@ -286,7 +288,7 @@ int validate_desc(const adgi_volume_desc* d)
         return fail(ADGI_ERR_INVALID_ARG, "need max(rays_min, 8) <= rays_avg <= rays_max <= 4096");
     if (!(d->hysteresis >= 0.0f && d->hysteresis < 1.0f)) return fail(ADGI_ERR_INVALID_ARG, "hysteresis in [0,1)");
     if (d->tr_theta < 1 || d->tr_theta > 255) return fail(ADGI_ERR_INVALID_ARG, "tr_theta in [1,255]");
-    if (d->atlas_fp16 < 0 || d->atlas_fp16 > 2) return fail(ADGI_ERR_INVALID_ARG, "atlas_fp16 in {0,1,2}");
+    if (d->atlas_fp16 < 0 || d->atlas_fp16 > 3) return fail(ADGI_ERR_INVALID_ARG, "atlas_fp16 in {0,1,2,3}");
     int64_t P = (int64_t)d->dims[0] * d->dims[1] * d->dims[2];
     if (P * (int64_t)d->rays_avg >= (int64_t)1 << 31) return fail(ADGI_ERR_INVALID_ARG, "ray budget too large");
     return ADGI_OK;
@@ -348,7 +350,7 @@ int adgi_create_volume(const adgi_volume_desc* desc, void* cuda_stream, adgi_vol
     V.m0 = d.rays_min > 8 ? d.rays_min : 8;
     V.rays_max = d.rays_max;
     V.rays_avg = d.rays_avg;
-    V.fp16 = d.atlas_fp16 == 2 ? 2 : (d.atlas_fp16 ? 1 : 0);
+    V.fp16 = d.atlas_fp16;
     const size_t P = (size_t)V.P;
     v->R_main = (uint32_t)((size_t)(d.rays_avg - 8) * P);
     size_t& B = v->bytes;
@@ -372,6 +374,20 @@ int adgi_create_volume(const adgi_volume_desc* desc, void* cuda_stream, adgi_vol
         v->plan = pb;
     }
     DA(v->tex_src, (size_t)V.Ti * V.Ti + (size_t)V.Td * V.Td);
+    // packed atlas codes (the paper's codecs): code k of a b-bit channel with
+    // parameters (beta, gamma) stands for (exp(beta k / (2^b - 1)) - 1) / gamma,
+    // computed in FP64 and rounded to FP32: 9-bit and 8-bit irradiance (5, 15),
+    // 13-bit mean distance (5, 15) and mean squared distance (8, 20)
+    std::vector<float> ctab;
+    for (auto cf : {std::make_tuple(9, 5.0, 15.0), std::make_tuple(8, 5.0, 15.0), std::make_tuple(13, 5.0, 15.0),
+                    std::make_tuple(13, 8.0, 20.0)}) {
+        const int bits = std::get<0>(cf);
+        const double beta = std::get<1>(cf), gamma = std::get<2>(cf), kmax = (double)((1 << bits) - 1);
+        for (int k = 0; k < (1 << bits); ++k) ctab.push_back((float)((std::exp(beta * (double)k / kmax) - 1.0) / gamma));
+    }
+    DA(v->ctab, ctab.size());
+    V.ctab = v->ctab;
+    V.s_f = (float)v->s;
     std::vector<uint16_t> tsrc;
     for (int n : {V.n_irr, V.n_dep}) {  // octahedral border fold of a tile with n x n interior
         const int T = n + 2;
@@ -401,7 +417,7 @@ int adgi_create_volume(const adgi_volume_desc* desc, void* cuda_stream, adgi_vol
     }
     // atlases
     size_t ti2 = (size_t)V.Ti * V.Ti, td2 = (size_t)V.Td * V.Td;
-    size_t irr_bytes = P * ti2 * (V.fp16 ? 8 : 16), dep_bytes = P * td2 * (V.fp16 ? 4 : 8);
+    size_t irr_bytes = P * ti2 * (V.fp16 == 3 ? 4 : V.fp16 ? 8 : 16), dep_bytes = P * td2 * (V.fp16 ? 4 : 8);
     {
         uint8_t* a;
         DA(a, irr_bytes);
@@ -448,6 +464,7 @@ int adgi_create_volume(const adgi_volume_desc* desc, void* cuda_stream, adgi_vol
     } while (0)
     CKV(cudaMemcpyAsync(v->sf, sf.data(), sizeof(float4) * sf.size(), cudaMemcpyHostToDevice, s));
     CKV(cudaMemcpyAsync(v->tex_src, tsrc.data(), sizeof(uint16_t) * tsrc.size(), cudaMemcpyHostToDevice, s));
+    CKV(cudaMemcpyAsync(v->ctab, ctab.data(), sizeof(float) * ctab.size(), cudaMemcpyHostToDevice, s));
     CKV(cudaMemcpyAsync(v->lut_v, lv.data(), 2 * 4096, cudaMemcpyHostToDevice, s));
     CKV(cudaMemcpyAsync(v->lut_c, lc.data(), 2 * 4096, cudaMemcpyHostToDevice, s));
     CKV(cudaMemsetAsync(v->irr, 0, irr_bytes, s));
@@ -1180,7 +1197,7 @@ int adgi_state_bytes(adgi_volume v, int32_t which, uint64_t* bytes)
     case ADGI_STATE_PILOT_LUM: *bytes = 4 * 8 * P; break;
     case ADGI_STATE_MAIN_HIT: *bytes = 8 * R; break;
     case ADGI_STATE_MAIN_REC: *bytes = 16 * R; break;
-    case ADGI_STATE_IRR: *bytes = P * ti2 * (v->V.fp16 ? 8 : 16); break;
+    case ADGI_STATE_IRR: *bytes = P * ti2 * (v->V.fp16 == 3 ? 4 : v->V.fp16 ? 8 : 16); break;
     case ADGI_STATE_DEP: *bytes = P * td2 * (v->V.fp16 ? 4 : 8); break;
     case ADGI_STATE_DEP_N: *bytes = P * td2; break;
     case ADGI_STATE_ROT: *bytes = 36; break;

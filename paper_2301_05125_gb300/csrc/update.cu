@@ -427,6 +427,129 @@ __device__ __forceinline__ void prefetch_l2(const void* src, uint32_t bytes)
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
 }
 
+// ---- packed atlases (the paper's 32-bit codecs): one moving-average step
+// per sample (Alg. MovingAvgUpdate, serialised in sample order as the CAS
+// loop of Alg. atmMvAvgUpd would), each followed by coding the value again.
+constexpr uint32_t kPackNmax = 63u;  // 6-bit sample count
+
+// code of v >= 0: the largest k with tab[k] <= v (tab increasing, tab[0] = 0).
+// The log estimate only seeds the search; the thresholds decide.
+__device__ __forceinline__ uint32_t code_of(const float* __restrict__ tab, int kmax, float beta, float gamma, float v)
+{
+    if (!(v > 0.0f)) return 0u;
+    const float u = fminf(__logf(fmaf(gamma, v, 1.0f)), beta) * ((float)kmax / beta);
+    int k = (int)fminf(fmaxf(u, 0.0f), (float)kmax);
+    for (int it = 0; it < 3 && k > 0 && __ldg(tab + k) > v; ++it) --k;
+    for (int it = 0; it < 3 && k < kmax && __ldg(tab + k + 1) <= v; ++it) ++k;
+    if (__ldg(tab + k) > v || (k < kmax && __ldg(tab + k + 1) <= v)) {  // not bracketed yet: bisect
+        int lo = 0, hi = kmax;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (__ldg(tab + mid) <= v)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        k = lo;
+    }
+    return (uint32_t)k;
+}
+
+// V = v/(n+1) + (n o)/(n+1), FP32, in this order
+__device__ __forceinline__ float mav_step(float o, float v, uint32_t n)
+{
+    const float n1 = (float)(n + 1u);
+    return fa(fd(v, n1), fd(fm((float)n, o), n1));
+}
+
+struct PkIrr {
+    uint32_t k0, k1, k2, n;
+    float o0, o1, o2;
+    __device__ __forceinline__ void load(const float* ct, uint32_t c)
+    {
+        k0 = c & 511u, k1 = (c >> 9) & 511u, k2 = (c >> 18) & 255u, n = c >> 26;
+        o0 = __ldg(ct + kCt9 + k0), o1 = __ldg(ct + kCt9 + k1), o2 = __ldg(ct + kCt8 + k2);
+    }
+    __device__ __forceinline__ void add(const float* ct, float r, float g, float b)
+    {
+        k0 = code_of(ct + kCt9, 511, 5.0f, 15.0f, mav_step(o0, r, n));
+        k1 = code_of(ct + kCt9, 511, 5.0f, 15.0f, mav_step(o1, g, n));
+        k2 = code_of(ct + kCt8, 255, 5.0f, 15.0f, mav_step(o2, b, n));
+        o0 = __ldg(ct + kCt9 + k0), o1 = __ldg(ct + kCt9 + k1), o2 = __ldg(ct + kCt8 + k2);
+        n = min(n + 1u, kPackNmax);
+    }
+    __device__ __forceinline__ uint32_t code() const { return k0 | (k1 << 9) | (k2 << 18) | (n << 26); }
+};
+
+struct PkDep {
+    uint32_t km, kq, n;
+    float om, oq;
+    __device__ __forceinline__ void load(const float* ct, uint32_t c)
+    {
+        km = c & 8191u, kq = (c >> 13) & 8191u, n = c >> 26;
+        om = __ldg(ct + kCtM + km), oq = __ldg(ct + kCtQ + kq);
+    }
+    __device__ __forceinline__ void add(const float* ct, float x)  // x: distance / cage diagonal
+    {
+        km = code_of(ct + kCtM, 8191, 5.0f, 15.0f, mav_step(om, x, n));
+        kq = code_of(ct + kCtQ, 8191, 8.0f, 20.0f, mav_step(oq, fm(x, x), n));
+        om = __ldg(ct + kCtM + km), oq = __ldg(ct + kCtQ + kq);
+        n = min(n + 1u, kPackNmax);
+    }
+    __device__ __forceinline__ uint32_t code() const { return km | (kq << 13) | (n << 26); }
+};
+
+// One warp, one probe tile, packed atlases: each lane takes whole texels and
+// applies their samples in sample order (pilots, then the plan bucket in SF
+// index order); then the border fold and coalesced stores of the codes.
+__device__ __forceinline__ void blend_packed(const VolConst& V, const BlendBufs& B, int p, uint32_t m, int npil,
+                                             const float4* __restrict__ mrec, const float4* prs, const int* pk_i,
+                                             const int* pk_d, const uint16_t* __restrict__ ord_i,
+                                             const uint16_t* __restrict__ ord_d, const uint16_t* __restrict__ beg_i,
+                                             const uint16_t* __restrict__ beg_d, uint32_t* irr_new, uint32_t* dep_new,
+                                             int lane)
+{
+    const int Ti = V.Ti, Td = V.Td, ni = V.n_irr, nd = V.n_dep;
+    const int ti2 = Ti * Ti, td2 = Td * Td;
+    const float* ct = V.ctab;
+    const uint32_t* girr = reinterpret_cast<const uint32_t*>(B.irr) + (size_t)p * ti2;
+    const uint32_t* gdep = reinterpret_cast<const uint32_t*>(B.dep) + (size_t)p * td2;
+    const float rni = 1.0f / (float)ni, rnd = 1.0f / (float)nd;
+    for (int q = lane; q < ni * ni; q += 32) {
+        const int r = (int)(((float)q + 0.5f) * rni), t = (r + 1) * Ti + (q - r * ni) + 1;
+        PkIrr x;
+        x.load(ct, __ldg(girr + t));
+        for (int o = 0; o < npil; ++o)
+            if (pk_i[o] == t) x.add(ct, prs[o].x, prs[o].y, prs[o].z);
+        if (m) {
+            const uint32_t b1 = __ldg(beg_i + t + 1);
+            for (uint32_t u = __ldg(beg_i + t); u < b1; ++u) {
+                const float4 rc = __ldg(mrec + min((uint32_t)__ldg(ord_i + u), m - 1));
+                x.add(ct, rc.x, rc.y, rc.z);
+            }
+        }
+        irr_new[t] = x.code();
+    }
+    for (int q = lane; q < nd * nd; q += 32) {
+        const int r = (int)(((float)q + 0.5f) * rnd), t = (r + 1) * Td + (q - r * nd) + 1;
+        PkDep x;
+        x.load(ct, __ldg(gdep + t));
+        for (int o = 0; o < npil; ++o)
+            if (pk_d[o] == t) x.add(ct, fd(prs[o].w, V.s_f));
+        if (m) {
+            const uint32_t b1 = __ldg(beg_d + t + 1);
+            for (uint32_t u = __ldg(beg_d + t); u < b1; ++u)
+                x.add(ct, fd(__ldg(&mrec[min((uint32_t)__ldg(ord_d + u), m - 1)].w), V.s_f));
+        }
+        dep_new[t] = x.code();
+    }
+    __syncwarp();
+    uint32_t* oirr = reinterpret_cast<uint32_t*>(B.irr) + (size_t)p * ti2;
+    uint32_t* odep = reinterpret_cast<uint32_t*>(B.dep) + (size_t)p * td2;
+    for (int t = lane; t < ti2; t += 32) oirr[t] = irr_new[__ldg(B.src + t)];
+    for (int t = lane; t < td2; t += 32) odep[t] = dep_new[__ldg(B.src + ti2 + t)];
+}
+
 __global__ void __launch_bounds__(128) k_blend(VolConst V, const FrameDev* __restrict__ FD, BlendBufs B)
 {
     const FrameConst& F = FD->F;
@@ -456,10 +579,11 @@ __global__ void __launch_bounds__(128) k_blend(VolConst V, const FrameDev* __res
     const float4* mrec = B.main_rec + base;
     if (lane == 0) {  // L2 prefetch of the records and the old tiles, gathered below
         if (m) prefetch_l2(mrec, 16u * m);
-        const uint32_t irr_b = (uint32_t)ti2 * (V.fp16 ? 8u : 16u), dep_b = (uint32_t)td2 * (V.fp16 ? 4u : 8u);
+        const uint32_t irr_b = (uint32_t)ti2 * (V.fp16 == 3 ? 4u : V.fp16 ? 8u : 16u);
+        const uint32_t dep_b = (uint32_t)td2 * (V.fp16 == 3 ? 4u : V.fp16 ? 4u : 8u);
         if ((irr_b % 16u) == 0u) prefetch_l2(reinterpret_cast<const unsigned char*>(B.irr) + (size_t)p * irr_b, irr_b);
         if ((dep_b % 16u) == 0u) prefetch_l2(reinterpret_cast<const unsigned char*>(B.dep) + (size_t)p * dep_b, dep_b);
-        if ((td2 % 16) == 0) prefetch_l2(B.dep_n + dof, (uint32_t)td2);
+        if (V.fp16 != 3 && (td2 % 16) == 0) prefetch_l2(B.dep_n + dof, (uint32_t)td2);
     }
     // pilot samples: records and bins (pilots come first in every texel's sum)
     if (npil && lane < kPilots) {
@@ -473,6 +597,11 @@ __global__ void __launch_bounds__(128) k_blend(VolConst V, const FrameDev* __res
     const uint16_t* beg_i = B.plan.beg_i + (size_t)(m ? m - 1 : 0) * (ti2 + 1);
     const uint16_t* beg_d = B.plan.beg_d + (size_t)(m ? m - 1 : 0) * (td2 + 1);
     __syncwarp();
+    if (V.fp16 == 3) {
+        blend_packed(V, B, p, m, npil, mrec, prs, pk_i, pk_d, ord_i, ord_d, beg_i, beg_d,
+                     reinterpret_cast<uint32_t*>(irr_new), reinterpret_cast<uint32_t*>(dep_new), lane);
+        return;
+    }
     // each lane sums whole texels: the pilots of the texel in pilot order,
     // then the texel's bucket of the plan in SF index order (the sample
     // order), and blends the texel
@@ -490,7 +619,7 @@ __global__ void __launch_bounds__(128) k_blend(VolConst V, const FrameDev* __res
                 sz += x.z;
                 ++k;
             }
-        float4 v = irr_load(B.irr, io + t, V.fp16);  // issued early: independent of the sums
+        float4 v = irr_load(V, B.irr, io + t);  // issued early: independent of the sums
         if (m) {
             const uint32_t b0 = __ldg(beg_i + t), b1 = __ldg(beg_i + t + 1);
             uint32_t u = b0;
@@ -538,7 +667,7 @@ __global__ void __launch_bounds__(128) k_blend(VolConst V, const FrameDev* __res
                 s2 += x * x;
                 ++k;
             }
-        float2 v = dep_load(B.dep, dof + t, V.fp16);  // issued early: independent of the sums
+        float2 v = dep_load(V, B.dep, dof + t);  // issued early: independent of the sums
         uint32_t c = B.dep_n[dof + t];
         if (m) {
             const uint32_t b0 = __ldg(beg_d + t), b1 = __ldg(beg_d + t + 1);
