@@ -890,6 +890,11 @@ static uint32_t pk_dep_update(uint32_t code, float x)
     return km | (kq << 13) | (nn << 26);
 }
 
+/* Metropolis chain steps per frame, rejected initial steps, samples per chain */
+#define MH_M 8
+#define MH_K 2
+#define MH_S (MH_M - MH_K - 1)
+
 /* ------------------------------------------------------------------------ */
 /* Volume state                                                              */
 /* ------------------------------------------------------------------------ */
@@ -902,6 +907,8 @@ typedef struct {
     float depth_max;      /* depth clamp; <= 0 selects 1.5 * voxel diagonal */
     int theta;            /* temporal trigger decay length (frames) */
     int packed;           /* 1: 32-bit packed atlases (the paper's codecs) */
+    int sampler;          /* 0: deterministic allocation; 1: Metropolis chains (static guide) */
+    float alpha;          /* confidence alpha in the cache term of the guide (Eq. DDGIBays) */
 } orc_desc;
 
 typedef struct {
@@ -966,6 +973,22 @@ typedef struct orc_vol {
     double* m_dep;
     float R[9];
     int nthreads;
+    /* Metropolis sampler (desc.sampler = 1) */
+    size_t B;            /* samples per frame: (avg - 8) * P */
+    size_t C;            /* chains: ceil(B / samples per chain) */
+    int chains_live;     /* chain states initialised */
+    float* ch_g;         /* C*3 grid coordinates */
+    float* ch_u;         /* C*2 octahedral coordinates */
+    int* smp_p;          /* B probe of each sample */
+    float* smp_dir;      /* B*3 direction */
+    float* smp_t;        /* B nearest hit along +w (inf on a miss) */
+    int* smp_tri;
+    float* smp_tn;       /* B nearest hit along -w */
+    int* smp_trin;
+    double* smp_rad;     /* B*3 radiance along +w */
+    double* smp_dep;     /* B distance along -w (clamped) */
+    uint32_t* smp_off;   /* P+1 first sample of each probe in smp_ord */
+    uint32_t* smp_ord;   /* B sample indices grouped by probe, in sample order */
 } orc_vol;
 
 static void build_luts(orc_vol* v)
@@ -991,6 +1014,8 @@ EXPORT void orc_luts(double s, uint16_t* lut_v, uint16_t* lut_c)
     memcpy(lut_v, tmp.lut_v, sizeof(tmp.lut_v));
     memcpy(lut_c, tmp.lut_c, sizeof(tmp.lut_c));
 }
+
+EXPORT void orc_destroy(orc_vol* v);
 
 EXPORT orc_vol* orc_create(const orc_desc* d, int nthreads)
 {
@@ -1055,6 +1080,26 @@ EXPORT orc_vol* orc_create(const orc_desc* d, int nthreads)
     v->m_rad = (double*)calloc((v->R_main + 1) * 3, 8);
     v->m_dep = (double*)calloc(v->R_main + 1, 8);
     v->nthreads = nthreads > 0 ? nthreads : 1;
+    if (d->sampler == 1) {
+        if (d->packed) { /* the Metropolis mode blends with the batched moving average only */
+            orc_destroy(v);
+            return NULL;
+        }
+        v->B = v->R_main;
+        v->C = (v->B + MH_S - 1) / MH_S;
+        v->ch_g = (float*)calloc(v->C * 3 + 1, 4);
+        v->ch_u = (float*)calloc(v->C * 2 + 1, 4);
+        v->smp_p = (int*)calloc(v->B + 1, 4);
+        v->smp_dir = (float*)calloc(v->B * 3 + 1, 4);
+        v->smp_t = (float*)calloc(v->B + 1, 4);
+        v->smp_tri = (int*)calloc(v->B + 1, 4);
+        v->smp_tn = (float*)calloc(v->B + 1, 4);
+        v->smp_trin = (int*)calloc(v->B + 1, 4);
+        v->smp_rad = (double*)calloc(v->B * 3 + 1, 8);
+        v->smp_dep = (double*)calloc(v->B + 1, 8);
+        v->smp_off = (uint32_t*)calloc(P + 1, 4);
+        v->smp_ord = (uint32_t*)calloc(v->B + 1, 4);
+    }
     return v;
 }
 
@@ -1072,6 +1117,18 @@ EXPORT void orc_destroy(orc_vol* v)
     free(v->dep_n);
     free(v->irr_pk);
     free(v->dep_pk);
+    free(v->ch_g);
+    free(v->ch_u);
+    free(v->smp_p);
+    free(v->smp_dir);
+    free(v->smp_t);
+    free(v->smp_tri);
+    free(v->smp_tn);
+    free(v->smp_trin);
+    free(v->smp_rad);
+    free(v->smp_dep);
+    free(v->smp_off);
+    free(v->smp_ord);
     free(v->qv_even);
     free(v->qr_even);
     free(v->trv);
@@ -1688,6 +1745,345 @@ typedef struct {
     int t0, t1;
 } job;
 
+/* ------------------------------------------------------------------------ */
+/* Metropolis sampling of the adaptive rays (desc.sampler = 1).              */
+/*   Guide (Eq. DDGIBays with the static heuristic of Sec. "Adaptive        */
+/*   sampling - static"): h(x) = exp(min(alpha g(x) / f_s(x), 1)) f_s(x),    */
+/*   f_s = f_c f_v = q_c q_v / 1023^2 (the 10-bit heuristics of the probe   */
+/*   and octant of x), g = Rec. 709 luminance of the irradiance texel of x   */
+/*   in the previous frame's atlas; h = 0 where f_s = 0.                     */
+/*   State x = (grid coordinates g in [0, dims-1]^3, octahedral coordinates */
+/*   u in [-1,1]^2); its probe is the nearest grid point, its direction the */
+/*   decoded u.  Chains persist across frames (Alg. MarkovChainMT): each     */
+/*   frame a chain re-evaluates h at its state and takes M = 8 random-walk  */
+/*   steps (Alg. MetropolisStep): Gaussian proposal (sigma 0.5 probe        */
+/*   spacings in position, sqrt(pi/256) in u), reflected into the domain;   */
+/*   accept when eps <= min(h'/h, 1) (always when h = 0); the states after  */
+/*   steps K+1..M-1 (K = 2) are the frame's samples.                         */
+/*   Each sample traces its direction w for the irradiance texel at w and   */
+/*   the opposite direction -w for the visibility texel at -w (the extra   */
+/*   ray of Sec. "Adaptive sampling - static").                             */
+/*   Random numbers: SplitMix64 counters; N(0,1) by a 4096-entry quantile   */
+/*   table (Phi^-1((i+0.5)/4096), FP64 bisection on erfc, rounded to FP32)  */
+/*   indexed by 12 random bits; exp(r), r in [0,1], by a 1024-entry table   */
+/*   at r = floor(1023 r)/1023.  Every decision is FP32 with these tables,  */
+/*   so two correct implementations agree bit for bit when alpha = 0.       */
+/* ------------------------------------------------------------------------ */
+static float g_nq[4096], g_ex[1024];
+static pthread_once_t g_mh_once = PTHREAD_ONCE_INIT;
+static void mh_tables_init(void)
+{
+    for (int i = 0; i < 4096; ++i) {
+        double pr = ((double)i + 0.5) / 4096.0, lo = -10.0, hi = 10.0;
+        for (int it = 0; it < 200; ++it) { /* Phi(x) = erfc(-x / sqrt 2) / 2 */
+            double mid = 0.5 * (lo + hi);
+            if (0.5 * erfc(-mid / sqrt(2.0)) < pr)
+                lo = mid;
+            else
+                hi = mid;
+        }
+        g_nq[i] = (float)(0.5 * (lo + hi));
+    }
+    for (int k = 0; k < 1024; ++k) g_ex[k] = (float)exp((double)k / 1023.0);
+}
+EXPORT float orc_mh_normal_quantile(int i)
+{
+    pthread_once(&g_mh_once, mh_tables_init);
+    return g_nq[i & 4095];
+}
+EXPORT float orc_mh_exp(int k)
+{
+    pthread_once(&g_mh_once, mh_tables_init);
+    return g_ex[k & 1023];
+}
+
+static uint64_t mh_bits(uint64_t seed, uint64_t frame, uint64_t chain, uint64_t step, uint64_t comp)
+{
+    return hash3(seed ^ 0x4D4554524FULL, frame, (chain * (MH_M + 1) + step) * 8u + comp);
+}
+static float mh_uniform(uint64_t r) { return (float)(uint32_t)(r >> 40) * 5.9604644775390625e-08f; }
+static float mh_normal(uint64_t r) { return g_nq[r >> 52]; }
+
+/* reflect x into [lo, hi] (symmetric proposal), then clamp */
+static float mh_reflect(float x, float lo, float hi)
+{
+    if (x < lo) x = lo + (lo - x);
+    if (x > hi) x = hi - (x - hi);
+    if (x < lo) x = lo;
+    if (x > hi) x = hi;
+    return x;
+}
+
+static int mh_probe(const orc_vol* v, const float g[3])
+{
+    int q[3];
+    for (int k = 0; k < 3; ++k) {
+        int i = (int)floorf(g[k] + 0.5f);
+        if (i < 0) i = 0;
+        if (i > v->d.dims[k] - 1) i = v->d.dims[k] - 1;
+        q[k] = i;
+    }
+    return q[0] + v->d.dims[0] * (q[1] + v->d.dims[1] * q[2]);
+}
+
+/* direction of octahedral coordinates u (FP32, unit length) */
+static void mh_dir(const float u[2], float w[3])
+{
+    float x = u[0], y = u[1];
+    float z = (1.0f - fabsf(x)) - fabsf(y);
+    if (z < 0.0f) {
+        float nx = (1.0f - fabsf(y)) * sgn_f(x);
+        float ny = (1.0f - fabsf(x)) * sgn_f(y);
+        x = nx;
+        y = ny;
+    }
+    float l = sqrtf((x * x + y * y) + z * z);
+    w[0] = x / l;
+    w[1] = y / l;
+    w[2] = z / l;
+}
+
+/* h(x) under this frame's guide */
+static float mh_guide(const orc_vol* v, const orc_frame* fr, const float g[3], const float u[2])
+{
+    int p = mh_probe(v, g);
+    float w[3];
+    mh_dir(u, w);
+    int o = (w[0] < 0.0f ? 1 : 0) | (w[1] < 0.0f ? 2 : 0) | (w[2] < 0.0f ? 4 : 0);
+    uint32_t qc = qc_of(v, fr, p), qv = v->qv[(size_t)p * 8 + (size_t)o];
+    float fs = (float)(qc * qv) * (1.0f / 1046529.0f); /* q_c q_v / 1023^2 */
+    if (!(fs > 0.0f)) return 0.0f;
+    int t = orc_texel_of_dir(w, v->d.n_irr);
+    const double* e = v->irr + ((size_t)p * v->Ti * v->Ti + (size_t)t) * 3;
+    float gl = (LUM_R * (float)e[0] + LUM_G * (float)e[1]) + LUM_B * (float)e[2];
+    float r = (v->d.alpha * gl) / fs;
+    if (!(r < 1.0f)) r = 1.0f;
+    if (r < 0.0f) r = 0.0f;
+    int k = (int)floorf(r * 1023.0f);
+    return g_ex[k] * fs;
+}
+
+/* M random-walk steps (Alg. MetropolisStep) of a chain in state (g, u) of a
+   dims grid, under guide(ctx, g, u); the states after steps K+1..M-1 are
+   written to samples (probe, direction) from index first (up to limit). */
+typedef float (*mh_guide_fn)(const void* ctx, const float g[3], const float u[2]);
+static void mh_walk(const int dims[3], uint64_t seed, uint64_t frame, size_t c, float* g, float* u, mh_guide_fn guide,
+                    const void* ctx, int* smp_p, float* smp_dir, size_t first, size_t limit)
+{
+    float y = guide(ctx, g, u);
+    const float sg = 0.5f, su = 0.11077321f; /* sqrt(pi / 256) */
+    for (int i = 0; i < MH_M; ++i) {
+        float g2[3], u2[2];
+        for (int k = 0; k < 3; ++k)
+            g2[k] = mh_reflect(g[k] + sg * mh_normal(mh_bits(seed, frame, c, (uint64_t)i, (uint64_t)k)), 0.0f,
+                               (float)(dims[k] - 1));
+        for (int k = 0; k < 2; ++k)
+            u2[k] = mh_reflect(u[k] + su * mh_normal(mh_bits(seed, frame, c, (uint64_t)i, (uint64_t)(3 + k))), -1.0f,
+                               1.0f);
+        float y2 = guide(ctx, g2, u2);
+        int accept = 1;
+        if (y > 0.0f) {
+            float mu = y2 / y;
+            float eps = mh_uniform(mh_bits(seed, frame, c, (uint64_t)i, 5u));
+            if (mu < 1.0f && eps > mu) accept = 0;
+        }
+        if (accept) {
+            for (int k = 0; k < 3; ++k) g[k] = g2[k];
+            u[0] = u2[0];
+            u[1] = u2[1];
+            y = y2;
+        }
+        if (i > MH_K) { /* the state after step i is sample i - K - 1 of the chain */
+            size_t sidx = first + (size_t)(i - MH_K - 1);
+            if (sidx < limit) {
+                int q[3];
+                for (int k = 0; k < 3; ++k) {
+                    int t = (int)floorf(g[k] + 0.5f);
+                    q[k] = t < 0 ? 0 : (t > dims[k] - 1 ? dims[k] - 1 : t);
+                }
+                smp_p[sidx] = q[0] + dims[0] * (q[1] + dims[1] * q[2]);
+                mh_dir(u, smp_dir + sidx * 3);
+            }
+        }
+    }
+}
+
+typedef struct {
+    const orc_vol* v;
+    const orc_frame* fr;
+} mh_vol_ctx;
+static float mh_vol_guide(const void* ctx, const float g[3], const float u[2])
+{
+    const mh_vol_ctx* c = (const mh_vol_ctx*)ctx;
+    return mh_guide(c->v, c->fr, g, u);
+}
+
+/* chain c of the volume: this frame's steps and samples */
+static void mh_chain(orc_vol* v, const orc_frame* fr, size_t c)
+{
+    mh_vol_ctx ctx = {v, fr};
+    mh_walk(v->d.dims, fr->seed, fr->frame, c, v->ch_g + c * 3, v->ch_u + c * 2, mh_vol_guide, &ctx, v->smp_p,
+            v->smp_dir, c * MH_S, v->B);
+}
+
+/* Test hook: chains on a fixed guide h(probe, octant) given as a table
+   (piecewise constant), for `frames` frames of M steps; counts[probe*8 +
+   octant] receives the samples of frames >= skip. */
+typedef struct {
+    const int* dims;
+    const float* table;
+} mh_tab_ctx;
+static float mh_tab_guide(const void* ctx, const float g[3], const float u[2])
+{
+    const mh_tab_ctx* c = (const mh_tab_ctx*)ctx;
+    int q[3];
+    for (int k = 0; k < 3; ++k) {
+        int t = (int)floorf(g[k] + 0.5f);
+        q[k] = t < 0 ? 0 : (t > c->dims[k] - 1 ? c->dims[k] - 1 : t);
+    }
+    float w[3];
+    mh_dir(u, w);
+    int o = (w[0] < 0.0f ? 1 : 0) | (w[1] < 0.0f ? 2 : 0) | (w[2] < 0.0f ? 4 : 0);
+    return c->table[(size_t)(q[0] + c->dims[0] * (q[1] + c->dims[1] * q[2])) * 8 + (size_t)o];
+}
+EXPORT void orc_mh_run_table(const int dims[3], const float* table, int chains, int frames, int skip, uint64_t seed,
+                             double* counts)
+{
+    pthread_once(&g_mh_once, mh_tables_init);
+    mh_tab_ctx ctx = {dims, table};
+    float* g = (float*)malloc(sizeof(float) * 3 * (size_t)chains);
+    float* u = (float*)malloc(sizeof(float) * 2 * (size_t)chains);
+    int* sp = (int*)malloc(sizeof(int) * MH_S);
+    float* sd = (float*)malloc(sizeof(float) * 3 * MH_S);
+    for (int c = 0; c < chains; ++c) {
+        for (int k = 0; k < 3; ++k)
+            g[c * 3 + k] = mh_uniform(mh_bits(seed ^ 0x494E4954ULL, 0, (uint64_t)c, MH_M, (uint64_t)k)) *
+                           (float)(dims[k] - 1);
+        for (int k = 0; k < 2; ++k)
+            u[c * 2 + k] = mh_uniform(mh_bits(seed ^ 0x494E4954ULL, 0, (uint64_t)c, MH_M, (uint64_t)(3 + k))) * 2.0f - 1.0f;
+    }
+    for (int f = 0; f < frames; ++f)
+        for (int c = 0; c < chains; ++c) {
+            mh_walk(dims, seed, (uint64_t)f, (size_t)c, g + c * 3, u + c * 2, mh_tab_guide, &ctx, sp, sd, 0, MH_S);
+            if (f < skip) continue;
+            for (int j = 0; j < MH_S; ++j) {
+                const float* d = sd + 3 * j;
+                int o = (d[0] < 0.0f ? 1 : 0) | (d[1] < 0.0f ? 2 : 0) | (d[2] < 0.0f ? 4 : 0);
+                counts[(size_t)sp[j] * 8 + (size_t)o] += 1.0;
+            }
+        }
+    free(g);
+    free(u);
+    free(sp);
+    free(sd);
+}
+
+static void mh_init(orc_vol* v, uint64_t seed)
+{
+    for (size_t c = 0; c < v->C; ++c) {
+        for (int k = 0; k < 3; ++k)
+            v->ch_g[c * 3 + k] = mh_uniform(mh_bits(seed ^ 0x494E4954ULL, 0, c, MH_M, (uint64_t)k)) *
+                                 (float)(v->d.dims[k] - 1);
+        for (int k = 0; k < 2; ++k)
+            v->ch_u[c * 2 + k] = mh_uniform(mh_bits(seed ^ 0x494E4954ULL, 0, c, MH_M, (uint64_t)(3 + k))) * 2.0f - 1.0f;
+    }
+    v->chains_live = 1;
+}
+
+/* trace and shade sample s: +w for radiance, -w for the visibility distance */
+static void mh_sample_rays(orc_vol* v, const orc_frame* fr, size_t sidx)
+{
+    float o[3];
+    probe_pos(v, v->smp_p[sidx], o);
+    const float* d = v->smp_dir + sidx * 3;
+    hitrec h = vol_closest(v, o, d, v->tmin, INFINITY);
+    v->smp_t[sidx] = h.tri >= 0 ? h.t : INFINITY;
+    v->smp_tri[sidx] = h.tri;
+    double dep_unused;
+    shade_ray(v, fr, o, d, h, v->smp_rad + sidx * 3, &dep_unused, NULL);
+    float dn[3] = {-d[0], -d[1], -d[2]};
+    hitrec hn = vol_closest(v, o, dn, v->tmin, INFINITY);
+    v->smp_tn[sidx] = hn.tri >= 0 ? hn.t : INFINITY;
+    v->smp_trin[sidx] = hn.tri;
+    v->smp_dep[sidx] = hn.tri >= 0 ? (hn.t < v->depth_max ? hn.t : v->depth_max) : v->depth_max;
+}
+
+/* the samples of each probe, in sample order (counting sort by probe) */
+static void mh_group(orc_vol* v)
+{
+    memset(v->smp_off, 0, sizeof(uint32_t) * ((size_t)v->P + 1));
+    for (size_t sidx = 0; sidx < v->B; ++sidx) v->smp_off[v->smp_p[sidx] + 1] += 1u;
+    for (int p = 0; p < v->P; ++p) v->smp_off[p + 1] += v->smp_off[p];
+    uint32_t* cur = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)v->P);
+    memcpy(cur, v->smp_off, sizeof(uint32_t) * (size_t)v->P);
+    for (size_t sidx = 0; sidx < v->B; ++sidx) v->smp_ord[cur[v->smp_p[sidx]]++] = (uint32_t)sidx;
+    free(cur);
+}
+
+/* blend probe p: pilots (even frames), then its samples in sample order;
+   irradiance texel at w, visibility texel at -w; the batched moving average
+   of blend_probe */
+static void mh_blend_probe(orc_vol* v, int p, int use_pilots, double h)
+{
+    const int Ti = v->Ti, Td = v->Td, ni = v->d.n_irr, nd = v->d.n_dep;
+    double* irr = v->irr + (size_t)p * Ti * Ti * 3;
+    uint8_t* irn = v->irr_n + (size_t)p * Ti * Ti;
+    double* dep = v->dep + (size_t)p * Td * Td * 2;
+    uint8_t* den = v->dep_n + (size_t)p * Td * Td;
+    double* si = (double*)calloc((size_t)Ti * Ti * 3, sizeof(double));
+    int* ki = (int*)calloc((size_t)Ti * Ti, sizeof(int));
+    double* sd = (double*)calloc((size_t)Td * Td * 2, sizeof(double));
+    int* kd = (int*)calloc((size_t)Td * Td, sizeof(int));
+    if (use_pilots)
+        for (int j = 0; j < 8; ++j) {
+            const float* d = v->pil_dir + ((size_t)p * 8 + (size_t)j) * 3;
+            const double* rad = v->pil_rad + ((size_t)p * 8 + (size_t)j) * 3;
+            double ds = v->pil_dep[(size_t)p * 8 + (size_t)j];
+            int ti = orc_texel_of_dir(d, ni), td = orc_texel_of_dir(d, nd);
+            for (int c = 0; c < 3; ++c) si[ti * 3 + c] += rad[c];
+            ki[ti] += 1;
+            sd[td * 2 + 0] += ds;
+            sd[td * 2 + 1] += ds * ds;
+            kd[td] += 1;
+        }
+    for (uint32_t q = v->smp_off[p]; q < v->smp_off[p + 1]; ++q) {
+        size_t sidx = v->smp_ord[q];
+        const float* d = v->smp_dir + sidx * 3;
+        float dn[3] = {-d[0], -d[1], -d[2]};
+        int ti = orc_texel_of_dir(d, ni), td = orc_texel_of_dir(dn, nd);
+        for (int c = 0; c < 3; ++c) si[ti * 3 + c] += v->smp_rad[sidx * 3 + c];
+        ki[ti] += 1;
+        double ds = v->smp_dep[sidx];
+        sd[td * 2 + 0] += ds;
+        sd[td * 2 + 1] += ds * ds;
+        kd[td] += 1;
+    }
+    for (int t = 0; t < Ti * Ti; ++t) {
+        if (!ki[t]) continue;
+        double k = ki[t], n = irn[t];
+        double w = k / (n + k);
+        if (w < 1.0 - h) w = 1.0 - h;
+        for (int c = 0; c < 3; ++c) irr[t * 3 + c] += w * (si[t * 3 + c] / k - irr[t * 3 + c]);
+        int nn = irn[t] + ki[t];
+        irn[t] = (uint8_t)(nn > 255 ? 255 : nn);
+    }
+    for (int t = 0; t < Td * Td; ++t) {
+        if (!kd[t]) continue;
+        double k = kd[t], n = den[t];
+        double w = k / (n + k);
+        if (w < 1.0 - h) w = 1.0 - h;
+        for (int c = 0; c < 2; ++c) dep[t * 2 + c] += w * (sd[t * 2 + c] / k - dep[t * 2 + c]);
+        int nn = den[t] + kd[t];
+        den[t] = (uint8_t)(nn > 255 ? 255 : nn);
+    }
+    border_copy(irr, irn, ni, 3);
+    border_copy(dep, den, nd, 2);
+    free(si);
+    free(ki);
+    free(sd);
+    free(kd);
+}
+
 static void pilot_probe(orc_vol* v, const orc_frame* fr, int p)
 {
     float o[3];
@@ -1723,7 +2119,13 @@ static void* worker(void* arg)
 {
     job* j = (job*)arg;
     for (int p = j->t0; p < j->t1; ++p) {
-        if (j->phase == 0)
+        if (j->phase == 3)
+            mh_chain(j->v, j->fr, (size_t)p);
+        else if (j->phase == 4)
+            mh_sample_rays(j->v, j->fr, (size_t)p);
+        else if (j->phase == 5)
+            mh_blend_probe(j->v, p, (j->fr->frame & 1u) == 0, (double)j->v->d.hyst);
+        else if (j->phase == 0)
             pilot_probe(j->v, j->fr, p);
         else if (j->phase == 1)
             main_probe(j->v, j->fr, p);
@@ -1738,8 +2140,11 @@ static void* worker(void* arg)
 
 static void run_phase(orc_vol* v, const orc_frame* fr, int phase)
 {
+    /* phases 3 and 4 run over chains and samples, the others over probes */
+    const long long N = phase == 3 ? (long long)v->C : phase == 4 ? (long long)v->B : (long long)v->P;
+    if (N == 0) return;
     int nt = v->nthreads;
-    if (nt > v->P) nt = v->P;
+    if (nt > N) nt = (int)N;
     pthread_t th[256];
     job jobs[256];
     if (nt > 256) nt = 256;
@@ -1747,8 +2152,8 @@ static void run_phase(orc_vol* v, const orc_frame* fr, int phase)
         jobs[t].v = v;
         jobs[t].fr = fr;
         jobs[t].phase = phase;
-        jobs[t].t0 = (int)((long long)v->P * t / nt);
-        jobs[t].t1 = (int)((long long)v->P * (t + 1) / nt);
+        jobs[t].t0 = (int)(N * t / nt);
+        jobs[t].t1 = (int)(N * (t + 1) / nt);
     }
     if (nt == 1) {
         worker(&jobs[0]);
@@ -1768,6 +2173,15 @@ EXPORT int orc_update(orc_vol* v, const orc_frame* fr)
     run_phase(v, fr, 0);
     change_detect(v, fr);
     if (orc_allocate(v->W, v->P, v->d.avg, v->d.rmin, v->d.rmax, v->n, v->off)) return -1;
+    if (v->d.sampler == 1) { /* Metropolis chains instead of the per-probe allocation */
+        pthread_once(&g_mh_once, mh_tables_init);
+        if (!v->chains_live) mh_init(v, fr->seed);
+        run_phase(v, fr, 3);
+        run_phase(v, fr, 4);
+        mh_group(v);
+        run_phase(v, fr, 5);
+        return 0;
+    }
     run_phase(v, fr, 1);
     run_phase(v, fr, 2);
     return 0;
@@ -1831,6 +2245,25 @@ EXPORT void orc_set_atlas(orc_vol* v, const double* irr, const uint8_t* irr_n, c
 }
 
 EXPORT void orc_border_copy(double* tile, uint8_t* cnt, int n, int ch) { border_copy(tile, cnt, n, ch); }
+
+/* Metropolis sampler state and samples (desc.sampler = 1) */
+EXPORT long long orc_mh_samples(const orc_vol* v) { return (long long)v->B; }
+EXPORT long long orc_mh_chains(const orc_vol* v) { return (long long)v->C; }
+EXPORT const float* orc_mh_chain_g(const orc_vol* v) { return v->ch_g; }
+EXPORT const float* orc_mh_chain_u(const orc_vol* v) { return v->ch_u; }
+EXPORT const int* orc_mh_probe(const orc_vol* v) { return v->smp_p; }
+EXPORT const float* orc_mh_dir(const orc_vol* v) { return v->smp_dir; }
+EXPORT const int* orc_mh_tri(const orc_vol* v) { return v->smp_tri; }
+EXPORT const int* orc_mh_tri_neg(const orc_vol* v) { return v->smp_trin; }
+EXPORT const double* orc_mh_rad(const orc_vol* v) { return v->smp_rad; }
+EXPORT const double* orc_mh_dep(const orc_vol* v) { return v->smp_dep; }
+/* Test hook: h(x) of the volume's current guide (last frame's heuristics and
+   atlas) at grid coordinates g and octahedral coordinates u */
+EXPORT float orc_mh_guide(const orc_vol* v, const orc_frame* fr, const float g[3], const float u[2])
+{
+    pthread_once(&g_mh_once, mh_tables_init);
+    return mh_guide(v, fr, g, u);
+}
 
 /* packed atlases (NULL unless the volume was created packed) */
 EXPORT const uint32_t* orc_irr_packed(const orc_vol* v) { return v->irr_pk; }

@@ -27,6 +27,8 @@ class OrcDesc(C.Structure):
         ("depth_max", C.c_float),
         ("theta", C.c_int),
         ("packed", C.c_int),
+        ("sampler", C.c_int),
+        ("alpha", C.c_float),
     ]
 
 
@@ -124,6 +126,21 @@ def lib():
         L.orc_cage_diag.argtypes = [vp]
         L.orc_cage_diag.restype = C.c_float
         L.orc_blend_packed_records.argtypes = [vp, C.c_int, C.c_int, f64p, f64p, f64p, f64p]
+        L.orc_mh_normal_quantile.argtypes = [C.c_int]
+        L.orc_mh_normal_quantile.restype = C.c_float
+        L.orc_mh_exp.argtypes = [C.c_int]
+        L.orc_mh_exp.restype = C.c_float
+        for name in ("orc_mh_samples", "orc_mh_chains"):
+            getattr(L, name).argtypes = [vp]
+            getattr(L, name).restype = C.c_longlong
+        for name, rt in [("orc_mh_chain_g", f32p), ("orc_mh_chain_u", f32p), ("orc_mh_probe", i32p),
+                         ("orc_mh_dir", f32p), ("orc_mh_tri", i32p), ("orc_mh_tri_neg", i32p), ("orc_mh_rad", f64p),
+                         ("orc_mh_dep", f64p)]:
+            getattr(L, name).argtypes = [vp]
+            getattr(L, name).restype = rt
+        L.orc_mh_guide.argtypes = [vp, C.POINTER(OrcFrame), f32p, f32p]
+        L.orc_mh_guide.restype = C.c_float
+        L.orc_mh_run_table.argtypes = [i32p, f32p, C.c_int, C.c_int, C.c_int, C.c_uint64, f64p]
         _lib = L
     return _lib
 
@@ -163,6 +180,25 @@ def codec_dec(which: int, k: int) -> float:
 def codec_table(which: int) -> np.ndarray:
     """decoded value of every code (FP32)"""
     return np.array([codec_dec(which, k) for k in range(1 << CODEC_BITS[which])], np.float32)
+
+
+def mh_normal_quantile(i: int) -> float:
+    return float(lib().orc_mh_normal_quantile(int(i)))
+
+
+def mh_run_table(dims, table, chains, frames, skip, seed=1):
+    """chains on a fixed piecewise-constant guide table[probe, octant];
+    sample counts per (probe, octant) of frames >= skip"""
+    d = np.ascontiguousarray(dims, np.int32)
+    t = _f32(table).reshape(-1)
+    out = np.zeros(t.shape[0], np.float64)
+    lib().orc_mh_run_table(_p(d, C.c_int), _p(t, C.c_float), int(chains), int(frames), int(skip), int(seed),
+                           _p(out, C.c_double))
+    return out.reshape(-1, 8)
+
+
+def mh_exp(k: int) -> float:
+    return float(lib().orc_mh_exp(int(k)))
 
 
 def codec_mav(o: float, v: float, n: int) -> float:
@@ -288,7 +324,7 @@ class OracleVolume:
     """FP64 oracle volume with the same five-call shape as the C-ABI."""
 
     def __init__(self, origin, spacing, dims, n_irr=6, n_dep=14, rays_avg=64, rays_min=8, rays_max=256,
-                 hysteresis=0.97, depth_max=0.0, theta=16, threads=None, packed=False):
+                 hysteresis=0.97, depth_max=0.0, theta=16, threads=None, packed=False, sampler=0, alpha=1.0):
         d = OrcDesc()
         d.origin[:] = [float(x) for x in origin]
         d.spacing[:] = [float(x) for x in spacing]
@@ -300,6 +336,8 @@ class OracleVolume:
         d.theta = int(theta)
         d.packed = int(bool(packed))
         self.packed = bool(packed)
+        d.sampler = int(sampler)
+        d.alpha = float(alpha)
         self.desc = d
         if threads is None:
             threads = os.cpu_count() or 1
@@ -400,6 +438,44 @@ class OracleVolume:
         keep = [None if a is None else np.ascontiguousarray(a, np.float64) for a in (pil_rad, pil_dep, m_rad, m_dep)]
         lib().orc_blend_packed_records(self.h, int(p), int(bool(use_pilots)),
                                        *[None if a is None else _p(a, C.c_double) for a in keep])
+
+    # Metropolis sampler (sampler=1): this frame's samples
+    @property
+    def mh_samples(self):
+        return int(lib().orc_mh_samples(self.h))
+
+    @property
+    def mh_chains(self):
+        return int(lib().orc_mh_chains(self.h))
+
+    def mh_probe(self):
+        return self._arr("orc_mh_probe", self.mh_samples, np.int32)
+
+    def mh_dir(self):
+        return self._arr("orc_mh_dir", self.mh_samples * 3, np.float32, (self.mh_samples, 3))
+
+    def mh_tri(self):
+        return self._arr("orc_mh_tri", self.mh_samples, np.int32)
+
+    def mh_tri_neg(self):
+        return self._arr("orc_mh_tri_neg", self.mh_samples, np.int32)
+
+    def mh_rad(self):
+        return self._arr("orc_mh_rad", self.mh_samples * 3, np.float64, (self.mh_samples, 3))
+
+    def mh_dep(self):
+        return self._arr("orc_mh_dep", self.mh_samples, np.float64)
+
+    def mh_chain_state(self):
+        C_ = self.mh_chains
+        return (self._arr("orc_mh_chain_g", C_ * 3, np.float32, (C_, 3)),
+                self._arr("orc_mh_chain_u", C_ * 2, np.float32, (C_, 2)))
+
+    def mh_guide(self, frame, g, u, camera=None, seed=0):
+        fr = make_frame(frame, seed, [], (0, 0, 0), camera)
+        g = _f32(g).reshape(3)
+        u = _f32(u).reshape(2)
+        return float(lib().orc_mh_guide(self.h, C.byref(fr), _p(g, C.c_float), _p(u, C.c_float)))
 
     def W(self):
         return self._arr("orc_W", self.P, np.uint32)
