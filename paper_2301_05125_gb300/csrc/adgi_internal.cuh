@@ -282,13 +282,31 @@ constexpr int kPartBit = 1 << 30;
 // a separate local array.
 struct Trav {
     WRay wr;
-    float3 o, inv;
+    float3 o, inv, oi;      // oi = o * inv: slab tests as one FMA per plane
     float tmin, tmax, lim;  // lim: box pruning bound
     float t_best, best_det;
     int best_orig;
     bool found;
     int sp, iter;
+    int next;  // the node to visit next (-1: take the stack top); saves a push and a pop per single-child step
 };
+
+// Conservative slab test of one box against [0, lim] with the plane
+// distances as fma(plane, 1/d, -o/d): the rounding of o/d moves a plane by
+// about 2^-24 |o|, far inside the boxes' enlargement (>= 1e-5 of the
+// largest coordinate), so no box that the ray enters is culled.  NaNs
+// (0 * inf) drop out of fminf/fmaxf, which keeps the test conservative.
+__device__ __forceinline__ bool slab_fma(float lox, float loy, float loz, float hix, float hiy, float hiz, float3 inv,
+                                         float3 oi, float lim, float& tnear)
+{
+    float tx0 = fmaf(lox, inv.x, -oi.x), tx1 = fmaf(hix, inv.x, -oi.x);
+    float ty0 = fmaf(loy, inv.y, -oi.y), ty1 = fmaf(hiy, inv.y, -oi.y);
+    float tz0 = fmaf(loz, inv.z, -oi.z), tz1 = fmaf(hiz, inv.z, -oi.z);
+    float tn = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fmaxf(fminf(tz0, tz1), 0.0f));
+    float tf = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fminf(fmaxf(tz0, tz1), lim));
+    tnear = tn;
+    return tn <= tf;
+}
 
 __device__ __forceinline__ void trav_tri(Trav& T, const float4* tv, bool any, uint32_t* ntri)
 {
@@ -317,6 +335,8 @@ __device__ __forceinline__ void trav_init(Trav& T, int* stack, const SceneDev& S
     T.wr = wray(o, d);
     T.o = o;
     T.inv = make_float3(1.0f / d.x, 1.0f / d.y, 1.0f / d.z);
+    T.oi = make_float3(o.x * T.inv.x, o.y * T.inv.y, o.z * T.inv.z);
+    T.next = -1;
     T.tmin = tmin;
     T.tmax = tmax;
     T.lim = any ? (isinf(tmax) ? tmax : tmax * kBoxSlack) : tmax * kBoxSlack;
@@ -342,14 +362,16 @@ __device__ __forceinline__ void trav_init(Trav& T, int* stack, const SceneDev& S
 __device__ __forceinline__ bool trav_step(Trav& T, int* stack, const SceneDev& S, bool any,
                                           uint32_t* nbox = nullptr, uint32_t* ntri = nullptr)
 {
-    if (T.sp <= 0) return false;
+    if (T.next < 0 && T.sp <= 0) return false;
     if (++T.iter > S.part[0].max_iter + S.part[1].max_iter) {
         atomicOr(S.err, kErrTraversal);
         T.sp = 0;
+        T.next = -1;
         return false;
     }
     if (nbox) *nbox += 2;
-    const int e = stack[--T.sp];
+    const int e = T.next >= 0 ? T.next : stack[--T.sp];
+    T.next = -1;
     const int part = e & kPartBit;
     const BNode* nd = (part ? S.part[1].nodes : S.part[0].nodes) + (e & ~kPartBit);
     const float4* tris = part ? S.part[1].tri_v : S.part[0].tri_v;
@@ -357,27 +379,27 @@ __device__ __forceinline__ bool trav_step(Trav& T, int* stack, const SceneDev& S
     int4 ch = __ldg(&nd->d);
     const float lim = any ? T.lim : T.t_best * kBoxSlack;
     float t0, t1;
-    const bool h0 = slab(a.x, a.y, a.z, a.w, b.x, b.y, T.o, T.inv, lim, t0);
-    const bool h1 = slab(b.z, b.w, c.x, c.y, c.z, c.w, T.o, T.inv, lim, t1);
+    const bool h0 = slab_fma(a.x, a.y, a.z, a.w, b.x, b.y, T.inv, T.oi, lim, t0);
+    const bool h1 = slab_fma(b.z, b.w, c.x, c.y, c.z, c.w, T.inv, T.oi, lim, t1);
     if (h0 && ch.x < 0) trav_tri(T, tris + 3 * (size_t)(~ch.x), any, ntri);
     if (h1 && ch.y < 0) trav_tri(T, tris + 3 * (size_t)(~ch.y), any, ntri);
     const bool i0 = h0 && ch.x >= 0, i1 = h1 && ch.y >= 0;
-    if (i0 && i1) {  // far child below the near one
+    if (i0 && i1) {  // the near child next, the far one on the stack
         const bool first0 = t0 <= t1;
-        if (T.sp + 2 <= kStack + 2) {
+        if (T.sp < kStack + 2) {
             stack[T.sp++] = (first0 ? ch.y : ch.x) | part;
-            stack[T.sp++] = (first0 ? ch.x : ch.y) | part;
+            T.next = (first0 ? ch.x : ch.y) | part;
         } else {
             atomicOr(S.err, kErrTraversal);  // cannot happen: depths are bounded by the builders
         }
     } else if (i0 || i1) {
-        if (T.sp < kStack + 2)
-            stack[T.sp++] = (i0 ? ch.x : ch.y) | part;
-        else
-            atomicOr(S.err, kErrTraversal);
+        T.next = (i0 ? ch.x : ch.y) | part;
     }
-    if (any && T.found) T.sp = 0;  // a blocker ends a shadow ray
-    return T.sp > 0;
+    if (any && T.found) {  // a blocker ends a shadow ray
+        T.sp = 0;
+        T.next = -1;
+    }
+    return T.next >= 0 || T.sp > 0;
 }
 
 __device__ __forceinline__ uint32_t trav_hit(const Trav& T)
