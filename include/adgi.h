@@ -81,6 +81,15 @@ typedef struct {
                                one moving-average step per sample (Alg. MovingAvgUpdate, count capped
                                at 63) in sample order; hysteresis is not used */
     int32_t tr_theta;       /* trigger decay length theta in frames (Fig. TrCam(a)), >= 1, <= 255 */
+    int32_t sampler;        /* 0: per-probe ray counts from the change weights (Sec. 4.2);
+                               1: Metropolis chains draw the (rays_avg - 8) * P adaptive samples
+                               over (probe, direction) from the static guide
+                               h = exp(min(alpha g / f_s, 1)) f_s, f_s = q_c q_v / 1023^2, g the
+                               cached irradiance luminance (Sec. "Adaptive sampling - static",
+                               Alg. MetropolisStep); each sample also traces -w for the visibility
+                               texel at -w.  Not with atlas_fp16 = 3, adgi_autotune or
+                               adgi_count_traversal */
+    float alpha;            /* sampler = 1: confidence alpha of the cached irradiance, >= 0 */
 } adgi_volume_desc;
 
 /* kind 0: point light at pos_or_dir with intensity rgb (irradiance rgb/d^2);
@@ -106,7 +115,8 @@ typedef struct {
 
 typedef struct {
     uint64_t frames;          /* updates run so far */
-    uint64_t rays_per_update; /* rays_avg * probes: pilot + adaptive rays */
+    uint64_t rays_per_update; /* rays_avg * probes: pilot + adaptive rays (Metropolis volumes:
+                                 8 * probes + 2 * samples, the -w visibility rays included) */
     uint64_t pilot_rays;      /* 8 * probes */
     uint64_t shadow_rays;     /* shadow rays of the last update (counted on the device) */
     uint32_t bvh_nodes;       /* internal nodes of the current BVH */
@@ -247,6 +257,16 @@ int adgi_enable_timing(adgi_volume vol, int32_t enable);
  *   ADGI_STATE_BVH_TRIS  float[T][3][4]    static triangles in BVH order (layout of adgi_build_bvh)
  *   ADGI_STATE_MOVING_BVH_NODES / _TRIS    the same for the moving part (triangles that touch a
  *                       vertex passed to adgi_move_vertices), a linear BVH rebuilt after moves
+ * Metropolis volumes (sampler = 1; B = (rays_avg - 8) * P samples, C = ceil(B / 5) chains):
+ *   ADGI_STATE_MH_CHAINS  float[2][C][4]   chain states after the last update: {g.xyz, u.x},
+ *                       then {u.y, 0, 0, 0} (g grid coordinates, u octahedral coordinates)
+ *   ADGI_STATE_MH_SAMPLES float[B][4]      the last update's samples in chain order (sample
+ *                       5c + j is the state after step K+1+j of chain c): {w.xyz, probe (int32 bits)}
+ *   ADGI_STATE_MH_ORDER uint32[B]         the sample at each grouped position (by probe, sample
+ *                       order inside a probe)
+ *   ADGI_STATE_MH_OFF   uint32[P+1]       first grouped position of each probe
+ *   ADGI_STATE_MH_HIT_NEG int32[B][2]     -w hits in grouped order (as PILOT_HIT); MAIN_HIT and
+ *                       MAIN_REC then hold the +w hits and records in grouped order
  * The scene is traced as two parts: triangles that touch any vertex ever passed
  * to adgi_move_vertices form the moving part (linear BVH, rebuilt at the next
  * update after each move); the others form the static part (agglomerative
@@ -272,7 +292,12 @@ enum {
     ADGI_STATE_BVH_NODES = 16,
     ADGI_STATE_BVH_TRIS = 17,
     ADGI_STATE_MOVING_BVH_NODES = 18,
-    ADGI_STATE_MOVING_BVH_TRIS = 19
+    ADGI_STATE_MOVING_BVH_TRIS = 19,
+    ADGI_STATE_MH_CHAINS = 20,
+    ADGI_STATE_MH_SAMPLES = 21,
+    ADGI_STATE_MH_ORDER = 22,
+    ADGI_STATE_MH_OFF = 23,
+    ADGI_STATE_MH_HIT_NEG = 24
 };
 int adgi_state_bytes(adgi_volume vol, int32_t which, uint64_t* bytes);
 int adgi_read_state(adgi_volume vol, int32_t which, void* dst_host, uint64_t bytes);

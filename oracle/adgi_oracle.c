@@ -2254,6 +2254,8 @@ EXPORT const float* orc_mh_chain_u(const orc_vol* v) { return v->ch_u; }
 EXPORT const int* orc_mh_probe(const orc_vol* v) { return v->smp_p; }
 EXPORT const float* orc_mh_dir(const orc_vol* v) { return v->smp_dir; }
 EXPORT const int* orc_mh_tri(const orc_vol* v) { return v->smp_tri; }
+EXPORT const float* orc_mh_t(const orc_vol* v) { return v->smp_t; }
+EXPORT const float* orc_mh_t_neg(const orc_vol* v) { return v->smp_tn; }
 EXPORT const int* orc_mh_tri_neg(const orc_vol* v) { return v->smp_trin; }
 EXPORT const double* orc_mh_rad(const orc_vol* v) { return v->smp_rad; }
 EXPORT const double* orc_mh_dep(const orc_vol* v) { return v->smp_dep; }

@@ -134,8 +134,8 @@ def lib():
             getattr(L, name).argtypes = [vp]
             getattr(L, name).restype = C.c_longlong
         for name, rt in [("orc_mh_chain_g", f32p), ("orc_mh_chain_u", f32p), ("orc_mh_probe", i32p),
-                         ("orc_mh_dir", f32p), ("orc_mh_tri", i32p), ("orc_mh_tri_neg", i32p), ("orc_mh_rad", f64p),
-                         ("orc_mh_dep", f64p)]:
+                         ("orc_mh_dir", f32p), ("orc_mh_tri", i32p), ("orc_mh_t", f32p), ("orc_mh_t_neg", f32p),
+                         ("orc_mh_tri_neg", i32p), ("orc_mh_rad", f64p), ("orc_mh_dep", f64p)]:
             getattr(L, name).argtypes = [vp]
             getattr(L, name).restype = rt
         L.orc_mh_guide.argtypes = [vp, C.POINTER(OrcFrame), f32p, f32p]
@@ -456,6 +456,12 @@ class OracleVolume:
 
     def mh_tri(self):
         return self._arr("orc_mh_tri", self.mh_samples, np.int32)
+
+    def mh_t(self):
+        return self._arr("orc_mh_t", self.mh_samples, np.float32)
+
+    def mh_t_neg(self):
+        return self._arr("orc_mh_t_neg", self.mh_samples, np.float32)
 
     def mh_tri_neg(self):
         return self._arr("orc_mh_tri_neg", self.mh_samples, np.int32)

@@ -18,7 +18,7 @@ ERRORS = {-1: "INVALID_ARG", -2: "OOM", -3: "OVER_BUDGET", -4: "NO_SCENE", -5: "
 
 STATE = dict(W=0, N=1, OFF=2, QV=3, QR=4, TRV=5, TRR=6, PILOT_HIT=7, PILOT_REC=8, PILOT_LUM=9, MAIN_HIT=10,
              MAIN_REC=11, IRR=12, DEP=13, DEP_N=14, ROT=15, BVH_NODES=16, BVH_TRIS=17, MOVING_BVH_NODES=18,
-             MOVING_BVH_TRIS=19)
+             MOVING_BVH_TRIS=19, MH_CHAINS=20, MH_SAMPLES=21, MH_ORDER=22, MH_OFF=23, MH_HIT_NEG=24)
 
 
 class AdgiError(RuntimeError):
@@ -41,6 +41,8 @@ class adgi_volume_desc(C.Structure):
         ("depth_max", C.c_float),
         ("atlas_fp16", C.c_int32),
         ("tr_theta", C.c_int32),
+        ("sampler", C.c_int32),
+        ("alpha", C.c_float),
     ]
 
 
@@ -388,7 +390,8 @@ def adgi_last_error() -> str:
 
 # ------------------------------------------------------------ convenience
 def make_desc(origin, spacing, dims, irr_interior=6, depth_interior=14, rays_avg=64, rays_min=8, rays_max=256,
-              hysteresis=0.97, depth_max=0.0, atlas_fp16=0, tr_theta=16) -> adgi_volume_desc:
+              hysteresis=0.97, depth_max=0.0, atlas_fp16=0, tr_theta=16, sampler=0,
+              alpha=1.0) -> adgi_volume_desc:
     d = adgi_volume_desc()
     d.origin[:] = [float(x) for x in origin]
     d.spacing[:] = [float(x) for x in spacing]
@@ -399,6 +402,8 @@ def make_desc(origin, spacing, dims, irr_interior=6, depth_interior=14, rays_avg
     d.depth_max = float(depth_max)
     d.atlas_fp16 = int(atlas_fp16)
     d.tr_theta = int(tr_theta)
+    d.sampler = int(sampler)
+    d.alpha = float(alpha)
     return d
 
 
@@ -525,6 +530,26 @@ class Volume:
 
     def main_rec(self):
         return self.state("MAIN_REC", np.float32).reshape(-1, 4)
+
+    # Metropolis volumes (sampler = 1)
+    def mh_chains(self):
+        """chain states: (g float32[C, 3], u float32[C, 2])"""
+        a = self.state("MH_CHAINS", np.float32).reshape(2, -1, 4)
+        return a[0, :, :3].copy(), np.stack([a[0, :, 3], a[1, :, 0]], axis=1)
+
+    def mh_samples(self):
+        """the last update's samples in chain order: (probe int32[B], direction float32[B, 3])"""
+        a = self.state("MH_SAMPLES", np.float32).reshape(-1, 4)
+        return a[:, 3].copy().view(np.int32), a[:, :3].copy()
+
+    def mh_order(self):
+        return self.state("MH_ORDER", np.uint32)
+
+    def mh_off(self):
+        return self.state("MH_OFF", np.uint32)
+
+    def mh_hit_neg(self):
+        return self.state("MH_HIT_NEG", np.int32).reshape(-1, 2)
 
     @property
     def packed(self):

@@ -73,6 +73,7 @@ struct FrameConst {
     int has_camera;
     float cam[3];
     float cam_k;
+    uint64_t mh_key;        // Metropolis counters of this frame: sm(sm(seed ^ 'METRO') ^ frame)
 };
 
 struct VolConst {
@@ -122,6 +123,21 @@ __device__ __forceinline__ float3 probe_pos(const VolConst& V, int p)
     int iz = p / (V.dims[0] * V.dims[1]);
     return make_float3(fa(V.origin[0], fm(V.spacing[0], (float)ix)), fa(V.origin[1], fm(V.spacing[1], (float)iy)),
                        fa(V.origin[2], fm(V.spacing[2], (float)iz)));
+}
+
+// q_c of probe p (Eq. cameraD): 1023 within cam_k of the camera, else the
+// LUT bin of width s/64 at the distance beyond cam_k; 1023 without a camera
+__device__ __forceinline__ uint32_t qc_of_probe(const VolConst& V, const FrameConst& F,
+                                                const uint16_t* __restrict__ lut_c, int p)
+{
+    if (!F.has_camera) return 1023u;
+    float3 pp = probe_pos(V, p);
+    float dx = fs(pp.x, F.cam[0]), dy = fs(pp.y, F.cam[1]), dz = fs(pp.z, F.cam[2]);
+    float dist = fsq(dot3x(dx, dy, dz, dx, dy, dz));
+    if (dist < F.cam_k) return 1023u;
+    float q = fm(fs(dist, F.cam_k), V.qc_scale);
+    uint32_t i = q < 4095.0f ? (uint32_t)floorf(q) : 4095u;
+    return __ldg(lut_c + i);
 }
 
 // Pilot direction of (probe, octant) for the frame pair encoded in key:

@@ -6,6 +6,7 @@
 // (8 passes of 8 bits, own kernels) -> Karras (HPG 2012) radix-tree hierarchy
 // -> bottom-up child boxes, each leaf box enlarged by eps so that box tests
 // stay conservative for the watertight triangle test.
+#include <algorithm>
 #include <cstdio>
 
 #include "adgi_internal.cuh"
@@ -535,6 +536,32 @@ size_t carve_bvh_scratch(void* base, int nt, BvhBufs& B)
     return off;
 }
 
+size_t radix_hist_entries(int n) { return 256 * (size_t)((std::max(n, 1) + kSortTile - 1) / kSortTile); }
+
+// Stable LSD radix sort of n (key, value) pairs on key bits [0, bits), eight
+// bits per pass (hist -> scan -> scatter); the result is in keys[*cur],
+// vals[*cur].  hist holds radix_hist_entries(n) counters.
+cudaError_t radix_sort_pairs(uint64_t* const keys[2], uint32_t* const vals[2], uint32_t* hist, int n, int bits,
+                             cudaStream_t s, int* cur_out)
+{
+    int cur = 0;
+    if (n > 0) {
+        const int nb = (n + kSortTile - 1) / kSortTile;
+        for (int shift = 0; shift < bits; shift += 8) {
+            k_hist<<<nb, kSortThreads, 0, s>>>(keys[cur], n, shift, hist, nb);
+            count_launches(1);
+            k_scan_small<<<1, 1024, 0, s>>>(hist, 256 * nb);
+            count_launches(1);
+            k_scatter<<<nb, kSortThreads, 0, s>>>(keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], n, shift, hist,
+                                                   nb);
+            count_launches(1);
+            cur ^= 1;
+        }
+    }
+    *cur_out = cur;
+    return cudaGetLastError();
+}
+
 // Morton order of the listed triangles into B.tri_v (all builds start here)
 static cudaError_t morton_order(const BvhBufs& B, const float* d_verts, const int* d_idx, const int* list, int nv,
                                 int nt, int* err, cudaStream_t s, int* cur_out)
@@ -546,18 +573,9 @@ static cudaError_t morton_order(const BvhBufs& B, const float* d_verts, const in
     count_launches(1);
     k_morton<<<(nt + T - 1) / T, T, 0, s>>>(B.tri_in, nt, B.bounds, B.keys[0], B.vals[0]);
     count_launches(1);
-    int nb = (nt + kSortTile - 1) / kSortTile;
     int cur = 0;
-    for (int shift = 0; shift < 64; shift += 8) {
-        k_hist<<<nb, kSortThreads, 0, s>>>(B.keys[cur], nt, shift, B.hist, nb);
-        count_launches(1);
-        k_scan_small<<<1, 1024, 0, s>>>(B.hist, 256 * nb);
-        count_launches(1);
-        k_scatter<<<nb, kSortThreads, 0, s>>>(B.keys[cur], B.vals[cur], B.keys[cur ^ 1], B.vals[cur ^ 1], nt, shift,
-                                               B.hist, nb);
-        count_launches(1);
-        cur ^= 1;
-    }
+    cudaError_t e = radix_sort_pairs(B.keys, B.vals, B.hist, nt, 64, s, &cur);
+    if (e != cudaSuccess) return e;
     k_tri_order<<<(nt + T - 1) / T, T, 0, s>>>(B.tri_in, B.vals[cur], nt, B.tri_v);
     count_launches(1);
     *cur_out = cur;

@@ -111,6 +111,30 @@ void build_sf(int M, std::vector<float4>& out)
     }
 }
 
+const uint64_t kMhSalt = 0x4D4554524Full;      // 'METRO': Metropolis counters
+const uint64_t kMhInitSalt = 0x494E4954ull;    // 'INIT': first chain states
+
+// Host tables of the Metropolis sampler.  nq[i] = Phi^-1((i + 0.5) / 4096) by
+// Newton's method on Phi(x) = erfc(-x / sqrt 2) / 2 from x = 0 (monotone:
+// Phi is convex left of 0 and concave right of it), FP64, rounded to FP32;
+// ex[k] = exp(k / 1023) rounded to FP32.
+void mh_tables(std::vector<float>& out)
+{
+    out.assign(kMhNq + kMhEx, 0.0f);
+    const double rs2 = 0.70710678118654752440, rs2pi = 0.39894228040143267794;
+    for (int i = 0; i < kMhNq; ++i) {
+        const double p = ((double)i + 0.5) / (double)kMhNq;
+        double x = 0.0;
+        for (int it = 0; it < 200; ++it) {
+            const double dx = (0.5 * std::erfc(-x * rs2) - p) / (rs2pi * std::exp(-0.5 * x * x));
+            x -= dx;
+            if (std::fabs(dx) <= 2e-16 * std::max(1.0, std::fabs(x))) break;
+        }
+        out[(size_t)i] = (float)x;
+    }
+    for (int k = 0; k < kMhEx; ++k) out[(size_t)kMhNq + k] = (float)std::exp((double)k / 1023.0);
+}
+
 uint64_t h3(uint64_t a, uint64_t b, uint64_t c) { return splitmix(splitmix(splitmix(a) ^ b) ^ c); }
 
 void frame_rotation(uint64_t seed, uint64_t frame, float R[9])
@@ -233,6 +257,18 @@ struct adgi_volume_s {
     // query scratch for host pointers
     float* q_buf = nullptr;
     int q_cap = 0;
+    // Metropolis sampler (desc.sampler = 1)
+    uint32_t mh_B = 0, mh_C = 0;       // samples and chains per update
+    float* mh_tab = nullptr;           // [4096] normal quantiles, then [1024] exp values
+    float4* mh_chain = nullptr;        // [2C] chain states
+    float4* mh_smp = nullptr;          // [B] samples, chain order
+    uint64_t* mh_keys = nullptr;       // [2B] radix sort by probe
+    uint32_t* mh_vals = nullptr;       // [2B]
+    uint32_t* mh_hist = nullptr;
+    uint32_t* mh_off = nullptr;        // [P+1]
+    int2* mh_hitn = nullptr;           // [B] -w hits, grouped order
+    const uint32_t* mh_ord = nullptr;  // grouped order of the last update
+    bool mh_live = false;              // chain states initialised
 };
 
 namespace {
@@ -244,7 +280,8 @@ void free_volume(adgi_volume v)
                     v->qv_even, v->qr_even, v->amp_v,  v->amp_r, v->trv,     v->trr,     v->age_v,  v->age_r,
                     v->G,       v->W,       v->n,      v->off,   v->pil_hit, v->pil_rec, v->pil_lum, v->m_hit,
                     v->m_rec,   v->shadow_ctr, v->verts, v->idx, v->albedo,  v->q_buf, v->err,
-                    v->vis,     v->jobs,    v->job_light, v->job_count, v->fdev};
+                    v->vis,     v->jobs,    v->job_light, v->job_count, v->fdev,
+                    v->mh_tab,  v->mh_chain, v->mh_smp, v->mh_keys, v->mh_vals, v->mh_hist, v->mh_off, v->mh_hitn};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     v->sbvh.release();
@@ -289,6 +326,11 @@ int validate_desc(const adgi_volume_desc* d)
     if (!(d->hysteresis >= 0.0f && d->hysteresis < 1.0f)) return fail(ADGI_ERR_INVALID_ARG, "hysteresis in [0,1)");
     if (d->tr_theta < 1 || d->tr_theta > 255) return fail(ADGI_ERR_INVALID_ARG, "tr_theta in [1,255]");
     if (d->atlas_fp16 < 0 || d->atlas_fp16 > 3) return fail(ADGI_ERR_INVALID_ARG, "atlas_fp16 in {0,1,2,3}");
+    if (d->sampler < 0 || d->sampler > 1) return fail(ADGI_ERR_INVALID_ARG, "sampler in {0,1}");
+    if (d->sampler == 1 && d->atlas_fp16 == 3)
+        return fail(ADGI_ERR_INVALID_ARG, "the Metropolis sampler blends batched moving averages: not with packed atlases");
+    if (d->sampler == 1 && !(d->alpha >= 0.0f && std::isfinite(d->alpha)))
+        return fail(ADGI_ERR_INVALID_ARG, "alpha must be finite and >= 0");
     int64_t P = (int64_t)d->dims[0] * d->dims[1] * d->dims[2];
     if (P * (int64_t)d->rays_avg >= (int64_t)1 << 31) return fail(ADGI_ERR_INVALID_ARG, "ray budget too large");
     return ADGI_OK;
@@ -307,6 +349,7 @@ FrameConst frame_const(adgi_volume v, const adgi_frame* f)
     F.has_camera = f->has_camera ? 1 : 0;
     for (int k = 0; k < 3; ++k) F.cam[k] = f->cam_pos[k];
     F.cam_k = f->cam_k;
+    F.mh_key = splitmix(splitmix(f->seed ^ kMhSalt) ^ f->frame);
     return F;
 }
 
@@ -450,6 +493,19 @@ int adgi_create_volume(const adgi_volume_desc* desc, void* cuda_stream, adgi_vol
     DA(v->fdev, 1);
     DA(v->vis, std::max<size_t>(P * 8, (size_t)v->R_main));
     DA(v->job_count, 1);
+    if (d.sampler == 1) {
+        v->mh_B = v->R_main;
+        v->mh_C = (v->mh_B + kMhPer - 1) / kMhPer;
+        const size_t nB = v->mh_B;
+        DA(v->mh_tab, (size_t)(kMhNq + kMhEx));
+        DA(v->mh_chain, 2 * (size_t)v->mh_C);
+        DA(v->mh_smp, nB);
+        DA(v->mh_keys, 2 * nB);
+        DA(v->mh_vals, 2 * nB);
+        DA(v->mh_hist, radix_hist_entries((int)nB));
+        DA(v->mh_off, P + 1);
+        DA(v->mh_hitn, nB);
+    }
 #undef DA
     V.R_main = v->R_main;
     V.err = v->err;
@@ -477,6 +533,13 @@ int adgi_create_volume(const adgi_volume_desc* desc, void* cuda_stream, adgi_vol
     CKV(cudaMemsetAsync(v->W, 0, P * 4, s));
     CKV(cudaMemsetAsync(v->shadow_ctr, 0, 8, s));
     CKV(cudaMemsetAsync(v->err, 0, 4, s));
+    std::vector<float> mh_tab;
+    if (d.sampler == 1) {
+        mh_tables(mh_tab);
+        CKV(cudaMemcpyAsync(v->mh_tab, mh_tab.data(), sizeof(float) * mh_tab.size(), cudaMemcpyHostToDevice, s));
+        CKV(cudaMemsetAsync(v->mh_off, 0, 4 * (P + 1), s));
+        v->mh_ord = v->mh_vals;
+    }
     v->shadow_blocks = shadow_grid_blocks(0);
     CKV(cudaEventCreate(&v->ev0));
     CKV(cudaEventCreate(&v->ev1));
@@ -654,6 +717,29 @@ int ensure_bvh(adgi_volume v, cudaStream_t s, bool moving_too = true)
     return ADGI_OK;
 }
 
+MhBufs mh_bufs(adgi_volume v)
+{
+    MhBufs M{};
+    M.n_samples = v->mh_B;
+    M.n_chains = v->mh_C;
+    M.alpha = v->desc.alpha;
+    M.inv_q2 = 1.0f / 1046529.0f;
+    M.nq = v->mh_tab;
+    M.ex = v->mh_tab ? v->mh_tab + kMhNq : nullptr;
+    M.chain = v->mh_chain;
+    M.smp = v->mh_smp;
+    M.keys[0] = v->mh_keys;
+    M.keys[1] = v->mh_keys ? v->mh_keys + v->mh_B : nullptr;
+    M.vals[0] = v->mh_vals;
+    M.vals[1] = v->mh_vals ? v->mh_vals + v->mh_B : nullptr;
+    M.hist = v->mh_hist;
+    M.off = v->mh_off;
+    M.lut_c = v->lut_c;
+    M.qv = v->qv;
+    M.irr = v->irr;
+    return M;
+}
+
 SceneDev scene_view(adgi_volume v)
 {
     SceneDev S;
@@ -718,6 +804,12 @@ int prepare_update(adgi_volume v, const adgi_frame* f, FrameDev& fd, bool* graph
         v->job_cap = need;
         stale = true;
     }
+    if (v->desc.sampler == 1 && !v->mh_live) {  // first update: the chains' first states, before any capture
+        const uint64_t key = splitmix(splitmix((f->seed ^ kMhInitSalt) ^ kMhSalt) ^ 0ull);
+        CK(launch_mh_init(V, mh_bufs(v), key, s));
+        v->mh_live = true;
+        stale = true;
+    }
     if (graph_stale) *graph_stale = stale;
     return ADGI_OK;
 }
@@ -752,12 +844,15 @@ int enqueue_update(adgi_volume v, const FrameDev& fd, cudaStream_t s, bool phase
     // stream, beside the traversals, and join before the blend
     BlendBufs Bb{v->off,  v->sf,  v->pil_rec, v->m_rec,
                  v->irr,  v->dep, v->dep_n,   carve_blend_plan(v->plan, V.rays_max - 8, V.Ti, V.Td), v->tex_src};
-    CK(cudaEventRecord(v->fork, s));
-    CK(cudaStreamWaitEvent(v->side, v->fork, 0));
-    if (phases) CK(cudaEventRecord(v->plq[0], v->side));
-    CK(launch_blend_plan(V, v->fdev, v->sf, Bb.plan, v->side));
-    if (phases) CK(cudaEventRecord(v->plq[1], v->side));
-    CK(cudaEventRecord(v->join, v->side));
+    const bool mh = v->desc.sampler == 1;
+    if (!mh) {
+        CK(cudaEventRecord(v->fork, s));
+        CK(cudaStreamWaitEvent(v->side, v->fork, 0));
+        if (phases) CK(cudaEventRecord(v->plq[0], v->side));
+        CK(launch_blend_plan(V, v->fdev, v->sf, Bb.plan, v->side));
+        if (phases) CK(cudaEventRecord(v->plq[1], v->side));
+        CK(cudaEventRecord(v->join, v->side));
+    }
     SceneDev S = scene_view(v);
     const FrameDev* FD = v->fdev;
     CK(cudaMemsetAsync(v->shadow_ctr, 0, 8, s));
@@ -777,16 +872,36 @@ int enqueue_update(adgi_volume v, const FrameDev& fd, cudaStream_t s, bool phase
     // 3. allocation
     PHASE(4);
     CK(launch_allocate(v->W, V.P, V.rays_avg, V.m0, V.rays_max, v->n, v->off, s));
-    // 4-5. adaptive rays: trace, shade
-    PHASE(5);
-    CK(launch_main_trace(V, FD, S, v->off, v->sf, v->R_main, v->m_hit, T, s));
-    PHASE(6);
-    CK(launch_shade(V, FD, S, 1, v->R_main, v->off, v->sf, v->irr, v->dep, v->m_hit, v->m_rec, nullptr, W, T, s,
-                    phases ? v->shq + 2 : nullptr));
-    // 6. blend (after every read of the previous atlases)
-    PHASE(7);
-    CK(cudaStreamWaitEvent(s, v->join, 0));
-    CK(launch_blend(V, FD, Bb, T, s));
+    if (mh) {
+        // 3'. Metropolis chains draw the samples; group them by probe
+        MhBufs M = mh_bufs(v);
+        const uint32_t* ord = nullptr;
+        CK(launch_mh_chain(V, FD, M, s));
+        CK(launch_mh_group(V, M, s, &ord));
+        v->mh_ord = ord;
+        // 4'-5'. the samples' +w and -w rays; shading of the +w rays
+        PHASE(5);
+        CK(launch_mh_trace(V, S, M, ord, v->m_hit, v->mh_hitn, T, s));
+        PHASE(6);
+        CK(launch_shade(V, FD, S, 2, M.n_samples, ord, v->mh_smp, v->irr, v->dep, v->m_hit, v->m_rec, nullptr, W, T,
+                        s, phases ? v->shq + 2 : nullptr));
+        // 6'. blend of the probes' samples
+        PHASE(7);
+        MhBlendBufs MB{M.n_samples, v->mh_off, ord,    v->mh_smp, v->m_rec, v->mh_hitn,
+                       v->pil_rec,  v->irr,    v->dep, v->dep_n,  v->tex_src};
+        CK(launch_mh_blend(V, FD, MB, s));
+    } else {
+        // 4-5. adaptive rays: trace, shade
+        PHASE(5);
+        CK(launch_main_trace(V, FD, S, v->off, v->sf, v->R_main, v->m_hit, T, s));
+        PHASE(6);
+        CK(launch_shade(V, FD, S, 1, v->R_main, v->off, v->sf, v->irr, v->dep, v->m_hit, v->m_rec, nullptr, W, T, s,
+                        phases ? v->shq + 2 : nullptr));
+        // 6. blend (after every read of the previous atlases)
+        PHASE(7);
+        CK(cudaStreamWaitEvent(s, v->join, 0));
+        CK(launch_blend(V, FD, Bb, T, s));
+    }
     PHASE(8);
 #undef PHASE
     if (phases) {
@@ -1016,6 +1131,7 @@ int adgi_autotune(adgi_volume v, const adgi_frame* f, int32_t reps, adgi_tuning*
 {
     if (!v || !f) return fail(ADGI_ERR_INVALID_ARG, "NULL argument");
     if (v->frames == 0) return fail(ADGI_ERR_INVALID_ARG, "autotune needs one update first");
+    if (v->desc.sampler == 1) return fail(ADGI_ERR_INVALID_ARG, "autotune: not available with the Metropolis sampler");
     if (reps < 1) reps = 1;
     FrameDev fd;
     int rc = prepare_update(v, f, fd, nullptr);
@@ -1151,7 +1267,8 @@ int adgi_get_stats(adgi_volume v, adgi_stats* out)
     CK(cudaStreamSynchronize(v->stream));
     std::memset(out, 0, sizeof(*out));
     out->frames = v->frames;
-    out->rays_per_update = (uint64_t)v->V.P * (uint64_t)v->V.rays_avg;
+    out->rays_per_update = v->desc.sampler == 1 ? (uint64_t)v->V.P * 8u + 2u * (uint64_t)v->mh_B
+                                                : (uint64_t)v->V.P * (uint64_t)v->V.rays_avg;
     out->pilot_rays = (uint64_t)v->V.P * 8u;
     unsigned long long sc = 0;
     CK(cudaMemcpy(&sc, v->shadow_ctr, 8, cudaMemcpyDeviceToHost));
@@ -1169,7 +1286,7 @@ int adgi_get_stats(adgi_volume v, adgi_stats* out)
         out->ms_last_update = ms;
         for (int i = 0; i < 8; ++i) CK(cudaEventElapsedTime(&out->ms_phase[i], v->ph[i], v->ph[i + 1]));
         for (int i = 0; i < 2; ++i) CK(cudaEventElapsedTime(&out->ms_shadow[i], v->shq[2 * i], v->shq[2 * i + 1]));
-        CK(cudaEventElapsedTime(&out->ms_blend_plan, v->plq[0], v->plq[1]));
+        if (v->desc.sampler != 1) CK(cudaEventElapsedTime(&out->ms_blend_plan, v->plq[0], v->plq[1]));
     }
     return ADGI_OK;
 }
@@ -1205,6 +1322,18 @@ int adgi_state_bytes(adgi_volume v, int32_t which, uint64_t* bytes)
     case ADGI_STATE_BVH_TRIS: *bytes = 48 * (uint64_t)v->ns; break;
     case ADGI_STATE_MOVING_BVH_NODES: *bytes = 64 * (uint64_t)(v->nd > 1 ? v->nd - 1 : 1); break;
     case ADGI_STATE_MOVING_BVH_TRIS: *bytes = 48 * (uint64_t)v->nd; break;
+    case ADGI_STATE_MH_CHAINS:
+    case ADGI_STATE_MH_SAMPLES:
+    case ADGI_STATE_MH_ORDER:
+    case ADGI_STATE_MH_OFF:
+    case ADGI_STATE_MH_HIT_NEG:
+        if (v->desc.sampler != 1) return fail(ADGI_ERR_INVALID_ARG, "not a Metropolis volume");
+        *bytes = which == ADGI_STATE_MH_CHAINS    ? 32 * (uint64_t)v->mh_C
+                 : which == ADGI_STATE_MH_SAMPLES ? 16 * (uint64_t)v->mh_B
+                 : which == ADGI_STATE_MH_ORDER   ? 4 * (uint64_t)v->mh_B
+                 : which == ADGI_STATE_MH_OFF     ? 4 * (P + 1)
+                                                  : 8 * (uint64_t)v->mh_B;
+        break;
     default: return fail(ADGI_ERR_INVALID_ARG, "unknown state");
     }
     return ADGI_OK;
@@ -1248,6 +1377,11 @@ int adgi_read_state(adgi_volume v, int32_t which, void* dst, uint64_t bytes)
     case ADGI_STATE_BVH_TRIS: src = v->sbvh.tri_v; count_tris = v->ns; break;
     case ADGI_STATE_MOVING_BVH_NODES: src = v->dbvh.nodes; count_tris = v->nd; break;
     case ADGI_STATE_MOVING_BVH_TRIS: src = v->dbvh.tri_v; count_tris = v->nd; break;
+    case ADGI_STATE_MH_CHAINS: src = v->mh_chain; break;
+    case ADGI_STATE_MH_SAMPLES: src = v->mh_smp; break;
+    case ADGI_STATE_MH_ORDER: src = v->mh_ord; break;
+    case ADGI_STATE_MH_OFF: src = v->mh_off; break;
+    case ADGI_STATE_MH_HIT_NEG: src = v->mh_hitn; break;
     }
     bool nodes = which == ADGI_STATE_BVH_NODES || which == ADGI_STATE_MOVING_BVH_NODES;
     if (count_tris >= 0 && (count_tris == 0 || (nodes && count_tris < 2))) {
@@ -1296,6 +1430,7 @@ int adgi_count_traversal(adgi_volume v, const adgi_frame* f, uint64_t* counts)
 {
     if (!v || !f || !counts) return fail(ADGI_ERR_INVALID_ARG, "NULL argument");
     if (!v->has_scene) return fail(ADGI_ERR_NO_SCENE, "no scene");
+    if (v->desc.sampler == 1) return fail(ADGI_ERR_INVALID_ARG, "count_traversal: not available with the Metropolis sampler");
     if (f->n_lights < 0 || f->n_lights > kMaxLights || (f->n_lights > 0 && !f->lights))
         return fail(ADGI_ERR_INVALID_ARG, "bad light list");
     cudaStream_t s = v->stream;

@@ -86,6 +86,55 @@ struct BlendBufs {
     const uint16_t* src;  // [Ti^2 + Td^2]: the texel each texel copies (itself, or a border's fold partner)
 };
 
+// Metropolis sampling of the adaptive rays (sampler.cu): the chains' state
+// and this frame's samples, grouped by probe.
+constexpr int kMhSteps = 8;                        // M: random-walk steps per chain per frame
+constexpr int kMhBurn = 2;                         // K: leading steps whose states are not used
+constexpr int kMhPer = kMhSteps - kMhBurn - 1;     // samples per chain per frame (steps K+1..M-1)
+constexpr int kMhNq = 4096;                        // normal quantile table entries
+constexpr int kMhEx = 1024;                        // exp table entries
+
+struct MhBufs {
+    uint32_t n_samples;       // B = (rays_avg - 8) * P
+    uint32_t n_chains;        // ceil(B / kMhPer)
+    float alpha;              // confidence of the cached irradiance in the guide
+    float inv_q2;             // 1 / 1023^2 (FP32)
+    const float* nq;          // [4096] Phi^-1((i + 0.5) / 4096)
+    const float* ex;          // [1024] exp(k / 1023)
+    float4* chain;            // [2C]: {g.xyz, u.x} then {u.y, -, -, -}
+    float4* smp;              // [B] sample direction xyz, probe (int bits) in .w, chain order
+    uint64_t* keys[2];        // radix sort of the samples by probe
+    uint32_t* vals[2];
+    uint32_t* hist;
+    uint32_t* off;            // [P+1] first grouped sample of each probe
+    const uint16_t* lut_c;
+    const uint16_t* qv;       // this frame's q_v per (probe, octant)
+    const void* irr;          // previous irradiance atlas (the cache term of the guide)
+};
+
+cudaError_t launch_mh_init(const VolConst& V, const MhBufs& M, uint64_t init_key, cudaStream_t s);
+cudaError_t launch_mh_chain(const VolConst& V, const FrameDev* FD, const MhBufs& M, cudaStream_t s);
+// group the samples by probe (stable: sample order inside a probe); *ord receives the order
+cudaError_t launch_mh_group(const VolConst& V, const MhBufs& M, cudaStream_t s, const uint32_t** ord);
+// the +w rays to hit_pos[0..B), the -w rays to hit_neg[0..B), in grouped order
+cudaError_t launch_mh_trace(const VolConst& V, const SceneDev& S, const MhBufs& M, const uint32_t* ord,
+                            int2* hit_pos, int2* hit_neg, const Tuning& T, cudaStream_t s);
+
+struct MhBlendBufs {
+    uint32_t n;               // samples
+    const uint32_t* off;      // [P+1] grouped sample ranges
+    const uint32_t* ord;      // [B] sample at each grouped position
+    const float4* smp;        // [B] samples, chain order
+    const float4* rec;        // [B] +w records, grouped order
+    const int2* hit_neg;      // [B] -w hits, grouped order
+    const float4* pil_rec;
+    void* irr;
+    void* dep;
+    uint8_t* dep_n;
+    const uint16_t* src;      // border fold table (as BlendBufs::src)
+};
+cudaError_t launch_mh_blend(const VolConst& V, const FrameDev* FD, const MhBlendBufs& B, cudaStream_t s);
+
 cudaError_t launch_set_frame(FrameDev* dst, const FrameDev& src, cudaStream_t s);
 void set_frame_node_params(FrameDev** dst_slot, const FrameDev* src, cudaKernelNodeParams* kp, void** args);
 cudaError_t launch_pilot_trace(const VolConst& V, const FrameDev* FD, const SceneDev& S, int2* hit, const Tuning& T,

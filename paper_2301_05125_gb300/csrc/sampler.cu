@@ -1,0 +1,201 @@
+// sampler.cu -- Metropolis sampling of the adaptive rays (sm_103a).
+//
+// The static form of the paper's adaptive sampling (Sec. "Adaptive sampling -
+// static", Alg. MetropolisStep): instead of a ray count per probe, chains of
+// a random walk over (probe position, direction) draw the frame's B =
+// (rays_avg - 8) * P adaptive samples from the guide
+//     h(x) = exp(min(alpha * g(x) / f_s(x), 1)) * f_s(x),
+//     f_s = q_c(probe) * q_v(probe, octant of w) / 1023^2,
+// g = luminance of the cached irradiance texel of w (previous atlas).
+// A state x = (g, u): g continuous grid coordinates in [0, dims-1]^3 (the
+// probe is the nearest grid point), u octahedral coordinates in [-1, 1]^2.
+// Each frame every chain takes M = 8 steps; a step proposes g + 0.5 N(0,1)
+// per axis and u + sqrt(pi/256) N(0,1) per coordinate, both mirrored into
+// the domain, and accepts when eps <= h(x')/h(x) (always when h(x) = 0).
+// The states after steps K+1..M-1 (K = 2) are the frame's samples.
+//
+// Random numbers: the SplitMix64 counter hash of the pilot rays, keyed by
+// (seed, frame) and counted by (chain, step, component); N(0,1) comes from a
+// table of 4096 quantiles indexed by the top 12 bits, exp from a table of
+// 1024 values at r = floor(1023 r) / 1023.  Every decision is exact FP32, so
+// with the same atlas the chains follow the same path on any correct
+// implementation.
+#include "adgi_internal.cuh"
+#include "bvh.cuh"
+#include "kernels.cuh"
+
+namespace adgi {
+
+namespace {
+
+constexpr float kLumR = 0.2126f, kLumG = 0.7152f, kLumB = 0.0722f;
+constexpr float kStepG = 0.5f;          // proposal sigma in grid units
+constexpr float kStepU = 0.11077321f;   // proposal sigma in octahedral units: sqrt(pi / 256)
+constexpr float k2m24 = 5.9604644775390625e-08f;
+
+__device__ __forceinline__ uint64_t mh_hash(uint64_t key, uint32_t chain, int step, int comp)
+{
+    return splitmix(key ^ (((uint64_t)chain * (kMhSteps + 1) + (uint64_t)step) * 8u + (uint64_t)comp));
+}
+
+__device__ __forceinline__ float mh_unif(uint64_t h) { return fm(__uint2float_rn((uint32_t)(h >> 40)), k2m24); }
+
+// mirror x at the ends of [lo, hi], then clamp
+__device__ __forceinline__ float mh_mirror(float x, float lo, float hi)
+{
+    if (x < lo) x = fa(lo, fs(lo, x));
+    if (x > hi) x = fs(hi, fs(x, hi));
+    return fminf(fmaxf(x, lo), hi);
+}
+
+// nearest probe of grid coordinates g
+__device__ __forceinline__ int mh_probe_of(const VolConst& V, float gx, float gy, float gz)
+{
+    const int ix = min(max((int)floorf(fa(gx, 0.5f)), 0), V.dims[0] - 1);
+    const int iy = min(max((int)floorf(fa(gy, 0.5f)), 0), V.dims[1] - 1);
+    const int iz = min(max((int)floorf(fa(gz, 0.5f)), 0), V.dims[2] - 1);
+    return ix + V.dims[0] * (iy + V.dims[1] * iz);
+}
+
+// unit direction of octahedral coordinates (ux, uy)
+__device__ __forceinline__ float3 mh_oct_dir(float ux, float uy)
+{
+    float x = ux, y = uy;
+    const float z = fs(fs(1.0f, fabsf(x)), fabsf(y));
+    if (z < 0.0f) {
+        const float fx = fm(fs(1.0f, fabsf(uy)), sgnf(ux));
+        const float fy = fm(fs(1.0f, fabsf(ux)), sgnf(uy));
+        x = fx;
+        y = fy;
+    }
+    const float l = fsq(dot3x(x, y, z, x, y, z));
+    return make_float3(fd(x, l), fd(y, l), fd(z, l));
+}
+
+// guide h at state (g, u); also returns the probe and the direction
+__device__ __forceinline__ float mh_guide(const VolConst& V, const FrameConst& F, const MhBufs& M, float gx, float gy,
+                                          float gz, float ux, float uy, int* probe, float3* dir)
+{
+    const int p = mh_probe_of(V, gx, gy, gz);
+    const float3 w = mh_oct_dir(ux, uy);
+    *probe = p;
+    *dir = w;
+    const int o = (w.x < 0.0f ? 1 : 0) | (w.y < 0.0f ? 2 : 0) | (w.z < 0.0f ? 4 : 0);
+    const uint32_t q = qc_of_probe(V, F, M.lut_c, p) * (uint32_t)__ldg(M.qv + (size_t)p * 8 + o);
+    const float f_s = fm(__uint2float_rn(q), M.inv_q2);
+    if (!(f_s > 0.0f)) return 0.0f;
+    const int t = texel_of(oct_encode_x(w), V.n_irr);
+    const float4 e = irr_load(V, M.irr, (size_t)p * V.Ti * V.Ti + t);
+    const float g = fa(fa(fm(kLumR, e.x), fm(kLumG, e.y)), fm(kLumB, e.z));
+    float r = fd(fm(M.alpha, g), f_s);
+    if (!(r < 1.0f)) r = 1.0f;
+    if (r < 0.0f) r = 0.0f;
+    const int k = (int)floorf(fm(r, 1023.0f));
+    return fm(__ldg(M.ex + k), f_s);
+}
+
+// first states: uniform over the domain, from the volume's first frame seed
+__global__ void __launch_bounds__(128) k_mh_init(VolConst V, MhBufs M, uint64_t key)
+{
+    const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= M.n_chains) return;
+    float4 a;
+    a.x = fm(mh_unif(mh_hash(key, c, kMhSteps, 0)), (float)(V.dims[0] - 1));
+    a.y = fm(mh_unif(mh_hash(key, c, kMhSteps, 1)), (float)(V.dims[1] - 1));
+    a.z = fm(mh_unif(mh_hash(key, c, kMhSteps, 2)), (float)(V.dims[2] - 1));
+    a.w = fs(fm(mh_unif(mh_hash(key, c, kMhSteps, 3)), 2.0f), 1.0f);
+    const float uy = fs(fm(mh_unif(mh_hash(key, c, kMhSteps, 4)), 2.0f), 1.0f);
+    M.chain[c] = a;
+    M.chain[M.n_chains + c] = make_float4(uy, 0.f, 0.f, 0.f);
+}
+
+// One chain per thread: this frame's M steps and its samples
+__global__ void __launch_bounds__(128) k_mh_chain(VolConst V, const FrameDev* __restrict__ FD, MhBufs M)
+{
+    const FrameConst& F = FD->F;
+    const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= M.n_chains) return;
+    const float4 a = M.chain[c];
+    float gx = a.x, gy = a.y, gz = a.z, ux = a.w, uy = M.chain[M.n_chains + c].x;
+    const float hx = (float)(V.dims[0] - 1), hy = (float)(V.dims[1] - 1), hz = (float)(V.dims[2] - 1);
+    int p;
+    float3 w;
+    float y = mh_guide(V, F, M, gx, gy, gz, ux, uy, &p, &w);
+    for (int i = 0; i < kMhSteps; ++i) {
+        const float gx2 = mh_mirror(fa(gx, fm(kStepG, __ldg(M.nq + (mh_hash(F.mh_key, c, i, 0) >> 52)))), 0.0f, hx);
+        const float gy2 = mh_mirror(fa(gy, fm(kStepG, __ldg(M.nq + (mh_hash(F.mh_key, c, i, 1) >> 52)))), 0.0f, hy);
+        const float gz2 = mh_mirror(fa(gz, fm(kStepG, __ldg(M.nq + (mh_hash(F.mh_key, c, i, 2) >> 52)))), 0.0f, hz);
+        const float ux2 = mh_mirror(fa(ux, fm(kStepU, __ldg(M.nq + (mh_hash(F.mh_key, c, i, 3) >> 52)))), -1.0f, 1.0f);
+        const float uy2 = mh_mirror(fa(uy, fm(kStepU, __ldg(M.nq + (mh_hash(F.mh_key, c, i, 4) >> 52)))), -1.0f, 1.0f);
+        int p2;
+        float3 w2;
+        const float y2 = mh_guide(V, F, M, gx2, gy2, gz2, ux2, uy2, &p2, &w2);
+        bool take = true;
+        if (y > 0.0f) {
+            const float ratio = fd(y2, y);
+            take = !(ratio < 1.0f && mh_unif(mh_hash(F.mh_key, c, i, 5)) > ratio);
+        }
+        if (take) {
+            gx = gx2, gy = gy2, gz = gz2, ux = ux2, uy = uy2, y = y2, p = p2, w = w2;
+        }
+        if (i > kMhBurn) {
+            const uint32_t sidx = c * kMhPer + (uint32_t)(i - kMhBurn - 1);
+            if (sidx < M.n_samples) {
+                M.smp[sidx] = make_float4(w.x, w.y, w.z, __int_as_float(p));
+                M.keys[0][sidx] = (uint64_t)p;
+                M.vals[0][sidx] = sidx;
+            }
+        }
+    }
+    M.chain[c] = make_float4(gx, gy, gz, ux);
+    M.chain[M.n_chains + c] = make_float4(uy, 0.f, 0.f, 0.f);
+}
+
+// off[p] = first grouped position whose probe is >= p (keys sorted), p in [0, P]
+__global__ void k_mh_offsets(const uint64_t* __restrict__ keys, uint32_t n, int P, uint32_t* __restrict__ off)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p > P) return;
+    uint32_t lo = 0, hi = n;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (__ldg(keys + mid) < (uint64_t)p)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    off[p] = lo;
+}
+
+}  // namespace
+
+cudaError_t launch_mh_init(const VolConst& V, const MhBufs& M, uint64_t init_key, cudaStream_t s)
+{
+    if (M.n_chains == 0) return cudaSuccess;
+    k_mh_init<<<(M.n_chains + 127) / 128, 128, 0, s>>>(V, M, init_key);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mh_chain(const VolConst& V, const FrameDev* FD, const MhBufs& M, cudaStream_t s)
+{
+    if (M.n_chains == 0) return cudaSuccess;
+    k_mh_chain<<<(M.n_chains + 127) / 128, 128, 0, s>>>(V, FD, M);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mh_group(const VolConst& V, const MhBufs& M, cudaStream_t s, const uint32_t** ord)
+{
+    int bits = 0;
+    while (bits < 32 && ((uint64_t)1 << bits) < (uint64_t)V.P) ++bits;
+    int cur = 0;
+    cudaError_t e = radix_sort_pairs(M.keys, M.vals, M.hist, (int)M.n_samples, bits, s, &cur);
+    if (e != cudaSuccess) return e;
+    *ord = M.vals[cur];
+    k_mh_offsets<<<(V.P + 1 + 255) / 256, 256, 0, s>>>(M.keys[cur], M.n_samples, V.P, M.off);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+}  // namespace adgi

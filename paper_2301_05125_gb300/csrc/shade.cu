@@ -33,14 +33,15 @@ __device__ __forceinline__ int probe_of_ray(const uint32_t* __restrict__ off, ui
     return lo;
 }
 
-// The rays of a block: pilot rays (ray r = probe r/8, octant r%8) or adaptive
-// rays (ray r of the prefix offsets off[]).  The block's probe range is found
-// once by two threads.
+// The rays of a block: pilot rays (ray r = probe r/8, octant r%8), adaptive
+// rays (ray r of the prefix offsets off[]; the block's probe range is found
+// once by two threads) or Metropolis samples (ray r = sample off[r], whose
+// direction and probe are sf[off[r]]).
 struct RaySet {
-    int mode;                 // 0 pilot, 1 adaptive
+    int mode;                 // 0 pilot, 1 adaptive, 2 Metropolis samples in grouped order
     uint32_t n;               // rays in the set
-    const uint32_t* off;      // adaptive: prefix offsets
-    const float4* sf;         // adaptive: spherical Fibonacci sets
+    const uint32_t* off;      // adaptive: prefix offsets; samples: the grouped order
+    const float4* sf;         // adaptive: spherical Fibonacci sets; samples: {w.xyz, probe bits}
 };
 
 __device__ __forceinline__ void block_range(const VolConst& V, const RaySet& Rs, int* s_lo, int* s_hi)
@@ -66,6 +67,17 @@ __device__ __forceinline__ bool ray_of(const VolConst& V, const FrameConst& F, c
         slot = r;
         o = probe_pos(V, p);
         d = pilot_dir(F.pilot_key, (uint32_t)p, (int)(r & 7));
+        return true;
+    }
+    if (Rs.mode == 2) {
+        const uint32_t sidx = __ldg(Rs.off + r);
+        if (sidx >= Rs.n) return false;
+        const float4 a = __ldg(Rs.sf + sidx);
+        const int p = __float_as_int(a.w);
+        if (p < 0 || p >= V.P) return false;
+        slot = r;
+        o = probe_pos(V, p);
+        d = make_float3(a.x, a.y, a.z);
         return true;
     }
     int p = probe_of_ray(Rs.off, r, lo, hi);
@@ -187,9 +199,9 @@ __global__ void __launch_bounds__(256) k_shade_finish(VolConst V, const FrameDev
 {
     const FrameConst& F = FD->F;
     const LightSet& L = FD->L;
-    // adaptive rays always carry the multi-bounce term; pilot records are
-    // blended (so need it) only on the first frame of a pair
-    const int bounce = Rs.mode == 1 || F.even;
+    // adaptive rays and samples always carry the multi-bounce term; pilot
+    // records are blended (so need it) only on the first frame of a pair
+    const int bounce = Rs.mode != 0 || F.even;
     __shared__ int s_lo, s_hi;
     block_range(V, Rs, &s_lo, &s_hi);
     const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;

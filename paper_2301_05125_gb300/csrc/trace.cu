@@ -98,6 +98,39 @@ __global__ void __launch_bounds__(256) k_main_trace(VolConst V, const FrameDev* 
     hit[base + i] = make_int2((int)h, __float_as_int(t));
 }
 
+// Metropolis samples, in grouped order: thread r < n traces sample ord[r]
+// along +w into hit_pos[r], thread n + r along -w into hit_neg[r] (the
+// visibility ray of the texel at -w).
+__global__ void __launch_bounds__(256) k_mh_trace(VolConst V, SceneDev S, const float4* __restrict__ smp,
+                                                  const uint32_t* __restrict__ ord, uint32_t n,
+                                                  int2* __restrict__ hit_pos, int2* __restrict__ hit_neg)
+{
+    const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= 2 * n) return;
+    const bool neg = r >= n;
+    const uint32_t q = neg ? r - n : r;
+    const uint32_t sidx = __ldg(ord + q);
+    int2* dst = neg ? hit_neg : hit_pos;
+    const int2 miss = make_int2((int)kMiss, 0x7F800000);
+    if (sidx >= n) {
+        atomicOr(V.err, kErrRayRange);
+        dst[q] = miss;
+        return;
+    }
+    const float4 a = __ldg(smp + sidx);
+    const int p = __float_as_int(a.w);
+    if (p < 0 || p >= V.P) {
+        atomicOr(V.err, kErrRayRange);
+        dst[q] = miss;
+        return;
+    }
+    const float3 d = neg ? make_float3(-a.x, -a.y, -a.z) : make_float3(a.x, a.y, a.z);
+    float t;
+    uint32_t h;
+    trace_closest(S, probe_pos(V, p), d, V.tmin, __int_as_float(0x7F800000), t, h);
+    dst[q] = make_int2((int)h, __float_as_int(t));
+}
+
 // Re-trace the last update's rays with work counters (roofline accounting).
 __global__ void __launch_bounds__(128) k_count(VolConst V, const FrameDev* __restrict__ FD, SceneDev S,
                                                const uint32_t* __restrict__ off, const float4* __restrict__ sf,
@@ -227,6 +260,17 @@ cudaError_t launch_main_trace(const VolConst& V, const FrameDev* FD, const Scene
     if (R == 0) return cudaSuccess;
     const unsigned b = (unsigned)T.trace_block;
     k_main_trace<<<(R + b - 1) / b, b, 0, s>>>(V, FD, S, off, sf, R, hit);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mh_trace(const VolConst& V, const SceneDev& S, const MhBufs& M, const uint32_t* ord,
+                            int2* hit_pos, int2* hit_neg, const Tuning& T, cudaStream_t s)
+{
+    const uint32_t n = M.n_samples;
+    if (n == 0) return cudaSuccess;
+    const unsigned b = (unsigned)T.trace_block;
+    k_mh_trace<<<(2 * n + b - 1) / b, b, 0, s>>>(V, S, M.smp, ord, n, hit_pos, hit_neg);
     count_launches(1);
     return cudaGetLastError();
 }

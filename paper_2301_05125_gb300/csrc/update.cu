@@ -107,17 +107,7 @@ __global__ void __launch_bounds__(128) k_change_weight(VolConst V, const FrameDe
                 f[6] += b.z;
                 f[7] += b.w;
             }
-    uint32_t qc = 1023u;
-    if (F.has_camera) {
-        float3 pp = probe_pos(V, p);
-        float dx = fs(pp.x, F.cam[0]), dy = fs(pp.y, F.cam[1]), dz = fs(pp.z, F.cam[2]);
-        float dist = fsq(dot3x(dx, dy, dz, dx, dy, dz));
-        if (!(dist < F.cam_k)) {
-            float q = fm(fs(dist, F.cam_k), V.qc_scale);
-            uint32_t i = q < 4095.0f ? (uint32_t)floorf(q) : 4095u;
-            qc = __ldg(B.lut_c + i);
-        }
-    }
+    const uint32_t qc = qc_of_probe(V, F, B.lut_c, p);
     uint64_t Wp = 0;
 #pragma unroll
     for (int o = 0; o < 8; ++o) Wp += ((uint64_t)qc * (uint64_t)B.qv[(size_t)p * 8 + o] * (uint64_t)f[o]) >> 20;
@@ -550,6 +540,81 @@ __device__ __forceinline__ void blend_packed(const VolConst& V, const BlendBufs&
     for (int t = lane; t < td2; t += 32) odep[t] = dep_new[__ldg(B.src + ti2 + t)];
 }
 
+// One texel of the batched moving average (Alg. ApproxAlgo + Alg.
+// MovingAvgUpdate): k samples with sums (sx, sy, sz) update {rgb, count}.
+__device__ __forceinline__ float4 irr_texel_blend(float4 v, float sx, float sy, float sz, uint32_t k, float omh)
+{
+    const float kf = (float)k;
+    const float w = fmaxf(omh, __fdividef(kf, v.w + kf));
+    const float ik = __frcp_rn(kf);
+    v.x += w * (sx * ik - v.x);
+    v.y += w * (sy * ik - v.y);
+    v.z += w * (sz * ik - v.z);
+    v.w = fminf(v.w + kf, 255.0f);
+    return v;
+}
+
+// The depth texel stores {mean, variance}; with batch mean m and batch
+// variance vb of k samples (sums s1, s2) the moving average of {d, d^2} becomes
+//   mean' = mean + w (m - mean)
+//   var'  = (1-w) var + w vb + w (1-w) (m - mean)^2
+// (every term non-negative: no cancellation in storage); c is the count.
+__device__ __forceinline__ float2 dep_texel_blend(float2 v, uint32_t& c, float s1, float s2, uint32_t k, float omh)
+{
+    const float kf = (float)k;
+    const float w = fmaxf(omh, __fdividef(kf, (float)c + kf));
+    const float ik = __frcp_rn(kf);
+    const float mb = s1 * ik;
+    const float vb = fmaxf(s2 * ik - mb * mb, 0.0f);
+    const float dm = mb - v.x;
+    v.y = (1.0f - w) * v.y + w * vb + w * (1.0f - w) * dm * dm;
+    v.x += w * dm;
+    c = (uint32_t)fminf((float)c + kf, 255.0f);
+    return v;
+}
+
+// Every texel of probe p's updated tiles (a border texel from its octahedral
+// fold partner src[t]) in the storage format, stored in texel order
+// (coalesced), by one warp.
+__device__ __forceinline__ void store_tiles(const VolConst& V, const FrameConst& F, void* irr, void* dep,
+                                            uint8_t* dep_n, const uint16_t* __restrict__ src, int p,
+                                            const float4* irr_new, const float2* dep_new, const uint8_t* dn_new,
+                                            int lane)
+{
+    const int ti2 = V.Ti * V.Ti, td2 = V.Td * V.Td;
+    const size_t io = (size_t)p * ti2, dof = (size_t)p * td2;
+    const uint64_t srkey = F.pilot_key ^ (F.even ? 0x5352ull : 0x5353ull);
+    for (int t = lane; t < ti2; t += 32) {
+        const float4 v = irr_new[__ldg(src + t)];
+        if (V.fp16 == 2) {
+            __half2* h = reinterpret_cast<__half2*>(irr) + 2 * (io + t);
+            const __half2 h0 = __halves2half2(half_sr(v.x, sr_bits(srkey, p, t, 0)), half_sr(v.y, sr_bits(srkey, p, t, 1)));
+            const __half2 h1 = __halves2half2(half_sr(v.z, sr_bits(srkey, p, t, 2)), __float2half_rn(v.w));
+            *reinterpret_cast<uint2*>(h) = make_uint2(*reinterpret_cast<const uint32_t*>(&h0),
+                                                     *reinterpret_cast<const uint32_t*>(&h1));
+        } else if (V.fp16) {
+            __half2* h = reinterpret_cast<__half2*>(irr) + 2 * (io + t);
+            const __half2 h0 = __floats2half2_rn(v.x, v.y), h1 = __floats2half2_rn(v.z, v.w);
+            *reinterpret_cast<uint2*>(h) = make_uint2(*reinterpret_cast<const uint32_t*>(&h0),
+                                                     *reinterpret_cast<const uint32_t*>(&h1));
+        } else {
+            reinterpret_cast<float4*>(irr)[io + t] = v;
+        }
+    }
+    for (int t = lane; t < td2; t += 32) {
+        const int st = __ldg(src + ti2 + t);
+        const float2 v = dep_new[st];
+        if (V.fp16 == 2)
+            reinterpret_cast<__half2*>(dep)[dof + t] =
+                __halves2half2(half_sr(v.x, sr_bits(srkey, p, t, 4)), half_sr(v.y, sr_bits(srkey, p, t, 5)));
+        else if (V.fp16)
+            reinterpret_cast<__half2*>(dep)[dof + t] = __floats2half2_rn(v.x, v.y);
+        else
+            reinterpret_cast<float2*>(dep)[dof + t] = v;
+        dep_n[dof + t] = dn_new[st];
+    }
+}
+
 __global__ void __launch_bounds__(128) k_blend(VolConst V, const FrameDev* __restrict__ FD, BlendBufs B)
 {
     const FrameConst& F = FD->F;
@@ -645,15 +710,7 @@ __global__ void __launch_bounds__(128) k_blend(VolConst V, const FrameDev* __res
             }
             k += b1 - b0;
         }
-        if (k) {
-            const float kf = (float)k;
-            const float w = fmaxf(omh, __fdividef(kf, v.w + kf));
-            const float ik = __frcp_rn(kf);
-            v.x += w * (sx * ik - v.x);
-            v.y += w * (sy * ik - v.y);
-            v.z += w * (sz * ik - v.z);
-            v.w = fminf(v.w + kf, 255.0f);
-        }
+        if (k) v = irr_texel_blend(v, sx, sy, sz, k, omh);
         irr_new[t] = v;
     }
     for (int q = lane; q < nd * nd; q += 32) {
@@ -687,58 +744,151 @@ __global__ void __launch_bounds__(128) k_blend(VolConst V, const FrameDev* __res
             }
             k += b1 - b0;
         }
-        if (k) {
-            // the texel stores {mean, variance}; with batch mean m and batch
-            // variance vb the moving average of {d, d^2} becomes
-            //   mean' = mean + w (m - mean)
-            //   var'  = (1-w) var + w vb + w (1-w) (m - mean)^2
-            // (every term non-negative: no cancellation in storage)
-            const float kf = (float)k;
-            const float w = fmaxf(omh, __fdividef(kf, (float)c + kf));
-            const float ik = __frcp_rn(kf);
-            const float mb = s1 * ik;
-            const float vb = fmaxf(s2 * ik - mb * mb, 0.0f);
-            const float dm = mb - v.x;
-            v.y = (1.0f - w) * v.y + w * vb + w * (1.0f - w) * dm * dm;
-            v.x += w * dm;
-            c = (uint32_t)fminf((float)c + kf, 255.0f);
-        }
+        if (k) v = dep_texel_blend(v, c, s1, s2, k, omh);
         dep_new[t] = v;
         dn_new[t] = (uint8_t)c;
     }
     __syncwarp();
-    // every texel (a border texel from its octahedral fold partner) in the
-    // storage format, stored in texel order (coalesced)
-    const uint64_t srkey = F.pilot_key ^ (F.even ? 0x5352ull : 0x5353ull);
-    for (int t = lane; t < ti2; t += 32) {
-        const float4 v = irr_new[__ldg(B.src + t)];
-        if (V.fp16 == 2) {
-            __half2* h = reinterpret_cast<__half2*>(B.irr) + 2 * (io + t);
-            const __half2 h0 = __halves2half2(half_sr(v.x, sr_bits(srkey, p, t, 0)), half_sr(v.y, sr_bits(srkey, p, t, 1)));
-            const __half2 h1 = __halves2half2(half_sr(v.z, sr_bits(srkey, p, t, 2)), __float2half_rn(v.w));
-            *reinterpret_cast<uint2*>(h) = make_uint2(*reinterpret_cast<const uint32_t*>(&h0),
-                                                     *reinterpret_cast<const uint32_t*>(&h1));
-        } else if (V.fp16) {
-            __half2* h = reinterpret_cast<__half2*>(B.irr) + 2 * (io + t);
-            const __half2 h0 = __floats2half2_rn(v.x, v.y), h1 = __floats2half2_rn(v.z, v.w);
-            *reinterpret_cast<uint2*>(h) = make_uint2(*reinterpret_cast<const uint32_t*>(&h0),
-                                                     *reinterpret_cast<const uint32_t*>(&h1));
-        } else {
-            reinterpret_cast<float4*>(B.irr)[io + t] = v;
+    store_tiles(V, F, B.irr, B.dep, B.dep_n, B.src, p, irr_new, dep_new, dn_new, lane);
+}
+
+// ---- Metropolis samples (sampler.cu): one warp per probe tile.  The
+// samples of probe p are contiguous in grouped order (sample order inside the
+// probe).  Sample s adds its +w radiance to the irradiance texel of w and the
+// distance along -w to the visibility texel of -w (the extra ray of the
+// static adaptive sampling); the pilots come first on the first frame of a
+// pair.  Per texel the sums run in that order; then the batched moving
+// average and the stores of k_blend.
+struct MhLayout {
+    uint32_t acc_i, acc_d, cnt_d, dn, e_rec, e_key, total;
+};
+
+__host__ __device__ inline MhLayout mh_layout(int Ti, int Td)
+{
+    const uint32_t ti2 = (uint32_t)(Ti * Ti), td2 = (uint32_t)(Td * Td);
+    MhLayout L;
+    uint32_t o = 0;
+    L.acc_i = o, o += al16(16 * ti2);  // {sum r, g, b, count}, then the updated texel
+    L.acc_d = o, o += al16(8 * td2);   // {sum d, sum d^2}, then the updated texel
+    L.cnt_d = o, o += al16(4 * td2);
+    L.dn = o, o += al16(td2);
+    L.e_rec = o, o += 16 * 32;  // one chunk of samples: {r, g, b, depth}
+    L.e_key = o, o += 8 * 32;   // {irradiance texel, visibility texel}
+    L.total = o;
+    return L;
+}
+
+// add a chunk of cnt samples in order; the lane owning texel t (t % 32) adds
+__device__ __forceinline__ void mh_accumulate(const float4* e_rec, const int2* e_key, int cnt, float4* acc_i,
+                                              float2* acc_d, uint32_t* cnt_d, int lane)
+{
+    for (int j = 0; j < cnt; ++j) {
+        const int2 kk = e_key[j];
+        const float4 r = e_rec[j];
+        if (kk.x >= 0 && (kk.x & 31) == lane) {
+            float4 a = acc_i[kk.x];
+            a.x += r.x;
+            a.y += r.y;
+            a.z += r.z;
+            a.w += 1.0f;
+            acc_i[kk.x] = a;
+        }
+        if (kk.y >= 0 && (kk.y & 31) == lane) {
+            float2 d = acc_d[kk.y];
+            d.x += r.w;
+            d.y += r.w * r.w;
+            acc_d[kk.y] = d;
+            cnt_d[kk.y] += 1u;
         }
     }
-    for (int t = lane; t < td2; t += 32) {
-        const int src = __ldg(B.src + ti2 + t);
-        const float2 v = dep_new[src];
-        if (V.fp16 == 2)
-            reinterpret_cast<__half2*>(B.dep)[dof + t] =
-                __halves2half2(half_sr(v.x, sr_bits(srkey, p, t, 4)), half_sr(v.y, sr_bits(srkey, p, t, 5)));
-        else if (V.fp16)
-            reinterpret_cast<__half2*>(B.dep)[dof + t] = __floats2half2_rn(v.x, v.y);
-        else
-            reinterpret_cast<float2*>(B.dep)[dof + t] = v;
-        B.dep_n[dof + t] = dn_new[src];
+}
+
+__global__ void __launch_bounds__(128) k_mh_blend(VolConst V, const FrameDev* __restrict__ FD, MhBlendBufs B)
+{
+    const FrameConst& F = FD->F;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int p = blockIdx.x * (blockDim.x >> 5) + wib;
+    if (p >= V.P) return;  // the whole warp
+    const uint32_t b0 = __ldg(B.off + p);
+    uint32_t b1 = __ldg(B.off + p + 1);
+    if (b1 < b0 || b1 > B.n) {
+        if (lane == 0) atomicOr(V.err, kErrRayRange);
+        b1 = b0;
     }
+    const int npil = F.even ? kPilots : 0;
+    if (b1 == b0 && npil == 0) return;  // untouched tile
+    const int Ti = V.Ti, Td = V.Td, ni = V.n_irr, nd = V.n_dep;
+    const int ti2 = Ti * Ti, td2 = Td * Td;
+    const MhLayout L = mh_layout(Ti, Td);
+    unsigned char* ws = smem + (size_t)wib * L.total;
+    float4* acc_i = reinterpret_cast<float4*>(ws + L.acc_i);
+    float2* acc_d = reinterpret_cast<float2*>(ws + L.acc_d);
+    uint32_t* cnt_d = reinterpret_cast<uint32_t*>(ws + L.cnt_d);
+    uint8_t* dn = ws + L.dn;
+    float4* e_rec = reinterpret_cast<float4*>(ws + L.e_rec);
+    int2* e_key = reinterpret_cast<int2*>(ws + L.e_key);
+    for (int t = lane; t < ti2; t += 32) acc_i[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int t = lane; t < td2; t += 32) {
+        acc_d[t] = make_float2(0.f, 0.f);
+        cnt_d[t] = 0u;
+    }
+    if (npil) {
+        if (lane < kPilots) {
+            e_rec[lane] = __ldg(B.pil_rec + (size_t)p * kPilots + lane);
+            const float2 e = oct_encode_x(pilot_dir(F.pilot_key, (uint32_t)p, lane));
+            e_key[lane] = make_int2(texel_of(e, ni), texel_of(e, nd));
+        }
+        __syncwarp();
+        mh_accumulate(e_rec, e_key, kPilots, acc_i, acc_d, cnt_d, lane);
+        __syncwarp();
+    }
+    for (uint32_t c0 = b0; c0 < b1; c0 += 32) {
+        const uint32_t q = c0 + (uint32_t)lane;
+        if (q < b1) {
+            const uint32_t sidx = __ldg(B.ord + q);
+            int2 key = make_int2(-1, -1);
+            float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (sidx < B.n) {
+                const float4 a = __ldg(B.smp + sidx);
+                const float4 x = __ldg(B.rec + q);
+                const int2 hn = __ldg(B.hit_neg + q);
+                const float dep = (uint32_t)hn.x == kMiss ? V.depth_max : fminf(__int_as_float(hn.y), V.depth_max);
+                r = make_float4(x.x, x.y, x.z, dep);
+                key = make_int2(texel_of(oct_encode_x(make_float3(a.x, a.y, a.z)), ni),
+                                texel_of(oct_encode_x(make_float3(-a.x, -a.y, -a.z)), nd));
+            } else {
+                atomicOr(V.err, kErrRayRange);
+            }
+            e_rec[lane] = r;
+            e_key[lane] = key;
+        }
+        __syncwarp();
+        mh_accumulate(e_rec, e_key, (int)min(32u, b1 - c0), acc_i, acc_d, cnt_d, lane);
+        __syncwarp();
+    }
+    const float omh = 1.0f - V.hyst;
+    const float rni = 1.0f / (float)ni, rnd = 1.0f / (float)nd;
+    const size_t io = (size_t)p * ti2, dof = (size_t)p * td2;
+    for (int q = lane; q < ni * ni; q += 32) {
+        const int r = tile_row(q, rni), t = (r + 1) * Ti + (q - r * ni) + 1;
+        const float4 a = acc_i[t];
+        float4 v = irr_load(V, B.irr, io + t);
+        if (a.w > 0.0f) v = irr_texel_blend(v, a.x, a.y, a.z, (uint32_t)a.w, omh);
+        acc_i[t] = v;
+    }
+    for (int q = lane; q < nd * nd; q += 32) {
+        const int r = tile_row(q, rnd), t = (r + 1) * Td + (q - r * nd) + 1;
+        const float2 a = acc_d[t];
+        const uint32_t k = cnt_d[t];
+        float2 v = dep_load(V, B.dep, dof + t);
+        uint32_t c = B.dep_n[dof + t];
+        if (k) v = dep_texel_blend(v, c, a.x, a.y, k, omh);
+        acc_d[t] = v;
+        dn[t] = (uint8_t)c;
+    }
+    __syncwarp();
+    store_tiles(V, F, B.irr, B.dep, B.dep_n, B.src, p, acc_i, acc_d, dn, lane);
 }
 
 // ============================================================== query
@@ -822,6 +972,20 @@ cudaError_t launch_blend(const VolConst& V, const FrameDev* FD, const BlendBufs&
         if (e != cudaSuccess) return e;
     }
     k_blend<<<(V.P + wpb - 1) / wpb, 32 * wpb, sm, s>>>(V, FD, B);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mh_blend(const VolConst& V, const FrameDev* FD, const MhBlendBufs& B, cudaStream_t s)
+{
+    const size_t per = mh_layout(V.Ti, V.Td).total;
+    const int wpb = std::max(1, std::min(4, (int)((227u * 1024u) / per)));
+    const size_t sm = per * (size_t)wpb;
+    if (sm > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_mh_blend, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+    }
+    k_mh_blend<<<(V.P + wpb - 1) / wpb, 32 * wpb, sm, s>>>(V, FD, B);
     count_launches(1);
     return cudaGetLastError();
 }

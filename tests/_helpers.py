@@ -18,7 +18,8 @@ def oracle_volume(O, w, **over):
     vd.update(over)
     v = O.OracleVolume(vd["origin"], vd["spacing"], vd["dims"], vd["irr_interior"], vd["depth_interior"],
                        vd["rays_avg"], vd["rays_min"], vd["rays_max"], vd["hysteresis"], vd["depth_max"],
-                       vd["tr_theta"], packed=int(vd.get("atlas_fp16", 0)) == 3)
+                       vd["tr_theta"], packed=int(vd.get("atlas_fp16", 0)) == 3, sampler=int(vd.get("sampler", 0)),
+                       alpha=float(vd.get("alpha", 1.0)))
     v.set_scene(w.verts, w.idx, w.albedo)
     return v
 
