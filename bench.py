@@ -42,6 +42,7 @@ OPS_TRI = 55
 # and depth counts (256 B); plus 16 B per blended ray record read.
 TILE_BYTES_FP32 = 2 * (8 * 8 * 16 + 16 * 16 * 8 + 16 * 16)
 REC_BYTES = 16
+MH_REC_BYTES = 40
 
 
 def _peaks():
@@ -166,7 +167,7 @@ def _workload(name, seed):
     return {"tunnel_city": S.tunnel_city, "box_room": S.box_room, "scaled": S.scaled}[name](seed)
 
 
-def _cpu_baseline(w, budget_s=20.0, threads=None, steps=None):
+def _cpu_baseline(w, budget_s=20.0, threads=None, steps=None, sampler=0, alpha=1.0):
     """The oracle as it stands on the host cores: full updates of the same
     workload until the time budget is spent (at least one)."""
     from oracle import oracle as O
@@ -175,7 +176,7 @@ def _cpu_baseline(w, budget_s=20.0, threads=None, steps=None):
     vd = w.volume
     ov = O.OracleVolume(vd["origin"], vd["spacing"], vd["dims"], vd["irr_interior"], vd["depth_interior"],
                         vd["rays_avg"], vd["rays_min"], vd["rays_max"], vd["hysteresis"], vd["depth_max"],
-                        vd["tr_theta"], threads=threads)
+                        vd["tr_theta"], threads=threads, sampler=sampler, alpha=alpha)
     ov.set_scene(w.verts, w.idx, w.albedo)
     times = []
     f = 0
@@ -501,6 +502,49 @@ def _precision_section(args, adgi, torch, dev):
     return out
 
 
+def _metropolis_section(args, adgi, torch, dev):
+    """Metropolis form (sampler = 1, alpha = 1) on the same workload: chains
+    draw the (rays_avg - 8) * P adaptive samples over (probe, direction),
+    each tracing +w (radiance) and -w (visibility); timed per update with
+    the L2 flushed between updates, like the headline line."""
+    w = _workload(args.workload, args.seed)
+    vd = dict(w.volume)
+    vd["sampler"], vd["alpha"] = 1, 1.0
+    stream = torch.cuda.Stream(device=dev)
+    v = adgi.Volume(stream=stream.cuda_stream, **vd)
+    v.set_scene(w.verts, w.idx, w.albedo)
+    adgi.adgi_enable_timing(v.h, True)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    have_dyn = w.dyn_at is not None and w.dyn_count > 0
+    warm, steps = 3, max(4, min(args.steps, 30))
+    ms, ph, sh = [], {k: [] for k in adgi.PHASES}, []
+    for f in range(warm + steps):
+        if have_dyn:
+            v.move_vertices(w.dyn_first, np.ascontiguousarray(w.dyn_at(f), np.float32))
+        with torch.cuda.stream(stream):
+            flush.fill_(float(f))
+        v.update(f, w.seed, w.lights_at(f), w.sky)
+        st = v.stats()
+        if f >= warm:
+            ms.append(st.ms_last_update)
+            for i, name in enumerate(adgi.PHASES):
+                ph[name].append(st.ms_phase[i])
+            sh.append(st.ms_shadow[1])
+    st = v.stats()
+    rays = int(st.rays_per_update)
+    m = float(np.mean(ms))
+    out = {"workload": w.name, "probes": w.n_probes, "alpha": 1.0, "samples_per_update": rays // 2 - 4 * w.n_probes,
+           "rays_per_update": rays, "ms_per_update": m, "rays_per_s": rays / (m / 1e3),
+           "rays_incl_shadow_per_s": (rays + int(st.shadow_rays)) / (m / 1e3),
+           "phases_ms": {k: float(np.mean(x)) for k, x in ph.items()},
+           "k_shadow_ms (samples)": float(np.mean(sh)), "frames_timed": steps, "device_bytes": int(st.device_bytes),
+           "note": "rays = 8 pilots per probe + a +w and a -w ray per sample; the allocation phase also holds "
+                   "the chain steps and the grouping of the samples by probe (python bench.py --sampler times "
+                   "this form as the main line, with its roofline)"}
+    v.close()
+    return out
+
+
 def run_ours(args):
     import torch
 
@@ -525,6 +569,8 @@ def run_ours(args):
     vd = dict(w.volume)
     if args.fp16:
         vd["atlas_fp16"] = 1
+    if args.sampler:
+        vd["sampler"], vd["alpha"] = 1, args.alpha
     stream = torch.cuda.Stream(device=dev)
     vol = adgi.Volume(stream=stream.cuda_stream, **vd)
     vol.set_scene(w.verts, w.idx, w.albedo)
@@ -578,9 +624,11 @@ def run_ours(args):
         for i in range(2):
             shadow_ms[i].append(st.ms_shadow[i])
         plan_ms.append(st.ms_blend_plan)
-        n = vol.n()
-        m = n.astype(np.int64) - 8
         even = f % 2 == 0
+        if args.sampler:  # samples per probe from the grouping
+            m = np.diff(vol.mh_off().astype(np.int64))
+        else:
+            m = vol.n().astype(np.int64) - 8
         tiles_touched.append(vol.P if even else int((m > 0).sum()))
         rays_blended.append(int(m.sum()) + (8 * vol.P if even else 0))
     torch.cuda.synchronize()
@@ -590,19 +638,24 @@ def run_ours(args):
     last_frame = frames[args.warmup + args.steps - 1]
     counts = adgi.adgi_count_traversal(vol.h, last_frame)
     ms_step = _job_ms(float(np.mean(dev_ms)), ws, dev)
-    rays = w.rays_per_update
+    rays = int(vol.stats().rays_per_update)  # Metropolis: 8 pilots per probe + a +w and a -w ray per sample
     value = ws * rays / (ms_step / 1e3)
     hbm, smax_nominal, peak_src = _peaks()
     mean_ph = {k: float(np.mean(v)) for k, v in phases.items()}
     # per-kernel device times (CUDA events on the volume's stream around each
     # kernel) and the counted traversal work of each traversal kernel
-    kern_ms = {"k_main_trace": mean_ph["trace"], "k_shadow (adaptive rays)": float(np.mean(shadow_ms[1])),
+    main_k, blend_k = ("k_mh_trace", "k_mh_blend") if args.sampler else ("k_main_trace", "k_blend")
+    kern_ms = {main_k: mean_ph["trace"], "k_shadow (adaptive rays)": float(np.mean(shadow_ms[1])),
                "k_pilot_trace": mean_ph["pilot_trace"], "k_shadow (pilot rays)": float(np.mean(shadow_ms[0])),
-               "k_blend": mean_ph["blend"], "k_blend_plan (side stream, overlapped)": float(np.mean(plan_ms))}
+               blend_k: mean_ph["blend"]}
+    if args.sampler:
+        kern_ms["allocation + chains + grouping (phase)"] = mean_ph["allocation"]
+    else:
+        kern_ms["k_blend_plan (side stream, overlapped)"] = float(np.mean(plan_ms))
     work = {
         "k_pilot_trace": OPS_BOX * counts[0] + OPS_TRI * counts[1],
         "k_shadow (pilot rays)": OPS_BOX * counts[2] + OPS_TRI * counts[3],
-        "k_main_trace": OPS_BOX * counts[4] + OPS_TRI * counts[5],
+        main_k: OPS_BOX * counts[4] + OPS_TRI * counts[5],
         "k_shadow (adaptive rays)": OPS_BOX * counts[6] + OPS_TRI * counts[7],
     }
     dominant = max((k for k in kern_ms if "side stream" not in k), key=kern_ms.get)
@@ -610,7 +663,9 @@ def run_ours(args):
     # 152 SMs x 128 FP32 lanes x max SM clock
     alu_peak = 152 * 128 * smax_nominal * 1e6 / 1e12  # T lane-ops/s
     tile_bytes = TILE_BYTES_FP32 if not args.fp16 else 2 * (8 * 8 * 8 + 16 * 16 * 4 + 16 * 16)
-    blend_bytes = float(np.mean(tiles_touched)) * tile_bytes + float(np.mean(rays_blended)) * REC_BYTES
+    # a Metropolis sample reads its direction (16 B), its +w record (16 B) and its -w hit (8 B)
+    rec_bytes = MH_REC_BYTES if args.sampler else REC_BYTES
+    blend_bytes = float(np.mean(tiles_touched)) * tile_bytes + float(np.mean(rays_blended)) * rec_bytes
     blend_ach = blend_bytes / (mean_ph["blend"] / 1e3) / 1e9
     if dominant in work:
         ach = work[dominant] / (kern_ms[dominant] / 1e3) / 1e12
@@ -621,10 +676,11 @@ def run_ours(args):
                 "peak_source": "152 SMs x 128 FP32 lanes x %.0f MHz (nominal max clock)" % smax_nominal}
     else:
         roof = {"bound": "hbm", "achieved": blend_ach, "peak": hbm, "unit": "GB/s", "frac": blend_ach / hbm,
-                "traffic": _ncu_traffic("k_blend"), "kernel": "k_blend", "ms": mean_ph["blend"]}
+                "traffic": _ncu_traffic(blend_k), "kernel": blend_k, "ms": mean_ph["blend"]}
     roof_blend = {"bound": "hbm", "achieved": blend_ach, "peak": hbm, "unit": "GB/s", "frac": blend_ach / hbm,
-                  "traffic": _ncu_traffic("k_blend"), "algorithmic_bytes": blend_bytes, "ms": mean_ph["blend"],
-                  "kernel": "k_blend (the per-frame plan runs beforehand on a side stream, see kernels_ms)",
+                  "traffic": _ncu_traffic(blend_k), "algorithmic_bytes": blend_bytes, "ms": mean_ph["blend"],
+                  "kernel": blend_k if args.sampler else
+                  "k_blend (the per-frame plan runs beforehand on a side stream, see kernels_ms)",
                   "peak_source": "%s hbm_gbs" % peak_src}
     # end to end through the C ABI with host buffers
     e2e = None
@@ -662,9 +718,12 @@ def run_ours(args):
     precision = None
     if rank == 0 and not args.no_precision:
         precision = _precision_section(args, adgi, torch, dev)
+    metropolis = None
+    if rank == 0 and not args.no_metropolis and not args.sampler:
+        metropolis = _metropolis_section(args, adgi, torch, dev)
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        times, cores = _cpu_baseline(w, budget_s=args.cpu_budget)
+        times, cores = _cpu_baseline(w, budget_s=args.cpu_budget, sampler=int(args.sampler), alpha=args.alpha)
         cpu = {"value": rays / float(np.mean(times)), "unit": "rays/s", "cores": cores, "kind": "oracle",
                "sample": "%d full oracle update(s) of the same workload (frames 0-%d, every probe and phase, "
                          "BVH rebuild included), host threads = cores" % (len(times), len(times) - 1)}
@@ -676,6 +735,7 @@ def run_ours(args):
             "data": "synthetic (seeded tunnel+city generator standing in for the paper's scenes)",
             "config": {"workload": w.name, "probes": w.n_probes, "rays_per_update": rays,
                        "triangles": w.n_tris, "lights": len(w.lights_at(0)), "atlas": "fp16" if args.fp16 else "fp32",
+                       "sampler": "metropolis (alpha %g)" % args.alpha if args.sampler else "per-probe allocation",
                        "l2": "flushed (256 MB write) between timed steps", "parallelism": "replicas" if ws > 1 else "1 GPU"},
             "latency_ms": {"device_p50": float(np.percentile(dev_ms, 50)), "device_p99": float(np.percentile(dev_ms, 99)),
                            "host_p50": float(np.percentile(host_ms, 50)), "host_p99": float(np.percentile(host_ms, 99))},
@@ -692,6 +752,7 @@ def run_ours(args):
             "batched": batched,
             "serving": serving,
             "precision": precision,
+            "metropolis": metropolis,
             "gpu_launches": int(launches),
             "clocks": clk,
             "wall_s": wall,
@@ -712,11 +773,15 @@ def main():
     ap.add_argument("--workload", default="tunnel_city", choices=["tunnel_city", "box_room", "scaled"])
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--fp16", action="store_true")
+    ap.add_argument("--sampler", action="store_true",
+                    help="time the Metropolis form (sampler = 1) as the main line")
+    ap.add_argument("--alpha", type=float, default=1.0, help="confidence alpha of the Metropolis guide")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-precision", action="store_true")
+    ap.add_argument("--no-metropolis", action="store_true")
     ap.add_argument("--precision-frames", type=int, default=12)
     ap.add_argument("--serve-requests", type=int, default=10000)
     ap.add_argument("--serve-streams", type=int, default=8)

@@ -87,8 +87,7 @@ typedef struct {
                                h = exp(min(alpha g / f_s, 1)) f_s, f_s = q_c q_v / 1023^2, g the
                                cached irradiance luminance (Sec. "Adaptive sampling - static",
                                Alg. MetropolisStep); each sample also traces -w for the visibility
-                               texel at -w.  Not with atlas_fp16 = 3, adgi_autotune or
-                               adgi_count_traversal */
+                               texel at -w.  Not with atlas_fp16 = 3 or adgi_autotune */
     float alpha;            /* sampler = 1: confidence alpha of the cached irradiance, >= 0 */
 } adgi_volume_desc;
 
@@ -262,8 +261,9 @@ int adgi_enable_timing(adgi_volume vol, int32_t enable);
  *                       then {u.y, 0, 0, 0} (g grid coordinates, u octahedral coordinates)
  *   ADGI_STATE_MH_SAMPLES float[B][4]      the last update's samples in chain order (sample
  *                       5c + j is the state after step K+1+j of chain c): {w.xyz, probe (int32 bits)}
- *   ADGI_STATE_MH_ORDER uint32[B]         the sample at each grouped position (by probe, sample
- *                       order inside a probe)
+ *   ADGI_STATE_MH_ORDER uint32[B]         the sample at each grouped position: by probe, then by
+ *                       the Morton index of the direction's cell in a 16 x 16 octahedral grid,
+ *                       then by sample index
  *   ADGI_STATE_MH_OFF   uint32[P+1]       first grouped position of each probe
  *   ADGI_STATE_MH_HIT_NEG int32[B][2]     -w hits in grouped order (as PILOT_HIT); MAIN_HIT and
  *                       MAIN_REC then hold the +w hits and records in grouped order
@@ -321,7 +321,9 @@ int adgi_trace_closest(adgi_volume vol, const float* o, const float* d, int32_t 
  * changing any state.  counts (host uint64[8]) receives, for the pilot rays
  * then for the adaptive rays: nearest-hit box tests, nearest-hit triangle
  * tests, shadow-ray box tests, shadow-ray triangle tests (a BVH node visit
- * tests the boxes of both children: 2 box tests).  Synchronises the stream.
+ * tests the boxes of both children: 2 box tests).  Metropolis volumes: the
+ * adaptive part counts the samples' +w and -w rays and the +w rays' shadow
+ * rays.  Synchronises the stream.
  * Errors: INVALID_ARG, NO_SCENE, CUDA. */
 int adgi_count_traversal(adgi_volume vol, const adgi_frame* frame, uint64_t* counts);
 

@@ -262,6 +262,7 @@ struct adgi_volume_s {
     float* mh_tab = nullptr;           // [4096] normal quantiles, then [1024] exp values
     float4* mh_chain = nullptr;        // [2C] chain states
     float4* mh_smp = nullptr;          // [B] samples, chain order
+    float4* mh_smp_g = nullptr;        // [B] samples, grouped order
     uint64_t* mh_keys = nullptr;       // [2B] radix sort by probe
     uint32_t* mh_vals = nullptr;       // [2B]
     uint32_t* mh_hist = nullptr;
@@ -281,7 +282,7 @@ void free_volume(adgi_volume v)
                     v->G,       v->W,       v->n,      v->off,   v->pil_hit, v->pil_rec, v->pil_lum, v->m_hit,
                     v->m_rec,   v->shadow_ctr, v->verts, v->idx, v->albedo,  v->q_buf, v->err,
                     v->vis,     v->jobs,    v->job_light, v->job_count, v->fdev,
-                    v->mh_tab,  v->mh_chain, v->mh_smp, v->mh_keys, v->mh_vals, v->mh_hist, v->mh_off, v->mh_hitn};
+                    v->mh_tab,  v->mh_chain, v->mh_smp, v->mh_smp_g, v->mh_keys, v->mh_vals, v->mh_hist, v->mh_off, v->mh_hitn};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     v->sbvh.release();
@@ -500,6 +501,7 @@ int adgi_create_volume(const adgi_volume_desc* desc, void* cuda_stream, adgi_vol
         DA(v->mh_tab, (size_t)(kMhNq + kMhEx));
         DA(v->mh_chain, 2 * (size_t)v->mh_C);
         DA(v->mh_smp, nB);
+        DA(v->mh_smp_g, nB);
         DA(v->mh_keys, 2 * nB);
         DA(v->mh_vals, 2 * nB);
         DA(v->mh_hist, radix_hist_entries((int)nB));
@@ -728,6 +730,7 @@ MhBufs mh_bufs(adgi_volume v)
     M.ex = v->mh_tab ? v->mh_tab + kMhNq : nullptr;
     M.chain = v->mh_chain;
     M.smp = v->mh_smp;
+    M.smp_g = v->mh_smp_g;
     M.keys[0] = v->mh_keys;
     M.keys[1] = v->mh_keys ? v->mh_keys + v->mh_B : nullptr;
     M.vals[0] = v->mh_vals;
@@ -881,14 +884,14 @@ int enqueue_update(adgi_volume v, const FrameDev& fd, cudaStream_t s, bool phase
         v->mh_ord = ord;
         // 4'-5'. the samples' +w and -w rays; shading of the +w rays
         PHASE(5);
-        CK(launch_mh_trace(V, S, M, ord, v->m_hit, v->mh_hitn, T, s));
+        CK(launch_mh_trace(V, S, M, v->m_hit, v->mh_hitn, T, s));
         PHASE(6);
-        CK(launch_shade(V, FD, S, 2, M.n_samples, ord, v->mh_smp, v->irr, v->dep, v->m_hit, v->m_rec, nullptr, W, T,
+        CK(launch_shade(V, FD, S, 2, M.n_samples, nullptr, v->mh_smp_g, v->irr, v->dep, v->m_hit, v->m_rec, nullptr, W, T,
                         s, phases ? v->shq + 2 : nullptr));
         // 6'. blend of the probes' samples
         PHASE(7);
-        MhBlendBufs MB{M.n_samples, v->mh_off, ord,    v->mh_smp, v->m_rec, v->mh_hitn,
-                       v->pil_rec,  v->irr,    v->dep, v->dep_n,  v->tex_src};
+        MhBlendBufs MB{M.n_samples, v->mh_off, v->mh_smp_g, v->m_rec, v->mh_hitn,
+                       v->pil_rec,  v->irr,    v->dep,      v->dep_n, v->tex_src};
         CK(launch_mh_blend(V, FD, MB, s));
     } else {
         // 4-5. adaptive rays: trace, shade
@@ -1430,7 +1433,6 @@ int adgi_count_traversal(adgi_volume v, const adgi_frame* f, uint64_t* counts)
 {
     if (!v || !f || !counts) return fail(ADGI_ERR_INVALID_ARG, "NULL argument");
     if (!v->has_scene) return fail(ADGI_ERR_NO_SCENE, "no scene");
-    if (v->desc.sampler == 1) return fail(ADGI_ERR_INVALID_ARG, "count_traversal: not available with the Metropolis sampler");
     if (f->n_lights < 0 || f->n_lights > kMaxLights || (f->n_lights > 0 && !f->lights))
         return fail(ADGI_ERR_INVALID_ARG, "bad light list");
     cudaStream_t s = v->stream;
@@ -1456,7 +1458,9 @@ int adgi_count_traversal(adgi_volume v, const adgi_frame* f, uint64_t* counts)
     if (dalloc(&d, 8, &dummy) != cudaSuccess) return fail(ADGI_ERR_OOM, "counter buffer");
     cudaError_t e = cudaMemsetAsync(d, 0, 64, s);
     if (e == cudaSuccess) e = launch_set_frame(v->fdev, fd, s);
-    if (e == cudaSuccess) e = launch_count(v->V, v->fdev, scene_view(v), v->off, v->sf, v->R_main, d, s);
+    if (e == cudaSuccess)
+        e = v->desc.sampler == 1 ? launch_count(v->V, v->fdev, scene_view(v), v->off, v->sf, 2 * v->mh_B, d, s, v->mh_smp_g)
+                                 : launch_count(v->V, v->fdev, scene_view(v), v->off, v->sf, v->R_main, d, s);
     unsigned long long h[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     if (e == cudaSuccess) e = cudaMemcpyAsync(h, d, 64, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);

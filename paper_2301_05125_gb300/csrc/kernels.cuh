@@ -93,6 +93,7 @@ constexpr int kMhBurn = 2;                         // K: leading steps whose sta
 constexpr int kMhPer = kMhSteps - kMhBurn - 1;     // samples per chain per frame (steps K+1..M-1)
 constexpr int kMhNq = 4096;                        // normal quantile table entries
 constexpr int kMhEx = 1024;                        // exp table entries
+constexpr int kMhCellBits = 8;                     // direction cell below the probe in the grouping key
 
 struct MhBufs {
     uint32_t n_samples;       // B = (rays_avg - 8) * P
@@ -103,6 +104,7 @@ struct MhBufs {
     const float* ex;          // [1024] exp(k / 1023)
     float4* chain;            // [2C]: {g.xyz, u.x} then {u.y, -, -, -}
     float4* smp;              // [B] sample direction xyz, probe (int bits) in .w, chain order
+    float4* smp_g;            // [B] the same, in grouped order
     uint64_t* keys[2];        // radix sort of the samples by probe
     uint32_t* vals[2];
     uint32_t* hist;
@@ -114,17 +116,17 @@ struct MhBufs {
 
 cudaError_t launch_mh_init(const VolConst& V, const MhBufs& M, uint64_t init_key, cudaStream_t s);
 cudaError_t launch_mh_chain(const VolConst& V, const FrameDev* FD, const MhBufs& M, cudaStream_t s);
-// group the samples by probe (stable: sample order inside a probe); *ord receives the order
+// group the samples by probe, then by direction cell (stable: sample order
+// inside a cell); *ord receives the order, M.smp_g the samples in that order
 cudaError_t launch_mh_group(const VolConst& V, const MhBufs& M, cudaStream_t s, const uint32_t** ord);
 // the +w rays to hit_pos[0..B), the -w rays to hit_neg[0..B), in grouped order
-cudaError_t launch_mh_trace(const VolConst& V, const SceneDev& S, const MhBufs& M, const uint32_t* ord,
-                            int2* hit_pos, int2* hit_neg, const Tuning& T, cudaStream_t s);
+cudaError_t launch_mh_trace(const VolConst& V, const SceneDev& S, const MhBufs& M, int2* hit_pos, int2* hit_neg,
+                            const Tuning& T, cudaStream_t s);
 
 struct MhBlendBufs {
     uint32_t n;               // samples
     const uint32_t* off;      // [P+1] grouped sample ranges
-    const uint32_t* ord;      // [B] sample at each grouped position
-    const float4* smp;        // [B] samples, chain order
+    const float4* smp_g;      // [B] samples, grouped order
     const float4* rec;        // [B] +w records, grouped order
     const int2* hit_neg;      // [B] -w hits, grouped order
     const float4* pil_rec;
@@ -146,8 +148,10 @@ cudaError_t launch_shade(const VolConst& V, const FrameDev* FD, const SceneDev& 
                          float4* rec, float* lum, const ShadeWork& W, const Tuning& T, cudaStream_t s,
                          cudaEvent_t* ev_shadow = nullptr);
 unsigned shadow_grid_blocks(int mult);
+// smp_g: the Metropolis samples in grouped order (then R = 2B), else null
 cudaError_t launch_count(const VolConst& V, const FrameDev* FD, const SceneDev& S, const uint32_t* off,
-                         const float4* sf, uint32_t R, unsigned long long* out, cudaStream_t s);
+                         const float4* sf, uint32_t R, unsigned long long* out, cudaStream_t s,
+                         const float4* smp_g = nullptr);
 cudaError_t launch_trace_list(const SceneDev& S, const float* o, const float* d, int n, float tmin, float tmax,
                               float* t_out, int* tri_out, cudaStream_t s);
 

@@ -48,6 +48,20 @@ __device__ __forceinline__ float mh_mirror(float x, float lo, float hi)
     return fminf(fmaxf(x, lo), hi);
 }
 
+// Morton index of the direction's cell in a 16 x 16 grid over the
+// octahedral square: the grouping key below the probe, so that the rays of a
+// probe run in a spatially coherent direction order
+__device__ __forceinline__ uint32_t mh_dir_cell(float3 w)
+{
+    const float2 e = oct_encode_x(w);
+    const uint32_t cx = (uint32_t)min(max((int)floorf(fm(fm(fa(e.x, 1.0f), 0.5f), 16.0f)), 0), 15);
+    const uint32_t cy = (uint32_t)min(max((int)floorf(fm(fm(fa(e.y, 1.0f), 0.5f), 16.0f)), 0), 15);
+    uint32_t m = 0;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) m |= (((cx >> b) & 1u) << (2 * b)) | (((cy >> b) & 1u) << (2 * b + 1));
+    return m;
+}
+
 // nearest probe of grid coordinates g
 __device__ __forceinline__ int mh_probe_of(const VolConst& V, float gx, float gy, float gz)
 {
@@ -142,7 +156,7 @@ __global__ void __launch_bounds__(128) k_mh_chain(VolConst V, const FrameDev* __
             const uint32_t sidx = c * kMhPer + (uint32_t)(i - kMhBurn - 1);
             if (sidx < M.n_samples) {
                 M.smp[sidx] = make_float4(w.x, w.y, w.z, __int_as_float(p));
-                M.keys[0][sidx] = (uint64_t)p;
+                M.keys[0][sidx] = ((uint64_t)p << kMhCellBits) | mh_dir_cell(w);
                 M.vals[0][sidx] = sidx;
             }
         }
@@ -151,20 +165,38 @@ __global__ void __launch_bounds__(128) k_mh_chain(VolConst V, const FrameDev* __
     M.chain[M.n_chains + c] = make_float4(uy, 0.f, 0.f, 0.f);
 }
 
-// off[p] = first grouped position whose probe is >= p (keys sorted), p in [0, P]
+// off[p] = first grouped position whose probe is >= p (keys sorted by probe,
+// then direction cell), p in [0, P]
 __global__ void k_mh_offsets(const uint64_t* __restrict__ keys, uint32_t n, int P, uint32_t* __restrict__ off)
 {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p > P) return;
+    const uint64_t key = (uint64_t)p << kMhCellBits;
     uint32_t lo = 0, hi = n;
     while (lo < hi) {
         const uint32_t mid = (lo + hi) >> 1;
-        if (__ldg(keys + mid) < (uint64_t)p)
+        if (__ldg(keys + mid) < key)
             lo = mid + 1;
         else
             hi = mid;
     }
     off[p] = lo;
+}
+
+// the samples in grouped order: smp_g[q] = smp[ord[q]] (one gather, after
+// which the traces, the shading and the blend read them contiguously)
+__global__ void k_mh_permute(const float4* __restrict__ smp, const uint32_t* __restrict__ ord, uint32_t n,
+                             float4* __restrict__ smp_g, int* err)
+{
+    const uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    const uint32_t s = __ldg(ord + q);
+    if (s >= n) {
+        atomicOr(err, kErrRayRange);
+        smp_g[q] = make_float4(0.f, 0.f, 1.f, __int_as_float(-1));
+        return;
+    }
+    smp_g[q] = __ldg(smp + s);
 }
 
 }  // namespace
@@ -187,14 +219,18 @@ cudaError_t launch_mh_chain(const VolConst& V, const FrameDev* FD, const MhBufs&
 
 cudaError_t launch_mh_group(const VolConst& V, const MhBufs& M, cudaStream_t s, const uint32_t** ord)
 {
-    int bits = 0;
-    while (bits < 32 && ((uint64_t)1 << bits) < (uint64_t)V.P) ++bits;
+    int bits = kMhCellBits;
+    while (bits < 40 && ((uint64_t)1 << bits) < ((uint64_t)V.P << kMhCellBits)) ++bits;
     int cur = 0;
     cudaError_t e = radix_sort_pairs(M.keys, M.vals, M.hist, (int)M.n_samples, bits, s, &cur);
     if (e != cudaSuccess) return e;
     *ord = M.vals[cur];
     k_mh_offsets<<<(V.P + 1 + 255) / 256, 256, 0, s>>>(M.keys[cur], M.n_samples, V.P, M.off);
     count_launches(1);
+    if (M.n_samples) {
+        k_mh_permute<<<(M.n_samples + 255) / 256, 256, 0, s>>>(M.smp, M.vals[cur], M.n_samples, M.smp_g, V.err);
+        count_launches(1);
+    }
     return cudaGetLastError();
 }
 

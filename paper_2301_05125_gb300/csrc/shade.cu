@@ -35,12 +35,12 @@ __device__ __forceinline__ int probe_of_ray(const uint32_t* __restrict__ off, ui
 
 // The rays of a block: pilot rays (ray r = probe r/8, octant r%8), adaptive
 // rays (ray r of the prefix offsets off[]; the block's probe range is found
-// once by two threads) or Metropolis samples (ray r = sample off[r], whose
-// direction and probe are sf[off[r]]).
+// once by two threads) or Metropolis samples (ray r = sample sf[r] of the
+// grouped order).
 struct RaySet {
     int mode;                 // 0 pilot, 1 adaptive, 2 Metropolis samples in grouped order
     uint32_t n;               // rays in the set
-    const uint32_t* off;      // adaptive: prefix offsets; samples: the grouped order
+    const uint32_t* off;      // adaptive: prefix offsets
     const float4* sf;         // adaptive: spherical Fibonacci sets; samples: {w.xyz, probe bits}
 };
 
@@ -70,9 +70,7 @@ __device__ __forceinline__ bool ray_of(const VolConst& V, const FrameConst& F, c
         return true;
     }
     if (Rs.mode == 2) {
-        const uint32_t sidx = __ldg(Rs.off + r);
-        if (sidx >= Rs.n) return false;
-        const float4 a = __ldg(Rs.sf + sidx);
+        const float4 a = __ldg(Rs.sf + r);
         const int p = __float_as_int(a.w);
         if (p < 0 || p >= V.P) return false;
         slot = r;

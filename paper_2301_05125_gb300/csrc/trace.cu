@@ -98,30 +98,22 @@ __global__ void __launch_bounds__(256) k_main_trace(VolConst V, const FrameDev* 
     hit[base + i] = make_int2((int)h, __float_as_int(t));
 }
 
-// Metropolis samples, in grouped order: thread r < n traces sample ord[r]
-// along +w into hit_pos[r], thread n + r along -w into hit_neg[r] (the
-// visibility ray of the texel at -w).
-__global__ void __launch_bounds__(256) k_mh_trace(VolConst V, SceneDev S, const float4* __restrict__ smp,
-                                                  const uint32_t* __restrict__ ord, uint32_t n,
+// Metropolis samples, in grouped order: thread r < n traces sample r along +w
+// into hit_pos[r], thread n + r along -w into hit_neg[r] (the visibility ray
+// of the texel at -w).
+__global__ void __launch_bounds__(256) k_mh_trace(VolConst V, SceneDev S, const float4* __restrict__ smp_g, uint32_t n,
                                                   int2* __restrict__ hit_pos, int2* __restrict__ hit_neg)
 {
     const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= 2 * n) return;
     const bool neg = r >= n;
     const uint32_t q = neg ? r - n : r;
-    const uint32_t sidx = __ldg(ord + q);
     int2* dst = neg ? hit_neg : hit_pos;
-    const int2 miss = make_int2((int)kMiss, 0x7F800000);
-    if (sidx >= n) {
-        atomicOr(V.err, kErrRayRange);
-        dst[q] = miss;
-        return;
-    }
-    const float4 a = __ldg(smp + sidx);
+    const float4 a = __ldg(smp_g + q);
     const int p = __float_as_int(a.w);
     if (p < 0 || p >= V.P) {
         atomicOr(V.err, kErrRayRange);
-        dst[q] = miss;
+        dst[q] = make_int2((int)kMiss, 0x7F800000);
         return;
     }
     const float3 d = neg ? make_float3(-a.x, -a.y, -a.z) : make_float3(a.x, a.y, a.z);
@@ -132,9 +124,12 @@ __global__ void __launch_bounds__(256) k_mh_trace(VolConst V, SceneDev S, const 
 }
 
 // Re-trace the last update's rays with work counters (roofline accounting).
+// Metropolis volumes (smp_g given): the R = 2B rays after the pilots are the
+// samples' +w rays (with their shadow rays) and then their -w rays.
 __global__ void __launch_bounds__(128) k_count(VolConst V, const FrameDev* __restrict__ FD, SceneDev S,
                                                const uint32_t* __restrict__ off, const float4* __restrict__ sf,
-                                               uint32_t R, unsigned long long* __restrict__ out)
+                                               uint32_t R, unsigned long long* __restrict__ out,
+                                               const float4* __restrict__ smp_g)
 {
     const FrameConst& F = FD->F;
     const LightSet& L = FD->L;
@@ -145,15 +140,24 @@ __global__ void __launch_bounds__(128) k_count(VolConst V, const FrameDev* __res
     uint32_t b0 = blockIdx.x * blockDim.x;
     uint32_t m0r = b0 > NP ? b0 - NP : 0u;
     uint32_t m1r = min(R ? R - 1 : 0u, (b0 + blockDim.x - 1 > NP ? b0 + blockDim.x - 1 - NP : 0u));
-    if (R) block_probe_range(off, V.P, m0r, m1r, &s_lo, &s_hi);
+    if (R && !smp_g) block_probe_range(off, V.P, m0r, m1r, &s_lo, &s_hi);
     uint32_t cv = 0, ct = 0, sv = 0, st = 0;
     if (r < NP + R) {
         float3 org, d;
-        bool ok = true;
+        bool ok = true, shadows = true;
         if (r < NP) {
             int p = r >> 3;
             org = probe_pos(V, p);
             d = pilot_dir(F.pilot_key, (uint32_t)p, r & 7);
+        } else if (smp_g) {
+            const uint32_t q = r - NP, n = R / 2;
+            const bool neg = q >= n;
+            const float4 a = __ldg(smp_g + (neg ? q - n : q));
+            const int p = __float_as_int(a.w);
+            ok = p >= 0 && p < V.P;
+            shadows = !neg;
+            org = probe_pos(V, ok ? p : 0);
+            d = neg ? make_float3(-a.x, -a.y, -a.z) : make_float3(a.x, a.y, a.z);
         } else {
             uint32_t q = r - NP;
             int p = probe_of_ray(off, q, s_lo, s_hi);
@@ -167,7 +171,7 @@ __global__ void __launch_bounds__(128) k_count(VolConst V, const FrameDev* __res
             float t;
             uint32_t h;
             trace_closest(S, org, d, V.tmin, __int_as_float(0x7F800000), t, h, &cv, &ct);
-            if (h != kMiss && !(h & kBackBit)) {
+            if (shadows && h != kMiss && !(h & kBackBit)) {
                 int tri = (int)h;
                 float4 A = __ldg(S.tri_orig + 3 * (size_t)tri), B = __ldg(S.tri_orig + 3 * (size_t)tri + 1),
                        C = __ldg(S.tri_orig + 3 * (size_t)tri + 2);
@@ -264,22 +268,22 @@ cudaError_t launch_main_trace(const VolConst& V, const FrameDev* FD, const Scene
     return cudaGetLastError();
 }
 
-cudaError_t launch_mh_trace(const VolConst& V, const SceneDev& S, const MhBufs& M, const uint32_t* ord,
-                            int2* hit_pos, int2* hit_neg, const Tuning& T, cudaStream_t s)
+cudaError_t launch_mh_trace(const VolConst& V, const SceneDev& S, const MhBufs& M, int2* hit_pos, int2* hit_neg,
+                            const Tuning& T, cudaStream_t s)
 {
     const uint32_t n = M.n_samples;
     if (n == 0) return cudaSuccess;
     const unsigned b = (unsigned)T.trace_block;
-    k_mh_trace<<<(2 * n + b - 1) / b, b, 0, s>>>(V, S, M.smp, ord, n, hit_pos, hit_neg);
+    k_mh_trace<<<(2 * n + b - 1) / b, b, 0, s>>>(V, S, M.smp_g, n, hit_pos, hit_neg);
     count_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_count(const VolConst& V, const FrameDev* FD, const SceneDev& S, const uint32_t* off,
-                         const float4* sf, uint32_t R, unsigned long long* out, cudaStream_t s)
+                         const float4* sf, uint32_t R, unsigned long long* out, cudaStream_t s, const float4* smp_g)
 {
     uint32_t n = (uint32_t)V.P * kPilots + R;
-    k_count<<<(n + 127) / 128, 128, 0, s>>>(V, FD, S, off, sf, R, out);
+    k_count<<<(n + 127) / 128, 128, 0, s>>>(V, FD, S, off, sf, R, out, smp_g);
     count_launches(1);
     return cudaGetLastError();
 }

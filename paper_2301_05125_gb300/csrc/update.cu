@@ -843,27 +843,29 @@ __global__ void __launch_bounds__(128) k_mh_blend(VolConst V, const FrameDev* __
         mh_accumulate(e_rec, e_key, kPilots, acc_i, acc_d, cnt_d, lane);
         __syncwarp();
     }
+    // chunks of 32 samples, one per lane; the next chunk's loads are issued
+    // before the current chunk is added (two chunks in flight per warp)
+    float4 a = make_float4(0.f, 0.f, 0.f, 0.f), x = a;
+    int2 hn = make_int2((int)kMiss, 0);
+    if (b0 + lane < b1) {
+        a = __ldg(B.smp_g + b0 + lane);
+        x = __ldg(B.rec + b0 + lane);
+        hn = __ldg(B.hit_neg + b0 + lane);
+    }
     for (uint32_t c0 = b0; c0 < b1; c0 += 32) {
-        const uint32_t q = c0 + (uint32_t)lane;
-        if (q < b1) {
-            const uint32_t sidx = __ldg(B.ord + q);
-            int2 key = make_int2(-1, -1);
-            float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (sidx < B.n) {
-                const float4 a = __ldg(B.smp + sidx);
-                const float4 x = __ldg(B.rec + q);
-                const int2 hn = __ldg(B.hit_neg + q);
-                const float dep = (uint32_t)hn.x == kMiss ? V.depth_max : fminf(__int_as_float(hn.y), V.depth_max);
-                r = make_float4(x.x, x.y, x.z, dep);
-                key = make_int2(texel_of(oct_encode_x(make_float3(a.x, a.y, a.z)), ni),
-                                texel_of(oct_encode_x(make_float3(-a.x, -a.y, -a.z)), nd));
-            } else {
-                atomicOr(V.err, kErrRayRange);
-            }
-            e_rec[lane] = r;
-            e_key[lane] = key;
+        if (c0 + lane < b1) {
+            const float dep = (uint32_t)hn.x == kMiss ? V.depth_max : fminf(__int_as_float(hn.y), V.depth_max);
+            e_rec[lane] = make_float4(x.x, x.y, x.z, dep);
+            e_key[lane] = make_int2(texel_of(oct_encode_x(make_float3(a.x, a.y, a.z)), ni),
+                                    texel_of(oct_encode_x(make_float3(-a.x, -a.y, -a.z)), nd));
         }
         __syncwarp();
+        const uint32_t qn = c0 + 32 + lane;
+        if (qn < b1) {
+            a = __ldg(B.smp_g + qn);
+            x = __ldg(B.rec + qn);
+            hn = __ldg(B.hit_neg + qn);
+        }
         mh_accumulate(e_rec, e_key, (int)min(32u, b1 - c0), acc_i, acc_d, cnt_d, lane);
         __syncwarp();
     }
@@ -872,18 +874,18 @@ __global__ void __launch_bounds__(128) k_mh_blend(VolConst V, const FrameDev* __
     const size_t io = (size_t)p * ti2, dof = (size_t)p * td2;
     for (int q = lane; q < ni * ni; q += 32) {
         const int r = tile_row(q, rni), t = (r + 1) * Ti + (q - r * ni) + 1;
-        const float4 a = acc_i[t];
+        const float4 sum = acc_i[t];
         float4 v = irr_load(V, B.irr, io + t);
-        if (a.w > 0.0f) v = irr_texel_blend(v, a.x, a.y, a.z, (uint32_t)a.w, omh);
+        if (sum.w > 0.0f) v = irr_texel_blend(v, sum.x, sum.y, sum.z, (uint32_t)sum.w, omh);
         acc_i[t] = v;
     }
     for (int q = lane; q < nd * nd; q += 32) {
         const int r = tile_row(q, rnd), t = (r + 1) * Td + (q - r * nd) + 1;
-        const float2 a = acc_d[t];
+        const float2 sum = acc_d[t];
         const uint32_t k = cnt_d[t];
         float2 v = dep_load(V, B.dep, dof + t);
         uint32_t c = B.dep_n[dof + t];
-        if (k) v = dep_texel_blend(v, c, a.x, a.y, k, omh);
+        if (k) v = dep_texel_blend(v, c, sum.x, sum.y, k, omh);
         acc_d[t] = v;
         dn[t] = (uint8_t)c;
     }

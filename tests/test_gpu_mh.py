@@ -44,7 +44,7 @@ def _compare(A, gv, ov, tag, check_atlas=True, rad_rtol=IRR_RTOL):
     probe, d = gv.mh_samples()
     np.testing.assert_array_equal(probe, ov.mh_probe(), err_msg=tag + " sample probes")
     np.testing.assert_array_equal(d.view(np.uint32), ov.mh_dir().view(np.uint32), err_msg=tag + " sample directions")
-    order = np.argsort(ov.mh_probe(), kind="stable")
+    order = np.argsort(ov.mh_probe().astype(np.int64) * 256 + _dir_cell(ov.mh_dir()), kind="stable")
     np.testing.assert_array_equal(gv.mh_order(), order, err_msg=tag + " grouping")
     counts = np.bincount(ov.mh_probe(), minlength=gv.P)
     np.testing.assert_array_equal(gv.mh_off(), np.concatenate([[0], np.cumsum(counts)]), err_msg=tag + " offsets")
@@ -64,6 +64,30 @@ def _compare(A, gv, ov, tag, check_atlas=True, rad_rtol=IRR_RTOL):
         np.testing.assert_array_equal(gv.dep_n(), ov.dep_n(), err_msg=tag + " depth counts")
         rel_check(gi[..., :3], ov.irr(), IRR_RTOL, tag + " irradiance atlas")
         rel_check(gv.dep_moments(), ov.dep(), DEP_RTOL, tag + " depth atlas")
+
+
+def _dir_cell(d):
+    """Morton index of each direction's cell in a 16 x 16 grid over the
+    octahedral square (the order of the samples inside a probe), FP32 steps"""
+    d = np.asarray(d, np.float32)
+    ax = np.abs(d)
+    l1 = (ax[:, 0] + ax[:, 1]) + ax[:, 2]
+    px, py = d[:, 0] / l1, d[:, 1] / l1
+    sx = np.where(px >= 0, np.float32(1), np.float32(-1))
+    sy = np.where(py >= 0, np.float32(1), np.float32(-1))
+    neg = d[:, 2] < 0
+    qx = (np.float32(1) - np.abs(py)) * sx
+    qy = (np.float32(1) - np.abs(px)) * sy
+    px, py = np.where(neg, qx, px), np.where(neg, qy, py)
+    f16 = np.float32(16)
+    cx = np.clip(np.floor(((px + np.float32(1)) * np.float32(0.5)) * f16), 0, 15).astype(np.int64)
+    cy = np.clip(np.floor(((py + np.float32(1)) * np.float32(0.5)) * f16), 0, 15).astype(np.int64)
+    for k in range(0, len(d), max(1, len(d) // 200)):  # the oracle's texel binning, 16 x 16 interior
+        assert O.texel_of_dir(d[k], 16) == (cy[k] + 1) * 18 + cx[k] + 1
+    m = np.zeros(len(d), np.int64)
+    for b in range(4):
+        m |= ((cx >> b) & 1) << (2 * b) | ((cy >> b) & 1) << (2 * b + 1)
+    return m
 
 
 def _run(A, w, frames, over, camera=None, atlas=None, moving=False, what=""):
@@ -90,6 +114,8 @@ def test_mh_alpha0_small_city(adgi):
     gv, _ = _run(adgi, w, 4, dict(sampler=1, alpha=0.0), moving=True, what="alpha 0 city")
     st = gv.stats()
     assert st.rays_per_update == 8 * gv.P + 2 * (40 - 8) * gv.P
+    c = adgi.adgi_count_traversal(gv.h, adgi.make_frame(3, w.seed, w.lights_at(3), w.sky))
+    assert all(x > 0 for x in c), c  # pilots, then the samples' +w/-w rays and the +w shadow rays
     gv.close()
 
 
