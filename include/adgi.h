@@ -124,7 +124,8 @@ typedef struct {
     float ms_last_update;     /* device time of the last update (0 unless timing was enabled) */
     float ms_phase[8];        /* device time per phase of the last update (timing enabled):
                                  0 BVH rebuild, 1 pilot trace, 2 pilot shade, 3 heuristics,
-                                 4 allocation, 5 adaptive trace, 6 adaptive shade, 7 blend */
+                                 4 allocation (Metropolis: chain steps and grouping),
+                                 5 adaptive trace, 6 adaptive shade, 7 blend */
     uint64_t kernels_launched; /* kernels this library has launched in the process so far */
     float ms_shadow[2];        /* device time of the shadow-ray kernel inside phases 2 and 6 (timing enabled) */
     float ms_blend_plan;       /* device time of the per-frame blend plan, which runs on a side stream
@@ -266,7 +267,8 @@ int adgi_enable_timing(adgi_volume vol, int32_t enable);
  *                       then by sample index
  *   ADGI_STATE_MH_OFF   uint32[P+1]       first grouped position of each probe
  *   ADGI_STATE_MH_HIT_NEG int32[B][2]     -w hits in grouped order (as PILOT_HIT); MAIN_HIT and
- *                       MAIN_REC then hold the +w hits and records in grouped order
+ *                       MAIN_REC then hold the +w hits and records in grouped order, and N and
+ *                       OFF are not computed (the chains replace the per-probe counts)
  * The scene is traced as two parts: triangles that touch any vertex ever passed
  * to adgi_move_vertices form the moving part (linear BVH, rebuilt at the next
  * update after each move); the others form the static part (agglomerative

@@ -172,6 +172,68 @@ __global__ void k_scan_small(uint32_t* __restrict__ a, int n)
     }
 }
 
+// Exclusive scan of a large array in three launches: per-chunk sums, a scan
+// of the (at most 1024) sums, and a scan of each chunk from its carry.
+constexpr int kScanChunks = 1024;
+
+__global__ void __launch_bounds__(256) k_scan_reduce(const uint32_t* __restrict__ a, int n, int per,
+                                                     uint32_t* __restrict__ part)
+{
+    __shared__ uint32_t red[8];
+    const int b0 = blockIdx.x * per, b1 = min(n, b0 + per);
+    uint32_t s = 0;
+    for (int i = b0 + threadIdx.x; i < b1; i += blockDim.x) s += a[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t t = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        part[blockIdx.x] = t;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_scan_apply(uint32_t* __restrict__ a, int n, int per,
+                                                    const uint32_t* __restrict__ part)
+{
+    __shared__ uint32_t wsum[8];
+    const int b0 = blockIdx.x * per, b1 = min(n, b0 + per);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    uint32_t carry = part[blockIdx.x];
+    for (int t0 = b0; t0 < b1; t0 += 4 * (int)blockDim.x) {  // tiles of 4 items per thread
+        const int i0 = t0 + 4 * (int)threadIdx.x;
+        uint32_t v[4], tot = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            v[k] = i0 + k < b1 ? a[i0 + k] : 0u;
+            tot += v[k];
+        }
+        uint32_t x = tot;  // inclusive scan of the thread totals in the warp
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wsum[warp] = x;
+        __syncthreads();
+        uint32_t before = carry, all = 0;
+        for (int w = 0; w < nw; ++w) {
+            const uint32_t ws = wsum[w];
+            if (w < warp) before += ws;
+            all += ws;
+        }
+        before += x - tot;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (i0 + k < b1) a[i0 + k] = before;
+            before += v[k];
+        }
+        carry += all;
+        __syncthreads();
+    }
+}
+
 __global__ void k_scatter(const uint64_t* __restrict__ kin, const uint32_t* __restrict__ vin,
                           uint64_t* __restrict__ kout, uint32_t* __restrict__ vout, int n, int shift,
                           const uint32_t* __restrict__ hist, int nblocks)
@@ -540,18 +602,30 @@ size_t radix_hist_entries(int n) { return 256 * (size_t)((std::max(n, 1) + kSort
 
 // Stable LSD radix sort of n (key, value) pairs on key bits [0, bits), eight
 // bits per pass (hist -> scan -> scatter); the result is in keys[*cur],
-// vals[*cur].  hist holds radix_hist_entries(n) counters.
+// vals[*cur].  hist holds radix_hist_entries(n) counters; part (optional,
+// 1024 entries) lets large histograms use the three-launch scan.
 cudaError_t radix_sort_pairs(uint64_t* const keys[2], uint32_t* const vals[2], uint32_t* hist, int n, int bits,
-                             cudaStream_t s, int* cur_out)
+                             cudaStream_t s, int* cur_out, uint32_t* part)
 {
     int cur = 0;
     if (n > 0) {
         const int nb = (n + kSortTile - 1) / kSortTile;
+        const int nh = 256 * nb;
+        // large histograms (and a partial-sum buffer): the three-launch scan
+        const int G = std::min(kScanChunks, (nh + 1023) / 1024), per = (nh + G - 1) / G;
+        const bool big = part != nullptr && nh > 65536;
         for (int shift = 0; shift < bits; shift += 8) {
             k_hist<<<nb, kSortThreads, 0, s>>>(keys[cur], n, shift, hist, nb);
             count_launches(1);
-            k_scan_small<<<1, 1024, 0, s>>>(hist, 256 * nb);
-            count_launches(1);
+            if (big) {
+                k_scan_reduce<<<G, 256, 0, s>>>(hist, nh, per, part);
+                k_scan_small<<<1, 1024, 0, s>>>(part, G);
+                k_scan_apply<<<G, 256, 0, s>>>(hist, nh, per, part);
+                count_launches(3);
+            } else {
+                k_scan_small<<<1, 1024, 0, s>>>(hist, nh);
+                count_launches(1);
+            }
             k_scatter<<<nb, kSortThreads, 0, s>>>(keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], n, shift, hist,
                                                    nb);
             count_launches(1);

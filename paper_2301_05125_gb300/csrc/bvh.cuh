@@ -36,7 +36,7 @@ struct PlocBufs {
 size_t bvh_scratch_bytes(int nt);
 size_t radix_hist_entries(int n);
 cudaError_t radix_sort_pairs(uint64_t* const keys[2], uint32_t* const vals[2], uint32_t* hist, int n, int bits,
-                             cudaStream_t s, int* cur_out);
+                             cudaStream_t s, int* cur_out, uint32_t* part = nullptr);
 size_t carve_bvh_scratch(void* base, int nt, BvhBufs& B);
 size_t ploc_scratch_bytes(int nt);
 size_t carve_ploc_scratch(void* base, int nt, PlocBufs& Q);

@@ -265,7 +265,7 @@ struct adgi_volume_s {
     float4* mh_smp_g = nullptr;        // [B] samples, grouped order
     uint64_t* mh_keys = nullptr;       // [2B] radix sort by probe
     uint32_t* mh_vals = nullptr;       // [2B]
-    uint32_t* mh_hist = nullptr;
+    uint32_t* mh_hist = nullptr;       // radix histograms, then [1024] partial sums
     uint32_t* mh_off = nullptr;        // [P+1]
     int2* mh_hitn = nullptr;           // [B] -w hits, grouped order
     const uint32_t* mh_ord = nullptr;  // grouped order of the last update
@@ -504,7 +504,7 @@ int adgi_create_volume(const adgi_volume_desc* desc, void* cuda_stream, adgi_vol
         DA(v->mh_smp_g, nB);
         DA(v->mh_keys, 2 * nB);
         DA(v->mh_vals, 2 * nB);
-        DA(v->mh_hist, radix_hist_entries((int)nB));
+        DA(v->mh_hist, radix_hist_entries((int)nB) + 1024);
         DA(v->mh_off, P + 1);
         DA(v->mh_hitn, nB);
     }
@@ -736,6 +736,7 @@ MhBufs mh_bufs(adgi_volume v)
     M.vals[0] = v->mh_vals;
     M.vals[1] = v->mh_vals ? v->mh_vals + v->mh_B : nullptr;
     M.hist = v->mh_hist;
+    M.part = v->mh_hist + radix_hist_entries((int)v->mh_B);
     M.off = v->mh_off;
     M.lut_c = v->lut_c;
     M.qv = v->qv;
@@ -874,7 +875,7 @@ int enqueue_update(adgi_volume v, const FrameDev& fd, cudaStream_t s, bool phase
     CK(launch_change(V, FD, C, s));
     // 3. allocation
     PHASE(4);
-    CK(launch_allocate(v->W, V.P, V.rays_avg, V.m0, V.rays_max, v->n, v->off, s));
+    if (!mh) CK(launch_allocate(v->W, V.P, V.rays_avg, V.m0, V.rays_max, v->n, v->off, s));
     if (mh) {
         // 3'. Metropolis chains draw the samples; group them by probe
         MhBufs M = mh_bufs(v);

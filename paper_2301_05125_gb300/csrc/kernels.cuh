@@ -108,6 +108,7 @@ struct MhBufs {
     uint64_t* keys[2];        // radix sort of the samples by probe
     uint32_t* vals[2];
     uint32_t* hist;
+    uint32_t* part;           // [1024] partial sums of the histogram scan
     uint32_t* off;            // [P+1] first grouped sample of each probe
     const uint16_t* lut_c;
     const uint16_t* qv;       // this frame's q_v per (probe, octant)

@@ -222,7 +222,7 @@ cudaError_t launch_mh_group(const VolConst& V, const MhBufs& M, cudaStream_t s, 
     int bits = kMhCellBits;
     while (bits < 40 && ((uint64_t)1 << bits) < ((uint64_t)V.P << kMhCellBits)) ++bits;
     int cur = 0;
-    cudaError_t e = radix_sort_pairs(M.keys, M.vals, M.hist, (int)M.n_samples, bits, s, &cur);
+    cudaError_t e = radix_sort_pairs(M.keys, M.vals, M.hist, (int)M.n_samples, bits, s, &cur, M.part);
     if (e != cudaSuccess) return e;
     *ord = M.vals[cur];
     k_mh_offsets<<<(V.P + 1 + 255) / 256, 256, 0, s>>>(M.keys[cur], M.n_samples, V.P, M.off);

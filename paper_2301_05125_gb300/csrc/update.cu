@@ -757,10 +757,11 @@ __global__ void __launch_bounds__(128) k_blend(VolConst V, const FrameDev* __res
 // probe).  Sample s adds its +w radiance to the irradiance texel of w and the
 // distance along -w to the visibility texel of -w (the extra ray of the
 // static adaptive sampling); the pilots come first on the first frame of a
-// pair.  Per texel the sums run in that order; then the batched moving
-// average and the stores of k_blend.
+// pair.  Per texel the sums run in that order (a chunk's samples of one
+// texel summed first, in order); then the batched moving average and the
+// stores of k_blend.
 struct MhLayout {
-    uint32_t acc_i, acc_d, cnt_d, dn, e_rec, e_key, total;
+    uint32_t acc_i, acc_d, cnt_d, dn, e_rec, total;
 };
 
 __host__ __device__ inline MhLayout mh_layout(int Ti, int Td)
@@ -773,33 +774,47 @@ __host__ __device__ inline MhLayout mh_layout(int Ti, int Td)
     L.cnt_d = o, o += al16(4 * td2);
     L.dn = o, o += al16(td2);
     L.e_rec = o, o += 16 * 32;  // one chunk of samples: {r, g, b, depth}
-    L.e_key = o, o += 8 * 32;   // {irradiance texel, visibility texel}
     L.total = o;
     return L;
 }
 
-// add a chunk of cnt samples in order; the lane owning texel t (t % 32) adds
-__device__ __forceinline__ void mh_accumulate(const float4* e_rec, const int2* e_key, int cnt, float4* acc_i,
-                                              float2* acc_d, uint32_t* cnt_d, int lane)
+// Add a chunk of samples, one per lane (lane j holds sample j of the chunk
+// with its texels ki, kd; -1 for none): the lanes of one texel form a group
+// (match_any) whose lowest lane sums the group's records in lane order and
+// adds the sum to the texel.  Texels are distinct across groups, so the
+// adds do not race; per texel the chunks are added in order.
+__device__ __forceinline__ void mh_accumulate(const float4* e_rec, int ki, int kd, float4* acc_i, float2* acc_d,
+                                              uint32_t* cnt_d, int lane)
 {
-    for (int j = 0; j < cnt; ++j) {
-        const int2 kk = e_key[j];
-        const float4 r = e_rec[j];
-        if (kk.x >= 0 && (kk.x & 31) == lane) {
-            float4 a = acc_i[kk.x];
-            a.x += r.x;
-            a.y += r.y;
-            a.z += r.z;
-            a.w += 1.0f;
-            acc_i[kk.x] = a;
+    const uint32_t below = (1u << lane) - 1u;
+    const uint32_t gi = __match_any_sync(0xFFFFFFFFu, ki), gd = __match_any_sync(0xFFFFFFFFu, kd);
+    if (ki >= 0 && (gi & below) == 0u) {
+        float sx = 0.f, sy = 0.f, sz = 0.f;
+        for (uint32_t m = gi; m; m &= m - 1u) {
+            const float4 r = e_rec[__ffs(m) - 1];
+            sx += r.x;
+            sy += r.y;
+            sz += r.z;
         }
-        if (kk.y >= 0 && (kk.y & 31) == lane) {
-            float2 d = acc_d[kk.y];
-            d.x += r.w;
-            d.y += r.w * r.w;
-            acc_d[kk.y] = d;
-            cnt_d[kk.y] += 1u;
+        float4 t = acc_i[ki];
+        t.x += sx;
+        t.y += sy;
+        t.z += sz;
+        t.w += (float)__popc(gi);
+        acc_i[ki] = t;
+    }
+    if (kd >= 0 && (gd & below) == 0u) {
+        float s1 = 0.f, s2 = 0.f;
+        for (uint32_t m = gd; m; m &= m - 1u) {
+            const float x = e_rec[__ffs(m) - 1].w;
+            s1 += x;
+            s2 += x * x;
         }
+        float2 t = acc_d[kd];
+        t.x += s1;
+        t.y += s2;
+        acc_d[kd] = t;
+        cnt_d[kd] += (uint32_t)__popc(gd);
     }
 }
 
@@ -827,20 +842,22 @@ __global__ void __launch_bounds__(128) k_mh_blend(VolConst V, const FrameDev* __
     uint32_t* cnt_d = reinterpret_cast<uint32_t*>(ws + L.cnt_d);
     uint8_t* dn = ws + L.dn;
     float4* e_rec = reinterpret_cast<float4*>(ws + L.e_rec);
-    int2* e_key = reinterpret_cast<int2*>(ws + L.e_key);
     for (int t = lane; t < ti2; t += 32) acc_i[t] = make_float4(0.f, 0.f, 0.f, 0.f);
     for (int t = lane; t < td2; t += 32) {
         acc_d[t] = make_float2(0.f, 0.f);
         cnt_d[t] = 0u;
     }
+    __syncwarp();
     if (npil) {
+        int ki = -1, kd = -1;
         if (lane < kPilots) {
             e_rec[lane] = __ldg(B.pil_rec + (size_t)p * kPilots + lane);
             const float2 e = oct_encode_x(pilot_dir(F.pilot_key, (uint32_t)p, lane));
-            e_key[lane] = make_int2(texel_of(e, ni), texel_of(e, nd));
+            ki = texel_of(e, ni);
+            kd = texel_of(e, nd);
         }
         __syncwarp();
-        mh_accumulate(e_rec, e_key, kPilots, acc_i, acc_d, cnt_d, lane);
+        mh_accumulate(e_rec, ki, kd, acc_i, acc_d, cnt_d, lane);
         __syncwarp();
     }
     // chunks of 32 samples, one per lane; the next chunk's loads are issued
@@ -853,11 +870,12 @@ __global__ void __launch_bounds__(128) k_mh_blend(VolConst V, const FrameDev* __
         hn = __ldg(B.hit_neg + b0 + lane);
     }
     for (uint32_t c0 = b0; c0 < b1; c0 += 32) {
+        int ki = -1, kd = -1;
         if (c0 + lane < b1) {
             const float dep = (uint32_t)hn.x == kMiss ? V.depth_max : fminf(__int_as_float(hn.y), V.depth_max);
             e_rec[lane] = make_float4(x.x, x.y, x.z, dep);
-            e_key[lane] = make_int2(texel_of(oct_encode_x(make_float3(a.x, a.y, a.z)), ni),
-                                    texel_of(oct_encode_x(make_float3(-a.x, -a.y, -a.z)), nd));
+            ki = texel_of(oct_encode_x(make_float3(a.x, a.y, a.z)), ni);
+            kd = texel_of(oct_encode_x(make_float3(-a.x, -a.y, -a.z)), nd);
         }
         __syncwarp();
         const uint32_t qn = c0 + 32 + lane;
@@ -866,7 +884,7 @@ __global__ void __launch_bounds__(128) k_mh_blend(VolConst V, const FrameDev* __
             x = __ldg(B.rec + qn);
             hn = __ldg(B.hit_neg + qn);
         }
-        mh_accumulate(e_rec, e_key, (int)min(32u, b1 - c0), acc_i, acc_d, cnt_d, lane);
+        mh_accumulate(e_rec, ki, kd, acc_i, acc_d, cnt_d, lane);
         __syncwarp();
     }
     const float omh = 1.0f - V.hyst;
