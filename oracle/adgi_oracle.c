@@ -894,6 +894,12 @@ static uint32_t pk_dep_update(uint32_t code, float x)
 #define MH_M 8
 #define MH_K 2
 #define MH_S (MH_M - MH_K - 1)
+/* proposal sigmas of the static chains: half a probe spacing, sqrt(pi / 256) */
+#define MH_SG 0.5f
+#define MH_SU 0.11077321f
+/* the dynamic chains step 3x and 6x farther (in proxy units: half a proxy) */
+#define DYN_SG 0.5f
+#define DYN_SU 0.66463926f
 
 /* ------------------------------------------------------------------------ */
 /* Volume state                                                              */
@@ -909,6 +915,9 @@ typedef struct {
     int packed;           /* 1: 32-bit packed atlases (the paper's codecs) */
     int sampler;          /* 0: deterministic allocation; 1: Metropolis chains (static guide) */
     float alpha;          /* confidence alpha in the cache term of the guide (Eq. DDGIBays) */
+    int dyn_ratio;        /* sampler = 1: > 0 adds the dynamic chains (Sec. "Adaptive sampling -  */
+                          /* dynamic") with a static:dynamic budget split of dyn_ratio:1      */
+    float hyst_dyn;       /* hysteresis of the dynamic rays' batch update */
 } orc_desc;
 
 typedef struct {
@@ -989,6 +998,32 @@ typedef struct orc_vol {
     double* smp_dep;     /* B distance along -w (clamped) */
     uint32_t* smp_off;   /* P+1 first sample of each probe in smp_ord */
     uint32_t* smp_ord;   /* B sample indices grouped by probe, in sample order */
+    uint32_t* qd;        /* P*8 dynamic weight q_d of each probe and octant (Eq. priorDynamic) */
+    /* dynamic chains over virtual proxies (desc.dyn_ratio > 0) */
+    int Dp[3], Pp;       /* proxy grid: ceil(dims / 3) */
+    size_t Cd, Bd;       /* dynamic chains, dynamic samples per frame (5 per chain) */
+    size_t Rd;           /* dynamic ray budget per frame */
+    int dyn_live;
+    float* dch_g;        /* Cd*3 proxy-grid coordinates */
+    float* dch_u;        /* Cd*2 octahedral coordinates */
+    int* dsm_q;          /* Bd proxy of each dynamic sample */
+    float* dsm_dir;      /* Bd*3 */
+    int* dsm_cell;       /* Bd proxy*8 + octant, -1 where the target is 0 */
+    uint32_t* dfirst;    /* Pp*8 first dynamic sample of each cell (UINT32_MAX: unmarked) */
+    int* dmark;          /* marked cells in first-sample order */
+    int n_marked, n_incl;/* marked cells; the leading ones within the ray budget */
+    uint8_t* dincl;      /* Pp*8 1: the cell's rays are traced this frame */
+    int ntex[8];         /* irradiance interior texels whose centre lies in each octant */
+    int* tex_t;          /* [8][n_irr^2] their tile indices, in texel order */
+    float* tex_dir;      /* [8][n_irr^2][3] their centre directions (FP32) */
+    uint32_t* doff;      /* P+1 dynamic rays of each probe */
+    size_t Rdyn;         /* this frame's dynamic rays */
+    int* d_p;            /* Rd probe of each dynamic ray */
+    int* d_k;            /* Rd octant * n_irr^2 + index in the octant's texel list */
+    float* d_t;
+    int* d_tri;
+    double* d_rad;       /* Rd*3 */
+    double* d_dep;       /* Rd */
 } orc_vol;
 
 static void build_luts(orc_vol* v)
@@ -1016,6 +1051,7 @@ EXPORT void orc_luts(double s, uint16_t* lut_v, uint16_t* lut_c)
 }
 
 EXPORT void orc_destroy(orc_vol* v);
+static void dyn_create(orc_vol* v);
 
 EXPORT orc_vol* orc_create(const orc_desc* d, int nthreads)
 {
@@ -1064,6 +1100,7 @@ EXPORT orc_vol* orc_create(const orc_desc* d, int nthreads)
     memset(v->age_r, 255, P * 8);
     v->qv = (uint16_t*)calloc(P * 8, 2);
     v->qr = (uint16_t*)calloc(P * 8, 2);
+    v->qd = (uint32_t*)calloc(P * 8, 4);
     v->last_even = -2;
     v->W = (uint32_t*)calloc(P, 4);
     v->n = (uint32_t*)calloc(P, 4);
@@ -1086,6 +1123,11 @@ EXPORT orc_vol* orc_create(const orc_desc* d, int nthreads)
             return NULL;
         }
         v->B = v->R_main;
+        if (d->dyn_ratio > 0) { /* budget split static:dynamic = r:1; a static sample costs two rays */
+            size_t B = v->B, r = (size_t)d->dyn_ratio;
+            v->B = B * r / (r + 1);
+            v->Rd = 2 * (B - v->B);
+        }
         v->C = (v->B + MH_S - 1) / MH_S;
         v->ch_g = (float*)calloc(v->C * 3 + 1, 4);
         v->ch_u = (float*)calloc(v->C * 2 + 1, 4);
@@ -1099,6 +1141,10 @@ EXPORT orc_vol* orc_create(const orc_desc* d, int nthreads)
         v->smp_dep = (double*)calloc(v->B + 1, 8);
         v->smp_off = (uint32_t*)calloc(P + 1, 4);
         v->smp_ord = (uint32_t*)calloc(v->B + 1, 4);
+        if (d->dyn_ratio > 0) dyn_create(v);
+    } else if (d->dyn_ratio != 0) { /* the dynamic chains belong to the Metropolis mode */
+        orc_destroy(v);
+        return NULL;
     }
     return v;
 }
@@ -1129,6 +1175,24 @@ EXPORT void orc_destroy(orc_vol* v)
     free(v->smp_dep);
     free(v->smp_off);
     free(v->smp_ord);
+    free(v->qd);
+    free(v->dch_g);
+    free(v->dch_u);
+    free(v->dsm_q);
+    free(v->dsm_dir);
+    free(v->dsm_cell);
+    free(v->dfirst);
+    free(v->dmark);
+    free(v->dincl);
+    free(v->tex_t);
+    free(v->tex_dir);
+    free(v->doff);
+    free(v->d_p);
+    free(v->d_k);
+    free(v->d_t);
+    free(v->d_tri);
+    free(v->d_rad);
+    free(v->d_dep);
     free(v->qv_even);
     free(v->qr_even);
     free(v->trv);
@@ -1452,6 +1516,21 @@ static void shade_ray(const orc_vol* v, const orc_frame* fr, const float o[3], c
 /* n' = min(n + k, 255).  Untouched texels keep their value.  Then the      */
 /* one-texel octahedral border is refreshed from the interior.             */
 /* ------------------------------------------------------------------------ */
+/* one batched moving-average step of the texels with k > 0 samples (sums s):
+   V += w (s/k - V), w = max(1 - h, k/(n + k)), n = min(n + k, 255) */
+static void batch_apply(double* val, uint8_t* cnt, const double* s, const int* kk, int texels, int ch, double h)
+{
+    for (int t = 0; t < texels; ++t) {
+        if (!kk[t]) continue;
+        double k = kk[t], n = cnt[t];
+        double w = k / (n + k);
+        if (w < 1.0 - h) w = 1.0 - h;
+        for (int c = 0; c < ch; ++c) val[t * ch + c] += w * (s[t * ch + c] / k - val[t * ch + c]);
+        int nn = cnt[t] + kk[t];
+        cnt[t] = (uint8_t)(nn > 255 ? 255 : nn);
+    }
+}
+
 static void border_copy(double* tile, uint8_t* cnt, int n, int ch)
 {
     int T = n + 2;
@@ -1596,24 +1675,8 @@ static void blend_probe(orc_vol* v, int p, int use_pilots, double h)
         sd[td * 2 + 1] += ds * ds;
         kd[td] += 1;
     }
-    for (int t = 0; t < Ti * Ti; ++t) {
-        if (!ki[t]) continue;
-        double k = ki[t], n = irn[t];
-        double w = k / (n + k);
-        if (w < 1.0 - h) w = 1.0 - h;
-        for (int c = 0; c < 3; ++c) irr[t * 3 + c] += w * (si[t * 3 + c] / k - irr[t * 3 + c]);
-        int nn = irn[t] + ki[t];
-        irn[t] = (uint8_t)(nn > 255 ? 255 : nn);
-    }
-    for (int t = 0; t < Td * Td; ++t) {
-        if (!kd[t]) continue;
-        double k = kd[t], n = den[t];
-        double w = k / (n + k);
-        if (w < 1.0 - h) w = 1.0 - h;
-        for (int c = 0; c < 2; ++c) dep[t * 2 + c] += w * (sd[t * 2 + c] / k - dep[t * 2 + c]);
-        int nn = den[t] + kd[t];
-        den[t] = (uint8_t)(nn > 255 ? 255 : nn);
-    }
+    batch_apply(irr, irn, si, ki, Ti * Ti, 3, h);
+    batch_apply(dep, den, sd, kd, Td * Td, 2, h);
     border_copy(irr, irn, ni, 3);
     border_copy(dep, den, nd, 2);
     free(si);
@@ -1727,6 +1790,7 @@ static void change_detect(orc_vol* v, const orc_frame* fr)
                         }
                     }
             uint64_t qd = ((uint64_t)qc * (uint64_t)v->qv[(size_t)p * 8 + o] * (fdv + 2u * fdr)) >> 20;
+            v->qd[(size_t)p * 8 + o] = (uint32_t)(qd < 0xFFFFFFFFu ? qd : 0xFFFFFFFFu);
             Wp += qd;
         }
         v->W[p] = (uint32_t)(Wp < 0xFFFFFFu ? Wp : 0xFFFFFFu);
@@ -1864,27 +1928,32 @@ static float mh_guide(const orc_vol* v, const orc_frame* fr, const float g[3], c
 }
 
 /* M random-walk steps (Alg. MetropolisStep) of a chain in state (g, u) of a
-   dims grid, under guide(ctx, g, u); the states after steps K+1..M-1 are
-   written to samples (probe, direction) from index first (up to limit). */
+   dims grid, under guide(ctx, g, u), with proposal sigmas sg (grid units)
+   and su (octahedral units) and random numbers hash3(key, frame, counter);
+   the states after steps K+1..M-1 are written to samples (grid point,
+   direction) from index first (up to limit). */
 typedef float (*mh_guide_fn)(const void* ctx, const float g[3], const float u[2]);
-static void mh_walk(const int dims[3], uint64_t seed, uint64_t frame, size_t c, float* g, float* u, mh_guide_fn guide,
-                    const void* ctx, int* smp_p, float* smp_dir, size_t first, size_t limit)
+static uint64_t mh_key_bits(uint64_t key, uint64_t frame, uint64_t chain, uint64_t step, uint64_t comp)
+{
+    return hash3(key, frame, (chain * (MH_M + 1) + step) * 8u + comp);
+}
+static void mh_walk(const int dims[3], uint64_t key, uint64_t frame, size_t c, float sg, float su, float* g, float* u,
+                    mh_guide_fn guide, const void* ctx, int* smp_p, float* smp_dir, size_t first, size_t limit)
 {
     float y = guide(ctx, g, u);
-    const float sg = 0.5f, su = 0.11077321f; /* sqrt(pi / 256) */
     for (int i = 0; i < MH_M; ++i) {
         float g2[3], u2[2];
         for (int k = 0; k < 3; ++k)
-            g2[k] = mh_reflect(g[k] + sg * mh_normal(mh_bits(seed, frame, c, (uint64_t)i, (uint64_t)k)), 0.0f,
+            g2[k] = mh_reflect(g[k] + sg * mh_normal(mh_key_bits(key, frame, c, (uint64_t)i, (uint64_t)k)), 0.0f,
                                (float)(dims[k] - 1));
         for (int k = 0; k < 2; ++k)
-            u2[k] = mh_reflect(u[k] + su * mh_normal(mh_bits(seed, frame, c, (uint64_t)i, (uint64_t)(3 + k))), -1.0f,
-                               1.0f);
+            u2[k] = mh_reflect(u[k] + su * mh_normal(mh_key_bits(key, frame, c, (uint64_t)i, (uint64_t)(3 + k))),
+                               -1.0f, 1.0f);
         float y2 = guide(ctx, g2, u2);
         int accept = 1;
         if (y > 0.0f) {
             float mu = y2 / y;
-            float eps = mh_uniform(mh_bits(seed, frame, c, (uint64_t)i, 5u));
+            float eps = mh_uniform(mh_key_bits(key, frame, c, (uint64_t)i, 5u));
             if (mu < 1.0f && eps > mu) accept = 0;
         }
         if (accept) {
@@ -1922,8 +1991,8 @@ static float mh_vol_guide(const void* ctx, const float g[3], const float u[2])
 static void mh_chain(orc_vol* v, const orc_frame* fr, size_t c)
 {
     mh_vol_ctx ctx = {v, fr};
-    mh_walk(v->d.dims, fr->seed, fr->frame, c, v->ch_g + c * 3, v->ch_u + c * 2, mh_vol_guide, &ctx, v->smp_p,
-            v->smp_dir, c * MH_S, v->B);
+    mh_walk(v->d.dims, fr->seed ^ 0x4D4554524FULL, fr->frame, c, MH_SG, MH_SU, v->ch_g + c * 3, v->ch_u + c * 2,
+            mh_vol_guide, &ctx, v->smp_p, v->smp_dir, c * MH_S, v->B);
 }
 
 /* Test hook: chains on a fixed guide h(probe, octant) given as a table
@@ -1964,7 +2033,8 @@ EXPORT void orc_mh_run_table(const int dims[3], const float* table, int chains, 
     }
     for (int f = 0; f < frames; ++f)
         for (int c = 0; c < chains; ++c) {
-            mh_walk(dims, seed, (uint64_t)f, (size_t)c, g + c * 3, u + c * 2, mh_tab_guide, &ctx, sp, sd, 0, MH_S);
+            mh_walk(dims, seed ^ 0x4D4554524FULL, (uint64_t)f, (size_t)c, MH_SG, MH_SU, g + c * 3, u + c * 2,
+                    mh_tab_guide, &ctx, sp, sd, 0, MH_S);
             if (f < skip) continue;
             for (int j = 0; j < MH_S; ++j) {
                 const float* d = sd + 3 * j;
@@ -1990,22 +2060,232 @@ static void mh_init(orc_vol* v, uint64_t seed)
     v->chains_live = 1;
 }
 
-/* trace and shade sample s: +w for radiance, -w for the visibility distance */
+static int octant_of(const float w[3]) { return (w[0] < 0.0f ? 1 : 0) | (w[1] < 0.0f ? 2 : 0) | (w[2] < 0.0f ? 4 : 0); }
+
+/* direction through the centre of interior texel (cx, cy) of an n x n
+   octahedral grid: u = (c + 1/2)/n * 2 - 1 per axis, FP32 in that order,
+   decoded like a chain state */
+static void texel_centre_dir(int cx, int cy, int n, float w[3])
+{
+    float u[2] = {(((float)cx + 0.5f) / (float)n) * 2.0f - 1.0f, (((float)cy + 0.5f) / (float)n) * 2.0f - 1.0f};
+    mh_dir(u, w);
+}
+
+/* the centre direction of the texel a direction bins to (n x n interior) */
+static void snap_to_texel(const float d[3], int n, float w[3])
+{
+    int t = orc_texel_of_dir(d, n), T = n + 2;
+    texel_centre_dir(t % T - 1, t / T - 1, n, w);
+}
+
+/* trace and shade sample s: +w for radiance, -w for the visibility distance.
+   With the dynamic chains on, a sample whose probe and octant carry a
+   dynamic weight (q_d > 0) traces through texel centres instead: +w through
+   the centre of its irradiance texel, -w through the centre of the
+   visibility texel of -w (Sec. "Adaptive sampling - dynamic", last
+   paragraph), so that it adds no sampling noise there. */
 static void mh_sample_rays(orc_vol* v, const orc_frame* fr, size_t sidx)
 {
     float o[3];
     probe_pos(v, v->smp_p[sidx], o);
-    const float* d = v->smp_dir + sidx * 3;
+    const float* d0 = v->smp_dir + sidx * 3;
+    float d[3] = {d0[0], d0[1], d0[2]}, dn[3] = {-d0[0], -d0[1], -d0[2]};
+    if (v->d.dyn_ratio > 0 && v->qd[(size_t)v->smp_p[sidx] * 8 + (size_t)octant_of(d0)] > 0) {
+        snap_to_texel(d0, v->d.n_irr, d);
+        float m[3] = {-d0[0], -d0[1], -d0[2]};
+        snap_to_texel(m, v->d.n_dep, dn);
+    }
     hitrec h = vol_closest(v, o, d, v->tmin, INFINITY);
     v->smp_t[sidx] = h.tri >= 0 ? h.t : INFINITY;
     v->smp_tri[sidx] = h.tri;
     double dep_unused;
     shade_ray(v, fr, o, d, h, v->smp_rad + sidx * 3, &dep_unused, NULL);
-    float dn[3] = {-d[0], -d[1], -d[2]};
     hitrec hn = vol_closest(v, o, dn, v->tmin, INFINITY);
     v->smp_tn[sidx] = hn.tri >= 0 ? hn.t : INFINITY;
     v->smp_trin[sidx] = hn.tri;
     v->smp_dep[sidx] = hn.tri >= 0 ? (hn.t < v->depth_max ? hn.t : v->depth_max) : v->depth_max;
+}
+
+
+/* ------------------------------------------------------------------------ */
+/* Dynamic chains over virtual proxies (desc.dyn_ratio > 0; Sec. "Adaptive */
+/* sampling - dynamic").                                                    */
+/*   A proxy stands for a 3x3x3 block of probes (clipped at the grid end); */
+/*   its value in octant o is the max of q_d over its probes (the coarsened */
+/*   f_d), and the guide is that value with alpha = 0 (no cache term).     */
+/*   The chains walk proxy-grid coordinates and octahedral coordinates with */
+/*   steps 3x and 6x those of the static chains, 8 steps per frame, the     */
+/*   states after steps 3..7 being the samples (as the static chains).      */
+/*   A sample marks its (proxy, octant) cell when the guide there is > 0;   */
+/*   a cell is marked once per frame, by its first sample.  Marked cells in */
+/*   first-sample order are traced while the running ray count stays within */
+/*   the dynamic budget; a traced cell sends, from each of its probes, one  */
+/*   ray through the centre of every irradiance texel whose centre lies in  */
+/*   the octant (deterministic directions).  Each such ray updates its      */
+/*   irradiance texel and the visibility texel of its direction, in a       */
+/*   second batched step after the static samples, with hysteresis          */
+/*   hyst_dyn.  Budget: the adaptive samples B are split r:1; the static    */
+/*   chains draw B_s = floor(B r/(r+1)) samples, the dynamic rays get the   */
+/*   remaining 2(B - B_s) rays (a static sample traces two rays); there are */
+/*   ceil(C_s / r) dynamic chains (the paper's 4096:1024 at r = 4).          */
+/* ------------------------------------------------------------------------ */
+#define DYN_KEY 0x44594E414DULL /* 'DYNAM' */
+
+static void dyn_create(orc_vol* v)
+{
+    for (int k = 0; k < 3; ++k) v->Dp[k] = (v->d.dims[k] + 2) / 3;
+    v->Pp = v->Dp[0] * v->Dp[1] * v->Dp[2];
+    size_t r = (size_t)v->d.dyn_ratio;
+    v->Cd = v->C ? (v->C + r - 1) / r : 0;
+    v->Bd = v->Cd * MH_S;
+    v->dch_g = (float*)calloc(v->Cd * 3 + 1, 4);
+    v->dch_u = (float*)calloc(v->Cd * 2 + 1, 4);
+    v->dsm_q = (int*)calloc(v->Bd + 1, 4);
+    v->dsm_dir = (float*)calloc(v->Bd * 3 + 1, 4);
+    v->dsm_cell = (int*)calloc(v->Bd + 1, 4);
+    v->dfirst = (uint32_t*)calloc((size_t)v->Pp * 8, 4);
+    v->dmark = (int*)calloc((size_t)v->Pp * 8, 4);
+    v->dincl = (uint8_t*)calloc((size_t)v->Pp * 8, 1);
+    const int n = v->d.n_irr, T = n + 2;
+    v->tex_t = (int*)calloc((size_t)8 * n * n, 4);
+    v->tex_dir = (float*)calloc((size_t)8 * n * n * 3, 4);
+    for (int cy = 0; cy < n; ++cy)
+        for (int cx = 0; cx < n; ++cx) {
+            float w[3];
+            texel_centre_dir(cx, cy, n, w);
+            int o = octant_of(w), j = v->ntex[o]++;
+            v->tex_t[o * n * n + j] = (cy + 1) * T + (cx + 1);
+            memcpy(v->tex_dir + ((size_t)o * n * n + (size_t)j) * 3, w, sizeof(w));
+        }
+    v->doff = (uint32_t*)calloc((size_t)v->P + 1, 4);
+    v->d_p = (int*)calloc(v->Rd + 1, 4);
+    v->d_k = (int*)calloc(v->Rd + 1, 4);
+    v->d_t = (float*)calloc(v->Rd + 1, 4);
+    v->d_tri = (int*)calloc(v->Rd + 1, 4);
+    v->d_rad = (double*)calloc(v->Rd * 3 + 1, 8);
+    v->d_dep = (double*)calloc(v->Rd + 1, 8);
+}
+
+static void dyn_init(orc_vol* v, uint64_t seed)
+{
+    for (size_t c = 0; c < v->Cd; ++c) {
+        for (int k = 0; k < 3; ++k)
+            v->dch_g[c * 3 + k] =
+                mh_uniform(mh_key_bits(seed ^ DYN_KEY ^ 0x494E4954ULL, 0, c, MH_M, (uint64_t)k)) * (float)(v->Dp[k] - 1);
+        for (int k = 0; k < 2; ++k)
+            v->dch_u[c * 2 + k] =
+                mh_uniform(mh_key_bits(seed ^ DYN_KEY ^ 0x494E4954ULL, 0, c, MH_M, (uint64_t)(3 + k))) * 2.0f - 1.0f;
+    }
+    v->dyn_live = 1;
+}
+
+/* coarsened dynamic target of proxy q in octant o: max of q_d over its probes */
+static uint32_t dyn_value(const orc_vol* v, int q, int o)
+{
+    const int X = v->d.dims[0], Y = v->d.dims[1], Z = v->d.dims[2];
+    int qx = q % v->Dp[0], qy = (q / v->Dp[0]) % v->Dp[1], qz = q / (v->Dp[0] * v->Dp[1]);
+    uint32_t m = 0;
+    for (int z = 3 * qz; z < 3 * qz + 3 && z < Z; ++z)
+        for (int y = 3 * qy; y < 3 * qy + 3 && y < Y; ++y)
+            for (int x = 3 * qx; x < 3 * qx + 3 && x < X; ++x) {
+                uint32_t w = v->qd[((size_t)x + (size_t)X * ((size_t)y + (size_t)Y * (size_t)z)) * 8 + (size_t)o];
+                if (w > m) m = w;
+            }
+    return m;
+}
+
+static int dyn_proxy_of(const orc_vol* v, const float g[3])
+{
+    int q[3];
+    for (int k = 0; k < 3; ++k) {
+        int i = (int)floorf(g[k] + 0.5f);
+        q[k] = i < 0 ? 0 : (i > v->Dp[k] - 1 ? v->Dp[k] - 1 : i);
+    }
+    return q[0] + v->Dp[0] * (q[1] + v->Dp[1] * q[2]);
+}
+
+static float dyn_guide(const void* ctx, const float g[3], const float u[2])
+{
+    const orc_vol* v = (const orc_vol*)ctx;
+    float w[3];
+    mh_dir(u, w);
+    return (float)dyn_value(v, dyn_proxy_of(v, g), octant_of(w));
+}
+
+static void dyn_chain(orc_vol* v, const orc_frame* fr, size_t c)
+{
+    mh_walk(v->Dp, fr->seed ^ DYN_KEY, fr->frame, c, DYN_SG, DYN_SU, v->dch_g + c * 3, v->dch_u + c * 2, dyn_guide, v,
+            v->dsm_q, v->dsm_dir, c * MH_S, v->Bd);
+}
+
+/* probes of proxy q (index order) */
+static int dyn_probes(const orc_vol* v, int q, int* out)
+{
+    const int X = v->d.dims[0], Y = v->d.dims[1], Z = v->d.dims[2];
+    int qx = q % v->Dp[0], qy = (q / v->Dp[0]) % v->Dp[1], qz = q / (v->Dp[0] * v->Dp[1]), n = 0;
+    for (int z = 3 * qz; z < 3 * qz + 3 && z < Z; ++z)
+        for (int y = 3 * qy; y < 3 * qy + 3 && y < Y; ++y)
+            for (int x = 3 * qx; x < 3 * qx + 3 && x < X; ++x) out[n++] = x + X * (y + Y * z);
+    return n;
+}
+
+/* marks, the budget, and this frame's dynamic rays grouped by probe */
+static void dyn_marks(orc_vol* v)
+{
+    const size_t cells = (size_t)v->Pp * 8;
+    for (size_t k = 0; k < cells; ++k) v->dfirst[k] = UINT32_MAX;
+    for (size_t sidx = 0; sidx < v->Bd; ++sidx) {
+        const int o = octant_of(v->dsm_dir + sidx * 3), q = v->dsm_q[sidx];
+        int cell = dyn_value(v, q, o) > 0 ? q * 8 + o : -1;
+        v->dsm_cell[sidx] = cell;
+        if (cell >= 0 && v->dfirst[cell] == UINT32_MAX) v->dfirst[cell] = (uint32_t)sidx;
+    }
+    /* marked cells in first-sample order (each sample marks at most one cell) */
+    v->n_marked = 0;
+    for (size_t sidx = 0; sidx < v->Bd; ++sidx) {
+        int cell = v->dsm_cell[sidx];
+        if (cell >= 0 && v->dfirst[cell] == (uint32_t)sidx) v->dmark[v->n_marked++] = cell;
+    }
+    memset(v->dincl, 0, cells);
+    size_t used = 0;
+    int pr[27];
+    v->n_incl = 0;
+    for (int m = 0; m < v->n_marked; ++m) {
+        int cell = v->dmark[m];
+        size_t rays = (size_t)dyn_probes(v, cell / 8, pr) * (size_t)v->ntex[cell % 8];
+        if (used + rays > v->Rd) break;
+        used += rays;
+        v->dincl[cell] = 1;
+        v->n_incl++;
+    }
+    /* rays grouped by probe: octants in order, texels in the octant's list order */
+    const int X = v->d.dims[0], Y = v->d.dims[1], nn = v->d.n_irr * v->d.n_irr;
+    size_t r = 0;
+    for (int p = 0; p < v->P; ++p) {
+        v->doff[p] = (uint32_t)r;
+        int ix = p % X, iy = (p / X) % Y, iz = p / (X * Y);
+        int q = (ix / 3) + v->Dp[0] * ((iy / 3) + v->Dp[1] * (iz / 3));
+        for (int o = 0; o < 8; ++o) {
+            if (!v->dincl[q * 8 + o]) continue;
+            for (int j = 0; j < v->ntex[o]; ++j, ++r) {
+                v->d_p[r] = p;
+                v->d_k[r] = o * nn + j;
+            }
+        }
+    }
+    v->doff[v->P] = (uint32_t)r;
+    v->Rdyn = r;
+}
+
+static void dyn_ray(orc_vol* v, const orc_frame* fr, size_t r)
+{
+    float o[3];
+    probe_pos(v, v->d_p[r], o);
+    const float* d = v->tex_dir + (size_t)v->d_k[r] * 3;
+    hitrec h = vol_closest(v, o, d, v->tmin, INFINITY);
+    v->d_t[r] = h.tri >= 0 ? h.t : INFINITY;
+    v->d_tri[r] = h.tri;
+    shade_ray(v, fr, o, d, h, v->d_rad + r * 3, v->d_dep + r, NULL);
 }
 
 /* the samples of each probe, in sample order (counting sort by probe) */
@@ -2058,23 +2338,25 @@ static void mh_blend_probe(orc_vol* v, int p, int use_pilots, double h)
         sd[td * 2 + 1] += ds * ds;
         kd[td] += 1;
     }
-    for (int t = 0; t < Ti * Ti; ++t) {
-        if (!ki[t]) continue;
-        double k = ki[t], n = irn[t];
-        double w = k / (n + k);
-        if (w < 1.0 - h) w = 1.0 - h;
-        for (int c = 0; c < 3; ++c) irr[t * 3 + c] += w * (si[t * 3 + c] / k - irr[t * 3 + c]);
-        int nn = irn[t] + ki[t];
-        irn[t] = (uint8_t)(nn > 255 ? 255 : nn);
-    }
-    for (int t = 0; t < Td * Td; ++t) {
-        if (!kd[t]) continue;
-        double k = kd[t], n = den[t];
-        double w = k / (n + k);
-        if (w < 1.0 - h) w = 1.0 - h;
-        for (int c = 0; c < 2; ++c) dep[t * 2 + c] += w * (sd[t * 2 + c] / k - dep[t * 2 + c]);
-        int nn = den[t] + kd[t];
-        den[t] = (uint8_t)(nn > 255 ? 255 : nn);
+    batch_apply(irr, irn, si, ki, Ti * Ti, 3, h);
+    batch_apply(dep, den, sd, kd, Td * Td, 2, h);
+    if (v->d.dyn_ratio > 0) { /* then the dynamic rays of the probe, a second batch with hyst_dyn */
+        memset(si, 0, sizeof(double) * (size_t)Ti * Ti * 3);
+        memset(ki, 0, sizeof(int) * (size_t)Ti * Ti);
+        memset(sd, 0, sizeof(double) * (size_t)Td * Td * 2);
+        memset(kd, 0, sizeof(int) * (size_t)Td * Td);
+        for (uint32_t r = v->doff[p]; r < v->doff[p + 1]; ++r) {
+            const float* d = v->tex_dir + (size_t)v->d_k[r] * 3;
+            int ti = orc_texel_of_dir(d, ni), td = orc_texel_of_dir(d, nd);
+            for (int c = 0; c < 3; ++c) si[ti * 3 + c] += v->d_rad[(size_t)r * 3 + c];
+            ki[ti] += 1;
+            double ds = v->d_dep[r];
+            sd[td * 2 + 0] += ds;
+            sd[td * 2 + 1] += ds * ds;
+            kd[td] += 1;
+        }
+        batch_apply(irr, irn, si, ki, Ti * Ti, 3, (double)v->d.hyst_dyn);
+        batch_apply(dep, den, sd, kd, Td * Td, 2, (double)v->d.hyst_dyn);
     }
     border_copy(irr, irn, ni, 3);
     border_copy(dep, den, nd, 2);
@@ -2125,6 +2407,10 @@ static void* worker(void* arg)
             mh_sample_rays(j->v, j->fr, (size_t)p);
         else if (j->phase == 5)
             mh_blend_probe(j->v, p, (j->fr->frame & 1u) == 0, (double)j->v->d.hyst);
+        else if (j->phase == 6)
+            dyn_chain(j->v, j->fr, (size_t)p);
+        else if (j->phase == 7)
+            dyn_ray(j->v, j->fr, (size_t)p);
         else if (j->phase == 0)
             pilot_probe(j->v, j->fr, p);
         else if (j->phase == 1)
@@ -2140,8 +2426,13 @@ static void* worker(void* arg)
 
 static void run_phase(orc_vol* v, const orc_frame* fr, int phase)
 {
-    /* phases 3 and 4 run over chains and samples, the others over probes */
-    const long long N = phase == 3 ? (long long)v->C : phase == 4 ? (long long)v->B : (long long)v->P;
+    /* phases 3 and 4 run over chains and samples, 6 and 7 over dynamic
+       chains and rays, the others over probes */
+    const long long N = phase == 3   ? (long long)v->C
+                        : phase == 4 ? (long long)v->B
+                        : phase == 6 ? (long long)v->Cd
+                        : phase == 7 ? (long long)v->Rdyn
+                                     : (long long)v->P;
     if (N == 0) return;
     int nt = v->nthreads;
     if (nt > N) nt = (int)N;
@@ -2179,6 +2470,12 @@ EXPORT int orc_update(orc_vol* v, const orc_frame* fr)
         run_phase(v, fr, 3);
         run_phase(v, fr, 4);
         mh_group(v);
+        if (v->d.dyn_ratio > 0) { /* the dynamic chains run after the static ones */
+            if (!v->dyn_live) dyn_init(v, fr->seed);
+            run_phase(v, fr, 6);
+            dyn_marks(v);
+            run_phase(v, fr, 7);
+        }
         run_phase(v, fr, 5);
         return 0;
     }
@@ -2248,6 +2545,35 @@ EXPORT void orc_border_copy(double* tile, uint8_t* cnt, int n, int ch) { border_
 
 /* Metropolis sampler state and samples (desc.sampler = 1) */
 EXPORT long long orc_mh_samples(const orc_vol* v) { return (long long)v->B; }
+EXPORT const uint32_t* orc_qd(const orc_vol* v) { return v->qd; }
+EXPORT void orc_dyn_sizes(const orc_vol* v, long long out[8])
+{
+    out[0] = (long long)v->Cd;
+    out[1] = (long long)v->Bd;
+    out[2] = (long long)v->Rd;
+    out[3] = (long long)v->Rdyn;
+    out[4] = v->n_marked;
+    out[5] = v->n_incl;
+    out[6] = v->Pp;
+    out[7] = 0;
+}
+EXPORT const float* orc_dyn_chain_g(const orc_vol* v) { return v->dch_g; }
+EXPORT const float* orc_dyn_chain_u(const orc_vol* v) { return v->dch_u; }
+EXPORT const int* orc_dyn_proxy(const orc_vol* v) { return v->dsm_q; }
+EXPORT const float* orc_dyn_dir(const orc_vol* v) { return v->dsm_dir; }
+EXPORT const int* orc_dyn_cell(const orc_vol* v) { return v->dsm_cell; }
+EXPORT const int* orc_dyn_marks(const orc_vol* v) { return v->dmark; }
+EXPORT const uint32_t* orc_dyn_off(const orc_vol* v) { return v->doff; }
+EXPORT const int* orc_dyn_ray_probe(const orc_vol* v) { return v->d_p; }
+EXPORT const int* orc_dyn_ray_key(const orc_vol* v) { return v->d_k; }
+EXPORT const float* orc_dyn_t(const orc_vol* v) { return v->d_t; }
+EXPORT const int* orc_dyn_tri(const orc_vol* v) { return v->d_tri; }
+EXPORT const double* orc_dyn_rad(const orc_vol* v) { return v->d_rad; }
+EXPORT const double* orc_dyn_dep(const orc_vol* v) { return v->d_dep; }
+EXPORT int orc_dyn_ntex(const orc_vol* v, int o) { return v->ntex[o & 7]; }
+EXPORT const int* orc_dyn_tex(const orc_vol* v) { return v->tex_t; }
+EXPORT const float* orc_dyn_tex_dir(const orc_vol* v) { return v->tex_dir; }
+EXPORT void orc_texel_centre_dir(int cx, int cy, int n, float w[3]) { texel_centre_dir(cx, cy, n, w); }
 EXPORT long long orc_mh_chains(const orc_vol* v) { return (long long)v->C; }
 EXPORT const float* orc_mh_chain_g(const orc_vol* v) { return v->ch_g; }
 EXPORT const float* orc_mh_chain_u(const orc_vol* v) { return v->ch_u; }

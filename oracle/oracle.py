@@ -29,6 +29,8 @@ class OrcDesc(C.Structure):
         ("packed", C.c_int),
         ("sampler", C.c_int),
         ("alpha", C.c_float),
+        ("dyn_ratio", C.c_int),
+        ("hyst_dyn", C.c_float),
     ]
 
 
@@ -138,6 +140,20 @@ def lib():
                          ("orc_mh_tri_neg", i32p), ("orc_mh_rad", f64p), ("orc_mh_dep", f64p)]:
             getattr(L, name).argtypes = [vp]
             getattr(L, name).restype = rt
+        L.orc_qd.argtypes = [vp]
+        L.orc_qd.restype = C.POINTER(C.c_uint32)
+        L.orc_dyn_sizes.argtypes = [vp, C.POINTER(C.c_longlong)]
+        for name, rt in [("orc_dyn_chain_g", f32p), ("orc_dyn_chain_u", f32p), ("orc_dyn_proxy", i32p),
+                         ("orc_dyn_dir", f32p), ("orc_dyn_cell", i32p), ("orc_dyn_marks", i32p),
+                         ("orc_dyn_off", C.POINTER(C.c_uint32)), ("orc_dyn_ray_probe", i32p),
+                         ("orc_dyn_ray_key", i32p), ("orc_dyn_t", f32p), ("orc_dyn_tri", i32p),
+                         ("orc_dyn_rad", f64p), ("orc_dyn_dep", f64p), ("orc_dyn_tex", i32p),
+                         ("orc_dyn_tex_dir", f32p)]:
+            getattr(L, name).argtypes = [vp]
+            getattr(L, name).restype = rt
+        L.orc_dyn_ntex.argtypes = [vp, C.c_int]
+        L.orc_dyn_ntex.restype = C.c_int
+        L.orc_texel_centre_dir.argtypes = [C.c_int, C.c_int, C.c_int, f32p]
         L.orc_mh_guide.argtypes = [vp, C.POINTER(OrcFrame), f32p, f32p]
         L.orc_mh_guide.restype = C.c_float
         L.orc_mh_run_table.argtypes = [i32p, f32p, C.c_int, C.c_int, C.c_int, C.c_uint64, f64p]
@@ -195,6 +211,13 @@ def mh_run_table(dims, table, chains, frames, skip, seed=1):
     lib().orc_mh_run_table(_p(d, C.c_int), _p(t, C.c_float), int(chains), int(frames), int(skip), int(seed),
                            _p(out, C.c_double))
     return out.reshape(-1, 8)
+
+
+def texel_centre_dir(cx: int, cy: int, n: int) -> np.ndarray:
+    """FP32 direction through the centre of interior texel (cx, cy) of an n x n octahedral grid"""
+    w = np.zeros(3, np.float32)
+    lib().orc_texel_centre_dir(int(cx), int(cy), int(n), _p(w, C.c_float))
+    return w
 
 
 def mh_exp(k: int) -> float:
@@ -324,7 +347,8 @@ class OracleVolume:
     """FP64 oracle volume with the same five-call shape as the C-ABI."""
 
     def __init__(self, origin, spacing, dims, n_irr=6, n_dep=14, rays_avg=64, rays_min=8, rays_max=256,
-                 hysteresis=0.97, depth_max=0.0, theta=16, threads=None, packed=False, sampler=0, alpha=1.0):
+                 hysteresis=0.97, depth_max=0.0, theta=16, threads=None, packed=False, sampler=0, alpha=1.0,
+                 dyn_ratio=0, hyst_dyn=0.91):
         d = OrcDesc()
         d.origin[:] = [float(x) for x in origin]
         d.spacing[:] = [float(x) for x in spacing]
@@ -338,6 +362,8 @@ class OracleVolume:
         self.packed = bool(packed)
         d.sampler = int(sampler)
         d.alpha = float(alpha)
+        d.dyn_ratio = int(dyn_ratio)
+        d.hyst_dyn = float(hyst_dyn)
         self.desc = d
         if threads is None:
             threads = os.cpu_count() or 1
@@ -471,6 +497,52 @@ class OracleVolume:
 
     def mh_dep(self):
         return self._arr("orc_mh_dep", self.mh_samples, np.float64)
+
+    def qd(self):
+        """per (probe, octant) dynamic weight q_d of the last update"""
+        return self._arr("orc_qd", self.P * 8, np.uint32, (self.P, 8))
+
+    # dynamic chains (dyn_ratio > 0)
+    def dyn_sizes(self):
+        """dict: chains, samples, ray budget, rays this frame, marked cells, traced cells, proxies"""
+        out = (C.c_longlong * 8)()
+        lib().orc_dyn_sizes(self.h, out)
+        return dict(zip(("chains", "samples", "budget", "rays", "marked", "traced", "proxies"), [int(x) for x in out]))
+
+    def dyn_chain_state(self):
+        n = self.dyn_sizes()["chains"]
+        return (self._arr("orc_dyn_chain_g", n * 3, np.float32, (n, 3)),
+                self._arr("orc_dyn_chain_u", n * 2, np.float32, (n, 2)))
+
+    def dyn_samples(self):
+        """(proxy int32[Bd], direction float32[Bd, 3], cell int32[Bd] (-1: target 0))"""
+        n = self.dyn_sizes()["samples"]
+        return (self._arr("orc_dyn_proxy", n, np.int32), self._arr("orc_dyn_dir", n * 3, np.float32, (n, 3)),
+                self._arr("orc_dyn_cell", n, np.int32))
+
+    def dyn_marks(self):
+        """marked cells in first-sample order, and how many of them were traced"""
+        s = self.dyn_sizes()
+        return self._arr("orc_dyn_marks", s["marked"], np.int32), s["traced"]
+
+    def dyn_rays(self):
+        """dict of this frame's dynamic rays grouped by probe"""
+        n = self.dyn_sizes()["rays"]
+        return {"off": self._arr("orc_dyn_off", self.P + 1, np.uint32),
+                "probe": self._arr("orc_dyn_ray_probe", n, np.int32), "key": self._arr("orc_dyn_ray_key", n, np.int32),
+                "t": self._arr("orc_dyn_t", n, np.float32), "tri": self._arr("orc_dyn_tri", n, np.int32),
+                "rad": self._arr("orc_dyn_rad", n * 3, np.float64, (n, 3)), "dep": self._arr("orc_dyn_dep", n, np.float64)}
+
+    def dyn_texels(self):
+        """per octant: (tile texel indices, centre directions) of the irradiance texels whose centre lies in it"""
+        nn = self.n_irr * self.n_irr
+        t = self._arr("orc_dyn_tex", 8 * nn, np.int32, (8, nn))
+        d = self._arr("orc_dyn_tex_dir", 8 * nn * 3, np.float32, (8, nn, 3))
+        out = []
+        for o in range(8):
+            k = int(lib().orc_dyn_ntex(self.h, o))
+            out.append((t[o, :k].copy(), d[o, :k].copy()))
+        return out
 
     def mh_chain_state(self):
         C_ = self.mh_chains

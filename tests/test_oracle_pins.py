@@ -846,3 +846,165 @@ def test_mh_visibility_ray_is_opposite():
     lo = r * math.cos(math.pi / 64) * math.cos(math.pi / 32)
     assert (dep <= r * (1 + 1e-6)).all() and (dep >= lo * (1 - 1e-6)).all()
     assert (v.mh_tri()[m] >= 0).all() and (v.mh_tri_neg()[m] >= 0).all()
+
+
+# --------------------------------------------------------------- dynamic chains (virtual proxies)
+def test_dyn_texel_centre_table():
+    # every interior irradiance texel appears in exactly one octant list; its
+    # FP32 centre direction is unit length, lies in that octant and bins back
+    # to the texel (so a dynamic ray updates exactly the texel it was aimed at)
+    for n in (1, 2, 6, 7):
+        v = O.OracleVolume((0, 0, 0), (1, 1, 1), (3, 3, 3), n_irr=n, rays_avg=16, rays_min=8, rays_max=64,
+                           sampler=1, dyn_ratio=4)
+        tabs = v.dyn_texels()
+        seen = np.concatenate([t for t, _ in tabs])
+        T = n + 2
+        interior = sorted((i + 1) * T + (j + 1) for i in range(n) for j in range(n))
+        assert sorted(seen.tolist()) == interior
+        for o, (ts, ds) in enumerate(tabs):
+            for t, d in zip(ts, ds):
+                assert abs(float(np.linalg.norm(d.astype(np.float64))) - 1.0) < 1e-6
+                assert ((d[0] < 0) | ((d[1] < 0) << 1) | ((d[2] < 0) << 2)) == o
+                assert O.texel_of_dir(d, n) == t
+                np.testing.assert_array_equal(d, O.texel_centre_dir(t % T - 1, t // T - 1, n))
+
+
+def test_dyn_budget_split():
+    # adaptive samples B = (avg - 8) P split r:1: the static chains draw
+    # floor(B r / (r + 1)) samples, the dynamic rays get twice the rest (a
+    # static sample traces two rays), with ceil(C_s / r) dynamic chains
+    for r, avg, dims in ((4, 64, (4, 4, 4)), (1, 16, (3, 5, 2)), (3, 8, (2, 2, 2)), (7, 40, (9, 5, 7))):
+        v = O.OracleVolume((0, 0, 0), (1, 1, 1), dims, rays_avg=avg, rays_min=8, rays_max=256, sampler=1, dyn_ratio=r)
+        P = int(np.prod(dims))
+        B = (avg - 8) * P
+        Bs = B * r // (r + 1)
+        Cs = (Bs + 4) // 5
+        s = v.dyn_sizes()
+        assert v.mh_samples == Bs and v.mh_chains == Cs
+        assert s["budget"] == 2 * (B - Bs)
+        assert s["chains"] == (Cs + r - 1) // r and s["samples"] == 5 * s["chains"]
+        assert s["proxies"] == int(np.prod([(d + 2) // 3 for d in dims]))
+    with pytest.raises(ValueError):  # the dynamic chains belong to the Metropolis mode
+        O.OracleVolume((0, 0, 0), (1, 1, 1), (3, 3, 3), rays_avg=16, sampler=0, dyn_ratio=4)
+
+
+def _proxy_probes(q, dims):
+    Dp = [(d + 2) // 3 for d in dims]
+    qx, qy, qz = q % Dp[0], (q // Dp[0]) % Dp[1], q // (Dp[0] * Dp[1])
+    return [x + dims[0] * (y + dims[1] * z) for z in range(3 * qz, min(3 * qz + 3, dims[2]))
+            for y in range(3 * qy, min(3 * qy + 3, dims[1])) for x in range(3 * qx, min(3 * qx + 3, dims[0]))]
+
+
+def _dyn_room(hyst=0.97, hyst_dyn=0.91, dims=(4, 4, 4), r=4, frames=6):
+    w = S.box_room(1)
+    vd = w.volume
+    spacing = tuple(7.0 / (d - 1) for d in dims)
+    v = O.OracleVolume((0.5, 0.5, 0.5), spacing, dims, rays_avg=48, rays_min=8, rays_max=128, hysteresis=hyst,
+                       theta=8, sampler=1, alpha=1.0, dyn_ratio=r, hyst_dyn=hyst_dyn)
+    v.set_scene(w.verts, w.idx, w.albedo)
+    on = w.lights_at(0)
+    for f in range(frames):  # the light is off on the second frame of every pair: a change in each pair
+        v.update(f, 9, on if f % 2 == 0 else [])
+    return w, v, dims
+
+
+def test_dyn_marks_proxy_max_and_rays():
+    w, v, dims = _dyn_room()
+    qd = v.qd().astype(np.int64)
+    assert qd.sum() > 0  # the toggling light gives the scene a dynamic component
+    proxy, d, cell = v.dyn_samples()
+    octant = (d[:, 0] < 0) | ((d[:, 1] < 0) << 1) | ((d[:, 2] < 0) << 2)
+    # the coarsened target: max of q_d over the proxy's (clipped) 3x3x3 probes
+    target = np.array([qd[_proxy_probes(q, dims), o].max() for q, o in zip(proxy, octant)])
+    np.testing.assert_array_equal(cell, np.where(target > 0, proxy * 8 + octant, -1))
+    # marks: each positive cell once, in the order of its first sample
+    pos = np.flatnonzero(cell >= 0)
+    _, first = np.unique(cell[pos], return_index=True)
+    marks, traced = v.dyn_marks()
+    np.testing.assert_array_equal(marks, cell[pos][np.sort(first)])
+    ntex = [len(t) for t, _ in v.dyn_texels()]
+    per_mark = np.array([len(_proxy_probes(c // 8, dims)) * ntex[c % 8] for c in marks], np.int64)
+    s = v.dyn_sizes()
+    csum = np.cumsum(per_mark)
+    assert traced == int((csum <= s["budget"]).sum()) and s["rays"] == (int(csum[traced - 1]) if traced else 0)
+    assert 0 < traced < len(marks)  # the budget cap binds in this case
+    # the rays, grouped by probe: from every probe of a traced cell, one ray
+    # per texel of the octant, through the texel centre
+    R = v.dyn_rays()
+    tabs = v.dyn_texels()
+    nn = 36
+    expect = []
+    X, Y = dims[0], dims[1]
+    inc = set(marks[:traced].tolist())
+    for p in range(int(np.prod(dims))):
+        q = (p % X) // 3 + ((dims[0] + 2) // 3) * (((p // X) % Y) // 3 + ((dims[1] + 2) // 3) * ((p // (X * Y)) // 3))
+        for o in range(8):
+            if q * 8 + o in inc:
+                expect += [(p, o * nn + j) for j in range(ntex[o])]
+    assert [(int(a), int(b)) for a, b in zip(R["probe"], R["key"])] == expect
+    np.testing.assert_array_equal(R["off"], np.searchsorted(R["probe"], np.arange(len(R["off"])), side="left"))
+    # hits against the brute-force trace
+    o_ = np.stack([v.probe_pos(int(p)) for p in R["probe"]]).astype(np.float32)
+    dirs = np.stack([tabs[k // nn][1][k % nn] for k in R["key"]]).astype(np.float32)
+    t, tri, _ = O.trace_closest(w.verts, w.idx, o_, dirs, v.tmin, np.inf, use_bvh=False)
+    np.testing.assert_array_equal(tri, R["tri"])
+    hit = tri >= 0
+    np.testing.assert_array_equal(t[hit], R["t"][hit])
+
+
+def test_dyn_blend_step_closed_form():
+    # hyst_dyn = 0: the dynamic batch weight is max(1, k/(n+k)) = 1, so after
+    # the update a texel reached by k dynamic rays holds their mean radiance
+    # (and their mean depth moments) whatever the static samples did before
+    w, v, dims = _dyn_room(hyst_dyn=0.0)
+    R = v.dyn_rays()
+    assert len(R["probe"]) > 0
+    tabs = v.dyn_texels()
+    nn = 36
+    irr, dep = v.irr(), v.dep()
+    sums, cnt = {}, {}
+    dsum, dcnt = {}, {}
+    for p, k, rad, dp in zip(R["probe"], R["key"], R["rad"], R["dep"]):
+        t = int(tabs[k // nn][0][k % nn])
+        sums[(p, t)] = sums.get((p, t), 0) + rad
+        cnt[(p, t)] = cnt.get((p, t), 0) + 1
+        td = O.texel_of_dir(tabs[k // nn][1][k % nn], 14)
+        dsum[(p, td)] = dsum.get((p, td), 0) + np.array([dp, dp * dp])
+        dcnt[(p, td)] = dcnt.get((p, td), 0) + 1
+    for (p, t), s_ in sums.items():
+        np.testing.assert_allclose(irr[p].reshape(-1, 3)[t], s_ / cnt[(p, t)], rtol=1e-12, atol=1e-15)
+    for (p, t), s_ in dsum.items():
+        np.testing.assert_allclose(dep[p].reshape(-1, 2)[t], s_ / dcnt[(p, t)], rtol=1e-12, atol=1e-15)
+
+
+def test_dyn_static_samples_snap_to_texel_centres():
+    # static samples whose probe and octant carry q_d > 0 trace through texel
+    # centres: +w through the centre of its irradiance texel, -w through the
+    # centre of the visibility texel of -w
+    w, v, dims = _dyn_room(frames=6)
+    qd = v.qd()
+    p, d = v.mh_probe(), v.mh_dir()
+    octant = (d[:, 0] < 0) | ((d[:, 1] < 0) << 1) | ((d[:, 2] < 0) << 2)
+    snap = qd[p, octant] > 0
+    assert snap.sum() > 0
+    idx = np.flatnonzero(snap)[:300]
+    o_ = np.stack([v.probe_pos(int(q)) for q in p[idx]]).astype(np.float32)
+    dp, dn = [], []
+    for k in idx:
+        t = O.texel_of_dir(d[k], 6)
+        dp.append(O.texel_centre_dir(t % 8 - 1, t // 8 - 1, 6))
+        tn = O.texel_of_dir(-d[k], 14)
+        dn.append(O.texel_centre_dir(tn % 16 - 1, tn // 16 - 1, 14))
+    _, trp, _ = O.trace_closest(w.verts, w.idx, o_, np.array(dp), v.tmin, np.inf, use_bvh=False)
+    _, trn, _ = O.trace_closest(w.verts, w.idx, o_, np.array(dn), v.tmin, np.inf, use_bvh=False)
+    np.testing.assert_array_equal(trp, v.mh_tri()[idx])
+    np.testing.assert_array_equal(trn, v.mh_tri_neg()[idx])
+    # the first frame has no pair yet (q_d = 0): samples trace their own directions
+    w, v, dims = _dyn_room(frames=1)
+    assert v.qd().sum() == 0
+    p, d = v.mh_probe()[:300], v.mh_dir()[:300]
+    o_ = np.stack([v.probe_pos(int(q)) for q in p]).astype(np.float32)
+    _, trp, _ = O.trace_closest(w.verts, w.idx, o_, d, v.tmin, np.inf, use_bvh=False)
+    _, trn, _ = O.trace_closest(w.verts, w.idx, o_, -d, v.tmin, np.inf, use_bvh=False)
+    np.testing.assert_array_equal(trp, v.mh_tri()[:300])
+    np.testing.assert_array_equal(trn, v.mh_tri_neg()[:300])
