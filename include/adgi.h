@@ -89,6 +89,19 @@ typedef struct {
                                Alg. MetropolisStep); each sample also traces -w for the visibility
                                texel at -w.  Not with atlas_fp16 = 3 or adgi_autotune */
     float alpha;            /* sampler = 1: confidence alpha of the cached irradiance, >= 0 */
+    int32_t dyn_ratio;      /* sampler = 1: > 0 adds the dynamic chains (Sec. "Adaptive sampling -
+                               dynamic"): proxies of 3x3x3 probes, target max over the proxy of the
+                               per-octant dynamic weight q_d (alpha = 0), steps 3x and 6x the static
+                               ones; a sample marks its (proxy, octant) cell once per frame, and marked
+                               cells in first-sample order send, within the dynamic ray budget, one ray
+                               from each probe of the proxy through the centre of every irradiance
+                               texel of the octant.  The adaptive budget is split static:dynamic =
+                               dyn_ratio:1 (the paper's 4096:1024 chains at 4): floor(B r/(r+1)) static
+                               samples, 2 (B - that) dynamic rays, ceil(C_s / r) dynamic chains; static
+                               samples at probes and octants with q_d > 0 trace through texel centres.
+                               0: off.  <= 1024 */
+    float hysteresis_dyn;   /* dyn_ratio > 0: hysteresis of the dynamic rays' batch step, applied after
+                               the static samples' (Table cacheDetails: 0.91), in [0, 1) */
 } adgi_volume_desc;
 
 /* kind 0: point light at pos_or_dir with intensity rgb (irradiance rgb/d^2);
@@ -115,7 +128,8 @@ typedef struct {
 typedef struct {
     uint64_t frames;          /* updates run so far */
     uint64_t rays_per_update; /* rays_avg * probes: pilot + adaptive rays (Metropolis volumes:
-                                 8 * probes + 2 * samples, the -w visibility rays included) */
+                                 8 * probes + 2 * samples, the -w visibility rays included, plus
+                                 the last update's dynamic rays) */
     uint64_t pilot_rays;      /* 8 * probes */
     uint64_t shadow_rays;     /* shadow rays of the last update (counted on the device) */
     uint32_t bvh_nodes;       /* internal nodes of the current BVH */
@@ -269,6 +283,17 @@ int adgi_enable_timing(adgi_volume vol, int32_t enable);
  *   ADGI_STATE_MH_HIT_NEG int32[B][2]     -w hits in grouped order (as PILOT_HIT); MAIN_HIT and
  *                       MAIN_REC then hold the +w hits and records in grouped order, and N and
  *                       OFF are not computed (the chains replace the per-probe counts)
+ *   ADGI_STATE_QD       uint32[P][8]      dynamic weight q_d per probe and octant (W_p is their sum)
+ * Dynamic chains (dyn_ratio > 0; Cd chains, Bd = 5 Cd samples, Pp proxies, Rd = ray budget):
+ *   ADGI_STATE_DYN_CHAINS  float[2][Cd][4] chain states (as MH_CHAINS, in proxy-grid units)
+ *   ADGI_STATE_DYN_SAMPLES float[Bd][4]    {w.xyz, proxy (int32 bits)}, chain order
+ *   ADGI_STATE_DYN_CELLS   int32[Bd]       proxy*8 + octant of each sample, -1 where the target is 0
+ *   ADGI_STATE_DYN_FIRST   uint32[Pp*8]    first sample marking each cell (0xFFFFFFFF: unmarked)
+ *   ADGI_STATE_DYN_INCL    uint8[Pp*8]     1: the cell's rays were traced
+ *   ADGI_STATE_DYN_OFF     uint32[P+1]     first dynamic ray of each probe (off[P] = rays)
+ *   ADGI_STATE_DYN_HIT     int32[Rd][2]    dynamic ray hits (as PILOT_HIT), grouped by probe:
+ *                       octants in order, texels in texel order within the octant
+ *   ADGI_STATE_DYN_REC     float[Rd][4]    dynamic ray records {r, g, b, depth}
  * The scene is traced as two parts: triangles that touch any vertex ever passed
  * to adgi_move_vertices form the moving part (linear BVH, rebuilt at the next
  * update after each move); the others form the static part (agglomerative
@@ -299,7 +324,16 @@ enum {
     ADGI_STATE_MH_SAMPLES = 21,
     ADGI_STATE_MH_ORDER = 22,
     ADGI_STATE_MH_OFF = 23,
-    ADGI_STATE_MH_HIT_NEG = 24
+    ADGI_STATE_MH_HIT_NEG = 24,
+    ADGI_STATE_QD = 25,
+    ADGI_STATE_DYN_CHAINS = 26,
+    ADGI_STATE_DYN_SAMPLES = 27,
+    ADGI_STATE_DYN_CELLS = 28,
+    ADGI_STATE_DYN_FIRST = 29,
+    ADGI_STATE_DYN_INCL = 30,
+    ADGI_STATE_DYN_OFF = 31,
+    ADGI_STATE_DYN_HIT = 32,
+    ADGI_STATE_DYN_REC = 33
 };
 int adgi_state_bytes(adgi_volume vol, int32_t which, uint64_t* bytes);
 int adgi_read_state(adgi_volume vol, int32_t which, void* dst_host, uint64_t bytes);

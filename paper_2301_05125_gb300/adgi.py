@@ -18,7 +18,9 @@ ERRORS = {-1: "INVALID_ARG", -2: "OOM", -3: "OVER_BUDGET", -4: "NO_SCENE", -5: "
 
 STATE = dict(W=0, N=1, OFF=2, QV=3, QR=4, TRV=5, TRR=6, PILOT_HIT=7, PILOT_REC=8, PILOT_LUM=9, MAIN_HIT=10,
              MAIN_REC=11, IRR=12, DEP=13, DEP_N=14, ROT=15, BVH_NODES=16, BVH_TRIS=17, MOVING_BVH_NODES=18,
-             MOVING_BVH_TRIS=19, MH_CHAINS=20, MH_SAMPLES=21, MH_ORDER=22, MH_OFF=23, MH_HIT_NEG=24)
+             MOVING_BVH_TRIS=19, MH_CHAINS=20, MH_SAMPLES=21, MH_ORDER=22, MH_OFF=23, MH_HIT_NEG=24,
+             QD=25, DYN_CHAINS=26, DYN_SAMPLES=27, DYN_CELLS=28, DYN_FIRST=29, DYN_INCL=30, DYN_OFF=31, DYN_HIT=32,
+             DYN_REC=33)
 
 
 class AdgiError(RuntimeError):
@@ -43,6 +45,8 @@ class adgi_volume_desc(C.Structure):
         ("tr_theta", C.c_int32),
         ("sampler", C.c_int32),
         ("alpha", C.c_float),
+        ("dyn_ratio", C.c_int32),
+        ("hysteresis_dyn", C.c_float),
     ]
 
 
@@ -391,7 +395,7 @@ def adgi_last_error() -> str:
 # ------------------------------------------------------------ convenience
 def make_desc(origin, spacing, dims, irr_interior=6, depth_interior=14, rays_avg=64, rays_min=8, rays_max=256,
               hysteresis=0.97, depth_max=0.0, atlas_fp16=0, tr_theta=16, sampler=0,
-              alpha=1.0) -> adgi_volume_desc:
+              alpha=1.0, dyn_ratio=0, hysteresis_dyn=0.91) -> adgi_volume_desc:
     d = adgi_volume_desc()
     d.origin[:] = [float(x) for x in origin]
     d.spacing[:] = [float(x) for x in spacing]
@@ -404,6 +408,8 @@ def make_desc(origin, spacing, dims, irr_interior=6, depth_interior=14, rays_avg
     d.tr_theta = int(tr_theta)
     d.sampler = int(sampler)
     d.alpha = float(alpha)
+    d.dyn_ratio = int(dyn_ratio)
+    d.hysteresis_dyn = float(hysteresis_dyn)
     return d
 
 
@@ -550,6 +556,34 @@ class Volume:
 
     def mh_hit_neg(self):
         return self.state("MH_HIT_NEG", np.int32).reshape(-1, 2)
+
+    def qd(self):
+        return self.state("QD", np.uint32).reshape(self.P, 8)
+
+    # dynamic chains (dyn_ratio > 0)
+    def dyn_chains(self):
+        a = self.state("DYN_CHAINS", np.float32).reshape(2, -1, 4)
+        return a[0, :, :3].copy(), np.stack([a[0, :, 3], a[1, :, 0]], axis=1)
+
+    def dyn_samples(self):
+        """(proxy int32[Bd], direction float32[Bd, 3], cell int32[Bd])"""
+        a = self.state("DYN_SAMPLES", np.float32).reshape(-1, 4)
+        return a[:, 3].copy().view(np.int32), a[:, :3].copy(), self.state("DYN_CELLS", np.int32)
+
+    def dyn_first(self):
+        return self.state("DYN_FIRST", np.uint32)
+
+    def dyn_incl(self):
+        return self.state("DYN_INCL", np.uint8)
+
+    def dyn_off(self):
+        return self.state("DYN_OFF", np.uint32)
+
+    def dyn_hit(self):
+        return self.state("DYN_HIT", np.int32).reshape(-1, 2)
+
+    def dyn_rec(self):
+        return self.state("DYN_REC", np.float32).reshape(-1, 4)
 
     @property
     def packed(self):

@@ -74,6 +74,7 @@ struct FrameConst {
     float cam[3];
     float cam_k;
     uint64_t mh_key;        // Metropolis counters of this frame: sm(sm(seed ^ 'METRO') ^ frame)
+    uint64_t dyn_key;       // the dynamic chains' counters: sm(sm(seed ^ 'DYNAM') ^ frame)
 };
 
 struct VolConst {
@@ -94,6 +95,20 @@ struct VolConst {
     float s_f;              // (float) cage diagonal: the packed visibility normaliser
     uint32_t R_main;        // main-ray buffer length
     int* err;               // anomaly flags (kErr*)
+    int dyn;                // dynamic chains on (Metropolis mode with dyn_ratio > 0)
+    float hyst_dyn;         // hysteresis of the dynamic rays' batch step
+};
+
+// This frame's dynamic rays (dynamic chains over virtual proxies), grouped
+// by probe: probe p sends, for every octant o whose proxy cell is traced,
+// one ray through the centre of each irradiance texel listed for o.
+struct DynRays {
+    const uint32_t* off;      // [P+1] first dynamic ray of each probe; off[P] = rays this frame
+    const uint8_t* incl;      // [Pp*8] 1: the cell (proxy, octant) is traced
+    const int* ntex;          // [8] texels whose centre lies in each octant
+    const int* tex_t;         // [8][n_irr^2] their tile indices
+    const float4* tex_dir;    // [8][n_irr^2] their centre directions
+    int dp[3];                // proxy grid
 };
 
 // ----------------------------------------------------------------- exact FP32
@@ -350,7 +365,18 @@ __device__ __forceinline__ void trav_init(Trav& T, int* stack, const SceneDev& S
 {
     T.wr = wray(o, d);
     T.o = o;
-    T.inv = make_float3(1.0f / d.x, 1.0f / d.y, 1.0f / d.z);
+    // The box test uses 1/d with components below 1e-20 in magnitude raised
+    // to +-1e-20: a zero component would make o * inv infinite and the FMA
+    // slab form inf - inf = NaN, rejecting every box (axis-aligned rays: an
+    // axis-aligned sun, texel-centre directions on the octahedral diamond).
+    // The raised component moves the ray by 1e-20 t along that axis, far
+    // below the boxes' enlargement, so the test stays conservative; the
+    // triangle test keeps the exact direction.
+    const float kTiny = 1e-20f;
+    const float dx = fabsf(d.x) < kTiny ? copysignf(kTiny, d.x) : d.x;
+    const float dy = fabsf(d.y) < kTiny ? copysignf(kTiny, d.y) : d.y;
+    const float dz = fabsf(d.z) < kTiny ? copysignf(kTiny, d.z) : d.z;
+    T.inv = make_float3(1.0f / dx, 1.0f / dy, 1.0f / dz);
     T.oi = make_float3(o.x * T.inv.x, o.y * T.inv.y, o.z * T.inv.z);
     T.next = -1;
     T.tmin = tmin;
@@ -677,7 +703,7 @@ __device__ __forceinline__ float3 query_irr_at(const VolConst& V, const void* ir
 {
     float os[3] = {o.x, o.y, o.z}, ds[3] = {d.x, d.y, d.z};
     int b[3];
-    float al[3];
+    float al[3], be[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         float g = floorf((fa(os[k], fm(t, ds[k])) - V.origin[k]) / V.spacing[k]);
@@ -694,7 +720,14 @@ __device__ __forceinline__ float3 query_irr_at(const VolConst& V, const void* ir
             }
         }
         b[k] = bi;
-        al[k] = fminf(fmaxf(l / V.spacing[k], 0.0f), 1.0f);
+        // both layer weights from the double-float offset l to plane b: alpha
+        // = l/s and 1 - alpha = (s - l)/s, each with full relative precision
+        // (1 - alpha formed in FP32 loses it next to the upper plane, where a
+        // nearly empty lower-layer weight can still decide the normalised sum)
+        const df lf = df_offset(os[k], pcoord(V, k, bi), t, ds[k]);
+        const df rf = df_add({V.spacing[k], 0.0f}, df_neg(lf));
+        al[k] = fminf(fmaxf(fa(lf.h, lf.l) / V.spacing[k], 0.0f), 1.0f);
+        be[k] = fminf(fmaxf(fa(rf.h, rf.l) / V.spacing[k], 0.0f), 1.0f);
     }
     float nl = sqrtf(nrm.x * nrm.x + nrm.y * nrm.y + nrm.z * nrm.z);
     float3 nd = nl > 0.0f ? make_float3(nrm.x / nl, nrm.y / nl, nrm.z / nl) : make_float3(0.f, 0.f, 1.f);
@@ -704,7 +737,7 @@ __device__ __forceinline__ float3 query_irr_at(const VolConst& V, const void* ir
 #pragma unroll 1
     for (int c = 0; c < 8; ++c) {
         int o0 = c & 1, o1 = (c >> 1) & 1, o2 = (c >> 2) & 1;
-        float wt = (o0 ? al[0] : 1.f - al[0]) * (o1 ? al[1] : 1.f - al[1]) * (o2 ? al[2] : 1.f - al[2]);
+        float wt = (o0 ? al[0] : be[0]) * (o1 ? al[1] : be[1]) * (o2 ? al[2] : be[2]);
         int ix = b[0] + o0, iy = b[1] + o1, iz = b[2] + o2;
         int p = ix + V.dims[0] * (iy + V.dims[1] * iz);
         float px = pcoord(V, 0, ix), py = pcoord(V, 1, iy), pz = pcoord(V, 2, iz);
@@ -752,6 +785,38 @@ __device__ __forceinline__ float3 query_irr_hit(const VolConst& V, const void* i
                                                 float3 d, float3 nrm)
 {
     return query_irr_at(V, irr, dep, o, t, d, nrm);
+}
+
+// Dynamic ray r: its probe p, irradiance texel t (tile index) and direction
+// d; false beyond this frame's rays.
+__device__ __forceinline__ bool dyn_ray_of(const VolConst& V, const DynRays& D, uint32_t r, int& p, int& t, float3& d)
+{
+    if (r >= __ldg(D.off + V.P)) return false;
+    int lo = 0, hi = V.P - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(D.off + mid) <= r)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    p = lo;
+    uint32_t j = r - __ldg(D.off + p);
+    const int ix = p % V.dims[0], iy = (p / V.dims[0]) % V.dims[1], iz = p / (V.dims[0] * V.dims[1]);
+    const int q = ix / 3 + D.dp[0] * (iy / 3 + D.dp[1] * (iz / 3));
+    const int nn = V.n_irr * V.n_irr;
+    for (int o = 0; o < 8; ++o) {
+        if (!__ldg(D.incl + q * 8 + o)) continue;
+        const uint32_t n = (uint32_t)__ldg(D.ntex + o);
+        if (j < n) {
+            t = __ldg(D.tex_t + o * nn + (int)j);
+            const float4 w = __ldg(D.tex_dir + o * nn + (int)j);
+            d = make_float3(w.x, w.y, w.z);
+            return true;
+        }
+        j -= n;
+    }
+    return false;
 }
 
 }  // namespace adgi

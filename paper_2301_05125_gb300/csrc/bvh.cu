@@ -636,6 +636,24 @@ cudaError_t radix_sort_pairs(uint64_t* const keys[2], uint32_t* const vals[2], u
     return cudaGetLastError();
 }
 
+// Exclusive scan of a[0..n) in place: one block for small arrays, the
+// three-launch scan (part: 1024 partial sums) for large ones.
+cudaError_t scan_exclusive_u32(uint32_t* a, int n, uint32_t* part, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    if (part != nullptr && n > 65536) {
+        const int G = std::min(kScanChunks, (n + 1023) / 1024), per = (n + G - 1) / G;
+        k_scan_reduce<<<G, 256, 0, s>>>(a, n, per, part);
+        k_scan_small<<<1, 1024, 0, s>>>(part, G);
+        k_scan_apply<<<G, 256, 0, s>>>(a, n, per, part);
+        count_launches(3);
+    } else {
+        k_scan_small<<<1, 1024, 0, s>>>(a, n);
+        count_launches(1);
+    }
+    return cudaGetLastError();
+}
+
 // Morton order of the listed triangles into B.tri_v (all builds start here)
 static cudaError_t morton_order(const BvhBufs& B, const float* d_verts, const int* d_idx, const int* list, int nv,
                                 int nt, int* err, cudaStream_t s, int* cur_out)

@@ -35,6 +35,7 @@ struct PlocBufs {
 
 size_t bvh_scratch_bytes(int nt);
 size_t radix_hist_entries(int n);
+cudaError_t scan_exclusive_u32(uint32_t* a, int n, uint32_t* part, cudaStream_t s);
 cudaError_t radix_sort_pairs(uint64_t* const keys[2], uint32_t* const vals[2], uint32_t* hist, int n, int bits,
                              cudaStream_t s, int* cur_out, uint32_t* part = nullptr);
 size_t carve_bvh_scratch(void* base, int nt, BvhBufs& B);

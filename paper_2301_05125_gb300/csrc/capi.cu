@@ -113,6 +113,7 @@ void build_sf(int M, std::vector<float4>& out)
 
 const uint64_t kMhSalt = 0x4D4554524Full;      // 'METRO': Metropolis counters
 const uint64_t kMhInitSalt = 0x494E4954ull;    // 'INIT': first chain states
+const uint64_t kDynSalt = 0x44594E414Dull;     // 'DYNAM': the dynamic chains
 
 // Host tables of the Metropolis sampler.  nq[i] = Phi^-1((i + 0.5) / 4096) by
 // Newton's method on Phi(x) = erfc(-x / sqrt 2) / 2 from x = 0 (monotone:
@@ -270,6 +271,28 @@ struct adgi_volume_s {
     int2* mh_hitn = nullptr;           // [B] -w hits, grouped order
     const uint32_t* mh_ord = nullptr;  // grouped order of the last update
     bool mh_live = false;              // chain states initialised
+    uint32_t* qd = nullptr;            // [P][8] q_d of the last update
+    // dynamic chains over virtual proxies (desc.dyn_ratio > 0)
+    uint32_t dyn_Cd = 0, dyn_Bd = 0, dyn_Rd = 0;
+    int dyn_dp[3] = {0, 0, 0}, dyn_pp = 0;
+    float4* mh_smp_gn = nullptr;       // [B] -w ray directions, grouped order
+    float4* dyn_chain = nullptr;       // [2Cd]
+    float4* dyn_smp = nullptr;         // [Bd]
+    int* dyn_cell = nullptr;           // [Bd]
+    uint32_t* dyn_val = nullptr;       // [Pp*8]
+    uint32_t* dyn_first = nullptr;     // [Pp*8]
+    uint64_t* dyn_keys = nullptr;      // [2][Pp*8]
+    uint32_t* dyn_vals = nullptr;      // [2][Pp*8]
+    uint32_t* dyn_hist = nullptr;
+    uint8_t* dyn_incl = nullptr;       // [Pp*8]
+    uint32_t* dyn_off = nullptr;       // [P+1]
+    uint32_t* dyn_part = nullptr;      // [1024]
+    uint32_t* dyn_info = nullptr;      // [2]
+    int* dyn_tab = nullptr;            // [8] texels per octant, then [8][n_irr^2] their tile indices
+    float4* dyn_tex_dir = nullptr;     // [8][n_irr^2]
+    int2* dyn_hit = nullptr;           // [Rd]
+    float4* dyn_rec = nullptr;         // [Rd]
+    bool dyn_live = false;
 };
 
 namespace {
@@ -282,6 +305,9 @@ void free_volume(adgi_volume v)
                     v->G,       v->W,       v->n,      v->off,   v->pil_hit, v->pil_rec, v->pil_lum, v->m_hit,
                     v->m_rec,   v->shadow_ctr, v->verts, v->idx, v->albedo,  v->q_buf, v->err,
                     v->vis,     v->jobs,    v->job_light, v->job_count, v->fdev,
+                    v->qd, v->mh_smp_gn, v->dyn_chain, v->dyn_smp, v->dyn_cell, v->dyn_val, v->dyn_first, v->dyn_keys,
+                    v->dyn_vals, v->dyn_hist, v->dyn_incl, v->dyn_off, v->dyn_part, v->dyn_info, v->dyn_tab,
+                    v->dyn_tex_dir, v->dyn_hit, v->dyn_rec,
                     v->mh_tab,  v->mh_chain, v->mh_smp, v->mh_smp_g, v->mh_keys, v->mh_vals, v->mh_hist, v->mh_off, v->mh_hitn};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -332,6 +358,10 @@ int validate_desc(const adgi_volume_desc* d)
         return fail(ADGI_ERR_INVALID_ARG, "the Metropolis sampler blends batched moving averages: not with packed atlases");
     if (d->sampler == 1 && !(d->alpha >= 0.0f && std::isfinite(d->alpha)))
         return fail(ADGI_ERR_INVALID_ARG, "alpha must be finite and >= 0");
+    if (d->dyn_ratio < 0 || d->dyn_ratio > 1024 || (d->dyn_ratio > 0 && d->sampler != 1))
+        return fail(ADGI_ERR_INVALID_ARG, "dyn_ratio in [0, 1024], and > 0 only with sampler = 1");
+    if (d->dyn_ratio > 0 && !(d->hysteresis_dyn >= 0.0f && d->hysteresis_dyn < 1.0f))
+        return fail(ADGI_ERR_INVALID_ARG, "hysteresis_dyn in [0,1)");
     int64_t P = (int64_t)d->dims[0] * d->dims[1] * d->dims[2];
     if (P * (int64_t)d->rays_avg >= (int64_t)1 << 31) return fail(ADGI_ERR_INVALID_ARG, "ray budget too large");
     return ADGI_OK;
@@ -351,12 +381,17 @@ FrameConst frame_const(adgi_volume v, const adgi_frame* f)
     for (int k = 0; k < 3; ++k) F.cam[k] = f->cam_pos[k];
     F.cam_k = f->cam_k;
     F.mh_key = splitmix(splitmix(f->seed ^ kMhSalt) ^ f->frame);
+    F.dyn_key = splitmix(splitmix(f->seed ^ kDynSalt) ^ f->frame);
     return F;
 }
 
 }  // namespace
 
 extern "C" {
+
+namespace {
+DynBufs dyn_bufs(adgi_volume v);
+}
 
 const char* adgi_last_error(void) { return g_err.c_str(); }
 
@@ -494,8 +529,14 @@ int adgi_create_volume(const adgi_volume_desc* desc, void* cuda_stream, adgi_vol
     DA(v->fdev, 1);
     DA(v->vis, std::max<size_t>(P * 8, (size_t)v->R_main));
     DA(v->job_count, 1);
+    DA(v->qd, P * 8);
     if (d.sampler == 1) {
         v->mh_B = v->R_main;
+        if (d.dyn_ratio > 0) {  // budget split static:dynamic = r:1; a static sample traces two rays
+            const uint64_t Bt = v->R_main, r = (uint64_t)d.dyn_ratio;
+            v->mh_B = (uint32_t)(Bt * r / (r + 1));
+            v->dyn_Rd = (uint32_t)(2 * (Bt - v->mh_B));
+        }
         v->mh_C = (v->mh_B + kMhPer - 1) / kMhPer;
         const size_t nB = v->mh_B;
         DA(v->mh_tab, (size_t)(kMhNq + kMhEx));
@@ -507,10 +548,37 @@ int adgi_create_volume(const adgi_volume_desc* desc, void* cuda_stream, adgi_vol
         DA(v->mh_hist, radix_hist_entries((int)nB) + 1024);
         DA(v->mh_off, P + 1);
         DA(v->mh_hitn, nB);
+        if (d.dyn_ratio > 0) {
+            const uint32_t r = (uint32_t)d.dyn_ratio;
+            v->dyn_Cd = v->mh_C ? (v->mh_C + r - 1) / r : 0;
+            v->dyn_Bd = v->dyn_Cd * kMhPer;
+            for (int k = 0; k < 3; ++k) v->dyn_dp[k] = (d.dims[k] + 2) / 3;
+            v->dyn_pp = v->dyn_dp[0] * v->dyn_dp[1] * v->dyn_dp[2];
+            const size_t cells = (size_t)v->dyn_pp * 8, nn = (size_t)V.n_irr * V.n_irr;
+            DA(v->mh_smp_gn, nB);
+            DA(v->dyn_chain, 2 * (size_t)v->dyn_Cd);
+            DA(v->dyn_smp, (size_t)v->dyn_Bd);
+            DA(v->dyn_cell, (size_t)v->dyn_Bd);
+            DA(v->dyn_val, cells);
+            DA(v->dyn_first, cells);
+            DA(v->dyn_keys, 2 * cells);
+            DA(v->dyn_vals, 2 * cells);
+            DA(v->dyn_hist, radix_hist_entries((int)cells));
+            DA(v->dyn_incl, cells);
+            DA(v->dyn_off, P + 1);
+            DA(v->dyn_part, 1024);
+            DA(v->dyn_info, 2);
+            DA(v->dyn_tab, 8 + 8 * nn);
+            DA(v->dyn_tex_dir, 8 * nn);
+            DA(v->dyn_hit, (size_t)v->dyn_Rd);
+            DA(v->dyn_rec, (size_t)v->dyn_Rd);
+        }
     }
 #undef DA
     V.R_main = v->R_main;
     V.err = v->err;
+    V.dyn = d.dyn_ratio > 0 ? 1 : 0;
+    V.hyst_dyn = d.hysteresis_dyn;
     cudaStream_t s = v->stream;
 #define CKV(call)                                                                                        \
     do {                                                                                                 \
@@ -541,7 +609,14 @@ int adgi_create_volume(const adgi_volume_desc* desc, void* cuda_stream, adgi_vol
         CKV(cudaMemcpyAsync(v->mh_tab, mh_tab.data(), sizeof(float) * mh_tab.size(), cudaMemcpyHostToDevice, s));
         CKV(cudaMemsetAsync(v->mh_off, 0, 4 * (P + 1), s));
         v->mh_ord = v->mh_vals;
+        if (V.dyn) {
+            CKV(cudaMemsetAsync(v->dyn_off, 0, 4 * (P + 1), s));
+            CKV(cudaMemsetAsync(v->dyn_incl, 0, (size_t)v->dyn_pp * 8, s));
+            CKV(cudaMemsetAsync(v->dyn_info, 0, 8, s));
+            CKV(launch_dyn_tables(V, dyn_bufs(v), s));
+        }
     }
+    CKV(cudaMemsetAsync(v->qd, 0, P * 8 * 4, s));
     v->shadow_blocks = shadow_grid_blocks(0);
     CKV(cudaEventCreate(&v->ev0));
     CKV(cudaEventCreate(&v->ev1));
@@ -741,7 +816,40 @@ MhBufs mh_bufs(adgi_volume v)
     M.lut_c = v->lut_c;
     M.qv = v->qv;
     M.irr = v->irr;
+    M.qd = v->V.dyn ? v->qd : nullptr;
+    M.smp_gn = v->V.dyn ? v->mh_smp_gn : nullptr;
     return M;
+}
+
+DynBufs dyn_bufs(adgi_volume v)
+{
+    DynBufs D{};
+    D.n_chains = v->dyn_Cd;
+    D.n_samples = v->dyn_Bd;
+    D.budget = v->dyn_Rd;
+    for (int k = 0; k < 3; ++k) D.dp[k] = v->dyn_dp[k];
+    D.pp = v->dyn_pp;
+    D.nq = v->mh_tab;
+    D.qd = v->qd;
+    D.chain = v->dyn_chain;
+    D.smp = v->dyn_smp;
+    D.cell = v->dyn_cell;
+    D.val = v->dyn_val;
+    D.first = v->dyn_first;
+    const size_t cells = (size_t)v->dyn_pp * 8;
+    D.keys[0] = v->dyn_keys;
+    D.keys[1] = v->dyn_keys ? v->dyn_keys + cells : nullptr;
+    D.vals[0] = v->dyn_vals;
+    D.vals[1] = v->dyn_vals ? v->dyn_vals + cells : nullptr;
+    D.hist = v->dyn_hist;
+    D.incl = v->dyn_incl;
+    D.off = v->dyn_off;
+    D.part = v->dyn_part;
+    D.info = v->dyn_info;
+    D.ntex = v->dyn_tab;
+    D.tex_t = v->dyn_tab ? v->dyn_tab + 8 : nullptr;
+    D.tex_dir = v->dyn_tex_dir;
+    return D;
 }
 
 SceneDev scene_view(adgi_volume v)
@@ -814,6 +922,12 @@ int prepare_update(adgi_volume v, const adgi_frame* f, FrameDev& fd, bool* graph
         v->mh_live = true;
         stale = true;
     }
+    if (V.dyn && !v->dyn_live) {
+        const uint64_t key = splitmix(splitmix(f->seed ^ kDynSalt ^ kMhInitSalt) ^ 0ull);
+        CK(launch_dyn_init(V, dyn_bufs(v), key, s));
+        v->dyn_live = true;
+        stale = true;
+    }
     if (graph_stale) *graph_stale = stale;
     return ADGI_OK;
 }
@@ -871,7 +985,7 @@ int enqueue_update(adgi_volume v, const FrameDev& fd, cudaStream_t s, bool phase
     // 2. heuristics -> W_p
     PHASE(3);
     ChangeBufs C{v->pil_hit, v->pil_lum, v->lut_v, v->lut_c, v->qv,  v->qr,  v->qv_even, v->qr_even,
-                 v->amp_v,   v->amp_r,   v->age_v, v->age_r, v->trv, v->trr, v->G,       v->W};
+                 v->amp_v,   v->amp_r,   v->age_v, v->age_r, v->trv, v->trr, v->G,       v->W, v->qd};
     CK(launch_change(V, FD, C, s));
     // 3. allocation
     PHASE(4);
@@ -883,16 +997,26 @@ int enqueue_update(adgi_volume v, const FrameDev& fd, cudaStream_t s, bool phase
         CK(launch_mh_chain(V, FD, M, s));
         CK(launch_mh_group(V, M, s, &ord));
         v->mh_ord = ord;
-        // 4'-5'. the samples' +w and -w rays; shading of the +w rays
+        DynRays R{};
+        if (V.dyn) {  // the dynamic chains, their marks and this frame's dynamic rays
+            const DynBufs D = dyn_bufs(v);
+            CK(launch_dyn_plan(V, FD, D, s));
+            R = dyn_rays_of(D);
+        }
+        // 4'-5'. the samples' +w and -w rays (and the dynamic rays); shading
         PHASE(5);
         CK(launch_mh_trace(V, S, M, v->m_hit, v->mh_hitn, T, s));
+        if (V.dyn) CK(launch_dyn_trace(V, S, R, v->dyn_Rd, v->dyn_hit, T, s));
         PHASE(6);
         CK(launch_shade(V, FD, S, 2, M.n_samples, nullptr, v->mh_smp_g, v->irr, v->dep, v->m_hit, v->m_rec, nullptr, W, T,
                         s, phases ? v->shq + 2 : nullptr));
-        // 6'. blend of the probes' samples
+        if (V.dyn)
+            CK(launch_shade(V, FD, S, 3, v->dyn_Rd, nullptr, nullptr, v->irr, v->dep, v->dyn_hit, v->dyn_rec, nullptr, W,
+                            T, s, nullptr, &R));
+        // 6'. blend of the probes' samples (then their dynamic rays)
         PHASE(7);
-        MhBlendBufs MB{M.n_samples, v->mh_off, v->mh_smp_g, v->m_rec, v->mh_hitn,
-                       v->pil_rec,  v->irr,    v->dep,      v->dep_n, v->tex_src};
+        MhBlendBufs MB{M.n_samples, v->mh_off, v->mh_smp_g, v->m_rec,  v->mh_hitn, v->pil_rec, v->irr,
+                       v->dep,      v->dep_n,  v->tex_src,  v->mh_smp_gn, R,         v->dyn_rec};
         CK(launch_mh_blend(V, FD, MB, s));
     } else {
         // 4-5. adaptive rays: trace, shade
@@ -1273,6 +1397,11 @@ int adgi_get_stats(adgi_volume v, adgi_stats* out)
     out->frames = v->frames;
     out->rays_per_update = v->desc.sampler == 1 ? (uint64_t)v->V.P * 8u + 2u * (uint64_t)v->mh_B
                                                 : (uint64_t)v->V.P * (uint64_t)v->V.rays_avg;
+    if (v->V.dyn) {  // plus the last update's dynamic rays
+        uint32_t nd = 0;
+        CK(cudaMemcpy(&nd, v->dyn_off + v->V.P, 4, cudaMemcpyDeviceToHost));
+        out->rays_per_update += nd;
+    }
     out->pilot_rays = (uint64_t)v->V.P * 8u;
     unsigned long long sc = 0;
     CK(cudaMemcpy(&sc, v->shadow_ctr, 8, cudaMemcpyDeviceToHost));
@@ -1338,6 +1467,27 @@ int adgi_state_bytes(adgi_volume v, int32_t which, uint64_t* bytes)
                  : which == ADGI_STATE_MH_OFF     ? 4 * (P + 1)
                                                   : 8 * (uint64_t)v->mh_B;
         break;
+    case ADGI_STATE_QD: *bytes = 4 * 8 * P; break;
+    case ADGI_STATE_DYN_CHAINS:
+    case ADGI_STATE_DYN_SAMPLES:
+    case ADGI_STATE_DYN_CELLS:
+    case ADGI_STATE_DYN_FIRST:
+    case ADGI_STATE_DYN_INCL:
+    case ADGI_STATE_DYN_OFF:
+    case ADGI_STATE_DYN_HIT:
+    case ADGI_STATE_DYN_REC: {
+        if (!v->V.dyn) return fail(ADGI_ERR_INVALID_ARG, "no dynamic chains in this volume");
+        const uint64_t cells = 8 * (uint64_t)v->dyn_pp;
+        *bytes = which == ADGI_STATE_DYN_CHAINS    ? 32 * (uint64_t)v->dyn_Cd
+                 : which == ADGI_STATE_DYN_SAMPLES ? 16 * (uint64_t)v->dyn_Bd
+                 : which == ADGI_STATE_DYN_CELLS   ? 4 * (uint64_t)v->dyn_Bd
+                 : which == ADGI_STATE_DYN_FIRST   ? 4 * cells
+                 : which == ADGI_STATE_DYN_INCL    ? cells
+                 : which == ADGI_STATE_DYN_OFF     ? 4 * (P + 1)
+                 : which == ADGI_STATE_DYN_HIT     ? 8 * (uint64_t)v->dyn_Rd
+                                                   : 16 * (uint64_t)v->dyn_Rd;
+        break;
+    }
     default: return fail(ADGI_ERR_INVALID_ARG, "unknown state");
     }
     return ADGI_OK;
@@ -1386,6 +1536,15 @@ int adgi_read_state(adgi_volume v, int32_t which, void* dst, uint64_t bytes)
     case ADGI_STATE_MH_ORDER: src = v->mh_ord; break;
     case ADGI_STATE_MH_OFF: src = v->mh_off; break;
     case ADGI_STATE_MH_HIT_NEG: src = v->mh_hitn; break;
+    case ADGI_STATE_QD: src = v->qd; break;
+    case ADGI_STATE_DYN_CHAINS: src = v->dyn_chain; break;
+    case ADGI_STATE_DYN_SAMPLES: src = v->dyn_smp; break;
+    case ADGI_STATE_DYN_CELLS: src = v->dyn_cell; break;
+    case ADGI_STATE_DYN_FIRST: src = v->dyn_first; break;
+    case ADGI_STATE_DYN_INCL: src = v->dyn_incl; break;
+    case ADGI_STATE_DYN_OFF: src = v->dyn_off; break;
+    case ADGI_STATE_DYN_HIT: src = v->dyn_hit; break;
+    case ADGI_STATE_DYN_REC: src = v->dyn_rec; break;
     }
     bool nodes = which == ADGI_STATE_BVH_NODES || which == ADGI_STATE_MOVING_BVH_NODES;
     if (count_tris >= 0 && (count_tris == 0 || (nodes && count_tris < 2))) {

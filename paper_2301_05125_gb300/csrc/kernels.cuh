@@ -47,6 +47,7 @@ struct ChangeBufs {
     uint16_t* trr;
     uint32_t* G;  // per (probe, octant): octant-neighbourhood sum of trv + 2 trr
     uint32_t* W;
+    uint32_t* qd; // per (probe, octant): the dynamic weight q_d summed into W (null: not kept)
 };
 
 // work buffers of the shading wavefront (shade.cu)
@@ -113,7 +114,43 @@ struct MhBufs {
     const uint16_t* lut_c;
     const uint16_t* qv;       // this frame's q_v per (probe, octant)
     const void* irr;          // previous irradiance atlas (the cache term of the guide)
+    const uint32_t* qd;       // dynamic chains on: q_d per (probe, octant), else null
+    float4* smp_gn;           // dynamic chains on: [B] the -w ray direction in grouped order, else null
 };
+
+// Dynamic chains over virtual proxies of 3x3x3 probes (sampler.cu).
+struct DynBufs {
+    uint32_t n_chains;        // ceil(C_s / dyn_ratio)
+    uint32_t n_samples;       // 5 per chain
+    uint32_t budget;          // dynamic rays per frame at most
+    int dp[3];                // proxy grid: ceil(dims / 3)
+    int pp;                   // proxies
+    const float* nq;          // normal quantile table (shared with the static chains)
+    const uint32_t* qd;       // [P][8] this frame's q_d
+    float4* chain;            // [2Cd] states: {g.xyz, u.x}, then {u.y, ...}
+    float4* smp;              // [Bd] sample direction, proxy (int bits) in .w
+    int* cell;                // [Bd] proxy*8 + octant, -1 where the target is 0
+    uint32_t* val;            // [Pp*8] coarsened target: max q_d over the proxy
+    uint32_t* first;          // [Pp*8] first sample marking each cell (UINT32_MAX: none)
+    uint64_t* keys[2];        // sort of the cells by first sample
+    uint32_t* vals[2];
+    uint32_t* hist;
+    uint8_t* incl;            // [Pp*8] traced this frame
+    uint32_t* off;            // [P+1] dynamic rays of each probe (counts, then offsets)
+    uint32_t* part;           // [1024] partial sums of the offsets scan
+    uint32_t* info;           // [2] marked cells, traced cells
+    int* ntex;                // [8]
+    int* tex_t;               // [8][n_irr^2]
+    float4* tex_dir;          // [8][n_irr^2]
+};
+DynRays dyn_rays_of(const DynBufs& D);
+// the per-octant texel-centre table (once per volume)
+cudaError_t launch_dyn_tables(const VolConst& V, const DynBufs& D, cudaStream_t s);
+cudaError_t launch_dyn_init(const VolConst& V, const DynBufs& D, uint64_t init_key, cudaStream_t s);
+// target table, chain steps and marks, the budget and the per-probe ray offsets
+cudaError_t launch_dyn_plan(const VolConst& V, const FrameDev* FD, const DynBufs& D, cudaStream_t s);
+cudaError_t launch_dyn_trace(const VolConst& V, const SceneDev& S, const DynRays& R, uint32_t budget, int2* hit,
+                             const Tuning& T, cudaStream_t s);
 
 cudaError_t launch_mh_init(const VolConst& V, const MhBufs& M, uint64_t init_key, cudaStream_t s);
 cudaError_t launch_mh_chain(const VolConst& V, const FrameDev* FD, const MhBufs& M, cudaStream_t s);
@@ -127,7 +164,7 @@ cudaError_t launch_mh_trace(const VolConst& V, const SceneDev& S, const MhBufs& 
 struct MhBlendBufs {
     uint32_t n;               // samples
     const uint32_t* off;      // [P+1] grouped sample ranges
-    const float4* smp_g;      // [B] samples, grouped order
+    const float4* smp_g;      // [B] samples, grouped order (the +w ray direction)
     const float4* rec;        // [B] +w records, grouped order
     const int2* hit_neg;      // [B] -w hits, grouped order
     const float4* pil_rec;
@@ -135,6 +172,9 @@ struct MhBlendBufs {
     void* dep;
     uint8_t* dep_n;
     const uint16_t* src;      // border fold table (as BlendBufs::src)
+    const float4* smp_gn;     // [B] the -w ray direction (dynamic chains on), else null: -smp_g
+    DynRays dyn;              // dynamic rays (dynamic chains on)
+    const float4* drec;       // [budget] dynamic ray records
 };
 cudaError_t launch_mh_blend(const VolConst& V, const FrameDev* FD, const MhBlendBufs& B, cudaStream_t s);
 
@@ -144,10 +184,12 @@ cudaError_t launch_pilot_trace(const VolConst& V, const FrameDev* FD, const Scen
                                cudaStream_t s);
 cudaError_t launch_main_trace(const VolConst& V, const FrameDev* FD, const SceneDev& S, const uint32_t* off,
                               const float4* sf, uint32_t R, int2* hit, const Tuning& T, cudaStream_t s);
+// mode 0 pilot rays, 1 adaptive rays (off, sf), 2 Metropolis samples (sf = the
+// grouped samples), 3 dynamic rays (dyn; n_rays = the budget)
 cudaError_t launch_shade(const VolConst& V, const FrameDev* FD, const SceneDev& S, int mode, uint32_t n_rays,
                          const uint32_t* off, const float4* sf, const void* irr, const void* dep, const int2* hit,
                          float4* rec, float* lum, const ShadeWork& W, const Tuning& T, cudaStream_t s,
-                         cudaEvent_t* ev_shadow = nullptr);
+                         cudaEvent_t* ev_shadow = nullptr, const DynRays* dyn = nullptr);
 unsigned shadow_grid_blocks(int mult);
 // smp_g: the Metropolis samples in grouped order (then R = 2B), else null
 cudaError_t launch_count(const VolConst& V, const FrameDev* FD, const SceneDev& S, const uint32_t* off,

@@ -38,10 +38,11 @@ __device__ __forceinline__ int probe_of_ray(const uint32_t* __restrict__ off, ui
 // once by two threads) or Metropolis samples (ray r = sample sf[r] of the
 // grouped order).
 struct RaySet {
-    int mode;                 // 0 pilot, 1 adaptive, 2 Metropolis samples in grouped order
-    uint32_t n;               // rays in the set
+    int mode;                 // 0 pilot, 1 adaptive, 2 Metropolis samples in grouped order, 3 dynamic rays
+    uint32_t n;               // rays in the set (dynamic rays: the budget)
     const uint32_t* off;      // adaptive: prefix offsets
     const float4* sf;         // adaptive: spherical Fibonacci sets; samples: {w.xyz, probe bits}
+    DynRays dyn;              // dynamic rays
 };
 
 __device__ __forceinline__ void block_range(const VolConst& V, const RaySet& Rs, int* s_lo, int* s_hi)
@@ -67,6 +68,13 @@ __device__ __forceinline__ bool ray_of(const VolConst& V, const FrameConst& F, c
         slot = r;
         o = probe_pos(V, p);
         d = pilot_dir(F.pilot_key, (uint32_t)p, (int)(r & 7));
+        return true;
+    }
+    if (Rs.mode == 3) {
+        int p, t;
+        if (!dyn_ray_of(V, Rs.dyn, r, p, t, d)) return false;
+        slot = r;
+        o = probe_pos(V, p);
         return true;
     }
     if (Rs.mode == 2) {
@@ -277,10 +285,10 @@ unsigned shadow_grid_blocks(int mult)
 cudaError_t launch_shade(const VolConst& V, const FrameDev* FD, const SceneDev& S, int mode, uint32_t n_rays,
                          const uint32_t* off, const float4* sf, const void* irr, const void* dep, const int2* hit,
                          float4* rec, float* lum, const ShadeWork& W, const Tuning& T, cudaStream_t s,
-                         cudaEvent_t* ev_shadow)
+                         cudaEvent_t* ev_shadow, const DynRays* dyn)
 {
     if (n_rays == 0) return cudaSuccess;
-    RaySet Rs{mode, n_rays, off, sf};
+    RaySet Rs{mode, n_rays, off, sf, dyn ? *dyn : DynRays{}};
     const unsigned b = (unsigned)T.shade_block;
     const unsigned nb = (n_rays + b - 1) / b;
     cudaError_t e = cudaMemsetAsync(W.job_count, 0, sizeof(unsigned), s);

@@ -101,7 +101,8 @@ __global__ void __launch_bounds__(256) k_main_trace(VolConst V, const FrameDev* 
 // Metropolis samples, in grouped order: thread r < n traces sample r along +w
 // into hit_pos[r], thread n + r along -w into hit_neg[r] (the visibility ray
 // of the texel at -w).
-__global__ void __launch_bounds__(256) k_mh_trace(VolConst V, SceneDev S, const float4* __restrict__ smp_g, uint32_t n,
+__global__ void __launch_bounds__(256) k_mh_trace(VolConst V, SceneDev S, const float4* __restrict__ smp_g,
+                                                  const float4* __restrict__ smp_gn, uint32_t n,
                                                   int2* __restrict__ hit_pos, int2* __restrict__ hit_neg)
 {
     const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
@@ -116,11 +117,30 @@ __global__ void __launch_bounds__(256) k_mh_trace(VolConst V, SceneDev S, const 
         dst[q] = make_int2((int)kMiss, 0x7F800000);
         return;
     }
-    const float3 d = neg ? make_float3(-a.x, -a.y, -a.z) : make_float3(a.x, a.y, a.z);
+    float3 d = make_float3(a.x, a.y, a.z);
+    if (neg) {  // the -w ray: its own direction when snapped to a texel centre
+        const float4 b = smp_gn ? __ldg(smp_gn + q) : make_float4(-a.x, -a.y, -a.z, 0.f);
+        d = make_float3(b.x, b.y, b.z);
+    }
     float t;
     uint32_t h;
     trace_closest(S, probe_pos(V, p), d, V.tmin, __int_as_float(0x7F800000), t, h);
     dst[q] = make_int2((int)h, __float_as_int(t));
+}
+
+// Dynamic rays (grouped by probe; r beyond this frame's rays does nothing)
+__global__ void __launch_bounds__(256) k_dyn_trace(VolConst V, SceneDev S, DynRays R, uint32_t budget,
+                                                   int2* __restrict__ hit)
+{
+    const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= budget) return;
+    int p, t;
+    float3 d;
+    if (!dyn_ray_of(V, R, r, p, t, d)) return;
+    float th;
+    uint32_t h;
+    trace_closest(S, probe_pos(V, p), d, V.tmin, __int_as_float(0x7F800000), th, h);
+    hit[r] = make_int2((int)h, __float_as_int(th));
 }
 
 // Re-trace the last update's rays with work counters (roofline accounting).
@@ -274,7 +294,17 @@ cudaError_t launch_mh_trace(const VolConst& V, const SceneDev& S, const MhBufs& 
     const uint32_t n = M.n_samples;
     if (n == 0) return cudaSuccess;
     const unsigned b = (unsigned)T.trace_block;
-    k_mh_trace<<<(2 * n + b - 1) / b, b, 0, s>>>(V, S, M.smp_g, n, hit_pos, hit_neg);
+    k_mh_trace<<<(2 * n + b - 1) / b, b, 0, s>>>(V, S, M.smp_g, M.smp_gn, n, hit_pos, hit_neg);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dyn_trace(const VolConst& V, const SceneDev& S, const DynRays& R, uint32_t budget, int2* hit,
+                             const Tuning& T, cudaStream_t s)
+{
+    if (budget == 0) return cudaSuccess;
+    const unsigned b = (unsigned)T.trace_block;
+    k_dyn_trace<<<(budget + b - 1) / b, b, 0, s>>>(V, S, R, budget, hit);
     count_launches(1);
     return cudaGetLastError();
 }

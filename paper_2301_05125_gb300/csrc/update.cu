@@ -110,7 +110,11 @@ __global__ void __launch_bounds__(128) k_change_weight(VolConst V, const FrameDe
     const uint32_t qc = qc_of_probe(V, F, B.lut_c, p);
     uint64_t Wp = 0;
 #pragma unroll
-    for (int o = 0; o < 8; ++o) Wp += ((uint64_t)qc * (uint64_t)B.qv[(size_t)p * 8 + o] * (uint64_t)f[o]) >> 20;
+    for (int o = 0; o < 8; ++o) {
+        const uint64_t qd = ((uint64_t)qc * (uint64_t)B.qv[(size_t)p * 8 + o] * (uint64_t)f[o]) >> 20;
+        if (B.qd) B.qd[(size_t)p * 8 + o] = (uint32_t)(qd < 0xFFFFFFFFull ? qd : 0xFFFFFFFFull);
+        Wp += qd;
+    }
     B.W[p] = (uint32_t)(Wp < 0xFFFFFFull ? Wp : 0xFFFFFFull);
 }
 
@@ -761,10 +765,10 @@ __global__ void __launch_bounds__(128) k_blend(VolConst V, const FrameDev* __res
 // texel summed first, in order); then the batched moving average and the
 // stores of k_blend.
 struct MhLayout {
-    uint32_t acc_i, acc_d, cnt_d, dn, e_rec, total;
+    uint32_t acc_i, acc_d, cnt_d, dn, e_rec, dacc_i, dacc_d, dcnt_d, total;
 };
 
-__host__ __device__ inline MhLayout mh_layout(int Ti, int Td)
+__host__ __device__ inline MhLayout mh_layout(int Ti, int Td, bool dyn)
 {
     const uint32_t ti2 = (uint32_t)(Ti * Ti), td2 = (uint32_t)(Td * Td);
     MhLayout L;
@@ -774,6 +778,12 @@ __host__ __device__ inline MhLayout mh_layout(int Ti, int Td)
     L.cnt_d = o, o += al16(4 * td2);
     L.dn = o, o += al16(td2);
     L.e_rec = o, o += 16 * 32;  // one chunk of samples: {r, g, b, depth}
+    L.dacc_i = L.dacc_d = L.dcnt_d = o;
+    if (dyn) {  // the dynamic rays' sums: a second batch step
+        L.dacc_i = o, o += al16(16 * ti2);
+        L.dacc_d = o, o += al16(8 * td2);
+        L.dcnt_d = o, o += al16(4 * td2);
+    }
     L.total = o;
     return L;
 }
@@ -832,10 +842,11 @@ __global__ void __launch_bounds__(128) k_mh_blend(VolConst V, const FrameDev* __
         b1 = b0;
     }
     const int npil = F.even ? kPilots : 0;
-    if (b1 == b0 && npil == 0) return;  // untouched tile
+    const uint32_t r0 = V.dyn ? __ldg(B.dyn.off + p) : 0u, r1 = V.dyn ? __ldg(B.dyn.off + p + 1) : 0u;
+    if (b1 == b0 && npil == 0 && r1 <= r0) return;  // untouched tile
     const int Ti = V.Ti, Td = V.Td, ni = V.n_irr, nd = V.n_dep;
     const int ti2 = Ti * Ti, td2 = Td * Td;
-    const MhLayout L = mh_layout(Ti, Td);
+    const MhLayout L = mh_layout(Ti, Td, V.dyn != 0);
     unsigned char* ws = smem + (size_t)wib * L.total;
     float4* acc_i = reinterpret_cast<float4*>(ws + L.acc_i);
     float2* acc_d = reinterpret_cast<float2*>(ws + L.acc_d);
@@ -846,6 +857,16 @@ __global__ void __launch_bounds__(128) k_mh_blend(VolConst V, const FrameDev* __
     for (int t = lane; t < td2; t += 32) {
         acc_d[t] = make_float2(0.f, 0.f);
         cnt_d[t] = 0u;
+    }
+    float4* dacc_i = reinterpret_cast<float4*>(ws + L.dacc_i);
+    float2* dacc_d = reinterpret_cast<float2*>(ws + L.dacc_d);
+    uint32_t* dcnt_d = reinterpret_cast<uint32_t*>(ws + L.dcnt_d);
+    if (V.dyn) {
+        for (int t = lane; t < ti2; t += 32) dacc_i[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int t = lane; t < td2; t += 32) {
+            dacc_d[t] = make_float2(0.f, 0.f);
+            dcnt_d[t] = 0u;
+        }
     }
     __syncwarp();
     if (npil) {
@@ -875,7 +896,8 @@ __global__ void __launch_bounds__(128) k_mh_blend(VolConst V, const FrameDev* __
             const float dep = (uint32_t)hn.x == kMiss ? V.depth_max : fminf(__int_as_float(hn.y), V.depth_max);
             e_rec[lane] = make_float4(x.x, x.y, x.z, dep);
             ki = texel_of(oct_encode_x(make_float3(a.x, a.y, a.z)), ni);
-            kd = texel_of(oct_encode_x(make_float3(-a.x, -a.y, -a.z)), nd);
+            const float4 an = B.smp_gn ? __ldg(B.smp_gn + c0 + lane) : make_float4(-a.x, -a.y, -a.z, 0.f);
+            kd = texel_of(oct_encode_x(make_float3(an.x, an.y, an.z)), nd);
         }
         __syncwarp();
         const uint32_t qn = c0 + 32 + lane;
@@ -887,6 +909,25 @@ __global__ void __launch_bounds__(128) k_mh_blend(VolConst V, const FrameDev* __
         mh_accumulate(e_rec, ki, kd, acc_i, acc_d, cnt_d, lane);
         __syncwarp();
     }
+    // the dynamic rays of the probe (each at its own texel centre): sums of
+    // the second batch step
+    for (uint32_t c0 = r0; c0 < r1; c0 += 32) {
+        int ki = -1, kd = -1;
+        if (c0 + lane < r1) {
+            int pp, t;
+            float3 d;
+            if (dyn_ray_of(V, B.dyn, c0 + lane, pp, t, d) && pp == p) {
+                e_rec[lane] = __ldg(B.drec + c0 + lane);
+                ki = t;
+                kd = texel_of(oct_encode_x(d), nd);
+            } else {
+                atomicOr(V.err, kErrRayRange);
+            }
+        }
+        __syncwarp();
+        mh_accumulate(e_rec, ki, kd, dacc_i, dacc_d, dcnt_d, lane);
+        __syncwarp();
+    }
     const float omh = 1.0f - V.hyst;
     const float rni = 1.0f / (float)ni, rnd = 1.0f / (float)nd;
     const size_t io = (size_t)p * ti2, dof = (size_t)p * td2;
@@ -895,6 +936,10 @@ __global__ void __launch_bounds__(128) k_mh_blend(VolConst V, const FrameDev* __
         const float4 sum = acc_i[t];
         float4 v = irr_load(V, B.irr, io + t);
         if (sum.w > 0.0f) v = irr_texel_blend(v, sum.x, sum.y, sum.z, (uint32_t)sum.w, omh);
+        if (V.dyn) {
+            const float4 ds = dacc_i[t];
+            if (ds.w > 0.0f) v = irr_texel_blend(v, ds.x, ds.y, ds.z, (uint32_t)ds.w, 1.0f - V.hyst_dyn);
+        }
         acc_i[t] = v;
     }
     for (int q = lane; q < nd * nd; q += 32) {
@@ -904,6 +949,11 @@ __global__ void __launch_bounds__(128) k_mh_blend(VolConst V, const FrameDev* __
         float2 v = dep_load(V, B.dep, dof + t);
         uint32_t c = B.dep_n[dof + t];
         if (k) v = dep_texel_blend(v, c, sum.x, sum.y, k, omh);
+        if (V.dyn) {
+            const uint32_t kd2 = dcnt_d[t];
+            const float2 ds = dacc_d[t];
+            if (kd2) v = dep_texel_blend(v, c, ds.x, ds.y, kd2, 1.0f - V.hyst_dyn);
+        }
         acc_d[t] = v;
         dn[t] = (uint8_t)c;
     }
@@ -998,7 +1048,7 @@ cudaError_t launch_blend(const VolConst& V, const FrameDev* FD, const BlendBufs&
 
 cudaError_t launch_mh_blend(const VolConst& V, const FrameDev* FD, const MhBlendBufs& B, cudaStream_t s)
 {
-    const size_t per = mh_layout(V.Ti, V.Td).total;
+    const size_t per = mh_layout(V.Ti, V.Td, V.dyn != 0).total;
     const int wpb = std::max(1, std::min(4, (int)((227u * 1024u) / per)));
     const size_t sm = per * (size_t)wpb;
     if (sm > 48 * 1024) {

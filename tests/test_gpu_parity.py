@@ -153,6 +153,38 @@ def test_trace_city_bit_exact_vs_oracle(adgi):
     _trace_case(adgi, w, O_, D, use_bvh=True)
 
 
+def test_trace_axis_aligned_directions(adgi):
+    # directions with exact zero components (axis-aligned rays, rays in a
+    # coordinate plane, signed zeros): 1/0 in the box test must not reject boxes
+    rng = np.random.default_rng(14)
+    w = S.small_city(3, n_boxes=2000)
+    n = 60000
+    O_ = rng.uniform(-40, 40, (n, 3)).astype(np.float32)
+    O_[:, 1] = rng.uniform(0.5, 30, n)
+    D = rng.normal(size=(n, 3)).astype(np.float32)
+    ax = rng.integers(0, 3, n)
+    D[np.arange(n) % 3 == 0, :] = 0.0  # axis-aligned: keep one component
+    keep = np.arange(n) % 3 == 0
+    D[keep, ax[keep]] = np.where(rng.random(keep.sum()) < 0.5, -1.0, 1.0)
+    one = np.arange(n) % 3 == 1  # one component zero (+0 or -0)
+    D[one, ax[one]] = np.where(rng.random(one.sum()) < 0.5, 0.0, -0.0)
+    _trace_case(adgi, w, O_, D, use_bvh=True)
+
+
+def test_update_axis_aligned_sun(adgi):
+    # a sun straight down: every shadow ray points straight up (two zero
+    # direction components)
+    w = S.small_city(4, n_boxes=800, dims=(9, 5, 7), rays_avg=40)
+    sun = [(1, (0.0, -1.0, 0.0), (2.0, 2.0, 2.0))]
+    gv = gpu_volume(adgi, w)
+    ov = oracle_volume(O, w)
+    for f in range(2):
+        gv.update(f, w.seed, sun, w.sky)
+        ov.update(f, w.seed, sun, w.sky)
+        _compare_update(gv, ov, f, what="axis-aligned sun")
+    gv.close()
+
+
 def test_trace_degenerate_scenes(adgi):
     rng = np.random.default_rng(13)
     O_ = rng.uniform(-1, 1, (5000, 3)).astype(np.float32)
