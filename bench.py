@@ -58,6 +58,7 @@ def _peaks():
 KERNEL_SOURCES = {
     "k_main_trace": ["trace.cu"], "k_pilot_trace": ["trace.cu"], "k_shadow": ["shade.cu"],
     "k_shade_finish": ["shade.cu"], "k_blend": ["update.cu"], "k_blend_plan": ["update.cu"],
+    "k_mh_trace": ["trace.cu"], "k_mh_blend": ["update.cu"],
 }
 
 
@@ -506,10 +507,19 @@ def _metropolis_section(args, adgi, torch, dev):
     """Metropolis form (sampler = 1, alpha = 1) on the same workload: chains
     draw the (rays_avg - 8) * P adaptive samples over (probe, direction),
     each tracing +w (radiance) and -w (visibility); timed per update with
-    the L2 flushed between updates, like the headline line."""
+    the L2 flushed between updates, like the headline line.  Then the same
+    with the dynamic chains over virtual proxies (budget split 4:1,
+    hysteresis 0.91 for the dynamic rays)."""
+    out = _metropolis_run(args, adgi, torch, dev, 0)
+    out["dynamic_chains"] = _metropolis_run(args, adgi, torch, dev, 4)
+    return out
+
+
+def _metropolis_run(args, adgi, torch, dev, dyn_ratio):
     w = _workload(args.workload, args.seed)
     vd = dict(w.volume)
     vd["sampler"], vd["alpha"] = 1, 1.0
+    vd["dyn_ratio"], vd["hysteresis_dyn"] = dyn_ratio, 0.91
     stream = torch.cuda.Stream(device=dev)
     v = adgi.Volume(stream=stream.cuda_stream, **vd)
     v.set_scene(w.verts, w.idx, w.albedo)
@@ -533,7 +543,8 @@ def _metropolis_section(args, adgi, torch, dev):
     st = v.stats()
     rays = int(st.rays_per_update)
     m = float(np.mean(ms))
-    out = {"workload": w.name, "probes": w.n_probes, "alpha": 1.0, "samples_per_update": rays // 2 - 4 * w.n_probes,
+    samples = len(v.mh_order())
+    out = {"workload": w.name, "probes": w.n_probes, "alpha": 1.0, "samples_per_update": samples,
            "rays_per_update": rays, "ms_per_update": m, "rays_per_s": rays / (m / 1e3),
            "rays_incl_shadow_per_s": (rays + int(st.shadow_rays)) / (m / 1e3),
            "phases_ms": {k: float(np.mean(x)) for k, x in ph.items()},
@@ -541,6 +552,12 @@ def _metropolis_section(args, adgi, torch, dev):
            "note": "rays = 8 pilots per probe + a +w and a -w ray per sample; the allocation phase also holds "
                    "the chain steps and the grouping of the samples by probe (python bench.py --sampler times "
                    "this form as the main line, with its roofline)"}
+    if dyn_ratio:
+        out["dyn_ratio"] = dyn_ratio
+        out["dynamic_rays_last_update"] = rays - 8 * w.n_probes - 2 * samples
+        out["traced_cells_last_update"] = int(v.dyn_incl().sum())
+        out["note"] = ("static samples (budget split 4:1) + dynamic rays of the traced proxy cells; the allocation "
+                       "phase holds both chain sets, the grouping and the marks")
     v.close()
     return out
 
