@@ -710,14 +710,25 @@ EXPORT void orc_trace_any(const float* V, int nv, const int* I, int nt, int n_ra
 /* ------------------------------------------------------------------------ */
 #define ORC_ALLOC_MAX_ITERS 64
 
-EXPORT int orc_allocate(const uint32_t* W, int P, int avg, int rmin, int rmax, uint32_t* n_out, uint32_t* off_out)
+/* Allocation restricted by the clip volumes (cls: 2 V_in, 1 V_out only, 0
+   outside; NULL: every probe in V_in).  Only V_in probes take adaptive
+   rays: n = m0 + extra in V_in, 8 (the pilots) in V_out - V_in, 0 outside.
+   The adaptive budget stays (avg - 8) P; beyond the V_in floors, E =
+   (avg - 8) P - (m0 - 8) |V_in| is spread over V_in as below, capped at
+   rmax - m0 per probe (what the caps cannot hold stays unspent; the pilots
+   of culled probes are saved, not reassigned).  With every probe in V_in
+   this is exactly the plain rule. */
+EXPORT int orc_allocate_masked(const uint32_t* W, const uint8_t* cls, int P, int avg, int rmin, int rmax,
+                               uint32_t* n_out, uint32_t* off_out)
 {
     if (P <= 0) return -1;
     int m0 = rmin > 8 ? rmin : 8;
     if (avg < m0 || avg > rmax || m0 > rmax) return -1;
-    uint64_t B = (uint64_t)avg * (uint64_t)P;
-    uint64_t E = B - (uint64_t)m0 * (uint64_t)P;
     uint64_t cap = (uint64_t)(rmax - m0);
+    uint64_t Pin = 0;
+    for (int p = 0; p < P; ++p) Pin += !cls || cls[p] == 2;
+    uint64_t E = (uint64_t)(avg - 8) * (uint64_t)P - (uint64_t)(m0 - 8) * Pin;
+    if (E > Pin * cap) E = Pin * cap;
     uint64_t* extra = (uint64_t*)calloc((size_t)P, sizeof(uint64_t));
     uint8_t* inU = (uint8_t*)calloc((size_t)P, 1);
     if (!extra || !inU) {
@@ -725,14 +736,19 @@ EXPORT int orc_allocate(const uint32_t* W, int P, int avg, int rmin, int rmax, u
         free(inU);
         return -1;
     }
+#define IN_VIN(p) (!cls || cls[p] == 2)
     uint64_t S = 0;
-    for (int p = 0; p < P; ++p) S += W[p];
+    for (int p = 0; p < P; ++p)
+        if (IN_VIN(p)) S += W[p];
     if (S == 0) {
-        uint64_t q = E / (uint64_t)P, r = E % (uint64_t)P;
-        for (int p = 0; p < P; ++p) extra[p] = q + ((uint64_t)p < r ? 1u : 0u);
+        if (Pin > 0) { /* uniform over V_in, the remainder to the lowest ranks */
+            uint64_t q = E / Pin, r = E % Pin, rank = 0;
+            for (int p = 0; p < P; ++p)
+                if (IN_VIN(p)) extra[p] = q + (rank++ < r ? 1u : 0u);
+        }
     } else {
         uint64_t Erem = E;
-        for (int p = 0; p < P; ++p) inU[p] = W[p] > 0 && cap > 0;
+        for (int p = 0; p < P; ++p) inU[p] = IN_VIN(p) && W[p] > 0 && cap > 0;
         for (int it = 0; it < ORC_ALLOC_MAX_ITERS; ++it) {
             uint64_t SU = 0;
             for (int p = 0; p < P; ++p)
@@ -756,12 +772,12 @@ EXPORT int orc_allocate(const uint32_t* W, int P, int avg, int rmin, int rmax, u
         while (Erem > 0) {
             int anyA = 0;
             for (int p = 0; p < P; ++p)
-                if (W[p] > 0 && extra[p] < cap) {
+                if (IN_VIN(p) && W[p] > 0 && extra[p] < cap) {
                     anyA = 1;
                     break;
                 }
             for (int p = 0; p < P && Erem > 0; ++p) {
-                int elig = extra[p] < cap && (anyA ? W[p] > 0 : 1);
+                int elig = IN_VIN(p) && extra[p] < cap && (anyA ? W[p] > 0 : 1);
                 if (elig) {
                     extra[p] += 1;
                     Erem -= 1;
@@ -771,14 +787,21 @@ EXPORT int orc_allocate(const uint32_t* W, int P, int avg, int rmin, int rmax, u
     }
     uint32_t acc = 0;
     for (int p = 0; p < P; ++p) {
-        n_out[p] = (uint32_t)((uint64_t)m0 + extra[p]);
+        int c = cls ? cls[p] : 2;
+        n_out[p] = (uint32_t)((c == 2 ? (uint64_t)m0 : (c == 1 ? 8u : 0u)) + extra[p]);
         if (off_out) off_out[p] = acc;
-        acc += n_out[p] - 8u;
+        acc += n_out[p] > 8u ? n_out[p] - 8u : 0u;
     }
     if (off_out) off_out[P] = acc;
+#undef IN_VIN
     free(extra);
     free(inU);
     return 0;
+}
+
+EXPORT int orc_allocate(const uint32_t* W, int P, int avg, int rmin, int rmax, uint32_t* n_out, uint32_t* off_out)
+{
+    return orc_allocate_masked(W, NULL, P, avg, rmin, rmax, n_out, off_out);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -934,6 +957,8 @@ typedef struct {
     int has_camera;
     float cam[3];
     float cam_k;
+    int has_clip;    /* 1: clip volumes from the camera's view-projection matrix (Fig. TrCam(b)) */
+    float clip[16];  /* row-major 4x4: clip = M (x, y, z, 1) */
 } orc_frame;
 
 typedef struct orc_vol {
@@ -999,6 +1024,8 @@ typedef struct orc_vol {
     uint32_t* smp_off;   /* P+1 first sample of each probe in smp_ord */
     uint32_t* smp_ord;   /* B sample indices grouped by probe, in sample order */
     uint32_t* qd;        /* P*8 dynamic weight q_d of each probe and octant (Eq. priorDynamic) */
+    uint8_t* cls;        /* P clip volume of each probe this frame: 2 V_in, 1 V_out - V_in, 0 outside */
+    uint8_t* vout_even;  /* P 1: the probe was in V_out on the last first-of-pair frame */
     /* dynamic chains over virtual proxies (desc.dyn_ratio > 0) */
     int Dp[3], Pp;       /* proxy grid: ceil(dims / 3) */
     size_t Cd, Bd;       /* dynamic chains, dynamic samples per frame (5 per chain) */
@@ -1101,6 +1128,9 @@ EXPORT orc_vol* orc_create(const orc_desc* d, int nthreads)
     v->qv = (uint16_t*)calloc(P * 8, 2);
     v->qr = (uint16_t*)calloc(P * 8, 2);
     v->qd = (uint32_t*)calloc(P * 8, 4);
+    v->cls = (uint8_t*)malloc(P);
+    memset(v->cls, 2, P);
+    v->vout_even = (uint8_t*)calloc(P, 1);
     v->last_even = -2;
     v->W = (uint32_t*)calloc(P, 4);
     v->n = (uint32_t*)calloc(P, 4);
@@ -1176,6 +1206,8 @@ EXPORT void orc_destroy(orc_vol* v)
     free(v->smp_off);
     free(v->smp_ord);
     free(v->qd);
+    free(v->cls);
+    free(v->vout_even);
     free(v->dch_g);
     free(v->dch_u);
     free(v->dsm_q);
@@ -1604,7 +1636,7 @@ static void blend_probe_packed(orc_vol* v, int p, int use_pilots)
     const int Ti = v->Ti, Td = v->Td, ni = v->d.n_irr, nd = v->d.n_dep;
     uint32_t* irr = v->irr_pk + (size_t)p * Ti * Ti;
     uint32_t* dep = v->dep_pk + (size_t)p * Td * Td;
-    const uint32_t mp = v->n[p] - 8u;
+    const uint32_t mp = v->n[p] > 8u ? v->n[p] - 8u : 0u;
     const int total = (int)mp + (use_pilots ? 8 : 0);
     for (int j = 0; j < total; ++j) {
         float d[3];
@@ -1631,6 +1663,12 @@ static void blend_probe_packed(orc_vol* v, int p, int use_pilots)
         float x = (float)ds / v->s_f; /* distance in units of the cage diagonal */
         dep[td] = pk_dep_update(dep[td], x);
     }
+    if (v->cls[p] == 1) { /* V_out - V_in: sample counts set down to 16 (catch-up) */
+        for (int t = 0; t < Ti * Ti; ++t)
+            if ((irr[t] >> 26) > 16u) irr[t] = (irr[t] & 0x03FFFFFFu) | (16u << 26);
+        for (int t = 0; t < Td * Td; ++t)
+            if ((dep[t] >> 26) > 16u) dep[t] = (dep[t] & 0x03FFFFFFu) | (16u << 26);
+    }
     border_copy_u32(irr, ni);
     border_copy_u32(dep, nd);
     decode_probe(v, p);
@@ -1647,7 +1685,7 @@ static void blend_probe(orc_vol* v, int p, int use_pilots, double h)
     int* ki = (int*)calloc((size_t)Ti * Ti, sizeof(int));
     double* sd = (double*)calloc((size_t)Td * Td * 2, sizeof(double));
     int* kd = (int*)calloc((size_t)Td * Td, sizeof(int));
-    const uint32_t mp = v->n[p] - 8u;
+    const uint32_t mp = v->n[p] > 8u ? v->n[p] - 8u : 0u;
     const int total = (int)mp + (use_pilots ? 8 : 0);
     for (int j = 0; j < total; ++j) {
         float d[3];
@@ -1677,6 +1715,12 @@ static void blend_probe(orc_vol* v, int p, int use_pilots, double h)
     }
     batch_apply(irr, irn, si, ki, Ti * Ti, 3, h);
     batch_apply(dep, den, sd, kd, Td * Td, 2, h);
+    if (v->cls[p] == 1) { /* V_out - V_in: sample counts set down to 16 (catch-up) */
+        for (int t = 0; t < Ti * Ti; ++t)
+            if (irn[t] > 16) irn[t] = 16;
+        for (int t = 0; t < Td * Td; ++t)
+            if (den[t] > 16) den[t] = 16;
+    }
     border_copy(irr, irn, ni, 3);
     border_copy(dep, den, nd, 2);
     free(si);
@@ -1731,24 +1775,64 @@ static uint32_t qc_of(const orc_vol* v, const orc_frame* fr, int p)
     return v->lut_c[i];
 }
 
+/* Clip volumes (Fig. TrCam(b), Sec. "Improving construction efficiency"):
+   with the camera's view-projection matrix M, probe p is inside the
+   extended frustum |clip_xy| <= L when w > 0, |c_x| <= L w and |c_y| <= L w
+   ((c_x, c_y, -, w) = M (p, 1), FP32 in row order).  V_in: L = 1.2 and f_c
+   >= 0.75; V_out: L = 1.4 and f_c >= 0.5, with f_c = q_c / 1023 (q_c >= 768,
+   resp. >= 512).  Without a matrix every probe is in V_in. */
+static int in_frustum(const float m[16], const float x[3], float L)
+{
+    float w = ((m[12] * x[0] + m[13] * x[1]) + m[14] * x[2]) + m[15];
+    float cx = ((m[0] * x[0] + m[1] * x[1]) + m[2] * x[2]) + m[3];
+    float cy = ((m[4] * x[0] + m[5] * x[1]) + m[6] * x[2]) + m[7];
+    if (!(w > 0.0f)) return 0;
+    float lw = L * w;
+    return fabsf(cx) <= lw && fabsf(cy) <= lw;
+}
+
+static void classify(orc_vol* v, const orc_frame* fr)
+{
+    for (int p = 0; p < v->P; ++p) {
+        if (!fr->has_clip) {
+            v->cls[p] = 2;
+            continue;
+        }
+        float x[3];
+        probe_pos(v, p, x);
+        uint32_t qc = qc_of(v, fr, p);
+        if (qc >= 768u && in_frustum(fr->clip, x, 1.2f))
+            v->cls[p] = 2;
+        else if (qc >= 512u && in_frustum(fr->clip, x, 1.4f))
+            v->cls[p] = 1;
+        else
+            v->cls[p] = 0;
+    }
+}
+
 static void change_detect(orc_vol* v, const orc_frame* fr)
 {
     const int P = v->P;
     for (int p = 0; p < P; ++p)
         for (int o = 0; o < 8; ++o) {
             size_t opp = (size_t)p * 8 + (size_t)(7 - o);
-            v->qv[(size_t)p * 8 + o] = v->lut_v[qt_of(v, v->pil_t[opp], v->pil_tri[opp] >= 0)];
-            v->qr[(size_t)p * 8 + o] = (uint16_t)qr_of(v->pil_lum[(size_t)p * 8 + o]);
+            v->qv[(size_t)p * 8 + o] = v->cls[p] ? v->lut_v[qt_of(v, v->pil_t[opp], v->pil_tri[opp] >= 0)] : 0;
+            v->qr[(size_t)p * 8 + o] = v->cls[p] ? (uint16_t)qr_of(v->pil_lum[(size_t)p * 8 + o]) : 0;
         }
     const int theta = v->d.theta;
     const int even = (fr->frame & 1u) == 0;
     const int valid = !even && v->last_even == (int64_t)fr->frame - 1;
     for (size_t i = 0; i < (size_t)P * 8; ++i) {
+        const size_t pi = i / 8;
+        if (v->cls[pi] == 0) { /* outside V_out: no heuristics; the state waits */
+            v->trv[i] = v->trr[i] = 0;
+            continue;
+        }
         uint16_t* amp[2] = {&v->amp_v[i], &v->amp_r[i]};
         uint8_t* age[2] = {&v->age_v[i], &v->age_r[i]};
         uint16_t* out[2] = {&v->trv[i], &v->trr[i]};
         int delta[2] = {0, 0};
-        if (!even && valid) {
+        if (!even && valid && v->vout_even[pi]) { /* both frames of the pair inside V_out */
             delta[0] = abs((int)v->qv[i] - (int)v->qv_even[i]);
             delta[1] = abs((int)v->qr[i] - (int)v->qr_even[i]);
         }
@@ -1769,6 +1853,8 @@ static void change_detect(orc_vol* v, const orc_frame* fr)
             v->qr_even[i] = v->qr[i];
         }
     }
+    if (even)
+        for (int p = 0; p < P; ++p) v->vout_even[p] = v->cls[p] >= 1;
     if (even) v->last_even = (int64_t)fr->frame;
     const int X = v->d.dims[0], Y = v->d.dims[1], Z = v->d.dims[2];
     for (int p = 0; p < P; ++p) {
@@ -1790,6 +1876,7 @@ static void change_detect(orc_vol* v, const orc_frame* fr)
                         }
                     }
             uint64_t qd = ((uint64_t)qc * (uint64_t)v->qv[(size_t)p * 8 + o] * (fdv + 2u * fdr)) >> 20;
+            if (v->cls[p] != 2) qd = 0; /* only V_in probes take adaptive samples */
             v->qd[(size_t)p * 8 + o] = (uint32_t)(qd < 0xFFFFFFFFu ? qd : 0xFFFFFFFFu);
             Wp += qd;
         }
@@ -1911,6 +1998,7 @@ static void mh_dir(const float u[2], float w[3])
 static float mh_guide(const orc_vol* v, const orc_frame* fr, const float g[3], const float u[2])
 {
     int p = mh_probe(v, g);
+    if (v->cls[p] != 2) return 0.0f; /* adaptive samples only inside V_in */
     float w[3];
     mh_dir(u, w);
     int o = (w[0] < 0.0f ? 1 : 0) | (w[1] < 0.0f ? 2 : 0) | (w[2] < 0.0f ? 4 : 0);
@@ -2086,6 +2174,13 @@ static void snap_to_texel(const float d[3], int n, float w[3])
    paragraph), so that it adds no sampling noise there. */
 static void mh_sample_rays(orc_vol* v, const orc_frame* fr, size_t sidx)
 {
+    if (v->cls[v->smp_p[sidx]] != 2) { /* outside V_in: the sample is dropped (no rays, not blended) */
+        v->smp_t[sidx] = v->smp_tn[sidx] = INFINITY;
+        v->smp_tri[sidx] = v->smp_trin[sidx] = -1;
+        v->smp_rad[sidx * 3] = v->smp_rad[sidx * 3 + 1] = v->smp_rad[sidx * 3 + 2] = 0.0;
+        v->smp_dep[sidx] = v->depth_max;
+        return;
+    }
     float o[3];
     probe_pos(v, v->smp_p[sidx], o);
     const float* d0 = v->smp_dir + sidx * 3;
@@ -2218,14 +2313,17 @@ static void dyn_chain(orc_vol* v, const orc_frame* fr, size_t c)
             v->dsm_q, v->dsm_dir, c * MH_S, v->Bd);
 }
 
-/* probes of proxy q (index order) */
+/* probes of proxy q inside V_in (index order) */
 static int dyn_probes(const orc_vol* v, int q, int* out)
 {
     const int X = v->d.dims[0], Y = v->d.dims[1], Z = v->d.dims[2];
     int qx = q % v->Dp[0], qy = (q / v->Dp[0]) % v->Dp[1], qz = q / (v->Dp[0] * v->Dp[1]), n = 0;
     for (int z = 3 * qz; z < 3 * qz + 3 && z < Z; ++z)
         for (int y = 3 * qy; y < 3 * qy + 3 && y < Y; ++y)
-            for (int x = 3 * qx; x < 3 * qx + 3 && x < X; ++x) out[n++] = x + X * (y + Y * z);
+            for (int x = 3 * qx; x < 3 * qx + 3 && x < X; ++x) {
+                int p = x + X * (y + Y * z);
+                if (v->cls[p] == 2) out[n++] = p;
+            }
     return n;
 }
 
@@ -2263,6 +2361,7 @@ static void dyn_marks(orc_vol* v)
     size_t r = 0;
     for (int p = 0; p < v->P; ++p) {
         v->doff[p] = (uint32_t)r;
+        if (v->cls[p] != 2) continue; /* dynamic rays only from V_in probes */
         int ix = p % X, iy = (p / X) % Y, iz = p / (X * Y);
         int q = (ix / 3) + v->Dp[0] * ((iy / 3) + v->Dp[1] * (iz / 3));
         for (int o = 0; o < 8; ++o) {
@@ -2326,7 +2425,7 @@ static void mh_blend_probe(orc_vol* v, int p, int use_pilots, double h)
             sd[td * 2 + 1] += ds * ds;
             kd[td] += 1;
         }
-    for (uint32_t q = v->smp_off[p]; q < v->smp_off[p + 1]; ++q) {
+    for (uint32_t q = v->smp_off[p]; q < v->smp_off[p + 1] && v->cls[p] == 2; ++q) {
         size_t sidx = v->smp_ord[q];
         const float* d = v->smp_dir + sidx * 3;
         float dn[3] = {-d[0], -d[1], -d[2]};
@@ -2358,6 +2457,12 @@ static void mh_blend_probe(orc_vol* v, int p, int use_pilots, double h)
         batch_apply(irr, irn, si, ki, Ti * Ti, 3, (double)v->d.hyst_dyn);
         batch_apply(dep, den, sd, kd, Td * Td, 2, (double)v->d.hyst_dyn);
     }
+    if (v->cls[p] == 1) { /* V_out - V_in: sample counts set down to 16 (catch-up) */
+        for (int t = 0; t < Ti * Ti; ++t)
+            if (irn[t] > 16) irn[t] = 16;
+        for (int t = 0; t < Td * Td; ++t)
+            if (den[t] > 16) den[t] = 16;
+    }
     border_copy(irr, irn, ni, 3);
     border_copy(dep, den, nd, 2);
     free(si);
@@ -2368,6 +2473,18 @@ static void mh_blend_probe(orc_vol* v, int p, int use_pilots, double h)
 
 static void pilot_probe(orc_vol* v, const orc_frame* fr, int p)
 {
+    if (v->cls[p] == 0) { /* outside V_out: no pilot rays (records: a miss with nothing gathered) */
+        for (int k = 0; k < 8; ++k) {
+            size_t i = (size_t)p * 8 + (size_t)k;
+            orc_pilot_dir(fr->seed, fr->frame, (uint32_t)p, k, v->pil_dir + i * 3);
+            v->pil_t[i] = INFINITY;
+            v->pil_tri[i] = -1;
+            v->pil_lum[i] = 0.0f;
+            v->pil_rad[i * 3] = v->pil_rad[i * 3 + 1] = v->pil_rad[i * 3 + 2] = 0.0;
+            v->pil_dep[i] = v->depth_max;
+        }
+        return;
+    }
     float o[3];
     probe_pos(v, p, o);
     for (int k = 0; k < 8; ++k) {
@@ -2385,7 +2502,7 @@ static void main_probe(orc_vol* v, const orc_frame* fr, int p)
 {
     float o[3];
     probe_pos(v, p, o);
-    int mp = (int)v->n[p] - 8;
+    int mp = v->n[p] > 8u ? (int)v->n[p] - 8 : 0;
     for (int i = 0; i < mp; ++i) {
         float d[3];
         main_dir(v, mp, i, d);
@@ -2406,20 +2523,20 @@ static void* worker(void* arg)
         else if (j->phase == 4)
             mh_sample_rays(j->v, j->fr, (size_t)p);
         else if (j->phase == 5)
-            mh_blend_probe(j->v, p, (j->fr->frame & 1u) == 0, (double)j->v->d.hyst);
+            mh_blend_probe(j->v, p, (j->fr->frame & 1u) == 0 && j->v->cls[p] >= 1, (double)j->v->d.hyst);
         else if (j->phase == 6)
             dyn_chain(j->v, j->fr, (size_t)p);
         else if (j->phase == 7)
             dyn_ray(j->v, j->fr, (size_t)p);
         else if (j->phase == 0)
-            pilot_probe(j->v, j->fr, p);
+            pilot_probe(j->v, j->fr, p);  /* outside V_out: no pilot rays (see pilot_probe) */
         else if (j->phase == 1)
             main_probe(j->v, j->fr, p);
         else
             if (j->v->d.packed)
-                blend_probe_packed(j->v, p, (j->fr->frame & 1u) == 0);
+                blend_probe_packed(j->v, p, (j->fr->frame & 1u) == 0 && j->v->cls[p] >= 1);
             else
-                blend_probe(j->v, p, (j->fr->frame & 1u) == 0, (double)j->v->d.hyst);
+                blend_probe(j->v, p, (j->fr->frame & 1u) == 0 && j->v->cls[p] >= 1, (double)j->v->d.hyst);
     }
     return NULL;
 }
@@ -2461,9 +2578,10 @@ EXPORT int orc_update(orc_vol* v, const orc_frame* fr)
         v->bvh_dirty = 0;
     }
     orc_frame_rotation(fr->seed, fr->frame, v->R);
+    classify(v, fr);
     run_phase(v, fr, 0);
     change_detect(v, fr);
-    if (orc_allocate(v->W, v->P, v->d.avg, v->d.rmin, v->d.rmax, v->n, v->off)) return -1;
+    if (orc_allocate_masked(v->W, v->cls, v->P, v->d.avg, v->d.rmin, v->d.rmax, v->n, v->off)) return -1;
     if (v->d.sampler == 1) { /* Metropolis chains instead of the per-probe allocation */
         pthread_once(&g_mh_once, mh_tables_init);
         if (!v->chains_live) mh_init(v, fr->seed);
@@ -2546,6 +2664,7 @@ EXPORT void orc_border_copy(double* tile, uint8_t* cnt, int n, int ch) { border_
 /* Metropolis sampler state and samples (desc.sampler = 1) */
 EXPORT long long orc_mh_samples(const orc_vol* v) { return (long long)v->B; }
 EXPORT const uint32_t* orc_qd(const orc_vol* v) { return v->qd; }
+EXPORT const uint8_t* orc_cls(const orc_vol* v) { return v->cls; }
 EXPORT void orc_dyn_sizes(const orc_vol* v, long long out[8])
 {
     out[0] = (long long)v->Cd;

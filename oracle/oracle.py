@@ -48,6 +48,8 @@ class OrcFrame(C.Structure):
         ("has_camera", C.c_int),
         ("cam", C.c_float * 3),
         ("cam_k", C.c_float),
+        ("has_clip", C.c_int),
+        ("clip", C.c_float * 16),
     ]
 
 
@@ -140,6 +142,10 @@ def lib():
                          ("orc_mh_tri_neg", i32p), ("orc_mh_rad", f64p), ("orc_mh_dep", f64p)]:
             getattr(L, name).argtypes = [vp]
             getattr(L, name).restype = rt
+        L.orc_cls.argtypes = [vp]
+        L.orc_cls.restype = C.POINTER(C.c_uint8)
+        L.orc_allocate_masked.argtypes = [C.POINTER(C.c_uint32), C.POINTER(C.c_uint8), C.c_int, C.c_int, C.c_int,
+                                          C.c_int, C.POINTER(C.c_uint32), C.POINTER(C.c_uint32)]
         L.orc_qd.argtypes = [vp]
         L.orc_qd.restype = C.POINTER(C.c_uint32)
         L.orc_dyn_sizes.argtypes = [vp, C.POINTER(C.c_longlong)]
@@ -211,6 +217,20 @@ def mh_run_table(dims, table, chains, frames, skip, seed=1):
     lib().orc_mh_run_table(_p(d, C.c_int), _p(t, C.c_float), int(chains), int(frames), int(skip), int(seed),
                            _p(out, C.c_double))
     return out.reshape(-1, 8)
+
+
+def allocate_masked(W, cls, avg, rmin, rmax):
+    """the allocation restricted to the clip volumes (cls per probe: 2, 1, 0)"""
+    W = np.ascontiguousarray(W, np.uint32)
+    cls = np.ascontiguousarray(cls, np.uint8)
+    P = len(W)
+    n = np.zeros(P, np.uint32)
+    off = np.zeros(P + 1, np.uint32)
+    rc = lib().orc_allocate_masked(_p(W, C.c_uint32), _p(cls, C.c_uint8), P, int(avg), int(rmin), int(rmax),
+                                   _p(n, C.c_uint32), _p(off, C.c_uint32))
+    if rc:
+        raise ValueError("invalid allocation arguments")
+    return n, off
 
 
 def texel_centre_dir(cx: int, cy: int, n: int) -> np.ndarray:
@@ -323,7 +343,9 @@ def border_copy(tile, cnt, n):
 
 # ---------------------------------------------------------------- volume
 def make_frame(frame, seed, lights, sky=(0.0, 0.0, 0.0), camera=None):
-    """lights: list of (kind, (x,y,z), (r,g,b)); camera: None or (pos, k)."""
+    """lights: list of (kind, (x,y,z), (r,g,b)); camera: None, (pos, k), or
+    (pos, k, M) with M the row-major 4x4 view-projection matrix of the clip
+    volumes (Fig. TrCam(b))."""
     arr = (OrcLight * max(1, len(lights)))()
     for i, (kind, v, rgb) in enumerate(lights):
         arr[i].kind = int(kind)
@@ -339,6 +361,9 @@ def make_frame(frame, seed, lights, sky=(0.0, 0.0, 0.0), camera=None):
         fr.has_camera = 1
         fr.cam[:] = [float(x) for x in camera[0]]
         fr.cam_k = float(camera[1])
+        if len(camera) > 2 and camera[2] is not None:
+            fr.has_clip = 1
+            fr.clip[:] = [float(x) for x in np.asarray(camera[2], np.float32).reshape(16)]
     fr._keep = arr
     return fr
 
@@ -497,6 +522,10 @@ class OracleVolume:
 
     def mh_dep(self):
         return self._arr("orc_mh_dep", self.mh_samples, np.float64)
+
+    def cls(self):
+        """clip volume of each probe this frame: 2 V_in, 1 V_out - V_in, 0 outside"""
+        return self._arr("orc_cls", self.P, np.uint8)
 
     def qd(self):
         """per (probe, octant) dynamic weight q_d of the last update"""

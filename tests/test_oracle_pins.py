@@ -1008,3 +1008,121 @@ def test_dyn_static_samples_snap_to_texel_centres():
     _, trn, _ = O.trace_closest(w.verts, w.idx, o_, -d, v.tmin, np.inf, use_bvh=False)
     np.testing.assert_array_equal(trp, v.mh_tri()[:300])
     np.testing.assert_array_equal(trn, v.mh_tri_neg()[:300])
+
+
+# --------------------------------------------------------------- camera clip volumes
+def _clip_room(sampler=0, avg=32, dims=(5, 5, 5)):
+    w = S.box_room(2)
+    v = O.OracleVolume((-2.0, -2.0, -2.0), (1.0, 1.0, 1.0), dims, rays_avg=avg, rays_min=8, rays_max=128, theta=8,
+                       sampler=sampler, alpha=0.0)
+    # the room spans [0, 8]; probes at -2..2 sit partly outside: fine for classification
+    v.set_scene(w.verts, w.idx, w.albedo)
+    return w, v
+
+
+def test_clip_volume_classification_closed_form():
+    # M = identity: clip = (x, y, z, 1), so the extended frusta are the slabs
+    # |x|, |y| <= 1.2 (V_in) and <= 1.4 (V_out); a camera at the origin with a
+    # large k keeps f_c = 1 (probe grid at integer coordinates -2..2)
+    w, v = _clip_room()
+    M = np.eye(4, dtype=np.float32)
+    v.update(0, 1, [], camera=((0.0, 0.0, 0.0), 100.0, M))
+    cls = v.cls().reshape(5, 5, 5)  # [z][y][x]
+    xs = np.arange(-2, 3)
+    inner = (np.abs(xs)[None, :] <= 1) & (np.abs(xs)[:, None] <= 1)  # [y][x]
+    expect = np.where(inner, 2, 0)[None, :, :].repeat(5, axis=0)
+    np.testing.assert_array_equal(cls, expect)
+    # a camera whose distance heuristic falls off: f_c >= 0.75 needs q_c >= 768
+    v2 = _clip_room()[1]
+    v2.update(0, 1, [], camera=((0.0, 0.0, 0.0), 0.0, M))
+    lut_c = O.luts(v2.voxel_diag)[1]
+    scale = np.float32(64.0 / v2.voxel_diag)
+    qc = []
+    for p in range(125):
+        x = np.asarray(v2.probe_pos(p), np.float32)  # the camera at the origin: FP32 distance, then the LUT bin
+        dist = np.sqrt((x[0] * x[0] + x[1] * x[1]) + x[2] * x[2], dtype=np.float32)
+        qc.append(int(lut_c[min(int(np.floor(np.float32(dist * scale))), 4095)]))
+    qc = np.array(qc)
+    c2 = v2.cls()
+    assert ((c2 == 2) == ((qc >= 768) & (expect.reshape(-1) == 2))).all()
+    # no matrix: every probe in V_in
+    v3 = _clip_room()[1]
+    v3.update(0, 1, [], camera=((0.0, 0.0, 0.0), 100.0))
+    assert (v3.cls() == 2).all()
+
+
+def test_clip_allocation_masked_invariants():
+    rng = np.random.default_rng(5)
+    for _ in range(200):
+        P = int(rng.integers(1, 60))
+        rmin = int(rng.integers(0, 20))
+        m0 = max(rmin, 8)
+        rmax = int(rng.integers(m0, 80))
+        avg = int(rng.integers(m0, rmax + 1))
+        W = (rng.integers(0, 4, P) * rng.integers(0, 1000, P)).astype(np.uint32)
+        cls = rng.integers(0, 3, P).astype(np.uint8)
+        n, off = O.allocate_masked(W, cls, avg, rmin, rmax)
+        assert (n[cls == 0] == 0).all() and (n[cls == 1] == 8).all()
+        vin = cls == 2
+        assert (n[vin] >= m0).all() and (n[vin] <= rmax).all()
+        # the adaptive budget (avg - 8) P, beyond the V_in floors, as far as the caps allow
+        spend = min((avg - 8) * P - (m0 - 8) * int(vin.sum()), int(vin.sum()) * (rmax - m0))
+        assert int(n[vin].sum()) - int(vin.sum()) * m0 == spend
+        a = np.where(n > 8, n - 8, 0).astype(np.int64)
+        np.testing.assert_array_equal(off, np.concatenate([[0], np.cumsum(a)]))
+        # every probe in V_in: the plain rule
+        n2, off2 = O.allocate_masked(W, np.full(P, 2, np.uint8), avg, rmin, rmax)
+        n3, off3 = O.allocate(W, avg, rmin, rmax)
+        np.testing.assert_array_equal(n2, n3)
+        np.testing.assert_array_equal(off2, off3)
+
+
+def test_clip_outside_probes_frozen_and_static_scene_stays_quiet():
+    # a static scene while the camera (hence the clip volumes) moves: probes
+    # outside V_out trace nothing and keep their atlases; gradients need both
+    # frames of a pair inside V_out, so W stays 0 (no spurious triggers)
+    w, v = _clip_room(avg=32)
+    light = [(0, (4.0, 6.0, 4.0), (30.0, 30.0, 30.0))]
+    M = np.eye(4, dtype=np.float32)
+    for f in range(12):
+        Mf = M.copy()
+        Mf[0, 3] = [0.0, 1.0, -1.0, 0.5][f % 4]  # slide the slab in x every frame
+        before_irr, before_n = v.irr().copy(), v.irr_n().copy()
+        v.update(f, 3, light, camera=((0.0, 0.0, 0.0), 100.0, Mf))
+        cls = v.cls()
+        out = cls == 0
+        assert (v.pilot_tri()[out] == -1).all()
+        np.testing.assert_array_equal(v.irr()[out], before_irr[out])
+        np.testing.assert_array_equal(v.irr_n()[out], before_n[out])
+        assert (v.n()[out] == 0).all() and (v.n()[cls == 1] == 8).all()
+        assert v.W().sum() == 0, f
+
+
+def test_clip_catch_up_counts_and_vin_keeps_counting():
+    # V_out - V_in probes have every texel count set down to 16 (Sec.
+    # "Adaptive sampling - static", last paragraph); V_in probes keep counting
+    w, v = _clip_room(avg=64)
+    light = [(0, (4.0, 6.0, 4.0), (30.0, 30.0, 30.0))]
+    M = np.eye(4, dtype=np.float32)
+    M[0, 0] = M[1, 1] = 0.65  # V_in: |x|, |y| <= 1.2 / 0.65 = 1.85; V_out: <= 1.4 / 0.65 = 2.15
+    for f in range(16):
+        v.update(f, 3, light)  # everything in V_in: counts grow past 16
+    assert v.irr_n().max() > 16
+    v.update(16, 3, light, camera=((0.0, 0.0, 0.0), 100.0, M))
+    cls = v.cls()
+    assert (cls == 1).any() and (cls == 2).any()
+    assert (v.irr_n()[cls == 1] <= 16).all() and (v.dep_n()[cls == 1] <= 16).all()
+    assert v.irr_n()[cls == 2].max() > 16
+
+
+def test_clip_metropolis_samples_only_inside_vin():
+    w, v = _clip_room(sampler=1, avg=32)
+    M = np.eye(4, dtype=np.float32)
+    light = [(0, (4.0, 6.0, 4.0), (30.0, 30.0, 30.0))]
+    for f in range(4):
+        v.update(f, 3, light, camera=((0.0, 0.0, 0.0), 100.0, M))
+    cls = v.cls()
+    p = v.mh_probe()
+    outside = cls[p] != 2
+    assert outside.any() and (~outside).any()
+    assert (v.mh_tri()[outside] == -1).all() and (v.mh_tri_neg()[outside] == -1).all()
