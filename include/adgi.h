@@ -123,6 +123,18 @@ typedef struct {
     int32_t has_camera;       /* 1: apply the camera-distance heuristic f_c (Eq. cameraD) */
     float cam_pos[3];
     float cam_k;              /* f_c = 1 within cam_k of the camera */
+    int32_t has_clip;         /* 1 (with has_camera): clip volumes (Fig. TrCam(b)) from view_proj: a
+                                 probe is in V_in when |c_x|, |c_y| <= 1.2 w (w > 0, (c_x, c_y, -, w)
+                                 = view_proj (p, 1) in FP32, row order) and f_c >= 0.75 (q_c >= 768),
+                                 in V_out when <= 1.4 w and f_c >= 0.5 (q_c >= 512).  Outside V_out:
+                                 no pilot rays, heuristic state and atlases left as they are; a pair
+                                 gradient needs both frames inside V_out; only V_in probes take adaptive
+                                 rays or samples (the (rays_avg - 8) * probes adaptive budget spread
+                                 over V_in, capped at rays_max; culled pilots are not reassigned);
+                                 V_out - V_in probes have their texel counts set down to 16
+                                 (Sec. "Adaptive sampling - static", last paragraph).  0: every probe
+                                 in V_in */
+    float view_proj[16];      /* row-major 4x4 camera view-projection matrix */
 } adgi_frame;
 
 typedef struct {
@@ -284,6 +296,7 @@ int adgi_enable_timing(adgi_volume vol, int32_t enable);
  *                       MAIN_REC then hold the +w hits and records in grouped order, and N and
  *                       OFF are not computed (the chains replace the per-probe counts)
  *   ADGI_STATE_QD       uint32[P][8]      dynamic weight q_d per probe and octant (W_p is their sum)
+ *   ADGI_STATE_CLS      uint8[P]          clip volume of the last update: 2 V_in, 1 V_out - V_in, 0 outside
  * Dynamic chains (dyn_ratio > 0; Cd chains, Bd = 5 Cd samples, Pp proxies, Rd = ray budget):
  *   ADGI_STATE_DYN_CHAINS  float[2][Cd][4] chain states (as MH_CHAINS, in proxy-grid units)
  *   ADGI_STATE_DYN_SAMPLES float[Bd][4]    {w.xyz, proxy (int32 bits)}, chain order
@@ -333,7 +346,8 @@ enum {
     ADGI_STATE_DYN_INCL = 30,
     ADGI_STATE_DYN_OFF = 31,
     ADGI_STATE_DYN_HIT = 32,
-    ADGI_STATE_DYN_REC = 33
+    ADGI_STATE_DYN_REC = 33,
+    ADGI_STATE_CLS = 34
 };
 int adgi_state_bytes(adgi_volume vol, int32_t which, uint64_t* bytes);
 int adgi_read_state(adgi_volume vol, int32_t which, void* dst_host, uint64_t bytes);

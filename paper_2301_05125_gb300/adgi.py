@@ -20,7 +20,7 @@ STATE = dict(W=0, N=1, OFF=2, QV=3, QR=4, TRV=5, TRR=6, PILOT_HIT=7, PILOT_REC=8
              MAIN_REC=11, IRR=12, DEP=13, DEP_N=14, ROT=15, BVH_NODES=16, BVH_TRIS=17, MOVING_BVH_NODES=18,
              MOVING_BVH_TRIS=19, MH_CHAINS=20, MH_SAMPLES=21, MH_ORDER=22, MH_OFF=23, MH_HIT_NEG=24,
              QD=25, DYN_CHAINS=26, DYN_SAMPLES=27, DYN_CELLS=28, DYN_FIRST=29, DYN_INCL=30, DYN_OFF=31, DYN_HIT=32,
-             DYN_REC=33)
+             DYN_REC=33, CLS=34)
 
 
 class AdgiError(RuntimeError):
@@ -64,6 +64,8 @@ class adgi_frame(C.Structure):
         ("has_camera", C.c_int32),
         ("cam_pos", C.c_float * 3),
         ("cam_k", C.c_float),
+        ("has_clip", C.c_int32),
+        ("view_proj", C.c_float * 16),
     ]
 
 
@@ -429,6 +431,9 @@ def make_frame(frame, seed, lights, sky=(0.0, 0.0, 0.0), camera=None) -> adgi_fr
         f.has_camera = 1
         f.cam_pos[:] = [float(x) for x in camera[0]]
         f.cam_k = float(camera[1])
+        if len(camera) > 2 and camera[2] is not None:  # (pos, k, row-major 4x4 view-projection)
+            f.has_clip = 1
+            f.view_proj[:] = [float(x) for x in np.asarray(camera[2], np.float32).reshape(16)]
     f._keep = arr
     return f
 
@@ -559,6 +564,9 @@ class Volume:
 
     def qd(self):
         return self.state("QD", np.uint32).reshape(self.P, 8)
+
+    def cls(self):
+        return self.state("CLS", np.uint8)
 
     # dynamic chains (dyn_ratio > 0)
     def dyn_chains(self):

@@ -75,6 +75,8 @@ struct FrameConst {
     float cam_k;
     uint64_t mh_key;        // Metropolis counters of this frame: sm(sm(seed ^ 'METRO') ^ frame)
     uint64_t dyn_key;       // the dynamic chains' counters: sm(sm(seed ^ 'DYNAM') ^ frame)
+    int has_clip;           // clip volumes from clip[] (with has_camera)
+    float clip[16];         // row-major view-projection
 };
 
 struct VolConst {
@@ -97,6 +99,7 @@ struct VolConst {
     int* err;               // anomaly flags (kErr*)
     int dyn;                // dynamic chains on (Metropolis mode with dyn_ratio > 0)
     float hyst_dyn;         // hysteresis of the dynamic rays' batch step
+    const uint8_t* cls;     // [P] clip volume of this frame: 2 V_in, 1 V_out - V_in, 0 outside
 };
 
 // This frame's dynamic rays (dynamic chains over virtual proxies), grouped

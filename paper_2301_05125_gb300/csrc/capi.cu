@@ -272,6 +272,9 @@ struct adgi_volume_s {
     const uint32_t* mh_ord = nullptr;  // grouped order of the last update
     bool mh_live = false;              // chain states initialised
     uint32_t* qd = nullptr;            // [P][8] q_d of the last update
+    uint8_t* cls = nullptr;            // [P] clip volume of the last update
+    uint8_t* vout_even = nullptr;      // [P] in V_out on the last first-of-pair frame
+    uint32_t* dyn_npin = nullptr;      // [Pp] probes of each proxy inside V_in
     // dynamic chains over virtual proxies (desc.dyn_ratio > 0)
     uint32_t dyn_Cd = 0, dyn_Bd = 0, dyn_Rd = 0;
     int dyn_dp[3] = {0, 0, 0}, dyn_pp = 0;
@@ -305,7 +308,7 @@ void free_volume(adgi_volume v)
                     v->G,       v->W,       v->n,      v->off,   v->pil_hit, v->pil_rec, v->pil_lum, v->m_hit,
                     v->m_rec,   v->shadow_ctr, v->verts, v->idx, v->albedo,  v->q_buf, v->err,
                     v->vis,     v->jobs,    v->job_light, v->job_count, v->fdev,
-                    v->qd, v->mh_smp_gn, v->dyn_chain, v->dyn_smp, v->dyn_cell, v->dyn_val, v->dyn_first, v->dyn_keys,
+                    v->qd, v->cls, v->vout_even, v->dyn_npin, v->mh_smp_gn, v->dyn_chain, v->dyn_smp, v->dyn_cell, v->dyn_val, v->dyn_first, v->dyn_keys,
                     v->dyn_vals, v->dyn_hist, v->dyn_incl, v->dyn_off, v->dyn_part, v->dyn_info, v->dyn_tab,
                     v->dyn_tex_dir, v->dyn_hit, v->dyn_rec,
                     v->mh_tab,  v->mh_chain, v->mh_smp, v->mh_smp_g, v->mh_keys, v->mh_vals, v->mh_hist, v->mh_off, v->mh_hitn};
@@ -382,6 +385,8 @@ FrameConst frame_const(adgi_volume v, const adgi_frame* f)
     F.cam_k = f->cam_k;
     F.mh_key = splitmix(splitmix(f->seed ^ kMhSalt) ^ f->frame);
     F.dyn_key = splitmix(splitmix(f->seed ^ kDynSalt) ^ f->frame);
+    F.has_clip = f->has_clip && f->has_camera ? 1 : 0;
+    for (int k = 0; k < 16; ++k) F.clip[k] = f->view_proj[k];
     return F;
 }
 
@@ -530,6 +535,8 @@ int adgi_create_volume(const adgi_volume_desc* desc, void* cuda_stream, adgi_vol
     DA(v->vis, std::max<size_t>(P * 8, (size_t)v->R_main));
     DA(v->job_count, 1);
     DA(v->qd, P * 8);
+    DA(v->cls, P);
+    DA(v->vout_even, P);
     if (d.sampler == 1) {
         v->mh_B = v->R_main;
         if (d.dyn_ratio > 0) {  // budget split static:dynamic = r:1; a static sample traces two rays
@@ -560,6 +567,7 @@ int adgi_create_volume(const adgi_volume_desc* desc, void* cuda_stream, adgi_vol
             DA(v->dyn_smp, (size_t)v->dyn_Bd);
             DA(v->dyn_cell, (size_t)v->dyn_Bd);
             DA(v->dyn_val, cells);
+            DA(v->dyn_npin, (size_t)v->dyn_pp);
             DA(v->dyn_first, cells);
             DA(v->dyn_keys, 2 * cells);
             DA(v->dyn_vals, 2 * cells);
@@ -579,6 +587,7 @@ int adgi_create_volume(const adgi_volume_desc* desc, void* cuda_stream, adgi_vol
     V.err = v->err;
     V.dyn = d.dyn_ratio > 0 ? 1 : 0;
     V.hyst_dyn = d.hysteresis_dyn;
+    V.cls = v->cls;
     cudaStream_t s = v->stream;
 #define CKV(call)                                                                                        \
     do {                                                                                                 \
@@ -617,6 +626,8 @@ int adgi_create_volume(const adgi_volume_desc* desc, void* cuda_stream, adgi_vol
         }
     }
     CKV(cudaMemsetAsync(v->qd, 0, P * 8 * 4, s));
+    CKV(cudaMemsetAsync(v->cls, 2, P, s));
+    CKV(cudaMemsetAsync(v->vout_even, 0, P, s));
     v->shadow_blocks = shadow_grid_blocks(0);
     CKV(cudaEventCreate(&v->ev0));
     CKV(cudaEventCreate(&v->ev1));
@@ -835,6 +846,7 @@ DynBufs dyn_bufs(adgi_volume v)
     D.smp = v->dyn_smp;
     D.cell = v->dyn_cell;
     D.val = v->dyn_val;
+    D.npin = v->dyn_npin;
     D.first = v->dyn_first;
     const size_t cells = (size_t)v->dyn_pp * 8;
     D.keys[0] = v->dyn_keys;
@@ -976,8 +988,10 @@ int enqueue_update(adgi_volume v, const FrameDev& fd, cudaStream_t s, bool phase
     CK(cudaMemsetAsync(v->shadow_ctr, 0, 8, s));
     ShadeWork W{v->vis, v->jobs, v->job_light, v->job_count, (unsigned)std::min<size_t>(v->job_cap, 0xFFFFFFFFu),
                 v->shadow_blocks, v->shadow_ctr};
-    // 1. pilot rays (trace + shade; the shading reads the previous atlases)
+    // 1. pilot rays (trace + shade; the shading reads the previous atlases),
+    // for the probes inside this frame's clip volume V_out
     PHASE(1);
+    CK(launch_classify(V, FD, v->lut_c, v->cls, s));
     CK(launch_pilot_trace(V, FD, S, v->pil_hit, T, s));
     PHASE(2);
     CK(launch_shade(V, FD, S, 0, (uint32_t)V.P * kPilots, nullptr, nullptr, v->irr, v->dep, v->pil_hit, v->pil_rec,
@@ -985,11 +999,11 @@ int enqueue_update(adgi_volume v, const FrameDev& fd, cudaStream_t s, bool phase
     // 2. heuristics -> W_p
     PHASE(3);
     ChangeBufs C{v->pil_hit, v->pil_lum, v->lut_v, v->lut_c, v->qv,  v->qr,  v->qv_even, v->qr_even,
-                 v->amp_v,   v->amp_r,   v->age_v, v->age_r, v->trv, v->trr, v->G,       v->W, v->qd};
+                 v->amp_v,   v->amp_r,   v->age_v, v->age_r, v->trv, v->trr, v->G,       v->W, v->qd, v->vout_even};
     CK(launch_change(V, FD, C, s));
     // 3. allocation
     PHASE(4);
-    if (!mh) CK(launch_allocate(v->W, V.P, V.rays_avg, V.m0, V.rays_max, v->n, v->off, s));
+    if (!mh) CK(launch_allocate(v->W, V.P, V.rays_avg, V.m0, V.rays_max, v->n, v->off, s, v->cls));
     if (mh) {
         // 3'. Metropolis chains draw the samples; group them by probe
         MhBufs M = mh_bufs(v);
@@ -1468,6 +1482,7 @@ int adgi_state_bytes(adgi_volume v, int32_t which, uint64_t* bytes)
                                                   : 8 * (uint64_t)v->mh_B;
         break;
     case ADGI_STATE_QD: *bytes = 4 * 8 * P; break;
+    case ADGI_STATE_CLS: *bytes = P; break;
     case ADGI_STATE_DYN_CHAINS:
     case ADGI_STATE_DYN_SAMPLES:
     case ADGI_STATE_DYN_CELLS:
@@ -1537,6 +1552,7 @@ int adgi_read_state(adgi_volume v, int32_t which, void* dst, uint64_t bytes)
     case ADGI_STATE_MH_OFF: src = v->mh_off; break;
     case ADGI_STATE_MH_HIT_NEG: src = v->mh_hitn; break;
     case ADGI_STATE_QD: src = v->qd; break;
+    case ADGI_STATE_CLS: src = v->cls; break;
     case ADGI_STATE_DYN_CHAINS: src = v->dyn_chain; break;
     case ADGI_STATE_DYN_SAMPLES: src = v->dyn_smp; break;
     case ADGI_STATE_DYN_CELLS: src = v->dyn_cell; break;

@@ -48,6 +48,7 @@ struct ChangeBufs {
     uint32_t* G;  // per (probe, octant): octant-neighbourhood sum of trv + 2 trr
     uint32_t* W;
     uint32_t* qd; // per (probe, octant): the dynamic weight q_d summed into W (null: not kept)
+    uint8_t* vout_even;  // [P] 1: the probe was in V_out on the last first-of-pair frame
 };
 
 // work buffers of the shading wavefront (shade.cu)
@@ -131,6 +132,7 @@ struct DynBufs {
     float4* smp;              // [Bd] sample direction, proxy (int bits) in .w
     int* cell;                // [Bd] proxy*8 + octant, -1 where the target is 0
     uint32_t* val;            // [Pp*8] coarsened target: max q_d over the proxy
+    uint32_t* npin;           // [Pp] probes of each proxy inside V_in
     uint32_t* first;          // [Pp*8] first sample marking each cell (UINT32_MAX: none)
     uint64_t* keys[2];        // sort of the cells by first sample
     uint32_t* vals[2];
@@ -198,9 +200,13 @@ cudaError_t launch_count(const VolConst& V, const FrameDev* FD, const SceneDev& 
 cudaError_t launch_trace_list(const SceneDev& S, const float* o, const float* d, int n, float tmin, float tmax,
                               float* t_out, int* tri_out, cudaStream_t s);
 
-cudaError_t launch_change(const VolConst& V, const FrameDev* FD, const ChangeBufs& B, cudaStream_t s);
-cudaError_t launch_allocate(const uint32_t* W, int P, int avg, int m0, int rmax, uint32_t* n_out, uint32_t* off_out,
+// clip volume of every probe for this frame (V.cls; 2 everywhere without a matrix)
+cudaError_t launch_classify(const VolConst& V, const FrameDev* FD, const uint16_t* lut_c, uint8_t* cls,
                             cudaStream_t s);
+cudaError_t launch_change(const VolConst& V, const FrameDev* FD, const ChangeBufs& B, cudaStream_t s);
+// cls: clip volumes (null: every probe in V_in, the plain rule)
+cudaError_t launch_allocate(const uint32_t* W, int P, int avg, int m0, int rmax, uint32_t* n_out, uint32_t* off_out,
+                            cudaStream_t s, const uint8_t* cls = nullptr);
 // this frame's blend plan (needs only the frame rotation: may run beside the traces)
 cudaError_t launch_blend_plan(const VolConst& V, const FrameDev* FD, const float4* sf, const BlendPlan& plan,
                               cudaStream_t s);

@@ -94,6 +94,7 @@ __device__ __forceinline__ float mh_guide(const VolConst& V, const FrameConst& F
     const float3 w = mh_oct_dir(ux, uy);
     *probe = p;
     *dir = w;
+    if (V.cls[p] != 2) return 0.0f;  // adaptive samples only inside V_in
     const int o = (w.x < 0.0f ? 1 : 0) | (w.y < 0.0f ? 2 : 0) | (w.z < 0.0f ? 4 : 0);
     const uint32_t q = qc_of_probe(V, F, M.lut_c, p) * (uint32_t)__ldg(M.qv + (size_t)p * 8 + o);
     const float f_s = fm(__uint2float_rn(q), M.inv_q2);
@@ -274,12 +275,16 @@ __global__ void __launch_bounds__(256) k_dyn_target(VolConst V, DynBufs D)
     if (cell >= D.pp * 8) return;
     const int q = cell >> 3, o = cell & 7;
     const int qx = q % D.dp[0], qy = (q / D.dp[0]) % D.dp[1], qz = q / (D.dp[0] * D.dp[1]);
-    uint32_t m = 0;
+    uint32_t m = 0, nin = 0;
     for (int z = 3 * qz; z < min(3 * qz + 3, V.dims[2]); ++z)
         for (int y = 3 * qy; y < min(3 * qy + 3, V.dims[1]); ++y)
-            for (int x = 3 * qx; x < min(3 * qx + 3, V.dims[0]); ++x)
-                m = max(m, __ldg(D.qd + ((size_t)x + (size_t)V.dims[0] * ((size_t)y + (size_t)V.dims[1] * z)) * 8 + o));
+            for (int x = 3 * qx; x < min(3 * qx + 3, V.dims[0]); ++x) {
+                const size_t pi = (size_t)x + (size_t)V.dims[0] * ((size_t)y + (size_t)V.dims[1] * z);
+                m = max(m, __ldg(D.qd + pi * 8 + o));
+                nin += V.cls[pi] == 2;
+            }
     D.val[cell] = m;
+    if (o == 0) D.npin[q] = nin;  // probes of the proxy inside V_in (they alone send dynamic rays)
     D.first[cell] = 0xFFFFFFFFu;
     D.incl[cell] = 0;
 }
@@ -343,13 +348,6 @@ __global__ void k_dyn_keys(DynBufs D)
     D.vals[0][cell] = (uint32_t)cell;
 }
 
-__device__ __forceinline__ int dyn_proxy_probes(const VolConst& V, const DynBufs& D, int q)
-{
-    const int qx = q % D.dp[0], qy = (q / D.dp[0]) % D.dp[1], qz = q / (D.dp[0] * D.dp[1]);
-    return (min(3 * qx + 3, V.dims[0]) - 3 * qx) * (min(3 * qy + 3, V.dims[1]) - 3 * qy) *
-           (min(3 * qz + 3, V.dims[2]) - 3 * qz);
-}
-
 // One block: the marked cells in first-sample order are traced while the
 // running ray count stays within the budget.
 __global__ void __launch_bounds__(1024) k_dyn_budget(VolConst V, DynBufs D, const uint64_t* __restrict__ keys,
@@ -373,7 +371,7 @@ __global__ void __launch_bounds__(1024) k_dyn_budget(VolConst V, DynBufs D, cons
         if (i < n) {
             marked = keys[i] < (uint64_t)D.n_samples;
             cell = (int)cells[i];
-            if (marked) rays = (unsigned long long)dyn_proxy_probes(V, D, cell >> 3) * (unsigned)__ldg(D.ntex + (cell & 7));
+            if (marked) rays = (unsigned long long)D.npin[cell >> 3] * (unsigned)__ldg(D.ntex + (cell & 7));
         }
         unsigned long long x = rays;  // inclusive scan in the block
 #pragma unroll
@@ -418,8 +416,9 @@ __global__ void k_dyn_count(VolConst V, DynBufs D)
     const int ix = p % V.dims[0], iy = (p / V.dims[0]) % V.dims[1], iz = p / (V.dims[0] * V.dims[1]);
     const int q = ix / 3 + D.dp[0] * (iy / 3 + D.dp[1] * (iz / 3));
     uint32_t c = 0;
-    for (int o = 0; o < 8; ++o)
-        if (D.incl[q * 8 + o]) c += (uint32_t)__ldg(D.ntex + o);
+    if (V.cls[p] == 2)  // dynamic rays only from V_in probes
+        for (int o = 0; o < 8; ++o)
+            if (D.incl[q * 8 + o]) c += (uint32_t)__ldg(D.ntex + o);
     D.off[p] = c;
 }
 

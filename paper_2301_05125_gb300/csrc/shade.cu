@@ -65,6 +65,7 @@ __device__ __forceinline__ bool ray_of(const VolConst& V, const FrameConst& F, c
 {
     if (Rs.mode == 0) {
         int p = (int)(r >> 3);
+        if (V.cls[p] == 0) return false;  // outside V_out: no pilot ray
         slot = r;
         o = probe_pos(V, p);
         d = pilot_dir(F.pilot_key, (uint32_t)p, (int)(r & 7));
@@ -80,12 +81,13 @@ __device__ __forceinline__ bool ray_of(const VolConst& V, const FrameConst& F, c
     if (Rs.mode == 2) {
         const float4 a = __ldg(Rs.sf + r);
         const int p = __float_as_int(a.w);
-        if (p < 0 || p >= V.P) return false;
+        if (p < 0 || p >= V.P || V.cls[p] != 2) return false;  // samples outside V_in are dropped
         slot = r;
         o = probe_pos(V, p);
         d = make_float3(a.x, a.y, a.z);
         return true;
     }
+    if (r >= __ldg(Rs.off + V.P)) return false;  // beyond this frame's adaptive rays (unspent budget)
     int p = probe_of_ray(Rs.off, r, lo, hi);
     uint32_t base = __ldg(Rs.off + p), m = __ldg(Rs.off + p + 1) - base;
     if (m > (uint32_t)(V.rays_max - kPilots) || r - base >= m) return false;
@@ -214,6 +216,18 @@ __global__ void __launch_bounds__(256) k_shade_finish(VolConst V, const FrameDev
     if (r >= Rs.n) return;
     uint32_t slot;
     float3 o, d;
+    if (Rs.mode == 0 && V.cls[r >> 3] == 0) {  // a culled pilot: a miss with nothing gathered
+        rec[r] = make_float4(0.f, 0.f, 0.f, V.depth_max);
+        if (lum) lum[r] = 0.0f;
+        return;
+    }
+    if (Rs.mode == 2) {  // a sample outside V_in: dropped, an empty record
+        const int p = __float_as_int(__ldg(Rs.sf + r).w);
+        if (p >= 0 && p < V.P && V.cls[p] != 2) {
+            rec[r] = make_float4(0.f, 0.f, 0.f, V.depth_max);
+            return;
+        }
+    }
     if (!ray_of(V, F, Rs, r, s_lo, s_hi, slot, o, d)) return;  // flagged by the trace kernel
     int2 hv = hit[slot];
     uint32_t h = (uint32_t)hv.x;

@@ -56,6 +56,10 @@ __global__ void __launch_bounds__(256) k_pilot_trace(VolConst V, const FrameDev*
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= V.P * kPilots) return;
     int p = i >> 3, o = i & 7;
+    if (V.cls[p] == 0) {  // outside V_out: no pilot rays
+        hit[i] = make_int2((int)kMiss, 0x7F800000);
+        return;
+    }
     float3 org = probe_pos(V, p);
     float3 d = pilot_dir(F.pilot_key, (uint32_t)p, o);
     float t;
@@ -77,7 +81,7 @@ __global__ void __launch_bounds__(256) k_main_trace(VolConst V, const FrameDev* 
     uint32_t r1 = min(R - 1, r0 + blockDim.x - 1);
     block_probe_range(off, V.P, r0, r1, &s_lo, &s_hi);
     uint32_t r = r0 + threadIdx.x;
-    if (r >= R) return;
+    if (r >= R || r >= __ldg(off + V.P)) return;  // with clip volumes part of the budget may stay unspent
     int p = probe_of_ray(off, r, s_lo, s_hi);
     uint32_t base = __ldg(off + p);
     uint32_t m = __ldg(off + p + 1) - base;
@@ -114,6 +118,10 @@ __global__ void __launch_bounds__(256) k_mh_trace(VolConst V, SceneDev S, const 
     const int p = __float_as_int(a.w);
     if (p < 0 || p >= V.P) {
         atomicOr(V.err, kErrRayRange);
+        dst[q] = make_int2((int)kMiss, 0x7F800000);
+        return;
+    }
+    if (V.cls[p] != 2) {  // a sample outside V_in is dropped
         dst[q] = make_int2((int)kMiss, 0x7F800000);
         return;
     }
@@ -167,6 +175,7 @@ __global__ void __launch_bounds__(128) k_count(VolConst V, const FrameDev* __res
         bool ok = true, shadows = true;
         if (r < NP) {
             int p = r >> 3;
+            ok = V.cls[p] != 0;  // no pilots outside V_out
             org = probe_pos(V, p);
             d = pilot_dir(F.pilot_key, (uint32_t)p, r & 7);
         } else if (smp_g) {
@@ -182,7 +191,7 @@ __global__ void __launch_bounds__(128) k_count(VolConst V, const FrameDev* __res
             uint32_t q = r - NP;
             int p = probe_of_ray(off, q, s_lo, s_hi);
             uint32_t base = __ldg(off + p), m = __ldg(off + p + 1) - base;
-            ok = m <= (uint32_t)(V.rays_max - kPilots) && q - base < m;
+            ok = q < __ldg(off + V.P) && m <= (uint32_t)(V.rays_max - kPilots) && q - base < m;
             org = probe_pos(V, p);
             uint32_t i;
             if (ok) d = main_dir(F, sf, m, q - base, &i);

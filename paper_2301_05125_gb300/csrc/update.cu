@@ -34,12 +34,58 @@ __device__ __forceinline__ uint16_t trigger(uint16_t& amp, uint8_t& age, int del
     return (uint16_t)cur;
 }
 
+// Clip volumes (Fig. TrCam(b)): with the view-projection M, probe p is in
+// the extended frustum |clip_xy| <= L when w > 0 and |c_x|, |c_y| <= L w,
+// (c_x, c_y, -, w) = M (p, 1) in FP32 row order; V_in: L = 1.2 and q_c >= 768
+// (f_c >= 0.75), V_out: L = 1.4 and q_c >= 512 (f_c >= 0.5).
+__device__ __forceinline__ bool in_frustum(const float* m, float3 x, float L)
+{
+    const float w = fa(fa(fa(fm(m[12], x.x), fm(m[13], x.y)), fm(m[14], x.z)), m[15]);
+    const float cx = fa(fa(fa(fm(m[0], x.x), fm(m[1], x.y)), fm(m[2], x.z)), m[3]);
+    const float cy = fa(fa(fa(fm(m[4], x.x), fm(m[5], x.y)), fm(m[6], x.z)), m[7]);
+    if (!(w > 0.0f)) return false;
+    const float lw = fm(L, w);
+    return fabsf(cx) <= lw && fabsf(cy) <= lw;
+}
+
+__global__ void __launch_bounds__(256) k_classify(VolConst V, const FrameDev* __restrict__ FD,
+                                                  const uint16_t* __restrict__ lut_c, uint8_t* __restrict__ cls)
+{
+    const FrameConst& F = FD->F;
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= V.P) return;
+    uint8_t c = 2;
+    if (F.has_clip && F.has_camera) {
+        const float3 x = probe_pos(V, p);
+        const uint32_t qc = qc_of_probe(V, F, lut_c, p);
+        c = (qc >= 768u && in_frustum(F.clip, x, 1.2f)) ? 2 : ((qc >= 512u && in_frustum(F.clip, x, 1.4f)) ? 1 : 0);
+    }
+    cls[p] = c;
+}
+
 __global__ void __launch_bounds__(128) k_change_state(VolConst V, const FrameDev* __restrict__ FD, ChangeBufs B)
 {
     const FrameConst& F = FD->F;
     int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= V.P) return;
     uint32_t yv[8], yr[8];
+    const uint8_t cl = V.cls[p];
+    if (cl == 0) {  // outside V_out: no heuristics this frame; the state waits
+        for (int o = 0; o < 8; ++o) {
+            const size_t i = (size_t)p * 8 + o;
+            B.trv[i] = 0;
+            B.trr[i] = 0;
+            B.qv[i] = 0;
+            B.qr[i] = 0;
+            yv[o] = yr[o] = 0u;
+        }
+        if (F.even) B.vout_even[p] = 0;
+        uint4* G4 = reinterpret_cast<uint4*>(B.G + (size_t)p * 8);
+        G4[0] = make_uint4(0u, 0u, 0u, 0u);
+        G4[1] = make_uint4(0u, 0u, 0u, 0u);
+        return;
+    }
+    const bool gradient = !F.even && F.pair_valid && B.vout_even[p];  // both frames of the pair in V_out
 #pragma unroll
     for (int o = 0; o < 8; ++o) {
         size_t i = (size_t)p * 8 + o;
@@ -52,7 +98,7 @@ __global__ void __launch_bounds__(128) k_change_state(VolConst V, const FrameDev
         uint16_t qv = __ldg(B.lut_v + qt);
         uint16_t qr = (uint16_t)qr_of(B.pil_lum[i]);
         int dv = 0, dr = 0;
-        if (!F.even && F.pair_valid) {
+        if (gradient) {
             dv = abs((int)qv - (int)B.qv_even[i]);
             dr = abs((int)qr - (int)B.qr_even[i]);
         }
@@ -73,6 +119,7 @@ __global__ void __launch_bounds__(128) k_change_state(VolConst V, const FrameDev
             B.qr_even[i] = qr;
         }
     }
+    if (F.even) B.vout_even[p] = 1;
     uint32_t g[8];
 #pragma unroll
     for (int o = 0; o < 8; ++o) {
@@ -110,8 +157,9 @@ __global__ void __launch_bounds__(128) k_change_weight(VolConst V, const FrameDe
     const uint32_t qc = qc_of_probe(V, F, B.lut_c, p);
     uint64_t Wp = 0;
 #pragma unroll
+    const bool vin = V.cls[p] == 2;  // only V_in probes take adaptive samples
     for (int o = 0; o < 8; ++o) {
-        const uint64_t qd = ((uint64_t)qc * (uint64_t)B.qv[(size_t)p * 8 + o] * (uint64_t)f[o]) >> 20;
+        const uint64_t qd = vin ? ((uint64_t)qc * (uint64_t)B.qv[(size_t)p * 8 + o] * (uint64_t)f[o]) >> 20 : 0ull;
         if (B.qd) B.qd[(size_t)p * 8 + o] = (uint32_t)(qd < 0xFFFFFFFFull ? qd : 0xFFFFFFFFull);
         Wp += qd;
     }
@@ -178,37 +226,59 @@ __device__ __forceinline__ uint64_t block_exscan(uint64_t v, uint64_t* red, uint
     return before;
 }
 
-__global__ void __launch_bounds__(kAllocThreads) k_allocate(const uint32_t* __restrict__ W, int P, int avg, int m0,
-                                                            int rmax, uint32_t* __restrict__ n, uint32_t* __restrict__ off)
+// With clip volumes (cls given) only V_in probes (cls 2) take adaptive rays:
+// floors m0 in V_in, 8 (the pilots) in V_out - V_in, 0 outside; beyond the
+// V_in floors E = (avg - 8) P - (m0 - 8) |V_in| is spread over V_in, capped
+// at rmax - m0 per probe.  Without cls every probe is in V_in and E =
+// (avg - m0) P.
+__global__ void __launch_bounds__(kAllocThreads) k_allocate(const uint32_t* __restrict__ Win, int P, int avg, int m0,
+                                                            int rmax, uint32_t* __restrict__ n, uint32_t* __restrict__ off,
+                                                            const uint8_t* __restrict__ cls)
 {
     __shared__ uint64_t red[33];
     const int chunk = (P + kAllocThreads - 1) / kAllocThreads;
     const int c0 = min(P, (int)threadIdx.x * chunk), c1 = min(P, c0 + chunk);
-    const uint64_t E = (uint64_t)(avg - m0) * (uint64_t)P;
+    uint64_t pin = 0;
+    for (int p = c0; p < c1; ++p) pin += (!cls || cls[p] == 2) ? 1u : 0u;
+    uint64_t rank0, Pin;
+    rank0 = block_exscan(pin, red, &Pin);  // V_in rank of this chunk's first V_in probe
     const uint32_t cap = (uint32_t)(rmax - m0);
+    uint64_t E = (uint64_t)(avg - 8) * (uint64_t)P - (uint64_t)(m0 - 8) * Pin;
+    if (E > Pin * cap) E = Pin * cap;
+    // W of the probes outside V_in counts as 0, and their cap as 0
+#define W_OF(p) ((!cls || cls[p] == 2) ? Win[p] : 0u)
+#define CAP_OF(p) ((!cls || cls[p] == 2) ? cap : 0u)
     uint64_t s = 0;
-    for (int p = c0; p < c1; ++p) s += W[p];
+    for (int p = c0; p < c1; ++p) s += W_OF(p);
     const uint64_t S = block_sum(s, red);
-    if (S == 0) {
-        const uint64_t q = E / (uint64_t)P, r = E % (uint64_t)P;
-        for (int p = c0; p < c1; ++p) n[p] = (uint32_t)(q + ((uint64_t)p < r ? 1u : 0u));
+    if (S == 0) {  // uniform over V_in, the remainder to the lowest V_in ranks
+        const uint64_t q = Pin ? E / Pin : 0, r = Pin ? E % Pin : 0;
+        uint64_t rank = rank0;
+        for (int p = c0; p < c1; ++p) {
+            if (cls && cls[p] != 2) {
+                n[p] = 0u;
+                continue;
+            }
+            n[p] = (uint32_t)(q + (rank < r ? 1u : 0u));
+            ++rank;
+        }
     } else {
         for (int p = c0; p < c1; ++p) n[p] = 0u;
         uint64_t Erem = E;
         for (int it = 0; it < kAllocIters; ++it) {
             uint64_t su = 0;
             for (int p = c0; p < c1; ++p) {
-                uint32_t w = W[p];
-                if (w > 0u && n[p] < cap) su += w;
+                uint32_t w = W_OF(p);
+                if (w > 0u && n[p] < CAP_OF(p)) su += w;
             }
             const uint64_t SU = block_sum(su, red);
             if (SU == 0 || Erem == 0) break;
             uint64_t given = 0;
             for (int p = c0; p < c1; ++p) {
-                uint32_t w = W[p], e = n[p];
-                if (w == 0u || e >= cap) continue;
+                uint32_t w = W_OF(p), e = n[p];
+                if (w == 0u || e >= CAP_OF(p)) continue;
                 uint64_t share = Erem * (uint64_t)w / SU;
-                uint64_t room = cap - e;
+                uint64_t room = CAP_OF(p) - e;
                 uint64_t a = share < room ? share : room;
                 n[p] = e + (uint32_t)a;
                 given += a;
@@ -221,16 +291,16 @@ __global__ void __launch_bounds__(kAllocThreads) k_allocate(const uint32_t* __re
         for (int guard = 0; Erem > 0 && guard < (1 << 20); ++guard) {
             uint64_t ca = 0;
             for (int p = c0; p < c1; ++p)
-                if (W[p] > 0u && n[p] < cap) ++ca;
+                if (W_OF(p) > 0u && n[p] < CAP_OF(p)) ++ca;
             const bool modeA = block_sum(ca, red) > 0;
             uint64_t ce = 0;
             for (int p = c0; p < c1; ++p)
-                if (n[p] < cap && (!modeA || W[p] > 0u)) ++ce;
+                if (n[p] < CAP_OF(p) && (!modeA || W_OF(p) > 0u)) ++ce;
             uint64_t tot;
             uint64_t pre = block_exscan(ce, red, &tot);
             if (tot == 0) break;
             for (int p = c0; p < c1; ++p) {
-                if (n[p] < cap && (!modeA || W[p] > 0u)) {
+                if (n[p] < CAP_OF(p) && (!modeA || W_OF(p) > 0u)) {
                     if (pre < Erem) n[p] += 1u;
                     ++pre;
                 }
@@ -238,17 +308,25 @@ __global__ void __launch_bounds__(kAllocThreads) k_allocate(const uint32_t* __re
             Erem -= tot < Erem ? tot : Erem;
         }
     }
+    // rays per probe: the floor plus the extra; adaptive rays = rays - 8 (0 outside V_in)
+#define FLOOR_OF(p) ((!cls || cls[p] == 2) ? (uint32_t)m0 : (cls[p] == 1 ? 8u : 0u))
     uint64_t loc = 0;
-    for (int p = c0; p < c1; ++p) loc += (uint64_t)(m0 - 8) + n[p];
+    for (int p = c0; p < c1; ++p) {
+        const uint32_t np = FLOOR_OF(p) + n[p];
+        loc += np > 8u ? np - 8u : 0u;
+    }
     uint64_t tot;
     uint64_t pre = block_exscan(loc, red, &tot);
     for (int p = c0; p < c1; ++p) {
         off[p] = (uint32_t)pre;
-        uint32_t np = (uint32_t)m0 + n[p];
-        pre += np - 8u;
+        const uint32_t np = FLOOR_OF(p) + n[p];
+        pre += np > 8u ? np - 8u : 0u;
         n[p] = np;
     }
     if (threadIdx.x == 0) off[P] = (uint32_t)tot;
+#undef W_OF
+#undef CAP_OF
+#undef FLOOR_OF
 }
 
 // ============================================================== blend
@@ -522,6 +600,7 @@ __device__ __forceinline__ void blend_packed(const VolConst& V, const BlendBufs&
                 x.add(ct, rc.x, rc.y, rc.z);
             }
         }
+        if (V.cls[p] == 1) x.n = min(x.n, 16u);  // V_out - V_in: counts set down to 16
         irr_new[t] = x.code();
     }
     for (int q = lane; q < nd * nd; q += 32) {
@@ -535,6 +614,7 @@ __device__ __forceinline__ void blend_packed(const VolConst& V, const BlendBufs&
             for (uint32_t u = __ldg(beg_d + t); u < b1; ++u)
                 x.add(ct, fd(__ldg(&mrec[min((uint32_t)__ldg(ord_d + u), m - 1)].w), V.s_f));
         }
+        if (V.cls[p] == 1) x.n = min(x.n, 16u);
         dep_new[t] = x.code();
     }
     __syncwarp();
@@ -632,8 +712,9 @@ __global__ void __launch_bounds__(128) k_blend(VolConst V, const FrameDev* __res
         if (lane == 0) atomicOr(V.err, kErrRayRange);
         m = 0;
     }
-    const int npil = F.even ? kPilots : 0;
-    if ((int)m + npil == 0) return;  // untouched tile: nothing to read or write
+    const uint8_t cl = V.cls[p];
+    const int npil = (F.even && cl >= 1) ? kPilots : 0;  // pilots exist inside V_out only
+    if ((int)m + npil == 0 && cl != 1) return;  // untouched tile (V_out - V_in tiles get the count catch-up)
     const int Ti = V.Ti, Td = V.Td, ni = V.n_irr, nd = V.n_dep;
     const int ti2 = Ti * Ti, td2 = Td * Td;
     const BlendLayout L = blend_layout(Ti, Td);
@@ -715,6 +796,7 @@ __global__ void __launch_bounds__(128) k_blend(VolConst V, const FrameDev* __res
             k += b1 - b0;
         }
         if (k) v = irr_texel_blend(v, sx, sy, sz, k, omh);
+        if (cl == 1) v.w = fminf(v.w, 16.0f);  // V_out - V_in: counts set down to 16 (catch-up)
         irr_new[t] = v;
     }
     for (int q = lane; q < nd * nd; q += 32) {
@@ -749,6 +831,7 @@ __global__ void __launch_bounds__(128) k_blend(VolConst V, const FrameDev* __res
             k += b1 - b0;
         }
         if (k) v = dep_texel_blend(v, c, s1, s2, k, omh);
+        if (cl == 1) c = min(c, 16u);
         dep_new[t] = v;
         dn_new[t] = (uint8_t)c;
     }
@@ -841,9 +924,11 @@ __global__ void __launch_bounds__(128) k_mh_blend(VolConst V, const FrameDev* __
         if (lane == 0) atomicOr(V.err, kErrRayRange);
         b1 = b0;
     }
-    const int npil = F.even ? kPilots : 0;
+    const uint8_t cl = V.cls[p];
+    if (cl != 2) b1 = b0;  // samples outside V_in are dropped
+    const int npil = (F.even && cl >= 1) ? kPilots : 0;
     const uint32_t r0 = V.dyn ? __ldg(B.dyn.off + p) : 0u, r1 = V.dyn ? __ldg(B.dyn.off + p + 1) : 0u;
-    if (b1 == b0 && npil == 0 && r1 <= r0) return;  // untouched tile
+    if (b1 == b0 && npil == 0 && r1 <= r0 && cl != 1) return;  // untouched tile
     const int Ti = V.Ti, Td = V.Td, ni = V.n_irr, nd = V.n_dep;
     const int ti2 = Ti * Ti, td2 = Td * Td;
     const MhLayout L = mh_layout(Ti, Td, V.dyn != 0);
@@ -940,6 +1025,7 @@ __global__ void __launch_bounds__(128) k_mh_blend(VolConst V, const FrameDev* __
             const float4 ds = dacc_i[t];
             if (ds.w > 0.0f) v = irr_texel_blend(v, ds.x, ds.y, ds.z, (uint32_t)ds.w, 1.0f - V.hyst_dyn);
         }
+        if (cl == 1) v.w = fminf(v.w, 16.0f);
         acc_i[t] = v;
     }
     for (int q = lane; q < nd * nd; q += 32) {
@@ -954,6 +1040,7 @@ __global__ void __launch_bounds__(128) k_mh_blend(VolConst V, const FrameDev* __
             const float2 ds = dacc_d[t];
             if (kd2) v = dep_texel_blend(v, c, ds.x, ds.y, kd2, 1.0f - V.hyst_dyn);
         }
+        if (cl == 1) c = min(c, 16u);
         acc_d[t] = v;
         dn[t] = (uint8_t)c;
     }
@@ -1008,10 +1095,18 @@ cudaError_t launch_change(const VolConst& V, const FrameDev* FD, const ChangeBuf
     return cudaGetLastError();
 }
 
-cudaError_t launch_allocate(const uint32_t* W, int P, int avg, int m0, int rmax, uint32_t* n_out, uint32_t* off_out,
+cudaError_t launch_classify(const VolConst& V, const FrameDev* FD, const uint16_t* lut_c, uint8_t* cls,
                             cudaStream_t s)
 {
-    k_allocate<<<1, kAllocThreads, 0, s>>>(W, P, avg, m0, rmax, n_out, off_out);
+    k_classify<<<(V.P + 255) / 256, 256, 0, s>>>(V, FD, lut_c, cls);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_allocate(const uint32_t* W, int P, int avg, int m0, int rmax, uint32_t* n_out, uint32_t* off_out,
+                            cudaStream_t s, const uint8_t* cls)
+{
+    k_allocate<<<1, kAllocThreads, 0, s>>>(W, P, avg, m0, rmax, n_out, off_out, cls);
     count_launches(1);
     return cudaGetLastError();
 }
