@@ -938,6 +938,7 @@ typedef struct {
     int packed;           /* 1: 32-bit packed atlases (the paper's codecs) */
     int sampler;          /* 0: deterministic allocation; 1: Metropolis chains (static guide) */
     float alpha;          /* confidence alpha in the cache term of the guide (Eq. DDGIBays) */
+    int blend_mode;       /* 0 nearest texel (Alg. ApproxAlgo); 1 DDGI cosine gather (Sec. 3.1)  */
     int dyn_ratio;        /* sampler = 1: > 0 adds the dynamic chains (Sec. "Adaptive sampling -  */
                           /* dynamic") with a static:dynamic budget split of dyn_ratio:1      */
     float hyst_dyn;       /* hysteresis of the dynamic rays' batch update */
@@ -1174,6 +1175,10 @@ EXPORT orc_vol* orc_create(const orc_desc* d, int nthreads)
         if (d->dyn_ratio > 0) dyn_create(v);
     } else if (d->dyn_ratio != 0) { /* the dynamic chains belong to the Metropolis mode */
         orc_destroy(v);
+        return NULL;
+    }
+    if (d->blend_mode != 0 && (d->blend_mode != 1 || d->sampler != 0 || d->packed)) {
+        orc_destroy(v); /* the cosine gather blends the allocated rays into FP64 atlases */
         return NULL;
     }
     return v;
@@ -2471,6 +2476,103 @@ static void mh_blend_probe(orc_vol* v, int p, int use_pilots, double h)
     free(kd);
 }
 
+/* DDGI's cosine-gather blend (Sec. 3.1; the variant of the texel update):
+   every ray of the probe contributes to every texel of its hemisphere.  For
+   interior texel t with centre direction n_t (the octahedral decode of the
+   texel centre) and ray r of direction w_r, c = n_t . w_r: the irradiance
+   texel takes the c-weighted mean of the rays' radiance over c > 0, the
+   visibility texel the c^50-weighted mean of {d, d^2} (DDGI's depth
+   sharpness 50); k = the number of rays with c > 0 enters the batched
+   moving average as the sample count (w = max(1 - h, k/(n + k))). */
+#define COS_DEPTH_SHARPNESS 50
+static void blend_probe_cos(orc_vol* v, int p, int use_pilots, double h)
+{
+    const int Ti = v->Ti, Td = v->Td, ni = v->d.n_irr, nd = v->d.n_dep;
+    double* irr = v->irr + (size_t)p * Ti * Ti * 3;
+    uint8_t* irn = v->irr_n + (size_t)p * Ti * Ti;
+    double* dep = v->dep + (size_t)p * Td * Td * 2;
+    uint8_t* den = v->dep_n + (size_t)p * Td * Td;
+    const uint32_t mp = v->n[p] > 8u ? v->n[p] - 8u : 0u;
+    const int total = (int)mp + (use_pilots ? 8 : 0);
+    double* dirs = (double*)malloc(sizeof(double) * 3 * (size_t)(total + 1));
+    const double** rads = (const double**)malloc(sizeof(double*) * (size_t)(total + 1));
+    double* deps = (double*)malloc(sizeof(double) * (size_t)(total + 1));
+    for (int j = 0; j < total; ++j) {
+        float d[3];
+        if (use_pilots && j < 8) {
+            const float* pd = v->pil_dir + ((size_t)p * 8 + (size_t)j) * 3;
+            d[0] = pd[0];
+            d[1] = pd[1];
+            d[2] = pd[2];
+            rads[j] = v->pil_rad + ((size_t)p * 8 + (size_t)j) * 3;
+            deps[j] = v->pil_dep[(size_t)p * 8 + (size_t)j];
+        } else {
+            int i = use_pilots ? j - 8 : j;
+            main_dir(v, (int)mp, i, d);
+            size_t r = (size_t)v->off[p] + (size_t)i;
+            rads[j] = v->m_rad + r * 3;
+            deps[j] = v->m_dep[r];
+        }
+        for (int c = 0; c < 3; ++c) dirs[j * 3 + c] = d[c];
+    }
+    double* si = (double*)calloc((size_t)Ti * Ti * 3, sizeof(double));
+    int* ki = (int*)calloc((size_t)Ti * Ti, sizeof(int));
+    double* sd = (double*)calloc((size_t)Td * Td * 2, sizeof(double));
+    int* kd = (int*)calloc((size_t)Td * Td, sizeof(int));
+    for (int pass = 0; pass < 2; ++pass) {
+        const int n = pass ? nd : ni, T = n + 2;
+        for (int cy = 0; cy < n; ++cy)
+            for (int cx = 0; cx < n; ++cx) {
+                const int t = (cy + 1) * T + (cx + 1);
+                double uv[2] = {((cx + 0.5) / n) * 2.0 - 1.0, ((cy + 0.5) / n) * 2.0 - 1.0}, nt[3];
+                orc_oct_decode(uv, nt);
+                double sw = 0.0, acc[3] = {0.0, 0.0, 0.0};
+                int k = 0;
+                for (int j = 0; j < total; ++j) {
+                    double c = nt[0] * dirs[j * 3] + nt[1] * dirs[j * 3 + 1] + nt[2] * dirs[j * 3 + 2];
+                    if (!(c > 0.0)) continue;
+                    ++k;
+                    if (!pass) {
+                        sw += c;
+                        for (int q = 0; q < 3; ++q) acc[q] += c * rads[j][q];
+                    } else {
+                        double wgt = pow(c, COS_DEPTH_SHARPNESS);
+                        sw += wgt;
+                        acc[0] += wgt * deps[j];
+                        acc[1] += wgt * deps[j] * deps[j];
+                    }
+                }
+                if (!k || !(sw > 0.0)) continue;
+                /* the weighted mean times k: batch_apply divides the sums by k */
+                if (!pass) {
+                    for (int q = 0; q < 3; ++q) si[t * 3 + q] = acc[q] / sw * k;
+                    ki[t] = k;
+                } else {
+                    sd[t * 2] = acc[0] / sw * k;
+                    sd[t * 2 + 1] = acc[1] / sw * k;
+                    kd[t] = k;
+                }
+            }
+    }
+    batch_apply(irr, irn, si, ki, Ti * Ti, 3, h);
+    batch_apply(dep, den, sd, kd, Td * Td, 2, h);
+    if (v->cls[p] == 1) {
+        for (int t = 0; t < Ti * Ti; ++t)
+            if (irn[t] > 16) irn[t] = 16;
+        for (int t = 0; t < Td * Td; ++t)
+            if (den[t] > 16) den[t] = 16;
+    }
+    border_copy(irr, irn, ni, 3);
+    border_copy(dep, den, nd, 2);
+    free(si);
+    free(ki);
+    free(sd);
+    free(kd);
+    free(dirs);
+    free(rads);
+    free(deps);
+}
+
 static void pilot_probe(orc_vol* v, const orc_frame* fr, int p)
 {
     if (v->cls[p] == 0) { /* outside V_out: no pilot rays (records: a miss with nothing gathered) */
@@ -2535,6 +2637,8 @@ static void* worker(void* arg)
         else
             if (j->v->d.packed)
                 blend_probe_packed(j->v, p, (j->fr->frame & 1u) == 0 && j->v->cls[p] >= 1);
+            else if (j->v->d.blend_mode == 1)
+                blend_probe_cos(j->v, p, (j->fr->frame & 1u) == 0 && j->v->cls[p] >= 1, (double)j->v->d.hyst);
             else
                 blend_probe(j->v, p, (j->fr->frame & 1u) == 0 && j->v->cls[p] >= 1, (double)j->v->d.hyst);
     }

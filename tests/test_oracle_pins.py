@@ -1126,3 +1126,51 @@ def test_clip_metropolis_samples_only_inside_vin():
     outside = cls[p] != 2
     assert outside.any() and (~outside).any()
     assert (v.mh_tri()[outside] == -1).all() and (v.mh_tri_neg()[outside] == -1).all()
+
+
+# --------------------------------------------------------------- DDGI cosine-gather blend
+def test_cosine_gather_constant_environment():
+    # sky only (radiance c everywhere, every ray a miss): the c-weighted mean
+    # of a constant is that constant, and the depth moments are those of
+    # depth_max, at every texel after the first frame
+    v = O.OracleVolume((0, 0, 0), (1, 1, 1), (2, 2, 2), rays_avg=64, rays_min=8, rays_max=64, blend_mode=1)
+    v.set_scene(np.zeros((3, 3), np.float32), np.zeros((0, 3), np.int32), np.zeros((0, 3), np.float32))
+    sky = (0.3, 1.2, 2.5)
+    v.update(0, 1, [], sky)
+    irr, dep = v.irr(), v.dep()
+    np.testing.assert_allclose(irr, np.broadcast_to(np.float32(sky).astype(np.float64), irr.shape), rtol=1e-12)
+    dm = v.depth_max
+    np.testing.assert_allclose(dep[..., 0], dm, rtol=1e-12)
+    np.testing.assert_allclose(dep[..., 1], dm * dm, rtol=1e-12)
+    assert (v.irr_n() > 16).all()  # about half of the 64 rays face each texel
+
+
+def test_cosine_gather_half_space_closed_form():
+    # a probe high above an infinite black floor under a sky of radiance c:
+    # the cosine-weighted share of the hemisphere around n that sees the sky
+    # is (1 + n_z)/2, so the irradiance texel at n holds c (1 + n_z)/2; a
+    # downward depth texel (the sharp c^50 lobe) holds about h / |n_z|
+    h = 3.0
+    big = 1e4
+    verts = np.array([[-big, -big, 0], [big, -big, 0], [big, big, 0], [-big, big, 0]], np.float32)
+    idx = np.array([[0, 1, 2], [0, 2, 3]], np.int32)
+    v = O.OracleVolume((0, 0, h), (0.5, 0.5, 0.5), (2, 2, 2), rays_avg=1024, rays_min=1024, rays_max=1024,
+                       depth_max=100.0, blend_mode=1, hysteresis=0.0)
+    v.set_scene(verts, idx, np.zeros((2, 3), np.float32))
+    c = 2.0
+    v.update(1, 5, [], (c, c, c))  # an odd frame: no pilots, the 1016 spherical-Fibonacci rays alone
+    irr = v.irr()[0]  # probe 0 at (0, 0, 3)
+    dep = v.dep()[0]
+    n = 6
+    for cy in range(n):
+        for cx in range(n):
+            nt = O.oct_decode([((cx + 0.5) / n) * 2 - 1, ((cy + 0.5) / n) * 2 - 1])
+            np.testing.assert_allclose(irr[cy + 1, cx + 1], c * (1 + nt[2]) / 2, atol=0.02 * c)
+    nd = 14
+    for cy in range(nd):
+        for cx in range(nd):
+            nt = O.oct_decode([((cx + 0.5) / nd) * 2 - 1, ((cy + 0.5) / nd) * 2 - 1])
+            if nt[2] < -0.9:  # the lobe's spread (~1/sqrt(50) rad) biases h / |n_z| upward by ~1-2 %
+                assert abs(dep[cy + 1, cx + 1, 0] / (h / -nt[2]) - 1) < 0.03
+            elif nt[2] > 0.6:  # sky: misses at depth_max (floor rays are >= 37 deg off the lobe: weight < 2e-5)
+                assert abs(dep[cy + 1, cx + 1, 0] / v.depth_max - 1) < 1e-3
