@@ -515,6 +515,42 @@ def _metropolis_section(args, adgi, torch, dev):
     return out
 
 
+def _cosine_section(args, adgi, torch, dev):
+    """The same workload with DDGI's cosine-gather blend (blend_mode = 1):
+    every ray feeds every texel of its hemisphere (ALU-bound), timed like
+    the headline line."""
+    w = _workload(args.workload, args.seed)
+    vd = dict(w.volume)
+    vd["blend_mode"] = 1
+    stream = torch.cuda.Stream(device=dev)
+    v = adgi.Volume(stream=stream.cuda_stream, **vd)
+    v.set_scene(w.verts, w.idx, w.albedo)
+    adgi.adgi_enable_timing(v.h, True)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    have_dyn = w.dyn_at is not None and w.dyn_count > 0
+    warm, steps = 3, max(4, min(args.steps, 30))
+    ms, blend = [], []
+    for f in range(warm + steps):
+        if have_dyn:
+            v.move_vertices(w.dyn_first, np.ascontiguousarray(w.dyn_at(f), np.float32))
+        with torch.cuda.stream(stream):
+            flush.fill_(float(f))
+        v.update(f, w.seed, w.lights_at(f), w.sky)
+        st = v.stats()
+        if f >= warm:
+            ms.append(st.ms_last_update)
+            blend.append(st.ms_phase[7])
+    m = float(np.mean(ms))
+    # (texel, ray) pairs per update: every interior texel of both tiles meets every ray of its probe
+    texels = vd["irr_interior"] ** 2 + vd["depth_interior"] ** 2
+    pairs = texels * (w.rays_per_update - 8 * w.n_probes // 2)  # pilots count on every other frame
+    out = {"workload": w.name, "ms_per_update": m, "rays_per_s": w.rays_per_update / (m / 1e3),
+           "blend_ms": float(np.mean(blend)), "texel_ray_pairs_per_update": pairs,
+           "texel_ray_pairs_per_s": pairs / (float(np.mean(blend)) / 1e3), "frames_timed": steps}
+    v.close()
+    return out
+
+
 def _metropolis_run(args, adgi, torch, dev, dyn_ratio):
     w = _workload(args.workload, args.seed)
     vd = dict(w.volume)
@@ -738,6 +774,9 @@ def run_ours(args):
     metropolis = None
     if rank == 0 and not args.no_metropolis and not args.sampler:
         metropolis = _metropolis_section(args, adgi, torch, dev)
+    cosine = None
+    if rank == 0 and not args.no_metropolis and not args.sampler:
+        cosine = _cosine_section(args, adgi, torch, dev)
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         times, cores = _cpu_baseline(w, budget_s=args.cpu_budget, sampler=int(args.sampler), alpha=args.alpha)
@@ -770,6 +809,7 @@ def run_ours(args):
             "serving": serving,
             "precision": precision,
             "metropolis": metropolis,
+            "cosine_gather": cosine,
             "gpu_launches": int(launches),
             "clocks": clk,
             "wall_s": wall,

@@ -102,6 +102,12 @@ typedef struct {
                                0: off.  <= 1024 */
     float hysteresis_dyn;   /* dyn_ratio > 0: hysteresis of the dynamic rays' batch step, applied after
                                the static samples' (Table cacheDetails: 0.91), in [0, 1) */
+    int32_t blend_mode;     /* 0: nearest texel (Alg. ApproxAlgo).  1: DDGI's cosine gather (Sec. 3.1):
+                               every ray feeds every texel of its hemisphere, the irradiance texel at
+                               centre direction n taking the (n . w)-weighted mean radiance over
+                               n . w > 0 (tested in FP32), the visibility texel the (n . w)^50-weighted
+                               mean of {d, d^2}; the number of rays with n . w > 0 is the batch count
+                               of the moving average.  Only with sampler = 0 and atlas_fp16 < 3 */
 } adgi_volume_desc;
 
 /* kind 0: point light at pos_or_dir with intensity rgb (irradiance rgb/d^2);

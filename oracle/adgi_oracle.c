@@ -2478,13 +2478,16 @@ static void mh_blend_probe(orc_vol* v, int p, int use_pilots, double h)
 
 /* DDGI's cosine-gather blend (Sec. 3.1; the variant of the texel update):
    every ray of the probe contributes to every texel of its hemisphere.  For
-   interior texel t with centre direction n_t (the octahedral decode of the
-   texel centre) and ray r of direction w_r, c = n_t . w_r: the irradiance
+   interior texel t with centre direction n_t (the FP32 decode of the texel
+   centre, as the dynamic rays') and ray r of direction w_r, c = n_t . w_r
+   (the test c > 0 in FP32, ((x x' + y y') + z z'); the weights in FP64,
+   at least 0): the irradiance
    texel takes the c-weighted mean of the rays' radiance over c > 0, the
    visibility texel the c^50-weighted mean of {d, d^2} (DDGI's depth
    sharpness 50); k = the number of rays with c > 0 enters the batched
    moving average as the sample count (w = max(1 - h, k/(n + k))). */
 #define COS_DEPTH_SHARPNESS 50
+static void texel_centre_dir(int cx, int cy, int n, float w[3]);
 static void blend_probe_cos(orc_vol* v, int p, int use_pilots, double h)
 {
     const int Ti = v->Ti, Td = v->Td, ni = v->d.n_irr, nd = v->d.n_dep;
@@ -2524,19 +2527,30 @@ static void blend_probe_cos(orc_vol* v, int p, int use_pilots, double h)
         for (int cy = 0; cy < n; ++cy)
             for (int cx = 0; cx < n; ++cx) {
                 const int t = (cy + 1) * T + (cx + 1);
-                double uv[2] = {((cx + 0.5) / n) * 2.0 - 1.0, ((cy + 0.5) / n) * 2.0 - 1.0}, nt[3];
-                orc_oct_decode(uv, nt);
-                double sw = 0.0, acc[3] = {0.0, 0.0, 0.0};
+                float nt[3];
+                texel_centre_dir(cx, cy, n, nt);
+                double sw = 0.0, acc[3] = {0.0, 0.0, 0.0}, cmax = 0.0;
                 int k = 0;
+                if (pass) /* the depth weights relative to the largest c: the same mean, no underflow */
+                    for (int j = 0; j < total; ++j) {
+                        const float c32 = (nt[0] * (float)dirs[j * 3] + nt[1] * (float)dirs[j * 3 + 1]) +
+                                          nt[2] * (float)dirs[j * 3 + 2];
+                        double c = (double)nt[0] * dirs[j * 3] + (double)nt[1] * dirs[j * 3 + 1] +
+                                   (double)nt[2] * dirs[j * 3 + 2];
+                        if (c32 > 0.0f && c > cmax) cmax = c;
+                    }
                 for (int j = 0; j < total; ++j) {
-                    double c = nt[0] * dirs[j * 3] + nt[1] * dirs[j * 3 + 1] + nt[2] * dirs[j * 3 + 2];
-                    if (!(c > 0.0)) continue;
+                    const float c32 = (nt[0] * (float)dirs[j * 3] + nt[1] * (float)dirs[j * 3 + 1]) +
+                                      nt[2] * (float)dirs[j * 3 + 2];
+                    if (!(c32 > 0.0f)) continue;
                     ++k;
+                    double c = (double)nt[0] * dirs[j * 3] + (double)nt[1] * dirs[j * 3 + 1] + (double)nt[2] * dirs[j * 3 + 2];
+                    if (c < 0.0) c = 0.0;
                     if (!pass) {
                         sw += c;
                         for (int q = 0; q < 3; ++q) acc[q] += c * rads[j][q];
                     } else {
-                        double wgt = pow(c, COS_DEPTH_SHARPNESS);
+                        double wgt = cmax > 0.0 ? pow(c / cmax, COS_DEPTH_SHARPNESS) : 1.0;
                         sw += wgt;
                         acc[0] += wgt * deps[j];
                         acc[1] += wgt * deps[j] * deps[j];

@@ -47,6 +47,7 @@ class adgi_volume_desc(C.Structure):
         ("alpha", C.c_float),
         ("dyn_ratio", C.c_int32),
         ("hysteresis_dyn", C.c_float),
+        ("blend_mode", C.c_int32),
     ]
 
 
@@ -397,7 +398,7 @@ def adgi_last_error() -> str:
 # ------------------------------------------------------------ convenience
 def make_desc(origin, spacing, dims, irr_interior=6, depth_interior=14, rays_avg=64, rays_min=8, rays_max=256,
               hysteresis=0.97, depth_max=0.0, atlas_fp16=0, tr_theta=16, sampler=0,
-              alpha=1.0, dyn_ratio=0, hysteresis_dyn=0.91) -> adgi_volume_desc:
+              alpha=1.0, dyn_ratio=0, hysteresis_dyn=0.91, blend_mode=0) -> adgi_volume_desc:
     d = adgi_volume_desc()
     d.origin[:] = [float(x) for x in origin]
     d.spacing[:] = [float(x) for x in spacing]
@@ -412,6 +413,7 @@ def make_desc(origin, spacing, dims, irr_interior=6, depth_interior=14, rays_avg
     d.alpha = float(alpha)
     d.dyn_ratio = int(dyn_ratio)
     d.hysteresis_dyn = float(hysteresis_dyn)
+    d.blend_mode = int(blend_mode)
     return d
 
 

@@ -202,6 +202,29 @@ __device__ __forceinline__ float2 oct_encode_x(float3 w)
     return make_float2(px, py);
 }
 
+// unit direction of octahedral coordinates (ux, uy), exact FP32
+__device__ __forceinline__ float3 oct_decode_x(float ux, float uy)
+{
+    float x = ux, y = uy;
+    const float z = fs(fs(1.0f, fabsf(x)), fabsf(y));
+    if (z < 0.0f) {
+        const float fx = fm(fs(1.0f, fabsf(uy)), sgnf(ux));
+        const float fy = fm(fs(1.0f, fabsf(ux)), sgnf(uy));
+        x = fx;
+        y = fy;
+    }
+    const float l = fsq(dot3x(x, y, z, x, y, z));
+    return make_float3(fd(x, l), fd(y, l), fd(z, l));
+}
+
+// direction through the centre of interior texel (cx, cy) of an n x n
+// octahedral grid: u = (c + 1/2)/n * 2 - 1 per axis, FP32 in that order
+__device__ __forceinline__ float3 texel_centre_dir(int cx, int cy, int n)
+{
+    const float fn = (float)n;
+    return oct_decode_x(fs(fm(fd(fa((float)cx, 0.5f), fn), 2.0f), 1.0f), fs(fm(fd(fa((float)cy, 0.5f), fn), 2.0f), 1.0f));
+}
+
 // nearest interior texel, as row*(n+2)+col with both in 1..n
 __device__ __forceinline__ int texel_of(float2 p, int n)
 {

@@ -365,6 +365,8 @@ int validate_desc(const adgi_volume_desc* d)
         return fail(ADGI_ERR_INVALID_ARG, "dyn_ratio in [0, 1024], and > 0 only with sampler = 1");
     if (d->dyn_ratio > 0 && !(d->hysteresis_dyn >= 0.0f && d->hysteresis_dyn < 1.0f))
         return fail(ADGI_ERR_INVALID_ARG, "hysteresis_dyn in [0,1)");
+    if (d->blend_mode < 0 || d->blend_mode > 1 || (d->blend_mode == 1 && (d->sampler != 0 || d->atlas_fp16 == 3)))
+        return fail(ADGI_ERR_INVALID_ARG, "blend_mode in {0,1}; the cosine gather needs sampler 0 and atlas_fp16 < 3");
     int64_t P = (int64_t)d->dims[0] * d->dims[1] * d->dims[2];
     if (P * (int64_t)d->rays_avg >= (int64_t)1 << 31) return fail(ADGI_ERR_INVALID_ARG, "ray budget too large");
     return ADGI_OK;
@@ -974,8 +976,8 @@ int enqueue_update(adgi_volume v, const FrameDev& fd, cudaStream_t s, bool phase
     // stream, beside the traversals, and join before the blend
     BlendBufs Bb{v->off,  v->sf,  v->pil_rec, v->m_rec,
                  v->irr,  v->dep, v->dep_n,   carve_blend_plan(v->plan, V.rays_max - 8, V.Ti, V.Td), v->tex_src};
-    const bool mh = v->desc.sampler == 1;
-    if (!mh) {
+    const bool mh = v->desc.sampler == 1, cosg = v->desc.blend_mode == 1;
+    if (!mh && !cosg) {
         CK(cudaEventRecord(v->fork, s));
         CK(cudaStreamWaitEvent(v->side, v->fork, 0));
         if (phases) CK(cudaEventRecord(v->plq[0], v->side));
@@ -1041,8 +1043,12 @@ int enqueue_update(adgi_volume v, const FrameDev& fd, cudaStream_t s, bool phase
                         phases ? v->shq + 2 : nullptr));
         // 6. blend (after every read of the previous atlases)
         PHASE(7);
-        CK(cudaStreamWaitEvent(s, v->join, 0));
-        CK(launch_blend(V, FD, Bb, T, s));
+        if (cosg) {
+            CK(launch_blend_cos(V, FD, Bb, T, s));
+        } else {
+            CK(cudaStreamWaitEvent(s, v->join, 0));
+            CK(launch_blend(V, FD, Bb, T, s));
+        }
     }
     PHASE(8);
 #undef PHASE
@@ -1273,7 +1279,8 @@ int adgi_autotune(adgi_volume v, const adgi_frame* f, int32_t reps, adgi_tuning*
 {
     if (!v || !f) return fail(ADGI_ERR_INVALID_ARG, "NULL argument");
     if (v->frames == 0) return fail(ADGI_ERR_INVALID_ARG, "autotune needs one update first");
-    if (v->desc.sampler == 1) return fail(ADGI_ERR_INVALID_ARG, "autotune: not available with the Metropolis sampler");
+    if (v->desc.sampler == 1 || v->desc.blend_mode == 1)
+        return fail(ADGI_ERR_INVALID_ARG, "autotune: not available with the Metropolis sampler or the cosine gather");
     if (reps < 1) reps = 1;
     FrameDev fd;
     int rc = prepare_update(v, f, fd, nullptr);
@@ -1433,7 +1440,8 @@ int adgi_get_stats(adgi_volume v, adgi_stats* out)
         out->ms_last_update = ms;
         for (int i = 0; i < 8; ++i) CK(cudaEventElapsedTime(&out->ms_phase[i], v->ph[i], v->ph[i + 1]));
         for (int i = 0; i < 2; ++i) CK(cudaEventElapsedTime(&out->ms_shadow[i], v->shq[2 * i], v->shq[2 * i + 1]));
-        if (v->desc.sampler != 1) CK(cudaEventElapsedTime(&out->ms_blend_plan, v->plq[0], v->plq[1]));
+        if (v->desc.sampler != 1 && v->desc.blend_mode != 1)
+            CK(cudaEventElapsedTime(&out->ms_blend_plan, v->plq[0], v->plq[1]));
     }
     return ADGI_OK;
 }

@@ -212,6 +212,8 @@ cudaError_t launch_blend_plan(const VolConst& V, const FrameDev* FD, const float
                               cudaStream_t s);
 // the tiles (after the plan and every read of the previous atlases)
 cudaError_t launch_blend(const VolConst& V, const FrameDev* FD, const BlendBufs& B, const Tuning& T, cudaStream_t s);
+// the DDGI cosine-gather variant of the blend (blend_mode = 1; no plan needed)
+cudaError_t launch_blend_cos(const VolConst& V, const FrameDev* FD, const BlendBufs& B, const Tuning& T, cudaStream_t s);
 cudaError_t launch_query(const VolConst& V, const void* irr, const void* dep, const float* pos, const float* nrm, int n,
                          float* out, cudaStream_t s);
 

@@ -839,6 +839,163 @@ __global__ void __launch_bounds__(128) k_blend(VolConst V, const FrameDev* __res
     store_tiles(V, F, B.irr, B.dep, B.dep_n, B.src, p, irr_new, dep_new, dn_new, lane);
 }
 
+// ---- DDGI cosine gather (blend_mode = 1, Sec. 3.1): every ray of the probe
+// feeds every texel of its hemisphere.  Texel t with centre direction n_t
+// (FP32 decode of the texel centre) and ray direction w, c = n_t . w: the
+// test c > 0 is exact FP32 ((x x' + y y') + z z'), the irradiance texel
+// takes the c-weighted mean radiance, the visibility texel the c^50-weighted
+// mean of {d, d^2} (weights taken relative to the texel's largest c); the number of rays with c > 0 is the batch count of the
+// moving average.  One warp per probe; rays are staged 32 at a time in
+// shared memory; each lane holds 4 texels per pass over the rays (one pass
+// for the irradiance tile, two for the 14 x 14 depth interior).
+constexpr int kCosPer = 4;
+
+struct CosLayout {
+    uint32_t ray_d, ray_r, irr_new, dep_new, dn_new, total;
+};
+
+__host__ __device__ inline CosLayout cos_layout(int Ti, int Td)
+{
+    const uint32_t ti2 = (uint32_t)(Ti * Ti), td2 = (uint32_t)(Td * Td);
+    CosLayout L;
+    uint32_t o = 0;
+    L.ray_d = o, o += 16 * 32;  // a chunk of ray directions
+    L.ray_r = o, o += 16 * 32;  // and records {r, g, b, depth}
+    L.irr_new = o, o += al16(16 * ti2);
+    L.dep_new = o, o += al16(8 * td2);
+    L.dn_new = o, o += al16(td2);
+    L.total = o;
+    return L;
+}
+
+__device__ __forceinline__ float pow50(float c)
+{
+    const float c2 = c * c, c4 = c2 * c2, c8 = c4 * c4, c16 = c8 * c8, c32 = c16 * c16;
+    return c32 * c16 * c2;
+}
+
+__global__ void __launch_bounds__(128) k_blend_cos(VolConst V, const FrameDev* __restrict__ FD, BlendBufs B)
+{
+    const FrameConst& F = FD->F;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int p = blockIdx.x * (blockDim.x >> 5) + wib;
+    if (p >= V.P) return;  // the whole warp
+    const uint32_t base = __ldg(B.off + p);
+    uint32_t m = __ldg(B.off + p + 1) - base;
+    if (m > (uint32_t)(V.rays_max - kPilots) || base > V.R_main || m > V.R_main - base) {
+        if (lane == 0) atomicOr(V.err, kErrRayRange);
+        m = 0;
+    }
+    const uint8_t cl = V.cls[p];
+    const int npil = (F.even && cl >= 1) ? kPilots : 0;
+    if ((int)m + npil == 0 && cl != 1) return;  // untouched tile
+    const int Ti = V.Ti, Td = V.Td, ni = V.n_irr, nd = V.n_dep;
+    const CosLayout L = cos_layout(Ti, Td);
+    unsigned char* ws = smem + (size_t)wib * L.total;
+    float4* rd = reinterpret_cast<float4*>(ws + L.ray_d);
+    float4* rr = reinterpret_cast<float4*>(ws + L.ray_r);
+    float4* irr_new = reinterpret_cast<float4*>(ws + L.irr_new);
+    float2* dep_new = reinterpret_cast<float2*>(ws + L.dep_new);
+    uint8_t* dn_new = ws + L.dn_new;
+    const size_t io = (size_t)p * Ti * Ti, dof = (size_t)p * Td * Td;
+    const float4* sfrow = B.sf + (m ? (size_t)m * (m - 1) / 2 : 0);
+    const float4* mrec = B.main_rec + base;
+    const int nrays = npil + (int)m;
+    const float omh = 1.0f - V.hyst;
+    // passes: 0 the irradiance interior, then the depth interior in groups of 32 * kCosPer texels
+    const int ngi = (ni * ni + 32 * kCosPer - 1) / (32 * kCosPer), ngd = (nd * nd + 32 * kCosPer - 1) / (32 * kCosPer);
+    for (int pass = 0; pass < ngi + ngd; ++pass) {
+        const bool depth = pass >= ngi;
+        const int n = depth ? nd : ni, g = depth ? pass - ngi : pass;
+        float3 nt[kCosPer];
+        float s0[kCosPer], s1[kCosPer], s2[kCosPer], sw[kCosPer], cm[kCosPer];
+        uint32_t k[kCosPer];
+#pragma unroll
+        for (int j = 0; j < kCosPer; ++j) {
+            const int q = (g * kCosPer + j) * 32 + lane;
+            nt[j] = q < n * n ? texel_centre_dir(q % n, q / n, n) : make_float3(0.f, 0.f, 0.f);
+            s0[j] = s1[j] = s2[j] = sw[j] = cm[j] = 0.f;
+            k[j] = 0u;
+        }
+        for (int c0 = 0; c0 < nrays; c0 += 32) {
+            const int j = c0 + lane;
+            if (j < nrays) {
+                float3 d;
+                float4 r;
+                if (j < npil) {
+                    d = pilot_dir(F.pilot_key, (uint32_t)p, j);
+                    r = __ldg(B.pil_rec + (size_t)p * kPilots + j);
+                } else {
+                    const float4 sfp = __ldg(sfrow + (j - npil));
+                    const uint32_t i = min((uint32_t)__float_as_int(sfp.w), m - 1);
+                    d = rotate(F.R, sfp);
+                    r = __ldg(mrec + i);
+                }
+                rd[lane] = make_float4(d.x, d.y, d.z, 0.f);
+                rr[lane] = r;
+            }
+            __syncwarp();
+            const int cnt = min(32, nrays - c0);
+            for (int u = 0; u < cnt; ++u) {
+                const float4 d = rd[u], r = rr[u];
+#pragma unroll
+                for (int jj = 0; jj < kCosPer; ++jj) {
+                    const float c = dot3x(nt[jj].x, nt[jj].y, nt[jj].z, d.x, d.y, d.z);
+                    if (c > 0.0f) {
+                        k[jj] += 1u;
+                        if (!depth) {
+                            sw[jj] += c;
+                            s0[jj] = fmaf(c, r.x, s0[jj]);
+                            s1[jj] = fmaf(c, r.y, s1[jj]);
+                            s2[jj] = fmaf(c, r.z, s2[jj]);
+                        } else {
+                            // weights (c / c_max)^50 relative to the largest c so far (the
+                            // mean is scale-free; c^50 itself underflows FP32 at grazing c):
+                            // a new maximum rescales the running sums
+                            if (c > cm[jj]) {
+                                const float sc = cm[jj] > 0.0f ? pow50(cm[jj] / c) : 0.0f;
+                                sw[jj] *= sc;
+                                s0[jj] *= sc;
+                                s1[jj] *= sc;
+                                cm[jj] = c;
+                            }
+                            const float wgt = pow50(c / cm[jj]);
+                            sw[jj] += wgt;
+                            s0[jj] = fmaf(wgt, r.w, s0[jj]);
+                            s1[jj] = fmaf(wgt * r.w, r.w, s1[jj]);
+                        }
+                    }
+                }
+            }
+            __syncwarp();
+        }
+#pragma unroll
+        for (int j = 0; j < kCosPer; ++j) {
+            const int q = (g * kCosPer + j) * 32 + lane;
+            if (q >= n * n) continue;
+            const int row = q / n, t = (row + 1) * (n + 2) + (q - row * n) + 1;
+            const bool ok = k[j] > 0u && sw[j] > 0.0f;
+            const float kf = (float)k[j], inv = ok ? kf / sw[j] : 0.0f;  // sums of the k-sample batch: mean * k
+            if (!depth) {
+                float4 v = irr_load(V, B.irr, io + t);
+                if (ok) v = irr_texel_blend(v, s0[j] * inv, s1[j] * inv, s2[j] * inv, k[j], omh);
+                if (cl == 1) v.w = fminf(v.w, 16.0f);
+                irr_new[t] = v;
+            } else {
+                float2 v = dep_load(V, B.dep, dof + t);
+                uint32_t c = B.dep_n[dof + t];
+                if (ok) v = dep_texel_blend(v, c, s0[j] * inv, s1[j] * inv, k[j], omh);
+                if (cl == 1) c = min(c, 16u);
+                dep_new[t] = v;
+                dn_new[t] = (uint8_t)c;
+            }
+        }
+    }
+    __syncwarp();
+    store_tiles(V, F, B.irr, B.dep, B.dep_n, B.src, p, irr_new, dep_new, dn_new, lane);
+}
+
 // ---- Metropolis samples (sampler.cu): one warp per probe tile.  The
 // samples of probe p are contiguous in grouped order (sample order inside the
 // probe).  Sample s adds its +w radiance to the irradiance texel of w and the
@@ -1137,6 +1294,21 @@ cudaError_t launch_blend(const VolConst& V, const FrameDev* FD, const BlendBufs&
         if (e != cudaSuccess) return e;
     }
     k_blend<<<(V.P + wpb - 1) / wpb, 32 * wpb, sm, s>>>(V, FD, B);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_blend_cos(const VolConst& V, const FrameDev* FD, const BlendBufs& B, const Tuning& T, cudaStream_t s)
+{
+    (void)T;
+    const size_t per = cos_layout(V.Ti, V.Td).total;
+    const int wpb = std::max(1, std::min(4, (int)((227u * 1024u) / per)));
+    const size_t sm = per * (size_t)wpb;
+    if (sm > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_blend_cos, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+    }
+    k_blend_cos<<<(V.P + wpb - 1) / wpb, 32 * wpb, sm, s>>>(V, FD, B);
     count_launches(1);
     return cudaGetLastError();
 }
