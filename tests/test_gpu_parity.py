@@ -235,7 +235,8 @@ def test_update_small_city_ragged(adgi):
     gv.close()
 
 
-@pytest.mark.parametrize("case", ["pilots_only", "uniform_forced", "empty_scene", "theta1_camera", "minimal_grid"])
+@pytest.mark.parametrize("case", ["pilots_only", "uniform_forced", "empty_scene", "theta1_camera", "minimal_grid",
+                                  "tiles_8_16", "tiles_5_9", "tiles_1_1"])
 def test_update_edge_cases(adgi, case):
     w = S.box_room(2)
     over = {}
@@ -252,6 +253,12 @@ def test_update_edge_cases(adgi, case):
         cam = ((2.0, 3.0, 2.5), 1.5)
     elif case == "minimal_grid":
         over = dict(dims=(2, 2, 2), spacing=(4.0, 4.0, 4.0), rays_avg=100, rays_max=300)
+    elif case == "tiles_8_16":  # the 8 x 8 / 16 x 16 interiors of the DDGI paper
+        over = dict(irr_interior=8, depth_interior=16)
+    elif case == "tiles_5_9":  # odd tiles, and texel runs split across 32-sample passes
+        over = dict(irr_interior=5, depth_interior=9, rays_avg=120, rays_max=300)
+    elif case == "tiles_1_1":  # one texel per tile: every sample in one run, counts above 255
+        over = dict(irr_interior=1, depth_interior=1, rays_avg=290, rays_min=290, rays_max=300)
     gv = gpu_volume(adgi, w, **over)
     ov = oracle_volume(O, w, **over)
     for f in range(4):
