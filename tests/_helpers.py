@@ -7,12 +7,23 @@ Tolerances (FP32 GPU path vs FP64 oracle):
   * irradiance texels: |a - b| <= 1e-3 * max(|b|, 1e-3 * mean|b|);
   * depth moments:     |a - b| <= 1e-4 * max(|b|, 1e-3 * mean|b|).
 """
+import os
+import tempfile
+
 import numpy as np
 
 from oracle import oracle as O
 
 IRR_RTOL = 1e-3
 DEP_RTOL = 1e-4
+
+
+def diag_path(name):
+    """where a test writes a diagnostic file (measured errors, failing
+    rays): the folder named by ADGI_DIAG_DIR, else a temporary folder"""
+    d = os.environ.get("ADGI_DIAG_DIR") or os.path.join(tempfile.gettempdir(), "adgi_diag")
+    os.makedirs(d, exist_ok=True)
+    return os.path.join(d, name)
 
 
 def oracle_volume(O, w, **over):

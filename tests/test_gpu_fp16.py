@@ -4,10 +4,10 @@ The paper fixes no FP16 behaviour, so this parity is unpinned: the test
 checks that everything the atlas does not feed stays bit-exact (allocation,
 heuristics, hits) and that the atlas and query errors stay within the bounds
 measured for round-to-nearest and stochastic-rounding storage.  The measured
-errors are written to gpurun_out/fp16_errors.json.
+errors are written to fp16_errors.json in the diagnostics folder
+(ADGI_DIAG_DIR).
 """
 import json
-import os
 
 import numpy as np
 import pytest
@@ -15,7 +15,7 @@ import pytest
 from oracle import oracle as O
 from paper_2301_05125_gb300 import scenegen as S
 
-from _helpers import gpu_volume, oracle_volume
+from _helpers import diag_path, gpu_volume, oracle_volume
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -74,8 +74,7 @@ def test_fp16_atlases(adgi, mode, scene):
     eq = _rel_err(gv.query(pos, nrm), ov.query(pos, nrm))
     RESULTS["%s_mode%d" % (scene, mode)] = {"irr_max": ei[0], "irr_mean": ei[1], "dep_max": ed[0], "dep_mean": ed[1],
                                             "query_max": eq[0], "query_mean": eq[1], "frames": frames}
-    os.makedirs("gpurun_out", exist_ok=True)
-    json.dump(RESULTS, open("gpurun_out/fp16_errors.json", "w"), indent=1)
+    json.dump(RESULTS, open(diag_path("fp16_errors.json"), "w"), indent=1)
     gv.close()
     # half has 11 significant bits (relative spacing 2^-10 ~ 1e-3).  Measured
     # on a GB300 over 8 frames: means 1-4e-4, maxima 2-4e-3 (atlases) and

@@ -10,7 +10,7 @@ import pytest
 from oracle import oracle as O
 from paper_2301_05125_gb300 import scenegen as S
 
-from _helpers import DEP_RTOL, IRR_RTOL, gpu_volume, oracle_volume, rel_check
+from _helpers import DEP_RTOL, IRR_RTOL, diag_path, gpu_volume, oracle_volume, rel_check
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -29,12 +29,9 @@ def adgi():
 
 
 def _dump_rays(gv, ov, frame, what):
-    import os
-
     def dump(rows):
-        os.makedirs("gpurun_out", exist_ok=True)
         R = int(ov.off()[-1])
-        np.savez("gpurun_out/fail_%s_f%d.npz" % (what.replace(" ", "_"), frame), rows=rows[:64],
+        np.savez(diag_path("fail_%s_f%d.npz" % (what.replace(" ", "_"), frame)), rows=rows[:64],
                  gpu_rec=gv.main_rec()[:R][rows[:64]], ora_rad=ov.main_rad()[rows[:64]],
                  ora_dep=ov.main_dep()[rows[:64]], tri=ov.main_tri()[rows[:64]], t=ov.main_t()[rows[:64]],
                  off=ov.off(), n=ov.n())
