@@ -36,21 +36,19 @@ struct __align__(16) BNode {
     int4 d;    // left, right, -, -
 };
 
-// One BVH over a subset of the scene's triangles.
-struct SubBvh {
-    int n_tris;
-    int root_leaf;          // n_tris == 1: the single triangle slot
-    const float4* tri_v;    // [n_tris*3] vertices in BVH order, .w of v0 = original index
-    const BNode* nodes;     // [n_tris-1]
-    int max_iter;           // traversal step limit (a correct tree needs < n_tris steps)
-};
-
 // The scene: a static part (quality BVH, built once) and a moving part
-// (linear BVH, rebuilt when vertices move).  Hits are ranked over both by
-// (t, original triangle index).
+// (linear BVH, rebuilt when vertices move), in one node array and one
+// triangle array.  The static part's ns triangles occupy slots [0, ns) and
+// its internal nodes [0, ns-1); the moving part's triangles follow at slot
+// ns and its nodes at node max(ns-1, 0), with child references relocated
+// to these global indices, so a traversal needs no per-part pointers.  Hits
+// are ranked over both by (t, original triangle index).
 struct SceneDev {
-    SubBvh part[2];
-    int n_parts;
+    const BNode* nodes;     // internal nodes of both parts
+    const float4* tri_v;    // both parts' triangles in BVH order, .w of v0 = original index
+    int root[2];            // root node of each part's tree (-1: fewer than two triangles)
+    int leaf[2];            // slot of a part's only triangle (-1: none, or a tree)
+    int max_iter;           // traversal step limit (a correct tree needs fewer node visits)
     int n_tris;
     int n_verts;
     const float4* tri_orig; // [n_tris*3] vertices in original order (shading normal)
@@ -327,10 +325,9 @@ constexpr float kBoxSlack = 1.0001f;  // pruning slack on the best t (conservati
 constexpr int kMaxDepth = 96;
 constexpr int kStack = kMaxDepth;
 
-// Traversal of the two-part scene as one flat loop over one stack: an entry
-// is an internal node of part 0 (bit 30 clear) or part 1 (bit 30 set).  The
-// loop has no early exit, so the lanes of a warp reconverge every iteration.
-constexpr int kPartBit = 1 << 30;
+// Traversal of the two-part scene as one flat loop over one stack of
+// global node indices.  The loop has no early exit, so the lanes of a warp
+// reconverge every iteration.
 
 // One traversal in flight.  Closest hit: t in (tmin, tmax], ranked by
 // (t, original index) -- a strict order, so the result does not depend on
@@ -416,12 +413,11 @@ __device__ __forceinline__ void trav_init(Trav& T, int* stack, const SceneDev& S
     T.iter = 0;
     if (S.n_tris == 0) return;
     for (int pi = 1; pi >= 0; --pi) {
-        const int nt = pi ? S.part[1].n_tris : S.part[0].n_tris;
-        const int rl = pi ? S.part[1].root_leaf : S.part[0].root_leaf;
-        if (nt >= 2)
-            stack[T.sp++] = pi ? kPartBit : 0;
-        else if (nt == 1)
-            trav_tri(T, (pi ? S.part[1].tri_v : S.part[0].tri_v) + 3 * (size_t)rl, any, ntri);
+        const int root = pi ? S.root[1] : S.root[0], leaf = pi ? S.leaf[1] : S.leaf[0];
+        if (root >= 0)
+            stack[T.sp++] = root;
+        else if (leaf >= 0)
+            trav_tri(T, S.tri_v + 3 * (size_t)leaf, any, ntri);
     }
     if (any && T.found) T.sp = 0;
 }
@@ -431,7 +427,7 @@ __device__ __forceinline__ bool trav_step(Trav& T, int* stack, const SceneDev& S
                                           uint32_t* nbox = nullptr, uint32_t* ntri = nullptr)
 {
     if (T.next < 0 && T.sp <= 0) return false;
-    if (++T.iter > S.part[0].max_iter + S.part[1].max_iter) {
+    if (++T.iter > S.max_iter) {
         atomicOr(S.err, kErrTraversal);
         T.sp = 0;
         T.next = -1;
@@ -440,28 +436,26 @@ __device__ __forceinline__ bool trav_step(Trav& T, int* stack, const SceneDev& S
     if (nbox) *nbox += 2;
     const int e = T.next >= 0 ? T.next : stack[--T.sp];
     T.next = -1;
-    const int part = e & kPartBit;
-    const BNode* nd = (part ? S.part[1].nodes : S.part[0].nodes) + (e & ~kPartBit);
-    const float4* tris = part ? S.part[1].tri_v : S.part[0].tri_v;
+    const BNode* nd = S.nodes + e;
     float4 a = __ldg(&nd->a), b = __ldg(&nd->b), c = __ldg(&nd->c);
     int4 ch = __ldg(&nd->d);
     const float lim = any ? T.lim : T.t_best * kBoxSlack;
     float t0, t1;
     const bool h0 = slab_fma(a.x, a.y, a.z, a.w, b.x, b.y, T.inv, T.oi, lim, t0);
     const bool h1 = slab_fma(b.z, b.w, c.x, c.y, c.z, c.w, T.inv, T.oi, lim, t1);
-    if (h0 && ch.x < 0) trav_tri(T, tris + 3 * (size_t)(~ch.x), any, ntri);
-    if (h1 && ch.y < 0) trav_tri(T, tris + 3 * (size_t)(~ch.y), any, ntri);
+    if (h0 && ch.x < 0) trav_tri(T, S.tri_v + 3 * (size_t)(~ch.x), any, ntri);
+    if (h1 && ch.y < 0) trav_tri(T, S.tri_v + 3 * (size_t)(~ch.y), any, ntri);
     const bool i0 = h0 && ch.x >= 0, i1 = h1 && ch.y >= 0;
     if (i0 && i1) {  // the near child next, the far one on the stack
         const bool first0 = t0 <= t1;
         if (T.sp < kStack + 2) {
-            stack[T.sp++] = (first0 ? ch.y : ch.x) | part;
-            T.next = (first0 ? ch.x : ch.y) | part;
+            stack[T.sp++] = first0 ? ch.y : ch.x;
+            T.next = first0 ? ch.x : ch.y;
         } else {
             atomicOr(S.err, kErrTraversal);  // cannot happen: depths are bounded by the builders
         }
     } else if (i0 || i1) {
-        T.next = (i0 ? ch.x : ch.y) | part;
+        T.next = i0 ? ch.x : ch.y;
     }
     if (any && T.found) {  // a blocker ends a shadow ray
         T.sp = 0;

@@ -896,26 +896,38 @@ cudaError_t Bvh::reserve(int nt, bool ploc)
 }
 
 cudaError_t Bvh::build(const float* d_verts, const int* d_idx, int nv, int nt, float eps, int* err, cudaStream_t s,
-                       const int* list, bool ploc)
+                       const int* list, bool ploc, float4* tri_out, BNode* nodes_out)
 {
     n_tris = 0;
     if (nt == 0) return cudaSuccess;
     cudaError_t e = reserve(nt, ploc);  // may reset every member
     if (e != cudaSuccess) return e;
     n_tris = nt;
-    return ploc ? build_ploc(bufs, pbufs, d_verts, d_idx, nv, nt, eps, err, s, &root_leaf, list)
-                : build_lbvh(bufs, d_verts, d_idx, nv, nt, eps, err, s, &root_leaf, list);
+    BvhBufs B = bufs;
+    if (tri_out) B.tri_v = tri_out;
+    if (nodes_out) B.nodes = nodes_out;
+    return ploc ? build_ploc(B, pbufs, d_verts, d_idx, nv, nt, eps, err, s, &root_leaf, list)
+                : build_lbvh(B, d_verts, d_idx, nv, nt, eps, err, s, &root_leaf, list);
 }
 
-SubBvh Bvh::part() const
+namespace {
+__global__ void k_relocate(BNode* __restrict__ nodes, int n, int node_off, int tri_off)
 {
-    SubBvh P;
-    P.n_tris = n_tris;
-    P.root_leaf = root_leaf;
-    P.tri_v = tri_v;
-    P.nodes = nodes;
-    P.max_iter = 2 * n_tris + 16;
-    return P;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int4 d = nodes[i].d;
+    d.x = d.x >= 0 ? d.x + node_off : ~(~d.x + tri_off);
+    d.y = d.y >= 0 ? d.y + node_off : ~(~d.y + tri_off);
+    nodes[i].d = d;
+}
+}  // namespace
+
+cudaError_t relocate_nodes(BNode* nodes, int n_nodes, int node_off, int tri_off, cudaStream_t s)
+{
+    if (n_nodes <= 0 || (node_off == 0 && tri_off == 0)) return cudaSuccess;
+    k_relocate<<<(n_nodes + 255) / 256, 256, 0, s>>>(nodes, n_nodes, node_off, tri_off);
+    count_launches(1);
+    return cudaGetLastError();
 }
 
 }  // namespace adgi

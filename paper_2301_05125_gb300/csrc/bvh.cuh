@@ -49,6 +49,9 @@ cudaError_t split_static_moving(const int* d_idx, const uint8_t* vmoved, int nt,
                                 int* slist, int* dlist, int* ns, int* nd, cudaStream_t s);
 cudaError_t fill_tri_orig(const float* d_verts, const int* d_idx, const int* list, int nv, int nt, float4* tri_orig,
                           cudaStream_t s);
+// add node_off to the internal-node references and tri_off to the triangle
+// slots of n_nodes nodes (a tree built on its own, placed after another)
+cudaError_t relocate_nodes(BNode* nodes, int n_nodes, int node_off, int tri_off, cudaStream_t s);
 
 // A BVH owned by a volume (static part: PLOC; moving part: linear BVH).
 struct Bvh {
@@ -64,11 +67,11 @@ struct Bvh {
     size_t bytes_ = 0;
 
     cudaError_t reserve(int nt, bool ploc);
+    // build into the own tri_v / nodes, or into tri_out / nodes_out when given
     cudaError_t build(const float* d_verts, const int* d_idx, int nv, int nt, float eps, int* err, cudaStream_t s,
-                      const int* list, bool ploc);
+                      const int* list, bool ploc, float4* tri_out = nullptr, BNode* nodes_out = nullptr);
     void release();
     size_t bytes() const;
-    SubBvh part() const;
 };
 
 }  // namespace adgi

@@ -11,6 +11,7 @@
 // Per frame: the pilot hash key of the frame pair and the main-ray rotation (a
 // uniform unit quaternion by rejection from the 4-ball, FP64 -> FP32).
 #include <cmath>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -787,6 +788,23 @@ int adgi_move_vertices(adgi_volume v, int32_t first, int32_t count, const float*
 }
 
 namespace {
+// Where the moving part lives in the static part's arrays (which hold room
+// for every triangle): its nodes from node max(ns-1, 0), its triangles from
+// slot ns.
+int moving_node_off(adgi_volume v) { return v->ns > 1 ? v->ns - 1 : 0; }
+int moving_tri_off(adgi_volume v) { return v->ns; }
+
+// Rebuild the moving part's linear BVH after the static part's nodes and
+// triangles, and relocate its references to those global indices.
+int build_moving(adgi_volume v, cudaStream_t s)
+{
+    const int no = moving_node_off(v), to = moving_tri_off(v);
+    CK(v->dbvh.build(v->verts, v->idx, v->nv, v->nd, v->eps, v->err, s, v->dlist, false,
+                     v->sbvh.tri_v + 3 * (size_t)to, v->sbvh.nodes + no));
+    if (v->nd > 1) CK(relocate_nodes(v->sbvh.nodes + no, v->nd - 1, no, to, s));
+    return ADGI_OK;
+}
+
 // Bring both BVH parts up to date: re-split and rebuild the static part when
 // the moving set grew, rebuild the moving part when its vertices moved.
 int ensure_bvh(adgi_volume v, cudaStream_t s, bool moving_too = true)
@@ -801,7 +819,10 @@ int ensure_bvh(adgi_volume v, cudaStream_t s, bool moving_too = true)
     }
     if (v->dyn_dirty && moving_too) {
         CK(fill_tri_orig(v->verts, v->idx, v->dlist, v->nv, v->nd, v->tri_orig, s));
-        CK(v->dbvh.build(v->verts, v->idx, v->nv, v->nd, v->eps, v->err, s, v->dlist, false));
+        {
+            int rc = build_moving(v, s);
+            if (rc) return rc;
+        }
         v->dyn_dirty = false;
     }
     return ADGI_OK;
@@ -869,9 +890,13 @@ DynBufs dyn_bufs(adgi_volume v)
 SceneDev scene_view(adgi_volume v)
 {
     SceneDev S;
-    S.part[0] = v->sbvh.part();
-    S.part[1] = v->dbvh.part();
-    S.n_parts = 2;
+    S.nodes = v->sbvh.nodes;
+    S.tri_v = v->sbvh.tri_v;
+    S.root[0] = v->ns > 1 ? 0 : -1;
+    S.leaf[0] = v->ns == 1 ? 0 : -1;
+    S.root[1] = v->nd > 1 ? moving_node_off(v) : -1;
+    S.leaf[1] = v->nd == 1 ? moving_tri_off(v) : -1;
+    S.max_iter = 2 * (v->ns + v->nd) + 32;
     S.n_tris = v->nt;
     S.n_verts = v->nv;
     S.tri_orig = v->tri_orig;
@@ -969,7 +994,10 @@ int enqueue_update(adgi_volume v, const FrameDev& fd, cudaStream_t s, bool phase
     // the moving part of the scene: refresh its vertices and rebuild its BVH
     if (v->nd > 0 && (v->dyn_dirty || set_node)) {
         CK(fill_tri_orig(v->verts, v->idx, v->dlist, v->nv, v->nd, v->tri_orig, s));
-        CK(v->dbvh.build(v->verts, v->idx, v->nv, v->nd, v->eps, v->err, s, v->dlist, false));
+        {
+            int rc = build_moving(v, s);
+            if (rc) return rc;
+        }
     }
     if (!set_node) v->dyn_dirty = false;
     // the blend plan needs only the frame descriptor: run it on the side
@@ -1552,8 +1580,8 @@ int adgi_read_state(adgi_volume v, int32_t which, void* dst, uint64_t bytes)
     case ADGI_STATE_DEP_N: src = v->dep_n; break;
     case ADGI_STATE_BVH_NODES: src = v->sbvh.nodes; count_tris = v->ns; break;
     case ADGI_STATE_BVH_TRIS: src = v->sbvh.tri_v; count_tris = v->ns; break;
-    case ADGI_STATE_MOVING_BVH_NODES: src = v->dbvh.nodes; count_tris = v->nd; break;
-    case ADGI_STATE_MOVING_BVH_TRIS: src = v->dbvh.tri_v; count_tris = v->nd; break;
+    case ADGI_STATE_MOVING_BVH_NODES: src = v->sbvh.nodes + moving_node_off(v); count_tris = v->nd; break;
+    case ADGI_STATE_MOVING_BVH_TRIS: src = v->sbvh.tri_v + 3 * (size_t)moving_tri_off(v); count_tris = v->nd; break;
     case ADGI_STATE_MH_CHAINS: src = v->mh_chain; break;
     case ADGI_STATE_MH_SAMPLES: src = v->mh_smp; break;
     case ADGI_STATE_MH_ORDER: src = v->mh_ord; break;
@@ -1576,6 +1604,13 @@ int adgi_read_state(adgi_volume v, int32_t which, void* dst, uint64_t bytes)
         return ADGI_OK;
     }
     if (bytes) CK(cudaMemcpy(dst, src, bytes, cudaMemcpyDeviceToHost));
+    if (which == ADGI_STATE_MOVING_BVH_NODES) {  // references back to the moving tree's own indices
+        const int no = moving_node_off(v), to = moving_tri_off(v);
+        for (size_t i = 0; i < bytes / sizeof(BNode); ++i) {
+            int* c = reinterpret_cast<int*>(static_cast<char*>(dst) + i * sizeof(BNode) + offsetof(BNode, d));
+            for (int k = 0; k < 2; ++k) c[k] = c[k] >= 0 ? c[k] - no : ~(~c[k] - to);
+        }
+    }
     return ADGI_OK;
 }
 
