@@ -156,8 +156,8 @@ __global__ void __launch_bounds__(128) k_change_weight(VolConst V, const FrameDe
             }
     const uint32_t qc = qc_of_probe(V, F, B.lut_c, p);
     uint64_t Wp = 0;
-#pragma unroll
     const bool vin = V.cls[p] == 2;  // only V_in probes take adaptive samples
+#pragma unroll
     for (int o = 0; o < 8; ++o) {
         const uint64_t qd = vin ? ((uint64_t)qc * (uint64_t)B.qv[(size_t)p * 8 + o] * (uint64_t)f[o]) >> 20 : 0ull;
         if (B.qd) B.qd[(size_t)p * 8 + o] = (uint32_t)(qd < 0xFFFFFFFFull ? qd : 0xFFFFFFFFull);
@@ -197,6 +197,26 @@ __device__ __forceinline__ uint64_t block_sum(uint64_t v, uint64_t* red)
     return red[32];
 }
 
+// block sums of two values at once (one round of barriers)
+__device__ __forceinline__ void block_sum2(uint64_t& a, uint64_t& b, uint64_t* red)
+{
+    a = warp_sum(a);
+    b = warp_sum(b);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (int)(blockDim.x >> 5);
+    __syncthreads();
+    if (lane == 0) red[w] = a, red[32 + w] = b;
+    __syncthreads();
+    if (w == 0) {
+        uint64_t x = lane < nw ? red[lane] : 0ull, y = lane < nw ? red[32 + lane] : 0ull;
+        x = warp_sum(x);
+        y = warp_sum(y);
+        if (lane == 0) red[64] = x, red[65] = y;
+    }
+    __syncthreads();
+    a = red[64];
+    b = red[65];
+}
+
 // exclusive prefix of v over threads in index order; *total receives the sum
 __device__ __forceinline__ uint64_t block_exscan(uint64_t v, uint64_t* red, uint64_t* total)
 {
@@ -231,77 +251,99 @@ __device__ __forceinline__ uint64_t block_exscan(uint64_t v, uint64_t* red, uint
 // V_in floors E = (avg - 8) P - (m0 - 8) |V_in| is spread over V_in, capped
 // at rmax - m0 per probe.  Without cls every probe is in V_in and E =
 // (avg - m0) P.
-__global__ void __launch_bounds__(kAllocThreads) k_allocate(const uint32_t* __restrict__ Win, int P, int avg, int m0,
+// floor(x / d) for d >= 1 from inv = floor((2^64 - 1) / d): the high word of
+// x inv is floor(x / d) or at most two less (the error of inv is below one
+// part in d, that of the product below 2), and the remainder check corrects it
+__device__ __forceinline__ uint64_t div_by(uint64_t x, uint64_t d, uint64_t inv)
+{
+    uint64_t q = __umul64hi(x, inv), r = x - q * d;
+    if (r >= d) ++q, r -= d;
+    if (r >= d) ++q;
+    return q;
+}
+
+// Probes per CTA of shared memory for the staged weights and extras (8 bytes
+// a probe); larger grids work on global memory.
+constexpr int kAllocStageMax = 24 * 1024;
+
+// SM: each probe's weight (0 outside V_in) and extra rays are staged in
+// shared memory.  A probe outside V_in starts with its extras at the cap and
+// weight 0, so it is never eligible: every test below is w > 0 / n < cap.
+template <bool SM>
+__global__ void __launch_bounds__(kAllocThreads, 1) k_allocate(const uint32_t* __restrict__ Win, int P, int avg, int m0,
                                                             int rmax, uint32_t* __restrict__ n, uint32_t* __restrict__ off,
                                                             const uint8_t* __restrict__ cls)
 {
-    __shared__ uint64_t red[33];
+    __shared__ uint64_t red[66];
+    extern __shared__ uint32_t stage[];  // SM: [P] weights, then [P] extras
     const int chunk = (P + kAllocThreads - 1) / kAllocThreads;
     const int c0 = min(P, (int)threadIdx.x * chunk), c1 = min(P, c0 + chunk);
-    uint64_t pin = 0;
-    for (int p = c0; p < c1; ++p) pin += (!cls || cls[p] == 2) ? 1u : 0u;
-    uint64_t rank0, Pin;
-    rank0 = block_exscan(pin, red, &Pin);  // V_in rank of this chunk's first V_in probe
     const uint32_t cap = (uint32_t)(rmax - m0);
+    uint32_t* ws = SM ? stage : nullptr;
+    uint32_t* nx = SM ? stage + P : n;  // extra rays beyond the floor
+    auto vin = [&](int p) { return !cls || cls[p] == 2; };
+    auto w_of = [&](int p) -> uint32_t { return SM ? ws[p] : (vin(p) ? __ldg(Win + p) : 0u); };
+    uint64_t pin = 0, s = 0;
+    for (int p = c0; p < c1; ++p) {
+        const bool in = vin(p);
+        const uint32_t w = in ? __ldg(Win + p) : 0u;
+        pin += in ? 1u : 0u;
+        s += w;
+        if (SM) ws[p] = w;
+        nx[p] = in ? 0u : cap;
+    }
+    uint64_t Pin;
+    const uint64_t rank0 = block_exscan(pin, red, &Pin);  // V_in rank of this chunk's first V_in probe
+    const uint64_t S = block_sum(s, red);                  // also orders the staging writes before the reads
     uint64_t E = (uint64_t)(avg - 8) * (uint64_t)P - (uint64_t)(m0 - 8) * Pin;
     if (E > Pin * cap) E = Pin * cap;
-    // W of the probes outside V_in counts as 0, and their cap as 0
-#define W_OF(p) ((!cls || cls[p] == 2) ? Win[p] : 0u)
-#define CAP_OF(p) ((!cls || cls[p] == 2) ? cap : 0u)
-    uint64_t s = 0;
-    for (int p = c0; p < c1; ++p) s += W_OF(p);
-    const uint64_t S = block_sum(s, red);
     if (S == 0) {  // uniform over V_in, the remainder to the lowest V_in ranks
         const uint64_t q = Pin ? E / Pin : 0, r = Pin ? E % Pin : 0;
         uint64_t rank = rank0;
         for (int p = c0; p < c1; ++p) {
-            if (cls && cls[p] != 2) {
-                n[p] = 0u;
-                continue;
-            }
-            n[p] = (uint32_t)(q + (rank < r ? 1u : 0u));
+            if (!vin(p)) continue;
+            nx[p] = (uint32_t)(q + (rank < r ? 1u : 0u));
             ++rank;
         }
     } else {
-        for (int p = c0; p < c1; ++p) n[p] = 0u;
-        uint64_t Erem = E;
+        // proportional passes: SU = the weight of the probes below their cap
+        // (at first every V_in probe: S, unless the cap is 0); the pass that
+        // hands out shares also sums SU for the next pass
+        uint64_t Erem = E, SU = cap > 0u ? S : 0u;
         for (int it = 0; it < kAllocIters; ++it) {
-            uint64_t su = 0;
-            for (int p = c0; p < c1; ++p) {
-                uint32_t w = W_OF(p);
-                if (w > 0u && n[p] < CAP_OF(p)) su += w;
-            }
-            const uint64_t SU = block_sum(su, red);
             if (SU == 0 || Erem == 0) break;
-            uint64_t given = 0;
+            const uint64_t inv = 0xFFFFFFFFFFFFFFFFull / SU;
+            uint64_t G = 0, su = 0;
             for (int p = c0; p < c1; ++p) {
-                uint32_t w = W_OF(p), e = n[p];
-                if (w == 0u || e >= CAP_OF(p)) continue;
-                uint64_t share = Erem * (uint64_t)w / SU;
-                uint64_t room = CAP_OF(p) - e;
-                uint64_t a = share < room ? share : room;
-                n[p] = e + (uint32_t)a;
-                given += a;
+                const uint32_t w = w_of(p), e = nx[p];
+                if (w == 0u || e >= cap) continue;
+                const uint64_t share = div_by(Erem * (uint64_t)w, SU, inv);
+                const uint64_t room = cap - e;
+                const uint64_t a = share < room ? share : room;
+                nx[p] = e + (uint32_t)a;
+                G += a;
+                if (a < room) su += w;  // still below the cap after this pass
             }
-            const uint64_t G = block_sum(given, red);
+            block_sum2(G, su, red);
             if (G == 0) break;
             Erem -= G;
+            SU = su;
         }
         // remainder: one each, probe-index order, probes with W > 0 first
         for (int guard = 0; Erem > 0 && guard < (1 << 20); ++guard) {
             uint64_t ca = 0;
             for (int p = c0; p < c1; ++p)
-                if (W_OF(p) > 0u && n[p] < CAP_OF(p)) ++ca;
+                if (w_of(p) > 0u && nx[p] < cap) ++ca;
             const bool modeA = block_sum(ca, red) > 0;
             uint64_t ce = 0;
             for (int p = c0; p < c1; ++p)
-                if (n[p] < CAP_OF(p) && (!modeA || W_OF(p) > 0u)) ++ce;
+                if (nx[p] < cap && (!modeA || w_of(p) > 0u)) ++ce;
             uint64_t tot;
             uint64_t pre = block_exscan(ce, red, &tot);
             if (tot == 0) break;
             for (int p = c0; p < c1; ++p) {
-                if (n[p] < CAP_OF(p) && (!modeA || W_OF(p) > 0u)) {
-                    if (pre < Erem) n[p] += 1u;
+                if (nx[p] < cap && (!modeA || w_of(p) > 0u)) {
+                    if (pre < Erem) nx[p] += 1u;
                     ++pre;
                 }
             }
@@ -309,24 +351,24 @@ __global__ void __launch_bounds__(kAllocThreads) k_allocate(const uint32_t* __re
         }
     }
     // rays per probe: the floor plus the extra; adaptive rays = rays - 8 (0 outside V_in)
-#define FLOOR_OF(p) ((!cls || cls[p] == 2) ? (uint32_t)m0 : (cls[p] == 1 ? 8u : 0u))
+    auto rays_of = [&](int p) -> uint32_t {
+        if (vin(p)) return (uint32_t)m0 + nx[p];
+        return cls[p] == 1 ? 8u : 0u;
+    };
     uint64_t loc = 0;
     for (int p = c0; p < c1; ++p) {
-        const uint32_t np = FLOOR_OF(p) + n[p];
+        const uint32_t np = rays_of(p);
         loc += np > 8u ? np - 8u : 0u;
     }
     uint64_t tot;
     uint64_t pre = block_exscan(loc, red, &tot);
     for (int p = c0; p < c1; ++p) {
+        const uint32_t np = rays_of(p);
         off[p] = (uint32_t)pre;
-        const uint32_t np = FLOOR_OF(p) + n[p];
         pre += np > 8u ? np - 8u : 0u;
         n[p] = np;
     }
     if (threadIdx.x == 0) off[P] = (uint32_t)tot;
-#undef W_OF
-#undef CAP_OF
-#undef FLOOR_OF
 }
 
 // ============================================================== blend
@@ -1263,7 +1305,16 @@ cudaError_t launch_classify(const VolConst& V, const FrameDev* FD, const uint16_
 cudaError_t launch_allocate(const uint32_t* W, int P, int avg, int m0, int rmax, uint32_t* n_out, uint32_t* off_out,
                             cudaStream_t s, const uint8_t* cls)
 {
-    k_allocate<<<1, kAllocThreads, 0, s>>>(W, P, avg, m0, rmax, n_out, off_out, cls);
+    if (P <= kAllocStageMax) {
+        const int sm = 8 * P;
+        if (sm > 48 * 1024) {
+            cudaError_t e = cudaFuncSetAttribute(k_allocate<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+            if (e != cudaSuccess) return e;
+        }
+        k_allocate<true><<<1, kAllocThreads, sm, s>>>(W, P, avg, m0, rmax, n_out, off_out, cls);
+    } else {
+        k_allocate<false><<<1, kAllocThreads, 0, s>>>(W, P, avg, m0, rmax, n_out, off_out, cls);
+    }
     count_launches(1);
     return cudaGetLastError();
 }

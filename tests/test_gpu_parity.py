@@ -75,7 +75,7 @@ def _compare_update(gv, ov, frame, check_atlas=True, what=""):
 
 
 # ------------------------------------------------------------------ allocation
-@pytest.mark.parametrize("P", [1, 7, 64, 1000, 1025, 16384, 131072])
+@pytest.mark.parametrize("P", [1, 7, 64, 1000, 1025, 16384, 24576, 131072])
 def test_allocation_bit_exact(adgi, P):
     rng = np.random.default_rng(P)
     cases = [
@@ -85,6 +85,7 @@ def test_allocation_bit_exact(adgi, P):
         (np.zeros(P, np.int64), 33, 8, 40),
         (np.full(P, 5), 9, 8, 9),
         (rng.integers(0, 2, P) * ((1 << 24) - 1), 100, 16, 101),
+        (rng.integers(0, 1 << 32, P, dtype=np.uint64), 64, 8, 256),  # weights beyond what the heuristics make
     ]
     dev = torch.device("cuda")
     for W, avg, rmin, rmax in cases:
