@@ -44,6 +44,33 @@ __global__ void k_init_bounds(uint32_t* __restrict__ bounds)
     else if (threadIdx.x < 6) bounds[threadIdx.x] = 0u;
 }
 
+// listed triangle i: its vertices into tri_in[3i..3i+2] (v0.w = its index),
+// its centroid into the ordered-integer bounds s_lo / s_hi
+__device__ __forceinline__ void tri_fetch(const float* __restrict__ verts, const int* __restrict__ idx,
+                                          const int* __restrict__ list, int nv, int i, float4* __restrict__ tri_in,
+                                          uint32_t* s_lo, uint32_t* s_hi, int* __restrict__ err)
+{
+    const int t = list ? list[i] : i;
+    float c[3] = {0.f, 0.f, 0.f};
+    for (int v = 0; v < 3; ++v) {
+        int vi = idx[3 * (size_t)t + v];
+        if (vi < 0 || vi >= nv) {  // guarded: an out-of-range index reads vertex 0
+            atomicOr(err, kErrIndex);
+            vi = 0;
+        }
+        float x = verts[3 * (size_t)vi], y = verts[3 * (size_t)vi + 1], z = verts[3 * (size_t)vi + 2];
+        tri_in[3 * (size_t)i + v] = make_float4(x, y, z, v == 0 ? __int_as_float(t) : 0.f);
+        c[0] += x;
+        c[1] += y;
+        c[2] += z;
+    }
+    for (int k = 0; k < 3; ++k) {
+        uint32_t o = f2ord(c[k] * (1.0f / 3.0f));
+        atomicMin(&s_lo[k], o);
+        atomicMax(&s_hi[k], o);
+    }
+}
+
 __global__ void k_tri_prep(const float* __restrict__ verts, const int* __restrict__ idx, const int* __restrict__ list,
                            int nt, int nv, float4* __restrict__ tri_in, uint32_t* __restrict__ bounds,
                            int* __restrict__ err)
@@ -55,27 +82,7 @@ __global__ void k_tri_prep(const float* __restrict__ verts, const int* __restric
     }
     __syncthreads();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < nt) {
-        const int t = list ? list[i] : i;
-        float c[3] = {0.f, 0.f, 0.f};
-        for (int v = 0; v < 3; ++v) {
-            int vi = idx[3 * (size_t)t + v];
-            if (vi < 0 || vi >= nv) {  // guarded: an out-of-range index reads vertex 0
-                atomicOr(err, kErrIndex);
-                vi = 0;
-            }
-            float x = verts[3 * (size_t)vi], y = verts[3 * (size_t)vi + 1], z = verts[3 * (size_t)vi + 2];
-            tri_in[3 * (size_t)i + v] = make_float4(x, y, z, v == 0 ? __int_as_float(t) : 0.f);
-            c[0] += x;
-            c[1] += y;
-            c[2] += z;
-        }
-        for (int k = 0; k < 3; ++k) {
-            uint32_t o = f2ord(c[k] * (1.0f / 3.0f));
-            atomicMin(&s_lo[k], o);
-            atomicMax(&s_hi[k], o);
-        }
-    }
+    if (i < nt) tri_fetch(verts, idx, list, nv, i, tri_in, s_lo, s_hi, err);
     __syncthreads();
     if (threadIdx.x < 3) {
         atomicMin(&bounds[threadIdx.x], s_lo[threadIdx.x]);
@@ -109,18 +116,16 @@ __device__ __forceinline__ uint64_t spread21(uint32_t v)
     return x;
 }
 
-__global__ void k_morton(const float4* __restrict__ tri_in, int nt, const uint32_t* __restrict__ bounds,
-                         uint64_t* __restrict__ keys, uint32_t* __restrict__ vals)
+// 63-bit Morton code of a triangle's centroid in the centroid bounds
+// (ordered-integer lo / hi)
+__device__ __forceinline__ uint64_t morton_key(float4 A, float4 B, float4 C, const uint32_t* bounds)
 {
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= nt) return;
     float lo[3], ext[3];
     for (int k = 0; k < 3; ++k) {
         lo[k] = ord2f(bounds[k]);
         float hi = ord2f(bounds[3 + k]);
         ext[k] = fmaxf(hi - lo[k], 1e-30f);
     }
-    float4 A = tri_in[3 * (size_t)t], B = tri_in[3 * (size_t)t + 1], C = tri_in[3 * (size_t)t + 2];
     float c[3] = {(A.x + B.x + C.x) * (1.0f / 3.0f), (A.y + B.y + C.y) * (1.0f / 3.0f),
                   (A.z + B.z + C.z) * (1.0f / 3.0f)};
     uint32_t q[3];
@@ -129,7 +134,15 @@ __global__ void k_morton(const float4* __restrict__ tri_in, int nt, const uint32
         u = fminf(fmaxf(u, 0.0f), 2097151.0f);
         q[k] = (uint32_t)u;
     }
-    keys[t] = (spread21(q[0]) << 2) | (spread21(q[1]) << 1) | spread21(q[2]);
+    return (spread21(q[0]) << 2) | (spread21(q[1]) << 1) | spread21(q[2]);
+}
+
+__global__ void k_morton(const float4* __restrict__ tri_in, int nt, const uint32_t* __restrict__ bounds,
+                         uint64_t* __restrict__ keys, uint32_t* __restrict__ vals)
+{
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nt) return;
+    keys[t] = morton_key(tri_in[3 * (size_t)t], tri_in[3 * (size_t)t + 1], tri_in[3 * (size_t)t + 2], bounds);
     vals[t] = (uint32_t)t;
 }
 
@@ -282,6 +295,68 @@ __global__ void k_tri_order(const float4* __restrict__ tri_in, const uint32_t* _
     tri_v[3 * (size_t)i] = tri_in[3 * (size_t)t];
     tri_v[3 * (size_t)i + 1] = tri_in[3 * (size_t)t + 1];
     tri_v[3 * (size_t)i + 2] = tri_in[3 * (size_t)t + 2];
+}
+
+// The Morton order of a small build (nt <= kSmallBuild) in one block: the
+// triangles and their centroid bounds, the keys, a bitonic sort of (key,
+// index) pairs in shared memory -- the order of the stable radix sort, since
+// equal keys keep index order -- and the triangles gathered into that order.
+// One launch instead of the 8 radix passes and their scans.
+constexpr int kSmallBuild = 2048;
+constexpr int kSmallThreads = 1024;
+
+__global__ void __launch_bounds__(kSmallThreads) k_morton_small(const float* __restrict__ verts,
+                                                                const int* __restrict__ idx,
+                                                                const int* __restrict__ list, int nt, int nv,
+                                                                float4* __restrict__ tri_in, uint64_t* __restrict__ keys,
+                                                                uint32_t* __restrict__ vals,
+                                                                float4* __restrict__ tri_v, int* __restrict__ err)
+{
+    __shared__ uint32_t s_b[6];
+    __shared__ uint64_t sk[kSmallBuild];
+    __shared__ uint32_t sv[kSmallBuild];
+    const int tid = threadIdx.x;
+    if (tid < 3) s_b[tid] = 0xFFFFFFFFu;
+    else if (tid < 6) s_b[tid] = 0u;
+    __syncthreads();
+    for (int i = tid; i < nt; i += kSmallThreads) tri_fetch(verts, idx, list, nv, i, tri_in, s_b, s_b + 3, err);
+    __syncthreads();  // also orders this block's tri_in writes before the reads below
+    int n2 = 2;
+    while (n2 < nt) n2 <<= 1;
+    for (int i = tid; i < n2; i += kSmallThreads) {
+        if (i < nt) {
+            sk[i] = morton_key(tri_in[3 * (size_t)i], tri_in[3 * (size_t)i + 1], tri_in[3 * (size_t)i + 2], s_b);
+            sv[i] = (uint32_t)i;
+        } else {  // padding: after every real pair
+            sk[i] = ~0ull;
+            sv[i] = 0xFFFFFFFFu;
+        }
+    }
+    __syncthreads();
+    for (int k = 2; k <= n2; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = tid; i < n2; i += kSmallThreads) {
+                const int l = i ^ j;
+                if (l <= i) continue;
+                const uint64_t ka = sk[i], kb = sk[l];
+                const uint32_t va = sv[i], vb = sv[l];
+                const bool gt = ka > kb || (ka == kb && va > vb);
+                if (gt == ((i & k) == 0)) {  // ascending where bit k of i is clear
+                    sk[i] = kb, sk[l] = ka;
+                    sv[i] = vb, sv[l] = va;
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int i = tid; i < nt; i += kSmallThreads) {
+        const uint32_t t = sv[i];
+        keys[i] = sk[i];
+        vals[i] = t;
+        tri_v[3 * (size_t)i] = tri_in[3 * (size_t)t];
+        tri_v[3 * (size_t)i + 1] = tri_in[3 * (size_t)t + 1];
+        tri_v[3 * (size_t)i + 2] = tri_in[3 * (size_t)t + 2];
+    }
 }
 
 __device__ __forceinline__ int delta(const uint64_t* keys, int n, int i, int j)
@@ -659,6 +734,13 @@ static cudaError_t morton_order(const BvhBufs& B, const float* d_verts, const in
                                 int nt, int* err, cudaStream_t s, int* cur_out)
 {
     const int T = 256;
+    if (nt <= kSmallBuild) {
+        k_morton_small<<<1, kSmallThreads, 0, s>>>(d_verts, d_idx, list, nt, nv, B.tri_in, B.keys[0], B.vals[0],
+                                                    B.tri_v, err);
+        count_launches(1);
+        *cur_out = 0;
+        return cudaGetLastError();
+    }
     k_init_bounds<<<1, 32, 0, s>>>(B.bounds);
     count_launches(1);
     k_tri_prep<<<(nt + T - 1) / T, T, 0, s>>>(d_verts, d_idx, list, nt, nv, B.tri_in, B.bounds, err);
