@@ -336,6 +336,38 @@ def test_build_bvh_matches_volume_bvh(adgi, scene):
     gv.close()
 
 
+def test_moving_bvh_after_static_part(adgi):
+    """With static and moving triangles, the moving part is built after the
+    static part's nodes and triangles and its references relocated; the
+    state reader gives it back in the layout of a stand-alone build of the
+    moving triangles (those touching a moved vertex, in index order)."""
+    w = S.small_city(3, n_boxes=400, dims=(6, 4, 5), rays_avg=24)
+    gv = gpu_volume(adgi, w)
+    dv = w.dyn_at(1)
+    gv.move_vertices(w.dyn_first, dv)
+    gv.update(0, w.seed, w.lights_at(0), w.sky)
+    verts = w.verts.copy()
+    verts[w.dyn_first:w.dyn_first + len(dv)] = dv
+    moved = np.zeros(len(verts), bool)
+    moved[w.dyn_first:w.dyn_first + len(dv)] = True
+    mov = np.flatnonzero(moved[w.idx].any(axis=1))
+    assert 1 < len(mov) < w.n_tris  # both parts hold triangles
+    dev = torch.device("cuda")
+    nt = len(mov)
+    nodes = torch.zeros((nt - 1) * 16, dtype=torch.int32, device=dev)
+    tris = torch.zeros(nt * 12, dtype=torch.float32, device=dev)
+    adgi.adgi_build_bvh(torch.from_numpy(verts).to(dev), torch.from_numpy(np.ascontiguousarray(w.idx[mov])).to(dev),
+                        adgi.scene_eps(w.verts), nodes, tris, torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(gv.state("MOVING_BVH_NODES", np.int32), nodes.cpu().numpy())
+    got = gv.state("MOVING_BVH_TRIS", np.float32).reshape(nt, 3, 4)
+    ref = tris.cpu().numpy().reshape(nt, 3, 4)
+    np.testing.assert_array_equal(got[:, :, :3], ref[:, :, :3])
+    # the volume tags each triangle with its scene index, the stand-alone build with its list position
+    np.testing.assert_array_equal(got[:, 0, 3].view(np.int32), mov[ref[:, 0, 3].view(np.int32)])
+    gv.close()
+
+
 def test_build_bvh_rejects_bad_index(adgi):
     dev = torch.device("cuda")
     w = S.box_room(1)
