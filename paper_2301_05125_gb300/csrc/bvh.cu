@@ -453,6 +453,7 @@ __global__ void k_bounds(const float4* __restrict__ tri_v, int n, BNode* nodes, 
 // against 16 cut the traversals' box tests by a fifth (update 7.18 -> 6.25 ms)
 // for a static build of 7 instead of 4 ms.
 constexpr int kPlocR = 256;
+constexpr int kRotPasses = 4;  // rotation passes after the clustering
 constexpr int kPlocT = 256;
 
 __device__ __forceinline__ float box_area(float4 lo, float4 hi)
@@ -556,6 +557,110 @@ __global__ void k_ploc_merge(int count, const int* __restrict__ nn, const uint64
         blo2[pos] = blo[i];
         bhi2[pos] = bhi[i];
     }
+}
+
+// ---------------------------------------------------------------- rotations
+// Local tree rotations (Kensler, "Tree Rotations for Improving Bounding
+// Volume Hierarchies", 2008) after the PLOC build: node N may swap one child
+// with a grandchild under its other child C when that shrinks C's box (the
+// other boxes keep their leaf sets).  A pass treats the internal nodes of one
+// depth parity: a rotation writes only N and C, so no two rotations of a
+// pass touch the same node.  Hits do not depend on the tree's shape.
+
+// depth of internal node i below the root (node 0), bounded walk
+__global__ void k_node_depth(int n_int, const int* __restrict__ par_int, int* __restrict__ depth)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_int) return;
+    int d = 0, x = i;
+    while (x != 0 && d < 4096) {
+        x = par_int[x];
+        ++d;
+    }
+    depth[i] = d;
+}
+
+__device__ __forceinline__ void child_box(const BNode& n, int k, float4& lo, float4& hi)
+{
+    if (k == 0) {
+        lo = make_float4(n.a.x, n.a.y, n.a.z, 0.f);
+        hi = make_float4(n.a.w, n.b.x, n.b.y, 0.f);
+    } else {
+        lo = make_float4(n.b.z, n.b.w, n.c.x, 0.f);
+        hi = make_float4(n.c.y, n.c.z, n.c.w, 0.f);
+    }
+}
+
+__device__ __forceinline__ BNode make_node(float4 lo0, float4 hi0, float4 lo1, float4 hi1, int c0, int c1)
+{
+    BNode b;
+    b.a = make_float4(lo0.x, lo0.y, lo0.z, hi0.x);
+    b.b = make_float4(hi0.y, hi0.z, lo1.x, lo1.y);
+    b.c = make_float4(lo1.z, hi1.x, hi1.y, hi1.z);
+    b.d = make_int4(c0, c1, 0, 0);
+    return b;
+}
+
+__device__ __forceinline__ float4 fmin4(float4 a, float4 b)
+{
+    return make_float4(fminf(a.x, b.x), fminf(a.y, b.y), fminf(a.z, b.z), 0.f);
+}
+__device__ __forceinline__ float4 fmax4(float4 a, float4 b)
+{
+    return make_float4(fmaxf(a.x, b.x), fmaxf(a.y, b.y), fmaxf(a.z, b.z), 0.f);
+}
+
+__device__ __forceinline__ void set_parent(int ref, int parent, int* par_int, int* par_leaf)
+{
+    if (ref >= 0)
+        par_int[ref] = parent;
+    else
+        par_leaf[~ref] = parent;
+}
+
+__global__ void k_rotate(int n_int, BNode* __restrict__ nodes, const int* __restrict__ depth, int parity,
+                         int* __restrict__ par_int, int* __restrict__ par_leaf)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_int || (depth[i] & 1) != parity) return;
+    const BNode N = nodes[i];
+    const int ch[2] = {N.d.x, N.d.y};
+    float4 lo[2], hi[2];
+    child_box(N, 0, lo[0], hi[0]);
+    child_box(N, 1, lo[1], hi[1]);
+    float best = 0.0f;
+    int bs = -1, bg = -1;  // child s of N swaps with grandchild g under the other child
+    BNode C[2];
+    for (int s = 0; s < 2; ++s) {
+        const int o = 1 - s;
+        if (ch[o] < 0) continue;
+        C[o] = nodes[ch[o]];
+        float4 glo[2], ghi[2];
+        child_box(C[o], 0, glo[0], ghi[0]);
+        child_box(C[o], 1, glo[1], ghi[1]);
+        const float cur = box_area(lo[o], hi[o]);
+        for (int g = 0; g < 2; ++g) {  // the grandchild g moves up; the other one joins child s
+            const float a = box_area(fmin4(lo[s], glo[1 - g]), fmax4(hi[s], ghi[1 - g]));
+            const float gain = cur - a;
+            if (gain > best && gain > 1e-6f * cur) {
+                best = gain;
+                bs = s;
+                bg = g;
+            }
+        }
+    }
+    if (bs < 0) return;
+    const int s = bs, o = 1 - s, g = bg;
+    float4 glo[2], ghi[2];
+    child_box(C[o], 0, glo[0], ghi[0]);
+    child_box(C[o], 1, glo[1], ghi[1]);
+    // C keeps child 1-g and takes N's child s; N takes grandchild g in place of child s
+    const int cref = ch[o], gref = g ? C[o].d.y : C[o].d.x, kref = g ? C[o].d.x : C[o].d.y;
+    const float4 clo = fmin4(lo[s], glo[1 - g]), chi = fmax4(hi[s], ghi[1 - g]);
+    nodes[cref] = make_node(lo[s], hi[s], glo[1 - g], ghi[1 - g], ch[s], kref);
+    nodes[i] = s == 0 ? make_node(glo[g], ghi[g], clo, chi, gref, cref) : make_node(clo, chi, glo[g], ghi[g], cref, gref);
+    set_parent(ch[s], cref, par_int, par_leaf);
+    set_parent(gref, i, par_int, par_leaf);
 }
 
 // depth of every leaf below the root (node 0), bounded walk; max into *depth
@@ -838,6 +943,14 @@ cudaError_t build_ploc(const BvhBufs& B, const PlocBufs& Q, const float* d_verts
         c ^= 1;
     }
     if (node_top != 0) return cudaErrorUnknown;
+    // rotations: passes over the two depth parities, depths refreshed between
+    // passes (a rotation moves subtrees one level up or down)
+    for (int pass = 0; pass < kRotPasses; ++pass)
+        for (int parity = 0; parity < 2; ++parity) {
+            k_node_depth<<<(nt - 1 + T - 1) / T, T, 0, s>>>(nt - 1, B.par_int, Q.nn);
+            k_rotate<<<(nt - 1 + T - 1) / T, T, 0, s>>>(nt - 1, B.nodes, Q.nn, parity, B.par_int, B.par_leaf);
+            count_launches(2);
+        }
     // the traversal stack holds at most depth-1 entries: a deeper tree is
     // replaced by the linear BVH (depth <= 95 by construction)
     e = cudaMemsetAsync(Q.total, 0, sizeof(int), s);
