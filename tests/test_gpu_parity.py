@@ -368,6 +368,44 @@ def test_moving_bvh_after_static_part(adgi):
     gv.close()
 
 
+def _morton_keys(tv):
+    """63-bit Morton codes of triangles (vertices tv[n, 3, 3]) in their
+    centroid bounds, with the builder's FP32 steps"""
+    f = np.float32
+    c = ((tv[:, 0] + tv[:, 1]) + tv[:, 2]) * f(1.0 / 3.0)
+    lo, hi = c.min(0), c.max(0)
+    ext = np.maximum(hi - lo, f(1e-30))
+    q = np.clip((c - lo) / ext * f(2097152.0), f(0), f(2097151.0)).astype(np.uint64)
+    key = np.zeros(len(tv), np.uint64)
+    for b in range(21):
+        for k in range(3):
+            key |= ((q[:, k] >> np.uint64(b)) & np.uint64(1)) << np.uint64(3 * b + 2 - k)
+    return key
+
+
+@pytest.mark.parametrize("nt", [5, 1500, 2048, 2049, 30000])
+def test_build_order_is_stable_morton_order(adgi, nt):
+    # below 2,049 triangles one block sorts (bitonic, by key then index),
+    # above it the radix passes do: both must give the stable key order
+    rng = np.random.default_rng(nt)
+    verts = rng.uniform(-50, 50, (3 * nt, 3)).astype(np.float32)
+    verts[: 3 * nt // 2] = np.round(verts[: 3 * nt // 2] / 8.0) * 8.0  # repeated centroids: equal keys
+    idx = np.arange(3 * nt, dtype=np.int32).reshape(nt, 3)
+    dev = torch.device("cuda")
+    nodes = torch.zeros(max(nt - 1, 1) * 16, dtype=torch.int32, device=dev)
+    tris = torch.zeros(nt * 12, dtype=torch.float32, device=dev)
+    adgi.adgi_build_bvh(torch.from_numpy(verts).to(dev), torch.from_numpy(idx).to(dev), adgi.scene_eps(verts), nodes,
+                        tris, torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    t = tris.cpu().numpy().reshape(nt, 3, 4)
+    orig = t[:, 0, 3].view(np.int32)
+    assert sorted(orig.tolist()) == list(range(nt))
+    key = _morton_keys(verts.reshape(nt, 3, 3))[orig]
+    k0, k1 = key[:-1], key[1:]
+    assert np.all((k0 < k1) | ((k0 == k1) & (orig[:-1] < orig[1:]))), "not the stable Morton order"
+    assert (k0 == k1).any() or nt < 100  # the ties were exercised
+
+
 def test_build_bvh_rejects_bad_index(adgi):
     dev = torch.device("cuda")
     w = S.box_room(1)
