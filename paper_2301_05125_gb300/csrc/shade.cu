@@ -147,20 +147,39 @@ __global__ void __launch_bounds__(256) k_shade_prep(VolConst V, const FrameDev* 
             front = true;
         }
     }
-    const unsigned lane = threadIdx.x & 31;
-    for (int l = 0; l < L.n; ++l) {
-        bool want = false;
-        if (front) {
-            float3 D = shadow_dir(L.l[l], xs);
-            want = dot3x(n.x, n.y, n.z, D.x, D.y, D.z) > 0.0f;
+    // The block's jobs take one range of the job list: one atomic per block
+    // on the shared counter (one per warp and light contended on that
+    // address).  Pass 1 counts each warp's jobs, thread 0 scans the warp
+    // totals and claims the range, pass 2 writes each warp's jobs light by
+    // light (a warp's jobs for one light stay contiguous: nearby origins,
+    // one light, so k_shadow's warps trace coherent rays).
+    const unsigned lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    auto wants = [&](int l) {
+        if (!front) return false;
+        const float3 D = shadow_dir(L.l[l], xs);
+        return dot3x(n.x, n.y, n.z, D.x, D.y, D.z) > 0.0f;
+    };
+    unsigned wtot = 0;
+    for (int l = 0; l < L.n; ++l) wtot += (unsigned)__popc(__ballot_sync(0xFFFFFFFFu, wants(l)));
+    __shared__ unsigned s_w[8], s_base;  // at most 256 threads: 8 warps
+    if (lane == 0) s_w[w] = wtot;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned t = 0;
+        for (unsigned k = 0; k < (blockDim.x >> 5); ++k) {
+            const unsigned c = s_w[k];
+            s_w[k] = t;
+            t += c;
         }
-        unsigned mask = __ballot_sync(0xFFFFFFFFu, want);
-        if (!mask) continue;
-        unsigned base = 0;
-        if (lane == 0) base = atomicAdd(job_count, (unsigned)__popc(mask));
-        base = __shfl_sync(0xFFFFFFFFu, base, 0);
+        s_base = t ? atomicAdd(job_count, t) : 0u;
+    }
+    __syncthreads();
+    unsigned base = s_base + s_w[w];
+    for (int l = 0; l < L.n; ++l) {
+        const bool want = wants(l);
+        const unsigned mask = __ballot_sync(0xFFFFFFFFu, want);
         if (want) {
-            unsigned js = base + __popc(mask & ((1u << lane) - 1u));
+            const unsigned js = base + __popc(mask & ((1u << lane) - 1u));
             if (js < job_cap) {
                 jobs[js] = make_uint4(__float_as_uint(xs.x), __float_as_uint(xs.y), __float_as_uint(xs.z), slot);
                 job_light[js] = (uint8_t)l;
@@ -168,6 +187,7 @@ __global__ void __launch_bounds__(256) k_shade_prep(VolConst V, const FrameDev* 
                 atomicOr(V.err, kErrRayRange);
             }
         }
+        base += (unsigned)__popc(mask);
     }
 }
 
