@@ -219,7 +219,7 @@ __global__ void __launch_bounds__(128) k_shadow(const FrameDev* __restrict__ FD,
     }
 }
 
-__global__ void __launch_bounds__(256) k_shade_finish(VolConst V, const FrameDev* __restrict__ FD, SceneDev S,
+__global__ void __launch_bounds__(256, 4) k_shade_finish(VolConst V, const FrameDev* __restrict__ FD, SceneDev S,
                                                       RaySet Rs, const int2* __restrict__ hit,
                                                       const unsigned long long* __restrict__ vis,
                                                       const void* __restrict__ irr, const void* __restrict__ dep,
