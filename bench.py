@@ -748,20 +748,25 @@ def run_ours(args):
         dyn_pin = torch.from_numpy(dyn_host).pin_memory() if have_dyn else None
         f0 = args.warmup + args.steps
         e2e_ms = []
+        # the update as a replay of the volume's captured graph (one launch for
+        # the whole update); the untimed first call captures it
+        if have_dyn:
+            adgi.adgi_move_vertices(vol.h, w.dyn_first, dyn_pin[f0].numpy())
+        adgi.adgi_update_graph(vol.h, frames[f0])
         torch.cuda.synchronize()
         for k in range(min(args.steps, 10)):
             f = f0 + (k % 2)
             t0 = time.perf_counter()
             if have_dyn:
                 adgi.adgi_move_vertices(vol.h, w.dyn_first, dyn_pin[f].numpy())
-            adgi.adgi_update(vol.h, frames[f])
+            adgi.adgi_update_graph(vol.h, frames[f])
             adgi.adgi_query_irradiance(vol.h, qpos.numpy(), qnrm.numpy(), qout.numpy())
             e2e_ms.append(1e3 * (time.perf_counter() - t0))
         h2d = (w.dyn_count * 12 if have_dyn else 0) + 2 * nq * 12 + len(w.lights_at(0)) * 28
         e2e = {"value": ws * rays / (float(np.mean(e2e_ms)) / 1e3), "unit": "rays/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": nq * 12, "ms_per_step": float(np.mean(e2e_ms)),
                "includes": "host->device occluder vertices + 65536-point shading query (positions, normals) "
-                           "from pinned memory, update, query results back to the host"}
+                           "from pinned memory, update (graph replay), query results back to the host"}
     batched = None
     if rank == 0 and not args.no_batched:
         batched = _batched_section(args, adgi, torch, dev)
