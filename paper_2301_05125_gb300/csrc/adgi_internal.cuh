@@ -601,8 +601,9 @@ __device__ __forceinline__ void filter_moments(float w00, float w01, float w10, 
 __device__ __forceinline__ void depth_moments(const VolConst& V, const void* dep, size_t tile, float dx, float dy,
                                               float dz, float* mom, float* cond)
 {
+    // the fractions only weight a bilinear lookup: fast division (2 ulp)
     float l1 = fabsf(dx) + fabsf(dy) + fabsf(dz);
-    float px = dx / l1, py = dy / l1;
+    float px = __fdividef(dx, l1), py = __fdividef(dy, l1);
     if (dz < 0.0f) {
         float qx = (1.0f - fabsf(py)) * sgnf(px);
         float qy = (1.0f - fabsf(px)) * sgnf(py);
@@ -626,7 +627,7 @@ __device__ __forceinline__ void depth_moments(const VolConst& V, const void* dep
     float var = fmaxf(mom[1], fmaxf(1e-3f * (mom[1] + mom[0] * mom[0]), V.var_min));
     float d00 = v00.x - mom[0], d01 = v01.x - mom[0], d10 = v10.x - mom[0], d11 = v11.x - mom[0];
     float s2 = fmaxf(fmaxf(v00.y + d00 * d00, v01.y + d01 * d01), fmaxf(v10.y + d10 * d10, v11.y + d11 * d11));
-    *cond = s2 / var;
+    *cond = __fdividef(s2, var);
 }
 
 // ---------------------------------------------------------------- double-float
@@ -780,7 +781,7 @@ __device__ __forceinline__ float3 query_irr_at(const VolConst& V, const void* ir
             // keeps the weight well conditioned at the precision of the moments
             float var = fmaxf(mom[1], fmaxf(1e-3f * (mom[1] + mom[0] * mom[0]), V.var_min));
             float dd = dist - mom[0];
-            wc = var / (var + dd * dd);
+            wc = __fdividef(var, var + dd * dd);
         }
         float E[3];
         tile_bilinear<3>(V, irr, (size_t)p * ti2, V.Ti, V.n_irr, pn, E);
