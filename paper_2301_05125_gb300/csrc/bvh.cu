@@ -453,7 +453,7 @@ __global__ void k_bounds(const float4* __restrict__ tri_v, int n, BNode* nodes, 
 // against 16 cut the traversals' box tests by a fifth (update 7.18 -> 6.25 ms)
 // for a static build of 7 instead of 4 ms.
 constexpr int kPlocR = 256;
-constexpr int kRotPasses = 4;  // rotation passes after the clustering
+constexpr int kRotPasses = 8;  // rotation passes after the clustering
 constexpr int kPlocT = 256;
 
 __device__ __forceinline__ float box_area(float4 lo, float4 hi)
@@ -562,10 +562,12 @@ __global__ void k_ploc_merge(int count, const int* __restrict__ nn, const uint64
 // ---------------------------------------------------------------- rotations
 // Local tree rotations (Kensler, "Tree Rotations for Improving Bounding
 // Volume Hierarchies", 2008) after the PLOC build: node N may swap one child
-// with a grandchild under its other child C when that shrinks C's box (the
-// other boxes keep their leaf sets).  A pass treats the internal nodes of one
-// depth parity: a rotation writes only N and C, so no two rotations of a
-// pass touch the same node.  Hits do not depend on the tree's shape.
+// with a grandchild under its other child C when that shrinks C's box, or a
+// grandchild under one child with one under the other when that shrinks the
+// two children's boxes together (every other box keeps its leaf set).  A
+// pass treats the internal nodes of one depth parity: a rotation writes only
+// N and its children, so no two rotations of a pass touch the same node.
+// Hits do not depend on the tree's shape.
 
 // depth of internal node i below the root (node 0), bounded walk
 __global__ void k_node_depth(int n_int, const int* __restrict__ par_int, int* __restrict__ depth)
@@ -625,42 +627,61 @@ __global__ void k_rotate(int n_int, BNode* __restrict__ nodes, const int* __rest
     if (i >= n_int || (depth[i] & 1) != parity) return;
     const BNode N = nodes[i];
     const int ch[2] = {N.d.x, N.d.y};
-    float4 lo[2], hi[2];
+    float4 lo[2], hi[2], glo[2][2], ghi[2][2];
     child_box(N, 0, lo[0], hi[0]);
     child_box(N, 1, lo[1], hi[1]);
-    float best = 0.0f;
-    int bs = -1, bg = -1;  // child s of N swaps with grandchild g under the other child
     BNode C[2];
+    float cur[2];
+    for (int k = 0; k < 2; ++k) {
+        cur[k] = box_area(lo[k], hi[k]);
+        if (ch[k] < 0) continue;
+        C[k] = nodes[ch[k]];
+        child_box(C[k], 0, glo[k][0], ghi[k][0]);
+        child_box(C[k], 1, glo[k][1], ghi[k][1]);
+    }
+    // (a) child s swaps with grandchild g under the other child o: o's box
+    //     becomes child s + grandchild 1-g;
+    // (b) grandchild a under child 0 swaps with grandchild b under child 1:
+    //     both children's boxes change
+    float best = 0.0f;
+    int kind = -1, bs = 0, bg = 0;
     for (int s = 0; s < 2; ++s) {
         const int o = 1 - s;
         if (ch[o] < 0) continue;
-        C[o] = nodes[ch[o]];
-        float4 glo[2], ghi[2];
-        child_box(C[o], 0, glo[0], ghi[0]);
-        child_box(C[o], 1, glo[1], ghi[1]);
-        const float cur = box_area(lo[o], hi[o]);
-        for (int g = 0; g < 2; ++g) {  // the grandchild g moves up; the other one joins child s
-            const float a = box_area(fmin4(lo[s], glo[1 - g]), fmax4(hi[s], ghi[1 - g]));
-            const float gain = cur - a;
-            if (gain > best && gain > 1e-6f * cur) {
-                best = gain;
-                bs = s;
-                bg = g;
-            }
+        for (int g = 0; g < 2; ++g) {
+            const float gain = cur[o] - box_area(fmin4(lo[s], glo[o][1 - g]), fmax4(hi[s], ghi[o][1 - g]));
+            if (gain > best && gain > 1e-6f * cur[o]) best = gain, kind = 0, bs = s, bg = g;
         }
     }
-    if (bs < 0) return;
-    const int s = bs, o = 1 - s, g = bg;
-    float4 glo[2], ghi[2];
-    child_box(C[o], 0, glo[0], ghi[0]);
-    child_box(C[o], 1, glo[1], ghi[1]);
-    // C keeps child 1-g and takes N's child s; N takes grandchild g in place of child s
-    const int cref = ch[o], gref = g ? C[o].d.y : C[o].d.x, kref = g ? C[o].d.x : C[o].d.y;
-    const float4 clo = fmin4(lo[s], glo[1 - g]), chi = fmax4(hi[s], ghi[1 - g]);
-    nodes[cref] = make_node(lo[s], hi[s], glo[1 - g], ghi[1 - g], ch[s], kref);
-    nodes[i] = s == 0 ? make_node(glo[g], ghi[g], clo, chi, gref, cref) : make_node(clo, chi, glo[g], ghi[g], cref, gref);
-    set_parent(ch[s], cref, par_int, par_leaf);
-    set_parent(gref, i, par_int, par_leaf);
+    if (ch[0] >= 0 && ch[1] >= 0)
+        for (int ga = 0; ga < 2; ++ga)
+            for (int gb = 0; gb < 2; ++gb) {
+                const float a0 = box_area(fmin4(glo[0][1 - ga], glo[1][gb]), fmax4(ghi[0][1 - ga], ghi[1][gb]));
+                const float a1 = box_area(fmin4(glo[1][1 - gb], glo[0][ga]), fmax4(ghi[1][1 - gb], ghi[0][ga]));
+                const float gain = (cur[0] + cur[1]) - (a0 + a1);
+                if (gain > best && gain > 1e-6f * (cur[0] + cur[1])) best = gain, kind = 1, bs = ga, bg = gb;
+            }
+    if (kind == 0) {
+        const int s = bs, o = 1 - s, g = bg;
+        // C keeps child 1-g and takes N's child s; N takes grandchild g in place of child s
+        const int cref = ch[o], gref = g ? C[o].d.y : C[o].d.x, kref = g ? C[o].d.x : C[o].d.y;
+        const float4 clo = fmin4(lo[s], glo[o][1 - g]), chi = fmax4(hi[s], ghi[o][1 - g]);
+        nodes[cref] = make_node(lo[s], hi[s], glo[o][1 - g], ghi[o][1 - g], ch[s], kref);
+        nodes[i] = s == 0 ? make_node(glo[o][g], ghi[o][g], clo, chi, gref, cref)
+                          : make_node(clo, chi, glo[o][g], ghi[o][g], cref, gref);
+        set_parent(ch[s], cref, par_int, par_leaf);
+        set_parent(gref, i, par_int, par_leaf);
+    } else if (kind == 1) {
+        const int ga = bs, gb = bg;
+        const int r0 = ga ? C[0].d.y : C[0].d.x, k0 = ga ? C[0].d.x : C[0].d.y;  // moves / stays under child 0
+        const int r1 = gb ? C[1].d.y : C[1].d.x, k1 = gb ? C[1].d.x : C[1].d.y;  // moves / stays under child 1
+        nodes[ch[0]] = make_node(glo[0][1 - ga], ghi[0][1 - ga], glo[1][gb], ghi[1][gb], k0, r1);
+        nodes[ch[1]] = make_node(glo[1][1 - gb], ghi[1][1 - gb], glo[0][ga], ghi[0][ga], k1, r0);
+        nodes[i] = make_node(fmin4(glo[0][1 - ga], glo[1][gb]), fmax4(ghi[0][1 - ga], ghi[1][gb]),
+                             fmin4(glo[1][1 - gb], glo[0][ga]), fmax4(ghi[1][1 - gb], ghi[0][ga]), ch[0], ch[1]);
+        set_parent(r1, ch[0], par_int, par_leaf);
+        set_parent(r0, ch[1], par_int, par_leaf);
+    }
 }
 
 // depth of every leaf below the root (node 0), bounded walk; max into *depth
