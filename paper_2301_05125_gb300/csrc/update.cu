@@ -1,6 +1,8 @@
 // update.cu -- heuristics, ray allocation, blend and query kernels (sm_103a).
 #include <algorithm>
 
+#include <cooperative_groups.h>
+
 #include "adgi_internal.cuh"
 #include "kernels.cuh"
 
@@ -262,34 +264,26 @@ __device__ __forceinline__ uint64_t div_by(uint64_t x, uint64_t d, uint64_t inv)
     return q;
 }
 
-// Probes per CTA of shared memory for the staged weights and extras (8 bytes
-// a probe); larger grids work on global memory.
-constexpr int kAllocStageMax = 24 * 1024;
-
-// SM: each probe's weight (0 outside V_in) and extra rays are staged in
-// shared memory.  A probe outside V_in starts with its extras at the cap and
-// weight 0, so it is never eligible: every test below is w > 0 / n < cap.
-template <bool SM>
+// One block over global memory, for grids beyond what a cluster stages
+// (k_allocate_cluster below).  A probe outside V_in starts with its extras
+// at the cap and weight 0, so it is never eligible: every test below is
+// w > 0 / n < cap.
 __global__ void __launch_bounds__(kAllocThreads, 1) k_allocate(const uint32_t* __restrict__ Win, int P, int avg, int m0,
                                                             int rmax, uint32_t* __restrict__ n, uint32_t* __restrict__ off,
                                                             const uint8_t* __restrict__ cls)
 {
     __shared__ uint64_t red[66];
-    extern __shared__ uint32_t stage[];  // SM: [P] weights, then [P] extras
     const int chunk = (P + kAllocThreads - 1) / kAllocThreads;
     const int c0 = min(P, (int)threadIdx.x * chunk), c1 = min(P, c0 + chunk);
     const uint32_t cap = (uint32_t)(rmax - m0);
-    uint32_t* ws = SM ? stage : nullptr;
-    uint32_t* nx = SM ? stage + P : n;  // extra rays beyond the floor
+    uint32_t* nx = n;  // extra rays beyond the floor, then the rays
     auto vin = [&](int p) { return !cls || cls[p] == 2; };
-    auto w_of = [&](int p) -> uint32_t { return SM ? ws[p] : (vin(p) ? __ldg(Win + p) : 0u); };
+    auto w_of = [&](int p) -> uint32_t { return vin(p) ? __ldg(Win + p) : 0u; };
     uint64_t pin = 0, s = 0;
     for (int p = c0; p < c1; ++p) {
         const bool in = vin(p);
-        const uint32_t w = in ? __ldg(Win + p) : 0u;
         pin += in ? 1u : 0u;
-        s += w;
-        if (SM) ws[p] = w;
+        s += in ? __ldg(Win + p) : 0u;
         nx[p] = in ? 0u : cap;
     }
     uint64_t Pin;
@@ -369,6 +363,163 @@ __global__ void __launch_bounds__(kAllocThreads, 1) k_allocate(const uint32_t* _
         n[p] = np;
     }
     if (threadIdx.x == 0) off[P] = (uint32_t)tot;
+}
+
+// The same allocation on a cluster of kAllocCluster CTAs, for grids of up
+// to kAllocClusterMaxP probes: CTA r stages and works on the r-th slice of
+// the probes, so each pass's loops are kAllocCluster times shorter.  A
+// cluster-wide sum is the CTAs' block sums, published in their shared
+// memory and added by every thread in rank order after a cluster barrier
+// (integer sums: the same totals everywhere).  Every loop bound and break
+// below depends only on such totals, so all threads pass the same sequence
+// of barriers.  The partials are double-buffered: a CTA can run at most one
+// reduction ahead of the slowest reader.
+namespace cg = cooperative_groups;
+constexpr int kAllocCluster = 8;
+constexpr int kAllocClusterMaxP = kAllocCluster * 24576;  // 8 B a probe: at most 192 KB of shared memory per CTA
+
+struct ClusterSums {
+    uint64_t* slot;  // this CTA's partials: [2 buffers][4]
+    int buf;
+};
+
+__device__ __forceinline__ void cluster_sum2(cg::cluster_group& cl, ClusterSums& C, uint64_t* red, uint64_t& a,
+                                             uint64_t& b)
+{
+    block_sum2(a, b, red);
+    if (threadIdx.x == 0) C.slot[4 * C.buf] = a, C.slot[4 * C.buf + 1] = b;
+    cl.sync();
+    uint64_t ta = 0, tb = 0;
+    for (int r = 0; r < kAllocCluster; ++r) {
+        const uint64_t* rs = cl.map_shared_rank(C.slot, r);
+        ta += rs[4 * C.buf];
+        tb += rs[4 * C.buf + 1];
+    }
+    C.buf ^= 1;
+    a = ta;
+    b = tb;
+}
+
+__device__ __forceinline__ uint64_t cluster_exscan(cg::cluster_group& cl, ClusterSums& C, uint64_t* red, uint64_t v,
+                                                   uint64_t* total)
+{
+    uint64_t bt;
+    const uint64_t pre = block_exscan(v, red, &bt);
+    if (threadIdx.x == 0) C.slot[4 * C.buf + 2] = bt;
+    cl.sync();
+    const int me = (int)cl.block_rank();
+    uint64_t below = 0, all = 0;
+    for (int r = 0; r < kAllocCluster; ++r) {
+        const uint64_t t = cl.map_shared_rank(C.slot, r)[4 * C.buf + 2];
+        below += r < me ? t : 0ull;
+        all += t;
+    }
+    C.buf ^= 1;
+    *total = all;
+    return below + pre;
+}
+
+__global__ void __cluster_dims__(kAllocCluster, 1, 1) __launch_bounds__(kAllocThreads, 1)
+    k_allocate_cluster(const uint32_t* __restrict__ Win, int P, int avg, int m0, int rmax, uint32_t* __restrict__ n,
+                       uint32_t* __restrict__ off, const uint8_t* __restrict__ cls)
+{
+    cg::cluster_group cl = cg::this_cluster();
+    __shared__ uint64_t red[66];
+    __shared__ uint64_t slot[8];
+    extern __shared__ uint32_t stage[];  // [Pc] weights, then [Pc] extras of this CTA's slice
+    ClusterSums C{slot, 0};
+    const int rank = (int)cl.block_rank();
+    const int Pc = (P + kAllocCluster - 1) / kAllocCluster;
+    const int b0 = min(P, rank * Pc), b1 = min(P, b0 + Pc);
+    const int chunk = (b1 - b0 + kAllocThreads - 1) / kAllocThreads;
+    const int c0 = min(b1, b0 + (int)threadIdx.x * chunk), c1 = min(b1, c0 + chunk);
+    const uint32_t cap = (uint32_t)(rmax - m0);
+    uint32_t* ws = stage;
+    uint32_t* nx = stage + Pc;
+    auto vin = [&](int p) { return !cls || cls[p] == 2; };
+    uint64_t pin = 0, S = 0, zero = 0;
+    for (int p = c0; p < c1; ++p) {
+        const bool in = vin(p);
+        const uint32_t w = in ? __ldg(Win + p) : 0u;
+        pin += in ? 1u : 0u;
+        S += w;
+        ws[p - b0] = w;
+        nx[p - b0] = in ? 0u : cap;
+    }
+    uint64_t Pin;
+    const uint64_t rank0 = cluster_exscan(cl, C, red, pin, &Pin);  // V_in rank of this chunk's first V_in probe
+    cluster_sum2(cl, C, red, S, zero);
+    uint64_t E = (uint64_t)(avg - 8) * (uint64_t)P - (uint64_t)(m0 - 8) * Pin;
+    if (E > Pin * cap) E = Pin * cap;
+    if (S == 0) {  // uniform over V_in, the remainder to the lowest V_in ranks
+        const uint64_t q = Pin ? E / Pin : 0, r = Pin ? E % Pin : 0;
+        uint64_t rk = rank0;
+        for (int p = c0; p < c1; ++p) {
+            if (!vin(p)) continue;
+            nx[p - b0] = (uint32_t)(q + (rk < r ? 1u : 0u));
+            ++rk;
+        }
+    } else {
+        uint64_t Erem = E, SU = cap > 0u ? S : 0u;
+        for (int it = 0; it < kAllocIters; ++it) {
+            if (SU == 0 || Erem == 0) break;
+            const uint64_t inv = 0xFFFFFFFFFFFFFFFFull / SU;
+            uint64_t G = 0, su = 0;
+            for (int p = c0; p < c1; ++p) {
+                const uint32_t w = ws[p - b0], e = nx[p - b0];
+                if (w == 0u || e >= cap) continue;
+                const uint64_t share = div_by(Erem * (uint64_t)w, SU, inv);
+                const uint64_t room = cap - e;
+                const uint64_t a = share < room ? share : room;
+                nx[p - b0] = e + (uint32_t)a;
+                G += a;
+                if (a < room) su += w;
+            }
+            cluster_sum2(cl, C, red, G, su);
+            if (G == 0) break;
+            Erem -= G;
+            SU = su;
+        }
+        for (int guard = 0; Erem > 0 && guard < (1 << 20); ++guard) {
+            uint64_t ca = 0;
+            for (int p = c0; p < c1; ++p)
+                if (ws[p - b0] > 0u && nx[p - b0] < cap) ++ca;
+            cluster_sum2(cl, C, red, ca, zero);
+            const bool modeA = ca > 0;
+            uint64_t ce = 0;
+            for (int p = c0; p < c1; ++p)
+                if (nx[p - b0] < cap && (!modeA || ws[p - b0] > 0u)) ++ce;
+            uint64_t tot;
+            uint64_t pre = cluster_exscan(cl, C, red, ce, &tot);
+            if (tot == 0) break;
+            for (int p = c0; p < c1; ++p) {
+                if (nx[p - b0] < cap && (!modeA || ws[p - b0] > 0u)) {
+                    if (pre < Erem) nx[p - b0] += 1u;
+                    ++pre;
+                }
+            }
+            Erem -= tot < Erem ? tot : Erem;
+        }
+    }
+    auto rays_of = [&](int p) -> uint32_t {
+        if (vin(p)) return (uint32_t)m0 + nx[p - b0];
+        return cls[p] == 1 ? 8u : 0u;
+    };
+    uint64_t loc = 0;
+    for (int p = c0; p < c1; ++p) {
+        const uint32_t np = rays_of(p);
+        loc += np > 8u ? np - 8u : 0u;
+    }
+    uint64_t tot;
+    uint64_t pre = cluster_exscan(cl, C, red, loc, &tot);
+    for (int p = c0; p < c1; ++p) {
+        const uint32_t np = rays_of(p);
+        off[p] = (uint32_t)pre;
+        pre += np > 8u ? np - 8u : 0u;
+        n[p] = np;
+    }
+    if (rank == 0 && threadIdx.x == 0) off[P] = (uint32_t)tot;
+    cl.sync();  // no CTA leaves while another may still read its partials
 }
 
 // ============================================================== blend
@@ -1305,15 +1456,15 @@ cudaError_t launch_classify(const VolConst& V, const FrameDev* FD, const uint16_
 cudaError_t launch_allocate(const uint32_t* W, int P, int avg, int m0, int rmax, uint32_t* n_out, uint32_t* off_out,
                             cudaStream_t s, const uint8_t* cls)
 {
-    if (P <= kAllocStageMax) {
-        const int sm = 8 * P;
+    if (P <= kAllocClusterMaxP) {
+        const int sm = 8 * ((P + kAllocCluster - 1) / kAllocCluster);
         if (sm > 48 * 1024) {
-            cudaError_t e = cudaFuncSetAttribute(k_allocate<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+            cudaError_t e = cudaFuncSetAttribute(k_allocate_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
             if (e != cudaSuccess) return e;
         }
-        k_allocate<true><<<1, kAllocThreads, sm, s>>>(W, P, avg, m0, rmax, n_out, off_out, cls);
+        k_allocate_cluster<<<kAllocCluster, kAllocThreads, sm, s>>>(W, P, avg, m0, rmax, n_out, off_out, cls);
     } else {
-        k_allocate<false><<<1, kAllocThreads, 0, s>>>(W, P, avg, m0, rmax, n_out, off_out, cls);
+        k_allocate<<<1, kAllocThreads, 0, s>>>(W, P, avg, m0, rmax, n_out, off_out, cls);
     }
     count_launches(1);
     return cudaGetLastError();

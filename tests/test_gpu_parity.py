@@ -75,7 +75,7 @@ def _compare_update(gv, ov, frame, check_atlas=True, what=""):
 
 
 # ------------------------------------------------------------------ allocation
-@pytest.mark.parametrize("P", [1, 7, 64, 1000, 1025, 16384, 24576, 131072])
+@pytest.mark.parametrize("P", [1, 7, 64, 1000, 1025, 16384, 24576, 131072, 200000])  # the last: one block
 def test_allocation_bit_exact(adgi, P):
     rng = np.random.default_rng(P)
     cases = [
