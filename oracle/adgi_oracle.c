@@ -942,6 +942,7 @@ typedef struct {
     int dyn_ratio;        /* sampler = 1: > 0 adds the dynamic chains (Sec. "Adaptive sampling -  */
                           /* dynamic") with a static:dynamic budget split of dyn_ratio:1      */
     float hyst_dyn;       /* hysteresis of the dynamic rays' batch update */
+    float var_rel;        /* Chebyshev minimum variance relative to mu2 (0: the absolute floor alone) */
 } orc_desc;
 
 typedef struct {
@@ -1087,6 +1088,7 @@ EXPORT orc_vol* orc_create(const orc_desc* d, int nthreads)
     if (d->n_irr < 1 || d->n_dep < 1 || d->theta < 1) return NULL;
     int m0 = d->rmin > 8 ? d->rmin : 8;
     if (d->avg < m0 || d->avg > d->rmax) return NULL;
+    if (!(d->var_rel >= 0.0f && d->var_rel < 1.0f)) return NULL;
     orc_vol* v = (orc_vol*)calloc(1, sizeof(orc_vol));
     v->d = *d;
     v->P = d->dims[0] * d->dims[1] * d->dims[2];
@@ -1429,10 +1431,13 @@ static void query_point(const orc_vol* v, const double x[3], const double nrm[3]
         bilinear(v->dep + (size_t)p * v->Td * v->Td * 2, v->Td, v->d.n_dep, 2, dir, mom);
         double wc = 1.0;
         if (dist > mom[0]) {
-            /* one-sided Chebyshev bound with a minimum variance (as in variance
-               shadow maps): max(mu2 - mu^2, 1e-3 mu2, 1e-6 s^2) */
+            /* one-sided Chebyshev bound P(d >= dist) <= var / (var + (dist - mu)^2)
+               on the filtered moments (variance shadow maps, cited for g_c),
+               var = mu2 - mu^2 raised to the minimum variance 1e-6 s^2; a
+               volume may ask for a larger floor var_rel * mu2 */
             double var = mom[1] - mom[0] * mom[0];
-            double vfloor = 1e-3 * mom[1] > varmin ? 1e-3 * mom[1] : varmin;
+            double vrel = (double)v->d.var_rel * mom[1];
+            double vfloor = vrel > varmin ? vrel : varmin;
             if (var < vfloor) var = vfloor;
             double dd = dist - mom[0];
             wc = var / (var + dd * dd);

@@ -32,6 +32,7 @@ class OrcDesc(C.Structure):
         ("blend_mode", C.c_int),
         ("dyn_ratio", C.c_int),
         ("hyst_dyn", C.c_float),
+        ("var_rel", C.c_float),
     ]
 
 
@@ -374,7 +375,7 @@ class OracleVolume:
 
     def __init__(self, origin, spacing, dims, n_irr=6, n_dep=14, rays_avg=64, rays_min=8, rays_max=256,
                  hysteresis=0.97, depth_max=0.0, theta=16, threads=None, packed=False, sampler=0, alpha=1.0,
-                 dyn_ratio=0, hyst_dyn=0.91, blend_mode=0):
+                 dyn_ratio=0, hyst_dyn=0.91, blend_mode=0, cheb_var_floor_rel=0.0):
         d = OrcDesc()
         d.origin[:] = [float(x) for x in origin]
         d.spacing[:] = [float(x) for x in spacing]
@@ -391,6 +392,7 @@ class OracleVolume:
         d.blend_mode = int(blend_mode)
         d.dyn_ratio = int(dyn_ratio)
         d.hyst_dyn = float(hyst_dyn)
+        d.var_rel = float(cheb_var_floor_rel)
         self.desc = d
         if threads is None:
             threads = os.cpu_count() or 1

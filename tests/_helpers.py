@@ -33,7 +33,8 @@ def oracle_volume(O, w, **over):
                        vd["rays_avg"], vd["rays_min"], vd["rays_max"], vd["hysteresis"], vd["depth_max"],
                        vd["tr_theta"], packed=int(vd.get("atlas_fp16", 0)) == 3, sampler=int(vd.get("sampler", 0)),
                        alpha=float(vd.get("alpha", 1.0)), dyn_ratio=int(vd.get("dyn_ratio", 0)),
-                       hyst_dyn=float(vd.get("hysteresis_dyn", 0.91)), blend_mode=int(vd.get("blend_mode", 0)))
+                       hyst_dyn=float(vd.get("hysteresis_dyn", 0.91)), blend_mode=int(vd.get("blend_mode", 0)),
+                       cheb_var_floor_rel=float(vd.get("cheb_var_floor_rel", 0.0)))
     v.set_scene(w.verts, w.idx, w.albedo)
     return v
 

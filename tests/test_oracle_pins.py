@@ -4,7 +4,9 @@ Each test checks the oracle against something other than itself: published
 test vectors, closed forms, invariants, special cases that reduce to a
 textbook result, or brute force on tiny inputs.
 """
+import itertools
 import math
+from fractions import Fraction
 
 import numpy as np
 import pytest
@@ -317,6 +319,67 @@ def test_allocation_invariants_random():
             assert np.all(np.abs((n - m0) - share) < 2.0 + 1e-9)
 
 
+def _waterfill_exact(W, E, cap):
+    """The continuous water-filling of E extra rays: x_p = min(cap, lam W_p)
+    with sum x = E, found by brute force over every candidate capped set of
+    the probes with W_p > 0 (exact rational arithmetic).  Returns x, or None
+    when every weighted probe is capped (the rest then goes to W = 0 probes)."""
+    P = len(W)
+    pos = [p for p in range(P) if W[p] > 0]
+    found = None
+    for r in range(len(pos) + 1):
+        for C in itertools.combinations(pos, r):
+            Er = E - cap * len(C)
+            U = [p for p in pos if p not in C]
+            SU = sum(int(W[p]) for p in U)
+            if Er < 0 or SU == 0:
+                continue
+            lam = Fraction(Er, SU)
+            if all(lam * int(W[p]) >= cap for p in C) and all(lam * int(W[p]) <= cap for p in U):
+                x = [Fraction(cap) if p in C else lam * int(W[p]) for p in range(P)]
+                assert found is None or found == x  # the water level is unique
+                found = x
+    return found
+
+
+def test_allocation_brute_force_waterfill():
+    # P <= 8: the integer allocation against the exact continuous
+    # water-filling share x_p of the extra rays (the fixed budget spread in
+    # proportion to W_p, capped at rays_max; Sec. 3.4 fixes the budget).  The
+    # proportional passes hand out floors of the shares, and the residual
+    # (fewer rays than probes after the first pass) goes one ray at a time in
+    # index order, so no probe may drift by 3 or more rays from x_p; probes
+    # with W = 0 take nothing while a weighted probe is below its cap.
+    rng = np.random.default_rng(11)
+    checked = 0
+    for trial in range(3000):
+        P = int(rng.integers(1, 9))
+        rmax = int(rng.integers(8, 40))
+        avg = int(rng.integers(8, rmax + 1))
+        kind = trial % 4
+        if kind == 0:
+            W = rng.integers(0, 50, P)
+        elif kind == 1:
+            W = rng.integers(0, 3, P)
+        elif kind == 2:
+            W = np.where(rng.random(P) < 0.3, rng.integers(1, 1 << 24, P), 0)
+        else:
+            W = rng.integers(0, 1 << 32, P, dtype=np.uint64)
+        W = W.astype(np.uint32)
+        n = _alloc_checks(W, avg, 8, rmax)
+        extra = n.astype(np.int64) - 8
+        E, cap = (avg - 8) * P, rmax - 8
+        x = _waterfill_exact(W, E, cap)
+        if x is None:
+            continue
+        checked += 1
+        dev = [abs(Fraction(int(extra[p])) - x[p]) for p in range(P)]
+        assert max(dev) < 3, (W, avg, rmax, extra, [float(v) for v in x])
+        if any(W[p] > 0 and extra[p] < cap for p in range(P)):
+            assert all(extra[p] == 0 for p in range(P) if W[p] == 0), (W, extra)
+    assert checked > 2000
+
+
 # --------------------------------------------------------------- heuristics
 def test_luts_closed_forms_and_no_boundary_ambiguity():
     s = math.sqrt(12.0)
@@ -508,7 +571,10 @@ def test_sphere_depth_moments():
     lo = r * math.cos(math.pi / 64) * math.cos(math.pi / 32)
     assert (mu <= r * (1 + 1e-6)).all() and (mu >= lo * (1 - 1e-6)).all()
     assert abs(mu.mean() - r) < 2e-3 * r
-    assert np.max(np.abs(mu2 - mu * mu)) < 1e-3 * r * r
+    # every sample of a texel lies in [lo, r], so its variance is at most
+    # (r - lo)^2 / 4 ~ 1e-5 r^2: the texel variance is ~0 at 1e-4 r^2
+    assert (r - lo) ** 2 / 4 < 1e-4 * r * r
+    assert np.max(np.abs(mu2 - mu * mu)) < 1e-4 * r * r
 
 
 def test_direct_light_closed_form_and_shadow():
@@ -570,8 +636,9 @@ def test_backface_hits_are_black():
 
 
 # --------------------------------------------------------------- query
-def _query_volume(values, depth_mu, depth_mu2=None):
-    v = O.OracleVolume((0, 0, 0), (1, 1, 1), (2, 2, 2), rays_avg=8, rays_min=8, rays_max=8)
+def _query_volume(values, depth_mu, depth_mu2=None, cheb_var_floor_rel=0.0):
+    v = O.OracleVolume((0, 0, 0), (1, 1, 1), (2, 2, 2), rays_avg=8, rays_min=8, rays_max=8,
+                       cheb_var_floor_rel=cheb_var_floor_rel)
     P = 8
     irr = np.zeros((P, v.Ti, v.Ti, 3))
     dep = np.zeros((P, v.Td, v.Td, 2))
@@ -608,28 +675,47 @@ def test_query_equal_probes_and_trilinear():
 
 def test_query_chebyshev_weight():
     # probe 0 sees a wall at mean depth 0.1 with zero variance: for a point at
-    # distance d > mu its weight is scaled by var/(var + (d-mu)^2), var floored
-    # at max(1e-3 mu2, 1e-6 s^2) (one-sided Chebyshev bound with the minimum
-    # variance of variance shadow maps).
+    # distance d > mu its weight is scaled by var/(var + (d-mu)^2), the
+    # one-sided Chebyshev bound of variance shadow maps, with var raised to
+    # the minimum 1e-6 s^2 (s^2 = 3 here).  A volume may opt in to a further
+    # floor r * mu2; at r = 1e-3 that floor (1e-5) is above 1e-6 s^2 here, so
+    # the two settings must give different weights.
     rng = np.random.default_rng(7)
     vals = rng.uniform(0, 5, (8, 3))
     mu = [0.1] + [10.0] * 7
-    v = _query_volume(list(vals), mu)
     s2 = 3.0
     x = np.array([0.5, 0.25, 0.4])
-    q = v.query(x[None].astype(np.float32), np.array([[0, 0, 1]], np.float32))[0]
     xf = x.astype(np.float32).astype(np.float64)
+    got = {}
+    for rel in (0.0, 1e-3):
+        v = _query_volume(list(vals), mu, cheb_var_floor_rel=rel)
+        q = v.query(x[None].astype(np.float32), np.array([[0, 0, 1]], np.float32))[0]
+        ref_w = []
+        for c in range(8):
+            o = [(c >> k) & 1 for k in range(3)]
+            w = np.prod([xf[k] if o[k] else 1 - xf[k] for k in range(3)])
+            if c == 0:
+                d = np.linalg.norm(xf)
+                var = max(rel * 0.1 ** 2, 1e-6 * s2)
+                w *= var / (var + (d - 0.1) ** 2)
+            ref_w.append(w)
+        ref_w = np.array(ref_w)
+        np.testing.assert_allclose(q, (ref_w[:, None] * vals).sum(0) / ref_w.sum(), rtol=1e-12)
+        got[rel] = q
+    assert np.max(np.abs(got[0.0] - got[1e-3])) > 1e-6 * np.max(np.abs(got[0.0]))
+    # a positive variance above both floors is used as it is
+    v = _query_volume(list(vals), mu, depth_mu2=[0.1 ** 2 + 0.02] + [100.0] * 7)
+    q = v.query(x[None].astype(np.float32), np.array([[0, 0, 1]], np.float32))[0]
     ref_w = []
     for c in range(8):
         o = [(c >> k) & 1 for k in range(3)]
         w = np.prod([xf[k] if o[k] else 1 - xf[k] for k in range(3)])
         if c == 0:
             d = np.linalg.norm(xf)
-            var = max(1e-3 * 0.1 ** 2, 1e-6 * s2)
-            w *= var / (var + (d - 0.1) ** 2)
+            w *= 0.02 / (0.02 + (d - 0.1) ** 2)
         ref_w.append(w)
     ref_w = np.array(ref_w)
-    np.testing.assert_allclose(q, (ref_w[:, None] * vals).sum(0) / ref_w.sum(), rtol=1e-12)
+    np.testing.assert_allclose(q, (ref_w[:, None] * vals).sum(0) / ref_w.sum(), rtol=1e-10)
 
 
 # --------------------------------------------------------------- packed atlases
