@@ -55,7 +55,7 @@ extern "C" {
 #define ADGI_ERR_OVER_BUDGET (-3) /* the volume does not fit the memory budget */
 #define ADGI_ERR_NO_SCENE (-4)    /* adgi_update() before adgi_set_scene() */
 #define ADGI_ERR_CUDA (-5)        /* a CUDA call failed (message in adgi_last_error) */
-#define ADGI_ERR_TIMEOUT (-6)     /* a bounded device-side wait gave up */
+#define ADGI_ERR_TIMEOUT (-6)     /* a bounded wait gave up (adgi_server_drain) */
 
 typedef struct adgi_volume_s* adgi_volume;
 
@@ -108,6 +108,13 @@ typedef struct {
                                n . w > 0 (tested in FP32), the visibility texel the (n . w)^50-weighted
                                mean of {d, d^2}; the number of rays with n . w > 0 is the batch count
                                of the moving average.  Only with sampler = 0 and atlas_fp16 < 3 */
+    float cheb_var_floor_rel; /* the query's Chebyshev visibility weight var / (var + (d - mu)^2)
+                               (one-sided bound on the filtered depth moments, as in variance shadow
+                               maps, which the paper cites for g_c) takes var = mu2 - mu^2 raised to at
+                               least 1e-6 s^2 (s the voxel diagonal).  A value r > 0 raises it further
+                               to r * mu2: an opt-in for reduced-precision (half) atlases, whose stored
+                               moments carry an error of about 1e-3 mu2.  0 (the default): the absolute
+                               floor alone.  In [0, 1) */
 } adgi_volume_desc;
 
 /* kind 0: point light at pos_or_dir with intensity rgb (irradiance rgb/d^2);
@@ -191,7 +198,7 @@ int adgi_move_vertices(adgi_volume vol, int32_t first, int32_t count, const floa
 
 /* Run one per-frame update (steps 1-6 above) on the volume's stream.  Host
  * data of *frame is copied before return; the call does not wait for the
- * device.  Errors: INVALID_ARG, NO_SCENE, CUDA, TIMEOUT. */
+ * device.  Errors: INVALID_ARG, NO_SCENE, CUDA. */
 int adgi_update(adgi_volume vol, const adgi_frame* frame);
 
 /* Irradiance query at n points with normals (float[3*n] each): 8-probe
@@ -281,6 +288,9 @@ int adgi_enable_timing(adgi_volume vol, int32_t enable);
  *   ADGI_STATE_DEP      float[P][Td][Td][2] {mean, variance} of the depth samples (the
  *                       second moment is variance + mean^2); half[...][2] when atlas_fp16
  *                       is 1 or 2; uint32[P][Td][Td] packed texels when it is 3
+ *   ADGI_STATE_DEP_MOMENTS double[P][Td][Td][2] the depth atlas as the moments {mean, mean^2}
+ *                       (mean^2 = variance + mean^2 of the stored texel, formed in FP64);
+ *                       FP32 and half atlases only (INVALID_ARG when atlas_fp16 is 3)
  *   ADGI_STATE_DEP_N    uint8[P][Td][Td]  depth sample counts (unused with packed texels,
  *                       which carry their own count)
  *   ADGI_STATE_ROT      float[9]          main-ray rotation of the last update
@@ -353,7 +363,8 @@ enum {
     ADGI_STATE_DYN_OFF = 31,
     ADGI_STATE_DYN_HIT = 32,
     ADGI_STATE_DYN_REC = 33,
-    ADGI_STATE_CLS = 34
+    ADGI_STATE_CLS = 34,
+    ADGI_STATE_DEP_MOMENTS = 35
 };
 int adgi_state_bytes(adgi_volume vol, int32_t which, uint64_t* bytes);
 int adgi_read_state(adgi_volume vol, int32_t which, void* dst_host, uint64_t bytes);
@@ -418,12 +429,16 @@ int adgi_build_bvh(const float* verts, int32_t n_verts, const int32_t* tri_idx, 
  *   - the scratch is one fixed device array inside the library (about
  *     2.6 MiB), held on every GPU that loads the library until exit; the call
  *     performs no cudaMalloc, cudaFree or other allocating routine;
- *   - the first call on a device looks up that array's device address (set-up,
- *     once per device); make it before any stream capture begins;
+ *   - each call looks up that array's device address in the calling thread's
+ *     current CUDA context (cudaGetSymbolAddress; nothing is allocated once
+ *     the library's device code is loaded there, which the first call in a
+ *     context may do), so any context works, also after a device reset;
  *   - every call shares the array, which keeps the last call's contents (each
  *     call clears what must start at zero); calls whose GPU work overlaps
  *     (other streams, other host threads) race on it: order them on one
- *     stream or serialise them. */
+ *     stream or serialise them;
+ *   - the call reads the build's error word back and synchronises the stream,
+ *     so it must not be called while that stream is being captured. */
 #define ADGI_BVH_NOALLOC_MAX_TRIS 32768
 int adgi_build_bvh_noalloc(const float* verts, int32_t n_verts, const int32_t* tri_idx, int32_t n_tris, float eps,
                            void* nodes_out, void* tris_out, void* cuda_stream);

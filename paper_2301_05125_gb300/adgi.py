@@ -20,7 +20,7 @@ STATE = dict(W=0, N=1, OFF=2, QV=3, QR=4, TRV=5, TRR=6, PILOT_HIT=7, PILOT_REC=8
              MAIN_REC=11, IRR=12, DEP=13, DEP_N=14, ROT=15, BVH_NODES=16, BVH_TRIS=17, MOVING_BVH_NODES=18,
              MOVING_BVH_TRIS=19, MH_CHAINS=20, MH_SAMPLES=21, MH_ORDER=22, MH_OFF=23, MH_HIT_NEG=24,
              QD=25, DYN_CHAINS=26, DYN_SAMPLES=27, DYN_CELLS=28, DYN_FIRST=29, DYN_INCL=30, DYN_OFF=31, DYN_HIT=32,
-             DYN_REC=33, CLS=34)
+             DYN_REC=33, CLS=34, DEP_MOMENTS=35)
 
 
 class AdgiError(RuntimeError):
@@ -48,6 +48,7 @@ class adgi_volume_desc(C.Structure):
         ("dyn_ratio", C.c_int32),
         ("hysteresis_dyn", C.c_float),
         ("blend_mode", C.c_int32),
+        ("cheb_var_floor_rel", C.c_float),
     ]
 
 
@@ -398,7 +399,8 @@ def adgi_last_error() -> str:
 # ------------------------------------------------------------ convenience
 def make_desc(origin, spacing, dims, irr_interior=6, depth_interior=14, rays_avg=64, rays_min=8, rays_max=256,
               hysteresis=0.97, depth_max=0.0, atlas_fp16=0, tr_theta=16, sampler=0,
-              alpha=1.0, dyn_ratio=0, hysteresis_dyn=0.91, blend_mode=0) -> adgi_volume_desc:
+              alpha=1.0, dyn_ratio=0, hysteresis_dyn=0.91, blend_mode=0,
+              cheb_var_floor_rel=0.0) -> adgi_volume_desc:
     d = adgi_volume_desc()
     d.origin[:] = [float(x) for x in origin]
     d.spacing[:] = [float(x) for x in spacing]
@@ -414,6 +416,7 @@ def make_desc(origin, spacing, dims, irr_interior=6, depth_interior=14, rays_avg
     d.dyn_ratio = int(dyn_ratio)
     d.hysteresis_dyn = float(hysteresis_dyn)
     d.blend_mode = int(blend_mode)
+    d.cheb_var_floor_rel = float(cheb_var_floor_rel)
     return d
 
 
@@ -616,10 +619,9 @@ class Volume:
         return self.state("DEP", dt).reshape(self.P, self.Td, self.Td, 2).astype(np.float32)
 
     def dep_moments(self):
-        """depth atlas as {mean, mean^2} (the library stores {mean, variance})."""
-        d = self.dep().astype(np.float64)
-        d[..., 1] = d[..., 1] + d[..., 0] * d[..., 0]
-        return d
+        """depth atlas as the moments {mean, mean^2} (the library stores
+        {mean, variance}; the C ABI forms mean^2 in FP64)."""
+        return self.state("DEP_MOMENTS", np.float64).reshape(self.P, self.Td, self.Td, 2)
 
     def dep_n(self):
         return self.state("DEP_N", np.uint8).reshape(self.P, self.Td, self.Td)

@@ -86,7 +86,8 @@ struct VolConst {
     float depth_max;
     float qv_scale;         // (float)(256 / s)
     float qc_scale;         // (float)(64 / s)
-    float var_min;          // (float)(1e-6 * s^2)
+    float var_min;          // (float)(1e-6 * s^2): the Chebyshev minimum variance
+    float var_rel;          // optional further floor var_rel * mu2 (0: none)
     float hyst;
     int theta;
     int m0, rays_max, rays_avg;
@@ -624,7 +625,7 @@ __device__ __forceinline__ void depth_moments(const VolConst& V, const void* dep
     filter_moments(w00, w01, w10, w11, v00, v01, v10, v11, mom);
     // conditioning of the filtered variance against the fractions: what a
     // texel adds to the variance per unit weight, over the floored variance
-    float var = fmaxf(mom[1], fmaxf(1e-3f * (mom[1] + mom[0] * mom[0]), V.var_min));
+    float var = fmaxf(mom[1], fmaxf(V.var_rel * (mom[1] + mom[0] * mom[0]), V.var_min));
     float d00 = v00.x - mom[0], d01 = v01.x - mom[0], d10 = v10.x - mom[0], d11 = v11.x - mom[0];
     float s2 = fmaxf(fmaxf(v00.y + d00 * d00, v01.y + d01 * d01), fmaxf(v10.y + d10 * d10, v11.y + d11 * d11));
     *cond = __fdividef(s2, var);
@@ -777,9 +778,9 @@ __device__ __forceinline__ float3 query_irr_at(const VolConst& V, const void* ir
         }
         float wc = 1.f;
         if (dist > mom[0]) {
-            // minimum variance: max(1e-3 mu2, 1e-6 s^2), mu2 = var + mean^2,
-            // keeps the weight well conditioned at the precision of the moments
-            float var = fmaxf(mom[1], fmaxf(1e-3f * (mom[1] + mom[0] * mom[0]), V.var_min));
+            // one-sided Chebyshev bound with the minimum variance 1e-6 s^2,
+            // or var_rel * mu2 (mu2 = var + mean^2) where a volume asks for it
+            float var = fmaxf(mom[1], fmaxf(V.var_rel * (mom[1] + mom[0] * mom[0]), V.var_min));
             float dd = dist - mom[0];
             wc = __fdividef(var, var + dd * dd);
         }

@@ -20,6 +20,7 @@ namespace {
 constexpr int kSortThreads = 256;
 constexpr int kSortItems = 16;
 constexpr int kSortTile = kSortThreads * kSortItems;
+static_assert(kSortTile == kBvhSortTile, "the scratch layout in bvh.cuh counts histograms per radix tile");
 
 __device__ __forceinline__ uint32_t f2ord(float f)
 {
@@ -799,7 +800,7 @@ size_t carve_bvh_scratch(void* base, int nt, BvhBufs& B)
     B.hist = (uint32_t*)take(sizeof(uint32_t) * 256 * nb);
     B.bounds = (uint32_t*)take(sizeof(uint32_t) * 8);
     B.err = (int*)take(sizeof(int) * 2);
-    return off;
+    return off;  // == bvh_scratch_layout_bytes(nt), the same pieces in the same order
 }
 
 size_t radix_hist_entries(int n) { return 256 * (size_t)((std::max(n, 1) + kSortTile - 1) / kSortTile); }

@@ -33,6 +33,20 @@ struct PlocBufs {
     uint64_t* total = nullptr;
 };
 
+// Bytes of the scratch block carve_bvh_scratch() cuts for a linear build of
+// nt triangles: the listed triangles (48 B each), parent links and flags
+// (3 x 4 B), sort keys (2 x 8 B) and values (2 x 4 B), one 256-bin histogram
+// per radix tile of kBvhSortTile keys, the centroid bounds and the error
+// word, every piece rounded up to 256 bytes.
+constexpr int kBvhSortTile = 4096;
+constexpr size_t bvh_r256(size_t b) { return (b + 255) & ~(size_t)255; }
+constexpr size_t bvh_scratch_layout_bytes(size_t nt)
+{
+    const size_t n = nt > 0 ? nt : 1;
+    return bvh_r256(48 * n) + 3 * bvh_r256(4 * n) + 2 * bvh_r256(8 * n) + 2 * bvh_r256(4 * n) +
+           bvh_r256(4 * 256 * ((n + kBvhSortTile - 1) / kBvhSortTile)) + bvh_r256(4 * 8) + bvh_r256(4 * 2);
+}
+
 size_t bvh_scratch_bytes(int nt);
 size_t radix_hist_entries(int n);
 cudaError_t scan_exclusive_u32(uint32_t* a, int n, uint32_t* part, cudaStream_t s);

@@ -368,6 +368,8 @@ int validate_desc(const adgi_volume_desc* d)
         return fail(ADGI_ERR_INVALID_ARG, "hysteresis_dyn in [0,1)");
     if (d->blend_mode < 0 || d->blend_mode > 1 || (d->blend_mode == 1 && (d->sampler != 0 || d->atlas_fp16 == 3)))
         return fail(ADGI_ERR_INVALID_ARG, "blend_mode in {0,1}; the cosine gather needs sampler 0 and atlas_fp16 < 3");
+    if (!(d->cheb_var_floor_rel >= 0.0f && d->cheb_var_floor_rel < 1.0f))
+        return fail(ADGI_ERR_INVALID_ARG, "cheb_var_floor_rel in [0,1)");
     int64_t P = (int64_t)d->dims[0] * d->dims[1] * d->dims[2];
     if (P * (int64_t)d->rays_avg >= (int64_t)1 << 31) return fail(ADGI_ERR_INVALID_ARG, "ray budget too large");
     return ADGI_OK;
@@ -432,6 +434,7 @@ int adgi_create_volume(const adgi_volume_desc* desc, void* cuda_stream, adgi_vol
     V.qv_scale = (float)(256.0 / v->s);
     V.qc_scale = (float)(64.0 / v->s);
     V.var_min = (float)(1e-6 * v->s * v->s);
+    V.var_rel = d.cheb_var_floor_rel;
     V.hyst = d.hysteresis;
     V.theta = d.tr_theta;
     V.m0 = d.rays_min > 8 ? d.rays_min : 8;
@@ -1500,6 +1503,10 @@ int adgi_state_bytes(adgi_volume v, int32_t which, uint64_t* bytes)
     case ADGI_STATE_IRR: *bytes = P * ti2 * (v->V.fp16 == 3 ? 4 : v->V.fp16 ? 8 : 16); break;
     case ADGI_STATE_DEP: *bytes = P * td2 * (v->V.fp16 ? 4 : 8); break;
     case ADGI_STATE_DEP_N: *bytes = P * td2; break;
+    case ADGI_STATE_DEP_MOMENTS:
+        if (v->V.fp16 == 3) return fail(ADGI_ERR_INVALID_ARG, "DEP_MOMENTS: packed atlases hold codes (read DEP)");
+        *bytes = P * td2 * 16;
+        break;
     case ADGI_STATE_ROT: *bytes = 36; break;
     case ADGI_STATE_BVH_NODES: *bytes = 64 * (uint64_t)(v->ns > 1 ? v->ns - 1 : 1); break;
     case ADGI_STATE_BVH_TRIS: *bytes = 48 * (uint64_t)v->ns; break;
@@ -1558,6 +1565,28 @@ int adgi_read_state(adgi_volume v, int32_t which, void* dst, uint64_t bytes)
     CK(cudaStreamSynchronize(v->stream));
     if (which == ADGI_STATE_ROT) {
         std::memcpy(dst, v->R, 36);
+        return ADGI_OK;
+    }
+    if (which == ADGI_STATE_DEP_MOMENTS) {  // {mean, variance} -> {mean, variance + mean^2} in FP64
+        const size_t n = (size_t)v->V.P * v->V.Td * v->V.Td;
+        double* out = static_cast<double*>(dst);
+        if (v->V.fp16) {
+            std::vector<__half> h(2 * n);
+            CK(cudaMemcpy(h.data(), v->dep, h.size() * sizeof(__half), cudaMemcpyDeviceToHost));
+            for (size_t i = 0; i < n; ++i) {
+                const double m = (double)__half2float(h[2 * i]), var = (double)__half2float(h[2 * i + 1]);
+                out[2 * i] = m;
+                out[2 * i + 1] = var + m * m;
+            }
+        } else {
+            std::vector<float> f(2 * n);
+            CK(cudaMemcpy(f.data(), v->dep, f.size() * sizeof(float), cudaMemcpyDeviceToHost));
+            for (size_t i = 0; i < n; ++i) {
+                const double m = (double)f[2 * i], var = (double)f[2 * i + 1];
+                out[2 * i] = m;
+                out[2 * i + 1] = var + m * m;
+            }
+        }
         return ADGI_OK;
     }
     const void* src = nullptr;

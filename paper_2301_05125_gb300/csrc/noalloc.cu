@@ -14,16 +14,20 @@
 //   * every GPU that loads this library holds the array (kNoallocScratchBytes,
 //     about 2.6 MiB) until the process exits;
 //   * host code cannot use the array's name as a device address (on the host
-//     it is only a stand-in symbol), so the first call on each device looks the
-//     address up with cudaGetSymbolAddress while that device is current and
-//     keeps it; make that first call before any stream capture begins;
+//     it is only a stand-in symbol), so each call looks the address up with
+//     cudaGetSymbolAddress in the context current on the calling thread and
+//     checks the result.  The lookup allocates nothing once the library's
+//     device code is loaded in that context (the first call in a context may
+//     load it), and it is right in any context, primary or not, and after a
+//     cudaDeviceReset;
 //   * all calls share the one array and it keeps the last call's contents;
 //     each call re-initialises what must start at zero (flags, bounds, error
 //     word) on its own stream;
 //   * two calls whose work overlaps on the GPU (different streams, or host
 //     threads racing) corrupt each other's scratch: order them on one stream
-//     or serialise them.
-#include <mutex>
+//     or serialise them;
+//   * a call reads the build's error word back and synchronises its stream,
+//     so it must not be called while that stream is being captured.
 #include <string>
 
 #include "adgi_internal.cuh"
@@ -37,22 +41,12 @@ using namespace adgi;
 
 namespace {
 
-// Scratch layout of carve_bvh_scratch() for kMaxTris triangles: each piece is
-// rounded up to 256 bytes.
-constexpr size_t r256(size_t b) { return (b + 255) & ~(size_t)255; }
-constexpr size_t scratch_bytes_for(size_t n)
-{
-    return r256(48 * n) + 3 * r256(4 * n) + 2 * r256(8 * n) + 2 * r256(4 * n) + r256(1024 * ((n + 4095) / 4096)) +
-           r256(32) + r256(8);
-}
 constexpr int kMaxTris = ADGI_BVH_NOALLOC_MAX_TRIS;
-constexpr size_t kNoallocScratchBytes = scratch_bytes_for(kMaxTris);
+// the layout carve_bvh_scratch() cuts for kMaxTris triangles
+constexpr size_t kNoallocScratchBytes = bvh_scratch_layout_bytes(kMaxTris);
+static_assert(kNoallocScratchBytes < (3u << 20), "the fixed scratch stays a modest static array");
 
 static __device__ __align__(256) unsigned char g_bvh_scratch[kNoallocScratchBytes];
-
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-void* g_addr[kMaxDevices] = {};
 
 }  // namespace
 
@@ -69,32 +63,18 @@ extern "C" int adgi_build_bvh_noalloc(const float* verts, int32_t nv, const int3
         return ADGI_ERR_INVALID_ARG;
     }
     if (nt == 0) return ADGI_OK;
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
-        noalloc_fail(std::string("adgi_build_bvh_noalloc: no usable current device: ") + cudaGetErrorString(e));
-        return ADGI_ERR_CUDA;
-    }
+    // the array's device address in the calling thread's current context
     void* base = nullptr;
-    {
-        std::lock_guard<std::mutex> lock(g_mu);
-        if (!g_addr[dev]) {
-            // set-up, once per device, with that device current
-            void* p = nullptr;
-            e = cudaGetSymbolAddress(&p, g_bvh_scratch);
-            if (e != cudaSuccess || !p) {
-                noalloc_fail(std::string("adgi_build_bvh_noalloc: cudaGetSymbolAddress failed: ") +
-                             cudaGetErrorString(e));
-                return ADGI_ERR_CUDA;
-            }
-            g_addr[dev] = p;
-        }
-        base = g_addr[dev];
+    cudaError_t e = cudaGetSymbolAddress(&base, g_bvh_scratch);
+    if (e != cudaSuccess || !base) {
+        noalloc_fail(std::string("adgi_build_bvh_noalloc: cudaGetSymbolAddress failed: ") + cudaGetErrorString(e));
+        return ADGI_ERR_CUDA;
     }
     cudaStream_t s = (cudaStream_t)cuda_stream;
     BvhBufs B;
-    if (carve_bvh_scratch(nullptr, nt, B) > kNoallocScratchBytes) {
-        noalloc_fail("adgi_build_bvh_noalloc: scratch layout exceeds the fixed array");
+    const size_t need = carve_bvh_scratch(nullptr, nt, B);
+    if (need != bvh_scratch_layout_bytes((size_t)nt) || need > kNoallocScratchBytes) {
+        noalloc_fail("adgi_build_bvh_noalloc: scratch layout does not fit the fixed array");
         return ADGI_ERR_INVALID_ARG;
     }
     carve_bvh_scratch(base, nt, B);

@@ -1,5 +1,8 @@
 // update.cu -- heuristics, ray allocation, blend and query kernels (sm_103a).
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <utility>
 
 #include <cooperative_groups.h>
 
@@ -1453,15 +1456,34 @@ cudaError_t launch_classify(const VolConst& V, const FrameDev* FD, const uint16_
     return cudaGetLastError();
 }
 
+// The dynamic shared-memory limit of a kernel is one attribute per device,
+// shared by every launch in the process, graphs captured earlier included.
+// It is only ever raised: lowering it for a small volume could invalidate a
+// launch or a graph made for a larger one.
+static cudaError_t raise_smem_limit(const void* func, size_t bytes)
+{
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    static std::mutex mu;
+    static std::map<std::pair<int, const void*>, size_t> limit;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> g(mu);
+    size_t& cur = limit[{dev, func}];
+    if (bytes <= cur) return cudaSuccess;
+    e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) cur = bytes;
+    return e;
+}
+
 cudaError_t launch_allocate(const uint32_t* W, int P, int avg, int m0, int rmax, uint32_t* n_out, uint32_t* off_out,
                             cudaStream_t s, const uint8_t* cls)
 {
     if (P <= kAllocClusterMaxP) {
         const int sm = 8 * ((P + kAllocCluster - 1) / kAllocCluster);
-        if (sm > 48 * 1024) {
-            cudaError_t e = cudaFuncSetAttribute(k_allocate_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-            if (e != cudaSuccess) return e;
-        }
+        // the limit for the largest grid the cluster kernel takes, set once
+        cudaError_t e = raise_smem_limit((const void*)k_allocate_cluster, 8 * (kAllocClusterMaxP / kAllocCluster));
+        if (e != cudaSuccess) return e;
         k_allocate_cluster<<<kAllocCluster, kAllocThreads, sm, s>>>(W, P, avg, m0, rmax, n_out, off_out, cls);
     } else {
         k_allocate<<<1, kAllocThreads, 0, s>>>(W, P, avg, m0, rmax, n_out, off_out, cls);
@@ -1476,8 +1498,8 @@ cudaError_t launch_blend_plan(const VolConst& V, const FrameDev* FD, const float
     const int M = V.rays_max - kPilots;
     if (M <= 0) return cudaSuccess;
     const size_t ps = blend_plan_smem(V);
-    if (ps > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k_blend_plan, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ps);
+    {
+        cudaError_t e = raise_smem_limit((const void*)k_blend_plan, ps);
         if (e != cudaSuccess) return e;
     }
     k_blend_plan<<<M, 256, ps, s>>>(V, FD, sf, plan);
@@ -1491,8 +1513,8 @@ cudaError_t launch_blend(const VolConst& V, const FrameDev* FD, const BlendBufs&
     const size_t per = blend_smem_bytes(V);
     const int wpb = std::max(1, std::min(T.blend_block / 32, (int)((227u * 1024u) / per)));
     const size_t sm = per * (size_t)wpb;
-    if (sm > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k_blend, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    {
+        cudaError_t e = raise_smem_limit((const void*)k_blend, sm);
         if (e != cudaSuccess) return e;
     }
     k_blend<<<(V.P + wpb - 1) / wpb, 32 * wpb, sm, s>>>(V, FD, B);
@@ -1506,8 +1528,8 @@ cudaError_t launch_blend_cos(const VolConst& V, const FrameDev* FD, const BlendB
     const size_t per = cos_layout(V.Ti, V.Td).total;
     const int wpb = std::max(1, std::min(4, (int)((227u * 1024u) / per)));
     const size_t sm = per * (size_t)wpb;
-    if (sm > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k_blend_cos, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    {
+        cudaError_t e = raise_smem_limit((const void*)k_blend_cos, sm);
         if (e != cudaSuccess) return e;
     }
     k_blend_cos<<<(V.P + wpb - 1) / wpb, 32 * wpb, sm, s>>>(V, FD, B);
@@ -1520,8 +1542,8 @@ cudaError_t launch_mh_blend(const VolConst& V, const FrameDev* FD, const MhBlend
     const size_t per = mh_layout(V.Ti, V.Td, V.dyn != 0).total;
     const int wpb = std::max(1, std::min(4, (int)((227u * 1024u) / per)));
     const size_t sm = per * (size_t)wpb;
-    if (sm > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k_mh_blend, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    {
+        cudaError_t e = raise_smem_limit((const void*)k_mh_blend, sm);
         if (e != cudaSuccess) return e;
     }
     k_mh_blend<<<(V.P + wpb - 1) / wpb, 32 * wpb, sm, s>>>(V, FD, B);

@@ -75,7 +75,9 @@ def _compare_update(gv, ov, frame, check_atlas=True, what=""):
 
 
 # ------------------------------------------------------------------ allocation
-@pytest.mark.parametrize("P", [1, 7, 64, 1000, 1025, 16384, 24576, 131072, 200000])  # the last: one block
+# 196608 is the largest grid of the 8-CTA cluster kernel, 196609 the smallest
+# of the one-block kernel
+@pytest.mark.parametrize("P", [1, 7, 64, 1000, 1025, 16384, 24576, 131072, 196608, 196609, 200000])
 def test_allocation_bit_exact(adgi, P):
     rng = np.random.default_rng(P)
     cases = [
@@ -98,6 +100,55 @@ def test_allocation_bit_exact(adgi, P):
         torch.cuda.synchronize()
         np.testing.assert_array_equal(nd.cpu().numpy().view(np.uint32), n_ref)
         np.testing.assert_array_equal(od.cpu().numpy().view(np.uint32), off_ref)
+
+
+def test_allocation_large_then_smaller_then_large(adgi):
+    # the cluster kernel's shared memory grows with P (8 B a probe): a grid
+    # above 49,152 probes, then a smaller one also above it, then the larger
+    # again must all match the oracle (the kernel's shared-memory limit is
+    # never lowered by the smaller grid)
+    dev = torch.device("cuda")
+    rng = np.random.default_rng(21)
+    for P in (131072, 60000, 131072, 50000, 196608):
+        W = rng.integers(0, 1 << 24, P).astype(np.uint32)
+        n_ref, off_ref = O.allocate(W, 64, 8, 256)
+        Wd = torch.from_numpy(W.view(np.int32)).to(dev)
+        nd = torch.empty(P, dtype=torch.int32, device=dev)
+        od = torch.empty(P + 1, dtype=torch.int32, device=dev)
+        adgi.adgi_allocate_rays(Wd, 64, 8, 256, nd, od, torch.cuda.current_stream().cuda_stream)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(nd.cpu().numpy().view(np.uint32), n_ref, err_msg="P=%d" % P)
+        np.testing.assert_array_equal(od.cpu().numpy().view(np.uint32), off_ref, err_msg="P=%d" % P)
+
+
+def test_graph_of_large_volume_replays_after_smaller_capture(adgi):
+    # two volumes above 49,152 probes (cluster allocation with more than
+    # 48 KB of shared memory): the larger one's captured update graph is
+    # replayed after the smaller one was captured, and must still equal
+    # plain updates of an identical volume
+    w = S.box_room(1)
+    big = dict(origin=(0.2, 0.2, 0.2), spacing=(7.6 / 63, 7.6 / 31, 7.6 / 63), dims=(64, 32, 64), rays_avg=9,
+               rays_min=8, rays_max=24)
+    small = dict(big, dims=(60, 25, 40), spacing=(7.6 / 59, 7.6 / 24, 7.6 / 39))
+    g_big = gpu_volume(adgi, w, **big)
+    p_big = gpu_volume(adgi, w, **big)
+    g_small = gpu_volume(adgi, w, **small)
+    wsum = 0
+    for f in range(5):
+        lights = w.lights_at(f)
+        g_big.update_graph(f, w.seed, lights, w.sky)
+        g_small.update_graph(f, w.seed, lights, w.sky)
+        p_big.update(f, w.seed, lights, w.sky)
+        torch.cuda.synchronize()
+        g_big.stats()
+        np.testing.assert_array_equal(g_big.W(), p_big.W(), err_msg="frame %d W" % f)
+        np.testing.assert_array_equal(g_big.n(), p_big.n(), err_msg="frame %d n" % f)
+        np.testing.assert_array_equal(g_big.main_hit(), p_big.main_hit(), err_msg="frame %d hits" % f)
+        np.testing.assert_array_equal(g_big.irr(), p_big.irr(), err_msg="frame %d irradiance" % f)
+        wsum += int(p_big.W().astype(np.int64).sum())
+    assert wsum > 0  # some allocation was not uniform
+    for v in (g_big, p_big, g_small):
+        v.close()
 
 
 def test_allocation_rejects_impossible_budget(adgi):

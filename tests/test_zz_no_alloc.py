@@ -57,6 +57,32 @@ def test_noalloc_build_matches_allocating_build_on_consecutive_calls():
                                           err_msg="%s call %d triangles" % (w.name, call))
 
 
+@pytest.mark.gpu
+def test_noalloc_build_at_its_maximum_size():
+    """A build of exactly BVH_NOALLOC_MAX_TRIS triangles fills the fixed
+    scratch to its limit and still equals the allocating build."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    A = _lib()
+    dev = torch.device("cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    w = S.small_city(9, n_boxes=3000)
+    n = A.BVH_NOALLOC_MAX_TRIS
+    assert w.n_tris >= n
+    idx = np.ascontiguousarray(w.idx.reshape(-1, 3)[:n])
+    V = torch.from_numpy(w.verts).to(dev)
+    I = torch.from_numpy(idx).to(dev)
+    eps = A.scene_eps(w.verts)
+    ref_nodes, ref_tris = _bufs(n, dev)
+    A.adgi_build_bvh(V, I, eps, ref_nodes, ref_tris, stream)
+    for call in range(2):
+        nodes, tris = _bufs(n, dev)
+        A.adgi_build_bvh_noalloc(V, I, eps, nodes, tris, stream)
+        np.testing.assert_array_equal(nodes.cpu().numpy(), ref_nodes.cpu().numpy(), err_msg="call %d nodes" % call)
+        np.testing.assert_array_equal(tris.cpu().numpy().view(np.int32), ref_tris.cpu().numpy().view(np.int32),
+                                      err_msg="call %d triangles" % call)
+
+
 def test_noalloc_build_rejects_sizes_beyond_its_scratch():
     """Host-side check, before any device work: too many triangles is an
     INVALID_ARG with a message that names the limit."""
