@@ -1820,10 +1820,15 @@ static void classify(orc_vol* v, const orc_frame* fr)
     }
 }
 
-static void change_detect(orc_vol* v, const orc_frame* fr)
+/* The change step of probes [p0, p1) in two parts: change_state (q_v, q_r,
+   the pair gradient and the trigger Tr, from each probe's own pilot rays)
+   and change_weights (the 5x5x5 x octant sum of Tr over the neighbours and
+   the composition into q_d and W_p).  The weights read the neighbours' Tr,
+   so with the probes split across ranks the Tr of the neighbouring planes
+   must be present before change_weights runs. */
+static void change_state(orc_vol* v, const orc_frame* fr, int p0, int p1)
 {
-    const int P = v->P;
-    for (int p = 0; p < P; ++p)
+    for (int p = p0; p < p1; ++p)
         for (int o = 0; o < 8; ++o) {
             size_t opp = (size_t)p * 8 + (size_t)(7 - o);
             v->qv[(size_t)p * 8 + o] = v->cls[p] ? v->lut_v[qt_of(v, v->pil_t[opp], v->pil_tri[opp] >= 0)] : 0;
@@ -1832,7 +1837,7 @@ static void change_detect(orc_vol* v, const orc_frame* fr)
     const int theta = v->d.theta;
     const int even = (fr->frame & 1u) == 0;
     const int valid = !even && v->last_even == (int64_t)fr->frame - 1;
-    for (size_t i = 0; i < (size_t)P * 8; ++i) {
+    for (size_t i = (size_t)p0 * 8; i < (size_t)p1 * 8; ++i) {
         const size_t pi = i / 8;
         if (v->cls[pi] == 0) { /* outside V_out: no heuristics; the state waits */
             v->trv[i] = v->trr[i] = 0;
@@ -1864,10 +1869,14 @@ static void change_detect(orc_vol* v, const orc_frame* fr)
         }
     }
     if (even)
-        for (int p = 0; p < P; ++p) v->vout_even[p] = v->cls[p] >= 1;
+        for (int p = p0; p < p1; ++p) v->vout_even[p] = v->cls[p] >= 1;
     if (even) v->last_even = (int64_t)fr->frame;
+}
+
+static void change_weights(orc_vol* v, const orc_frame* fr, int p0, int p1)
+{
     const int X = v->d.dims[0], Y = v->d.dims[1], Z = v->d.dims[2];
-    for (int p = 0; p < P; ++p) {
+    for (int p = p0; p < p1; ++p) {
         int ix = p % X, iy = (p / X) % Y, iz = p / (X * Y);
         uint32_t qc = qc_of(v, fr, p);
         uint64_t Wp = 0;
@@ -1892,6 +1901,12 @@ static void change_detect(orc_vol* v, const orc_frame* fr)
         }
         v->W[p] = (uint32_t)(Wp < 0xFFFFFFu ? Wp : 0xFFFFFFu);
     }
+}
+
+static void change_detect(orc_vol* v, const orc_frame* fr)
+{
+    change_state(v, fr, 0, v->P);
+    change_weights(v, fr, 0, v->P);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -2664,16 +2679,11 @@ static void* worker(void* arg)
     return NULL;
 }
 
-static void run_phase(orc_vol* v, const orc_frame* fr, int phase)
+/* a phase over items [lo, hi), split evenly over the threads */
+static void run_phase_range(orc_vol* v, const orc_frame* fr, int phase, long long lo, long long hi)
 {
-    /* phases 3 and 4 run over chains and samples, 6 and 7 over dynamic
-       chains and rays, the others over probes */
-    const long long N = phase == 3   ? (long long)v->C
-                        : phase == 4 ? (long long)v->B
-                        : phase == 6 ? (long long)v->Cd
-                        : phase == 7 ? (long long)v->Rdyn
-                                     : (long long)v->P;
-    if (N == 0) return;
+    const long long N = hi - lo;
+    if (N <= 0) return;
     int nt = v->nthreads;
     if (nt > N) nt = (int)N;
     pthread_t th[256];
@@ -2683,8 +2693,8 @@ static void run_phase(orc_vol* v, const orc_frame* fr, int phase)
         jobs[t].v = v;
         jobs[t].fr = fr;
         jobs[t].phase = phase;
-        jobs[t].t0 = (int)(N * t / nt);
-        jobs[t].t1 = (int)(N * (t + 1) / nt);
+        jobs[t].t0 = (int)(lo + N * t / nt);
+        jobs[t].t1 = (int)(lo + N * (t + 1) / nt);
     }
     if (nt == 1) {
         worker(&jobs[0]);
@@ -2692,6 +2702,18 @@ static void run_phase(orc_vol* v, const orc_frame* fr, int phase)
     }
     for (int t = 0; t < nt; ++t) pthread_create(&th[t], NULL, worker, &jobs[t]);
     for (int t = 0; t < nt; ++t) pthread_join(th[t], NULL);
+}
+
+static void run_phase(orc_vol* v, const orc_frame* fr, int phase)
+{
+    /* phases 3 and 4 run over chains and samples, 6 and 7 over dynamic
+       chains and rays, the others over probes */
+    const long long N = phase == 3   ? (long long)v->C
+                        : phase == 4 ? (long long)v->B
+                        : phase == 6 ? (long long)v->Cd
+                        : phase == 7 ? (long long)v->Rdyn
+                                     : (long long)v->P;
+    run_phase_range(v, fr, phase, 0, N);
 }
 
 EXPORT int orc_update(orc_vol* v, const orc_frame* fr)
@@ -2723,6 +2745,88 @@ EXPORT int orc_update(orc_vol* v, const orc_frame* fr)
     run_phase(v, fr, 1);
     run_phase(v, fr, 2);
     return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Probe-slab split of one update over ranks (the multi-GPU form of the     */
+/* deterministic mode).  A rank owns probes [p0, p1) and keeps full-size    */
+/* arrays; per frame:                                                        */
+/*   orc_slab_begin    rotation, clip classes of every probe, the pilot     */
+/*                     rays of its probes and their change state (q, Tr);   */
+/*   (the ranks exchange Tr of the two planes beside each slab border)      */
+/*   orc_slab_weights  W_p of its probes (5x5x5 x octant sum);              */
+/*   (the ranks all-gather W)                                               */
+/*   orc_slab_finish   the allocation of the whole budget over all W (every */
+/*                     rank computes the same integers), the adaptive rays  */
+/*                     of its probes (shading reads the previous atlases    */
+/*                     wherever a ray hits) and the blend of its tiles;     */
+/*   (the ranks all-gather the tiles, so every rank holds the whole atlas   */
+/*   that the next frame's shading reads: rays have no length limit).       */
+/* Each step is the single-volume step restricted to the rank's probes, so  */
+/* the result equals orc_update's.  Deterministic allocation and the FP64   */
+/* atlases only (sampler 0, not packed).                                    */
+/* ------------------------------------------------------------------------ */
+static int slab_ok(const orc_vol* v, int p0, int p1)
+{
+    return v->d.sampler == 0 && !v->d.packed && p0 >= 0 && p0 <= p1 && p1 <= v->P;
+}
+
+EXPORT int orc_slab_begin(orc_vol* v, const orc_frame* fr, int p0, int p1)
+{
+    if (!slab_ok(v, p0, p1)) return -1;
+    if (v->bvh_dirty) {
+        if (cbvh_build(&v->bvh, v->V, v->nv, v->I, v->nt)) return -1;
+        v->bvh_dirty = 0;
+    }
+    orc_frame_rotation(fr->seed, fr->frame, v->R);
+    classify(v, fr);
+    run_phase_range(v, fr, 0, p0, p1);
+    change_state(v, fr, p0, p1);
+    return 0;
+}
+
+EXPORT int orc_slab_weights(orc_vol* v, const orc_frame* fr, int p0, int p1)
+{
+    if (!slab_ok(v, p0, p1)) return -1;
+    change_weights(v, fr, p0, p1);
+    return 0;
+}
+
+EXPORT int orc_slab_finish(orc_vol* v, const orc_frame* fr, int p0, int p1)
+{
+    if (!slab_ok(v, p0, p1)) return -1;
+    if (orc_allocate_masked(v->W, v->cls, v->P, v->d.avg, v->d.rmin, v->d.rmax, v->n, v->off)) return -1;
+    run_phase_range(v, fr, 1, p0, p1);
+    run_phase_range(v, fr, 2, p0, p1);
+    return 0;
+}
+
+/* Copy the part of a per-probe state array that belongs to probes [p0, p1)
+   out to buf (into = 0) or in from buf (into = 1).  which: 0 Tr_v, 1 Tr_r
+   (uint16[8] a probe), 2 W (uint32), 3 irradiance tiles (double[Ti^2][3]),
+   4 irradiance counts (uint8[Ti^2]), 5 depth tiles (double[Td^2][2]),
+   6 depth counts (uint8[Td^2]).  Returns the bytes copied, or -1. */
+EXPORT long long orc_slab_slice(orc_vol* v, int which, int p0, int p1, void* buf, int into)
+{
+    if (p0 < 0 || p0 > p1 || p1 > v->P || !buf) return -1;
+    size_t per;
+    char* base;
+    switch (which) {
+    case 0: per = 16; base = (char*)v->trv; break;
+    case 1: per = 16; base = (char*)v->trr; break;
+    case 2: per = 4; base = (char*)v->W; break;
+    case 3: per = (size_t)v->Ti * v->Ti * 3 * sizeof(double); base = (char*)v->irr; break;
+    case 4: per = (size_t)v->Ti * v->Ti; base = (char*)v->irr_n; break;
+    case 5: per = (size_t)v->Td * v->Td * 2 * sizeof(double); base = (char*)v->dep; break;
+    case 6: per = (size_t)v->Td * v->Td; base = (char*)v->dep_n; break;
+    default: return -1;
+    }
+    const size_t n = per * (size_t)(p1 - p0);
+    if (into)
+        memcpy(base + per * (size_t)p0, buf, n);
+    else
+        memcpy(buf, base + per * (size_t)p0, n);
+    return (long long)n;
 }
 
 /* Trace + shade the pilot and main rays of a probe subset without blending */

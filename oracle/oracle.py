@@ -96,6 +96,11 @@ def lib():
         L.orc_update.restype = C.c_int
         L.orc_trace_shade_probes.argtypes = [vp, C.POINTER(OrcFrame), i32p, C.c_int]
         L.orc_trace_shade_probes.restype = C.c_longlong
+        for fn in ("orc_slab_begin", "orc_slab_weights", "orc_slab_finish"):
+            getattr(L, fn).argtypes = [vp, C.POINTER(OrcFrame), C.c_int, C.c_int]
+            getattr(L, fn).restype = C.c_int
+        L.orc_slab_slice.argtypes = [vp, C.c_int, C.c_int, C.c_int, vp, C.c_int]
+        L.orc_slab_slice.restype = C.c_longlong
         L.orc_query.argtypes = [vp, C.c_int, f32p, f32p, f64p]
         L.orc_num_probes.argtypes = [vp]
         L.orc_num_probes.restype = C.c_int
@@ -434,6 +439,44 @@ class OracleVolume:
         r = lib().orc_update(self.h, C.byref(fr))
         if r:
             raise RuntimeError("oracle update failed")
+
+    # ---- probe-slab split (one rank's share of an update; see orc_slab_*)
+    SLAB = {"TRV": (0, np.uint16, 8), "TRR": (1, np.uint16, 8), "W": (2, np.uint32, 1), "IRR": (3, np.float64, None),
+            "IRR_N": (4, np.uint8, None), "DEP": (5, np.float64, None), "DEP_N": (6, np.uint8, None)}
+
+    def _slab_call(self, fn, frame, seed, lights, p0, p1, sky, camera):
+        self._fr = make_frame(frame, seed, lights, sky, camera)
+        if getattr(lib(), fn)(self.h, C.byref(self._fr), int(p0), int(p1)):
+            raise ValueError(fn + " failed")
+
+    def slab_begin(self, frame, seed, lights, p0, p1, sky=(0, 0, 0), camera=None):
+        self._slab_call("orc_slab_begin", frame, seed, lights, p0, p1, sky, camera)
+
+    def slab_weights(self, frame, seed, lights, p0, p1, sky=(0, 0, 0), camera=None):
+        self._slab_call("orc_slab_weights", frame, seed, lights, p0, p1, sky, camera)
+
+    def slab_finish(self, frame, seed, lights, p0, p1, sky=(0, 0, 0), camera=None):
+        self._slab_call("orc_slab_finish", frame, seed, lights, p0, p1, sky, camera)
+
+    def _slab_elems(self, which):
+        code, dt, per = self.SLAB[which]
+        if per is None:
+            per = {"IRR": self.Ti * self.Ti * 3, "IRR_N": self.Ti * self.Ti, "DEP": self.Td * self.Td * 2,
+                   "DEP_N": self.Td * self.Td}[which]
+        return code, dt, per
+
+    def slab_get(self, which, p0, p1):
+        code, dt, per = self._slab_elems(which)
+        out = np.empty((p1 - p0) * per, dt)
+        if lib().orc_slab_slice(self.h, code, int(p0), int(p1), out.ctypes.data, 0) != out.nbytes:
+            raise ValueError("bad slice")
+        return out
+
+    def slab_set(self, which, p0, p1, data):
+        code, dt, per = self._slab_elems(which)
+        a = np.ascontiguousarray(data, dt).reshape(-1)
+        if a.size != (p1 - p0) * per or lib().orc_slab_slice(self.h, code, int(p0), int(p1), a.ctypes.data, 1) != a.nbytes:
+            raise ValueError("bad slice")
 
     def trace_shade_probes(self, frame, seed, lights, probes, sky=(0, 0, 0)):
         fr = make_frame(frame, seed, lights, sky)
