@@ -291,6 +291,9 @@ int adgi_enable_timing(adgi_volume vol, int32_t enable);
  *   ADGI_STATE_DEP_MOMENTS double[P][Td][Td][2] the depth atlas as the moments {mean, mean^2}
  *                       (mean^2 = variance + mean^2 of the stored texel, formed in FP64);
  *                       FP32 and half atlases only (INVALID_ARG when atlas_fp16 is 3)
+ *   ADGI_STATE_G        uint32[P][8]      per probe and octant: the sum over the octant and its
+ *                       three edge neighbours of Tr_v + 2 Tr_r, which W_p sums over the
+ *                       5x5x5 probes around p (step 2)
  *   ADGI_STATE_DEP_N    uint8[P][Td][Td]  depth sample counts (unused with packed texels,
  *                       which carry their own count)
  *   ADGI_STATE_ROT      float[9]          main-ray rotation of the last update
@@ -364,10 +367,43 @@ enum {
     ADGI_STATE_DYN_HIT = 32,
     ADGI_STATE_DYN_REC = 33,
     ADGI_STATE_CLS = 34,
-    ADGI_STATE_DEP_MOMENTS = 35
+    ADGI_STATE_DEP_MOMENTS = 35,
+    ADGI_STATE_G = 36
 };
 int adgi_state_bytes(adgi_volume vol, int32_t which, uint64_t* bytes);
 int adgi_read_state(adgi_volume vol, int32_t which, void* dst_host, uint64_t bytes);
+
+/* Probe-slab split of one volume's update over several GPUs (one process and
+ * one volume per GPU, each holding the whole grid's arrays; the paper runs one
+ * GPU, so this has no counterpart there and only restates the update's own
+ * data flow).  Rank r owns probes [p0, p1) -- whole z-planes of the grid --
+ * and calls, per frame, on its volume:
+ *   step 0: the frame set-up (moving-part BVH, rotation, clip classes of every
+ *           probe), the pilot rays of its probes and their change state up to
+ *           ADGI_STATE_G (Sec. 4.1, Sec. 4.4);
+ *   --- the ranks exchange G of the two z-planes beside each slab border ---
+ *   step 1: W_p of its probes (the 5x5x5 sum of G, Sec. 4.1-4.2);
+ *   --- the ranks all-gather W ---
+ *   step 2: the allocation of the whole budget over every W_p (identical on
+ *           every rank: the integers need no collective beyond the gather),
+ *           the adaptive rays of its probes (their shading reads the previous
+ *           atlases wherever a ray hits) and the blend of its tiles;
+ *   --- the ranks all-gather the irradiance / depth tiles (ADGI_STATE_IRR,
+ *       _DEP, _DEP_N), which the next frame's shading reads anywhere ---
+ * With every exchange done, each rank's probes end exactly as adgi_update
+ * leaves them.  The steps run in the order 0, 1, 2 with one frame and one
+ * probe range (INVALID_ARG otherwise); sampler 0 with FP32 or half atlases
+ * only.  Enqueued on the volume's stream; the caller moves the data between
+ * ranks (for example with NCCL on the same stream) using adgi_slab_copy. */
+int adgi_update_slab(adgi_volume vol, const adgi_frame* frame, int32_t step, int32_t p0, int32_t p1);
+
+/* Copy the part of a per-probe state array (ADGI_STATE_W, _TRV, _TRR, _G,
+ * _IRR, _DEP, _DEP_N; layouts as adgi_read_state) that belongs to probes
+ * [p0, p1) out to the device buffer dev_buf (into = 0) or in from it (into =
+ * 1); adgi_slab_bytes gives the size.  Enqueued on the volume's stream.
+ * Errors: INVALID_ARG, CUDA. */
+int adgi_slab_copy(adgi_volume vol, int32_t which, int32_t p0, int32_t p1, void* dev_buf, int32_t into);
+int adgi_slab_bytes(adgi_volume vol, int32_t which, int32_t p0, int32_t p1, uint64_t* bytes);
 
 /* Overwrite the atlases from host memory (same layouts as ADGI_STATE_IRR /
  * _DEP / _DEP_N; any pointer may be NULL to keep that part).  For tests and
@@ -385,12 +421,16 @@ int adgi_trace_closest(adgi_volume vol, const float* o, const float* d, int32_t 
 /* Traversal work of the last update, for roofline accounting: re-traces the
  * last update's pilot and adaptive rays (and their shadow rays for the lights
  * of *frame, which must be the last update's frame) with counters, without
- * changing any state.  counts (host uint64[8]) receives, for the pilot rays
+ * changing any state.  counts (host uint64[12]) receives, for the pilot rays
  * then for the adaptive rays: nearest-hit box tests, nearest-hit triangle
  * tests, shadow-ray box tests, shadow-ray triangle tests (a BVH node visit
- * tests the boxes of both children: 2 box tests).  Metropolis volumes: the
- * adaptive part counts the samples' +w and -w rays and the +w rays' shadow
- * rays.  Synchronises the stream.
+ * tests the boxes of both children: 2 box tests); then for the adaptive
+ * rays: [8] the sum over warps of 32 x the largest box-test count of the
+ * warp's rays (a warp traverses as long as its longest ray, so
+ * counts[4] / counts[8] is the lane efficiency the ray lengths allow),
+ * [9] the rays traced, [10] shadow rays that found a blocker, [11] shadow
+ * rays traced.  Metropolis volumes: the adaptive part counts the samples' +w
+ * and -w rays and the +w rays' shadow rays.  Synchronises the stream.
  * Errors: INVALID_ARG, NO_SCENE, CUDA. */
 int adgi_count_traversal(adgi_volume vol, const adgi_frame* frame, uint64_t* counts);
 

@@ -20,7 +20,7 @@ STATE = dict(W=0, N=1, OFF=2, QV=3, QR=4, TRV=5, TRR=6, PILOT_HIT=7, PILOT_REC=8
              MAIN_REC=11, IRR=12, DEP=13, DEP_N=14, ROT=15, BVH_NODES=16, BVH_TRIS=17, MOVING_BVH_NODES=18,
              MOVING_BVH_TRIS=19, MH_CHAINS=20, MH_SAMPLES=21, MH_ORDER=22, MH_OFF=23, MH_HIT_NEG=24,
              QD=25, DYN_CHAINS=26, DYN_SAMPLES=27, DYN_CELLS=28, DYN_FIRST=29, DYN_INCL=30, DYN_OFF=31, DYN_HIT=32,
-             DYN_REC=33, CLS=34, DEP_MOMENTS=35)
+             DYN_REC=33, CLS=34, DEP_MOMENTS=35, G=36)
 
 
 class AdgiError(RuntimeError):
@@ -112,7 +112,7 @@ EXPORTED = ["adgi_create_volume", "adgi_set_scene", "adgi_move_vertices", "adgi_
             "adgi_batch_update", "adgi_batch_destroy", "adgi_autotune", "adgi_set_tuning", "adgi_get_tuning",
             "adgi_server_create", "adgi_server_add_volume", "adgi_server_submit", "adgi_server_poll",
             "adgi_server_drain", "adgi_server_volume", "adgi_server_remove_volume", "adgi_server_info",
-            "adgi_server_destroy", "adgi_last_error"]
+            "adgi_server_destroy", "adgi_update_slab", "adgi_slab_copy", "adgi_slab_bytes", "adgi_last_error"]
 
 BVH_NOALLOC_MAX_TRIS = 32768
 
@@ -161,6 +161,9 @@ def load(path: str = LIB_PATH):
     L.adgi_server_remove_volume.argtypes = [vp, i32]
     L.adgi_server_info.argtypes = [vp, C.POINTER(u64), C.POINTER(u64), C.POINTER(i32), C.POINTER(i32)]
     L.adgi_server_destroy.argtypes = [vp]
+    L.adgi_update_slab.argtypes = [vp, C.POINTER(adgi_frame), i32, i32, i32]
+    L.adgi_slab_copy.argtypes = [vp, i32, i32, i32, vp, i32]
+    L.adgi_slab_bytes.argtypes = [vp, i32, i32, i32, C.POINTER(u64)]
     L.adgi_last_error.restype = C.c_char_p
     for name in EXPORTED[:-1]:
         getattr(L, name).restype = C.c_int
@@ -258,7 +261,7 @@ def adgi_trace_closest(vol, o, d, tmin, tmax, t_out, tri_out):
 
 
 def adgi_count_traversal(vol, frame: adgi_frame):
-    out = (C.c_uint64 * 8)()
+    out = (C.c_uint64 * 12)()
     _check(load().adgi_count_traversal(vol, C.byref(frame), out))
     return [int(x) for x in out]
 
@@ -390,6 +393,22 @@ def adgi_server_info(server):
 
 def adgi_server_destroy(server):
     _check(load().adgi_server_destroy(server))
+
+
+def adgi_update_slab(vol, frame: adgi_frame, step, p0, p1):
+    _check(load().adgi_update_slab(vol, C.byref(frame), int(step), int(p0), int(p1)))
+
+
+def adgi_slab_copy(vol, which, p0, p1, dev_buf, into):
+    _check(load().adgi_slab_copy(vol, STATE[which] if isinstance(which, str) else int(which), int(p0), int(p1),
+                                 _ptr(dev_buf), int(into)))
+
+
+def adgi_slab_bytes(vol, which, p0, p1) -> int:
+    b = C.c_uint64()
+    _check(load().adgi_slab_bytes(vol, STATE[which] if isinstance(which, str) else int(which), int(p0), int(p1),
+                                  C.byref(b)))
+    return int(b.value)
 
 
 def adgi_last_error() -> str:

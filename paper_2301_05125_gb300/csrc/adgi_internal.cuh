@@ -99,6 +99,7 @@ struct VolConst {
     int dyn;                // dynamic chains on (Metropolis mode with dyn_ratio > 0)
     float hyst_dyn;         // hysteresis of the dynamic rays' batch step
     const uint8_t* cls;     // [P] clip volume of this frame: 2 V_in, 1 V_out - V_in, 0 outside
+    int p_lo, p_hi;         // probes this launch works on: [0, P), or one rank's slab of a split update
 };
 
 // This frame's dynamic rays (dynamic chains over virtual proxies), grouped
@@ -363,9 +364,11 @@ __device__ __forceinline__ bool slab_fma(float lox, float loy, float loz, float 
     return tn <= tf;
 }
 
-__device__ __forceinline__ void trav_tri(Trav& T, const float4* tv, bool any, uint32_t* ntri)
+// the triangle at slot `slot` of the BVH-ordered array
+__device__ __forceinline__ void trav_tri(Trav& T, const float4* tri_v, int slot, bool any, uint32_t* ntri)
 {
     if (ntri) ++*ntri;
+    const float4* tv = tri_v + 3 * (size_t)slot;
     float4 A = __ldg(tv), Bv = __ldg(tv + 1), C = __ldg(tv + 2);
     float tt, det;
     if (!wtri(T.wr, A, Bv, C, tt, det) || !(tt > T.tmin)) return;
@@ -418,7 +421,7 @@ __device__ __forceinline__ void trav_init(Trav& T, int* stack, const SceneDev& S
         if (root >= 0)
             stack[T.sp++] = root;
         else if (leaf >= 0)
-            trav_tri(T, S.tri_v + 3 * (size_t)leaf, any, ntri);
+            trav_tri(T, S.tri_v, leaf, any, ntri);
     }
     if (any && T.found) T.sp = 0;
 }
@@ -444,8 +447,8 @@ __device__ __forceinline__ bool trav_step(Trav& T, int* stack, const SceneDev& S
     float t0, t1;
     const bool h0 = slab_fma(a.x, a.y, a.z, a.w, b.x, b.y, T.inv, T.oi, lim, t0);
     const bool h1 = slab_fma(b.z, b.w, c.x, c.y, c.z, c.w, T.inv, T.oi, lim, t1);
-    if (h0 && ch.x < 0) trav_tri(T, S.tri_v + 3 * (size_t)(~ch.x), any, ntri);
-    if (h1 && ch.y < 0) trav_tri(T, S.tri_v + 3 * (size_t)(~ch.y), any, ntri);
+    if (h0 && ch.x < 0) trav_tri(T, S.tri_v, ~ch.x, any, ntri);
+    if (h1 && ch.y < 0) trav_tri(T, S.tri_v, ~ch.y, any, ntri);
     const bool i0 = h0 && ch.x >= 0, i1 = h1 && ch.y >= 0;
     if (i0 && i1) {  // the near child next, the far one on the stack
         const bool first0 = t0 <= t1;

@@ -247,6 +247,10 @@ struct adgi_volume_s {
     // frame bookkeeping
     int64_t last_even = -2;
     uint64_t frames = 0;
+    // a split update in progress (adgi_update_slab): its frame, step and probes
+    FrameDev slab_fd;
+    uint64_t slab_frame = 0;
+    int slab_step = -1, slab_p0 = 0, slab_p1 = 0;
     float R[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
     bool timing = false;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -594,6 +598,8 @@ int adgi_create_volume(const adgi_volume_desc* desc, void* cuda_stream, adgi_vol
     V.dyn = d.dyn_ratio > 0 ? 1 : 0;
     V.hyst_dyn = d.hysteresis_dyn;
     V.cls = v->cls;
+    V.p_lo = 0;
+    V.p_hi = V.P;
     cudaStream_t s = v->stream;
 #define CKV(call)                                                                                        \
     do {                                                                                                 \
@@ -1109,6 +1115,119 @@ int adgi_update(adgi_volume v, const adgi_frame* f)
     return ADGI_OK;
 }
 
+// One rank's share of a probe-slab split update: the steps of
+// enqueue_update (deterministic allocation) with the probe work restricted
+// to [p0, p1); the allocation and the clip classes cover every probe.
+int adgi_update_slab(adgi_volume v, const adgi_frame* f, int32_t step, int32_t p0, int32_t p1)
+{
+    if (!v || !f) return fail(ADGI_ERR_INVALID_ARG, "NULL argument");
+    if (v->desc.sampler != 0 || v->desc.atlas_fp16 == 3)
+        return fail(ADGI_ERR_INVALID_ARG, "the slab split takes sampler 0 with FP32 or half atlases");
+    if (p0 < 0 || p0 > p1 || p1 > v->V.P) return fail(ADGI_ERR_INVALID_ARG, "probe range outside [0, P]");
+    if (step < 0 || step > 2) return fail(ADGI_ERR_INVALID_ARG, "step must be 0, 1 or 2");
+    if (step > 0 && (v->slab_step != step - 1 || v->slab_frame != f->frame || v->slab_p0 != p0 || v->slab_p1 != p1))
+        return fail(ADGI_ERR_INVALID_ARG, "slab steps must run 0, 1, 2 on one frame and one probe range");
+    cudaStream_t s = v->stream;
+    if (step == 0) {
+        int rc = prepare_update(v, f, v->slab_fd, nullptr);
+        if (rc) return rc;
+        v->slab_frame = f->frame;
+        v->slab_p0 = p0;
+        v->slab_p1 = p1;
+    }
+    v->slab_step = -1;  // until this step is enqueued
+    const FrameDev& fd = v->slab_fd;
+    const VolConst& V = v->V;
+    VolConst Vs = v->V;
+    Vs.p_lo = p0;
+    Vs.p_hi = p1;
+    const Tuning& T = v->tune;
+    SceneDev S = scene_view(v);
+    const FrameDev* FD = v->fdev;
+    ShadeWork W{v->vis, v->jobs, v->job_light, v->job_count, (unsigned)std::min<size_t>(v->job_cap, 0xFFFFFFFFu),
+                v->shadow_blocks, v->shadow_ctr};
+    ChangeBufs C{v->pil_hit, v->pil_lum, v->lut_v, v->lut_c, v->qv,  v->qr,  v->qv_even, v->qr_even,
+                 v->amp_v,   v->amp_r,   v->age_v, v->age_r, v->trv, v->trr, v->G,       v->W, v->qd, v->vout_even};
+    BlendBufs Bb{v->off,  v->sf,  v->pil_rec, v->m_rec,
+                 v->irr,  v->dep, v->dep_n,   carve_blend_plan(v->plan, V.rays_max - 8, V.Ti, V.Td), v->tex_src};
+    const bool cosg = v->desc.blend_mode == 1;
+    if (step == 0) {
+        CK(launch_set_frame(v->fdev, fd, s));
+        if (v->nd > 0 && v->dyn_dirty) {
+            CK(fill_tri_orig(v->verts, v->idx, v->dlist, v->nv, v->nd, v->tri_orig, s));
+            int rc = build_moving(v, s);
+            if (rc) return rc;
+        }
+        v->dyn_dirty = false;
+        if (!cosg) {  // the blend plan on the side stream; step 2 joins it before the blend
+            CK(cudaEventRecord(v->fork, s));
+            CK(cudaStreamWaitEvent(v->side, v->fork, 0));
+            CK(launch_blend_plan(V, v->fdev, v->sf, Bb.plan, v->side));
+            CK(cudaEventRecord(v->join, v->side));
+        }
+        CK(cudaMemsetAsync(v->shadow_ctr, 0, 8, s));
+        CK(launch_classify(V, FD, v->lut_c, v->cls, s));
+        CK(launch_pilot_trace(Vs, FD, S, v->pil_hit, T, s));
+        CK(launch_shade(Vs, FD, S, 0, (uint32_t)(p1 - p0) * kPilots, nullptr, nullptr, v->irr, v->dep, v->pil_hit,
+                        v->pil_rec, v->pil_lum, W, T, s));
+        CK(launch_change(Vs, FD, C, s, 1));
+    } else if (step == 1) {
+        CK(launch_change(Vs, FD, C, s, 2));
+    } else {
+        CK(launch_allocate(v->W, V.P, V.rays_avg, V.m0, V.rays_max, v->n, v->off, s, v->cls));
+        CK(launch_main_trace(Vs, FD, S, v->off, v->sf, v->R_main, v->m_hit, T, s));
+        CK(launch_shade(Vs, FD, S, 1, v->R_main, v->off, v->sf, v->irr, v->dep, v->m_hit, v->m_rec, nullptr, W, T, s));
+        if (cosg) {
+            CK(launch_blend_cos(Vs, FD, Bb, T, s));
+        } else {
+            CK(cudaStreamWaitEvent(s, v->join, 0));
+            CK(launch_blend(Vs, FD, Bb, T, s));
+        }
+        adgi_frame fcopy = *f;
+        finish_update(v, fd, &fcopy);
+    }
+    v->slab_step = step;
+    return ADGI_OK;
+}
+
+int adgi_slab_copy(adgi_volume v, int32_t which, int32_t p0, int32_t p1, void* dev_buf, int32_t into)
+{
+    if (!v || !dev_buf) return fail(ADGI_ERR_INVALID_ARG, "NULL argument");
+    if (p0 < 0 || p0 > p1 || p1 > v->V.P) return fail(ADGI_ERR_INVALID_ARG, "probe range outside [0, P]");
+    const size_t ti2 = (size_t)v->V.Ti * v->V.Ti, td2 = (size_t)v->V.Td * v->V.Td;
+    size_t per = 0;
+    char* base = nullptr;
+    switch (which) {
+    case ADGI_STATE_W: per = 4; base = (char*)v->W; break;
+    case ADGI_STATE_TRV: per = 16; base = (char*)v->trv; break;
+    case ADGI_STATE_TRR: per = 16; base = (char*)v->trr; break;
+    case ADGI_STATE_G: per = 32; base = (char*)v->G; break;
+    case ADGI_STATE_IRR: per = ti2 * (v->V.fp16 == 3 ? 4 : v->V.fp16 ? 8 : 16); base = (char*)v->irr; break;
+    case ADGI_STATE_DEP: per = td2 * (v->V.fp16 ? 4 : 8); base = (char*)v->dep; break;
+    case ADGI_STATE_DEP_N: per = td2; base = (char*)v->dep_n; break;
+    default: return fail(ADGI_ERR_INVALID_ARG, "adgi_slab_copy: state not per probe");
+    }
+    const size_t n = per * (size_t)(p1 - p0);
+    if (n == 0) return ADGI_OK;
+    char* at = base + per * (size_t)p0;
+    CK(cudaMemcpyAsync(into ? at : dev_buf, into ? dev_buf : at, n, cudaMemcpyDeviceToDevice, v->stream));
+    return ADGI_OK;
+}
+
+int adgi_slab_bytes(adgi_volume v, int32_t which, int32_t p0, int32_t p1, uint64_t* bytes)
+{
+    if (!v || !bytes) return fail(ADGI_ERR_INVALID_ARG, "NULL argument");
+    if (p0 < 0 || p0 > p1 || p1 > v->V.P) return fail(ADGI_ERR_INVALID_ARG, "probe range outside [0, P]");
+    uint64_t all = 0;
+    if (which != ADGI_STATE_W && which != ADGI_STATE_TRV && which != ADGI_STATE_TRR && which != ADGI_STATE_G &&
+        which != ADGI_STATE_IRR && which != ADGI_STATE_DEP && which != ADGI_STATE_DEP_N)
+        return fail(ADGI_ERR_INVALID_ARG, "adgi_slab_bytes: state not per probe");
+    int rc = adgi_state_bytes(v, which, &all);
+    if (rc) return rc;
+    *bytes = all / (uint64_t)v->V.P * (uint64_t)(p1 - p0);
+    return ADGI_OK;
+}
+
 namespace {
 
 cudaError_t capture_end(cudaStream_t s, cudaGraph_t* g)
@@ -1503,6 +1622,7 @@ int adgi_state_bytes(adgi_volume v, int32_t which, uint64_t* bytes)
     case ADGI_STATE_IRR: *bytes = P * ti2 * (v->V.fp16 == 3 ? 4 : v->V.fp16 ? 8 : 16); break;
     case ADGI_STATE_DEP: *bytes = P * td2 * (v->V.fp16 ? 4 : 8); break;
     case ADGI_STATE_DEP_N: *bytes = P * td2; break;
+    case ADGI_STATE_G: *bytes = 4 * 8 * P; break;
     case ADGI_STATE_DEP_MOMENTS:
         if (v->V.fp16 == 3) return fail(ADGI_ERR_INVALID_ARG, "DEP_MOMENTS: packed atlases hold codes (read DEP)");
         *bytes = P * td2 * 16;
@@ -1618,6 +1738,7 @@ int adgi_read_state(adgi_volume v, int32_t which, void* dst, uint64_t bytes)
     case ADGI_STATE_MH_HIT_NEG: src = v->mh_hitn; break;
     case ADGI_STATE_QD: src = v->qd; break;
     case ADGI_STATE_CLS: src = v->cls; break;
+    case ADGI_STATE_G: src = v->G; break;
     case ADGI_STATE_DYN_CHAINS: src = v->dyn_chain; break;
     case ADGI_STATE_DYN_SAMPLES: src = v->dyn_smp; break;
     case ADGI_STATE_DYN_CELLS: src = v->dyn_cell; break;
@@ -1703,18 +1824,18 @@ int adgi_count_traversal(adgi_volume v, const adgi_frame* f, uint64_t* counts)
     }
     unsigned long long* d = nullptr;
     size_t dummy = 0;
-    if (dalloc(&d, 8, &dummy) != cudaSuccess) return fail(ADGI_ERR_OOM, "counter buffer");
-    cudaError_t e = cudaMemsetAsync(d, 0, 64, s);
+    if (dalloc(&d, 12, &dummy) != cudaSuccess) return fail(ADGI_ERR_OOM, "counter buffer");
+    cudaError_t e = cudaMemsetAsync(d, 0, 96, s);
     if (e == cudaSuccess) e = launch_set_frame(v->fdev, fd, s);
     if (e == cudaSuccess)
         e = v->desc.sampler == 1 ? launch_count(v->V, v->fdev, scene_view(v), v->off, v->sf, 2 * v->mh_B, d, s, v->mh_smp_g)
                                  : launch_count(v->V, v->fdev, scene_view(v), v->off, v->sf, v->R_main, d, s);
-    unsigned long long h[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    if (e == cudaSuccess) e = cudaMemcpyAsync(h, d, 64, cudaMemcpyDeviceToHost, s);
+    unsigned long long h[12] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, d, 96, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     cudaFree(d);
     if (e != cudaSuccess) return fail(ADGI_ERR_CUDA, std::string("count: ") + cudaGetErrorString(e));
-    for (int i = 0; i < 8; ++i) counts[i] = h[i];
+    for (int i = 0; i < 12; ++i) counts[i] = h[i];
     return ADGI_OK;
 }
 

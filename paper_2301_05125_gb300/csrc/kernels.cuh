@@ -203,7 +203,9 @@ cudaError_t launch_trace_list(const SceneDev& S, const float* o, const float* d,
 // clip volume of every probe for this frame (V.cls; 2 everywhere without a matrix)
 cudaError_t launch_classify(const VolConst& V, const FrameDev* FD, const uint16_t* lut_c, uint8_t* cls,
                             cudaStream_t s);
-cudaError_t launch_change(const VolConst& V, const FrameDev* FD, const ChangeBufs& B, cudaStream_t s);
+// parts: 1 the change state (q, pair gradient, Tr, G), 2 the weights (the
+// 5x5x5 sum of G -> q_d, W), 3 both; over probes [V.p_lo, V.p_hi)
+cudaError_t launch_change(const VolConst& V, const FrameDev* FD, const ChangeBufs& B, cudaStream_t s, int parts = 3);
 // cls: clip volumes (null: every probe in V_in, the plain rule)
 cudaError_t launch_allocate(const uint32_t* W, int P, int avg, int m0, int rmax, uint32_t* n_out, uint32_t* off_out,
                             cudaStream_t s, const uint8_t* cls = nullptr);

@@ -45,11 +45,19 @@ struct RaySet {
     DynRays dyn;              // dynamic rays
 };
 
+// The first ray of the set for probes [p_lo, p_hi): pilot rays 8 p_lo,
+// adaptive rays off[p_lo]; thread idx of the launch takes ray base + idx.
+__device__ __forceinline__ uint32_t ray_base(const VolConst& V, const RaySet& Rs)
+{
+    return Rs.mode == 0 ? (uint32_t)V.p_lo * kPilots : Rs.mode == 1 ? __ldg(Rs.off + V.p_lo) : 0u;
+}
+
 __device__ __forceinline__ void block_range(const VolConst& V, const RaySet& Rs, int* s_lo, int* s_hi)
 {
     if (Rs.mode == 1) {
-        uint32_t r0 = blockIdx.x * blockDim.x;
-        uint32_t r1 = min(Rs.n - 1, r0 + blockDim.x - 1);
+        const uint32_t b = ray_base(V, Rs);
+        uint32_t r0 = b + blockIdx.x * blockDim.x;
+        uint32_t r1 = b + min(Rs.n - 1, blockIdx.x * blockDim.x + blockDim.x - 1);
         if (threadIdx.x == 0) *s_lo = probe_of_ray(Rs.off, r0, 0, V.P - 1);
         if (threadIdx.x == 32 % blockDim.x) *s_hi = probe_of_ray(Rs.off, r1, 0, V.P - 1);
     }
@@ -87,7 +95,7 @@ __device__ __forceinline__ bool ray_of(const VolConst& V, const FrameConst& F, c
         d = make_float3(a.x, a.y, a.z);
         return true;
     }
-    if (r >= __ldg(Rs.off + V.P)) return false;  // beyond this frame's adaptive rays (unspent budget)
+    if (r >= __ldg(Rs.off + V.p_hi)) return false;  // beyond the adaptive rays of the probes (unspent budget)
     int p = probe_of_ray(Rs.off, r, lo, hi);
     uint32_t base = __ldg(Rs.off + p), m = __ldg(Rs.off + p + 1) - base;
     if (m > (uint32_t)(V.rays_max - kPilots) || r - base >= m) return false;
@@ -130,12 +138,13 @@ __global__ void __launch_bounds__(256) k_shade_prep(VolConst V, const FrameDev* 
     const LightSet& L = FD->L;
     __shared__ int s_lo, s_hi;
     block_range(V, Rs, &s_lo, &s_hi);
-    const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t r = ray_base(V, Rs) + idx;
     bool front = false;
     float3 xs = make_float3(0.f, 0.f, 0.f), n = make_float3(0.f, 0.f, 1.f);
     uint32_t slot = r;
     float3 o, d;
-    if (r < Rs.n && ray_of(V, F, Rs, r, s_lo, s_hi, slot, o, d)) {
+    if (idx < Rs.n && ray_of(V, F, Rs, r, s_lo, s_hi, slot, o, d)) {
         vis[slot] = 0ull;
         int2 hv = hit[slot];
         uint32_t h = (uint32_t)hv.x;
@@ -232,8 +241,9 @@ __global__ void __launch_bounds__(256, 4) k_shade_finish(VolConst V, const Frame
     const int bounce = Rs.mode != 0 || F.even;
     __shared__ int s_lo, s_hi;
     block_range(V, Rs, &s_lo, &s_hi);
-    const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= Rs.n) return;
+    const uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= Rs.n) return;
+    const uint32_t r = ray_base(V, Rs) + idx;
     uint32_t slot;
     float3 o, d;
     if (Rs.mode == 0 && V.cls[r >> 3] == 0) {  // a culled pilot: a miss with nothing gathered

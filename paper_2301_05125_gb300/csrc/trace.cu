@@ -53,8 +53,8 @@ __global__ void __launch_bounds__(256) k_pilot_trace(VolConst V, const FrameDev*
                                                      int2* __restrict__ hit)
 {
     const FrameConst& F = FD->F;
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= V.P * kPilots) return;
+    int i = V.p_lo * kPilots + blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= V.p_hi * kPilots) return;
     int p = i >> 3, o = i & 7;
     if (V.cls[p] == 0) {  // outside V_out: no pilot rays
         hit[i] = make_int2((int)kMiss, 0x7F800000);
@@ -77,11 +77,15 @@ __global__ void __launch_bounds__(256) k_main_trace(VolConst V, const FrameDev* 
 {
     const FrameConst& F = FD->F;
     __shared__ int s_lo, s_hi;
-    uint32_t r0 = blockIdx.x * blockDim.x;
-    uint32_t r1 = min(R - 1, r0 + blockDim.x - 1);
+    // the rays of probes [p_lo, p_hi): [off[p_lo], off[p_hi]) (all probes:
+    // [0, off[P]); with clip volumes part of the budget may stay unspent)
+    const uint32_t rb = __ldg(off + V.p_lo), re = min(__ldg(off + V.p_hi), R);
+    uint32_t r0 = rb + blockIdx.x * blockDim.x;
+    if (r0 >= re) return;  // the whole block
+    uint32_t r1 = min(re - 1, r0 + blockDim.x - 1);
     block_probe_range(off, V.P, r0, r1, &s_lo, &s_hi);
     uint32_t r = r0 + threadIdx.x;
-    if (r >= R || r >= __ldg(off + V.P)) return;  // with clip volumes part of the budget may stay unspent
+    if (r >= re) return;
     int p = probe_of_ray(off, r, s_lo, s_hi);
     uint32_t base = __ldg(off + p);
     uint32_t m = __ldg(off + p + 1) - base;
@@ -169,7 +173,7 @@ __global__ void __launch_bounds__(128) k_count(VolConst V, const FrameDev* __res
     uint32_t m0r = b0 > NP ? b0 - NP : 0u;
     uint32_t m1r = min(R ? R - 1 : 0u, (b0 + blockDim.x - 1 > NP ? b0 + blockDim.x - 1 - NP : 0u));
     if (R && !smp_g) block_probe_range(off, V.P, m0r, m1r, &s_lo, &s_hi);
-    uint32_t cv = 0, ct = 0, sv = 0, st = 0;
+    uint32_t cv = 0, ct = 0, sv = 0, st = 0, sblk = 0, sn = 0;
     if (r < NP + R) {
         float3 org, d;
         bool ok = true, shadows = true;
@@ -219,12 +223,28 @@ __global__ void __launch_bounds__(128) k_count(VolConst V, const FrameDev* __res
                                             : make_float3(-Li.v[0], -Li.v[1], -Li.v[2]);
                     float thi = Li.kind == 0 ? 1.0f : __int_as_float(0x7F800000);
                     if (!(dot3x(n.x, n.y, n.z, D.x, D.y, D.z) > 0.0f)) continue;
-                    trace_any(S, xs, D, 0.0f, thi, &sv, &st);
+                    sblk += trace_any(S, xs, D, 0.0f, thi, &sv, &st) ? 1u : 0u;
+                    ++sn;
                 }
             }
         }
     }
     const bool main_ray = r >= NP && r < NP + R;
+    // SIMT bound of the main rays' traversal: a warp runs as many node visits
+    // as its longest ray, so sum(visits) / (32 x sum of warp maxima) is the
+    // lane efficiency that the ray lengths alone allow
+    {
+        const uint32_t mv = __reduce_max_sync(0xFFFFFFFFu, main_ray ? cv : 0u);
+        const uint32_t nr = __popc(__ballot_sync(0xFFFFFFFFu, main_ray));
+        const uint32_t nb = __reduce_add_sync(0xFFFFFFFFu, main_ray ? sblk : 0u);
+        const uint32_t ns = __reduce_add_sync(0xFFFFFFFFu, main_ray ? sn : 0u);
+        if ((threadIdx.x & 31) == 0) {
+            atomicAdd(out + 8, 32ull * mv);
+            atomicAdd(out + 9, (unsigned long long)nr);
+            atomicAdd(out + 10, (unsigned long long)nb);
+            atomicAdd(out + 11, (unsigned long long)ns);
+        }
+    }
     unsigned long long* o4 = out;
 #pragma unroll
     for (int part = 0; part < 2; ++part) {
@@ -281,7 +301,8 @@ cudaError_t launch_set_frame(FrameDev* dst, const FrameDev& src, cudaStream_t s)
 cudaError_t launch_pilot_trace(const VolConst& V, const FrameDev* FD, const SceneDev& S, int2* hit, const Tuning& T,
                                cudaStream_t s)
 {
-    int n = V.P * kPilots, b = T.trace_block;
+    int n = (V.p_hi - V.p_lo) * kPilots, b = T.trace_block;
+    if (n <= 0) return cudaSuccess;
     k_pilot_trace<<<(n + b - 1) / b, b, 0, s>>>(V, FD, S, hit);
     count_launches(1);
     return cudaGetLastError();

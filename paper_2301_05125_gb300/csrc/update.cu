@@ -71,8 +71,8 @@ __global__ void __launch_bounds__(256) k_classify(VolConst V, const FrameDev* __
 __global__ void __launch_bounds__(128) k_change_state(VolConst V, const FrameDev* __restrict__ FD, ChangeBufs B)
 {
     const FrameConst& F = FD->F;
-    int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= V.P) return;
+    int p = V.p_lo + blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= V.p_hi) return;
     uint32_t yv[8], yr[8];
     const uint8_t cl = V.cls[p];
     if (cl == 0) {  // outside V_out: no heuristics this frame; the state waits
@@ -140,8 +140,8 @@ __global__ void __launch_bounds__(128) k_change_state(VolConst V, const FrameDev
 __global__ void __launch_bounds__(128) k_change_weight(VolConst V, const FrameDev* __restrict__ FD, ChangeBufs B)
 {
     const FrameConst& F = FD->F;
-    int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= V.P) return;
+    int p = V.p_lo + blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= V.p_hi) return;
     const int X = V.dims[0], Y = V.dims[1], Z = V.dims[2];
     int ix = p % X, iy = (p / X) % Y, iz = p / (X * Y);
     uint32_t f[8] = {0, 0, 0, 0, 0, 0, 0, 0};
@@ -835,17 +835,22 @@ __device__ __forceinline__ float4 irr_texel_blend(float4 v, float sx, float sy, 
 }
 
 // The depth texel stores {mean, variance}; with batch mean m and batch
-// variance vb of k samples (sums s1, s2) the moving average of {d, d^2} becomes
+// variance vb of k samples the moving average of {d, d^2} becomes
 //   mean' = mean + w (m - mean)
 //   var'  = (1-w) var + w vb + w (1-w) (m - mean)^2
 // (every term non-negative: no cancellation in storage); c is the count.
-__device__ __forceinline__ float2 dep_texel_blend(float2 v, uint32_t& c, float s1, float s2, uint32_t k, float omh)
+// The batch arrives as sums s1, s2 of the samples' offsets d - x0 from a
+// shift x0 (the texel's first sample): m = x0 + s1/k, vb = s2/k - (s1/k)^2,
+// which cancels only at the scale of the samples' spread, not of d^2.
+__device__ __forceinline__ float2 dep_texel_blend(float2 v, uint32_t& c, float x0, float s1, float s2, uint32_t k,
+                                                  float omh)
 {
     const float kf = (float)k;
     const float w = fmaxf(omh, __fdividef(kf, (float)c + kf));
     const float ik = __frcp_rn(kf);
-    const float mb = s1 * ik;
-    const float vb = fmaxf(s2 * ik - mb * mb, 0.0f);
+    const float mo = s1 * ik;
+    const float mb = x0 + mo;
+    const float vb = fmaxf(s2 * ik - mo * mo, 0.0f);
     const float dm = mb - v.x;
     v.y = (1.0f - w) * v.y + w * vb + w * (1.0f - w) * dm * dm;
     v.x += w * dm;
@@ -900,8 +905,8 @@ __global__ void __launch_bounds__(128) k_blend(VolConst V, const FrameDev* __res
     const FrameConst& F = FD->F;
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int p = blockIdx.x * (blockDim.x >> 5) + wib;
-    if (p >= V.P) return;  // the whole warp
+    const int p = V.p_lo + blockIdx.x * (blockDim.x >> 5) + wib;
+    if (p >= V.p_hi) return;  // the whole warp
     const uint32_t base = __ldg(B.off + p);
     uint32_t m = __ldg(B.off + p + 1) - base;
     if (m > (uint32_t)(V.rays_max - kPilots) || base > V.R_main || m > V.R_main - base) {
@@ -997,36 +1002,40 @@ __global__ void __launch_bounds__(128) k_blend(VolConst V, const FrameDev* __res
     }
     for (int q = lane; q < nd * nd; q += 32) {
         const int r = tile_row(q, rnd), t = (r + 1) * Td + (q - r * nd) + 1;
-        float s1 = 0.f, s2 = 0.f;
+        // sums of the offsets from the texel's first sample x0
+        float x0 = 0.f, s1 = 0.f, s2 = 0.f;
         uint32_t k = 0;
         for (int o = 0; o < npil; ++o)
             if (pk_d[o] == t) {
                 const float x = prs[o].w;
-                s1 += x;
-                s2 += x * x;
+                if (k == 0) x0 = x;
+                const float dx = x - x0;
+                s1 += dx;
+                s2 += dx * dx;
                 ++k;
             }
         float2 v = dep_load(V, B.dep, dof + t);  // issued early: independent of the sums
         uint32_t c = B.dep_n[dof + t];
         if (m) {
             const uint32_t b0 = __ldg(beg_d + t), b1 = __ldg(beg_d + t + 1);
+            if (k == 0 && b0 < b1) x0 = __ldg(&mrec[min((uint32_t)__ldg(ord_d + b0), m - 1)].w);
             uint32_t u = b0;
             for (; u + 2 <= b1; u += 2) {  // two gathers in flight, added in order
                 const uint32_t i0 = min((uint32_t)__ldg(ord_d + u), m - 1), i1 = min((uint32_t)__ldg(ord_d + u + 1), m - 1);
-                const float x0 = __ldg(&mrec[i0].w), x1 = __ldg(&mrec[i1].w);
-                s1 += x0;
-                s2 += x0 * x0;
-                s1 += x1;
-                s2 += x1 * x1;
+                const float d0 = __ldg(&mrec[i0].w) - x0, d1 = __ldg(&mrec[i1].w) - x0;
+                s1 += d0;
+                s2 += d0 * d0;
+                s1 += d1;
+                s2 += d1 * d1;
             }
             if (u < b1) {
-                const float x = __ldg(&mrec[min((uint32_t)__ldg(ord_d + u), m - 1)].w);
-                s1 += x;
-                s2 += x * x;
+                const float dx = __ldg(&mrec[min((uint32_t)__ldg(ord_d + u), m - 1)].w) - x0;
+                s1 += dx;
+                s2 += dx * dx;
             }
             k += b1 - b0;
         }
-        if (k) v = dep_texel_blend(v, c, s1, s2, k, omh);
+        if (k) v = dep_texel_blend(v, c, x0, s1, s2, k, omh);
         if (cl == 1) c = min(c, 16u);
         dep_new[t] = v;
         dn_new[t] = (uint8_t)c;
@@ -1075,8 +1084,8 @@ __global__ void __launch_bounds__(128) k_blend_cos(VolConst V, const FrameDev* _
     const FrameConst& F = FD->F;
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int p = blockIdx.x * (blockDim.x >> 5) + wib;
-    if (p >= V.P) return;  // the whole warp
+    const int p = V.p_lo + blockIdx.x * (blockDim.x >> 5) + wib;
+    if (p >= V.p_hi) return;  // the whole warp
     const uint32_t base = __ldg(B.off + p);
     uint32_t m = __ldg(B.off + p + 1) - base;
     if (m > (uint32_t)(V.rays_max - kPilots) || base > V.R_main || m > V.R_main - base) {
@@ -1148,18 +1157,21 @@ __global__ void __launch_bounds__(128) k_blend_cos(VolConst V, const FrameDev* _
                         } else {
                             // weights (c / c_max)^50 relative to the largest c so far (the
                             // mean is scale-free; c^50 itself underflows FP32 at grazing c):
-                            // a new maximum rescales the running sums
+                            // a new maximum rescales the weight sum and the second moment.
+                            // Weighted running mean s0 and sum of squared deviations s1
+                            // (West's update of Welford's method): no cancellation between
+                            // the mean of d^2 and the square of the mean of d
                             if (c > cm[jj]) {
                                 const float sc = cm[jj] > 0.0f ? pow50(cm[jj] / c) : 0.0f;
                                 sw[jj] *= sc;
-                                s0[jj] *= sc;
                                 s1[jj] *= sc;
                                 cm[jj] = c;
                             }
                             const float wgt = pow50(c / cm[jj]);
                             sw[jj] += wgt;
-                            s0[jj] = fmaf(wgt, r.w, s0[jj]);
-                            s1[jj] = fmaf(wgt * r.w, r.w, s1[jj]);
+                            const float dx = r.w - s0[jj];
+                            s0[jj] = fmaf(dx, __fdividef(wgt, sw[jj]), s0[jj]);
+                            s1[jj] = fmaf(wgt * dx, r.w - s0[jj], s1[jj]);
                         }
                     }
                 }
@@ -1181,7 +1193,8 @@ __global__ void __launch_bounds__(128) k_blend_cos(VolConst V, const FrameDev* _
             } else {
                 float2 v = dep_load(V, B.dep, dof + t);
                 uint32_t c = B.dep_n[dof + t];
-                if (ok) v = dep_texel_blend(v, c, s0[j] * inv, s1[j] * inv, k[j], omh);
+                // the batch as mean s0 with zero offset sum and k x its variance s1 / sw
+                if (ok) v = dep_texel_blend(v, c, s0[j], 0.0f, s1[j] * inv, k[j], omh);
                 if (cl == 1) c = min(c, 16u);
                 dep_new[t] = v;
                 dn_new[t] = (uint8_t)c;
@@ -1201,7 +1214,7 @@ __global__ void __launch_bounds__(128) k_blend_cos(VolConst V, const FrameDev* _
 // texel summed first, in order); then the batched moving average and the
 // stores of k_blend.
 struct MhLayout {
-    uint32_t acc_i, acc_d, cnt_d, dn, e_rec, dacc_i, dacc_d, dcnt_d, total;
+    uint32_t acc_i, acc_d, cnt_d, sh_d, dn, e_rec, dacc_i, dacc_d, dcnt_d, dsh_d, total;
 };
 
 __host__ __device__ inline MhLayout mh_layout(int Ti, int Td, bool dyn)
@@ -1210,15 +1223,17 @@ __host__ __device__ inline MhLayout mh_layout(int Ti, int Td, bool dyn)
     MhLayout L;
     uint32_t o = 0;
     L.acc_i = o, o += al16(16 * ti2);  // {sum r, g, b, count}, then the updated texel
-    L.acc_d = o, o += al16(8 * td2);   // {sum d, sum d^2}, then the updated texel
+    L.acc_d = o, o += al16(8 * td2);   // {sum d - x0, sum (d - x0)^2}, then the updated texel
     L.cnt_d = o, o += al16(4 * td2);
+    L.sh_d = o, o += al16(4 * td2);    // x0: the texel's first sample (the shift of the sums)
     L.dn = o, o += al16(td2);
     L.e_rec = o, o += 16 * 32;  // one chunk of samples: {r, g, b, depth}
-    L.dacc_i = L.dacc_d = L.dcnt_d = o;
+    L.dacc_i = L.dacc_d = L.dcnt_d = L.dsh_d = o;
     if (dyn) {  // the dynamic rays' sums: a second batch step
         L.dacc_i = o, o += al16(16 * ti2);
         L.dacc_d = o, o += al16(8 * td2);
         L.dcnt_d = o, o += al16(4 * td2);
+        L.dsh_d = o, o += al16(4 * td2);
     }
     L.total = o;
     return L;
@@ -1230,7 +1245,7 @@ __host__ __device__ inline MhLayout mh_layout(int Ti, int Td, bool dyn)
 // adds the sum to the texel.  Texels are distinct across groups, so the
 // adds do not race; per texel the chunks are added in order.
 __device__ __forceinline__ void mh_accumulate(const float4* e_rec, int ki, int kd, float4* acc_i, float2* acc_d,
-                                              uint32_t* cnt_d, int lane)
+                                              uint32_t* cnt_d, float* sh_d, int lane)
 {
     const uint32_t below = (1u << lane) - 1u;
     const uint32_t gi = __match_any_sync(0xFFFFFFFFu, ki), gd = __match_any_sync(0xFFFFFFFFu, kd);
@@ -1250,11 +1265,15 @@ __device__ __forceinline__ void mh_accumulate(const float4* e_rec, int ki, int k
         acc_i[ki] = t;
     }
     if (kd >= 0 && (gd & below) == 0u) {
+        // offsets from the texel's first sample (this group's first when the
+        // texel has none yet)
+        if (cnt_d[kd] == 0u) sh_d[kd] = e_rec[__ffs(gd) - 1].w;
+        const float x0 = sh_d[kd];
         float s1 = 0.f, s2 = 0.f;
         for (uint32_t m = gd; m; m &= m - 1u) {
-            const float x = e_rec[__ffs(m) - 1].w;
-            s1 += x;
-            s2 += x * x;
+            const float dx = e_rec[__ffs(m) - 1].w - x0;
+            s1 += dx;
+            s2 += dx * dx;
         }
         float2 t = acc_d[kd];
         t.x += s1;
@@ -1289,6 +1308,7 @@ __global__ void __launch_bounds__(128) k_mh_blend(VolConst V, const FrameDev* __
     float4* acc_i = reinterpret_cast<float4*>(ws + L.acc_i);
     float2* acc_d = reinterpret_cast<float2*>(ws + L.acc_d);
     uint32_t* cnt_d = reinterpret_cast<uint32_t*>(ws + L.cnt_d);
+    float* sh_d = reinterpret_cast<float*>(ws + L.sh_d);
     uint8_t* dn = ws + L.dn;
     float4* e_rec = reinterpret_cast<float4*>(ws + L.e_rec);
     for (int t = lane; t < ti2; t += 32) acc_i[t] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -1299,6 +1319,7 @@ __global__ void __launch_bounds__(128) k_mh_blend(VolConst V, const FrameDev* __
     float4* dacc_i = reinterpret_cast<float4*>(ws + L.dacc_i);
     float2* dacc_d = reinterpret_cast<float2*>(ws + L.dacc_d);
     uint32_t* dcnt_d = reinterpret_cast<uint32_t*>(ws + L.dcnt_d);
+    float* dsh_d = reinterpret_cast<float*>(ws + L.dsh_d);
     if (V.dyn) {
         for (int t = lane; t < ti2; t += 32) dacc_i[t] = make_float4(0.f, 0.f, 0.f, 0.f);
         for (int t = lane; t < td2; t += 32) {
@@ -1316,7 +1337,7 @@ __global__ void __launch_bounds__(128) k_mh_blend(VolConst V, const FrameDev* __
             kd = texel_of(e, nd);
         }
         __syncwarp();
-        mh_accumulate(e_rec, ki, kd, acc_i, acc_d, cnt_d, lane);
+        mh_accumulate(e_rec, ki, kd, acc_i, acc_d, cnt_d, sh_d, lane);
         __syncwarp();
     }
     // chunks of 32 samples, one per lane; the next chunk's loads are issued
@@ -1344,7 +1365,7 @@ __global__ void __launch_bounds__(128) k_mh_blend(VolConst V, const FrameDev* __
             x = __ldg(B.rec + qn);
             hn = __ldg(B.hit_neg + qn);
         }
-        mh_accumulate(e_rec, ki, kd, acc_i, acc_d, cnt_d, lane);
+        mh_accumulate(e_rec, ki, kd, acc_i, acc_d, cnt_d, sh_d, lane);
         __syncwarp();
     }
     // the dynamic rays of the probe (each at its own texel centre): sums of
@@ -1363,7 +1384,7 @@ __global__ void __launch_bounds__(128) k_mh_blend(VolConst V, const FrameDev* __
             }
         }
         __syncwarp();
-        mh_accumulate(e_rec, ki, kd, dacc_i, dacc_d, dcnt_d, lane);
+        mh_accumulate(e_rec, ki, kd, dacc_i, dacc_d, dcnt_d, dsh_d, lane);
         __syncwarp();
     }
     const float omh = 1.0f - V.hyst;
@@ -1387,11 +1408,11 @@ __global__ void __launch_bounds__(128) k_mh_blend(VolConst V, const FrameDev* __
         const uint32_t k = cnt_d[t];
         float2 v = dep_load(V, B.dep, dof + t);
         uint32_t c = B.dep_n[dof + t];
-        if (k) v = dep_texel_blend(v, c, sum.x, sum.y, k, omh);
+        if (k) v = dep_texel_blend(v, c, sh_d[t], sum.x, sum.y, k, omh);
         if (V.dyn) {
             const uint32_t kd2 = dcnt_d[t];
             const float2 ds = dacc_d[t];
-            if (kd2) v = dep_texel_blend(v, c, ds.x, ds.y, kd2, 1.0f - V.hyst_dyn);
+            if (kd2) v = dep_texel_blend(v, c, dsh_d[t], ds.x, ds.y, kd2, 1.0f - V.hyst_dyn);
         }
         if (cl == 1) c = min(c, 16u);
         acc_d[t] = v;
@@ -1439,12 +1460,18 @@ BlendPlan carve_blend_plan(void* base, int M, int Ti, int Td)
 // shared memory of one probe (one warp) of k_blend
 size_t blend_smem_bytes(const VolConst& V) { return blend_layout(V.Ti, V.Td).total; }
 
-cudaError_t launch_change(const VolConst& V, const FrameDev* FD, const ChangeBufs& B, cudaStream_t s)
+cudaError_t launch_change(const VolConst& V, const FrameDev* FD, const ChangeBufs& B, cudaStream_t s, int parts)
 {
-    k_change_state<<<(V.P + 127) / 128, 128, 0, s>>>(V, FD, B);
-    count_launches(1);
-    k_change_weight<<<(V.P + 127) / 128, 128, 0, s>>>(V, FD, B);
-    count_launches(1);
+    const int n = V.p_hi - V.p_lo;
+    if (n <= 0) return cudaSuccess;
+    if (parts & 1) {
+        k_change_state<<<(n + 127) / 128, 128, 0, s>>>(V, FD, B);
+        count_launches(1);
+    }
+    if (parts & 2) {
+        k_change_weight<<<(n + 127) / 128, 128, 0, s>>>(V, FD, B);
+        count_launches(1);
+    }
     return cudaGetLastError();
 }
 
@@ -1517,7 +1544,9 @@ cudaError_t launch_blend(const VolConst& V, const FrameDev* FD, const BlendBufs&
         cudaError_t e = raise_smem_limit((const void*)k_blend, sm);
         if (e != cudaSuccess) return e;
     }
-    k_blend<<<(V.P + wpb - 1) / wpb, 32 * wpb, sm, s>>>(V, FD, B);
+    const int np = V.p_hi - V.p_lo;
+    if (np <= 0) return cudaSuccess;
+    k_blend<<<(np + wpb - 1) / wpb, 32 * wpb, sm, s>>>(V, FD, B);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -1532,7 +1561,9 @@ cudaError_t launch_blend_cos(const VolConst& V, const FrameDev* FD, const BlendB
         cudaError_t e = raise_smem_limit((const void*)k_blend_cos, sm);
         if (e != cudaSuccess) return e;
     }
-    k_blend_cos<<<(V.P + wpb - 1) / wpb, 32 * wpb, sm, s>>>(V, FD, B);
+    const int np = V.p_hi - V.p_lo;
+    if (np <= 0) return cudaSuccess;
+    k_blend_cos<<<(np + wpb - 1) / wpb, 32 * wpb, sm, s>>>(V, FD, B);
     count_launches(1);
     return cudaGetLastError();
 }
