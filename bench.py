@@ -3,9 +3,12 @@
 
 A step is one whole update (moving-occluder vertex update and BVH rebuild,
 pilot rays, heuristics, allocation, adaptive rays with shadow rays and the
-multi-bounce query, blend) of the tunnel + city workload: 32x16x32 probes,
-256 rays/probe (4,194,304 rays per update), ~200k triangles, 3 moving point
-lights + sun, 20 moving occluders; FP32 atlases.
+multi-bounce query, blend) of the order-of-magnitude workload: 64x32x64 =
+131,072 probes at 4 m over the seeded city generator scaled to ~2M
+triangles, 64 rays/probe on average (min 4, raised to 8 by the pilots; max
+512): 8,388,608 rays per update; 3 moving point lights + sun, moving tunnel
+gates; FP32 atlases.  The same workload with half atlases, and the 16,384-
+probe tunnel + city workload (256 rays/probe), are measured beside it.
 
 Prints one JSON line (rank 0).  `value` is probe rays per second per update
 with inputs resident in HBM (L2 flushed between timed steps); `e2e` is the
@@ -74,14 +77,14 @@ def _source_hash(kernel=None):
     return h.hexdigest()[:16]
 
 
-def _ncu_traffic(kernel):
-    """DRAM bytes per launch from a committed ncu summary, if it was taken on
-    the current kernel sources (else None)."""
+def _ncu_traffic(kernel, workload="tunnel_city"):
+    """DRAM bytes per launch from a committed ncu summary of this kernel on
+    this workload, if it was taken on the current kernel sources (else None)."""
     p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if not os.path.exists(p):
         return None
     d = json.load(open(p))
-    e = d.get(kernel)
+    e = d.get(kernel + "@" + workload) or (d.get(kernel) if workload == "tunnel_city" else None)
     if not e or e.get("source_hash") != _source_hash(kernel):
         return None
     return e.get("dram_bytes_per_launch_scaled", e.get("dram_bytes_per_launch"))
@@ -168,34 +171,56 @@ def _workload(name, seed):
     return {"tunnel_city": S.tunnel_city, "box_room": S.box_room, "scaled": S.scaled}[name](seed)
 
 
-def _cpu_baseline(w, budget_s=20.0, threads=None, steps=None, sampler=0, alpha=1.0):
-    """The oracle as it stands on the host cores: full updates of the same
-    workload until the time budget is spent (at least one)."""
+def _cpu_baseline_line(w, rays, args):
+    """The oracle as it stands, timed on all host cores on a bounded sample of
+    the same workload.  Its first update is untimed (the oracle builds its
+    CPU BVH there).  Then, if one update fits the time budget, whole updates
+    are timed until the budget is spent (at most 8); otherwise the trace and
+    shading (pilot and adaptive rays, shadow rays, multi-bounce query) of a
+    1 % probe sample of the next frame, and the rate is that sample's."""
     from oracle import oracle as O
 
-    threads = threads or os.cpu_count() or 1
+    threads = os.cpu_count() or 1
     vd = w.volume
     ov = O.OracleVolume(vd["origin"], vd["spacing"], vd["dims"], vd["irr_interior"], vd["depth_interior"],
                         vd["rays_avg"], vd["rays_min"], vd["rays_max"], vd["hysteresis"], vd["depth_max"],
-                        vd["tr_theta"], threads=threads, sampler=sampler, alpha=alpha)
+                        vd["tr_theta"], threads=threads, sampler=int(args.sampler), alpha=args.alpha)
     ov.set_scene(w.verts, w.idx, w.albedo)
-    times = []
-    f = 0
-    t_start = time.perf_counter()
-    while True:
-        if w.dyn_at is not None:
-            ov.move_vertices(w.dyn_first, w.dyn_at(f))
+    have_dyn = w.dyn_at is not None and w.dyn_count > 0
+    if have_dyn:
+        ov.move_vertices(w.dyn_first, w.dyn_at(0))
+    t0 = time.perf_counter()
+    ov.update(0, w.seed, w.lights_at(0), w.sky)
+    t_first = time.perf_counter() - t0
+    budget = args.cpu_budget
+    if t_first <= budget:
+        times = []
+        f = 1
+        t_start = time.perf_counter()
+        while not times or (time.perf_counter() - t_start < budget and f <= 8):
+            if have_dyn:
+                ov.move_vertices(w.dyn_first, w.dyn_at(f))
+            t0 = time.perf_counter()
+            ov.update(f, w.seed, w.lights_at(f), w.sky)
+            times.append(time.perf_counter() - t0)
+            f += 1
+        value = rays / float(np.mean(times))
+        sample = ("%d full oracle update(s) of the same workload (frames 1-%d, every probe and phase, moving-part "
+                  "BVH rebuild included) after an untimed first update" % (len(times), len(times)))
+    else:
+        probes = np.arange(0, w.n_probes, 100, dtype=np.int32)
+        if have_dyn:
+            ov.move_vertices(w.dyn_first, w.dyn_at(1))
         t0 = time.perf_counter()
-        ov.update(f, w.seed, w.lights_at(f), w.sky)
-        times.append(time.perf_counter() - t0)
-        f += 1
-        if steps is not None:
-            if f >= steps:
-                break
-        elif time.perf_counter() - t_start > budget_s or f >= 8:
-            break
+        r = ov.trace_shade_probes(1, w.seed, w.lights_at(1), probes, w.sky)
+        dt = time.perf_counter() - t0
+        value = r / dt
+        sample = ("trace + shade (pilot and adaptive rays, shadow rays, multi-bounce query) of every 100th probe "
+                  "(1 %% sample: %d probes, %d rays) on frame 1, after an untimed full update of frame 0 "
+                  "(%.1f s, CPU BVH build included); heuristics, allocation and blend are not in the sample"
+                  % (len(probes), r, t_first))
     ov.close()
-    return times, threads
+    return {"value": value, "unit": "rays/s", "cores": threads, "kind": "oracle", "sample": sample}
 
 
 def run_reference(args):
@@ -519,7 +544,7 @@ def _cosine_section(args, adgi, torch, dev):
     """The same workload with DDGI's cosine-gather blend (blend_mode = 1):
     every ray feeds every texel of its hemisphere (ALU-bound), timed like
     the headline line."""
-    w = _workload(args.workload, args.seed)
+    w = _workload("tunnel_city", args.seed)
     vd = dict(w.volume)
     vd["blend_mode"] = 1
     stream = torch.cuda.Stream(device=dev)
@@ -552,7 +577,7 @@ def _cosine_section(args, adgi, torch, dev):
 
 
 def _metropolis_run(args, adgi, torch, dev, dyn_ratio):
-    w = _workload(args.workload, args.seed)
+    w = _workload(args.workload if args.sampler else "tunnel_city", args.seed)
     vd = dict(w.volume)
     vd["sampler"], vd["alpha"] = 1, 1.0
     vd["dyn_ratio"], vd["hysteresis_dyn"] = dyn_ratio, 0.91
@@ -598,6 +623,187 @@ def _metropolis_run(args, adgi, torch, dev, dyn_ratio):
     return out
 
 
+def _measure(args, adgi, torch, dev, w, vd, steps, warmup, ws, e2e_on, sampler=False):
+    """Time `steps` whole updates of workload w (volume description vd) after
+    `warmup` untimed ones: CUDA events on the volume's stream around each
+    update, L2 flushed before each; library phase events; counted traversal
+    work; optionally the end-to-end leg through the C ABI with host buffers."""
+    stream = torch.cuda.Stream(device=dev)
+    vol = adgi.Volume(stream=stream.cuda_stream, **vd)
+    vol.set_scene(w.verts, w.idx, w.albedo)
+    adgi.adgi_enable_timing(vol.h, True)
+    n_frames = warmup + steps
+    have_dyn = w.dyn_at is not None and w.dyn_count > 0
+    if have_dyn:
+        dyn_host = np.stack([w.dyn_at(f) for f in range(n_frames + 12)]).astype(np.float32)
+        dyn_dev = torch.from_numpy(dyn_host).to(dev)
+    frames = [adgi.make_frame(f, w.seed, w.lights_at(f), w.sky) for f in range(n_frames + 12)]
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > 129 MB L2
+
+    def step(f):
+        if have_dyn:
+            vol.move_vertices(w.dyn_first, dyn_dev[f])
+        adgi.adgi_update(vol.h, frames[f])
+
+    with torch.cuda.stream(stream):
+        for f in range(warmup):
+            step(f)
+    torch.cuda.synchronize()
+    phases = {k: [] for k in adgi.PHASES}
+    shadow_ms = [[], []]
+    plan_ms = []
+    dev_ms, host_ms = [], []
+    tiles_touched, rays_blended = [], []
+    clocks = Clocks()
+    launches0 = vol.stats().kernels_launched
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t_wall0 = time.perf_counter()
+    for k in range(steps):
+        f = warmup + k
+        with torch.cuda.stream(stream):
+            flush.fill_(float(k))
+        stream.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        th0 = time.perf_counter()
+        e0.record(stream)
+        step(f)
+        e1.record(stream)
+        e1.synchronize()
+        host_ms.append(1e3 * (time.perf_counter() - th0))
+        dev_ms.append(e0.elapsed_time(e1))
+        st = vol.stats()
+        for i, name in enumerate(adgi.PHASES):
+            phases[name].append(st.ms_phase[i])
+        for i in range(2):
+            shadow_ms[i].append(st.ms_shadow[i])
+        plan_ms.append(st.ms_blend_plan)
+        even = f % 2 == 0
+        if sampler:  # samples per probe from the grouping
+            m = np.diff(vol.mh_off().astype(np.int64))
+        else:
+            m = vol.n().astype(np.int64) - 8
+        tiles_touched.append(vol.P if even else int((m > 0).sum()))
+        rays_blended.append(int(m.sum()) + (8 * vol.P if even else 0))
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t_wall0
+    clk = clocks.stop()
+    launches = vol.stats().kernels_launched - launches0
+    counts = adgi.adgi_count_traversal(vol.h, frames[warmup + steps - 1])
+    ms_step = _job_ms(float(np.mean(dev_ms)), ws, dev)
+    rays = int(vol.stats().rays_per_update)  # Metropolis: 8 pilots per probe + a +w and a -w ray per sample
+    hbm, smax_nominal, peak_src = _peaks()
+    sms, smax_dev = _device_alu(torch, dev, smax_nominal)
+    mean_ph = {k: float(np.mean(v)) for k, v in phases.items()}
+    # per-kernel device times (CUDA events on the volume's stream around each
+    # kernel) and the counted traversal work of each traversal kernel
+    main_k, blend_k = ("k_mh_trace", "k_mh_blend") if sampler else ("k_main_trace", "k_blend")
+    kern_ms = {main_k: mean_ph["trace"], "k_shadow (adaptive rays)": float(np.mean(shadow_ms[1])),
+               "k_pilot_trace": mean_ph["pilot_trace"], "k_shadow (pilot rays)": float(np.mean(shadow_ms[0])),
+               blend_k: mean_ph["blend"]}
+    if sampler:
+        kern_ms["allocation + chains + grouping (phase)"] = mean_ph["allocation"]
+    else:
+        kern_ms["k_blend_plan (side stream, overlapped)"] = float(np.mean(plan_ms))
+    work = {
+        "k_pilot_trace": OPS_BOX * counts[0] + OPS_TRI * counts[1],
+        "k_shadow (pilot rays)": OPS_BOX * counts[2] + OPS_TRI * counts[3],
+        main_k: OPS_BOX * counts[4] + OPS_TRI * counts[5],
+        "k_shadow (adaptive rays)": OPS_BOX * counts[6] + OPS_TRI * counts[7],
+    }
+    dominant = max((k for k in kern_ms if "side stream" not in k), key=kern_ms.get)
+    # ALU roofline of a traversal kernel: counted FP32 lane ops / time vs
+    # SMs x 128 FP32 lanes x maximum SM clock, both read from the device
+    alu_peak = sms * 128 * smax_dev * 1e6 / 1e12  # T lane-ops/s
+    fp16 = int(vd.get("atlas_fp16", 0))
+    tile_bytes = TILE_BYTES_FP32 if not fp16 else 2 * (8 * 8 * 8 + 16 * 16 * 4 + 16 * 16)
+    # a Metropolis sample reads its direction (16 B), its +w record (16 B) and its -w hit (8 B)
+    rec_bytes = MH_REC_BYTES if sampler else REC_BYTES
+    blend_bytes = float(np.mean(tiles_touched)) * tile_bytes + float(np.mean(rays_blended)) * rec_bytes
+    blend_ach = blend_bytes / (mean_ph["blend"] / 1e3) / 1e9
+    if dominant in work:
+        ach = work[dominant] / (kern_ms[dominant] / 1e3) / 1e12
+        kbase = dominant.split(" ")[0]
+        roof = {"bound": "alu", "achieved": ach, "peak": alu_peak, "unit": "Tops/s (FP32 lane ops)",
+                "frac": ach / alu_peak, "traffic": _ncu_traffic(kbase, w.name), "kernel": dominant,
+                "ms": kern_ms[dominant], "work_lane_ops": work[dominant],
+                "peak_source": "%d SMs x 128 FP32 lanes x %.0f MHz (device attributes)" % (sms, smax_dev)}
+    else:
+        roof = {"bound": "hbm", "achieved": blend_ach, "peak": hbm, "unit": "GB/s", "frac": blend_ach / hbm,
+                "traffic": _ncu_traffic(blend_k, w.name), "kernel": blend_k, "ms": mean_ph["blend"]}
+    roof_blend = {"bound": "hbm", "achieved": blend_ach, "peak": hbm, "unit": "GB/s", "frac": blend_ach / hbm,
+                  "traffic": _ncu_traffic(blend_k, w.name), "algorithmic_bytes": blend_bytes, "ms": mean_ph["blend"],
+                  "kernel": blend_k if sampler else
+                  "k_blend (the per-frame plan runs beforehand on a side stream, see kernels_ms)",
+                  "peak_source": "%s hbm_gbs" % peak_src}
+    # end to end through the C ABI with host buffers
+    e2e = None
+    if e2e_on:
+        nq = 65536
+        rng = np.random.default_rng(7)
+        o = np.array(vd["origin"], np.float32)
+        ext = np.array(vd["spacing"], np.float32) * (np.array(vd["dims"]) - 1)
+        qpos = torch.from_numpy((o + rng.random((nq, 3)) * ext).astype(np.float32)).pin_memory()
+        qnrm = torch.from_numpy(rng.normal(size=(nq, 3)).astype(np.float32)).pin_memory()
+        qout = torch.empty((nq, 3), dtype=torch.float32).pin_memory()
+        dyn_pin = torch.from_numpy(dyn_host).pin_memory() if have_dyn else None
+        f0 = warmup + steps
+        e2e_ms = []
+        # the update as a replay of the volume's captured graph (one launch for
+        # the whole update); the untimed first call captures it
+        if have_dyn:
+            adgi.adgi_move_vertices(vol.h, w.dyn_first, dyn_pin[f0].numpy())
+        adgi.adgi_update_graph(vol.h, frames[f0])
+        torch.cuda.synchronize()
+        for k in range(min(steps, 10)):
+            f = f0 + (k % 2)
+            t0 = time.perf_counter()
+            if have_dyn:
+                adgi.adgi_move_vertices(vol.h, w.dyn_first, dyn_pin[f].numpy())
+            adgi.adgi_update_graph(vol.h, frames[f])
+            adgi.adgi_query_irradiance(vol.h, qpos.numpy(), qnrm.numpy(), qout.numpy())
+            e2e_ms.append(1e3 * (time.perf_counter() - t0))
+        h2d = (w.dyn_count * 12 if have_dyn else 0) + 2 * nq * 12 + len(w.lights_at(0)) * 28
+        e2e = {"value": ws * rays / (float(np.mean(e2e_ms)) / 1e3), "unit": "rays/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": nq * 12, "ms_per_step": float(np.mean(e2e_ms)),
+               "includes": "host->device occluder vertices + 65536-point shading query (positions, normals) "
+                           "from pinned memory, update (graph replay), query results back to the host"}
+    res = {"value": ws * rays / (ms_step / 1e3), "ms_step": ms_step, "rays": rays, "dev_ms": dev_ms,
+           "host_ms": host_ms, "phases": mean_ph, "kernels": kern_ms, "counts": counts, "roofline": roof,
+           "roofline_blend": roof_blend, "e2e": e2e, "launches": int(launches), "clocks": clk, "wall": wall,
+           "shadow_rays": int(vol.stats().shadow_rays), "device_bytes": int(vol.stats().device_bytes)}
+    vol.close()
+    return res
+
+
+def _device_alu(torch, dev, smax_fallback):
+    """SM count and maximum SM clock (MHz) of the device"""
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = smax_fallback
+    try:
+        out = subprocess.run(["nvidia-smi", "-i", str(dev.index or 0), "--query-gpu=clocks.max.sm",
+                              "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=20)
+        mhz = float(out.stdout.strip().splitlines()[0])
+    except Exception:
+        pass
+    return int(sms), float(mhz)
+
+
+def _side_line(r, w):
+    """a workload measured beside the headline: its rate, phases and roofline"""
+    return {"workload": w.name, "probes": w.n_probes, "triangles": int(w.n_tris), "rays_per_update": r["rays"],
+            "value": r["value"], "unit": "rays/s", "ms_per_update": r["ms_step"],
+            "latency_ms": {"device_p50": float(np.percentile(r["dev_ms"], 50)),
+                           "device_p99": float(np.percentile(r["dev_ms"], 99))},
+            "phases_ms": r["phases"], "kernels_ms": r["kernels"], "roofline": r["roofline"],
+            "roofline_blend": r["roofline_blend"]}
+
+
 def run_ours(args):
     import torch
 
@@ -624,149 +830,23 @@ def run_ours(args):
         vd["atlas_fp16"] = 1
     if args.sampler:
         vd["sampler"], vd["alpha"] = 1, args.alpha
-    stream = torch.cuda.Stream(device=dev)
-    vol = adgi.Volume(stream=stream.cuda_stream, **vd)
-    vol.set_scene(w.verts, w.idx, w.albedo)
-    adgi.adgi_enable_timing(vol.h, True)
-    n_frames = args.warmup + args.steps
-    have_dyn = w.dyn_at is not None and w.dyn_count > 0
-    if have_dyn:
-        dyn_host = np.stack([w.dyn_at(f) for f in range(n_frames + args.steps + 2)]).astype(np.float32)
-        dyn_dev = torch.from_numpy(dyn_host).to(dev)
-    frames = [adgi.make_frame(f, w.seed, w.lights_at(f), w.sky) for f in range(n_frames + args.steps + 2)]
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > 129 MB L2
-
-    def step(f):
-        if have_dyn:
-            vol.move_vertices(w.dyn_first, dyn_dev[f])
-        adgi.adgi_update(vol.h, frames[f])
-
-    with torch.cuda.stream(stream):
-        for f in range(args.warmup):
-            step(f)
-    torch.cuda.synchronize()
-    phases = {k: [] for k in adgi.PHASES}
-    shadow_ms = [[], []]
-    plan_ms = []
-    dev_ms, host_ms = [], []
-    tiles_touched, rays_blended = [], []
-    clocks = Clocks()
-    launches0 = vol.stats().kernels_launched
-    if ws > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    clocks.start()
-    t_wall0 = time.perf_counter()
-    for k in range(args.steps):
-        f = args.warmup + k
-        with torch.cuda.stream(stream):
-            flush.fill_(float(k))
-        stream.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        th0 = time.perf_counter()
-        e0.record(stream)
-        step(f)
-        e1.record(stream)
-        e1.synchronize()
-        host_ms.append(1e3 * (time.perf_counter() - th0))
-        dev_ms.append(e0.elapsed_time(e1))
-        st = vol.stats()
-        for i, name in enumerate(adgi.PHASES):
-            phases[name].append(st.ms_phase[i])
-        for i in range(2):
-            shadow_ms[i].append(st.ms_shadow[i])
-        plan_ms.append(st.ms_blend_plan)
-        even = f % 2 == 0
-        if args.sampler:  # samples per probe from the grouping
-            m = np.diff(vol.mh_off().astype(np.int64))
-        else:
-            m = vol.n().astype(np.int64) - 8
-        tiles_touched.append(vol.P if even else int((m > 0).sum()))
-        rays_blended.append(int(m.sum()) + (8 * vol.P if even else 0))
-    torch.cuda.synchronize()
-    wall = time.perf_counter() - t_wall0
-    clk = clocks.stop()
-    launches = vol.stats().kernels_launched - launches0
-    last_frame = frames[args.warmup + args.steps - 1]
-    counts = adgi.adgi_count_traversal(vol.h, last_frame)
-    ms_step = _job_ms(float(np.mean(dev_ms)), ws, dev)
-    rays = int(vol.stats().rays_per_update)  # Metropolis: 8 pilots per probe + a +w and a -w ray per sample
-    value = ws * rays / (ms_step / 1e3)
-    hbm, smax_nominal, peak_src = _peaks()
-    mean_ph = {k: float(np.mean(v)) for k, v in phases.items()}
-    # per-kernel device times (CUDA events on the volume's stream around each
-    # kernel) and the counted traversal work of each traversal kernel
-    main_k, blend_k = ("k_mh_trace", "k_mh_blend") if args.sampler else ("k_main_trace", "k_blend")
-    kern_ms = {main_k: mean_ph["trace"], "k_shadow (adaptive rays)": float(np.mean(shadow_ms[1])),
-               "k_pilot_trace": mean_ph["pilot_trace"], "k_shadow (pilot rays)": float(np.mean(shadow_ms[0])),
-               blend_k: mean_ph["blend"]}
-    if args.sampler:
-        kern_ms["allocation + chains + grouping (phase)"] = mean_ph["allocation"]
-    else:
-        kern_ms["k_blend_plan (side stream, overlapped)"] = float(np.mean(plan_ms))
-    work = {
-        "k_pilot_trace": OPS_BOX * counts[0] + OPS_TRI * counts[1],
-        "k_shadow (pilot rays)": OPS_BOX * counts[2] + OPS_TRI * counts[3],
-        main_k: OPS_BOX * counts[4] + OPS_TRI * counts[5],
-        "k_shadow (adaptive rays)": OPS_BOX * counts[6] + OPS_TRI * counts[7],
-    }
-    dominant = max((k for k in kern_ms if "side stream" not in k), key=kern_ms.get)
-    # ALU roofline of a traversal kernel: counted FP32 lane ops / time vs
-    # 152 SMs x 128 FP32 lanes x max SM clock
-    alu_peak = 152 * 128 * smax_nominal * 1e6 / 1e12  # T lane-ops/s
-    tile_bytes = TILE_BYTES_FP32 if not args.fp16 else 2 * (8 * 8 * 8 + 16 * 16 * 4 + 16 * 16)
-    # a Metropolis sample reads its direction (16 B), its +w record (16 B) and its -w hit (8 B)
-    rec_bytes = MH_REC_BYTES if args.sampler else REC_BYTES
-    blend_bytes = float(np.mean(tiles_touched)) * tile_bytes + float(np.mean(rays_blended)) * rec_bytes
-    blend_ach = blend_bytes / (mean_ph["blend"] / 1e3) / 1e9
-    if dominant in work:
-        ach = work[dominant] / (kern_ms[dominant] / 1e3) / 1e12
-        kbase = dominant.split(" ")[0]
-        roof = {"bound": "alu", "achieved": ach, "peak": alu_peak, "unit": "Tops/s (FP32 lane ops)",
-                "frac": ach / alu_peak, "traffic": _ncu_traffic(kbase), "kernel": dominant,
-                "ms": kern_ms[dominant], "work_lane_ops": work[dominant],
-                "peak_source": "152 SMs x 128 FP32 lanes x %.0f MHz (nominal max clock)" % smax_nominal}
-    else:
-        roof = {"bound": "hbm", "achieved": blend_ach, "peak": hbm, "unit": "GB/s", "frac": blend_ach / hbm,
-                "traffic": _ncu_traffic(blend_k), "kernel": blend_k, "ms": mean_ph["blend"]}
-    roof_blend = {"bound": "hbm", "achieved": blend_ach, "peak": hbm, "unit": "GB/s", "frac": blend_ach / hbm,
-                  "traffic": _ncu_traffic(blend_k), "algorithmic_bytes": blend_bytes, "ms": mean_ph["blend"],
-                  "kernel": blend_k if args.sampler else
-                  "k_blend (the per-frame plan runs beforehand on a side stream, see kernels_ms)",
-                  "peak_source": "%s hbm_gbs" % peak_src}
-    # end to end through the C ABI with host buffers
-    e2e = None
-    if not args.no_e2e:
-        nq = 65536
-        rng = np.random.default_rng(7)
-        o = np.array(vd["origin"], np.float32)
-        ext = np.array(vd["spacing"], np.float32) * (np.array(vd["dims"]) - 1)
-        qpos = torch.from_numpy((o + rng.random((nq, 3)) * ext).astype(np.float32)).pin_memory()
-        qnrm = torch.from_numpy(rng.normal(size=(nq, 3)).astype(np.float32)).pin_memory()
-        qout = torch.empty((nq, 3), dtype=torch.float32).pin_memory()
-        dyn_pin = torch.from_numpy(dyn_host).pin_memory() if have_dyn else None
-        f0 = args.warmup + args.steps
-        e2e_ms = []
-        # the update as a replay of the volume's captured graph (one launch for
-        # the whole update); the untimed first call captures it
-        if have_dyn:
-            adgi.adgi_move_vertices(vol.h, w.dyn_first, dyn_pin[f0].numpy())
-        adgi.adgi_update_graph(vol.h, frames[f0])
-        torch.cuda.synchronize()
-        for k in range(min(args.steps, 10)):
-            f = f0 + (k % 2)
-            t0 = time.perf_counter()
-            if have_dyn:
-                adgi.adgi_move_vertices(vol.h, w.dyn_first, dyn_pin[f].numpy())
-            adgi.adgi_update_graph(vol.h, frames[f])
-            adgi.adgi_query_irradiance(vol.h, qpos.numpy(), qnrm.numpy(), qout.numpy())
-            e2e_ms.append(1e3 * (time.perf_counter() - t0))
-        h2d = (w.dyn_count * 12 if have_dyn else 0) + 2 * nq * 12 + len(w.lights_at(0)) * 28
-        e2e = {"value": ws * rays / (float(np.mean(e2e_ms)) / 1e3), "unit": "rays/s", "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": nq * 12, "ms_per_step": float(np.mean(e2e_ms)),
-               "includes": "host->device occluder vertices + 65536-point shading query (positions, normals) "
-                           "from pinned memory, update (graph replay), query results back to the host"}
+    r = _measure(args, adgi, torch, dev, w, vd, args.steps, args.warmup, ws, not args.no_e2e, args.sampler)
+    # the same workload with half atlases (FP32 blending), timed the same way
+    half = None
+    if rank == 0 and not args.fp16 and not args.sampler and not args.no_precision:
+        vh = dict(vd)
+        vh["atlas_fp16"] = 1
+        rh = _measure(args, adgi, torch, dev, w, vh, max(4, min(args.steps, 30)), 3, 1, False)
+        half = {"value": rh["value"], "unit": "rays/s", "ms_per_update": rh["ms_step"],
+                "latency_ms": {"device_p50": float(np.percentile(rh["dev_ms"], 50)),
+                               "device_p99": float(np.percentile(rh["dev_ms"], 99))},
+                "phases_ms": rh["phases"], "roofline_blend": rh["roofline_blend"],
+                "error_vs_fp64_oracle": "tests/test_gpu_scaled.py (scaled) and tests/test_gpu_fp16.py state it"}
+    side = None
+    if rank == 0 and args.workload != "tunnel_city" and not args.no_side:
+        wt = _workload("tunnel_city", args.seed)
+        rt = _measure(args, adgi, torch, dev, wt, dict(wt.volume), max(4, min(args.steps, 20)), 3, 1, False)
+        side = _side_line(rt, wt)
     batched = None
     if rank == 0 and not args.no_batched:
         batched = _batched_section(args, adgi, torch, dev)
@@ -784,43 +864,45 @@ def run_ours(args):
         cosine = _cosine_section(args, adgi, torch, dev)
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        times, cores = _cpu_baseline(w, budget_s=args.cpu_budget, sampler=int(args.sampler), alpha=args.alpha)
-        cpu = {"value": rays / float(np.mean(times)), "unit": "rays/s", "cores": cores, "kind": "oracle",
-               "sample": "%d full oracle update(s) of the same workload (frames 0-%d, every probe and phase, "
-                         "BVH rebuild included), host threads = cores" % (len(times), len(times) - 1)}
+        cpu = _cpu_baseline_line(w, r["rays"], args)
     if rank == 0:
+        rays = r["rays"]
         line = {
-            "metric": "probe rays/s per update", "value": value, "unit": "rays/s", "n_gpus": ws,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+            "metric": "probe rays/s per update", "value": r["value"], "unit": "rays/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_step"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32" if not args.fp16 else "f32 (f16 atlases)",
-            "data": "synthetic (seeded tunnel+city generator standing in for the paper's scenes)",
+            "data": "synthetic (seeded city generator standing in for the paper's scenes)",
             "config": {"workload": w.name, "probes": w.n_probes, "rays_per_update": rays,
                        "triangles": w.n_tris, "lights": len(w.lights_at(0)), "atlas": "fp16" if args.fp16 else "fp32",
                        "sampler": "metropolis (alpha %g)" % args.alpha if args.sampler else "per-probe allocation",
                        "l2": "flushed (256 MB write) between timed steps", "parallelism": "replicas" if ws > 1 else "1 GPU"},
-            "latency_ms": {"device_p50": float(np.percentile(dev_ms, 50)), "device_p99": float(np.percentile(dev_ms, 99)),
-                           "host_p50": float(np.percentile(host_ms, 50)), "host_p99": float(np.percentile(host_ms, 99))},
-            "phases_ms": mean_ph,
-            "kernels_ms": kern_ms,
-            "traversal_counts": {"pilot_boxes": counts[0], "pilot_tris": counts[1], "pilot_shadow_boxes": counts[2],
-                                 "pilot_shadow_tris": counts[3], "boxes": counts[4], "tris": counts[5],
-                                 "shadow_boxes": counts[6], "shadow_tris": counts[7]},
-            "rays_incl_shadow_per_s": ws * (rays + vol.stats().shadow_rays) / (ms_step / 1e3),
-            "roofline": roof,
-            "roofline_blend": roof_blend,
+            "latency_ms": {"device_p50": float(np.percentile(r["dev_ms"], 50)),
+                           "device_p99": float(np.percentile(r["dev_ms"], 99)),
+                           "host_p50": float(np.percentile(r["host_ms"], 50)),
+                           "host_p99": float(np.percentile(r["host_ms"], 99))},
+            "phases_ms": r["phases"],
+            "kernels_ms": r["kernels"],
+            "traversal_counts": dict(zip(["pilot_boxes", "pilot_tris", "pilot_shadow_boxes", "pilot_shadow_tris",
+                                          "boxes", "tris", "shadow_boxes", "shadow_tris", "warp_max_boxes_x32",
+                                          "rays_traced", "shadow_blocked", "shadow_traced"], r["counts"])),
+            "lane_efficiency_bound": r["counts"][4] / max(r["counts"][8], 1),
+            "rays_incl_shadow_per_s": ws * (rays + r["shadow_rays"]) / (r["ms_step"] / 1e3),
+            "roofline": r["roofline"],
+            "roofline_blend": r["roofline_blend"],
             "cpu_baseline": cpu,
-            "e2e": e2e,
+            "e2e": r["e2e"],
+            "half_atlases": half,
+            "tunnel_city": side,
             "batched": batched,
             "serving": serving,
             "precision": precision,
             "metropolis": metropolis,
             "cosine_gather": cosine,
-            "gpu_launches": int(launches),
-            "clocks": clk,
-            "wall_s": wall,
+            "gpu_launches": r["launches"],
+            "clocks": r["clocks"],
+            "wall_s": r["wall"],
         }
         print(json.dumps(line), flush=True)
-    vol.close()
     if ws > 1:
         dist.destroy_process_group()
     return 0
@@ -832,7 +914,7 @@ def main():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="tunnel_city", choices=["tunnel_city", "box_room", "scaled"])
+    ap.add_argument("--workload", default="scaled", choices=["tunnel_city", "box_room", "scaled"])
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--fp16", action="store_true")
     ap.add_argument("--sampler", action="store_true",
@@ -844,7 +926,8 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-precision", action="store_true")
     ap.add_argument("--no-metropolis", action="store_true")
-    ap.add_argument("--precision-frames", type=int, default=12)
+    ap.add_argument("--no-side", action="store_true", help="skip the tunnel+city measurement beside the headline")
+    ap.add_argument("--precision-frames", type=int, default=30)
     ap.add_argument("--serve-requests", type=int, default=10000)
     ap.add_argument("--serve-streams", type=int, default=8)
     ap.add_argument("--serve-budget-gb", type=int, default=120)
