@@ -43,7 +43,11 @@ struct __align__(16) BNode {
 // ns and its nodes at node max(ns-1, 0), with child references relocated
 // to these global indices, so a traversal needs no per-part pointers.  Hits
 // are ranked over both by (t, original triangle index).
+constexpr int kWideEmpty = (int)0x80000000;  // an unused child slot of a 4-wide node
+constexpr int kWide4Stack = 160;             // entries of the 4-wide traversal stack (>= the binary one's)
+
 struct SceneDev {
+    const float4* w4;       // 4-wide tree of the static part (7 float4 a node), or null: the binary tree
     const BNode* nodes;     // internal nodes of both parts
     const float4* tri_v;    // both parts' triangles in BVH order, .w of v0 = original index
     int root[2];            // root node of each part's tree (-1: fewer than two triangles)
@@ -326,6 +330,7 @@ constexpr float kBoxSlack = 1.0001f;  // pruning slack on the best t (conservati
 // traversal stack holds at most one pending entry per level.
 constexpr int kMaxDepth = 96;
 constexpr int kStack = kMaxDepth;
+static_assert(kWide4Stack >= kStack, "one stack array serves both traversals");
 
 // Traversal of the two-part scene as one flat loop over one stack of
 // global node indices.  The loop has no early exit, so the lanes of a warp
@@ -387,6 +392,8 @@ __device__ __forceinline__ void trav_tri(Trav& T, const float4* tri_v, int slot,
 }
 
 // set up a traversal; single-triangle parts are tested here, trees pushed
+// (the static part's only when it has no 4-wide tree: that one is walked
+// by trav4 beforehand)
 __device__ __forceinline__ void trav_init(Trav& T, int* stack, const SceneDev& S, float3 o, float3 d, float tmin,
                                           float tmax, bool any, uint32_t* ntri = nullptr)
 {
@@ -416,7 +423,7 @@ __device__ __forceinline__ void trav_init(Trav& T, int* stack, const SceneDev& S
     T.sp = 0;
     T.iter = 0;
     if (S.n_tris == 0) return;
-    for (int pi = 1; pi >= 0; --pi) {
+    for (int pi = 1; pi >= (S.w4 ? 1 : 0); --pi) {
         const int root = pi ? S.root[1] : S.root[0], leaf = pi ? S.leaf[1] : S.leaf[0];
         if (root >= 0)
             stack[T.sp++] = root;
@@ -473,14 +480,94 @@ __device__ __forceinline__ uint32_t trav_hit(const Trav& T)
     return T.found ? ((uint32_t)T.best_orig | (T.best_det < 0.0f ? kBackBit : 0u)) : kMiss;
 }
 
+// The static part's 4-wide tree (T set up by trav_init): from the root, each
+// visit tests the four child boxes with the near / far planes of each axis
+// read by the sign of the ray direction (so an entry distance is a max and an
+// exit distance a min of three FMAs), tests the triangles of hit leaf
+// children at once, and continues with the nearest hit internal child; the
+// other hit internal children are pushed, farthest first (closest hit).  An
+// any-hit traversal stops at the first blocker.  The pruning bound and the
+// (t, index) ranking are those of trav_step, so the hit is the same.
+__device__ __forceinline__ void trav4(Trav& T, int* stack, const SceneDev& S, bool any, uint32_t* nbox = nullptr,
+                                      uint32_t* ntri = nullptr)
+{
+    const int sx = T.inv.x >= 0.0f ? 0 : 1, sy = T.inv.y >= 0.0f ? 0 : 1, sz = T.inv.z >= 0.0f ? 0 : 1;
+    int node = 0, sp = 0;
+    while (true) {
+        if (++T.iter > S.max_iter) {
+            atomicOr(S.err, kErrTraversal);
+            return;
+        }
+        if (nbox) *nbox += 4;
+        const float4* N = S.w4 + 7 * (size_t)node;
+        const float4 nx = __ldg(N + sx), fx = __ldg(N + 1 - sx);
+        const float4 ny = __ldg(N + 2 + sy), fy = __ldg(N + 3 - sy);
+        const float4 nz = __ldg(N + 4 + sz), fz = __ldg(N + 5 - sz);
+        const int4 rf = __ldg(reinterpret_cast<const int4*>(N + 6));
+        const float lim = any ? T.lim : T.t_best * kBoxSlack;
+        float key[4];
+        int ref[4] = {rf.x, rf.y, rf.z, rf.w};
+        const float nxs[4] = {nx.x, nx.y, nx.z, nx.w}, fxs[4] = {fx.x, fx.y, fx.z, fx.w};
+        const float nys[4] = {ny.x, ny.y, ny.z, ny.w}, fys[4] = {fy.x, fy.y, fy.z, fy.w};
+        const float nzs[4] = {nz.x, nz.y, nz.z, nz.w}, fzs[4] = {fz.x, fz.y, fz.z, fz.w};
+        const float inf = __int_as_float(0x7F800000);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float tn = fmaxf(fmaxf(fmaf(nxs[k], T.inv.x, -T.oi.x), fmaf(nys[k], T.inv.y, -T.oi.y)),
+                                   fmaxf(fmaf(nzs[k], T.inv.z, -T.oi.z), 0.0f));
+            const float tf = fminf(fminf(fmaf(fxs[k], T.inv.x, -T.oi.x), fmaf(fys[k], T.inv.y, -T.oi.y)),
+                                   fminf(fmaf(fzs[k], T.inv.z, -T.oi.z), lim));
+            const bool hit = tn <= tf;
+            if (hit && ref[k] < 0) trav_tri(T, S.tri_v, ~ref[k], any, ntri);
+            key[k] = hit && ref[k] >= 0 ? tn : inf;
+        }
+        if (any && T.found) return;
+        // the hit internal children nearest first: a sorting network on (key, ref)
+#define ADGI_CSWAP(i, j)                                  \
+    if (key[j] < key[i]) {                                \
+        const float tk = key[i];                          \
+        key[i] = key[j];                                  \
+        key[j] = tk;                                      \
+        const int tr = ref[i];                            \
+        ref[i] = ref[j];                                  \
+        ref[j] = tr;                                      \
+    }
+        ADGI_CSWAP(0, 1)
+        ADGI_CSWAP(2, 3)
+        ADGI_CSWAP(0, 2)
+        ADGI_CSWAP(1, 3)
+        ADGI_CSWAP(1, 2)
+#undef ADGI_CSWAP
+        if (key[0] < inf) {
+            if (sp + 3 > kWide4Stack) {  // the builder bounds the depth, so this cannot happen
+                atomicOr(S.err, kErrTraversal);
+                return;
+            }
+            if (key[3] < inf) stack[sp++] = ref[3];
+            if (key[2] < inf) stack[sp++] = ref[2];
+            if (key[1] < inf) stack[sp++] = ref[1];
+            node = ref[0];
+        } else {
+            if (sp == 0) return;
+            node = stack[--sp];
+        }
+    }
+}
+
 // nearest hit with t in (tmin, tmax] (one thread, one ray)
 __device__ __forceinline__ void trace_closest(const SceneDev& S, float3 o, float3 d, float tmin, float tmax,
                                               float& t_best, uint32_t& hit_best, uint32_t* nbox = nullptr,
                                               uint32_t* ntri = nullptr)
 {
     Trav T;
-    int stack[kStack + 2];
+    int stack[kWide4Stack + 2];  // the moving part's root sits below the 4-wide traversal's entries
     trav_init(T, stack, S, o, d, tmin, tmax, false, ntri);
+    if (S.w4) {  // the static part's 4-wide tree first, then the moving part's binary tree
+        const int sp = T.sp;  // the moving part's root, pushed by trav_init, waits below
+        int* st = stack + sp;
+        trav4(T, st, S, false, nbox, ntri);
+        T.sp = sp;
+    }
     while (trav_step(T, stack, S, false, nbox, ntri)) {
     }
     t_best = T.t_best;
@@ -492,8 +579,13 @@ __device__ __forceinline__ bool trace_any(const SceneDev& S, float3 o, float3 d,
                                           uint32_t* nbox = nullptr, uint32_t* ntri = nullptr)
 {
     Trav T;
-    int stack[kStack + 2];
+    int stack[kWide4Stack + 2];  // the moving part's root sits below the 4-wide traversal's entries
     trav_init(T, stack, S, o, d, tlo, thi, true, ntri);
+    if (S.w4 && !T.found) {
+        const int sp = T.sp;
+        trav4(T, stack + sp, S, true, nbox, ntri);
+        T.sp = T.found ? 0 : sp;
+    }
     while (trav_step(T, stack, S, true, nbox, ntri)) {
     }
     return T.found;

@@ -2,6 +2,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <vector>
+
 #include "adgi_internal.cuh"
 
 namespace adgi {
@@ -46,6 +48,13 @@ constexpr size_t bvh_scratch_layout_bytes(size_t nt)
     return bvh_r256(48 * n) + 3 * bvh_r256(4 * n) + 2 * bvh_r256(8 * n) + 2 * bvh_r256(4 * n) +
            bvh_r256(4 * 256 * ((n + kBvhSortTile - 1) / kBvhSortTile)) + bvh_r256(4 * 8) + bvh_r256(4 * 2);
 }
+
+// The 4-wide tree of the static part (wide.cu): collapse the binary tree of
+// n_bnodes internal nodes (root 0) into out (7 float4 a node: the four
+// children's boxes as lo.x, hi.x, lo.y, hi.y, lo.z, hi.z, then int32 refs:
+// >= 0 a wide node, < 0 ~(triangle slot), kWideEmpty none); *depth receives
+// the tree depth.  Returns the number of wide nodes, or -1 on a malformed tree.
+int collapse_wide4(const BNode* bn, int n_bnodes, std::vector<float4>& out, int* depth);
 
 size_t bvh_scratch_bytes(int nt);
 size_t radix_hist_entries(int n);

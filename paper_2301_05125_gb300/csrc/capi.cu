@@ -235,6 +235,9 @@ struct adgi_volume_s {
     float eps = 0.f;
     // two-part scene: triangles that touch a moved vertex form the moving part
     Bvh sbvh, dbvh;               // static part (PLOC, built once) and moving part (linear, per move)
+    float4* w4 = nullptr;         // the static part's 4-wide tree (7 float4 a node), null: binary traversal
+    int w4_nodes = 0, w4_depth = 0;
+    size_t w4_bytes = 0;
     float4* tri_orig = nullptr;   // [3*nt] vertices in original order (shading normals)
     uint8_t* vmoved = nullptr;    // [nv] 1: vertex has been moved
     int* slist = nullptr;         // static triangles
@@ -321,6 +324,7 @@ void free_volume(adgi_volume v)
         if (p) cudaFree(p);
     v->sbvh.release();
     v->dbvh.release();
+    cudaFree(v->w4);
     cudaFree(v->tri_orig);
     cudaFree(v->vmoved);
     cudaFree(v->slist);
@@ -333,6 +337,7 @@ void free_volume(adgi_volume v)
         if (e) cudaEventDestroy(e);
     for (cudaEvent_t e : v->plq)
         if (e) cudaEventDestroy(e);
+
     if (v->fork) cudaEventDestroy(v->fork);
     if (v->join) cudaEventDestroy(v->join);
     if (v->side) cudaStreamDestroy(v->side);
@@ -814,6 +819,42 @@ int build_moving(adgi_volume v, cudaStream_t s)
     return ADGI_OK;
 }
 
+// The static part's 4-wide tree, collapsed on the host from its binary tree
+// (once per static build; collapse_wide4).  Left out, so that the binary
+// tree is traversed, when the static part has fewer than two triangles or the
+// tree is deeper than the traversal stack allows (3 entries a level).
+int build_wide(adgi_volume v, cudaStream_t s)
+{
+    if (v->w4) {
+        cudaFree(v->w4);
+        v->bytes -= v->w4_bytes;
+    }
+    v->w4 = nullptr;
+    v->w4_nodes = v->w4_depth = 0;
+    v->w4_bytes = 0;
+    if (v->ns < 2) return ADGI_OK;
+    std::vector<BNode> bn((size_t)v->ns - 1);
+    CK(cudaMemcpyAsync(bn.data(), v->sbvh.nodes, sizeof(BNode) * bn.size(), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    std::vector<float4> w;
+    int depth = 0;
+    const int nw = collapse_wide4(bn.data(), (int)bn.size(), w, &depth);
+    if (nw < 0) return fail(ADGI_ERR_CUDA, "4-wide collapse: malformed binary tree");
+    if (3 * depth > kWide4Stack) return ADGI_OK;
+    size_t b = 0;
+    if (dalloc(&v->w4, w.size(), &b) != cudaSuccess) {
+        v->w4 = nullptr;
+        return fail(ADGI_ERR_OOM, "4-wide tree");
+    }
+    CK(cudaMemcpyAsync(v->w4, w.data(), sizeof(float4) * w.size(), cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));  // w is freed on return
+    v->bytes += b;
+    v->w4_bytes = b;
+    v->w4_nodes = nw;
+    v->w4_depth = depth;
+    return ADGI_OK;
+}
+
 // Bring both BVH parts up to date: re-split and rebuild the static part when
 // the moving set grew, rebuild the moving part when its vertices moved.
 int ensure_bvh(adgi_volume v, cudaStream_t s, bool moving_too = true)
@@ -823,6 +864,10 @@ int ensure_bvh(adgi_volume v, cudaStream_t s, bool moving_too = true)
         if (!v->sbvh.pscratch) return fail(ADGI_ERR_OOM, "split scratch");
         CK(split_static_moving(v->idx, v->vmoved, v->nt, v->nv, v->sbvh.pbufs, v->slist, v->dlist, &v->ns, &v->nd, s));
         CK(v->sbvh.build(v->verts, v->idx, v->nv, v->ns, v->eps, v->err, s, v->slist, true));
+        {
+            int rc = build_wide(v, s);
+            if (rc) return rc;
+        }
         v->split_dirty = false;
         v->dyn_dirty = true;
     }
@@ -899,6 +944,7 @@ DynBufs dyn_bufs(adgi_volume v)
 SceneDev scene_view(adgi_volume v)
 {
     SceneDev S;
+    S.w4 = v->w4;
     S.nodes = v->sbvh.nodes;
     S.tri_v = v->sbvh.tri_v;
     S.root[0] = v->ns > 1 ? 0 : -1;

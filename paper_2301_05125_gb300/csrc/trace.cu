@@ -49,7 +49,7 @@ __global__ void k_set_frame(FrameDev* __restrict__ dst, const __grid_constant__ 
     for (int i = threadIdx.x; i < (int)(sizeof(FrameDev) / sizeof(int)); i += blockDim.x) b[i] = a[i];
 }
 
-__global__ void __launch_bounds__(256) k_pilot_trace(VolConst V, const FrameDev* __restrict__ FD, SceneDev S,
+__global__ void __launch_bounds__(256, 4) k_pilot_trace(VolConst V, const FrameDev* __restrict__ FD, SceneDev S,
                                                      int2* __restrict__ hit)
 {
     const FrameConst& F = FD->F;
@@ -71,7 +71,7 @@ __global__ void __launch_bounds__(256) k_pilot_trace(VolConst V, const FrameDev*
 // Thread r takes row position r - off[p] of probe p, whose SF index i names
 // the slot off[p] + i of the result: the threads of a warp trace nearby
 // directions (the rows are in a spatial order).
-__global__ void __launch_bounds__(256) k_main_trace(VolConst V, const FrameDev* __restrict__ FD, SceneDev S,
+__global__ void __launch_bounds__(256, 4) k_main_trace(VolConst V, const FrameDev* __restrict__ FD, SceneDev S,
                                                     const uint32_t* __restrict__ off, const float4* __restrict__ sf,
                                                     uint32_t R, int2* __restrict__ hit)
 {
