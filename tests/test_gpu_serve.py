@@ -149,6 +149,27 @@ def test_coalescing_keeps_the_newest_frame(adgi):
     srv.close()
 
 
+def test_drain_times_out_and_the_server_recovers(adgi):
+    # failure detection on the host: a drain whose time limit runs out while
+    # requests are still queued returns TIMEOUT (nothing on the device
+    # waits); the server keeps running, a later drain completes, and the
+    # volume ends as the same frames alone leave it
+    w = S.small_city(5, n_boxes=900, dims=(9, 5, 7), rays_avg=40)
+    srv = adgi.Server(streams=1, hbm_budget_bytes=8 << 30, coalesce=False)
+    vid = srv.add_volume(w.verts, w.idx, w.albedo, **w.volume)
+    ids = [_submit(srv, vid, w, f) for f in range(8)]
+    with pytest.raises(adgi.AdgiError) as e:
+        srv.drain(0.0)
+    assert e.value.code == -6
+    srv.drain(120.0)
+    res = srv.poll()
+    assert sorted(r.request_id for r in res) == ids and all(r.status == 0 for r in res)
+    alone = _alone(adgi, w, 8)
+    _same(srv.volume(vid), alone, "after a timed-out drain")
+    alone.close()
+    srv.close()
+
+
 def test_server_rejects_bad_calls(adgi):
     with pytest.raises(adgi.AdgiError):
         adgi.Server(streams=0)
