@@ -2830,16 +2830,51 @@ EXPORT long long orc_slab_slice(orc_vol* v, int which, int p0, int p1, void* buf
 }
 
 /* Trace + shade the pilot and main rays of a probe subset without blending */
-/* (timing sample for the CPU baseline).  Requires a previous orc_update.    */
+/* (timing sample for the CPU baseline), split over the volume's threads.    */
+/* Requires a previous orc_update.                                           */
+typedef struct {
+    orc_vol* v;
+    const orc_frame* fr;
+    const int* probes;
+    int k0, k1;
+    long long rays;
+} sample_job;
+
+static void* sample_worker(void* arg)
+{
+    sample_job* j = (sample_job*)arg;
+    for (int k = j->k0; k < j->k1; ++k) {
+        const int p = j->probes[k];
+        pilot_probe(j->v, j->fr, p);
+        main_probe(j->v, j->fr, p);
+        j->rays += j->v->n[p];
+    }
+    return NULL;
+}
+
 EXPORT long long orc_trace_shade_probes(orc_vol* v, const orc_frame* fr, const int* probes, int count)
 {
-    long long rays = 0;
-    for (int k = 0; k < count; ++k) {
-        int p = probes[k];
-        pilot_probe(v, fr, p);
-        main_probe(v, fr, p);
-        rays += v->n[p];
+    for (int k = 0; k < count; ++k)
+        if (probes[k] < 0 || probes[k] >= v->P) return -1;
+    int nt = v->nthreads;
+    if (nt > count) nt = count;
+    if (nt > 256) nt = 256;
+    if (nt < 1) return 0;
+    pthread_t th[256];
+    sample_job jobs[256];
+    for (int t = 0; t < nt; ++t) {
+        jobs[t].v = v;
+        jobs[t].fr = fr;
+        jobs[t].probes = probes;
+        jobs[t].k0 = (int)((long long)count * t / nt);
+        jobs[t].k1 = (int)((long long)count * (t + 1) / nt);
+        jobs[t].rays = 0;
     }
+    for (int t = 1; t < nt; ++t) pthread_create(&th[t], NULL, sample_worker, &jobs[t]);
+    sample_worker(&jobs[0]);
+    for (int t = 1; t < nt; ++t) pthread_join(th[t], NULL);
+    long long rays = 0;
+    for (int t = 0; t < nt; ++t) rays += jobs[t].rays;
     return rays;
 }
 
