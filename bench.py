@@ -34,11 +34,14 @@ if ROOT not in sys.path:
 import numpy as np  # noqa: E402
 
 # FP32 lane operations per unit of traversal work (counted from the kernels'
-# arithmetic): one child-box slab test is 6 sub, 6 mul, 8 min/max and 2
-# compares = 22 (a node visit tests both child boxes); one watertight triangle
-# test is 9 sub + 6 mul/sub pairs + 6 mul + 3 sub + 2 add (det) + 3 mul +
-# 4 (T) + 1 div (counted 8) + 6 compares = 55.
-OPS_BOX = 22
+# arithmetic): one child-box test of the 4-wide static tree is 6 FMAs (near
+# and far plane per axis, picked by the ray's direction signs), 6 min/max
+# (entry and exit distance, clamped to [0, limit]) and 1 compare = 13 (a
+# visit tests four children; the moving part's binary visits, two boxes each,
+# are counted at the same rate); one watertight triangle test is 9 sub + 6
+# mul/sub pairs + 6 mul + 3 sub + 2 add (det) + 3 mul + 4 (T) + 1 div
+# (counted 8) + 6 compares = 55.
+OPS_BOX = 13
 OPS_TRI = 55
 # algorithmic blend bytes per touched probe tile: read + write of the
 # irradiance tile (8x8 float4 = 1024 B), depth tile (16x16 float2 = 2048 B)
@@ -262,7 +265,7 @@ def run_reference(args):
             frame += 1
     else:
         frac = max(1e-3, budget / ((args.steps + args.warmup) * t_one))
-        stride = max(1, int(round(1.0 / frac)))
+        stride = max(2, int(np.ceil(1.0 / frac)))  # a sample, never the whole grid
         probes = np.arange(0, w.n_probes, stride, dtype=np.int32)
         sample = "trace+shade of every %d-th probe (%d probes) per step, frame %d" % (stride, len(probes), frame)
         for _ in range(args.steps):

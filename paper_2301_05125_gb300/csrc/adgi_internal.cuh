@@ -480,6 +480,85 @@ __device__ __forceinline__ uint32_t trav_hit(const Trav& T)
     return T.found ? ((uint32_t)T.best_orig | (T.best_det < 0.0f ? kBackBit : 0u)) : kMiss;
 }
 
+// One visit of the static part's 4-wide tree: node `node`, the traversal's
+// stack and its depth sp, the ray's direction signs (sx, sy, sz: 0 positive,
+// 1 negative).  Returns the node to visit next, or -1 once the static part is
+// done (an any-hit traversal: also when it found a blocker).
+__device__ __forceinline__ int trav4_visit(Trav& T, int* stack, int& sp, int node, const SceneDev& S, bool any,
+                                           int sx, int sy, int sz, uint32_t* nbox, uint32_t* ntri)
+{
+    if (++T.iter > S.max_iter) {
+        atomicOr(S.err, kErrTraversal);
+        return -1;
+    }
+    if (nbox) *nbox += 4;
+    const float4* N = S.w4 + 7 * (size_t)node;
+    const float4 nx = __ldg(N + sx), fx = __ldg(N + 1 - sx);
+    const float4 ny = __ldg(N + 2 + sy), fy = __ldg(N + 3 - sy);
+    const float4 nz = __ldg(N + 4 + sz), fz = __ldg(N + 5 - sz);
+    const int4 rf = __ldg(reinterpret_cast<const int4*>(N + 6));
+    const float lim = any ? T.lim : T.t_best * kBoxSlack;
+    float key[4];
+    int ref[4] = {rf.x, rf.y, rf.z, rf.w};
+    const float nxs[4] = {nx.x, nx.y, nx.z, nx.w}, fxs[4] = {fx.x, fx.y, fx.z, fx.w};
+    const float nys[4] = {ny.x, ny.y, ny.z, ny.w}, fys[4] = {fy.x, fy.y, fy.z, fy.w};
+    const float nzs[4] = {nz.x, nz.y, nz.z, nz.w}, fzs[4] = {fz.x, fz.y, fz.z, fz.w};
+    const float inf = __int_as_float(0x7F800000);
+    uint32_t leaves = 0;  // closest hit: hit leaf children, tested below in one loop (one divergent region, not four)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float tn = fmaxf(fmaxf(fmaf(nxs[k], T.inv.x, -T.oi.x), fmaf(nys[k], T.inv.y, -T.oi.y)),
+                               fmaxf(fmaf(nzs[k], T.inv.z, -T.oi.z), 0.0f));
+        const float tf = fminf(fminf(fmaf(fxs[k], T.inv.x, -T.oi.x), fmaf(fys[k], T.inv.y, -T.oi.y)),
+                               fminf(fmaf(fzs[k], T.inv.z, -T.oi.z), lim));
+        const bool hit = tn <= tf;
+        if (any) {  // any hit: each hit leaf at once (a blocker ends the search below)
+            if (hit && ref[k] < 0) trav_tri(T, S.tri_v, ~ref[k], true, ntri);
+        } else if (hit && ref[k] < 0) {
+            leaves |= 1u << k;
+        }
+        key[k] = hit && ref[k] >= 0 ? tn : inf;
+    }
+    if (any && T.found) return -1;
+    while (leaves) {
+        const int k = __ffs(leaves) - 1;
+        leaves &= leaves - 1u;
+        const int r = k == 0 ? rf.x : k == 1 ? rf.y : k == 2 ? rf.z : rf.w;
+        trav_tri(T, S.tri_v, ~r, any, ntri);
+        if (any && T.found) return -1;
+    }
+    // the hit internal children nearest first: a sorting network on (key, ref)
+    // (for an any-hit traversal only the nearest is put first)
+#define ADGI_CSWAP(i, j)                                  \
+    if (key[j] < key[i]) {                                \
+        const float tk = key[i];                          \
+        key[i] = key[j];                                  \
+        key[j] = tk;                                      \
+        const int tr = ref[i];                            \
+        ref[i] = ref[j];                                  \
+        ref[j] = tr;                                      \
+    }
+    ADGI_CSWAP(0, 1)
+    ADGI_CSWAP(2, 3)
+    ADGI_CSWAP(0, 2)
+    if (!any) {  // any hit: the nearest first is enough (measured: the full order costs more than it saves)
+        ADGI_CSWAP(1, 3)
+        ADGI_CSWAP(1, 2)
+    }
+#undef ADGI_CSWAP
+    if (key[0] < inf) {
+        if (sp + 3 > kWide4Stack) {  // the builder bounds the depth, so this cannot happen
+            atomicOr(S.err, kErrTraversal);
+            return -1;
+        }
+        if (key[3] < inf) stack[sp++] = ref[3];
+        if (key[2] < inf) stack[sp++] = ref[2];
+        if (key[1] < inf) stack[sp++] = ref[1];
+        return ref[0];
+    }
+    return sp == 0 ? -1 : stack[--sp];
+}
+
 // The static part's 4-wide tree (T set up by trav_init): from the root, each
 // visit tests the four child boxes with the near / far planes of each axis
 // read by the sign of the ray direction (so an entry distance is a max and an
@@ -493,65 +572,7 @@ __device__ __forceinline__ void trav4(Trav& T, int* stack, const SceneDev& S, bo
 {
     const int sx = T.inv.x >= 0.0f ? 0 : 1, sy = T.inv.y >= 0.0f ? 0 : 1, sz = T.inv.z >= 0.0f ? 0 : 1;
     int node = 0, sp = 0;
-    while (true) {
-        if (++T.iter > S.max_iter) {
-            atomicOr(S.err, kErrTraversal);
-            return;
-        }
-        if (nbox) *nbox += 4;
-        const float4* N = S.w4 + 7 * (size_t)node;
-        const float4 nx = __ldg(N + sx), fx = __ldg(N + 1 - sx);
-        const float4 ny = __ldg(N + 2 + sy), fy = __ldg(N + 3 - sy);
-        const float4 nz = __ldg(N + 4 + sz), fz = __ldg(N + 5 - sz);
-        const int4 rf = __ldg(reinterpret_cast<const int4*>(N + 6));
-        const float lim = any ? T.lim : T.t_best * kBoxSlack;
-        float key[4];
-        int ref[4] = {rf.x, rf.y, rf.z, rf.w};
-        const float nxs[4] = {nx.x, nx.y, nx.z, nx.w}, fxs[4] = {fx.x, fx.y, fx.z, fx.w};
-        const float nys[4] = {ny.x, ny.y, ny.z, ny.w}, fys[4] = {fy.x, fy.y, fy.z, fy.w};
-        const float nzs[4] = {nz.x, nz.y, nz.z, nz.w}, fzs[4] = {fz.x, fz.y, fz.z, fz.w};
-        const float inf = __int_as_float(0x7F800000);
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const float tn = fmaxf(fmaxf(fmaf(nxs[k], T.inv.x, -T.oi.x), fmaf(nys[k], T.inv.y, -T.oi.y)),
-                                   fmaxf(fmaf(nzs[k], T.inv.z, -T.oi.z), 0.0f));
-            const float tf = fminf(fminf(fmaf(fxs[k], T.inv.x, -T.oi.x), fmaf(fys[k], T.inv.y, -T.oi.y)),
-                                   fminf(fmaf(fzs[k], T.inv.z, -T.oi.z), lim));
-            const bool hit = tn <= tf;
-            if (hit && ref[k] < 0) trav_tri(T, S.tri_v, ~ref[k], any, ntri);
-            key[k] = hit && ref[k] >= 0 ? tn : inf;
-        }
-        if (any && T.found) return;
-        // the hit internal children nearest first: a sorting network on (key, ref)
-#define ADGI_CSWAP(i, j)                                  \
-    if (key[j] < key[i]) {                                \
-        const float tk = key[i];                          \
-        key[i] = key[j];                                  \
-        key[j] = tk;                                      \
-        const int tr = ref[i];                            \
-        ref[i] = ref[j];                                  \
-        ref[j] = tr;                                      \
-    }
-        ADGI_CSWAP(0, 1)
-        ADGI_CSWAP(2, 3)
-        ADGI_CSWAP(0, 2)
-        ADGI_CSWAP(1, 3)
-        ADGI_CSWAP(1, 2)
-#undef ADGI_CSWAP
-        if (key[0] < inf) {
-            if (sp + 3 > kWide4Stack) {  // the builder bounds the depth, so this cannot happen
-                atomicOr(S.err, kErrTraversal);
-                return;
-            }
-            if (key[3] < inf) stack[sp++] = ref[3];
-            if (key[2] < inf) stack[sp++] = ref[2];
-            if (key[1] < inf) stack[sp++] = ref[1];
-            node = ref[0];
-        } else {
-            if (sp == 0) return;
-            node = stack[--sp];
-        }
-    }
+    while (node >= 0) node = trav4_visit(T, stack, sp, node, S, any, sx, sy, sz, nbox, ntri);
 }
 
 // nearest hit with t in (tmin, tmax] (one thread, one ray)

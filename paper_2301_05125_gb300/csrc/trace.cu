@@ -53,9 +53,14 @@ __global__ void __launch_bounds__(256, 4) k_pilot_trace(VolConst V, const FrameD
                                                      int2* __restrict__ hit)
 {
     const FrameConst& F = FD->F;
-    int i = V.p_lo * kPilots + blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= V.p_hi * kPilots) return;
-    int p = i >> 3, o = i & 7;
+    // A warp traces one octant of 32 consecutive probes (the stratified
+    // directions of one octant, from neighbouring origins), not 8 octants of
+    // 4 probes.  Thread j of the launch: group g = j / 256 of 32 probes,
+    // octant (j / 32) % 8, probe 32 g + j % 32; results stay at 8 p + o.
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int p = V.p_lo + ((j >> 8) << 5) + (j & 31), o = (j >> 5) & 7;
+    if (p >= V.p_hi) return;
+    const int i = p * kPilots + o;
     if (V.cls[p] == 0) {  // outside V_out: no pilot rays
         hit[i] = make_int2((int)kMiss, 0x7F800000);
         return;
@@ -301,7 +306,7 @@ cudaError_t launch_set_frame(FrameDev* dst, const FrameDev& src, cudaStream_t s)
 cudaError_t launch_pilot_trace(const VolConst& V, const FrameDev* FD, const SceneDev& S, int2* hit, const Tuning& T,
                                cudaStream_t s)
 {
-    int n = (V.p_hi - V.p_lo) * kPilots, b = T.trace_block;
+    int n = ((V.p_hi - V.p_lo + 31) / 32) * 32 * kPilots, b = T.trace_block;
     if (n <= 0) return cudaSuccess;
     k_pilot_trace<<<(n + b - 1) / b, b, 0, s>>>(V, FD, S, hit);
     count_launches(1);
