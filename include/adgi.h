@@ -405,6 +405,15 @@ int adgi_update_slab(adgi_volume vol, const adgi_frame* frame, int32_t step, int
 int adgi_slab_copy(adgi_volume vol, int32_t which, int32_t p0, int32_t p1, void* dev_buf, int32_t into);
 int adgi_slab_bytes(adgi_volume vol, int32_t which, int32_t p0, int32_t p1, uint64_t* bytes);
 
+/* Fault injection for testing the failure paths (no counterpart in the
+ * paper): with n > 0, the n-th device allocation a volume makes from now on
+ * (adgi_create_volume's buffers, the shadow-job list, the 4-wide tree) fails
+ * as cudaMalloc would when the device is full -- without allocating -- and
+ * the call that made it returns ADGI_ERR_OOM after releasing what it had
+ * allocated.  One failure per arming; n = 0 disarms.  Process-wide.
+ * Errors: INVALID_ARG (n < 0). */
+int adgi_inject_alloc_failure(int32_t n);
+
 /* Overwrite the atlases from host memory (same layouts as ADGI_STATE_IRR /
  * _DEP / _DEP_N; any pointer may be NULL to keep that part).  For tests and
  * for restoring a saved state. */

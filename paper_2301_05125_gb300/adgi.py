@@ -112,7 +112,7 @@ EXPORTED = ["adgi_create_volume", "adgi_set_scene", "adgi_move_vertices", "adgi_
             "adgi_batch_update", "adgi_batch_destroy", "adgi_autotune", "adgi_set_tuning", "adgi_get_tuning",
             "adgi_server_create", "adgi_server_add_volume", "adgi_server_submit", "adgi_server_poll",
             "adgi_server_drain", "adgi_server_volume", "adgi_server_remove_volume", "adgi_server_info",
-            "adgi_server_destroy", "adgi_update_slab", "adgi_slab_copy", "adgi_slab_bytes", "adgi_last_error"]
+            "adgi_server_destroy", "adgi_update_slab", "adgi_slab_copy", "adgi_slab_bytes", "adgi_inject_alloc_failure", "adgi_last_error"]
 
 BVH_NOALLOC_MAX_TRIS = 32768
 
@@ -164,6 +164,7 @@ def load(path: str = LIB_PATH):
     L.adgi_update_slab.argtypes = [vp, C.POINTER(adgi_frame), i32, i32, i32]
     L.adgi_slab_copy.argtypes = [vp, i32, i32, i32, vp, i32]
     L.adgi_slab_bytes.argtypes = [vp, i32, i32, i32, C.POINTER(u64)]
+    L.adgi_inject_alloc_failure.argtypes = [i32]
     L.adgi_last_error.restype = C.c_char_p
     for name in EXPORTED[:-1]:
         getattr(L, name).restype = C.c_int
@@ -409,6 +410,10 @@ def adgi_slab_bytes(vol, which, p0, p1) -> int:
     _check(load().adgi_slab_bytes(vol, STATE[which] if isinstance(which, str) else int(which), int(p0), int(p1),
                                   C.byref(b)))
     return int(b.value)
+
+
+def adgi_inject_alloc_failure(n):
+    _check(load().adgi_inject_alloc_failure(int(n)))
 
 
 def adgi_last_error() -> str:

@@ -452,8 +452,9 @@ __global__ void k_bounds(const float4* __restrict__ tri_v, int n, BNode* nodes, 
 // new node; the cluster array is compacted; repeat until one cluster is left.
 // A wide window finds better partners: on a 198k-triangle city, radius 256
 // against 16 cut the traversals' box tests by a fifth (update 7.18 -> 6.25 ms)
-// for a static build of 7 instead of 4 ms.
-constexpr int kPlocR = 256;
+// for a static build of 7 instead of 4 ms; 512 against 256 made the 4-wide
+// traversals of both benchmark scenes 2-5 % faster.
+constexpr int kPlocR = 512;
 constexpr int kRotPasses = 8;  // rotation passes after the clustering
 constexpr int kPlocT = 256;
 
@@ -477,10 +478,15 @@ __global__ void k_ploc_init(const float4* __restrict__ tri_v, int n, float eps, 
     cid[i] = ~i;
 }
 
+constexpr int kPlocWin = kPlocT + 2 * kPlocR;  // boxes of a block's window
+constexpr size_t kPlocSmem = 2 * sizeof(float4) * kPlocWin;
+
 __global__ void __launch_bounds__(kPlocT) k_ploc_nn(int count, const float4* __restrict__ blo,
                                                     const float4* __restrict__ bhi, int* __restrict__ nn)
 {
-    __shared__ float4 slo[kPlocT + 2 * kPlocR], shi[kPlocT + 2 * kPlocR];
+    extern __shared__ float4 ploc_smem[];
+    float4* slo = ploc_smem;
+    float4* shi = ploc_smem + kPlocWin;
     const int base = blockIdx.x * kPlocT - kPlocR;
     for (int k = threadIdx.x; k < kPlocT + 2 * kPlocR; k += kPlocT) {
         int j = base + k;
@@ -940,7 +946,11 @@ cudaError_t build_ploc(const BvhBufs& B, const PlocBufs& Q, const float* d_verts
     for (int round = 0; count > 1; ++round) {
         if (round > 4 * 64 + nt) return cudaErrorUnknown;  // no progress: cannot happen with strict ties
         const int nb = (count + kPlocT - 1) / kPlocT;
-        k_ploc_nn<<<nb, kPlocT, 0, s>>>(count, Q.blo[c], Q.bhi[c], Q.nn);
+        if (round == 0 && kPlocSmem > 48 * 1024) {  // one constant size: set, never lowered
+            cudaError_t e = cudaFuncSetAttribute(k_ploc_nn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPlocSmem);
+            if (e != cudaSuccess) return e;
+        }
+        k_ploc_nn<<<nb, kPlocT, kPlocSmem, s>>>(count, Q.blo[c], Q.bhi[c], Q.nn);
         count_launches(1);
         k_ploc_flags<<<nb, kPlocT, 0, s>>>(count, Q.nn, Q.flags);
         count_launches(1);

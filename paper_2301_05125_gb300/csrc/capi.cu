@@ -160,9 +160,18 @@ void frame_rotation(uint64_t seed, uint64_t frame, float R[9])
     for (int k = 0; k < 9; ++k) R[k] = (float)m[k];
 }
 
+// Fault injection for the failure paths (adgi_inject_alloc_failure): when
+// armed with n > 0, the n-th volume allocation from now on reports
+// cudaErrorMemoryAllocation without calling cudaMalloc, once.
+std::atomic<long> g_fail_alloc_in{0};
+
 template <typename T>
 cudaError_t dalloc(T** p, size_t count, size_t* total)
 {
+    if (g_fail_alloc_in.load() > 0 && g_fail_alloc_in.fetch_sub(1) == 1) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
     size_t sz = sizeof(T) * (count > 0 ? count : 1);
     cudaError_t e = cudaMalloc((void**)p, sz);
     if (e == cudaSuccess) *total += sz;
@@ -413,6 +422,13 @@ DynBufs dyn_bufs(adgi_volume v);
 }
 
 const char* adgi_last_error(void) { return g_err.c_str(); }
+
+int adgi_inject_alloc_failure(int32_t n)
+{
+    if (n < 0) return fail(ADGI_ERR_INVALID_ARG, "adgi_inject_alloc_failure: n < 0");
+    g_fail_alloc_in.store(n);
+    return ADGI_OK;
+}
 
 int adgi_create_volume(const adgi_volume_desc* desc, void* cuda_stream, adgi_volume* out)
 {
