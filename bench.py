@@ -61,10 +61,14 @@ def _peaks():
 
 # the source files each profiled kernel is built from (its .cu file and the
 # shared headers): a committed ncu figure is used only while they are unchanged
+# (a traversal's traffic also depends on the trees the builders make)
 KERNEL_SOURCES = {
-    "k_main_trace": ["trace.cu"], "k_pilot_trace": ["trace.cu"], "k_shadow": ["shade.cu"],
-    "k_shade_finish": ["shade.cu"], "k_blend": ["update.cu"], "k_blend_plan": ["update.cu"],
-    "k_mh_trace": ["trace.cu"], "k_mh_blend": ["update.cu"],
+    "k_main_trace": ["trace.cu", "wave.cuh", "bvh.cu", "wide.cu"],
+    "k_pilot_trace": ["trace.cu", "wave.cuh", "bvh.cu", "wide.cu"],
+    "k_shadow": ["shade.cu", "wave.cuh", "bvh.cu", "wide.cu"], "k_shade_finish": ["shade.cu", "wave.cuh"],
+    "k_blend": ["update.cu", "phase.cuh"], "k_blend_plan": ["update.cu", "phase.cuh"],
+    "k_mh_trace": ["trace.cu", "wave.cuh", "bvh.cu", "wide.cu"], "k_mh_blend": ["update.cu", "phase.cuh"],
+    "k_tick": ["tick.cu", "wave.cuh", "phase.cuh", "bvh.cu", "wide.cu"],
 }
 
 
@@ -292,14 +296,17 @@ def run_reference(args):
 
 def _batched_section(args, adgi, torch, dev):
     """Batched form: 24 volumes of uneven size over 6 scenes.  Plain FP32
-    per-volume updates (one after another on one stream) against FP16 atlases
-    updated by one captured graph per tick with autotuned block shapes."""
+    per-volume updates (one after another on one stream) against one captured
+    graph per tick with autotuned block shapes (FP32 and FP16 atlases) and
+    against one persistent cooperative kernel per tick (FP32 and FP16)."""
     from paper_2301_05125_gb300 import scenegen as S
 
     ticks = max(3, min(args.steps, 20))
     out = {}
-    for label, fp16, batched in (("per_volume_fp32", 0, False), ("batched_fp32_graph", 0, True),
-                                 ("batched_fp16_graph", 1, True)):
+    for label, fp16, mode in (("per_volume_fp32", 0, "plain"), ("batched_fp32_graph", 0, "graph"),
+                              ("batched_fp16_graph", 1, "graph"), ("persistent_tick_fp32", 0, "tick"),
+                              ("persistent_tick_fp16", 1, "tick")):
+        batched = mode != "plain"
         ws = S.batched(args.seed, fp16=fp16)
         stream = torch.cuda.Stream(device=dev)
         vols = []
@@ -324,11 +331,13 @@ def _batched_section(args, adgi, torch, dev):
                 adgi.adgi_update(v.h, fr)
         tuned = []
         B = None
-        if batched:
+        if mode == "graph":
             for v, w in zip(vols, ws):
                 t = adgi.adgi_autotune(v.h, adgi.make_frame(0, w.seed, w.lights_at(0), w.sky), 2)
                 tuned.append([t.trace_block, t.shade_block, t.shadow_blocks_per_sm, t.blend_block])
             B = adgi.Batch(vols, stream.cuda_stream)
+        elif mode == "tick":
+            B = adgi.Tick(vols, stream.cuda_stream)
         f = 1
         for _ in range(2):  # warm-up ticks (the first one captures the graph)
             move(f)
@@ -357,6 +366,11 @@ def _batched_section(args, adgi, torch, dev):
             f += 1
         for v in vols:
             v.stats()
+        info = None
+        if mode == "tick":
+            if B.sync() != 0:
+                raise RuntimeError("persistent tick: " + adgi.adgi_last_error())
+            info = B.info()
         if B is not None:
             B.close()
         for v in vols:
@@ -365,12 +379,17 @@ def _batched_section(args, adgi, torch, dev):
                       "p50_ms": float(np.percentile(ms, 50)), "p99_ms": float(np.percentile(ms, 99)), "ticks": ticks}
         if tuned:
             out[label]["tuning_trace_shade_shadowPerSM_blend"] = tuned
+        if info:
+            out[label]["grid"] = info
+            out[label]["kernel_launches_per_tick"] = 1
     out["volumes"] = len(S.batched(args.seed))
     out["speedup_batched_fp16_vs_per_volume_fp32"] = (out["batched_fp16_graph"]["rays_per_s"] /
                                                       out["per_volume_fp32"]["rays_per_s"])
     # the same speed-up split into its two parts
     out["speedup_batching_fp32"] = out["batched_fp32_graph"]["rays_per_s"] / out["per_volume_fp32"]["rays_per_s"]
     out["speedup_fp16_batched"] = out["batched_fp16_graph"]["rays_per_s"] / out["batched_fp32_graph"]["rays_per_s"]
+    out["speedup_tick_vs_graph_fp32"] = (out["persistent_tick_fp32"]["rays_per_s"] /
+                                         out["batched_fp32_graph"]["rays_per_s"])
     out["fp16_error_vs_fp64_oracle"] = "see tests/test_gpu_fp16.py: mean 1-4e-4, max 2-4e-3 (atlases), 2.5e-3 (queries)"
     return out
 

@@ -55,7 +55,7 @@ extern "C" {
 #define ADGI_ERR_OVER_BUDGET (-3) /* the volume does not fit the memory budget */
 #define ADGI_ERR_NO_SCENE (-4)    /* adgi_update() before adgi_set_scene() */
 #define ADGI_ERR_CUDA (-5)        /* a CUDA call failed (message in adgi_last_error) */
-#define ADGI_ERR_TIMEOUT (-6)     /* a bounded wait gave up (adgi_server_drain) */
+#define ADGI_ERR_TIMEOUT (-6)     /* a bounded wait gave up (adgi_server_drain, adgi_tick_sync) */
 
 typedef struct adgi_volume_s* adgi_volume;
 
@@ -241,6 +241,41 @@ int adgi_batch_create(const adgi_volume* vols, int32_t n, void* cuda_stream, adg
 /* frames: host array of n frames, frames[i] for vols[i]. */
 int adgi_batch_update(adgi_batch batch, const adgi_frame* frames);
 int adgi_batch_destroy(adgi_batch batch);
+
+/* The batched update as ONE persistent kernel launch per tick (the batched
+ * form of Sec. 3.4's update with grid-wide phases): a cooperative grid of as
+ * many blocks as the GPU holds at once runs the update's phases (clip classes
+ * and blend plan, pilot rays and their shading, change measure, allocation,
+ * adaptive rays and their shading, blend) for every volume, with a grid-wide
+ * barrier between phases.  Results equal those of adgi_update on each volume
+ * (same integers, same floating-point operations in the same order).  Each
+ * tick copies the frame descriptors from pinned host memory, clears the
+ * tick's control block and launches the kernel on cuda_stream; a volume's
+ * moving part, when its vertices moved, is rebuilt before the launch.
+ *
+ * Every barrier wait gives up after a time limit (2 s unless set by
+ * adgi_tick_set_wait); the blocks then return and the tick's status records
+ * it: adgi_tick_sync waits for the stream and returns ADGI_ERR_TIMEOUT (the
+ * volumes' state of that tick is then undefined; the next tick runs normally).
+ *
+ * Volumes: deterministic allocation (sampler 0) and the texel blend
+ * (blend_mode 0), on the current device; their probes at most 8 x 2,048 per
+ * resident block in total.  Errors: INVALID_ARG (NULL, duplicates, another
+ * mode, too many probes), OOM, CUDA (no resident grid). */
+typedef struct adgi_tick_s* adgi_tick;
+int adgi_tick_create(const adgi_volume* vols, int32_t n, void* cuda_stream, adgi_tick* out);
+/* frames: host array of n frames, frames[i] for vols[i]; enqueues one tick. */
+int adgi_tick_update(adgi_tick tick, const adgi_frame* frames);
+/* Wait for cuda_stream; ADGI_ERR_TIMEOUT when a wait of the last tick gave up. */
+int adgi_tick_sync(adgi_tick tick);
+/* Barrier wait limit in ns (1 ns .. 60 s) and a test hook: stall_barrier >= 0
+ * names a barrier of the next ticks that no block arrives at, so its wait
+ * runs out (-1: none).  Synchronises cuda_stream. */
+int adgi_tick_set_wait(adgi_tick tick, uint64_t limit_ns, int32_t stall_barrier);
+/* The persistent grid (blocks), its dynamic shared memory per block and the
+ * allocation chunks of the last tick (0 before the first). */
+int adgi_tick_info(adgi_tick tick, uint32_t* grid_blocks, uint32_t* smem_bytes, uint32_t* chunks);
+int adgi_tick_destroy(adgi_tick tick);
 
 /* Block shapes of a volume's kernels.  adgi_autotune times candidate shapes
  * of the nearest-hit traversal (64/128/256 threads), the shading wavefront

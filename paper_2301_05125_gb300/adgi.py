@@ -112,7 +112,9 @@ EXPORTED = ["adgi_create_volume", "adgi_set_scene", "adgi_move_vertices", "adgi_
             "adgi_batch_update", "adgi_batch_destroy", "adgi_autotune", "adgi_set_tuning", "adgi_get_tuning",
             "adgi_server_create", "adgi_server_add_volume", "adgi_server_submit", "adgi_server_poll",
             "adgi_server_drain", "adgi_server_volume", "adgi_server_remove_volume", "adgi_server_info",
-            "adgi_server_destroy", "adgi_update_slab", "adgi_slab_copy", "adgi_slab_bytes", "adgi_inject_alloc_failure", "adgi_last_error"]
+            "adgi_server_destroy", "adgi_update_slab", "adgi_slab_copy", "adgi_slab_bytes", "adgi_inject_alloc_failure",
+            "adgi_tick_create", "adgi_tick_update", "adgi_tick_sync", "adgi_tick_set_wait", "adgi_tick_info",
+            "adgi_tick_destroy", "adgi_last_error"]
 
 BVH_NOALLOC_MAX_TRIS = 32768
 
@@ -149,6 +151,12 @@ def load(path: str = LIB_PATH):
     L.adgi_batch_create.argtypes = [C.POINTER(vp), i32, vp, C.POINTER(vp)]
     L.adgi_batch_update.argtypes = [vp, C.POINTER(adgi_frame)]
     L.adgi_batch_destroy.argtypes = [vp]
+    L.adgi_tick_create.argtypes = [C.POINTER(vp), i32, vp, C.POINTER(vp)]
+    L.adgi_tick_update.argtypes = [vp, C.POINTER(adgi_frame)]
+    L.adgi_tick_sync.argtypes = [vp]
+    L.adgi_tick_set_wait.argtypes = [vp, u64, i32]
+    L.adgi_tick_info.argtypes = [vp, C.POINTER(C.c_uint32), C.POINTER(C.c_uint32), C.POINTER(C.c_uint32)]
+    L.adgi_tick_destroy.argtypes = [vp]
     L.adgi_autotune.argtypes = [vp, C.POINTER(adgi_frame), i32, C.POINTER(adgi_tuning)]
     L.adgi_set_tuning.argtypes = [vp, C.POINTER(adgi_tuning)]
     L.adgi_get_tuning.argtypes = [vp, C.POINTER(adgi_tuning)]
@@ -316,6 +324,37 @@ def adgi_batch_update(batch, frames):
 
 def adgi_batch_destroy(batch):
     _check(load().adgi_batch_destroy(batch))
+
+
+def adgi_tick_create(vols, stream=None):
+    arr = (C.c_void_p * len(vols))(*[v.value if isinstance(v, C.c_void_p) else v for v in vols])
+    h = C.c_void_p()
+    _check(load().adgi_tick_create(arr, len(vols), stream, C.byref(h)))
+    return h
+
+
+def adgi_tick_update(tick, frames):
+    arr = (adgi_frame * len(frames))(*frames)
+    _check(load().adgi_tick_update(tick, arr))
+
+
+def adgi_tick_sync(tick) -> int:
+    """ADGI_OK, or the negative error code (ADGI_ERR_TIMEOUT: a barrier wait gave up)."""
+    return int(load().adgi_tick_sync(tick))
+
+
+def adgi_tick_set_wait(tick, limit_ns, stall_barrier=-1):
+    _check(load().adgi_tick_set_wait(tick, int(limit_ns), int(stall_barrier)))
+
+
+def adgi_tick_info(tick):
+    g, sm, ch = C.c_uint32(), C.c_uint32(), C.c_uint32()
+    _check(load().adgi_tick_info(tick, C.byref(g), C.byref(sm), C.byref(ch)))
+    return {"grid_blocks": g.value, "smem_bytes": sm.value, "chunks": ch.value}
+
+
+def adgi_tick_destroy(tick):
+    _check(load().adgi_tick_destroy(tick))
 
 
 def adgi_autotune(vol, frame: adgi_frame, reps=3) -> adgi_tuning:
@@ -721,6 +760,39 @@ class Batch:
     def close(self):
         if self.h:
             adgi_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Tick:
+    """Owning wrapper of an adgi_tick: one persistent kernel launch per tick for all volumes."""
+
+    def __init__(self, volumes, stream=None):
+        self.volumes = list(volumes)
+        self.h = adgi_tick_create([v.h for v in self.volumes], stream)
+
+    def update(self, frames):
+        """frames: list of adgi_frame (make_frame), one per volume."""
+        self._keep = frames
+        adgi_tick_update(self.h, frames)
+
+    def sync(self) -> int:
+        return adgi_tick_sync(self.h)
+
+    def set_wait(self, limit_ns, stall_barrier=-1):
+        adgi_tick_set_wait(self.h, limit_ns, stall_barrier)
+
+    def info(self):
+        return adgi_tick_info(self.h)
+
+    def close(self):
+        if self.h:
+            adgi_tick_destroy(self.h)
             self.h = None
 
     def __del__(self):

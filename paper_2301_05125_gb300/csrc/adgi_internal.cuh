@@ -332,6 +332,19 @@ constexpr int kMaxDepth = 96;
 constexpr int kStack = kMaxDepth;
 static_assert(kWide4Stack >= kStack, "one stack array serves both traversals");
 
+// A load of data that an earlier phase of the same launch may have written.
+// The ordinary kernels take the read-only (non-coherent) path; the
+// persistent batched tick (tick.cu), whose phases follow one another inside
+// one launch, takes a plain coherent load, which its grid barriers order.
+template <bool kLive, typename T>
+__device__ __forceinline__ T ldl(const T* p)
+{
+    if constexpr (kLive)
+        return *p;
+    else
+        return __ldg(p);
+}
+
 // Traversal of the two-part scene as one flat loop over one stack of
 // global node indices.  The loop has no early exit, so the lanes of a warp
 // reconverge every iteration.

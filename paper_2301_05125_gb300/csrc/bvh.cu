@@ -452,9 +452,11 @@ __global__ void k_bounds(const float4* __restrict__ tri_v, int n, BNode* nodes, 
 // new node; the cluster array is compacted; repeat until one cluster is left.
 // A wide window finds better partners: on a 198k-triangle city, radius 256
 // against 16 cut the traversals' box tests by a fifth (update 7.18 -> 6.25 ms)
-// for a static build of 7 instead of 4 ms; 512 against 256 made the 4-wide
-// traversals of both benchmark scenes 2-5 % faster.
-constexpr int kPlocR = 512;
+// for a static build of 7 instead of 4 ms.  With the 4-wide traversal, the
+// updates of the 2M- and 198k-triangle scenes took 18.56 / 5.12 ms at radius
+// 256, 18.24 / 4.94 at 512, 17.19 / 4.92 at 1024, 17.16 / 4.71 at 1536 and
+// 16.90 / 4.97 at 2048 (the static build of the 2M triangles: ~0.1 s).
+constexpr int kPlocR = 1536;
 constexpr int kRotPasses = 8;  // rotation passes after the clustering
 constexpr int kPlocT = 256;
 

@@ -1461,6 +1461,252 @@ int adgi_batch_destroy(adgi_batch b)
     return ADGI_OK;
 }
 
+// ---- the batched update as one persistent launch per tick (tick.cu)
+
+struct adgi_tick_s {
+    std::vector<adgi_volume> vols;
+    cudaStream_t stream = nullptr;
+    std::vector<cudaEvent_t> vol_ev;  // each volume's stream, joined before a tick
+    cudaEvent_t done = nullptr;       // the last tick has read the staged frames
+    FrameDev* h_fd = nullptr;         // pinned staging of the frame descriptors
+    TickCtl* d_ctl = nullptr;
+    TickVol* d_vols = nullptr;
+    uint32_t* d_pre = nullptr;
+    int* d_cvol = nullptr;
+    unsigned long long* d_scr = nullptr;
+    int n_chunks = 0;
+    unsigned grid = 0;
+    size_t smem = 0;
+    bool tables_ok = false;
+    bool launched = false;
+};
+
+namespace {
+void free_tick_tables(adgi_tick t)
+{
+    cudaFree(t->d_vols);
+    cudaFree(t->d_pre);
+    cudaFree(t->d_cvol);
+    cudaFree(t->d_scr);
+    t->d_vols = nullptr;
+    t->d_pre = nullptr;
+    t->d_cvol = nullptr;
+    t->d_scr = nullptr;
+    t->tables_ok = false;
+}
+
+void free_tick(adgi_tick t)
+{
+    if (!t) return;
+    free_tick_tables(t);
+    cudaFree(t->d_ctl);
+    if (t->h_fd) cudaFreeHost(t->h_fd);
+    for (cudaEvent_t e : t->vol_ev)
+        if (e) cudaEventDestroy(e);
+    if (t->done) cudaEventDestroy(t->done);
+    delete t;
+}
+
+TickVol tick_vol_of(adgi_tick t, int i)
+{
+    adgi_volume v = t->vols[i];
+    TickVol T;
+    std::memset(&T, 0, sizeof(T));
+    T.V = v->V;
+    T.V.p_lo = 0;
+    T.V.p_hi = v->V.P;
+    T.S = scene_view(v);
+    T.FD = v->fdev;
+    T.lut_c = v->lut_c;
+    T.cls = v->cls;
+    T.sf = v->sf;
+    T.pil_hit = v->pil_hit;
+    T.pil_rec = v->pil_rec;
+    T.pil_lum = v->pil_lum;
+    T.m_hit = v->m_hit;
+    T.m_rec = v->m_rec;
+    T.n = v->n;
+    T.off = v->off;
+    T.Wk = ShadeWork{v->vis, v->jobs, v->job_light, v->job_count,
+                     (unsigned)std::min<size_t>(v->job_cap, 0xFFFFFFFFu), 0u, v->shadow_ctr};
+    T.C = ChangeBufs{v->pil_hit, v->pil_lum, v->lut_v, v->lut_c, v->qv,  v->qr,  v->qv_even, v->qr_even,
+                     v->amp_v,   v->amp_r,   v->age_v, v->age_r, v->trv, v->trr, v->G,       v->W, v->qd, v->vout_even};
+    T.B = BlendBufs{v->off, v->sf,  v->pil_rec, v->m_rec,
+                    v->irr, v->dep, v->dep_n,   carve_blend_plan(v->plan, v->V.rays_max - 8, v->V.Ti, v->V.Td),
+                    v->tex_src};
+    T.avg = v->V.rays_avg;
+    T.m0 = v->V.m0;
+    T.rmax = v->V.rays_max;
+    return T;
+}
+
+// (Re)build the device tables: per-volume parameters, the phases' virtual
+// blocks, the allocation chunks, the grid and its shared memory.
+int build_tick_tables(adgi_tick t, std::vector<TickVol>& hv)
+{
+    CK(cudaStreamSynchronize(t->stream));  // no tick may still read the old tables
+    free_tick_tables(t);
+    const int n = (int)t->vols.size();
+    std::vector<uint32_t> pre((size_t)kTickPhases * (n + 1), 0u);
+    std::vector<int> cvol;
+    size_t smem = 0;
+    for (int i = 0; i < n; ++i) {
+        adgi_volume v = t->vols[i];
+        uint32_t cnt[kTickPhases];
+        tick_phase_blocks(v->V, v->R_main, cnt);
+        for (int ph = 0; ph < kTickPhases; ++ph) {
+            const uint64_t x = (uint64_t)pre[(size_t)ph * (n + 1) + i] + cnt[ph];
+            if (x > 0x7FFFFFFFull) return fail(ADGI_ERR_INVALID_ARG, "tick: too much work for one launch");
+            pre[(size_t)ph * (n + 1) + i + 1] = (uint32_t)x;
+        }
+        hv[i].chunk0 = (int)cvol.size();
+        for (int c = 0; c < (v->V.P + kTickChunk - 1) / kTickChunk; ++c) cvol.push_back(i);
+        smem = std::max(smem, tick_smem_bytes(v->V));
+    }
+    const unsigned grid = tick_grid_blocks(smem);
+    if (grid == 0) return fail(ADGI_ERR_CUDA, "tick: no resident grid for the persistent kernel");
+    if (cvol.size() > (size_t)kTickOwn * grid)
+        return fail(ADGI_ERR_INVALID_ARG, "tick: more probes than one persistent grid allocates");
+    size_t b = 0;
+    if (dalloc(&t->d_vols, (size_t)n, &b) != cudaSuccess || dalloc(&t->d_pre, pre.size(), &b) != cudaSuccess ||
+        dalloc(&t->d_cvol, cvol.size(), &b) != cudaSuccess ||
+        dalloc(&t->d_scr, (size_t)kTickScratch * cvol.size(), &b) != cudaSuccess) {
+        free_tick_tables(t);
+        return fail(ADGI_ERR_OOM, "tick tables");
+    }
+    CK(cudaMemcpyAsync(t->d_vols, hv.data(), sizeof(TickVol) * n, cudaMemcpyHostToDevice, t->stream));
+    CK(cudaMemcpyAsync(t->d_pre, pre.data(), sizeof(uint32_t) * pre.size(), cudaMemcpyHostToDevice, t->stream));
+    CK(cudaMemcpyAsync(t->d_cvol, cvol.data(), sizeof(int) * cvol.size(), cudaMemcpyHostToDevice, t->stream));
+    CK(cudaStreamSynchronize(t->stream));  // the host vectors are freed on return
+    t->n_chunks = (int)cvol.size();
+    t->grid = grid;
+    t->smem = smem;
+    t->tables_ok = true;
+    return ADGI_OK;
+}
+}  // namespace
+
+int adgi_tick_create(const adgi_volume* vols, int32_t n, void* cuda_stream, adgi_tick* out)
+{
+    if (!out || !vols || n <= 0 || n > 4096) return fail(ADGI_ERR_INVALID_ARG, "bad tick arguments");
+    *out = nullptr;
+    for (int i = 0; i < n; ++i) {
+        if (!vols[i]) return fail(ADGI_ERR_INVALID_ARG, "NULL volume in tick");
+        for (int j = 0; j < i; ++j)
+            if (vols[j] == vols[i]) return fail(ADGI_ERR_INVALID_ARG, "a volume appears twice in the tick");
+        if (vols[i]->desc.sampler != 0 || vols[i]->desc.blend_mode != 0)
+            return fail(ADGI_ERR_INVALID_ARG, "tick: only the deterministic allocation with the texel blend");
+    }
+    adgi_tick t = new adgi_tick_s();
+    t->vols.assign(vols, vols + n);
+    t->stream = (cudaStream_t)cuda_stream;
+    t->vol_ev.assign(n, nullptr);
+    cudaError_t e = cudaEventCreateWithFlags(&t->done, cudaEventDisableTiming);
+    for (int i = 0; i < n && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&t->vol_ev[i], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&t->h_fd, sizeof(FrameDev) * n);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&t->d_ctl, sizeof(TickCtl));
+    if (e == cudaSuccess) {
+        TickCtl c;
+        std::memset(&c, 0, sizeof(c));
+        c.limit_ns = 2000000000ull;  // 2 s: far beyond any phase of a tick
+        c.stall = -1;
+        e = cudaMemcpy(t->d_ctl, &c, sizeof(c), cudaMemcpyHostToDevice);
+    }
+    if (e != cudaSuccess) {
+        free_tick(t);
+        return fail(ADGI_ERR_CUDA, std::string("tick: ") + cudaGetErrorString(e));
+    }
+    *out = t;
+    return ADGI_OK;
+}
+
+int adgi_tick_update(adgi_tick t, const adgi_frame* frames)
+{
+    if (!t || !frames) return fail(ADGI_ERR_INVALID_ARG, "NULL argument");
+    const int n = (int)t->vols.size();
+    std::vector<FrameDev> fd(n);
+    bool stale = !t->tables_ok;  // a buffer the tables name may have moved
+    for (int i = 0; i < n; ++i) {
+        bool st = false;
+        int rc = prepare_update(t->vols[i], &frames[i], fd[i], &st);
+        if (rc) return rc;
+        stale = stale || st;
+    }
+    // work queued on the volumes' own streams (scene uploads, rebuilds) first
+    for (int i = 0; i < n; ++i) {
+        if (t->vols[i]->stream == t->stream) continue;
+        CK(cudaEventRecord(t->vol_ev[i], t->vols[i]->stream));
+        CK(cudaStreamWaitEvent(t->stream, t->vol_ev[i], 0));
+    }
+    // moving parts: refreshed and rebuilt before the launch
+    for (int i = 0; i < n; ++i) {
+        adgi_volume v = t->vols[i];
+        if (v->nd > 0 && v->dyn_dirty) {
+            CK(fill_tri_orig(v->verts, v->idx, v->dlist, v->nv, v->nd, v->tri_orig, t->stream));
+            int rc = build_moving(v, t->stream);
+            if (rc) return rc;
+            v->dyn_dirty = false;
+        }
+    }
+    if (stale) {
+        std::vector<TickVol> hv(n);
+        for (int i = 0; i < n; ++i) hv[i] = tick_vol_of(t, i);
+        int rc = build_tick_tables(t, hv);
+        if (rc) return rc;
+    }
+    // the staging buffer is rewritten once the previous tick has copied it
+    if (t->launched) CK(cudaEventSynchronize(t->done));
+    std::memcpy(t->h_fd, fd.data(), sizeof(FrameDev) * n);
+    for (int i = 0; i < n; ++i)  // each volume's own descriptor, as the plain update leaves it
+        CK(cudaMemcpyAsync(t->vols[i]->fdev, t->h_fd + i, sizeof(FrameDev), cudaMemcpyHostToDevice, t->stream));
+    CK(cudaMemsetAsync(t->d_ctl, 0, offsetof(TickCtl, limit_ns), t->stream));
+    CK(launch_tick(t->d_vols, n, t->d_pre, t->d_cvol, t->n_chunks, t->d_scr, t->d_ctl, t->grid, t->smem, t->stream));
+    CK(cudaEventRecord(t->done, t->stream));
+    t->launched = true;
+    for (int i = 0; i < n; ++i) finish_update(t->vols[i], fd[i], &frames[i]);
+    return ADGI_OK;
+}
+
+int adgi_tick_sync(adgi_tick t)
+{
+    if (!t) return fail(ADGI_ERR_INVALID_ARG, "NULL tick");
+    CK(cudaStreamSynchronize(t->stream));
+    int status = 0;
+    CK(cudaMemcpy(&status, &t->d_ctl->status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (status == kTickTimedOut) return fail(ADGI_ERR_TIMEOUT, "tick: a grid barrier wait gave up");
+    if (status != 0) return fail(ADGI_ERR_CUDA, "tick: bad status");
+    return ADGI_OK;
+}
+
+int adgi_tick_set_wait(adgi_tick t, uint64_t limit_ns, int32_t stall_barrier)
+{
+    if (!t || limit_ns == 0 || limit_ns > 60000000000ull || stall_barrier < -1)
+        return fail(ADGI_ERR_INVALID_ARG, "bad tick wait arguments");
+    CK(cudaStreamSynchronize(t->stream));
+    const unsigned long long lim = limit_ns;
+    const int st = stall_barrier;
+    CK(cudaMemcpy(&t->d_ctl->limit_ns, &lim, sizeof(lim), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(&t->d_ctl->stall, &st, sizeof(st), cudaMemcpyHostToDevice));
+    return ADGI_OK;
+}
+
+int adgi_tick_info(adgi_tick t, uint32_t* grid_blocks, uint32_t* smem_bytes, uint32_t* chunks)
+{
+    if (!t) return fail(ADGI_ERR_INVALID_ARG, "NULL tick");
+    if (grid_blocks) *grid_blocks = t->grid;
+    if (smem_bytes) *smem_bytes = (uint32_t)t->smem;
+    if (chunks) *chunks = (uint32_t)t->n_chunks;
+    return ADGI_OK;
+}
+
+int adgi_tick_destroy(adgi_tick t)
+{
+    if (!t) return ADGI_OK;
+    cudaStreamSynchronize(t->stream);
+    free_tick(t);
+    return ADGI_OK;
+}
+
 int adgi_set_tuning(adgi_volume v, const adgi_tuning* t)
 {
     if (!v || !t) return fail(ADGI_ERR_INVALID_ARG, "NULL argument");

@@ -219,4 +219,59 @@ cudaError_t launch_blend_cos(const VolConst& V, const FrameDev* FD, const BlendB
 cudaError_t launch_query(const VolConst& V, const void* irr, const void* dep, const float* pos, const float* nrm, int n,
                          float* out, cudaStream_t s);
 
+// ---- the batched update as one persistent launch per tick (tick.cu)
+
+// One volume of a tick: what the update's ordinary kernels take as
+// parameters, kept in device memory for the persistent kernel.
+struct TickVol {
+    VolConst V;
+    SceneDev S;
+    const FrameDev* FD;
+    const uint16_t* lut_c;
+    uint8_t* cls;             // [P] clip classes (written by the first phase)
+    const float4* sf;         // SF table
+    int2* pil_hit;
+    float4* pil_rec;
+    float* pil_lum;
+    int2* m_hit;
+    float4* m_rec;
+    uint32_t* n;              // [P] rays per probe (the allocation's output)
+    uint32_t* off;            // [P+1] adaptive-ray offsets
+    ShadeWork Wk;
+    ChangeBufs C;
+    BlendBufs B;
+    int avg, m0, rmax;        // the allocation's budget, floor and cap
+    int chunk0;               // first allocation chunk of this volume
+};
+
+constexpr int kTickThreads = 256;  // threads per block of the persistent kernel
+constexpr int kTickChunk = 2048;   // probes per allocation chunk (8 per thread)
+constexpr int kTickOwn = 8;        // allocation chunks one block owns at most
+constexpr int kTickPasses = 64;    // proportional allocation passes at most
+constexpr int kTickPhases = 13;    // phases of a tick (grid barriers between them)
+constexpr int kTickScratch = 9;    // 64-bit allocation partial sums per chunk
+constexpr int kTickTimedOut = 1;   // TickCtl::status: a barrier wait gave up
+
+// Control block of a tick (device memory).  The part up to `limit_ns` is
+// cleared before every launch; the wait limit and the test hook stay.
+struct TickCtl {
+    unsigned bar_count;             // blocks arrived at the current barrier
+    unsigned bar_gen;               // barriers completed
+    int status;                     // 0, or kTickTimedOut
+    unsigned pass_flag[kTickPasses];  // a chunk took part in allocation pass i
+    unsigned rem_flag[2];           // a chunk took part in remainder round j (j mod 2)
+    unsigned long long limit_ns;    // a barrier wait gives up after this long
+    int stall;                      // test hook: barrier that never completes (-1: none)
+};
+
+// Per-volume virtual-block counts of each phase (prefix sums, host side):
+// pre[ph * (nv + 1) + i] = the first virtual block of volume i in phase ph.
+void tick_phase_blocks(const VolConst& V, uint32_t R_main, uint32_t counts[kTickPhases]);
+// dynamic shared memory of the persistent kernel for a volume
+size_t tick_smem_bytes(const VolConst& V);
+// blocks of the persistent grid (all resident at once) for that shared memory, 0 on error
+unsigned tick_grid_blocks(size_t smem);
+cudaError_t launch_tick(const TickVol* vols, int nv, const uint32_t* pre, const int* cvol, int n_chunks,
+                        unsigned long long* scratch, TickCtl* ctl, unsigned grid, size_t smem, cudaStream_t s);
+
 }  // namespace adgi

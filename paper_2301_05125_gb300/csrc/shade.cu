@@ -13,120 +13,11 @@
 // loops over lights while its neighbours missed the scene or faced away.
 #include "adgi_internal.cuh"
 #include "kernels.cuh"
+#include "wave.cuh"
 
 namespace adgi {
 
 namespace {
-
-constexpr float kInvPi = 0.31830987f;
-constexpr float kLumR = 0.2126f, kLumG = 0.7152f, kLumB = 0.0722f;
-
-__device__ __forceinline__ int probe_of_ray(const uint32_t* __restrict__ off, uint32_t r, int lo, int hi)
-{
-    while (lo < hi) {
-        int mid = (lo + hi + 1) >> 1;
-        if (__ldg(off + mid) <= r)
-            lo = mid;
-        else
-            hi = mid - 1;
-    }
-    return lo;
-}
-
-// The rays of a block: pilot rays (ray r = probe r/8, octant r%8), adaptive
-// rays (ray r of the prefix offsets off[]; the block's probe range is found
-// once by two threads) or Metropolis samples (ray r = sample sf[r] of the
-// grouped order).
-struct RaySet {
-    int mode;                 // 0 pilot, 1 adaptive, 2 Metropolis samples in grouped order, 3 dynamic rays
-    uint32_t n;               // rays in the set (dynamic rays: the budget)
-    const uint32_t* off;      // adaptive: prefix offsets
-    const float4* sf;         // adaptive: spherical Fibonacci sets; samples: {w.xyz, probe bits}
-    DynRays dyn;              // dynamic rays
-};
-
-// The first ray of the set for probes [p_lo, p_hi): pilot rays 8 p_lo,
-// adaptive rays off[p_lo]; thread idx of the launch takes ray base + idx.
-__device__ __forceinline__ uint32_t ray_base(const VolConst& V, const RaySet& Rs)
-{
-    return Rs.mode == 0 ? (uint32_t)V.p_lo * kPilots : Rs.mode == 1 ? __ldg(Rs.off + V.p_lo) : 0u;
-}
-
-__device__ __forceinline__ void block_range(const VolConst& V, const RaySet& Rs, int* s_lo, int* s_hi)
-{
-    if (Rs.mode == 1) {
-        const uint32_t b = ray_base(V, Rs);
-        uint32_t r0 = b + blockIdx.x * blockDim.x;
-        uint32_t r1 = b + min(Rs.n - 1, blockIdx.x * blockDim.x + blockDim.x - 1);
-        if (threadIdx.x == 0) *s_lo = probe_of_ray(Rs.off, r0, 0, V.P - 1);
-        if (threadIdx.x == 32 % blockDim.x) *s_hi = probe_of_ray(Rs.off, r1, 0, V.P - 1);
-    }
-    __syncthreads();
-}
-
-// The ray a thread handles: thread r takes position r of the set; a pilot ray
-// is stored at slot r, an adaptive ray at base + (SF index of row position
-// r - base), so that a warp works on nearby directions.  Gives the slot,
-// origin and direction; false if the ray range is inconsistent.
-__device__ __forceinline__ bool ray_of(const VolConst& V, const FrameConst& F, const RaySet& Rs, uint32_t r, int lo,
-                                       int hi, uint32_t& slot, float3& o, float3& d)
-{
-    if (Rs.mode == 0) {
-        int p = (int)(r >> 3);
-        if (V.cls[p] == 0) return false;  // outside V_out: no pilot ray
-        slot = r;
-        o = probe_pos(V, p);
-        d = pilot_dir(F.pilot_key, (uint32_t)p, (int)(r & 7));
-        return true;
-    }
-    if (Rs.mode == 3) {
-        int p, t;
-        if (!dyn_ray_of(V, Rs.dyn, r, p, t, d)) return false;
-        slot = r;
-        o = probe_pos(V, p);
-        return true;
-    }
-    if (Rs.mode == 2) {
-        const float4 a = __ldg(Rs.sf + r);
-        const int p = __float_as_int(a.w);
-        if (p < 0 || p >= V.P || V.cls[p] != 2) return false;  // samples outside V_in are dropped
-        slot = r;
-        o = probe_pos(V, p);
-        d = make_float3(a.x, a.y, a.z);
-        return true;
-    }
-    if (r >= __ldg(Rs.off + V.p_hi)) return false;  // beyond the adaptive rays of the probes (unspent budget)
-    int p = probe_of_ray(Rs.off, r, lo, hi);
-    uint32_t base = __ldg(Rs.off + p), m = __ldg(Rs.off + p + 1) - base;
-    if (m > (uint32_t)(V.rays_max - kPilots) || r - base >= m) return false;
-    o = probe_pos(V, p);
-    float4 s = __ldg(Rs.sf + (size_t)m * (m - 1) / 2 + (r - base));
-    const uint32_t i = (uint32_t)__float_as_int(s.w);
-    if (i >= m) return false;
-    slot = base + i;
-    d = rotate(F.R, s);
-    return true;
-}
-
-// exact FP32 geometric normal of triangle tri (original order)
-__device__ __forceinline__ float3 tri_normal(const SceneDev& S, int tri)
-{
-    float4 A = __ldg(S.tri_orig + 3 * (size_t)tri), B = __ldg(S.tri_orig + 3 * (size_t)tri + 1),
-           C = __ldg(S.tri_orig + 3 * (size_t)tri + 2);
-    float e1x = fs(B.x, A.x), e1y = fs(B.y, A.y), e1z = fs(B.z, A.z);
-    float e2x = fs(C.x, A.x), e2y = fs(C.y, A.y), e2z = fs(C.z, A.z);
-    float cx = fs(fm(e1y, e2z), fm(e1z, e2y));
-    float cy = fs(fm(e1z, e2x), fm(e1x, e2z));
-    float cz = fs(fm(e1x, e2y), fm(e1y, e2x));
-    float cl = fsq(dot3x(cx, cy, cz, cx, cy, cz));
-    return cl > 0.0f ? make_float3(fd(cx, cl), fd(cy, cl), fd(cz, cl)) : make_float3(0.f, 0.f, 1.f);
-}
-
-__device__ __forceinline__ float3 shadow_dir(const Light& Li, float3 xs)
-{
-    return Li.kind == 0 ? make_float3(fs(Li.v[0], xs.x), fs(Li.v[1], xs.y), fs(Li.v[2], xs.z))
-                        : make_float3(-Li.v[0], -Li.v[1], -Li.v[2]);
-}
 
 __global__ void __launch_bounds__(256) k_shade_prep(VolConst V, const FrameDev* __restrict__ FD, SceneDev S,
                                                     RaySet Rs, const int2* __restrict__ hit,
@@ -134,70 +25,7 @@ __global__ void __launch_bounds__(256) k_shade_prep(VolConst V, const FrameDev* 
                                                     uint8_t* __restrict__ job_light, unsigned* __restrict__ job_count,
                                                     unsigned job_cap)
 {
-    const FrameConst& F = FD->F;
-    const LightSet& L = FD->L;
-    __shared__ int s_lo, s_hi;
-    block_range(V, Rs, &s_lo, &s_hi);
-    const uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x;
-    const uint32_t r = ray_base(V, Rs) + idx;
-    bool front = false;
-    float3 xs = make_float3(0.f, 0.f, 0.f), n = make_float3(0.f, 0.f, 1.f);
-    uint32_t slot = r;
-    float3 o, d;
-    if (idx < Rs.n && ray_of(V, F, Rs, r, s_lo, s_hi, slot, o, d)) {
-        vis[slot] = 0ull;
-        int2 hv = hit[slot];
-        uint32_t h = (uint32_t)hv.x;
-        if (h != kMiss && !(h & kBackBit)) {
-            float t = __int_as_float(hv.y);
-            n = tri_normal(S, (int)h);
-            float3 x = make_float3(fa(o.x, fm(t, d.x)), fa(o.y, fm(t, d.y)), fa(o.z, fm(t, d.z)));
-            xs = make_float3(fa(x.x, fm(V.tmin, n.x)), fa(x.y, fm(V.tmin, n.y)), fa(x.z, fm(V.tmin, n.z)));
-            front = true;
-        }
-    }
-    // The block's jobs take one range of the job list: one atomic per block
-    // on the shared counter (one per warp and light contended on that
-    // address).  Pass 1 counts each warp's jobs, thread 0 scans the warp
-    // totals and claims the range, pass 2 writes each warp's jobs light by
-    // light (a warp's jobs for one light stay contiguous: nearby origins,
-    // one light, so k_shadow's warps trace coherent rays).
-    const unsigned lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    auto wants = [&](int l) {
-        if (!front) return false;
-        const float3 D = shadow_dir(L.l[l], xs);
-        return dot3x(n.x, n.y, n.z, D.x, D.y, D.z) > 0.0f;
-    };
-    unsigned wtot = 0;
-    for (int l = 0; l < L.n; ++l) wtot += (unsigned)__popc(__ballot_sync(0xFFFFFFFFu, wants(l)));
-    __shared__ unsigned s_w[8], s_base;  // at most 256 threads: 8 warps
-    if (lane == 0) s_w[w] = wtot;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned t = 0;
-        for (unsigned k = 0; k < (blockDim.x >> 5); ++k) {
-            const unsigned c = s_w[k];
-            s_w[k] = t;
-            t += c;
-        }
-        s_base = t ? atomicAdd(job_count, t) : 0u;
-    }
-    __syncthreads();
-    unsigned base = s_base + s_w[w];
-    for (int l = 0; l < L.n; ++l) {
-        const bool want = wants(l);
-        const unsigned mask = __ballot_sync(0xFFFFFFFFu, want);
-        if (want) {
-            const unsigned js = base + __popc(mask & ((1u << lane) - 1u));
-            if (js < job_cap) {
-                jobs[js] = make_uint4(__float_as_uint(xs.x), __float_as_uint(xs.y), __float_as_uint(xs.z), slot);
-                job_light[js] = (uint8_t)l;
-            } else {
-                atomicOr(V.err, kErrRayRange);
-            }
-        }
-        base += (unsigned)__popc(mask);
-    }
+    shade_prep_body<false>(V, FD, S, Rs, hit, vis, jobs, job_light, job_count, job_cap, blockIdx.x);
 }
 
 __global__ void __launch_bounds__(128, 7) k_shadow(const FrameDev* __restrict__ FD, SceneDev S,
@@ -205,27 +33,7 @@ __global__ void __launch_bounds__(128, 7) k_shadow(const FrameDev* __restrict__ 
                                                 const unsigned* __restrict__ job_count, unsigned job_cap,
                                                 unsigned long long* __restrict__ vis, unsigned long long* shadow_ctr)
 {
-    const LightSet& L = FD->L;
-    const unsigned total = min(*job_count, job_cap);
-    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(shadow_ctr, (unsigned long long)total);
-    // rounds of one job per lane with a uniform trip count per warp, and an
-    // explicit reconvergence per round: lanes that finish early wait instead
-    // of running ahead into their next job on their own
-    const unsigned stride = gridDim.x * blockDim.x;
-    const unsigned warp0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31u);
-    for (unsigned base = warp0; base < total; base += stride) {
-        const unsigned j = base + (threadIdx.x & 31u);
-        if (j < total) {
-            uint4 jb = jobs[j];
-            int l = job_light[j];
-            const Light& Li = L.l[l];
-            float3 xs = make_float3(__uint_as_float(jb.x), __uint_as_float(jb.y), __uint_as_float(jb.z));
-            float3 D = shadow_dir(Li, xs);
-            float thi = Li.kind == 0 ? 1.0f : __int_as_float(0x7F800000);
-            if (!trace_any(S, xs, D, 0.0f, thi)) atomicOr(vis + jb.w, 1ull << l);
-        }
-        __syncwarp();
-    }
+    shadow_body(FD, S, jobs, job_light, job_count, job_cap, vis, shadow_ctr, blockIdx.x, gridDim.x);
 }
 
 __global__ void __launch_bounds__(256, 4) k_shade_finish(VolConst V, const FrameDev* __restrict__ FD, SceneDev S,
@@ -234,82 +42,7 @@ __global__ void __launch_bounds__(256, 4) k_shade_finish(VolConst V, const Frame
                                                       const void* __restrict__ irr, const void* __restrict__ dep,
                                                       float4* __restrict__ rec, float* __restrict__ lum)
 {
-    const FrameConst& F = FD->F;
-    const LightSet& L = FD->L;
-    // adaptive rays and samples always carry the multi-bounce term; pilot
-    // records are blended (so need it) only on the first frame of a pair
-    const int bounce = Rs.mode != 0 || F.even;
-    __shared__ int s_lo, s_hi;
-    block_range(V, Rs, &s_lo, &s_hi);
-    const uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= Rs.n) return;
-    const uint32_t r = ray_base(V, Rs) + idx;
-    uint32_t slot;
-    float3 o, d;
-    if (Rs.mode == 0 && V.cls[r >> 3] == 0) {  // a culled pilot: a miss with nothing gathered
-        rec[r] = make_float4(0.f, 0.f, 0.f, V.depth_max);
-        if (lum) lum[r] = 0.0f;
-        return;
-    }
-    if (Rs.mode == 2) {  // a sample outside V_in: dropped, an empty record
-        const int p = __float_as_int(__ldg(Rs.sf + r).w);
-        if (p >= 0 && p < V.P && V.cls[p] != 2) {
-            rec[r] = make_float4(0.f, 0.f, 0.f, V.depth_max);
-            return;
-        }
-    }
-    if (!ray_of(V, F, Rs, r, s_lo, s_hi, slot, o, d)) return;  // flagged by the trace kernel
-    int2 hv = hit[slot];
-    uint32_t h = (uint32_t)hv.x;
-    float4 out;
-    float lo = 0.0f;
-    if (h == kMiss) {
-        lo = fa(fa(fm(kLumR, F.sky[0]), fm(kLumG, F.sky[1])), fm(kLumB, F.sky[2]));
-        out = make_float4(F.sky[0], F.sky[1], F.sky[2], V.depth_max);
-    } else {
-        float t = __int_as_float(hv.y);
-        float depth = fminf(t, V.depth_max);
-        if (h & kBackBit) {
-            out = make_float4(0.f, 0.f, 0.f, depth);
-        } else {
-            int tri = (int)h;
-            float3 n = tri_normal(S, tri);
-            float3 x = make_float3(fa(o.x, fm(t, d.x)), fa(o.y, fm(t, d.y)), fa(o.z, fm(t, d.z)));
-            unsigned long long vm = vis[slot];
-            float E0 = 0.f, E1 = 0.f, E2 = 0.f;
-            for (int l = 0; l < L.n; ++l) {
-                if (!((vm >> l) & 1ull)) continue;
-                const Light& Li = L.l[l];
-                float g;
-                if (Li.kind == 0) {
-                    float dx = fs(Li.v[0], x.x), dy = fs(Li.v[1], x.y), dz = fs(Li.v[2], x.z);
-                    float d2 = dot3x(dx, dy, dz, dx, dy, dz);
-                    float nd = dot3x(n.x, n.y, n.z, dx, dy, dz);
-                    g = nd > 0.0f ? fd(nd, fm(d2, fsq(d2))) : 0.0f;
-                } else {
-                    float ndD = dot3x(n.x, n.y, n.z, -Li.v[0], -Li.v[1], -Li.v[2]);
-                    float l2 = dot3x(Li.v[0], Li.v[1], Li.v[2], Li.v[0], Li.v[1], Li.v[2]);
-                    g = fd(ndD, fsq(l2));
-                }
-                E0 = fa(E0, fm(Li.rgb[0], g));
-                E1 = fa(E1, fm(Li.rgb[1], g));
-                E2 = fa(E2, fm(Li.rgb[2], g));
-            }
-            const float a0 = __ldg(S.albedo + 3 * (size_t)tri), a1 = __ldg(S.albedo + 3 * (size_t)tri + 1),
-                        a2 = __ldg(S.albedo + 3 * (size_t)tri + 2);
-            float r0 = fm(fm(a0, kInvPi), E0), r1 = fm(fm(a1, kInvPi), E1), r2 = fm(fm(a2, kInvPi), E2);
-            lo = fa(fa(fm(kLumR, r0), fm(kLumG, r1)), fm(kLumB, r2));
-            if (bounce) {
-                float3 Q = query_irr_hit(V, irr, dep, o, t, d, n);
-                r0 += a0 * Q.x;
-                r1 += a1 * Q.y;
-                r2 += a2 * Q.z;
-            }
-            out = make_float4(r0, r1, r2, depth);
-        }
-    }
-    rec[slot] = out;
-    if (lum) lum[slot] = lo;
+    shade_finish_body<false>(V, FD, S, Rs, hit, vis, irr, dep, rec, lum, blockIdx.x);
 }
 
 }  // namespace

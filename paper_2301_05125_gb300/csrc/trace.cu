@@ -6,41 +6,11 @@
 // warp shares an origin and sweeps a spiral of nearby directions.
 #include "adgi_internal.cuh"
 #include "kernels.cuh"
+#include "wave.cuh"
 
 namespace adgi {
 
 namespace {
-
-// probe owning main ray r: the last p with off[p] <= r, searched in [lo, hi]
-__device__ __forceinline__ int probe_of_ray(const uint32_t* __restrict__ off, uint32_t r, int lo, int hi)
-{
-    while (lo < hi) {
-        int mid = (lo + hi + 1) >> 1;
-        if (__ldg(off + mid) <= r)
-            lo = mid;
-        else
-            hi = mid - 1;
-    }
-    return lo;
-}
-
-// per block: bounds of the probe range of this block's rays, in shared memory
-__device__ __forceinline__ void block_probe_range(const uint32_t* __restrict__ off, int P, uint32_t r0, uint32_t r1,
-                                                  int* s_lo, int* s_hi)
-{
-    if (threadIdx.x == 0) *s_lo = probe_of_ray(off, r0, 0, P - 1);
-    if (threadIdx.x == 32 % blockDim.x) *s_hi = probe_of_ray(off, r1, 0, P - 1);
-    __syncthreads();
-}
-
-// direction at position k of the SF row of m points, and its SF index *i
-__device__ __forceinline__ float3 main_dir(const FrameConst& F, const float4* __restrict__ sf, uint32_t m, uint32_t k,
-                                           uint32_t* i)
-{
-    float4 s = __ldg(sf + (size_t)m * (m - 1) / 2 + k);
-    *i = (uint32_t)__float_as_int(s.w);
-    return rotate(F.R, s);
-}
 
 __global__ void k_set_frame(FrameDev* __restrict__ dst, const __grid_constant__ FrameDev src)
 {
@@ -52,63 +22,14 @@ __global__ void k_set_frame(FrameDev* __restrict__ dst, const __grid_constant__ 
 __global__ void __launch_bounds__(256, 4) k_pilot_trace(VolConst V, const FrameDev* __restrict__ FD, SceneDev S,
                                                      int2* __restrict__ hit)
 {
-    const FrameConst& F = FD->F;
-    // A warp traces one octant of 32 consecutive probes (the stratified
-    // directions of one octant, from neighbouring origins), not 8 octants of
-    // 4 probes.  Thread j of the launch: group g = j / 256 of 32 probes,
-    // octant (j / 32) % 8, probe 32 g + j % 32; results stay at 8 p + o.
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    const int p = V.p_lo + ((j >> 8) << 5) + (j & 31), o = (j >> 5) & 7;
-    if (p >= V.p_hi) return;
-    const int i = p * kPilots + o;
-    if (V.cls[p] == 0) {  // outside V_out: no pilot rays
-        hit[i] = make_int2((int)kMiss, 0x7F800000);
-        return;
-    }
-    float3 org = probe_pos(V, p);
-    float3 d = pilot_dir(F.pilot_key, (uint32_t)p, o);
-    float t;
-    uint32_t h;
-    trace_closest(S, org, d, V.tmin, __int_as_float(0x7F800000), t, h);
-    hit[i] = make_int2((int)h, __float_as_int(t));
+    pilot_trace_body(V, FD, S, hit, blockIdx.x);
 }
 
-// Thread r takes row position r - off[p] of probe p, whose SF index i names
-// the slot off[p] + i of the result: the threads of a warp trace nearby
-// directions (the rows are in a spatial order).
 __global__ void __launch_bounds__(256, 4) k_main_trace(VolConst V, const FrameDev* __restrict__ FD, SceneDev S,
                                                     const uint32_t* __restrict__ off, const float4* __restrict__ sf,
                                                     uint32_t R, int2* __restrict__ hit)
 {
-    const FrameConst& F = FD->F;
-    __shared__ int s_lo, s_hi;
-    // the rays of probes [p_lo, p_hi): [off[p_lo], off[p_hi]) (all probes:
-    // [0, off[P]); with clip volumes part of the budget may stay unspent)
-    const uint32_t rb = __ldg(off + V.p_lo), re = min(__ldg(off + V.p_hi), R);
-    uint32_t r0 = rb + blockIdx.x * blockDim.x;
-    if (r0 >= re) return;  // the whole block
-    uint32_t r1 = min(re - 1, r0 + blockDim.x - 1);
-    block_probe_range(off, V.P, r0, r1, &s_lo, &s_hi);
-    uint32_t r = r0 + threadIdx.x;
-    if (r >= re) return;
-    int p = probe_of_ray(off, r, s_lo, s_hi);
-    uint32_t base = __ldg(off + p);
-    uint32_t m = __ldg(off + p + 1) - base;
-    if (m > (uint32_t)(V.rays_max - kPilots) || r - base >= m) {
-        atomicOr(V.err, kErrRayRange);
-        return;
-    }
-    float3 org = probe_pos(V, p);
-    uint32_t i;
-    float3 d = main_dir(F, sf, m, r - base, &i);
-    if (i >= m) {
-        atomicOr(V.err, kErrRayRange);
-        return;
-    }
-    float t;
-    uint32_t h;
-    trace_closest(S, org, d, V.tmin, __int_as_float(0x7F800000), t, h);
-    hit[base + i] = make_int2((int)h, __float_as_int(t));
+    main_trace_body<false>(V, FD, S, off, sf, R, hit, blockIdx.x);
 }
 
 // Metropolis samples, in grouped order: thread r < n traces sample r along +w
