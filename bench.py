@@ -63,12 +63,12 @@ def _peaks():
 # shared headers): a committed ncu figure is used only while they are unchanged
 # (a traversal's traffic also depends on the trees the builders make)
 KERNEL_SOURCES = {
-    "k_main_trace": ["trace.cu", "wave.cuh", "bvh.cu", "wide.cu"],
-    "k_pilot_trace": ["trace.cu", "wave.cuh", "bvh.cu", "wide.cu"],
-    "k_shadow": ["shade.cu", "wave.cuh", "bvh.cu", "wide.cu"], "k_shade_finish": ["shade.cu", "wave.cuh"],
+    "k_main_trace": ["trace.cu", "wave.cuh", "bvh.cu", "bvhbody.cuh", "wide.cu"],
+    "k_pilot_trace": ["trace.cu", "wave.cuh", "bvh.cu", "bvhbody.cuh", "wide.cu"],
+    "k_shadow": ["shade.cu", "wave.cuh", "bvh.cu", "bvhbody.cuh", "wide.cu"], "k_shade_finish": ["shade.cu", "wave.cuh"],
     "k_blend": ["update.cu", "phase.cuh"], "k_blend_plan": ["update.cu", "phase.cuh"],
-    "k_mh_trace": ["trace.cu", "wave.cuh", "bvh.cu", "wide.cu"], "k_mh_blend": ["update.cu", "phase.cuh"],
-    "k_tick": ["tick.cu", "wave.cuh", "phase.cuh", "bvh.cu", "wide.cu"],
+    "k_mh_trace": ["trace.cu", "wave.cuh", "bvh.cu", "bvhbody.cuh", "wide.cu"], "k_mh_blend": ["update.cu", "phase.cuh"],
+    "k_tick": ["tick.cu", "wave.cuh", "phase.cuh", "bvh.cu", "bvhbody.cuh", "wide.cu"],
 }
 
 
@@ -371,6 +371,8 @@ def _batched_section(args, adgi, torch, dev):
             if B.sync() != 0:
                 raise RuntimeError("persistent tick: " + adgi.adgi_last_error())
             info = B.info()
+            # the last tick's timeline: completion of each grid barrier (ms from the start)
+            info["barrier_ms"] = [round(x / 1e6, 4) for x in B.phase_ns(64) if x]
         if B is not None:
             B.close()
         for v in vols:

@@ -275,6 +275,11 @@ int adgi_tick_set_wait(adgi_tick tick, uint64_t limit_ns, int32_t stall_barrier)
 /* The persistent grid (blocks), its dynamic shared memory per block and the
  * allocation chunks of the last tick (0 before the first). */
 int adgi_tick_info(adgi_tick tick, uint32_t* grid_blocks, uint32_t* smem_bytes, uint32_t* chunks);
+/* Timeline of the last tick: out[i] = ns from the start of block 0 to the
+ * completion of grid barrier i (0 for barriers not reached or beyond 64).
+ * Barriers 0-6 end the phases before the allocation, then the allocation's
+ * own barriers, then one per remaining phase.  Synchronises cuda_stream. */
+int adgi_tick_phase_ns(adgi_tick tick, uint64_t* out, int32_t n);
 int adgi_tick_destroy(adgi_tick tick);
 
 /* Block shapes of a volume's kernels.  adgi_autotune times candidate shapes

@@ -114,7 +114,7 @@ EXPORTED = ["adgi_create_volume", "adgi_set_scene", "adgi_move_vertices", "adgi_
             "adgi_server_drain", "adgi_server_volume", "adgi_server_remove_volume", "adgi_server_info",
             "adgi_server_destroy", "adgi_update_slab", "adgi_slab_copy", "adgi_slab_bytes", "adgi_inject_alloc_failure",
             "adgi_tick_create", "adgi_tick_update", "adgi_tick_sync", "adgi_tick_set_wait", "adgi_tick_info",
-            "adgi_tick_destroy", "adgi_last_error"]
+            "adgi_tick_phase_ns", "adgi_tick_destroy", "adgi_last_error"]
 
 BVH_NOALLOC_MAX_TRIS = 32768
 
@@ -156,6 +156,7 @@ def load(path: str = LIB_PATH):
     L.adgi_tick_sync.argtypes = [vp]
     L.adgi_tick_set_wait.argtypes = [vp, u64, i32]
     L.adgi_tick_info.argtypes = [vp, C.POINTER(C.c_uint32), C.POINTER(C.c_uint32), C.POINTER(C.c_uint32)]
+    L.adgi_tick_phase_ns.argtypes = [vp, C.POINTER(C.c_uint64), i32]
     L.adgi_tick_destroy.argtypes = [vp]
     L.adgi_autotune.argtypes = [vp, C.POINTER(adgi_frame), i32, C.POINTER(adgi_tuning)]
     L.adgi_set_tuning.argtypes = [vp, C.POINTER(adgi_tuning)]
@@ -351,6 +352,12 @@ def adgi_tick_info(tick):
     g, sm, ch = C.c_uint32(), C.c_uint32(), C.c_uint32()
     _check(load().adgi_tick_info(tick, C.byref(g), C.byref(sm), C.byref(ch)))
     return {"grid_blocks": g.value, "smem_bytes": sm.value, "chunks": ch.value}
+
+
+def adgi_tick_phase_ns(tick, n=64):
+    out = (C.c_uint64 * n)()
+    _check(load().adgi_tick_phase_ns(tick, out, n))
+    return [int(x) for x in out]
 
 
 def adgi_tick_destroy(tick):
@@ -789,6 +796,10 @@ class Tick:
 
     def info(self):
         return adgi_tick_info(self.h)
+
+    def phase_ns(self, n=64):
+        """ns from the tick's start to the completion of each grid barrier (last tick)"""
+        return adgi_tick_phase_ns(self.h, n)
 
     def close(self):
         if self.h:

@@ -15,7 +15,7 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libadgi.so")
 SOURCES = ["capi.cu", "bvh.cu", "wide.cu", "trace.cu", "shade.cu", "update.cu", "tick.cu", "sampler.cu", "noalloc.cu",
            "server.cu"]
-HEADERS = ["adgi_internal.cuh", "bvh.cuh", "kernels.cuh", "wave.cuh", "phase.cuh"]
+HEADERS = ["adgi_internal.cuh", "bvh.cuh", "kernels.cuh", "wave.cuh", "phase.cuh", "bvhbody.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-ffp-contract=off", "--expt-relaxed-constexpr"]
 

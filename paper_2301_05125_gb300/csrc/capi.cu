@@ -1469,6 +1469,10 @@ struct adgi_tick_s {
     std::vector<cudaEvent_t> vol_ev;  // each volume's stream, joined before a tick
     cudaEvent_t done = nullptr;       // the last tick has read the staged frames
     FrameDev* h_fd = nullptr;         // pinned staging of the frame descriptors
+    int* h_rb = nullptr;              // pinned staging: moving parts rebuilt inside the tick
+    int* d_rb = nullptr;
+    unsigned char* d_sort = nullptr;  // [n][kTickRebuildMax x 12 B] the moving parts' Morton sorts
+    uint32_t* d_chunk = nullptr;      // the volumes' chunk_p arrays, one after the other
     TickCtl* d_ctl = nullptr;
     TickVol* d_vols = nullptr;
     uint32_t* d_pre = nullptr;
@@ -1500,7 +1504,11 @@ void free_tick(adgi_tick t)
     if (!t) return;
     free_tick_tables(t);
     cudaFree(t->d_ctl);
+    cudaFree(t->d_rb);
+    cudaFree(t->d_sort);
+    cudaFree(t->d_chunk);
     if (t->h_fd) cudaFreeHost(t->h_fd);
+    if (t->h_rb) cudaFreeHost(t->h_rb);
     for (cudaEvent_t e : t->vol_ev)
         if (e) cudaEventDestroy(e);
     if (t->done) cudaEventDestroy(t->done);
@@ -1512,23 +1520,24 @@ TickVol tick_vol_of(adgi_tick t, int i)
     adgi_volume v = t->vols[i];
     TickVol T;
     std::memset(&T, 0, sizeof(T));
-    T.V = v->V;
-    T.V.p_lo = 0;
-    T.V.p_hi = v->V.P;
-    T.S = scene_view(v);
-    T.FD = v->fdev;
+    T.w.V = v->V;
+    T.w.V.p_lo = 0;
+    T.w.V.p_hi = v->V.P;
+    T.w.S = scene_view(v);
+    T.w.FD = v->fdev;
+    T.w.off = v->off;
+    T.w.sf = v->sf;
+    T.w.pil_hit = v->pil_hit;
+    T.w.m_hit = v->m_hit;
+    T.w.Wk = ShadeWork{v->vis, v->jobs, v->job_light, v->job_count,
+                       (unsigned)std::min<size_t>(v->job_cap, 0xFFFFFFFFu), 0u, v->shadow_ctr};
     T.lut_c = v->lut_c;
     T.cls = v->cls;
-    T.sf = v->sf;
-    T.pil_hit = v->pil_hit;
     T.pil_rec = v->pil_rec;
     T.pil_lum = v->pil_lum;
-    T.m_hit = v->m_hit;
     T.m_rec = v->m_rec;
     T.n = v->n;
     T.off = v->off;
-    T.Wk = ShadeWork{v->vis, v->jobs, v->job_light, v->job_count,
-                     (unsigned)std::min<size_t>(v->job_cap, 0xFFFFFFFFu), 0u, v->shadow_ctr};
     T.C = ChangeBufs{v->pil_hit, v->pil_lum, v->lut_v, v->lut_c, v->qv,  v->qr,  v->qv_even, v->qr_even,
                      v->amp_v,   v->amp_r,   v->age_v, v->age_r, v->trv, v->trr, v->G,       v->W, v->qd, v->vout_even};
     T.B = BlendBufs{v->off, v->sf,  v->pil_rec, v->m_rec,
@@ -1537,6 +1546,24 @@ TickVol tick_vol_of(adgi_tick t, int i)
     T.avg = v->V.rays_avg;
     T.m0 = v->V.m0;
     T.rmax = v->V.rays_max;
+    T.verts = v->verts;
+    T.idx = v->idx;
+    T.dlist = v->dlist;
+    T.nv = v->nv;
+    T.nd = v->nd;
+    T.node_off = moving_node_off(v);
+    T.tri_off = moving_tri_off(v);
+    T.eps = v->eps;
+    T.tri_orig = v->tri_orig;
+    T.tri_in = v->dbvh.bufs.tri_in;
+    T.keys = v->dbvh.bufs.keys[0];
+    T.vals = v->dbvh.bufs.vals[0];
+    T.par_int = v->dbvh.bufs.par_int;
+    T.par_leaf = v->dbvh.bufs.par_leaf;
+    T.flags = v->dbvh.bufs.flags;
+    T.w.chunk_p = nullptr;  // set by build_tick_tables
+    T.sort_k = reinterpret_cast<uint64_t*>(t->d_sort + (size_t)12 * kTickRebuildMax * i);
+    T.sort_v = reinterpret_cast<uint32_t*>(T.sort_k + kTickRebuildMax);
     return T;
 }
 
@@ -1553,7 +1580,7 @@ int build_tick_tables(adgi_tick t, std::vector<TickVol>& hv)
     for (int i = 0; i < n; ++i) {
         adgi_volume v = t->vols[i];
         uint32_t cnt[kTickPhases];
-        tick_phase_blocks(v->V, v->R_main, cnt);
+        tick_phase_blocks(v->V, v->R_main, v->nd, cnt);
         for (int ph = 0; ph < kTickPhases; ++ph) {
             const uint64_t x = (uint64_t)pre[(size_t)ph * (n + 1) + i] + cnt[ph];
             if (x > 0x7FFFFFFFull) return fail(ADGI_ERR_INVALID_ARG, "tick: too much work for one launch");
@@ -1562,6 +1589,20 @@ int build_tick_tables(adgi_tick t, std::vector<TickVol>& hv)
         hv[i].chunk0 = (int)cvol.size();
         for (int c = 0; c < (v->V.P + kTickChunk - 1) / kTickChunk; ++c) cvol.push_back(i);
         smem = std::max(smem, tick_smem_bytes(v->V));
+    }
+    // the chunk-to-probe arrays (R_main / 32 + 2 entries a volume)
+    {
+        size_t total = 0;
+        std::vector<size_t> at(n);
+        for (int i = 0; i < n; ++i) {
+            at[i] = total;
+            total += (size_t)t->vols[i]->R_main / 32 + 2;
+        }
+        cudaFree(t->d_chunk);
+        t->d_chunk = nullptr;
+        size_t b = 0;
+        if (dalloc(&t->d_chunk, total, &b) != cudaSuccess) return fail(ADGI_ERR_OOM, "tick chunk table");
+        for (int i = 0; i < n; ++i) hv[i].w.chunk_p = t->d_chunk + at[i];
     }
     const unsigned grid = tick_grid_blocks(smem);
     if (grid == 0) return fail(ADGI_ERR_CUDA, "tick: no resident grid for the persistent kernel");
@@ -1604,6 +1645,9 @@ int adgi_tick_create(const adgi_volume* vols, int32_t n, void* cuda_stream, adgi
     cudaError_t e = cudaEventCreateWithFlags(&t->done, cudaEventDisableTiming);
     for (int i = 0; i < n && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&t->vol_ev[i], cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMallocHost((void**)&t->h_fd, sizeof(FrameDev) * n);
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&t->h_rb, sizeof(int) * n);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&t->d_rb, sizeof(int) * n);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&t->d_sort, (size_t)12 * kTickRebuildMax * n);
     if (e == cudaSuccess) e = cudaMalloc((void**)&t->d_ctl, sizeof(TickCtl));
     if (e == cudaSuccess) {
         TickCtl c;
@@ -1638,13 +1682,22 @@ int adgi_tick_update(adgi_tick t, const adgi_frame* frames)
         CK(cudaEventRecord(t->vol_ev[i], t->vols[i]->stream));
         CK(cudaStreamWaitEvent(t->stream, t->vol_ev[i], 0));
     }
-    // moving parts: refreshed and rebuilt before the launch
+    // moving parts whose vertices moved: rebuilt inside the launch (up to
+    // kTickRebuildMax triangles), else before it
+    if (t->launched) CK(cudaEventSynchronize(t->done));  // the staging buffers are rewritten below
+    int any_rb = 0;
     for (int i = 0; i < n; ++i) {
         adgi_volume v = t->vols[i];
+        t->h_rb[i] = 0;
         if (v->nd > 0 && v->dyn_dirty) {
-            CK(fill_tri_orig(v->verts, v->idx, v->dlist, v->nv, v->nd, v->tri_orig, t->stream));
-            int rc = build_moving(v, t->stream);
-            if (rc) return rc;
+            if (v->nd <= kTickRebuildMax) {
+                t->h_rb[i] = 1;
+                any_rb = 1;
+            } else {
+                CK(fill_tri_orig(v->verts, v->idx, v->dlist, v->nv, v->nd, v->tri_orig, t->stream));
+                int rc = build_moving(v, t->stream);
+                if (rc) return rc;
+            }
             v->dyn_dirty = false;
         }
     }
@@ -1654,13 +1707,13 @@ int adgi_tick_update(adgi_tick t, const adgi_frame* frames)
         int rc = build_tick_tables(t, hv);
         if (rc) return rc;
     }
-    // the staging buffer is rewritten once the previous tick has copied it
-    if (t->launched) CK(cudaEventSynchronize(t->done));
     std::memcpy(t->h_fd, fd.data(), sizeof(FrameDev) * n);
+    CK(cudaMemcpyAsync(t->d_rb, t->h_rb, sizeof(int) * n, cudaMemcpyHostToDevice, t->stream));
     for (int i = 0; i < n; ++i)  // each volume's own descriptor, as the plain update leaves it
         CK(cudaMemcpyAsync(t->vols[i]->fdev, t->h_fd + i, sizeof(FrameDev), cudaMemcpyHostToDevice, t->stream));
     CK(cudaMemsetAsync(t->d_ctl, 0, offsetof(TickCtl, limit_ns), t->stream));
-    CK(launch_tick(t->d_vols, n, t->d_pre, t->d_cvol, t->n_chunks, t->d_scr, t->d_ctl, t->grid, t->smem, t->stream));
+    CK(launch_tick(t->d_vols, n, t->d_pre, t->d_cvol, t->n_chunks, t->d_scr, t->d_ctl, t->d_rb, any_rb, t->grid,
+                   t->smem, t->stream));
     CK(cudaEventRecord(t->done, t->stream));
     t->launched = true;
     for (int i = 0; i < n; ++i) finish_update(t->vols[i], fd[i], &frames[i]);
@@ -1696,6 +1749,16 @@ int adgi_tick_info(adgi_tick t, uint32_t* grid_blocks, uint32_t* smem_bytes, uin
     if (grid_blocks) *grid_blocks = t->grid;
     if (smem_bytes) *smem_bytes = (uint32_t)t->smem;
     if (chunks) *chunks = (uint32_t)t->n_chunks;
+    return ADGI_OK;
+}
+
+int adgi_tick_phase_ns(adgi_tick t, uint64_t* out, int32_t n)
+{
+    if (!t || !out || n < 0) return fail(ADGI_ERR_INVALID_ARG, "bad tick phase arguments");
+    CK(cudaStreamSynchronize(t->stream));
+    unsigned long long st[1 + kTickStamps];
+    CK(cudaMemcpy(st, &t->d_ctl->t_start, sizeof(st), cudaMemcpyDeviceToHost));
+    for (int i = 0; i < n; ++i) out[i] = i < kTickStamps && st[i + 1] >= st[0] ? st[i + 1] - st[0] : 0;
     return ADGI_OK;
 }
 

@@ -221,36 +221,65 @@ cudaError_t launch_query(const VolConst& V, const void* irr, const void* dep, co
 
 // ---- the batched update as one persistent launch per tick (tick.cu)
 
-// One volume of a tick: what the update's ordinary kernels take as
-// parameters, kept in device memory for the persistent kernel.
-struct TickVol {
+// The part of a tick's volume that the ray phases (traces, shadow rays)
+// read; each warp keeps its own copy in shared memory (tick.cu).
+struct TickWave {
     VolConst V;
     SceneDev S;
     const FrameDev* FD;
-    const uint16_t* lut_c;
-    uint8_t* cls;             // [P] clip classes (written by the first phase)
+    const uint32_t* off;      // [P+1] adaptive-ray offsets
     const float4* sf;         // SF table
     int2* pil_hit;
+    int2* m_hit;
+    ShadeWork Wk;
+    uint32_t* chunk_p;        // [R_main/32 + 1] the probe of each 32-ray chunk's first ray (allocation)
+};
+
+// One volume of a tick: what the update's ordinary kernels take as
+// parameters, kept in device memory for the persistent kernel.
+struct TickVol {
+    TickWave w;
+    const uint16_t* lut_c;
+    uint8_t* cls;             // [P] clip classes (written by the first phase)
     float4* pil_rec;
     float* pil_lum;
-    int2* m_hit;
     float4* m_rec;
     uint32_t* n;              // [P] rays per probe (the allocation's output)
-    uint32_t* off;            // [P+1] adaptive-ray offsets
-    ShadeWork Wk;
+    uint32_t* off;            // [P+1] adaptive-ray offsets (writable)
     ChangeBufs C;
     BlendBufs B;
     int avg, m0, rmax;        // the allocation's budget, floor and cap
     int chunk0;               // first allocation chunk of this volume
+    // the moving part (nd <= kTickRebuildMax triangles), rebuilt inside the
+    // tick when its vertices moved: inputs, the build's scratch, and its
+    // place in the scene's arrays
+    const float* verts;
+    const int* idx;
+    const int* dlist;         // [nd] the moving triangles
+    int nv, nd;
+    int node_off, tri_off;    // the moving part's first node and triangle slot
+    float eps;
+    float4* tri_orig;
+    float4* tri_in;
+    uint64_t* keys;
+    uint32_t* vals;
+    int* par_int;
+    int* par_leaf;
+    int* flags;
+    uint64_t* sort_k;         // [kTickRebuildMax] the Morton sort's keys and values (global
+    uint32_t* sort_v;         // memory: shared memory stays with the L1 cache the traversals use)
 };
 
 constexpr int kTickThreads = 256;  // threads per block of the persistent kernel
 constexpr int kTickChunk = 2048;   // probes per allocation chunk (8 per thread)
 constexpr int kTickOwn = 8;        // allocation chunks one block owns at most
 constexpr int kTickPasses = 64;    // proportional allocation passes at most
-constexpr int kTickPhases = 13;    // phases of a tick (grid barriers between them)
+constexpr int kTickPhases = 15;    // phases of a tick (grid barriers between them)
+constexpr int kTickRebuildMax = 2048;  // moving parts up to this size are rebuilt inside the tick
+constexpr int kTickBlendWarps = 4;     // probe tiles a block blends at once (shared memory: 4 x 3.5 KB)
 constexpr int kTickScratch = 9;    // 64-bit allocation partial sums per chunk
 constexpr int kTickTimedOut = 1;   // TickCtl::status: a barrier wait gave up
+constexpr int kTickStamps = 64;    // barrier completion times kept per tick
 
 // Control block of a tick (device memory).  The part up to `limit_ns` is
 // cleared before every launch; the wait limit and the test hook stay.
@@ -260,18 +289,23 @@ struct TickCtl {
     int status;                     // 0, or kTickTimedOut
     unsigned pass_flag[kTickPasses];  // a chunk took part in allocation pass i
     unsigned rem_flag[2];           // a chunk took part in remainder round j (j mod 2)
+    unsigned long long t_start;     // %globaltimer at the start of block 0
+    unsigned long long t_bar[kTickStamps];  // %globaltimer when barrier i completed (the first kTickStamps)
     unsigned long long limit_ns;    // a barrier wait gives up after this long
     int stall;                      // test hook: barrier that never completes (-1: none)
 };
 
 // Per-volume virtual-block counts of each phase (prefix sums, host side):
 // pre[ph * (nv + 1) + i] = the first virtual block of volume i in phase ph.
-void tick_phase_blocks(const VolConst& V, uint32_t R_main, uint32_t counts[kTickPhases]);
+void tick_phase_blocks(const VolConst& V, uint32_t R_main, int nd, uint32_t counts[kTickPhases]);
 // dynamic shared memory of the persistent kernel for a volume
 size_t tick_smem_bytes(const VolConst& V);
 // blocks of the persistent grid (all resident at once) for that shared memory, 0 on error
 unsigned tick_grid_blocks(size_t smem);
+// rebuild: [nv] 1 where the volume's moving part is rebuilt in this tick;
+// any_rebuild: some entry is 1 (else the rebuild phases are skipped)
 cudaError_t launch_tick(const TickVol* vols, int nv, const uint32_t* pre, const int* cvol, int n_chunks,
-                        unsigned long long* scratch, TickCtl* ctl, unsigned grid, size_t smem, cudaStream_t s);
+                        unsigned long long* scratch, TickCtl* ctl, const int* rebuild, int any_rebuild, unsigned grid,
+                        size_t smem, cudaStream_t s);
 
 }  // namespace adgi

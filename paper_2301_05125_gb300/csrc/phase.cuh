@@ -630,13 +630,15 @@ __device__ __forceinline__ void store_tiles(const VolConst& V, const FrameConst&
 }
 
 template <bool kLive>
-__device__ __forceinline__ void blend_body(const VolConst& V, const FrameDev* FD, const BlendBufs& B, unsigned bx)
+// bx: the item of wpb probe tiles (one warp each) that this block works on
+__device__ __forceinline__ void blend_body(const VolConst& V, const FrameDev* FD, const BlendBufs& B, unsigned bx,
+                                           int wpb)
 {
     const FrameConst& F = FD->F;
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int p = V.p_lo + bx * (blockDim.x >> 5) + wib;
-    if (p >= V.p_hi) return;  // the whole warp
+    const int p = V.p_lo + bx * wpb + wib;
+    if (wib >= wpb || p >= V.p_hi) return;  // the whole warp
     const uint32_t base = ldl<kLive>(B.off + p);
     uint32_t m = ldl<kLive>(B.off + p + 1) - base;
     if (m > (uint32_t)(V.rays_max - kPilots) || base > V.R_main || m > V.R_main - base) {

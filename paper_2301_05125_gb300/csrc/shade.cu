@@ -33,7 +33,9 @@ __global__ void __launch_bounds__(128, 7) k_shadow(const FrameDev* __restrict__ 
                                                 const unsigned* __restrict__ job_count, unsigned job_cap,
                                                 unsigned long long* __restrict__ vis, unsigned long long* shadow_ctr)
 {
-    shadow_body(FD, S, jobs, job_light, job_count, job_cap, vis, shadow_ctr, blockIdx.x, gridDim.x);
+    shadow_body(FD, S, jobs, job_light, job_count, job_cap, vis, shadow_ctr,
+                blockIdx.x * blockDim.x + (threadIdx.x & ~31u), gridDim.x * blockDim.x,
+                blockIdx.x == 0 && threadIdx.x == 0);
 }
 
 __global__ void __launch_bounds__(256, 4) k_shade_finish(VolConst V, const FrameDev* __restrict__ FD, SceneDev S,

@@ -20,6 +20,7 @@
 // Nothing waits without a limit, so a tick whose grid is not fully resident
 // fails instead of hanging.
 #include "adgi_internal.cuh"
+#include "bvhbody.cuh"
 #include "kernels.cuh"
 #include "phase.cuh"
 #include "wave.cuh"
@@ -29,7 +30,9 @@ namespace adgi {
 namespace {
 
 enum TickPhase {
-    kPhClassify = 0,  // clip classes + this frame's blend plan
+    kPhClassify = 0,  // clip classes + this frame's blend plan (+ moving parts: triangles, Morton order)
+    kPhHierarchy,     // moving parts: radix tree
+    kPhBounds,        // moving parts: boxes, bottom up
     kPhPilot,         // pilot rays
     kPhPilotPrep,     // their shading: shadow jobs
     kPhPilotShadow,   // shadow rays
@@ -44,6 +47,7 @@ enum TickPhase {
     kPhBlend,         // atlases
 };
 static_assert(kPhBlend + 1 == kTickPhases, "phase count");
+static_assert(kTickRebuildMax == kSmallBuild, "a rebuilt moving part is sorted in one block");
 
 // allocation partial sums per chunk (scratch rows of n_chunks entries)
 enum TickRow { kRowPin = 0, kRowS, kRowG0, kRowG1, kRowSu0, kRowSu1, kRowCa, kRowCe, kRowLoc };
@@ -85,6 +89,7 @@ __device__ bool grid_sync(TickCtl* C, int idx)
         // the test hook: at barrier `stall` no block arrives, so it never completes
         const unsigned arrived = C->stall == idx ? 0u : atomicAdd(&C->bar_count, 1u) + 1u;
         if (arrived == gridDim.x) {
+            if (idx < kTickStamps) C->t_bar[idx] = global_ns();
             C->bar_count = 0u;
             st_release(&C->bar_gen, gen + 1u);
         } else {
@@ -124,10 +129,12 @@ __device__ __forceinline__ int volume_of(const uint32_t* row, int nv, uint32_t v
 }
 
 // Make volume i the block's current one (its parameters in shared memory).
-// Called by every thread of the block with the same i.
+// Called by every thread of the block with the same i.  The copy waits for
+// every thread first: one may still be reading the previous volume's.
 __device__ __forceinline__ void use_volume(const TickVol* __restrict__ vols, int i, TickVol& tv, int& cur)
 {
     if (cur == i) return;
+    __syncthreads();
     static_assert(sizeof(TickVol) % 8 == 0, "copied as 64-bit words");
     const unsigned long long* src = reinterpret_cast<const unsigned long long*>(vols + i);
     unsigned long long* dst = reinterpret_cast<unsigned long long*>(&tv);
@@ -135,6 +142,24 @@ __device__ __forceinline__ void use_volume(const TickVol* __restrict__ vols, int
     __syncthreads();
     if (threadIdx.x == 0) cur = i;
     __syncthreads();
+}
+
+// Make volume i the warp's current one for the ray phases (its TickWave in
+// this warp's slot of shared memory).  Called by every lane of the warp.
+// The lanes of a warp leave a ray item at different times (independent
+// thread scheduling), so the copy waits for all of them first: a slow lane
+// may still be traversing with the previous volume's parameters.
+__device__ __forceinline__ void use_wave(const TickVol* __restrict__ vols, int i, TickWave& w, int& cur)
+{
+    if (cur == i) return;
+    __syncwarp();
+    static_assert(sizeof(TickWave) % 8 == 0, "copied as 64-bit words");
+    const unsigned long long* src = reinterpret_cast<const unsigned long long*>(&vols[i].w);
+    unsigned long long* dst = reinterpret_cast<unsigned long long*>(&w);
+    for (int k = threadIdx.x & 31; k < (int)(sizeof(TickWave) / 8); k += 32) dst[k] = __ldg(src + k);
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) cur = i;
+    __syncwarp();
 }
 
 // sums over chunks [cb, ce) of row a: the total and the part before chunk c
@@ -178,7 +203,7 @@ __device__ bool tick_allocate(const TickVol* __restrict__ vols, const int* __res
     auto chunk = [&](int k) { return (int)blockIdx.x + k * (int)gridDim.x; };
     // thread range [c0, c1) of chunk c of the current volume, and the volume's chunks [cb, ce)
     auto range = [&](int c, int& c0, int& c1, int& cb, int& ce) {
-        const int P = tv.V.P, lc = c - tv.chunk0;
+        const int P = tv.w.V.P, lc = c - tv.chunk0;
         c0 = min(P, lc * kTickChunk + (int)threadIdx.x * kPer);
         c1 = min(P, c0 + kPer);
         cb = tv.chunk0;
@@ -215,7 +240,7 @@ __device__ bool tick_allocate(const TickVol* __restrict__ vols, const int* __res
         uint64_t Pin, rank0, S, s_bef;
         chunk_sums(row[kRowPin], cb, ce, c, red, Pin, rank0);
         chunk_sums(row[kRowS], cb, ce, c, red, S, s_bef);
-        uint64_t E = (uint64_t)(tv.avg - 8) * (uint64_t)tv.V.P - (uint64_t)(tv.m0 - 8) * Pin;
+        uint64_t E = (uint64_t)(tv.avg - 8) * (uint64_t)tv.w.V.P - (uint64_t)(tv.m0 - 8) * Pin;
         if (E > Pin * cap) E = Pin * cap;
         if (S == 0) {
             const uint64_t q = Pin ? E / Pin : 0, r = Pin ? E % Pin : 0;
@@ -413,12 +438,13 @@ __device__ bool tick_allocate(const TickVol* __restrict__ vols, const int* __res
         uint64_t t2;
         uint64_t pre = bef + block_exscan(loc, red, &t2);
         for (int p = c0; p < c1; ++p) {
-            const uint32_t np = rays_of(p);
-            tv.off[p] = (uint32_t)pre;
-            pre += np > 8u ? np - 8u : 0u;
+            const uint32_t np = rays_of(p), a = (uint32_t)pre, e = a + (np > 8u ? np - 8u : 0u);
+            tv.off[p] = a;
+            for (uint32_t q = (a + 31u) / 32u; 32u * q < e; ++q) tv.w.chunk_p[q] = (uint32_t)p;  // chunks starting here
+            pre = e;
             tv.n[p] = np;
         }
-        if (threadIdx.x == 0 && c == ce - 1) tv.off[tv.V.P] = (uint32_t)tot;
+        if (threadIdx.x == 0 && c == ce - 1) tv.off[tv.w.V.P] = (uint32_t)tot;
         __syncthreads();
     }
     return true;
@@ -427,23 +453,61 @@ __device__ bool tick_allocate(const TickVol* __restrict__ vols, const int* __res
 __global__ void __launch_bounds__(kTickThreads, 4) k_tick(const TickVol* __restrict__ vols, int nv,
                                                        const uint32_t* __restrict__ pre,
                                                        const int* __restrict__ cvol, int n_chunks,
-                                                       unsigned long long* scr, TickCtl* C)
+                                                       unsigned long long* scr, TickCtl* C,
+                                                       const int* __restrict__ rebuild, int any_rebuild)
 {
     __shared__ __align__(16) TickVol tv;
     __shared__ int cur;
+    // the ray phases run per warp, with no block barrier between a warp's
+    // work items (a block would otherwise wait for its slowest warp's rays)
+    constexpr int kWarps = kTickThreads / 32;
+    __shared__ __align__(16) TickWave wv[kWarps];
+    __shared__ int wcur[kWarps];
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x < kWarps) wcur[threadIdx.x] = -1;
     if (threadIdx.x == 0) cur = -1;
+    if (blockIdx.x == 0 && threadIdx.x == 0) C->t_start = global_ns();
     __syncthreads();
     int bar = 0;
     for (int ph = 0; ph < kTickPhases; ++ph) {
+        if (!any_rebuild && (ph == kPhHierarchy || ph == kPhBounds)) continue;  // (and their barriers)
         if (ph == kPhPilotShadow || ph == kPhMainShadow) {
-            // every volume's shadow jobs in turn, the whole grid over each list
+            // every volume's shadow jobs in turn, all warps of the grid over
+            // each list; each list starts where the previous one ended (in
+            // rounds of 32 jobs, around the warps), so small lists do not all
+            // land on the first warps
+            const unsigned nw = gridDim.x * kWarps, gw = blockIdx.x * kWarps + wid;
+            unsigned rot = 0;
             for (int i = 0; i < nv; ++i) {
-                use_volume(vols, i, tv, cur);
-                const ShadeWork& W = tv.Wk;
-                shadow_body(tv.FD, tv.S, W.jobs, W.job_light, W.job_count, W.job_cap, W.vis, W.shadow_ctr,
-                            blockIdx.x, gridDim.x);
-                __syncthreads();
+                use_wave(vols, i, wv[wid], wcur[wid]);
+                const TickWave& T = wv[wid];
+                const unsigned total = min(*T.Wk.job_count, T.Wk.job_cap);
+                const unsigned me = (gw + nw - rot) % nw;
+                shadow_body(T.FD, T.S, T.Wk.jobs, T.Wk.job_light, T.Wk.job_count, T.Wk.job_cap, T.Wk.vis,
+                            T.Wk.shadow_ctr, 32u * me, 32u * nw, me == 0 && lane == 0);
+                rot = (rot + (total + 31u) / 32u) % nw;
+                __syncwarp();  // the lanes go on to the next list together
             }
+            __syncthreads();
+        } else if (ph == kPhPilot || ph == kPhMain) {
+            // warp items: 32 pilot rays of one octant, or 32 adaptive rays
+            const uint32_t* row = pre + (size_t)ph * (nv + 1);
+            const uint32_t total = row[nv], nw = gridDim.x * kWarps;
+            for (uint32_t vw = blockIdx.x * kWarps + wid; vw < total; vw += nw) {
+                const int i = volume_of(row, nv, vw);
+                use_wave(vols, i, wv[wid], wcur[wid]);
+                const TickWave& T = wv[wid];
+                const uint32_t lw = vw - row[i];
+                if (ph == kPhPilot)
+                    pilot_trace_body(T.V, T.FD, T.S, T.pil_hit, (int)(32u * lw) + lane);
+                else
+                    main_trace_warp_body<true>(T.V, T.FD, T.S, T.off, T.sf, T.V.R_main, T.m_hit, lw, T.chunk_p);
+                // The lanes leave an item at different times (independent
+                // thread scheduling); they start the next one together, since
+                // its warp shuffles and its parameter copy need all of them.
+                __syncwarp();
+            }
+            __syncthreads();
         } else if (ph == kPhAllocate) {
             if (!tick_allocate(vols, cvol, n_chunks, scr, C, bar, tv, cur)) return;
         } else {
@@ -453,54 +517,73 @@ __global__ void __launch_bounds__(kTickThreads, 4) k_tick(const TickVol* __restr
                 const int i = volume_of(row, nv, vb);
                 use_volume(vols, i, tv, cur);
                 const uint32_t lb = vb - row[i];
-                const VolConst& V = tv.V;
+                const VolConst& V = tv.w.V;
+                const bool rb = rebuild[i] != 0;
                 switch (ph) {
                 case kPhClassify: {
                     const uint32_t nc = ((uint32_t)V.P + kTickThreads - 1) / kTickThreads;
-                    if (lb < nc)
-                        classify_body(V, tv.FD, tv.lut_c, tv.cls, lb);
-                    else
-                        blend_plan_body(V, tv.FD, tv.sf, tv.B.plan, lb - nc);
+                    const uint32_t np = (uint32_t)max(V.rays_max - kPilots, 0);
+                    const uint32_t nf = tv.nd > 0 && tv.nd <= kTickRebuildMax
+                                            ? ((uint32_t)tv.nd + kTickThreads - 1) / kTickThreads : 0u;
+                    if (lb < nc) {
+                        classify_body(V, tv.w.FD, tv.lut_c, tv.cls, lb);
+                    } else if (lb < nc + np) {
+                        blend_plan_body(V, tv.w.FD, tv.w.sf, tv.B.plan, lb - nc);
+                    } else if (lb < nc + np + nf) {  // the moving triangles in original order (shading)
+                        if (rb)
+                            fill_orig_body(tv.verts, tv.idx, tv.dlist, tv.nd, tv.nv, tv.tri_orig,
+                                           (int)(lb - nc - np) * kTickThreads + (int)threadIdx.x);
+                    } else if (rb) {  // the moving part's Morton order, sorted by this block (in global memory)
+                        morton_small_body(tv.verts, tv.idx, tv.dlist, tv.nd, tv.nv, tv.tri_in, tv.keys, tv.vals,
+                                          const_cast<float4*>(tv.w.S.tri_v) + 3 * (size_t)tv.tri_off, tv.w.S.err,
+                                          tv.sort_k, tv.sort_v);
+                        for (int k = threadIdx.x; k < tv.nd; k += blockDim.x) tv.flags[k] = 0;
+                    }
                     break;
                 }
-                case kPhPilot:
-                    pilot_trace_body(V, tv.FD, tv.S, tv.pil_hit, lb);
+                case kPhHierarchy:
+                    if (rb)
+                        hierarchy_body(tv.keys, tv.nd, const_cast<BNode*>(tv.w.S.nodes) + tv.node_off, tv.par_int,
+                                       tv.par_leaf, (int)lb * kTickThreads + (int)threadIdx.x, tv.node_off, tv.tri_off);
+                    break;
+                case kPhBounds:
+                    if (rb)
+                        bounds_body(tv.w.S.tri_v + 3 * (size_t)tv.tri_off, tv.nd, const_cast<BNode*>(tv.w.S.nodes) + tv.node_off,
+                                    tv.par_int, tv.par_leaf, tv.flags, tv.eps, tv.w.S.err,
+                                    (int)lb * kTickThreads + (int)threadIdx.x, tv.node_off, tv.tri_off);
                     break;
                 case kPhPilotPrep: {
                     const RaySet Rs{0, (uint32_t)V.P * kPilots, nullptr, nullptr, DynRays{}};
-                    shade_prep_body<true>(V, tv.FD, tv.S, Rs, tv.pil_hit, tv.Wk.vis, tv.Wk.jobs, tv.Wk.job_light,
-                                          tv.Wk.job_count, tv.Wk.job_cap, lb);
+                    shade_prep_body<true>(V, tv.w.FD, tv.w.S, Rs, tv.w.pil_hit, tv.w.Wk.vis, tv.w.Wk.jobs, tv.w.Wk.job_light,
+                                          tv.w.Wk.job_count, tv.w.Wk.job_cap, lb);
                     break;
                 }
                 case kPhPilotFinish: {
                     const RaySet Rs{0, (uint32_t)V.P * kPilots, nullptr, nullptr, DynRays{}};
-                    shade_finish_body<true>(V, tv.FD, tv.S, Rs, tv.pil_hit, tv.Wk.vis, tv.B.irr, tv.B.dep, tv.pil_rec,
+                    shade_finish_body<true>(V, tv.w.FD, tv.w.S, Rs, tv.w.pil_hit, tv.w.Wk.vis, tv.B.irr, tv.B.dep, tv.pil_rec,
                                             tv.pil_lum, lb);
                     break;
                 }
                 case kPhChangeState:
-                    change_state_body(V, tv.FD, tv.C, lb);
+                    change_state_body(V, tv.w.FD, tv.C, lb);
                     break;
                 case kPhChangeWeight:
-                    change_weight_body<true>(V, tv.FD, tv.C, lb);
-                    break;
-                case kPhMain:
-                    main_trace_body<true>(V, tv.FD, tv.S, tv.off, tv.sf, V.R_main, tv.m_hit, lb);
+                    change_weight_body<true>(V, tv.w.FD, tv.C, lb);
                     break;
                 case kPhMainPrep: {
-                    const RaySet Rs{1, V.R_main, tv.off, tv.sf, DynRays{}};
-                    shade_prep_body<true>(V, tv.FD, tv.S, Rs, tv.m_hit, tv.Wk.vis, tv.Wk.jobs, tv.Wk.job_light,
-                                          tv.Wk.job_count, tv.Wk.job_cap, lb);
+                    const RaySet Rs{1, V.R_main, tv.off, tv.w.sf, DynRays{}};
+                    shade_prep_body<true>(V, tv.w.FD, tv.w.S, Rs, tv.w.m_hit, tv.w.Wk.vis, tv.w.Wk.jobs, tv.w.Wk.job_light,
+                                          tv.w.Wk.job_count, tv.w.Wk.job_cap, lb);
                     break;
                 }
                 case kPhMainFinish: {
-                    const RaySet Rs{1, V.R_main, tv.off, tv.sf, DynRays{}};
-                    shade_finish_body<true>(V, tv.FD, tv.S, Rs, tv.m_hit, tv.Wk.vis, tv.B.irr, tv.B.dep, tv.m_rec,
+                    const RaySet Rs{1, V.R_main, tv.off, tv.w.sf, DynRays{}};
+                    shade_finish_body<true>(V, tv.w.FD, tv.w.S, Rs, tv.w.m_hit, tv.w.Wk.vis, tv.B.irr, tv.B.dep, tv.m_rec,
                                             nullptr, lb);
                     break;
                 }
                 case kPhBlend:
-                    blend_body<true>(V, tv.FD, tv.B, lb);
+                    blend_body<true>(V, tv.w.FD, tv.B, lb, kTickBlendWarps);
                     break;
                 default:
                     break;
@@ -511,8 +594,8 @@ __global__ void __launch_bounds__(kTickThreads, 4) k_tick(const TickVol* __restr
         // the shadow-job counters: cleared before each shading's prep step
         if ((ph == kPhClassify || ph == kPhPilotFinish) && blockIdx.x == 0) {
             for (int i = threadIdx.x; i < nv; i += blockDim.x) {
-                *vols[i].Wk.job_count = 0u;
-                if (ph == kPhClassify) *vols[i].Wk.shadow_ctr = 0ull;
+                *vols[i].w.Wk.job_count = 0u;
+                if (ph == kPhClassify) *vols[i].w.Wk.shadow_ctr = 0ull;
             }
         }
         if (ph + 1 < kTickPhases && !grid_sync(C, bar++)) return;
@@ -521,21 +604,30 @@ __global__ void __launch_bounds__(kTickThreads, 4) k_tick(const TickVol* __restr
 
 }  // namespace
 
-void tick_phase_blocks(const VolConst& V, uint32_t R_main, uint32_t counts[kTickPhases])
+void tick_phase_blocks(const VolConst& V, uint32_t R_main, int nd, uint32_t counts[kTickPhases])
 {
     const uint32_t P = (uint32_t)V.P, T = kTickThreads, M = (uint32_t)std::max(V.rays_max - kPilots, 0);
     for (int i = 0; i < kTickPhases; ++i) counts[i] = 0;
     counts[kPhClassify] = (P + T - 1) / T + M;
-    counts[kPhPilot] = (P + 31) / 32;  // 32 probes x 8 octants per block
+    if (nd > 0 && nd <= kTickRebuildMax) {  // the moving part's rebuild: fill + one sorting block, tree, boxes
+        const uint32_t n = (uint32_t)nd;
+        counts[kPhClassify] += (n + T - 1) / T + 1;
+        counts[kPhHierarchy] = n > 1 ? (n - 1 + T - 1) / T : 0;
+        counts[kPhBounds] = n > 1 ? (n + T - 1) / T : 0;
+    }
+    counts[kPhPilot] = (P + 31) / 32 * kPilots;  // warp items: 32 probes x one octant
     counts[kPhPilotPrep] = counts[kPhPilotFinish] = (P * kPilots + T - 1) / T;
     counts[kPhChangeState] = counts[kPhChangeWeight] = (P + T - 1) / T;
-    counts[kPhMain] = counts[kPhMainPrep] = counts[kPhMainFinish] = (R_main + T - 1) / T;
-    counts[kPhBlend] = (P + T / 32 - 1) / (T / 32);  // one warp per probe tile
+    counts[kPhMainPrep] = counts[kPhMainFinish] = (R_main + T - 1) / T;
+    counts[kPhMain] = (R_main + 31) / 32;  // warp items of 32 rays
+    counts[kPhBlend] = (P + kTickBlendWarps - 1) / kTickBlendWarps;  // one warp per probe tile
 }
 
+// Kept small: the shared-memory carve-out takes from the L1 cache that the
+// traversal phases read the tree, the triangles and their stacks through.
 size_t tick_smem_bytes(const VolConst& V)
 {
-    const size_t blend = (size_t)blend_layout(V.Ti, V.Td).total * (kTickThreads / 32);
+    const size_t blend = (size_t)blend_layout(V.Ti, V.Td).total * kTickBlendWarps;
     return std::max(blend, blend_plan_smem(V));
 }
 
@@ -553,7 +645,8 @@ unsigned tick_grid_blocks(size_t smem)
 }
 
 cudaError_t launch_tick(const TickVol* vols, int nv, const uint32_t* pre, const int* cvol, int n_chunks,
-                        unsigned long long* scratch, TickCtl* ctl, unsigned grid, size_t smem, cudaStream_t s)
+                        unsigned long long* scratch, TickCtl* ctl, const int* rebuild, int any_rebuild, unsigned grid,
+                        size_t smem, cudaStream_t s)
 {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid, 1, 1);
@@ -565,7 +658,7 @@ cudaError_t launch_tick(const TickVol* vols, int nv, const uint32_t* pre, const 
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    cudaError_t e = cudaLaunchKernelEx(&cfg, k_tick, vols, nv, pre, cvol, n_chunks, scratch, ctl);
+    cudaError_t e = cudaLaunchKernelEx(&cfg, k_tick, vols, nv, pre, cvol, n_chunks, scratch, ctl, rebuild, any_rebuild);
     count_launches(1);
     return e;
 }

@@ -22,7 +22,7 @@ __global__ void k_set_frame(FrameDev* __restrict__ dst, const __grid_constant__ 
 __global__ void __launch_bounds__(256, 4) k_pilot_trace(VolConst V, const FrameDev* __restrict__ FD, SceneDev S,
                                                      int2* __restrict__ hit)
 {
-    pilot_trace_body(V, FD, S, hit, blockIdx.x);
+    pilot_trace_body(V, FD, S, hit, (int)(blockIdx.x * blockDim.x + threadIdx.x));
 }
 
 __global__ void __launch_bounds__(256, 4) k_main_trace(VolConst V, const FrameDev* __restrict__ FD, SceneDev S,

@@ -39,7 +39,7 @@ __global__ void __launch_bounds__(256) k_blend_plan(VolConst V, const FrameDev* 
 
 __global__ void __launch_bounds__(128) k_blend(VolConst V, const FrameDev* __restrict__ FD, BlendBufs B)
 {
-    blend_body<false>(V, FD, B, blockIdx.x);
+    blend_body<false>(V, FD, B, blockIdx.x, blockDim.x >> 5);
 }
 
 // ============================================================== allocation

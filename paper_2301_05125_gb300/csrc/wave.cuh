@@ -42,15 +42,15 @@ __device__ __forceinline__ float3 main_dir(const FrameConst& F, const float4* __
     return rotate(F.R, s);
 }
 
+// j: the thread's index in the pilot-ray launch (one warp: 32 consecutive j)
 __device__ __forceinline__ void pilot_trace_body(const VolConst& V, const FrameDev* FD, const SceneDev& S, int2* hit,
-                                                 unsigned bx)
+                                                 int j)
 {
     const FrameConst& F = FD->F;
     // A warp traces one octant of 32 consecutive probes (the stratified
     // directions of one octant, from neighbouring origins), not 8 octants of
     // 4 probes.  Thread j of the launch: group g = j / 256 of 32 probes,
     // octant (j / 32) % 8, probe 32 g + j % 32; results stay at 8 p + o.
-    const int j = bx * blockDim.x + threadIdx.x;
     const int p = V.p_lo + ((j >> 8) << 5) + (j & 31), o = (j >> 5) & 7;
     if (p >= V.p_hi) return;
     const int i = p * kPilots + o;
@@ -64,6 +64,33 @@ __device__ __forceinline__ void pilot_trace_body(const VolConst& V, const FrameD
     uint32_t h;
     trace_closest(S, org, d, V.tmin, __int_as_float(0x7F800000), t, h);
     hit[i] = make_int2((int)h, __float_as_int(t));
+}
+
+// Adaptive ray r (its probe searched in [lo, hi]): row position r - off[p]
+// of probe p, whose SF index i names the slot off[p] + i of the result.
+template <bool kLive>
+__device__ __forceinline__ void main_trace_ray(const VolConst& V, const FrameConst& F, const SceneDev& S,
+                                               const uint32_t* off, const float4* __restrict__ sf, int2* hit,
+                                               uint32_t r, int lo, int hi)
+{
+    int p = probe_of_ray<kLive>(off, r, lo, hi);
+    uint32_t base = ldl<kLive>(off + p);
+    uint32_t m = ldl<kLive>(off + p + 1) - base;
+    if (m > (uint32_t)(V.rays_max - kPilots) || r - base >= m) {
+        atomicOr(V.err, kErrRayRange);
+        return;
+    }
+    float3 org = probe_pos(V, p);
+    uint32_t i;
+    float3 d = main_dir(F, sf, m, r - base, &i);
+    if (i >= m) {
+        atomicOr(V.err, kErrRayRange);
+        return;
+    }
+    float t;
+    uint32_t h;
+    trace_closest(S, org, d, V.tmin, __int_as_float(0x7F800000), t, h);
+    hit[base + i] = make_int2((int)h, __float_as_int(t));
 }
 
 // Thread r takes row position r - off[p] of probe p, whose SF index i names
@@ -85,24 +112,37 @@ __device__ __forceinline__ void main_trace_body(const VolConst& V, const FrameDe
     block_probe_range<kLive>(off, V.P, r0, r1, &s_lo, &s_hi);
     uint32_t r = r0 + threadIdx.x;
     if (r >= re) return;
-    int p = probe_of_ray<kLive>(off, r, s_lo, s_hi);
-    uint32_t base = ldl<kLive>(off + p);
-    uint32_t m = ldl<kLive>(off + p + 1) - base;
-    if (m > (uint32_t)(V.rays_max - kPilots) || r - base >= m) {
-        atomicOr(V.err, kErrRayRange);
-        return;
+    main_trace_ray<kLive>(V, F, S, off, sf, hit, r, s_lo, s_hi);
+}
+
+// The same for one warp: rays [rb + 32 w, rb + 32 w + 32), the probe range
+// found by two lanes and passed round the warp (no block barrier)
+// chunk_p (optional, all probes only): the probe of ray 32 c for every
+// chunk c below off[P], written by the allocation, which bounds the search.
+template <bool kLive>
+__device__ __forceinline__ void main_trace_warp_body(const VolConst& V, const FrameDev* FD, const SceneDev& S,
+                                                     const uint32_t* off, const float4* __restrict__ sf, uint32_t R,
+                                                     int2* hit, unsigned w, const uint32_t* chunk_p = nullptr)
+{
+    const FrameConst& F = FD->F;
+    const int lane = threadIdx.x & 31;
+    const uint32_t rb = ldl<kLive>(off + V.p_lo), re = min(ldl<kLive>(off + V.p_hi), R);
+    const uint32_t r0 = rb + 32u * w;
+    if (r0 >= re) return;  // the whole warp
+    const uint32_t r1 = min(re - 1, r0 + 31u);
+    int lo = 0, hi = 0;
+    if (chunk_p && V.p_lo == 0) {
+        lo = (int)ldl<kLive>(chunk_p + w);
+        hi = r0 + 32u < re ? (int)ldl<kLive>(chunk_p + w + 1) : V.P - 1;
+    } else {
+        if (lane == 0) lo = probe_of_ray<kLive>(off, r0, 0, V.P - 1);
+        if (lane == 1) hi = probe_of_ray<kLive>(off, r1, 0, V.P - 1);
+        lo = __shfl_sync(0xFFFFFFFFu, lo, 0);
+        hi = __shfl_sync(0xFFFFFFFFu, hi, 1);
     }
-    float3 org = probe_pos(V, p);
-    uint32_t i;
-    float3 d = main_dir(F, sf, m, r - base, &i);
-    if (i >= m) {
-        atomicOr(V.err, kErrRayRange);
-        return;
-    }
-    float t;
-    uint32_t h;
-    trace_closest(S, org, d, V.tmin, __int_as_float(0x7F800000), t, h);
-    hit[base + i] = make_int2((int)h, __float_as_int(t));
+    const uint32_t r = r0 + lane;
+    if (r >= re) return;
+    main_trace_ray<kLive>(V, F, S, off, sf, hit, r, lo, hi);
 }
 
 constexpr float kInvPi = 0.31830987f;
@@ -280,19 +320,19 @@ __device__ __forceinline__ void shade_prep_body(const VolConst& V, const FrameDe
 }
 
 // bx / gx: this block and the number of blocks walking the job list
+// warp0: the first job of this warp's rounds; stride: jobs between rounds
+// (32 x the warps walking the list); leader: the one lane that counts them
 __device__ __forceinline__ void shadow_body(const FrameDev* FD, const SceneDev& S, const uint4* jobs,
                                             const uint8_t* job_light, const unsigned* job_count, unsigned job_cap,
-                                            unsigned long long* vis, unsigned long long* shadow_ctr, unsigned bx,
-                                            unsigned gx)
+                                            unsigned long long* vis, unsigned long long* shadow_ctr, unsigned warp0,
+                                            unsigned stride, bool leader)
 {
     const LightSet& L = FD->L;
     const unsigned total = min(*job_count, job_cap);
-    if (bx == 0 && threadIdx.x == 0) atomicAdd(shadow_ctr, (unsigned long long)total);
+    if (leader) atomicAdd(shadow_ctr, (unsigned long long)total);
     // rounds of one job per lane with a uniform trip count per warp, and an
     // explicit reconvergence per round: lanes that finish early wait instead
     // of running ahead into their next job on their own
-    const unsigned stride = gx * blockDim.x;
-    const unsigned warp0 = bx * blockDim.x + (threadIdx.x & ~31u);
     for (unsigned base = warp0; base < total; base += stride) {
         const unsigned j = base + (threadIdx.x & 31u);
         if (j < total) {
