@@ -251,7 +251,8 @@ int adgi_batch_destroy(adgi_batch batch);
  * (same integers, same floating-point operations in the same order).  Each
  * tick copies the frame descriptors from pinned host memory, clears the
  * tick's control block and launches the kernel on cuda_stream; a volume's
- * moving part, when its vertices moved, is rebuilt before the launch.
+ * moving part, when its vertices moved, is rebuilt inside the launch (up to
+ * 2,048 triangles; a larger one before it).
  *
  * Every barrier wait gives up after a time limit (2 s unless set by
  * adgi_tick_set_wait); the blocks then return and the tick's status records
@@ -277,8 +278,11 @@ int adgi_tick_set_wait(adgi_tick tick, uint64_t limit_ns, int32_t stall_barrier)
 int adgi_tick_info(adgi_tick tick, uint32_t* grid_blocks, uint32_t* smem_bytes, uint32_t* chunks);
 /* Timeline of the last tick: out[i] = ns from the start of block 0 to the
  * completion of grid barrier i (0 for barriers not reached or beyond 64).
- * Barriers 0-6 end the phases before the allocation, then the allocation's
- * own barriers, then one per remaining phase.  Synchronises cuda_stream. */
+ * In order: one barrier after each phase before the allocation (clip
+ * classes and blend plan; when a moving part is rebuilt in the tick, its
+ * tree and its boxes; pilot trace; shadow jobs; shadow rays; pilot records;
+ * change state; change weights), the allocation's own barriers, then one
+ * after each later phase but the last.  Synchronises cuda_stream. */
 int adgi_tick_phase_ns(adgi_tick tick, uint64_t* out, int32_t n);
 int adgi_tick_destroy(adgi_tick tick);
 

@@ -74,3 +74,22 @@ def test_errors_without_gpu_work():
     d = adgi.make_desc((0, 0, 0), (1, 1, 1), (2, 2, 2), rays_avg=7)
     with pytest.raises(adgi.AdgiError):
         adgi.adgi_create_volume(d)
+
+
+def test_tick_arguments_checked_on_the_host():
+    """The persistent tick rejects bad arguments before any device work."""
+    import ctypes as C
+
+    from paper_2301_05125_gb300 import adgi
+
+    L = adgi.load()
+    out = C.c_void_p()
+    assert L.adgi_tick_create(None, 1, None, C.byref(out)) == -1
+    arr = (C.c_void_p * 1)(None)
+    assert L.adgi_tick_create(arr, 1, None, C.byref(out)) == -1 and "NULL volume" in adgi.adgi_last_error()
+    assert L.adgi_tick_create(arr, 0, None, C.byref(out)) == -1
+    assert L.adgi_tick_update(None, None) == -1
+    assert L.adgi_tick_sync(None) == -1
+    assert L.adgi_tick_set_wait(None, 1000, -1) == -1
+    assert L.adgi_tick_phase_ns(None, None, 0) == -1
+    assert L.adgi_tick_destroy(None) == 0
