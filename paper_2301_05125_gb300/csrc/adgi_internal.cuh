@@ -575,9 +575,9 @@ __device__ __forceinline__ int trav4_visit(Trav& T, int* stack, int& sp, int nod
 // One visit of the static part's 4-wide tree without its leaf tests: node
 // `node`, the traversal's stack and its depth sp, the ray's direction signs
 // (sx, sy, sz: 0 positive, 1 negative).  The hit leaf children go to
-// *leaves (bit k: slot k); the hit internal children nearest first: the
-// nearest is returned, the others pushed.  Returns -1 when no internal child
-// is hit and the stack is empty.
+// *leaves (bit k: slot k); of the hit internal children the first in the
+// order below is returned and the others pushed.  Returns -1 when no
+// internal child is hit and the stack is empty.
 __device__ __forceinline__ int trav4_inner(Trav& T, int* stack, int& sp, int node, const SceneDev& S, bool any,
                                            int sx, int sy, int sz, uint32_t* nbox, uint32_t& leaves)
 {
@@ -608,10 +608,13 @@ __device__ __forceinline__ int trav4_inner(Trav& T, int* stack, int& sp, int nod
                                fminf(fmaf(fzs[k], T.inv.z, -T.oi.z), lim));
         const bool hit = tn <= tf;
         if (hit && ref[k] < 0) leaves |= 1u << k;
-        key[k] = hit && ref[k] >= 0 ? tn : inf;
+        key[k] = hit && ref[k] >= 0 ? (any ? tn - tf : tn) : inf;
     }
-    // the hit internal children nearest first: a sorting network on (key, ref)
-    // (for an any-hit traversal only the nearest is put first)
+    // the hit internal children in order: a sorting network on (key, ref).
+    // Closest hit: nearest entry first.  Any hit: only the first place is
+    // sorted, and it goes to the child holding the longest stretch of the
+    // ray (tn - tf least), the likeliest to hold a blocker (measured: shadow
+    // rays 2-7 % faster than nearest first).
 #define ADGI_CSWAP(i, j)                                  \
     if (key[j] < key[i]) {                                \
         const float tk = key[i];                          \
