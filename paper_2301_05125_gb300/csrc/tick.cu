@@ -128,38 +128,35 @@ __device__ __forceinline__ int volume_of(const uint32_t* row, int nv, uint32_t v
     return lo;
 }
 
+// Threads [0, n) copy the object at src to dst in 8-byte words.  Through
+// memcpy, not a word-typed pointer: stores through a pointer of another type
+// would not count, for the optimizer, as writes to the struct's fields, so a
+// field read after a copy could return a value cached from before it.
+template <typename T>
+__device__ __forceinline__ void copy_words(T* dst, const T* src, size_t bytes, int t, int n)
+{
+    static_assert(sizeof(T) % 8 == 0, "copied as 8-byte words");
+    const char* s = reinterpret_cast<const char*>(src);
+    char* d = reinterpret_cast<char*>(dst);
+    for (size_t k = (size_t)t; k < bytes / 8; k += (size_t)n) {
+        unsigned long long w;
+        memcpy(&w, s + 8 * k, 8);
+        memcpy(d + 8 * k, &w, 8);
+    }
+}
+
 // Make volume i the block's current one (its parameters in shared memory).
 // Called by every thread of the block with the same i.  The copy waits for
 // every thread first: one may still be reading the previous volume's.
 __device__ __forceinline__ void use_volume(const TickVol* __restrict__ vols, int i, TickVol& tv, int& cur)
 {
-    if (cur == i) return;
-    __syncthreads();
-    static_assert(sizeof(TickVol) % 8 == 0, "copied as 64-bit words");
-    const unsigned long long* src = reinterpret_cast<const unsigned long long*>(vols + i);
-    unsigned long long* dst = reinterpret_cast<unsigned long long*>(&tv);
-    for (int k = threadIdx.x; k < (int)(sizeof(TickVol) / 8); k += blockDim.x) dst[k] = __ldg(src + k);
+    // one decision for the whole block (and a barrier: every thread is done
+    // with the previous volume's parameters before they are overwritten)
+    if (!__syncthreads_or(cur != i)) return;
+    copy_words(&tv, vols + i, sizeof(TickVol), threadIdx.x, blockDim.x);
     __syncthreads();
     if (threadIdx.x == 0) cur = i;
     __syncthreads();
-}
-
-// Make volume i the warp's current one for the ray phases (its TickWave in
-// this warp's slot of shared memory).  Called by every lane of the warp.
-// The lanes of a warp leave a ray item at different times (independent
-// thread scheduling), so the copy waits for all of them first: a slow lane
-// may still be traversing with the previous volume's parameters.
-__device__ __forceinline__ void use_wave(const TickVol* __restrict__ vols, int i, TickWave& w, int& cur)
-{
-    if (cur == i) return;
-    __syncwarp();
-    static_assert(sizeof(TickWave) % 8 == 0, "copied as 64-bit words");
-    const unsigned long long* src = reinterpret_cast<const unsigned long long*>(&vols[i].w);
-    unsigned long long* dst = reinterpret_cast<unsigned long long*>(&w);
-    for (int k = threadIdx.x & 31; k < (int)(sizeof(TickWave) / 8); k += 32) dst[k] = __ldg(src + k);
-    __syncwarp();
-    if ((threadIdx.x & 31) == 0) cur = i;
-    __syncwarp();
 }
 
 // sums over chunks [cb, ce) of row a: the total and the part before chunk c
@@ -458,13 +455,12 @@ __global__ void __launch_bounds__(kTickThreads, 4) k_tick(const TickVol* __restr
 {
     __shared__ __align__(16) TickVol tv;
     __shared__ int cur;
-    // the ray phases run per warp, with no block barrier between a warp's
-    // work items (a block would otherwise wait for its slowest warp's rays)
+    // The ray phases run per warp, with no block barrier between a warp's
+    // work items (a block would otherwise wait for its slowest warp's
+    // rays); a warp reads its volume's ray parameters (TickWave) straight
+    // from the read-only table.
     constexpr int kWarps = kTickThreads / 32;
-    __shared__ __align__(16) TickWave wv[kWarps];
-    __shared__ int wcur[kWarps];
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (threadIdx.x < kWarps) wcur[threadIdx.x] = -1;
     if (threadIdx.x == 0) cur = -1;
     if (blockIdx.x == 0 && threadIdx.x == 0) C->t_start = global_ns();
     __syncthreads();
@@ -479,8 +475,7 @@ __global__ void __launch_bounds__(kTickThreads, 4) k_tick(const TickVol* __restr
             const unsigned nw = gridDim.x * kWarps, gw = blockIdx.x * kWarps + wid;
             unsigned rot = 0;
             for (int i = 0; i < nv; ++i) {
-                use_wave(vols, i, wv[wid], wcur[wid]);
-                const TickWave& T = wv[wid];
+                const TickWave& T = vols[i].w;
                 const unsigned total = min(*T.Wk.job_count, T.Wk.job_cap);
                 const unsigned me = (gw + nw - rot) % nw;
                 shadow_body(T.FD, T.S, T.Wk.jobs, T.Wk.job_light, T.Wk.job_count, T.Wk.job_cap, T.Wk.vis,
@@ -495,8 +490,7 @@ __global__ void __launch_bounds__(kTickThreads, 4) k_tick(const TickVol* __restr
             const uint32_t total = row[nv], nw = gridDim.x * kWarps;
             for (uint32_t vw = blockIdx.x * kWarps + wid; vw < total; vw += nw) {
                 const int i = volume_of(row, nv, vw);
-                use_wave(vols, i, wv[wid], wcur[wid]);
-                const TickWave& T = wv[wid];
+                const TickWave& T = vols[i].w;
                 const uint32_t lw = vw - row[i];
                 if (ph == kPhPilot)
                     pilot_trace_body(T.V, T.FD, T.S, T.pil_hit, (int)(32u * lw) + lane);
@@ -504,7 +498,7 @@ __global__ void __launch_bounds__(kTickThreads, 4) k_tick(const TickVol* __restr
                     main_trace_warp_body<true>(T.V, T.FD, T.S, T.off, T.sf, T.V.R_main, T.m_hit, lw, T.chunk_p);
                 // The lanes leave an item at different times (independent
                 // thread scheduling); they start the next one together, since
-                // its warp shuffles and its parameter copy need all of them.
+                // its warp shuffles need all of them.
                 __syncwarp();
             }
             __syncthreads();
