@@ -382,12 +382,14 @@ __device__ __forceinline__ bool slab_fma(float lox, float loy, float loz, float 
     return tn <= tf;
 }
 
-// the triangle at slot `slot` of the BVH-ordered array
+// the triangle at slot `slot` of the BVH-ordered array (kLive: it may have
+// been written earlier in the same launch, see ldl)
+template <bool kLive = false>
 __device__ __forceinline__ void trav_tri(Trav& T, const float4* tri_v, int slot, bool any, uint32_t* ntri)
 {
     if (ntri) ++*ntri;
     const float4* tv = tri_v + 3 * (size_t)slot;
-    float4 A = __ldg(tv), Bv = __ldg(tv + 1), C = __ldg(tv + 2);
+    float4 A = ldl<kLive>(tv), Bv = ldl<kLive>(tv + 1), C = ldl<kLive>(tv + 2);
     float tt, det;
     if (!wtri(T.wr, A, Bv, C, tt, det) || !(tt > T.tmin)) return;
     if (any) {
@@ -406,7 +408,9 @@ __device__ __forceinline__ void trav_tri(Trav& T, const float4* tri_v, int slot,
 
 // set up a traversal; single-triangle parts are tested here, trees pushed
 // (the static part's only when it has no 4-wide tree: that one is walked
-// by trav4 beforehand)
+// by trav4 beforehand).  kLive: the moving part may have been rebuilt
+// earlier in the same launch (its nodes and triangles are read with ldl).
+template <bool kLive = false>
 __device__ __forceinline__ void trav_init(Trav& T, int* stack, const SceneDev& S, float3 o, float3 d, float tmin,
                                           float tmax, bool any, uint32_t* ntri = nullptr)
 {
@@ -441,12 +445,13 @@ __device__ __forceinline__ void trav_init(Trav& T, int* stack, const SceneDev& S
         if (root >= 0)
             stack[T.sp++] = root;
         else if (leaf >= 0)
-            trav_tri(T, S.tri_v, leaf, any, ntri);
+            trav_tri<kLive>(T, S.tri_v, leaf, any, ntri);
     }
     if (any && T.found) T.sp = 0;
 }
 
 // one node visit; false once the traversal is over
+template <bool kLive = false>
 __device__ __forceinline__ bool trav_step(Trav& T, int* stack, const SceneDev& S, bool any,
                                           uint32_t* nbox = nullptr, uint32_t* ntri = nullptr)
 {
@@ -461,14 +466,14 @@ __device__ __forceinline__ bool trav_step(Trav& T, int* stack, const SceneDev& S
     const int e = T.next >= 0 ? T.next : stack[--T.sp];
     T.next = -1;
     const BNode* nd = S.nodes + e;
-    float4 a = __ldg(&nd->a), b = __ldg(&nd->b), c = __ldg(&nd->c);
-    int4 ch = __ldg(&nd->d);
+    float4 a = ldl<kLive>(&nd->a), b = ldl<kLive>(&nd->b), c = ldl<kLive>(&nd->c);
+    int4 ch = ldl<kLive>(&nd->d);
     const float lim = any ? T.lim : T.t_best * kBoxSlack;
     float t0, t1;
     const bool h0 = slab_fma(a.x, a.y, a.z, a.w, b.x, b.y, T.inv, T.oi, lim, t0);
     const bool h1 = slab_fma(b.z, b.w, c.x, c.y, c.z, c.w, T.inv, T.oi, lim, t1);
-    if (h0 && ch.x < 0) trav_tri(T, S.tri_v, ~ch.x, any, ntri);
-    if (h1 && ch.y < 0) trav_tri(T, S.tri_v, ~ch.y, any, ntri);
+    if (h0 && ch.x < 0) trav_tri<kLive>(T, S.tri_v, ~ch.x, any, ntri);
+    if (h1 && ch.y < 0) trav_tri<kLive>(T, S.tri_v, ~ch.y, any, ntri);
     const bool i0 = h0 && ch.x >= 0, i1 = h1 && ch.y >= 0;
     if (i0 && i1) {  // the near child next, the far one on the stack
         const bool first0 = t0 <= t1;
@@ -716,39 +721,42 @@ __device__ __forceinline__ void trav4(Trav& T, int* stack, const SceneDev& S, bo
     }
 }
 
-// nearest hit with t in (tmin, tmax] (one thread, one ray)
+// nearest hit with t in (tmin, tmax] (one thread, one ray); kLive: as for
+// trav_init
+template <bool kLive = false>
 __device__ __forceinline__ void trace_closest(const SceneDev& S, float3 o, float3 d, float tmin, float tmax,
                                               float& t_best, uint32_t& hit_best, uint32_t* nbox = nullptr,
                                               uint32_t* ntri = nullptr)
 {
     Trav T;
     int stack[kWide4Stack + 2];  // the moving part's root sits below the 4-wide traversal's entries
-    trav_init(T, stack, S, o, d, tmin, tmax, false, ntri);
+    trav_init<kLive>(T, stack, S, o, d, tmin, tmax, false, ntri);
     if (S.w4) {  // the static part's 4-wide tree first, then the moving part's binary tree
         const int sp = T.sp;  // the moving part's root, pushed by trav_init, waits below
         int* st = stack + sp;
         trav4(T, st, S, false, nbox, ntri);
         T.sp = sp;
     }
-    while (trav_step(T, stack, S, false, nbox, ntri)) {
+    while (trav_step<kLive>(T, stack, S, false, nbox, ntri)) {
     }
     t_best = T.t_best;
     hit_best = trav_hit(T);
 }
 
 // any hit with t in (tlo, thi): shadow visibility (one thread, one ray)
+template <bool kLive = false>
 __device__ __forceinline__ bool trace_any(const SceneDev& S, float3 o, float3 d, float tlo, float thi,
                                           uint32_t* nbox = nullptr, uint32_t* ntri = nullptr)
 {
     Trav T;
     int stack[kWide4Stack + 2];  // the moving part's root sits below the 4-wide traversal's entries
-    trav_init(T, stack, S, o, d, tlo, thi, true, ntri);
+    trav_init<kLive>(T, stack, S, o, d, tlo, thi, true, ntri);
     if (S.w4 && !T.found) {
         const int sp = T.sp;
         trav4(T, stack + sp, S, true, nbox, ntri);
         T.sp = T.found ? 0 : sp;
     }
-    while (trav_step(T, stack, S, true, nbox, ntri)) {
+    while (trav_step<kLive>(T, stack, S, true, nbox, ntri)) {
     }
     return T.found;
 }

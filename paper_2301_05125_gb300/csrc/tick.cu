@@ -478,7 +478,7 @@ __global__ void __launch_bounds__(kTickThreads, 4) k_tick(const TickVol* __restr
                 const TickWave& T = vols[i].w;
                 const unsigned total = min(*T.Wk.job_count, T.Wk.job_cap);
                 const unsigned me = (gw + nw - rot) % nw;
-                shadow_body(T.FD, T.S, T.Wk.jobs, T.Wk.job_light, T.Wk.job_count, T.Wk.job_cap, T.Wk.vis,
+                shadow_body<true>(T.FD, T.S, T.Wk.jobs, T.Wk.job_light, T.Wk.job_count, T.Wk.job_cap, T.Wk.vis,
                             T.Wk.shadow_ctr, 32u * me, 32u * nw, me == 0 && lane == 0);
                 rot = (rot + (total + 31u) / 32u) % nw;
                 __syncwarp();  // the lanes go on to the next list together
@@ -493,7 +493,7 @@ __global__ void __launch_bounds__(kTickThreads, 4) k_tick(const TickVol* __restr
                 const TickWave& T = vols[i].w;
                 const uint32_t lw = vw - row[i];
                 if (ph == kPhPilot)
-                    pilot_trace_body(T.V, T.FD, T.S, T.pil_hit, (int)(32u * lw) + lane);
+                    pilot_trace_body<true>(T.V, T.FD, T.S, T.pil_hit, (int)(32u * lw) + lane);
                 else
                     main_trace_warp_body<true>(T.V, T.FD, T.S, T.off, T.sf, T.V.R_main, T.m_hit, lw, T.chunk_p);
                 // The lanes leave an item at different times (independent

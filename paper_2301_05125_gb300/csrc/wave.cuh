@@ -43,6 +43,7 @@ __device__ __forceinline__ float3 main_dir(const FrameConst& F, const float4* __
 }
 
 // j: the thread's index in the pilot-ray launch (one warp: 32 consecutive j)
+template <bool kLive = false>
 __device__ __forceinline__ void pilot_trace_body(const VolConst& V, const FrameDev* FD, const SceneDev& S, int2* hit,
                                                  int j)
 {
@@ -62,7 +63,7 @@ __device__ __forceinline__ void pilot_trace_body(const VolConst& V, const FrameD
     float3 d = pilot_dir(F.pilot_key, (uint32_t)p, o);
     float t;
     uint32_t h;
-    trace_closest(S, org, d, V.tmin, __int_as_float(0x7F800000), t, h);
+    trace_closest<kLive>(S, org, d, V.tmin, __int_as_float(0x7F800000), t, h);
     hit[i] = make_int2((int)h, __float_as_int(t));
 }
 
@@ -89,7 +90,7 @@ __device__ __forceinline__ void main_trace_ray(const VolConst& V, const FrameCon
     }
     float t;
     uint32_t h;
-    trace_closest(S, org, d, V.tmin, __int_as_float(0x7F800000), t, h);
+    trace_closest<kLive>(S, org, d, V.tmin, __int_as_float(0x7F800000), t, h);
     hit[base + i] = make_int2((int)h, __float_as_int(t));
 }
 
@@ -227,11 +228,13 @@ __device__ __forceinline__ bool ray_of(const VolConst& V, const FrameConst& F, c
     return true;
 }
 
-// exact FP32 geometric normal of triangle tri (original order)
+// exact FP32 geometric normal of triangle tri (original order; kLive: a
+// moving triangle's row may have been written earlier in the same launch)
+template <bool kLive = false>
 __device__ __forceinline__ float3 tri_normal(const SceneDev& S, int tri)
 {
-    float4 A = __ldg(S.tri_orig + 3 * (size_t)tri), B = __ldg(S.tri_orig + 3 * (size_t)tri + 1),
-           C = __ldg(S.tri_orig + 3 * (size_t)tri + 2);
+    float4 A = ldl<kLive>(S.tri_orig + 3 * (size_t)tri), B = ldl<kLive>(S.tri_orig + 3 * (size_t)tri + 1),
+           C = ldl<kLive>(S.tri_orig + 3 * (size_t)tri + 2);
     float e1x = fs(B.x, A.x), e1y = fs(B.y, A.y), e1z = fs(B.z, A.z);
     float e2x = fs(C.x, A.x), e2y = fs(C.y, A.y), e2z = fs(C.z, A.z);
     float cx = fs(fm(e1y, e2z), fm(e1z, e2y));
@@ -269,7 +272,7 @@ __device__ __forceinline__ void shade_prep_body(const VolConst& V, const FrameDe
         uint32_t h = (uint32_t)hv.x;
         if (h != kMiss && !(h & kBackBit)) {
             float t = __int_as_float(hv.y);
-            n = tri_normal(S, (int)h);
+            n = tri_normal<kLive>(S, (int)h);
             float3 x = make_float3(fa(o.x, fm(t, d.x)), fa(o.y, fm(t, d.y)), fa(o.z, fm(t, d.z)));
             xs = make_float3(fa(x.x, fm(V.tmin, n.x)), fa(x.y, fm(V.tmin, n.y)), fa(x.z, fm(V.tmin, n.z)));
             front = true;
@@ -322,6 +325,7 @@ __device__ __forceinline__ void shade_prep_body(const VolConst& V, const FrameDe
 // bx / gx: this block and the number of blocks walking the job list
 // warp0: the first job of this warp's rounds; stride: jobs between rounds
 // (32 x the warps walking the list); leader: the one lane that counts them
+template <bool kLive = false>
 __device__ __forceinline__ void shadow_body(const FrameDev* FD, const SceneDev& S, const uint4* jobs,
                                             const uint8_t* job_light, const unsigned* job_count, unsigned job_cap,
                                             unsigned long long* vis, unsigned long long* shadow_ctr, unsigned warp0,
@@ -342,7 +346,7 @@ __device__ __forceinline__ void shadow_body(const FrameDev* FD, const SceneDev& 
             float3 xs = make_float3(__uint_as_float(jb.x), __uint_as_float(jb.y), __uint_as_float(jb.z));
             float3 D = shadow_dir(Li, xs);
             float thi = Li.kind == 0 ? 1.0f : __int_as_float(0x7F800000);
-            if (!trace_any(S, xs, D, 0.0f, thi)) atomicOr(vis + jb.w, 1ull << l);
+            if (!trace_any<kLive>(S, xs, D, 0.0f, thi)) atomicOr(vis + jb.w, 1ull << l);
         }
         __syncwarp();
     }
@@ -393,7 +397,7 @@ __device__ __forceinline__ void shade_finish_body(const VolConst& V, const Frame
             out = make_float4(0.f, 0.f, 0.f, depth);
         } else {
             int tri = (int)h;
-            float3 n = tri_normal(S, tri);
+            float3 n = tri_normal<kLive>(S, tri);
             float3 x = make_float3(fa(o.x, fm(t, d.x)), fa(o.y, fm(t, d.y)), fa(o.z, fm(t, d.z)));
             unsigned long long vm = vis[slot];
             float E0 = 0.f, E1 = 0.f, E2 = 0.f;
