@@ -564,7 +564,7 @@ int adgi_create_volume(const adgi_volume_desc* desc, void* cuda_stream, adgi_vol
     DA(v->err, 1);
     DA(v->fdev, 1);
     DA(v->vis, std::max<size_t>(P * 8, (size_t)v->R_main));
-    DA(v->job_count, 1);
+    DA(v->job_count, 2);  // the shadow-job count and the shadow kernel's round counter
     DA(v->qd, P * 8);
     DA(v->cls, P);
     DA(v->vout_even, P);

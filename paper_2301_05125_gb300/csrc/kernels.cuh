@@ -56,7 +56,7 @@ struct ShadeWork {
     unsigned long long* vis;  // per ray: bit l = light l visible
     uint4* jobs;              // shadow jobs {origin xyz, ray}
     uint8_t* job_light;       // light of each job
-    unsigned* job_count;
+    unsigned* job_count;      // [2]: the jobs written, the next round of 32 jobs for the shadow kernel
     unsigned job_cap;
     unsigned shadow_blocks;   // persistent grid of the shadow kernel
     unsigned long long* shadow_ctr;
@@ -289,6 +289,7 @@ struct TickCtl {
     int status;                     // 0, or kTickTimedOut
     unsigned pass_flag[kTickPasses];  // a chunk took part in allocation pass i
     unsigned rem_flag[2];           // a chunk took part in remainder round j (j mod 2)
+    unsigned next_item[4];          // the next warp item of the pilot, adaptive, pilot-shadow, adaptive-shadow phases
     unsigned long long t_start;     // %globaltimer at the start of block 0
     unsigned long long t_bar[kTickStamps];  // %globaltimer when barrier i completed (the first kTickStamps)
     unsigned long long limit_ns;    // a barrier wait gives up after this long

@@ -31,10 +31,10 @@ __global__ void __launch_bounds__(256) k_shade_prep(VolConst V, const FrameDev* 
 __global__ void __launch_bounds__(128, 7) k_shadow(const FrameDev* __restrict__ FD, SceneDev S,
                                                 const uint4* __restrict__ jobs, const uint8_t* __restrict__ job_light,
                                                 const unsigned* __restrict__ job_count, unsigned job_cap,
-                                                unsigned long long* __restrict__ vis, unsigned long long* shadow_ctr)
+                                                unsigned long long* __restrict__ vis, unsigned long long* shadow_ctr,
+                                                unsigned* next_round)
 {
-    shadow_body(FD, S, jobs, job_light, job_count, job_cap, vis, shadow_ctr,
-                blockIdx.x * blockDim.x + (threadIdx.x & ~31u), gridDim.x * blockDim.x,
+    shadow_body(FD, S, jobs, job_light, job_count, job_cap, vis, shadow_ctr, next_round,
                 blockIdx.x == 0 && threadIdx.x == 0);
 }
 
@@ -70,13 +70,13 @@ cudaError_t launch_shade(const VolConst& V, const FrameDev* FD, const SceneDev& 
     RaySet Rs{mode, n_rays, off, sf, dyn ? *dyn : DynRays{}};
     const unsigned b = (unsigned)T.shade_block;
     const unsigned nb = (n_rays + b - 1) / b;
-    cudaError_t e = cudaMemsetAsync(W.job_count, 0, sizeof(unsigned), s);
+    cudaError_t e = cudaMemsetAsync(W.job_count, 0, 2 * sizeof(unsigned), s);  // the count and the round counter
     if (e != cudaSuccess) return e;
     k_shade_prep<<<nb, b, 0, s>>>(V, FD, S, Rs, hit, W.vis, W.jobs, W.job_light, W.job_count, W.job_cap);
     count_launches(1);
     if (ev_shadow && (e = cudaEventRecord(ev_shadow[0], s)) != cudaSuccess) return e;
     k_shadow<<<W.shadow_blocks, 128, 0, s>>>(FD, S, W.jobs, W.job_light, W.job_count, W.job_cap, W.vis,
-                                             W.shadow_ctr);
+                                             W.shadow_ctr, W.job_count + 1);
     count_launches(1);
     if (ev_shadow && (e = cudaEventRecord(ev_shadow[1], s)) != cudaSuccess) return e;
     k_shade_finish<<<nb, b, 0, s>>>(V, FD, S, Rs, hit, W.vis, irr, dep, rec, lum);

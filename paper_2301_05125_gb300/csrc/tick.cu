@@ -459,8 +459,7 @@ __global__ void __launch_bounds__(kTickThreads, 4) k_tick(const TickVol* __restr
     // work items (a block would otherwise wait for its slowest warp's
     // rays); a warp reads its volume's ray parameters (TickWave) straight
     // from the read-only table.
-    constexpr int kWarps = kTickThreads / 32;
-    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const unsigned lane = threadIdx.x & 31u;
     if (threadIdx.x == 0) cur = -1;
     if (blockIdx.x == 0 && threadIdx.x == 0) C->t_start = global_ns();
     __syncthreads();
@@ -468,27 +467,42 @@ __global__ void __launch_bounds__(kTickThreads, 4) k_tick(const TickVol* __restr
     for (int ph = 0; ph < kTickPhases; ++ph) {
         if (!any_rebuild && (ph == kPhHierarchy || ph == kPhBounds)) continue;  // (and their barriers)
         if (ph == kPhPilotShadow || ph == kPhMainShadow) {
-            // every volume's shadow jobs in turn, all warps of the grid over
-            // each list; each list starts where the previous one ended (in
-            // rounds of 32 jobs, around the warps), so small lists do not all
-            // land on the first warps
-            const unsigned nw = gridDim.x * kWarps, gw = blockIdx.x * kWarps + wid;
-            unsigned rot = 0;
-            for (int i = 0; i < nv; ++i) {
+            // every volume's shadow jobs, in rounds of 32 consecutive jobs
+            // of one list (one job a lane); the rounds of all lists in
+            // volume order form one sequence, and each warp takes the next
+            // round from a grid-wide counter, so warps that drew short rays
+            // take more rounds and all end together
+            unsigned* next = &C->next_item[ph == kPhPilotShadow ? 2 : 3];
+            int i = 0;
+            unsigned first = 0;  // the first round of volume i
+            unsigned total = min(*vols[0].w.Wk.job_count, vols[0].w.Wk.job_cap);
+            for (;;) {
+                unsigned g = 0;
+                if (lane == 0) g = atomicAdd(next, 1u);
+                g = __shfl_sync(0xFFFFFFFFu, g, 0);
+                while (i < nv && g >= first + (total + 31u) / 32u) {  // rounds are taken in increasing order
+                    first += (total + 31u) / 32u;
+                    if (++i < nv) total = min(*vols[i].w.Wk.job_count, vols[i].w.Wk.job_cap);
+                }
+                if (i >= nv) break;
                 const TickWave& T = vols[i].w;
-                const unsigned total = min(*T.Wk.job_count, T.Wk.job_cap);
-                const unsigned me = (gw + nw - rot) % nw;
-                shadow_body<true>(T.FD, T.S, T.Wk.jobs, T.Wk.job_light, T.Wk.job_count, T.Wk.job_cap, T.Wk.vis,
-                            T.Wk.shadow_ctr, 32u * me, 32u * nw, me == 0 && lane == 0);
-                rot = (rot + (total + 31u) / 32u) % nw;
-                __syncwarp();  // the lanes go on to the next list together
+                const unsigned r = g - first, j = 32u * r + lane;
+                if (r == 0 && lane == 0) atomicAdd(T.Wk.shadow_ctr, (unsigned long long)total);
+                if (j < total) shadow_job<true>(T.FD->L, T.S, T.Wk.jobs, T.Wk.job_light, T.Wk.vis, j);
+                __syncwarp();  // the lanes take the next round together
             }
             __syncthreads();
         } else if (ph == kPhPilot || ph == kPhMain) {
-            // warp items: 32 pilot rays of one octant, or 32 adaptive rays
+            // warp items: 32 pilot rays of one octant, or 32 adaptive rays,
+            // each warp taking the next item from a grid-wide counter
             const uint32_t* row = pre + (size_t)ph * (nv + 1);
-            const uint32_t total = row[nv], nw = gridDim.x * kWarps;
-            for (uint32_t vw = blockIdx.x * kWarps + wid; vw < total; vw += nw) {
+            const uint32_t total = row[nv];
+            unsigned* next = &C->next_item[ph == kPhPilot ? 0 : 1];
+            for (;;) {
+                uint32_t vw = 0;
+                if (lane == 0) vw = atomicAdd(next, 1u);
+                vw = __shfl_sync(0xFFFFFFFFu, vw, 0);
+                if (vw >= total) break;
                 const int i = volume_of(row, nv, vw);
                 const TickWave& T = vols[i].w;
                 const uint32_t lw = vw - row[i];

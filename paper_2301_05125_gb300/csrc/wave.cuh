@@ -322,32 +322,46 @@ __device__ __forceinline__ void shade_prep_body(const VolConst& V, const FrameDe
     }
 }
 
-// bx / gx: this block and the number of blocks walking the job list
-// warp0: the first job of this warp's rounds; stride: jobs between rounds
-// (32 x the warps walking the list); leader: the one lane that counts them
+// Shadow job j (one lane): light l of the job is seen from its origin when
+// no triangle blocks the segment (point light) or the ray (sun); then bit l
+// of the ray's visibility word is set.
+template <bool kLive = false>
+__device__ __forceinline__ void shadow_job(const LightSet& L, const SceneDev& S, const uint4* jobs,
+                                           const uint8_t* job_light, unsigned long long* vis, unsigned j)
+{
+    uint4 jb = jobs[j];
+    int l = job_light[j];
+    const Light& Li = L.l[l];
+    float3 xs = make_float3(__uint_as_float(jb.x), __uint_as_float(jb.y), __uint_as_float(jb.z));
+    float3 D = shadow_dir(Li, xs);
+    float thi = Li.kind == 0 ? 1.0f : __int_as_float(0x7F800000);
+    if (!trace_any<kLive>(S, xs, D, 0.0f, thi)) atomicOr(vis + jb.w, 1ull << l);
+}
+
+// The shadow jobs [0, min(*job_count, job_cap)) in rounds of 32 consecutive
+// jobs, one a lane, with a uniform trip count per warp and an explicit
+// reconvergence per round (lanes that finish early wait instead of running
+// ahead on their own).  Each warp takes the next round from the counter
+// next_round (zero before the launch), so a warp that drew short rays takes
+// more rounds and the warps end together.  leader: the one lane that counts
+// the jobs.
 template <bool kLive = false>
 __device__ __forceinline__ void shadow_body(const FrameDev* FD, const SceneDev& S, const uint4* jobs,
                                             const uint8_t* job_light, const unsigned* job_count, unsigned job_cap,
-                                            unsigned long long* vis, unsigned long long* shadow_ctr, unsigned warp0,
-                                            unsigned stride, bool leader)
+                                            unsigned long long* vis, unsigned long long* shadow_ctr,
+                                            unsigned* next_round, bool leader)
 {
     const LightSet& L = FD->L;
     const unsigned total = min(*job_count, job_cap);
     if (leader) atomicAdd(shadow_ctr, (unsigned long long)total);
-    // rounds of one job per lane with a uniform trip count per warp, and an
-    // explicit reconvergence per round: lanes that finish early wait instead
-    // of running ahead into their next job on their own
-    for (unsigned base = warp0; base < total; base += stride) {
-        const unsigned j = base + (threadIdx.x & 31u);
-        if (j < total) {
-            uint4 jb = jobs[j];
-            int l = job_light[j];
-            const Light& Li = L.l[l];
-            float3 xs = make_float3(__uint_as_float(jb.x), __uint_as_float(jb.y), __uint_as_float(jb.z));
-            float3 D = shadow_dir(Li, xs);
-            float thi = Li.kind == 0 ? 1.0f : __int_as_float(0x7F800000);
-            if (!trace_any<kLive>(S, xs, D, 0.0f, thi)) atomicOr(vis + jb.w, 1ull << l);
-        }
+    const unsigned lane = threadIdx.x & 31u, rounds = (total + 31u) / 32u;
+    for (;;) {
+        unsigned g = 0;
+        if (lane == 0) g = atomicAdd(next_round, 1u);
+        g = __shfl_sync(0xFFFFFFFFu, g, 0);
+        if (g >= rounds) break;
+        const unsigned j = 32u * g + lane;
+        if (j < total) shadow_job<kLive>(L, S, jobs, job_light, vis, j);
         __syncwarp();
     }
 }
