@@ -564,7 +564,7 @@ int adgi_create_volume(const adgi_volume_desc* desc, void* cuda_stream, adgi_vol
     DA(v->err, 1);
     DA(v->fdev, 1);
     DA(v->vis, std::max<size_t>(P * 8, (size_t)v->R_main));
-    DA(v->job_count, 2);  // the shadow-job count and the shadow kernel's round counter
+    DA(v->job_count, 4);  // the shadow-job count and the work counters of the shadow and trace kernels
     DA(v->qd, P * 8);
     DA(v->cls, P);
     DA(v->vout_even, P);
@@ -1093,7 +1093,7 @@ int enqueue_update(adgi_volume v, const FrameDev& fd, cudaStream_t s, bool phase
     // for the probes inside this frame's clip volume V_out
     PHASE(1);
     CK(launch_classify(V, FD, v->lut_c, v->cls, s));
-    CK(launch_pilot_trace(V, FD, S, v->pil_hit, T, s));
+    CK(launch_pilot_trace(V, FD, S, v->pil_hit, v->job_count + 2, T, s));
     PHASE(2);
     CK(launch_shade(V, FD, S, 0, (uint32_t)V.P * kPilots, nullptr, nullptr, v->irr, v->dep, v->pil_hit, v->pil_rec,
                     v->pil_lum, W, T, s, phases ? v->shq : nullptr));
@@ -1136,7 +1136,7 @@ int enqueue_update(adgi_volume v, const FrameDev& fd, cudaStream_t s, bool phase
     } else {
         // 4-5. adaptive rays: trace, shade
         PHASE(5);
-        CK(launch_main_trace(V, FD, S, v->off, v->sf, v->R_main, v->m_hit, T, s));
+        CK(launch_main_trace(V, FD, S, v->off, v->sf, v->R_main, v->m_hit, v->job_count + 3, T, s));
         PHASE(6);
         CK(launch_shade(V, FD, S, 1, v->R_main, v->off, v->sf, v->irr, v->dep, v->m_hit, v->m_rec, nullptr, W, T, s,
                         phases ? v->shq + 2 : nullptr));
@@ -1229,7 +1229,7 @@ int adgi_update_slab(adgi_volume v, const adgi_frame* f, int32_t step, int32_t p
         }
         CK(cudaMemsetAsync(v->shadow_ctr, 0, 8, s));
         CK(launch_classify(V, FD, v->lut_c, v->cls, s));
-        CK(launch_pilot_trace(Vs, FD, S, v->pil_hit, T, s));
+        CK(launch_pilot_trace(Vs, FD, S, v->pil_hit, v->job_count + 2, T, s));
         CK(launch_shade(Vs, FD, S, 0, (uint32_t)(p1 - p0) * kPilots, nullptr, nullptr, v->irr, v->dep, v->pil_hit,
                         v->pil_rec, v->pil_lum, W, T, s));
         CK(launch_change(Vs, FD, C, s, 1));
@@ -1237,7 +1237,7 @@ int adgi_update_slab(adgi_volume v, const adgi_frame* f, int32_t step, int32_t p
         CK(launch_change(Vs, FD, C, s, 2));
     } else {
         CK(launch_allocate(v->W, V.P, V.rays_avg, V.m0, V.rays_max, v->n, v->off, s, v->cls));
-        CK(launch_main_trace(Vs, FD, S, v->off, v->sf, v->R_main, v->m_hit, T, s));
+        CK(launch_main_trace(Vs, FD, S, v->off, v->sf, v->R_main, v->m_hit, v->job_count + 3, T, s));
         CK(launch_shade(Vs, FD, S, 1, v->R_main, v->off, v->sf, v->irr, v->dep, v->m_hit, v->m_rec, nullptr, W, T, s));
         if (cosg) {
             CK(launch_blend_cos(Vs, FD, Bb, T, s));
@@ -1830,7 +1830,7 @@ int adgi_autotune(adgi_volume v, const adgi_frame* f, int32_t reps, adgi_tuning*
         Tuning T = best;
         T.trace_block = b;
         float ms = 0.f;
-        rc = timed([&] { return launch_main_trace(V, v->fdev, S, v->off, v->sf, v->R_main, v->m_hit, T, s); }, &ms);
+        rc = timed([&] { return launch_main_trace(V, v->fdev, S, v->off, v->sf, v->R_main, v->m_hit, v->job_count + 3, T, s); }, &ms);
         if (rc) break;
         if (ms < t_trace) {
             t_trace = ms;

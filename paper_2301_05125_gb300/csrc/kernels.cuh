@@ -56,7 +56,8 @@ struct ShadeWork {
     unsigned long long* vis;  // per ray: bit l = light l visible
     uint4* jobs;              // shadow jobs {origin xyz, ray}
     uint8_t* job_light;       // light of each job
-    unsigned* job_count;      // [2]: the jobs written, the next round of 32 jobs for the shadow kernel
+    unsigned* job_count;      // [4]: the jobs written, the next round of 32 jobs for the shadow kernel,
+                              // the next item of the pilot and of the adaptive trace
     unsigned job_cap;
     unsigned shadow_blocks;   // persistent grid of the shadow kernel
     unsigned long long* shadow_ctr;
@@ -182,10 +183,12 @@ cudaError_t launch_mh_blend(const VolConst& V, const FrameDev* FD, const MhBlend
 
 cudaError_t launch_set_frame(FrameDev* dst, const FrameDev& src, cudaStream_t s);
 void set_frame_node_params(FrameDev** dst_slot, const FrameDev* src, cudaKernelNodeParams* kp, void** args);
-cudaError_t launch_pilot_trace(const VolConst& V, const FrameDev* FD, const SceneDev& S, int2* hit, const Tuning& T,
-                               cudaStream_t s);
+// next: one device word, the work counter of the launch (cleared by it)
+cudaError_t launch_pilot_trace(const VolConst& V, const FrameDev* FD, const SceneDev& S, int2* hit, unsigned* next,
+                               const Tuning& T, cudaStream_t s);
 cudaError_t launch_main_trace(const VolConst& V, const FrameDev* FD, const SceneDev& S, const uint32_t* off,
-                              const float4* sf, uint32_t R, int2* hit, const Tuning& T, cudaStream_t s);
+                              const float4* sf, uint32_t R, int2* hit, unsigned* next, const Tuning& T,
+                              cudaStream_t s);
 // mode 0 pilot rays, 1 adaptive rays (off, sf), 2 Metropolis samples (sf = the
 // grouped samples), 3 dynamic rays (dyn; n_rays = the budget)
 cudaError_t launch_shade(const VolConst& V, const FrameDev* FD, const SceneDev& S, int mode, uint32_t n_rays,

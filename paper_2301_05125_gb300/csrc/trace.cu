@@ -4,6 +4,9 @@
 // shades the hits (shadow rays to each light, then the multi-bounce term read
 // from the previous frame's atlases).  Rays of a probe are contiguous, so a
 // warp shares an origin and sweeps a spiral of nearby directions.
+#include <algorithm>
+#include <atomic>
+
 #include "adgi_internal.cuh"
 #include "kernels.cuh"
 #include "wave.cuh"
@@ -19,17 +22,41 @@ __global__ void k_set_frame(FrameDev* __restrict__ dst, const __grid_constant__ 
     for (int i = threadIdx.x; i < (int)(sizeof(FrameDev) / sizeof(int)); i += blockDim.x) b[i] = a[i];
 }
 
-__global__ void __launch_bounds__(256, 4) k_pilot_trace(VolConst V, const FrameDev* __restrict__ FD, SceneDev S,
-                                                     int2* __restrict__ hit)
+// The two ray kernels run a grid the GPU holds at once; each warp takes the
+// next item of 32 rays from the counter *next (zero before the launch), so
+// a warp that drew short rays takes more items and the warps end together.
+__device__ __forceinline__ unsigned next_item(unsigned* next)
 {
-    pilot_trace_body(V, FD, S, hit, (int)(blockIdx.x * blockDim.x + threadIdx.x));
+    unsigned w = 0;
+    if ((threadIdx.x & 31u) == 0) w = atomicAdd(next, 1u);
+    return __shfl_sync(0xFFFFFFFFu, w, 0);
 }
 
+// item w: launch threads [32 w, 32 w + 32) of the pilot-ray layout
+__global__ void __launch_bounds__(256, 4) k_pilot_trace(VolConst V, const FrameDev* __restrict__ FD, SceneDev S,
+                                                     int2* __restrict__ hit, unsigned* next, uint32_t items)
+{
+    for (;;) {
+        const unsigned w = next_item(next);
+        if (w >= items) break;
+        pilot_trace_body(V, FD, S, hit, (int)(32u * w + (threadIdx.x & 31u)));
+        __syncwarp();
+    }
+}
+
+// item w: adaptive rays [off[p_lo] + 32 w, off[p_lo] + 32 w + 32)
 __global__ void __launch_bounds__(256, 4) k_main_trace(VolConst V, const FrameDev* __restrict__ FD, SceneDev S,
                                                     const uint32_t* __restrict__ off, const float4* __restrict__ sf,
-                                                    uint32_t R, int2* __restrict__ hit)
+                                                    uint32_t R, int2* __restrict__ hit, unsigned* next)
 {
-    main_trace_body<false>(V, FD, S, off, sf, R, hit, blockIdx.x);
+    const uint32_t rb = __ldg(off + V.p_lo), re = min(__ldg(off + V.p_hi), R);
+    const uint32_t items = re > rb ? (re - rb + 31u) / 32u : 0u;
+    for (;;) {
+        const unsigned w = next_item(next);
+        if (w >= items) break;
+        main_trace_warp_body<false>(V, FD, S, off, sf, R, hit, w);
+        __syncwarp();
+    }
 }
 
 // Metropolis samples, in grouped order: thread r < n traces sample r along +w
@@ -224,22 +251,58 @@ cudaError_t launch_set_frame(FrameDev* dst, const FrameDev& src, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_pilot_trace(const VolConst& V, const FrameDev* FD, const SceneDev& S, int2* hit, const Tuning& T,
-                               cudaStream_t s)
+// Blocks of b threads (a multiple of 32, at most 256) that the current GPU
+// holds at once for kernel `which` (0 pilot, 1 adaptive trace): asked of the
+// runtime once per device, kernel and block size, then kept.
+static unsigned resident_blocks(int which, int b)
 {
-    int n = ((V.p_hi - V.p_lo + 31) / 32) * 32 * kPilots, b = T.trace_block;
+    constexpr int kDevs = 16, kSizes = 8;
+    static std::atomic<unsigned> cache[kDevs][2][kSizes];
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const int si = b / 32 - 1;
+    const bool keep = dev >= 0 && dev < kDevs && si >= 0 && si < kSizes && b % 32 == 0;
+    if (keep) {
+        const unsigned c = cache[dev][which][si].load(std::memory_order_relaxed);
+        if (c) return c;
+    }
+    int sms = 0, per = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (which == 0)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pilot_trace, b, 0);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_main_trace, b, 0);
+    if (sms <= 0) sms = 152;
+    if (per <= 0) per = 1;
+    const unsigned n = (unsigned)(sms * per);
+    if (keep) cache[dev][which][si].store(n, std::memory_order_relaxed);
+    return n;
+}
+
+cudaError_t launch_pilot_trace(const VolConst& V, const FrameDev* FD, const SceneDev& S, int2* hit, unsigned* next,
+                               const Tuning& T, cudaStream_t s)
+{
+    const int n = ((V.p_hi - V.p_lo + 31) / 32) * 32 * kPilots, b = T.trace_block;
     if (n <= 0) return cudaSuccess;
-    k_pilot_trace<<<(n + b - 1) / b, b, 0, s>>>(V, FD, S, hit);
+    const uint32_t items = (uint32_t)n / 32u;
+    cudaError_t e = cudaMemsetAsync(next, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    const unsigned g = std::min(resident_blocks(0, b), (items * 32u + (unsigned)b - 1u) / (unsigned)b);
+    k_pilot_trace<<<g, b, 0, s>>>(V, FD, S, hit, next, items);
     count_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_main_trace(const VolConst& V, const FrameDev* FD, const SceneDev& S, const uint32_t* off,
-                              const float4* sf, uint32_t R, int2* hit, const Tuning& T, cudaStream_t s)
+                              const float4* sf, uint32_t R, int2* hit, unsigned* next, const Tuning& T,
+                              cudaStream_t s)
 {
     if (R == 0) return cudaSuccess;
     const unsigned b = (unsigned)T.trace_block;
-    k_main_trace<<<(R + b - 1) / b, b, 0, s>>>(V, FD, S, off, sf, R, hit);
+    cudaError_t e = cudaMemsetAsync(next, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    const unsigned g = std::min(resident_blocks(1, (int)b), (R + b - 1) / b);
+    k_main_trace<<<g, b, 0, s>>>(V, FD, S, off, sf, R, hit, next);
     count_launches(1);
     return cudaGetLastError();
 }
