@@ -24,7 +24,7 @@ struct FrameDev {
 
 // Block shapes of the launch wrappers (picked per volume by the autotuner).
 struct Tuning {
-    int trace_block = 64;    // pilot/adaptive nearest-hit kernels (64 measured best of 32-256)
+    int trace_block = 64;    // pilot/adaptive nearest-hit kernels (resident grid: 64, 128, 256 measured equal)
     int shade_block = 128;   // shading prep/finish kernels
     int shadow_mult = 0;     // shadow-ray grid: blocks per SM (0: occupancy)
     int blend_block = 64;    // blend kernel threads per CTA: one warp per probe tile
