@@ -304,6 +304,10 @@ struct TickCtl {
 void tick_phase_blocks(const VolConst& V, uint32_t R_main, int nd, uint32_t counts[kTickPhases]);
 // dynamic shared memory of the persistent kernel for a volume
 size_t tick_smem_bytes(const VolConst& V);
+// Raise kernel func's dynamic shared-memory limit on the current device to
+// at least `bytes` (never lowers it: the attribute is shared by every launch
+// and captured graph in the process).
+cudaError_t raise_smem_limit(const void* func, size_t bytes);
 // blocks of the persistent grid (all resident at once) for that shared memory, 0 on error
 unsigned tick_grid_blocks(size_t smem);
 // rebuild: [nv] 1 where the volume's moving part is rebuilt in this tick;

@@ -644,10 +644,7 @@ unsigned tick_grid_blocks(size_t smem)
     int dev = 0, sms = 0, per = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-    if (smem > 48 * 1024 &&
-        cudaFuncSetAttribute((const void*)k_tick, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-            cudaSuccess)
-        return 0;
+    if (raise_smem_limit((const void*)k_tick, smem) != cudaSuccess) return 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_tick, kTickThreads, smem) != cudaSuccess) return 0;
     return sms > 0 && per > 0 ? (unsigned)(sms * per) : 0u;
 }

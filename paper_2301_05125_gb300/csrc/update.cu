@@ -758,7 +758,7 @@ cudaError_t launch_classify(const VolConst& V, const FrameDev* FD, const uint16_
 // shared by every launch in the process, graphs captured earlier included.
 // It is only ever raised: lowering it for a small volume could invalidate a
 // launch or a graph made for a larger one.
-static cudaError_t raise_smem_limit(const void* func, size_t bytes)
+cudaError_t raise_smem_limit(const void* func, size_t bytes)
 {
     if (bytes <= 48 * 1024) return cudaSuccess;
     static std::mutex mu;
