@@ -28,7 +28,7 @@ __global__ void __launch_bounds__(256) k_shade_prep(VolConst V, const FrameDev* 
     shade_prep_body<false>(V, FD, S, Rs, hit, vis, jobs, job_light, job_count, job_cap, blockIdx.x);
 }
 
-__global__ void __launch_bounds__(128, 7) k_shadow(const FrameDev* __restrict__ FD, SceneDev S,
+__global__ void __launch_bounds__(128, 8) k_shadow(const FrameDev* __restrict__ FD, SceneDev S,
                                                 const uint4* __restrict__ jobs, const uint8_t* __restrict__ job_light,
                                                 const unsigned* __restrict__ job_count, unsigned job_cap,
                                                 unsigned long long* __restrict__ vis, unsigned long long* shadow_ctr,
