@@ -184,7 +184,9 @@ def _cpu_baseline_line(w, rays, args):
     CPU BVH there).  Then, if one update fits the time budget, whole updates
     are timed until the budget is spent (at most 8); otherwise the trace and
     shading (pilot and adaptive rays, shadow rays, multi-bounce query) of a
-    1 % probe sample of the next frame, and the rate is that sample's."""
+    1 % probe sample of the next frame, and the rate is that sample's.  Then
+    the same oracle on one thread (`single_thread`): trace and shading of
+    about 1,024 probes of the next frame.
     from oracle import oracle as O
 
     threads = os.cpu_count() or 1
@@ -226,8 +228,20 @@ def _cpu_baseline_line(w, rays, args):
                   "(1 %% sample: %d probes, %d rays) on frame 1, after an untimed full update of frame 0 "
                   "(%.1f s, CPU BVH build included); heuristics, allocation and blend are not in the sample"
                   % (len(probes), r, t_first))
+        f = 1
+    # the same oracle on one core: trace and shading of about 1,024 probes
+    ov.set_threads(1)
+    probes1 = np.arange(0, w.n_probes, max(1, w.n_probes // 1024), dtype=np.int32)
+    t0 = time.perf_counter()
+    r1 = ov.trace_shade_probes(f, w.seed, w.lights_at(f), probes1, w.sky)
+    dt1 = time.perf_counter() - t0
     ov.close()
-    return {"value": value, "unit": "rays/s", "cores": threads, "kind": "oracle", "sample": sample}
+    single = {"value": r1 / dt1, "unit": "rays/s", "cores": 1,
+              "sample": "trace + shade (pilot and adaptive rays, shadow rays, multi-bounce query) of %d probes "
+                        "(probe stride %d, %d rays) on frame %d, one thread" % (len(probes1), max(1, w.n_probes // 1024),
+                                                                          r1, f)}
+    return {"value": value, "unit": "rays/s", "cores": threads, "kind": "oracle", "sample": sample,
+            "single_thread": single}
 
 
 def run_reference(args):

@@ -2881,6 +2881,9 @@ EXPORT long long orc_trace_shade_probes(orc_vol* v, const orc_frame* fr, const i
 /* ------------------------------------------------------------------------ */
 /* State readers for the tests.                                              */
 /* ------------------------------------------------------------------------ */
+/* the number of threads later phases split over (timing only: results do  */
+/* not depend on it)                                                        */
+EXPORT void orc_set_threads(orc_vol* v, int nthreads) { v->nthreads = nthreads > 0 ? nthreads : 1; }
 EXPORT int orc_num_probes(const orc_vol* v) { return v->P; }
 EXPORT long long orc_num_main_rays(const orc_vol* v) { return (long long)v->R_main; }
 EXPORT const double* orc_irr(const orc_vol* v) { return v->irr; }

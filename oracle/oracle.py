@@ -96,6 +96,7 @@ def lib():
         L.orc_update.restype = C.c_int
         L.orc_trace_shade_probes.argtypes = [vp, C.POINTER(OrcFrame), i32p, C.c_int]
         L.orc_trace_shade_probes.restype = C.c_longlong
+        L.orc_set_threads.argtypes = [vp, C.c_int]
         for fn in ("orc_slab_begin", "orc_slab_weights", "orc_slab_finish"):
             getattr(L, fn).argtypes = [vp, C.POINTER(OrcFrame), C.c_int, C.c_int]
             getattr(L, fn).restype = C.c_int
@@ -477,6 +478,10 @@ class OracleVolume:
         a = np.ascontiguousarray(data, dt).reshape(-1)
         if a.size != (p1 - p0) * per or lib().orc_slab_slice(self.h, code, int(p0), int(p1), a.ctypes.data, 1) != a.nbytes:
             raise ValueError("bad slice")
+
+    def set_threads(self, n):
+        """threads for the later phases (timing only: results do not depend on it)"""
+        lib().orc_set_threads(self.h, int(n))
 
     def trace_shade_probes(self, frame, seed, lights, probes, sky=(0, 0, 0)):
         fr = make_frame(frame, seed, lights, sky)
