@@ -186,7 +186,7 @@ def _cpu_baseline_line(w, rays, args):
     shading (pilot and adaptive rays, shadow rays, multi-bounce query) of a
     1 % probe sample of the next frame, and the rate is that sample's.  Then
     the same oracle on one thread (`single_thread`): trace and shading of
-    about 1,024 probes of the next frame.
+    about 1,024 probes of the next frame."""
     from oracle import oracle as O
 
     threads = os.cpu_count() or 1
