@@ -50,3 +50,22 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
     args = type("A", (), dict(workload="box_room", seed=1, steps=1, warmup=3))()
     assert bench.run_reference(args) == 0
     assert capsys.readouterr().out == ""
+
+
+def test_cpu_baseline_reports_all_cores_and_one_thread():
+    # the oracle timed as it stands, on the small room workload: all host
+    # cores on whole updates, then one thread on a probe sample
+    pytest.importorskip("numpy")
+    if ROOT not in sys.path:
+        sys.path.insert(0, ROOT)
+    import bench
+    from paper_2301_05125_gb300 import scenegen as S
+
+    w = S.box_room(1)
+    args = type("A", (), dict(sampler=False, alpha=1.0, cpu_budget=2.0))()
+    rays = w.n_probes * w.volume["rays_avg"]
+    line = bench._cpu_baseline_line(w, rays, args)
+    assert line["kind"] == "oracle" and line["unit"] == "rays/s" and line["value"] > 0
+    assert line["cores"] == (os.cpu_count() or 1)
+    one = line["single_thread"]
+    assert one["cores"] == 1 and one["value"] > 0 and "one thread" in one["sample"]
